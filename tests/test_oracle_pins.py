@@ -1,0 +1,400 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the mathematics
+(closed forms, invariants, textbook limits, brute force, finite differences).
+
+Each test would fail for a plausible mistake in the oracle: a dropped Green-tensor
+term, a wrong sign of the imaginary unit or of the cross blocks, a transposed
+operand in the solve, a wrong self-term or polarisability normalisation, a wrong
+cross-section prefactor, or a wrong adjoint term.
+"""
+import cmath
+import math
+
+import numpy as np
+import pytest
+
+import gdm_workloads as W
+import oracle as O
+
+
+# ---------------------------------------------------------------- helpers written independently of the oracle
+def dipole_field_vector_form(r, rp, p, k, eps_env=1.0):
+    """Jackson-style vector form of the radiating electric dipole field (Gaussian units):
+    E = e^{ikR}/eps_env { k^2 (n x p) x n / R + [3 n (n.p) - p] (1/R^3 - ik/R^2) }.
+    Pure-Python loops on complex scalars."""
+    R = [r[a] - rp[a] for a in range(3)]
+    Rn = math.sqrt(sum(x * x for x in R))
+    n = [x / Rn for x in R]
+    ndp = sum(n[a] * p[a] for a in range(3))
+    nxp = [n[1] * p[2] - n[2] * p[1], n[2] * p[0] - n[0] * p[2], n[0] * p[1] - n[1] * p[0]]
+    nxpxn = [nxp[1] * n[2] - nxp[2] * n[1], nxp[2] * n[0] - nxp[0] * n[2], nxp[0] * n[1] - nxp[1] * n[0]]
+    ph = cmath.exp(1j * k * Rn) / eps_env
+    return [ph * (k * k * nxpxn[a] / Rn + (3 * n[a] * ndp - p[a]) * (1 / Rn ** 3 - 1j * k / Rn ** 2))
+            for a in range(3)]
+
+
+def gauss_full_pivot(A, b):
+    """Gaussian elimination with full pivoting on Python complex lists (brute force)."""
+    n = len(A)
+    M = [list(map(complex, A[i])) + [complex(b[i])] for i in range(n)]
+    perm = list(range(n))
+    for c in range(n):
+        best, bi, bj = -1.0, c, c
+        for i in range(c, n):
+            for j in range(c, n):
+                if abs(M[i][j]) > best:
+                    best, bi, bj = abs(M[i][j]), i, j
+        M[c], M[bi] = M[bi], M[c]
+        for row in M:
+            row[c], row[bj] = row[bj], row[c]
+        perm[c], perm[bj] = perm[bj], perm[c]
+        for i in range(c + 1, n):
+            f = M[i][c] / M[c][c]
+            for j in range(c, n + 1):
+                M[i][j] -= f * M[c][j]
+    x = [0j] * n
+    for i in range(n - 1, -1, -1):
+        s = M[i][n] - sum(M[i][j] * x[j] for j in range(i + 1, n))
+        x[i] = s / M[i][i]
+    out = [0j] * n
+    for c in range(n):
+        out[perm[c]] = x[c]
+    return out
+
+
+# ---------------------------------------------------------------- P2: single cell closed form
+@pytest.mark.parametrize("eps,eps_env", [(12.25 + 0j, 1.0), (4.0 + 1.5j, 1.0), (6.0 + 0.2j, 1.7)])
+def test_single_cell_internal_field(eps, eps_env):
+    """alpha = chi d^3/(4pi) with the cubic self-term gives the exact small-sphere
+    internal field 3 eps_env / (eps + 2 eps_env) E0 (self-term Eq. selfterm_SEp_cubic)."""
+    pr = O.Problem(np.zeros((1, 3)), 500.0, 3, eps=[eps], step=7.0, eps_env=eps_env)
+    F0 = pr.plane_wave(W.XYPOL)
+    F = pr.solve(F0)
+    np.testing.assert_allclose(F, 3 * eps_env / (eps + 2 * eps_env) * F0, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- P1: single dipole vs Mie
+@pytest.mark.parametrize("radius,eps", [(50.0, 12.25 + 0j), (80.0, 9.0 + 0j), (40.0, 4.0 + 0.3j)])
+def test_single_dipole_mie_crosssections(radius, eps):
+    """A lone ED/MD point dipole with the Mie polarisabilities of Sec. 'Effective
+    polarizabilities' reproduces Mie's dipole-order extinction (6 pi/k^2) Re(a1+b1)
+    and scattering (6 pi/k^2)(|a1|^2+|b1|^2)."""
+    lam = 620.0
+    k = 2 * np.pi / lam
+    ae, am = O.mie_dipole_alpha(radius, eps, lam)
+    al = np.zeros((1, 6, 6), complex)
+    al[0, :3, :3] = ae * np.eye(3)
+    al[0, 3:, 3:] = am * np.eye(3)
+    pr = O.Problem(np.zeros((1, 3)), lam, 6, alpha6=al)
+    F0 = pr.plane_wave(W.XYPOL)
+    F = pr.solve(F0)
+    np.testing.assert_allclose(F, F0, rtol=0, atol=0)          # zero self-term: F = F0
+    ext, sca, ab = pr.cross_sections(F0, F, W.XYPOL)
+    a, b = O.mie_coefficients(np.sqrt(eps), k * radius)
+    np.testing.assert_allclose(ext, 6 * np.pi / k ** 2 * np.real(a[0] + b[0]), rtol=1e-12)
+    np.testing.assert_allclose(sca, 6 * np.pi / k ** 2 * (abs(a[0]) ** 2 + abs(b[0]) ** 2), rtol=1e-10)
+    ff = pr.farfield_scattering(F, W.XYPOL, n_theta=24, n_phi=48)
+    np.testing.assert_allclose(ff, sca, rtol=1e-10)
+
+
+def test_single_electric_dipole_optical_theorem():
+    """p = alpha E0; sigma_ext = 4 pi k Im(alpha); far field sigma_sca = (8 pi/3) k^4 |alpha|^2."""
+    lam, alpha = 700.0, 3.0e5 + 2.0e5j
+    k = 2 * np.pi / lam
+    al = np.zeros((1, 6, 6), complex)
+    al[0, :3, :3] = alpha * np.eye(3)
+    pr = O.Problem(np.array([[3.0, -2.0, 5.0]]), lam, 6, alpha6=al)
+    F0 = pr.plane_wave(W.XPOL)
+    F = pr.solve(F0)
+    ext, sca, ab = pr.cross_sections(F0, F, W.XPOL)
+    np.testing.assert_allclose(ext, 4 * np.pi * k * alpha.imag, rtol=1e-13)
+    ff = pr.farfield_scattering(F, W.XPOL, n_theta=16, n_phi=32)
+    np.testing.assert_allclose(ff, 8 * np.pi / 3 * k ** 4 * abs(alpha) ** 2, rtol=1e-12)
+    np.testing.assert_allclose(ab, ext - ff, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- P3: dimer closed forms
+@pytest.mark.parametrize("axis,pol,kind", [(1, 0, "perp"), (0, 0, "par")])
+def test_dimer_closed_form(axis, pol, kind):
+    """Two identical cells at distance D in a plane of constant incident phase:
+    E = E0 / (1 - S alpha - g alpha), g_perp = e^{ikD}(k^2/D + ik/D^2 - 1/D^3),
+    g_par = 2 e^{ikD}(1/D^3 - ik/D^2)."""
+    lam, D, d, eps = 530.0, 23.0, 10.0, 9.0 + 0.4j
+    k = 2 * np.pi / lam
+    pos = np.zeros((2, 3))
+    pos[1, axis] = D
+    pr = O.Problem(pos, lam, 3, eps=[eps, eps], step=d)
+    e0 = np.zeros((1, 3), complex)
+    e0[0, pol] = 1.0
+    F = pr.solve(pr.plane_wave(e0))
+    alpha = (eps - 1) * d ** 3 / (4 * np.pi)
+    S = -4 * np.pi / (3 * d ** 3)
+    if kind == "perp":
+        g = cmath.exp(1j * k * D) * (k * k / D + 1j * k / D ** 2 - 1 / D ** 3)
+    else:
+        g = 2 * cmath.exp(1j * k * D) * (1 / D ** 3 - 1j * k / D ** 2)
+    E = 1.0 / (1 - S * alpha - g * alpha)
+    np.testing.assert_allclose(F[pol, 0], E, rtol=1e-13)
+    np.testing.assert_allclose(F[3 + pol, 0], E, rtol=1e-13)
+    other = [c for c in range(3) if c != pol]
+    assert np.max(np.abs(F[other, 0])) < 1e-14 and np.max(np.abs(F[[3 + c for c in other], 0])) < 1e-14
+
+
+# ---------------------------------------------------------------- P4: reciprocity
+def test_reciprocity_cells():
+    """G_ij = G_ji^T with symmetric 3x3 blocks: A is complex-symmetric for uniform alpha,
+    and alpha^{-1} - G is complex-symmetric in general."""
+    s = W.random_cells(20, seed=11)
+    pr = O.Problem(s.pos, 480.0, 3, eps=np.full(20, 7.0 + 0.3j), step=s.step)
+    A = pr.matrix()
+    np.testing.assert_allclose(A, A.T, rtol=0, atol=1e-15 * np.abs(A).max())
+    pr2 = O.Problem(s.pos, 480.0, 3, eps=s.eps, step=s.step)
+    A2 = pr2.matrix()
+    al = np.repeat(pr2.alpha, 3)
+    M = (A2 / al[None, :])                       # alpha^{-1} - G
+    np.testing.assert_allclose(M, M.T, rtol=0, atol=1e-14 * np.abs(M).max())
+
+
+def test_reciprocity_edmd():
+    """6x6 dyad: G(r_i,r_j)^T = P G(r_j,r_i) P with P = diag(I3, -I3)."""
+    rng = np.random.default_rng(3)
+    pos = rng.uniform(-300, 300, (5, 3))
+    pr = O.Problem(pos, 650.0, 6, alpha6=np.zeros((5, 6, 6)))
+    G = pr.coupling_blocks()
+    P = np.diag([1, 1, 1, -1, -1, -1.0])
+    for i in range(5):
+        for j in range(5):
+            np.testing.assert_allclose(G[i, j].T, P @ G[j, i] @ P, rtol=0, atol=1e-15 * np.abs(G[i, j]).max() + 1e-300)
+
+
+# ---------------------------------------------------------------- P5: Maxwell / Helmholtz by finite differences
+def _curl(fun, r, h):
+    """Curl by fourth-order central differences."""
+    J = np.zeros((3, 3), complex)      # J[a, b] = d f_a / d r_b
+    for b in range(3):
+        dp = np.zeros(3)
+        dp[b] = h
+        J[:, b] = (-fun(r + 2 * dp) + 8 * fun(r + dp) - 8 * fun(r - dp) + fun(r - 2 * dp)) / (12 * h)
+    return np.array([J[2, 1] - J[1, 2], J[0, 2] - J[2, 0], J[1, 0] - J[0, 1]])
+
+
+@pytest.mark.parametrize("Rvec", [(37.0, -12.0, 5.0), (400.0, 150.0, -900.0), (8.0, 9.0, -3.0)])
+def test_green_curl_relations(Rvec):
+    """H = (1/(i k0)) curl E for the electric dipole (G^Hp from G^Ep), and, by duality,
+    E = -(1/(i k0)) curl H for the magnetic dipole (G^Em from G^Hm)."""
+    lam = 520.0
+    k0, k = O.wavenumbers(lam)
+    p = np.array([0.3 - 0.2j, 1.0, -0.7 + 0.1j])
+    R = np.array(Rvec)
+    h = 1e-3 * np.linalg.norm(R)
+    E = lambda r: O.green_ep(r, k) @ p
+    ref = O.green_hp(R, k0, k) @ p
+    np.testing.assert_allclose(_curl(E, R, h) / (1j * k0), ref, rtol=0, atol=1e-7 * np.abs(ref).max())
+    G6 = lambda r: O.green6(r, k0, k)
+    m = p
+    Hm = lambda r: G6(r)[3:, 3:] @ m
+    ref = G6(R)[:3, 3:] @ m
+    np.testing.assert_allclose(-_curl(Hm, R, h) / (1j * k0), ref, rtol=0, atol=1e-7 * np.abs(ref).max())
+
+
+def test_green_helmholtz_and_textbook_form():
+    """(lap + k^2) G^Ep p = 0 away from the source; G^Ep p equals the vector-form dipole
+    field written out on scalars; Im G^Ep(R -> 0) -> (2/3) k^3 I (radiation reaction)."""
+    lam, eps_env = 600.0, 2.0
+    k0, k = O.wavenumbers(lam, eps_env)
+    p = np.array([1.0 + 0.5j, -0.4, 0.2j])
+    for R in ([55.0, -20.0, 31.0], [700.0, 10.0, -250.0]):
+        R = np.array(R)
+        ref = dipole_field_vector_form(R, [0, 0, 0], list(p), k, eps_env)
+        np.testing.assert_allclose(O.green_ep(R, k, eps_env) @ p, ref, rtol=1e-13)
+        Rn = np.linalg.norm(R)
+        h = 1e-2 * Rn
+        f = lambda r: O.green_ep(r, k, eps_env) @ p
+        lap = sum((-f(R + 2 * h * e) + 16 * f(R + h * e) - 30 * f(R) + 16 * f(R - h * e) - f(R - 2 * h * e))
+                  / (12 * h * h) for e in np.eye(3))
+        scale = np.abs(f(R)).max() * (k * k + 1.0 / Rn ** 2)     # size of the individual terms
+        np.testing.assert_allclose(lap + k * k * f(R), 0, atol=1e-6 * scale)
+    Gs = O.green_ep(np.array([1e-3, 2e-3, -1e-3]), k, 1.0)
+    np.testing.assert_allclose(np.imag(Gs), 2.0 / 3.0 * k ** 3 * np.eye(3), rtol=0, atol=1e-6 * k ** 3)
+
+
+# ---------------------------------------------------------------- P6: energy identities and optical theorem
+@pytest.mark.parametrize("lossy", [False, True])
+def test_energy_identity_cells(lossy):
+    """sigma_ext - sigma_abs = c p^H Im(G) p exactly for the solved system, and the far-field
+    integral equals c [p^H Im(G) p + (2/3) k^3 sum |p|^2] (radiative term the cell alpha lacks).
+    Lossless eps gives sigma_abs = 0."""
+    s = W.random_cells(40, seed=21, lossy=lossy)
+    pr = O.Problem(s.pos, 560.0, 3, eps=s.eps, step=s.step)
+    F0 = pr.plane_wave(W.XYPOL)
+    F = pr.solve(F0)
+    ext, sca, ab = pr.cross_sections(F0, F, W.XYPOL)
+    P = pr.moments(F)
+    G = pr.coupling_blocks().transpose(0, 2, 1, 3).reshape(3 * pr.n, 3 * pr.n)
+    c = 4 * np.pi * pr.k
+    pImGp = np.real(np.einsum("ir,ij,jr->r", P.conj(), G.imag, P))
+    np.testing.assert_allclose(sca, c * pImGp, rtol=1e-9)
+    rad = 2.0 / 3.0 * pr.k ** 3 * np.sum(np.abs(P) ** 2, axis=0)
+    ff = pr.farfield_scattering(F, W.XYPOL, n_theta=48, n_phi=96)
+    np.testing.assert_allclose(ff, c * (pImGp + rad), rtol=1e-9)
+    if not lossy:
+        assert np.max(np.abs(ab)) < 1e-12 * np.max(ext)
+
+
+def test_optical_theorem_edmd_lorentz():
+    """Radiatively dressed Lorentzian ED/MD dipoles (zero self-term): sigma_ext =
+    sigma_sca(far field) + sigma_abs to quadrature accuracy."""
+    ms = W.metasurface_edmd(nx=3, ny=2, pitch=400.0, n_lambda=1)
+    lam = 610.0
+    al = O.lorentz_alpha6(ms.omega0_e, ms.omega0_m, ms.gamma_ev, ms.amp_nm, lam)
+    pr = O.Problem(ms.pos, lam, 6, alpha6=al)
+    F0 = pr.plane_wave(W.XYPOL)
+    F = pr.solve(F0)
+    ext, sca, ab = pr.cross_sections(F0, F, W.XYPOL)
+    ff = pr.farfield_scattering(F, W.XYPOL, n_theta=96, n_phi=192)
+    np.testing.assert_allclose(sca, ff, rtol=1e-8)
+    assert np.all(ab > 0)
+
+
+# ---------------------------------------------------------------- P7: Mie convergence of the discretised sphere
+def _sphere_error(eps, d, lam=600.0):
+    pos = W.sphere_cells(60.0, d)
+    n = len(pos)
+    pr = O.Problem(pos, lam, 3, eps=np.full(n, eps), step=d)
+    F0 = pr.plane_wave(W.XPOL)
+    ext, sca, ab = pr.cross_sections(F0, pr.solve(F0), W.XPOL)
+    aeq = (3 * n * d ** 3 / (4 * np.pi)) ** (1 / 3)      # equal-volume sphere
+    me, ms = O.mie_cross_sections(aeq, eps, lam)
+    return (ext[0] - me) / me, (sca[0] - ms) / ms, (ab[0] - (me - ms)) / (me - ms) if eps.imag else 0.0
+
+
+def test_mie_convergence_lossy_sphere():
+    """The discretised sphere converges to Mie theory as the mesh is refined (errors
+    shrink monotonically from d = 20 to 10 to 7.5 nm; percent level, cf. Sec. 'Mie comparison')."""
+    errs = [np.abs(_sphere_error(4.0 + 1.0j, d)) for d in (20.0, 10.0, 7.5)]
+    for a, b in zip(errs, errs[1:]):
+        assert np.all(b < a)
+    assert np.all(errs[-1] < 0.03)
+
+
+def test_mie_agreement_low_and_high_index():
+    assert abs(_sphere_error(2.25 + 0j, 10.0)[0]) < 0.015
+    e20 = abs(_sphere_error(12.25 + 0j, 20.0)[0])
+    e10 = abs(_sphere_error(12.25 + 0j, 10.0)[0])
+    assert e10 < e20 and e10 < 0.07
+
+
+def test_mie_series_limits():
+    """The Mie code itself: Rayleigh limit Q_ext = 4x Im K + ..., Q_sca = (8/3) x^4 |K|^2,
+    K = (m^2-1)/(m^2+2); extinction paradox Q_ext -> 2 for large x; Q_ext = Q_sca for real m."""
+    lam, a = 1000.0, 1.0
+    eps = 3.0 + 0.5j
+    x = 2 * np.pi * a / lam
+    K = (eps - 1) / (eps + 2)
+    ext, sca = O.mie_cross_sections(a, eps, lam)
+    np.testing.assert_allclose(ext / (np.pi * a * a), 4 * x * K.imag, rtol=1e-3)
+    np.testing.assert_allclose(sca / (np.pi * a * a), 8 / 3 * x ** 4 * abs(K) ** 2, rtol=1e-3)
+    ext, sca = O.mie_cross_sections(20000.0, 2.0 + 0.0j, 500.0)
+    assert abs(ext / (np.pi * 20000.0 ** 2) - 2.0) < 0.04
+    np.testing.assert_allclose(ext, sca, rtol=1e-10)
+
+
+# ---------------------------------------------------------------- P8: brute force on tiny inputs
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_bruteforce_tiny(n):
+    """Dense matrix built entry by entry from the vector-form field and the stated
+    alpha/self-term, solved by full-pivot Gaussian elimination on Python complex numbers."""
+    s = W.random_cells(n, seed=100 + n)
+    lam = 510.0
+    k = 2 * np.pi / lam
+    d = s.step
+    alpha = [(e - 1) * d ** 3 / (4 * math.pi) for e in s.eps]
+    S = -4 * math.pi / (3 * d ** 3)
+    A = [[0j] * (3 * n) for _ in range(3 * n)]
+    for i in range(n):
+        for j in range(n):
+            for b in range(3):
+                pcol = [0.0, 0.0, 0.0]
+                pcol[b] = 1.0
+                if i == j:
+                    g = [S * pcol[a] for a in range(3)]
+                else:
+                    g = dipole_field_vector_form(list(s.pos[i]), list(s.pos[j]), pcol, k)
+                for a in range(3):
+                    A[3 * i + a][3 * j + b] = (1.0 if (i == j and a == b) else 0.0) - g[a] * alpha[j]
+    pr = O.Problem(s.pos, lam, 3, eps=s.eps, step=d)
+    np.testing.assert_allclose(pr.matrix(), np.array(A), rtol=1e-13, atol=1e-15)
+    F0 = pr.plane_wave(W.XYPOL)
+    F = pr.solve(F0)
+    for r in range(2):
+        x = gauss_full_pivot(A, list(F0[:, r]))
+        np.testing.assert_allclose(F[:, r], x, rtol=1e-12)
+
+
+def test_residual_rows_definition():
+    s = W.random_cells(30, seed=9)
+    pr = O.Problem(s.pos, 600.0, 3, eps=s.eps, step=s.step)
+    F0 = pr.plane_wave(W.XYPOL)
+    F = pr.solve(F0)
+    rows = [0, 7, 29]
+    assert np.abs(O.residual_rows(pr, F0, F, rows)).max() < 1e-12
+    np.testing.assert_allclose(O.residual_rows(pr, F0, np.zeros_like(F), rows),
+                               F0.reshape(30, 3, 2)[rows], rtol=0, atol=0)
+
+
+def test_plane_wave():
+    r = np.array([[0, 0, 0], [10.0, -3, 125.0]])
+    k = 2 * np.pi / 400.0
+    F = O.plane_wave(r, k, 1.0, W.XYPOL, (0, 0, 1.0), 6).reshape(2, 6, 2)
+    np.testing.assert_allclose(F[1, :3, 0], [cmath.exp(1j * k * 125.0), 0, 0])
+    np.testing.assert_allclose(F[1, 3:, 0], [0, cmath.exp(1j * k * 125.0), 0])      # H0 = z x x = y
+    np.testing.assert_allclose(F[1, 3:, 1], [-cmath.exp(1j * k * 125.0), 0, 0])     # z x y = -x
+
+
+# ---------------------------------------------------------------- P9: adjoint gradients vs central differences
+def test_adjoint_gradient_vs_fd():
+    """Adjoint gradient of L = |E(r_probe)|^2 + sum sigma_sca w.r.t. positions, per-cell eps
+    and the wavelength, against central finite differences (h = 1e-4) on seeded directions."""
+    cyl = W.cylinder_diff(radius=20.0, height=20.0, step=10.0)
+    rng = np.random.default_rng(5)
+    eps = cyl.eps + rng.uniform(-0.5, 0.5, cyl.n)
+    lam = 610.0
+    rp = cyl.r_eval[0]
+
+    def L(pos=cyl.pos, e=eps, lm=lam):
+        return O.probe_sca_loss(O.Problem(pos, lm, 3, eps=e, step=cyl.step), cyl.e0, rp)
+
+    L0, gpos, geps, glam = O.loss_and_grad_probe_sca(O.Problem(cyl.pos, lam, 3, eps=eps, step=cyl.step), cyl.e0, rp)
+    assert abs(L0 - L()) < 1e-12 * abs(L0)
+    h = 1e-4
+    for _ in range(4):
+        v = rng.standard_normal(cyl.pos.shape)
+        fd = (L(pos=cyl.pos + h * v) - L(pos=cyl.pos - h * v)) / (2 * h)
+        np.testing.assert_allclose(np.sum(gpos * v), fd, rtol=1e-5)
+        w = rng.standard_normal(cyl.n) + 1j * rng.standard_normal(cyl.n)
+        fd = (L(e=eps + h * w) - L(e=eps - h * w)) / (2 * h)
+        np.testing.assert_allclose(np.sum(np.real(np.conj(geps) * w)), fd, rtol=1e-5)
+    fd = (L(lm=lam + h) - L(lm=lam - h)) / (2 * h)
+    np.testing.assert_allclose(glam, fd, rtol=1e-5)
+
+
+def test_linearity_in_incident_field():
+    s = W.random_cells(15, seed=2)
+    pr = O.Problem(s.pos, 450.0, 3, eps=s.eps, step=s.step)
+    F0 = pr.plane_wave(W.XYPOL)
+    F = pr.solve(F0)
+    Fc = pr.solve(F0 @ np.array([[2.0 - 1j], [0.5j]]))
+    np.testing.assert_allclose(Fc[:, 0], F @ np.array([2.0 - 1j, 0.5j]), rtol=1e-12)
+
+
+def test_workload_shapes():
+    assert W.sphere_plain_fp64().n == 925
+    assert W.sphere_plain_fp64().r_eval.shape == (968, 3)
+    assert W.cuboid_precision().n == 12000
+    assert W.metasurface_edmd().n == 4096
+    b = W.blob_batch(n_struct=4)
+    for s in b:
+        # face-connected: every cell but the first has a face neighbour among the cells
+        cells = {tuple(np.round(p / s.step).astype(int)) for p in s.pos}
+        for c in cells:
+            assert any((c[0] + dx, c[1] + dy, c[2] + dz) in cells
+                       for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)))
