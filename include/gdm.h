@@ -1,0 +1,206 @@
+/*
+ * gdm.h -- C ABI of the GB300 (sm_103a) Green's Dyadic Method hot path.
+ *
+ * The library solves the discretised Lippmann-Schwinger equation of the
+ * coupled-dipole / Green's Dyadic Method (Wiecha et al., "TorchGDM",
+ * arXiv:2505.09545, Sec. "Formalism and implementation"):
+ *
+ *     F_i = F0_i + sum_j G(r_i, r_j) alpha_j F_j          (Eq. LPS_6by6_discrete)
+ *     sum_j [delta_ij I - G(r_i, r_j) alpha_j] F_j = F0_i  (Eq. GDM_system_of_equations,
+ *                                                         read without the stray F(r_j))
+ *
+ * for every illumination, then evaluates near fields and cross sections from
+ * the self-consistent dipoles (Sec. "Observables") and gradients through the
+ * solve (Sec. "Numerical solution", automatic differentiation of the LU solve).
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * Units: Gaussian (cgs) as in the paper, lengths and wavelengths in nm. Time
+ *   factor exp(-i w t): outgoing waves are exp(+ikR), lossy media have Im(eps) > 0.
+ * Complex numbers are stored interleaved (re, im): complex128 = 2 doubles,
+ *   complex64 = 2 floats.
+ * Unknowns are dipole-interleaved: index kind*i + c, with kind = 3 (E of cell i,
+ *   c = x,y,z) or kind = 6 (E then H of effective dipole i). The paper orders all
+ *   E before all H (Sec. "Hybrid discretization GDM"); this is a permutation of it.
+ * Matrices are column-major with a leading dimension `lda` (complex elements):
+ *   entry (row, col) at A[col*lda + row]. Right-hand sides / fields are
+ *   (kind*n) x n_rhs column-major with leading dimension kind*n.
+ * Memory: every pointer documented as "device" is caller-owned device memory on
+ *   the context's device; "host" pointers are ordinary host memory. The library
+ *   never frees caller memory. The context owns only its scratch space.
+ * Streams: every call is enqueued on the context's stream and returns without
+ *   waiting for the GPU, unless documented otherwise. The returned status covers
+ *   argument validation and launch errors; errors found on the device (a zero
+ *   pivot, a refinement that did not converge, a bounded device wait that ran
+ *   out) are reported through gdm_solve_info and gdm_ctx_check().
+ * Errors: no call aborts or exits. On failure the call returns a non-zero
+ *   gdm_status and gdm_last_error() holds a one-line message.
+ */
+#ifndef GDM_H
+#define GDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GDM_OK = 0,
+    GDM_ERR_INVALID_ARG = 1,   /* null pointer, bad kind/precision, non-positive size */
+    GDM_ERR_SHAPE = 2,         /* lda too small, misaligned leading dimension */
+    GDM_ERR_NONFINITE = 3,     /* NaN/Inf found in an input or produced by the solve */
+    GDM_ERR_SINGULAR = 4,      /* exactly zero pivot in the LU factorisation */
+    GDM_ERR_NOT_CONVERGED = 5, /* iterative refinement did not reach the tolerance */
+    GDM_ERR_OOM = 6,           /* scratch allocation failed */
+    GDM_ERR_CUDA = 7,          /* CUDA runtime / driver error */
+    GDM_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up */
+    GDM_ERR_UNSUPPORTED = 9    /* valid request that this build does not implement */
+} gdm_status;
+
+/* Arithmetic of the factorisation. All modes return FP64 fields.
+ * GDM_FP64        : complex128 matrix, FP64 LU and triangular solves (the plain path).
+ * GDM_FP32        : complex64 matrix, LU with FP32-accurate tensor-core trailing
+ *                   updates (TF32 hi/lo split, three products), FP64 refinement.
+ * GDM_TF32_REFINE : complex64 matrix, LU with single-pass TF32 tensor-core
+ *                   trailing updates, FP64 refinement. */
+typedef enum { GDM_FP64 = 0, GDM_FP32 = 1, GDM_TF32_REFINE = 2 } gdm_precision;
+
+typedef struct gdm_ctx gdm_ctx;
+
+/* One scattering problem at one wavelength.
+ * kind 3: discretised cubic cells, electric response only. alpha_i =
+ *   (eps_i - eps_env) d^3 / (4 pi) (Sec. "Volume discretization polarizabilities"),
+ *   self-term S = -I 4 pi / (3 eps_env d^3) (Eq. selfterm_SEp_cubic).
+ * kind 6: effective electric/magnetic point dipoles with full 6x6 polarisability
+ *   alpha_i (dipole-moment relation (p, m) = alpha F), zero self-term; vacuum only. */
+typedef struct {
+    int64_t n;              /* number of dipoles (cells or effective dipoles), >= 1 */
+    int32_t kind;           /* 3 or 6 */
+    int32_t reserved;
+    const double *pos;      /* device, n x 3 row-major (x, y, z), nm */
+    const double *eps;      /* kind 3: device, n complex128 cell permittivities; else NULL */
+    const double *alpha6;   /* kind 6: device, n x 6 x 6 complex128, row-major per dipole; else NULL */
+    double step;            /* kind 3: cubic mesh step d (nm), > 0; ignored for kind 6 */
+    double eps_env;         /* real host permittivity, > 0 (kind 6: must be 1) */
+    double wavelength;      /* vacuum wavelength lambda0 (nm), > 0 */
+} gdm_problem;
+
+/* Refinement controls for gdm_solve. Zero-initialised => defaults. */
+typedef struct {
+    int32_t max_iter;       /* refinement steps allowed (default 40; FP64: default 3) */
+    int32_t flags;          /* GDM_SOLVE_* bit flags */
+    double tol;             /* stop when max_r ||dF_r|| / ||F_r|| <= tol (default 1e-12) */
+} gdm_solve_opts;
+
+#define GDM_SOLVE_FACTORED 1  /* A already holds this problem's factors and ipiv its pivots */
+#define GDM_SOLVE_NO_REFINE 2 /* return the plain triangular-solve result */
+
+typedef struct {
+    int32_t iterations;          /* refinement steps taken */
+    int32_t status;              /* gdm_status of the device-side checks */
+    double rel_correction;       /* last max_r ||dF_r|| / ||F_r|| */
+    double rel_residual;         /* last max_r ||F0_r - A F_r|| / ||F0_r|| (FP64, matrix-free) */
+    double factor_ms;            /* device time of the factorisation (0 if skipped) */
+    double refine_ms;            /* device time of solves + refinement */
+} gdm_solve_info;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`; `stream` is a cudaStream_t (NULL =
+ * the legacy default stream). Allocates nothing until a call needs scratch. */
+gdm_status gdm_create(gdm_ctx **ctx, int device, void *stream);
+gdm_status gdm_destroy(gdm_ctx *ctx);
+gdm_status gdm_set_stream(gdm_ctx *ctx, void *stream);
+/* Waits for the context's stream, then returns the first device-side error
+ * recorded since the last check (GDM_OK if none) and clears it. */
+gdm_status gdm_ctx_check(gdm_ctx *ctx);
+const char *gdm_status_string(gdm_status s);
+const char *gdm_last_error(gdm_ctx *ctx);
+/* Number of kernel launches this context has issued so far. */
+int64_t gdm_launch_count(gdm_ctx *ctx);
+
+/* Scratch bytes a gdm_solve / gdm_backward of this problem will hold in the
+ * context (pivot-independent panel buffers, tensor-core operand copies,
+ * refinement vectors). */
+gdm_status gdm_workspace_size(const gdm_problem *p, int n_rhs, gdm_precision prec, size_t *bytes);
+
+/* ---------------------------------------------------------------- illumination */
+
+/* Plane wave E0(r) = e0 exp(i k khat.r), H0 = n_env khat x E0, k = n_env 2 pi / lambda0,
+ * at m points. r: device m x 3. e0: host n_rhs x 3 complex128 amplitudes.
+ * khat: host 3 doubles, unit propagation direction. kind_out = 3 writes E only,
+ * 6 writes (E, H) per point. F0: device (kind_out*m) x n_rhs complex128. */
+gdm_status gdm_incident_planewave(gdm_ctx *ctx, const double *r, int64_t m, double wavelength,
+                                  double eps_env, const double *e0, const double *khat, int n_rhs,
+                                  int kind_out, double *F0);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* Assemble the dense system matrix A = I - G alpha (Eq. GDM_system_of_equations):
+ * block (i, j) = delta_ij I - G(r_i, r_j) alpha_j, with G(r_i, r_i) the self-term.
+ * prec GDM_FP64 writes complex128, otherwise complex64. A: device, column-major,
+ * (kind*n) x (kind*n), lda >= kind*n complex elements, lda even. */
+gdm_status gdm_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda);
+
+/* Factor A in place (blocked LU with partial pivoting; complex128 for GDM_FP64,
+ * complex64 otherwise) unless opts->flags has GDM_SOLVE_FACTORED, then solve
+ * A F = F0 for n_rhs right-hand sides and refine in FP64 with the residual
+ * F0 - A F computed matrix-free from the Green dyads (no stored FP64 matrix).
+ * A: device matrix from gdm_assemble (overwritten by its LU factors).
+ * ipiv: device int32 array of kind*n pivots (written, or read when FACTORED).
+ * F0: device (kind*n) x n_rhs complex128. F: device output, same shape.
+ * info: host, may be NULL. Synchronises the stream when info != NULL. */
+gdm_status gdm_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda,
+                     int32_t *ipiv, const double *F0, double *F, int n_rhs, const gdm_solve_opts *opts,
+                     gdm_solve_info *info);
+
+/* Near field by repropagation (Sec. "Observables"): at m points r_eval (device,
+ * m x 3, none on a dipole), E = E0 + sum_j [G^Ep p_j + G^Em m_j] and
+ * H = H0 + sum_j [G^Hp p_j + G^Hm m_j] with (p, m)_j = alpha_j F_j.
+ * F: device solved fields (kind*n) x n_rhs complex128. F0_eval: device (6*m) x n_rhs
+ * incident (E, H) at r_eval, or NULL for scattered fields only. E_out, H_out:
+ * device (3*m) x n_rhs complex128; H_out may be NULL. */
+gdm_status gdm_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, const double *r_eval,
+                         int64_t m, const double *F0_eval, int n_rhs, double *E_out, double *H_out);
+
+/* Cross sections (nm^2) per illumination, FP64:
+ *   ext = 4 pi k / (eps_env |E0|^2) sum_i Im(E0_i^* . p_i + H0_i^* . m_i)
+ *   abs = 4 pi k / (eps_env |E0|^2) sum_i Im(E_i^* . p_i)                      (kind 3)
+ *   abs = 4 pi k / |E0|^2 sum_i [Im(E_i^*.p_i) - 2/3 k^3 |p_i|^2
+ *                                + Im(H_i^*.m_i) - 2/3 k^3 |m_i|^2]            (kind 6)
+ *   sca = ext - abs.
+ * F0, F: device (kind*n) x n_rhs complex128. e0_norm2: host n_rhs values |E0|^2.
+ * ext, sca, abs: device n_rhs doubles each (any may be NULL). */
+gdm_status gdm_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,
+                              int n_rhs, const double *e0_norm2, double *ext, double *sca, double *abs);
+
+/* Adjoint backward of gdm_solve + gdm_cross_sections for plane-wave illumination
+ * (kind 3). Given the upstream gradient gF = dL/dF^* (device (3n) x n_rhs
+ * complex128, conjugate Wirtinger derivative, may be NULL) and g_sigma (host
+ * n_rhs x 3: dL/d(ext, sca, abs), may be NULL), solves A^H mu = g with the
+ * factors held in A/ipiv (FP64-refined, matrix-free A^H residual), then ADDS to
+ *   grad_pos  (device n x 3)        dL/dr
+ *   grad_eps  (device n complex128) dL/dRe(eps) + i dL/dIm(eps)
+ *   grad_wavelength (device 1 double) dL/dlambda0
+ * (each may be NULL). e0: host n_rhs x 3 complex128, khat: host 3 doubles, the
+ * plane waves that produced F0. info: host, may be NULL. */
+gdm_status gdm_backward(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
+                        const int32_t *ipiv, const double *F, int n_rhs, const double *e0, const double *khat,
+                        const double *gF, const double *g_sigma, double *grad_pos, double *grad_eps,
+                        double *grad_wavelength, gdm_solve_info *info);
+
+/* Backward of gdm_nearfield for plane-wave illumination (kind 3): given
+ * gE = dL/dE_out^* (device (3m) x n_rhs complex128), ADDS the explicit
+ * contributions to grad_pos, grad_eps, grad_wavelength (as in gdm_backward) and
+ * ADDS dL/dF^* to gF_accum (device (3n) x n_rhs complex128), to be passed on to
+ * gdm_backward. Any output may be NULL. */
+gdm_status gdm_nearfield_backward(gdm_ctx *ctx, const gdm_problem *p, const double *F, const double *r_eval,
+                                  int64_t m, int n_rhs, const double *e0, const double *khat, const double *gE,
+                                  double *gF_accum, double *grad_pos, double *grad_eps, double *grad_wavelength);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GDM_H */

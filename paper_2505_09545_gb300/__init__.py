@@ -1,0 +1,9 @@
+"""GB300-native (sm_103a) Green's Dyadic Method hot path.
+
+The compute lives in the CUDA library libgdm.so (C ABI: include/gdm.h); this
+package only builds/loads it and marshals arguments (see `binding`)."""
+from .binding import (Context, GDMError, GDMProblem, assemble, backward, cross_sections, incident_planewave, lib,
+                      nearfield, nearfield_backward, padded_lda, solve)
+
+__all__ = ["Context", "GDMError", "GDMProblem", "assemble", "backward", "cross_sections", "incident_planewave",
+           "lib", "nearfield", "nearfield_backward", "padded_lda", "solve"]

@@ -1,0 +1,301 @@
+"""Thin ctypes binding of the GDM C ABI (include/gdm.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA library.
+PyTorch provides device memory and the current CUDA stream. The functions keep
+the C names (without the ``gdm_`` prefix) and raise ``GDMError`` on a non-OK status.
+
+Tensor layouts (column-major C arrays seen from torch):
+* fields / right-hand sides: torch tensor (n_rhs, kind*m) complex128 -- row q is
+  column q of the C array;
+* system matrix: torch tensor (n_cols, lda) complex64/complex128 -- row j is column j.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import _build
+
+GDM_OK = 0
+STATUS = {0: "GDM_OK", 1: "GDM_ERR_INVALID_ARG", 2: "GDM_ERR_SHAPE", 3: "GDM_ERR_NONFINITE", 4: "GDM_ERR_SINGULAR",
+          5: "GDM_ERR_NOT_CONVERGED", 6: "GDM_ERR_OOM", 7: "GDM_ERR_CUDA", 8: "GDM_ERR_TIMEOUT",
+          9: "GDM_ERR_UNSUPPORTED"}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2}
+SOLVE_FACTORED = 1
+SOLVE_NO_REFINE = 2
+
+
+class GDMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Problem(C.Structure):
+    _fields_ = [("n", C.c_int64), ("kind", C.c_int32), ("reserved", C.c_int32), ("pos", C.c_void_p),
+                ("eps", C.c_void_p), ("alpha6", C.c_void_p), ("step", C.c_double), ("eps_env", C.c_double),
+                ("wavelength", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("flags", C.c_int32), ("tol", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("rel_correction", C.c_double),
+                ("rel_residual", C.c_double), ("factor_ms", C.c_double), ("refine_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+P = C.c_void_p
+I64 = C.c_int64
+D = C.c_double
+PD = C.POINTER(C.c_double)
+_SIGS = {
+    "gdm_create": ([C.POINTER(C.c_void_p), C.c_int, P], C.c_int),
+    "gdm_destroy": ([P], C.c_int),
+    "gdm_set_stream": ([P, P], C.c_int),
+    "gdm_ctx_check": ([P], C.c_int),
+    "gdm_status_string": ([C.c_int], C.c_char_p),
+    "gdm_last_error": ([P], C.c_char_p),
+    "gdm_launch_count": ([P], I64),
+    "gdm_workspace_size": ([C.POINTER(Problem), C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+    "gdm_incident_planewave": ([P, P, I64, D, D, PD, PD, C.c_int, C.c_int, P], C.c_int),
+    "gdm_assemble": ([P, C.POINTER(Problem), C.c_int, P, I64], C.c_int),
+    "gdm_solve": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, P, C.c_int, C.POINTER(SolveOpts),
+                   C.POINTER(SolveInfo)], C.c_int),
+    "gdm_nearfield": ([P, C.POINTER(Problem), P, P, I64, P, C.c_int, P, P], C.c_int),
+    "gdm_cross_sections": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
+    "gdm_backward": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, C.c_int, PD, PD, P, PD, P, P, P,
+                      C.POINTER(SolveInfo)], C.c_int),
+    "gdm_nearfield_backward": ([P, C.POINTER(Problem), P, P, I64, C.c_int, PD, PD, P, P, P, P, P], C.c_int),
+}
+
+
+def lib():
+    """Load libgdm.so (building it first if the sources are newer). Raises if it cannot be loaded:
+    there is no fallback path."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"GDM CUDA library missing at {path}")
+            L = C.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return C.c_void_p(0) if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dbl_array(x):
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return a, a.ctypes.data_as(PD)
+
+
+class Context:
+    """A library context bound to one CUDA device; calls run on torch's current stream."""
+
+    def __init__(self, device=None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = lib().gdm_create(C.byref(h), self.device.index or 0,
+                                  C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+        if st != GDM_OK:
+            raise GDMError(st, "gdm_create failed")
+        self.h = h
+
+    def _sync_stream(self):
+        lib().gdm_set_stream(self.h, C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+
+    def _check(self, st, what):
+        if st != GDM_OK:
+            raise GDMError(st, f"{what}: {lib().gdm_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gdm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self):
+        """Synchronise and raise on device-side errors recorded since the last check."""
+        self._check(lib().gdm_ctx_check(self.h), "device check")
+
+    @property
+    def launches(self):
+        return int(lib().gdm_launch_count(self.h))
+
+
+class GDMProblem:
+    """Device-resident description of one problem (keeps its tensors alive)."""
+
+    def __init__(self, pos, wavelength, kind=3, eps=None, step=0.0, alpha6=None, eps_env=1.0):
+        self.pos = pos.contiguous()
+        assert self.pos.dtype == torch.float64 and self.pos.is_cuda and self.pos.shape[-1] == 3
+        self.kind = int(kind)
+        self.eps = None if eps is None else eps.contiguous()
+        self.alpha6 = None if alpha6 is None else alpha6.contiguous()
+        if self.eps is not None:
+            assert self.eps.dtype == torch.complex128 and self.eps.is_cuda
+        if self.alpha6 is not None:
+            assert self.alpha6.dtype == torch.complex128 and self.alpha6.is_cuda
+        self.step = float(step)
+        self.eps_env = float(eps_env)
+        self.wavelength = float(wavelength)
+        self.n = int(self.pos.shape[0])
+
+    @property
+    def size(self):
+        return self.kind * self.n
+
+    def struct(self):
+        return Problem(self.n, self.kind, 0, self.pos.data_ptr(), 0 if self.eps is None else self.eps.data_ptr(),
+                       0 if self.alpha6 is None else self.alpha6.data_ptr(), self.step, self.eps_env,
+                       self.wavelength)
+
+
+def padded_lda(n_sys):
+    return (n_sys + 31) // 32 * 32
+
+
+def incident_planewave(ctx: Context, r, wavelength, e0, khat=(0.0, 0.0, 1.0), eps_env=1.0, kind_out=3):
+    """F0 at points r (device (m,3) f64): returns (n_rhs, kind_out*m) complex128."""
+    e0 = np.atleast_2d(np.asarray(e0, np.complex128))
+    n_rhs = e0.shape[0]
+    ea, ep = _dbl_array(e0.view(np.float64).reshape(-1))
+    ka, kp = _dbl_array(khat)
+    r = r.contiguous()
+    out = torch.empty((n_rhs, kind_out * r.shape[0]), dtype=torch.complex128, device=r.device)
+    ctx._sync_stream()
+    ctx._check(lib().gdm_incident_planewave(ctx.h, _ptr(r), r.shape[0], float(wavelength), float(eps_env), ep, kp,
+                                            n_rhs, kind_out, _ptr(out)), "gdm_incident_planewave")
+    return out
+
+
+def assemble(ctx: Context, prob: GDMProblem, precision="fp32", lda=None, out=None):
+    """A = I - G alpha, column-major: returns torch (n_sys, lda) complex64 (complex128 for fp64)."""
+    ns = prob.size
+    lda = padded_lda(ns) if lda is None else lda
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    if out is None:
+        out = torch.empty((ns, lda), dtype=dt, device=prob.pos.device)
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_assemble(ctx.h, C.byref(s), PRECISION[precision], _ptr(out), lda), "gdm_assemble")
+    return out
+
+
+def solve(ctx: Context, prob: GDMProblem, A, F0, precision="fp32", ipiv=None, factored=False, max_iter=0, tol=0.0,
+          no_refine=False, info=True, F=None):
+    """Factor A in place (unless factored) and solve A F = F0 with FP64 refinement.
+    F0: (n_rhs, n_sys) complex128. Returns (F, ipiv, info dict or None)."""
+    ns = prob.size
+    lda = A.shape[1]
+    if ipiv is None:
+        ipiv = torch.empty(ns, dtype=torch.int32, device=A.device)
+    if F is None:
+        F = torch.empty_like(F0)
+    n_rhs = F0.shape[0]
+    flags = (SOLVE_FACTORED if factored else 0) | (SOLVE_NO_REFINE if no_refine else 0)
+    opts = SolveOpts(int(max_iter), flags, float(tol))
+    inf = SolveInfo() if info else None
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_solve(ctx.h, C.byref(s), PRECISION[precision], _ptr(A), lda, _ptr(ipiv), _ptr(F0.contiguous()),
+                               _ptr(F), n_rhs, C.byref(opts), C.byref(inf) if info else None), "gdm_solve")
+    return F, ipiv, (inf.as_dict() if info else None)
+
+
+def nearfield(ctx: Context, prob: GDMProblem, F, r_eval, F0_eval=None, with_h=True):
+    """E (and H) at r_eval: returns (E, H) each (n_rhs, 3*m) complex128 (H None if not requested)."""
+    n_rhs = F.shape[0]
+    m = r_eval.shape[0]
+    E = torch.empty((n_rhs, 3 * m), dtype=torch.complex128, device=F.device)
+    H = torch.empty_like(E) if with_h else None
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_nearfield(ctx.h, C.byref(s), _ptr(F.contiguous()), _ptr(r_eval.contiguous()), m,
+                                   _ptr(None if F0_eval is None else F0_eval.contiguous()), n_rhs, _ptr(E), _ptr(H)),
+               "gdm_nearfield")
+    return E, H
+
+
+def cross_sections(ctx: Context, prob: GDMProblem, F0, F, e0_norm2):
+    """(ext, sca, abs) device tensors of n_rhs doubles (nm^2)."""
+    n_rhs = F.shape[0]
+    na, npp = _dbl_array(e0_norm2)
+    out = torch.empty((3, n_rhs), dtype=torch.float64, device=F.device)
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_cross_sections(ctx.h, C.byref(s), _ptr(F0.contiguous()), _ptr(F.contiguous()), n_rhs, npp,
+                                        _ptr(out[0]), _ptr(out[1]), _ptr(out[2])), "gdm_cross_sections")
+    return out[0], out[1], out[2]
+
+
+def backward(ctx: Context, prob: GDMProblem, A, ipiv, F, e0, khat=(0.0, 0.0, 1.0), gF=None, g_sigma=None,
+             precision="fp32", grad_pos=None, grad_eps=None, grad_wavelength=None):
+    """Adjoint backward (kind 3): adds dL/dr, dL/deps, dL/dlambda into the given (or new zero) tensors."""
+    n_rhs = F.shape[0]
+    dev = F.device
+    if grad_pos is None:
+        grad_pos = torch.zeros((prob.n, 3), dtype=torch.float64, device=dev)
+    if grad_eps is None:
+        grad_eps = torch.zeros(prob.n, dtype=torch.complex128, device=dev)
+    if grad_wavelength is None:
+        grad_wavelength = torch.zeros(1, dtype=torch.float64, device=dev)
+    e0 = np.atleast_2d(np.asarray(e0, np.complex128))
+    ea, ep = _dbl_array(e0.view(np.float64).reshape(-1))
+    ka, kp = _dbl_array(khat)
+    if g_sigma is not None:
+        ga, gp = _dbl_array(np.asarray(g_sigma, np.float64).reshape(-1))
+    else:
+        gp = None
+    inf = SolveInfo()
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_backward(ctx.h, C.byref(s), PRECISION[precision], _ptr(A), A.shape[1], _ptr(ipiv),
+                                  _ptr(F.contiguous()), n_rhs, ep, kp, _ptr(None if gF is None else gF.contiguous()),
+                                  gp, _ptr(grad_pos), _ptr(grad_eps), _ptr(grad_wavelength), C.byref(inf)),
+               "gdm_backward")
+    return grad_pos, grad_eps, grad_wavelength, inf.as_dict()
+
+
+def nearfield_backward(ctx: Context, prob: GDMProblem, F, r_eval, e0, gE, khat=(0.0, 0.0, 1.0), gF_accum=None,
+                       grad_pos=None, grad_eps=None, grad_wavelength=None):
+    n_rhs = F.shape[0]
+    dev = F.device
+    e0 = np.atleast_2d(np.asarray(e0, np.complex128))
+    ea, ep = _dbl_array(e0.view(np.float64).reshape(-1))
+    ka, kp = _dbl_array(khat)
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_nearfield_backward(ctx.h, C.byref(s), _ptr(F.contiguous()), _ptr(r_eval.contiguous()),
+                                            r_eval.shape[0], n_rhs, ep, kp, _ptr(gE.contiguous()), _ptr(gF_accum),
+                                            _ptr(grad_pos), _ptr(grad_eps), _ptr(grad_wavelength)),
+               "gdm_nearfield_backward")
+    return gF_accum, grad_pos, grad_eps, grad_wavelength

@@ -1,0 +1,304 @@
+// C-ABI entry points: context management, argument validation, dispatch.
+#include <math.h>
+#include <stdarg.h>
+
+#include <new>
+
+#include "gdm_internal.cuh"
+
+gdm_status gdm_fail(gdm_ctx *ctx, gdm_status s, const char *fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+gdm_status gdm_after_launch(gdm_ctx *ctx, const char *what) {
+    ctx->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return gdm_fail(ctx, GDM_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    return GDM_OK;
+}
+
+gdm_status gdm_scratch(gdm_ctx *ctx, size_t bytes, void **ptr) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes > ctx->ws_bytes) {
+        if (ctx->ws) {
+            GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            GDM_CUDA_TRY(ctx, cudaFree(ctx->ws));
+            ctx->ws = nullptr;
+            ctx->ws_bytes = 0;
+        }
+        GDM_CUDA_TRY(ctx, cudaMalloc(&ctx->ws, bytes));
+        ctx->ws_bytes = bytes;
+    }
+    *ptr = ctx->ws;
+    return GDM_OK;
+}
+
+gdm_status gdm_pinned(gdm_ctx *ctx, size_t bytes, void **ptr) {
+    if (bytes > ctx->hpinned_bytes) {
+        if (ctx->hpinned) {
+            GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            cudaFreeHost(ctx->hpinned);
+            ctx->hpinned = nullptr;
+            ctx->hpinned_bytes = 0;
+        }
+        GDM_CUDA_TRY(ctx, cudaMallocHost(&ctx->hpinned, bytes));
+        ctx->hpinned_bytes = bytes;
+    }
+    *ptr = ctx->hpinned;
+    return GDM_OK;
+}
+
+gdm_status gdm_upload(gdm_ctx *ctx, const void *host, size_t bytes, void **dev) {
+    size_t off = (ctx->param_off + 255) & ~size_t(255);
+    if (off + bytes > GDM_PARAM_BYTES) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "parameter block too large");
+    GDM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->dparams + off, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->param_off = off + bytes;
+    *dev = ctx->dparams + off;
+    return GDM_OK;
+}
+
+extern "C" {
+
+const char *gdm_status_string(gdm_status s) {
+    switch (s) {
+        case GDM_OK: return "GDM_OK";
+        case GDM_ERR_INVALID_ARG: return "GDM_ERR_INVALID_ARG";
+        case GDM_ERR_SHAPE: return "GDM_ERR_SHAPE";
+        case GDM_ERR_NONFINITE: return "GDM_ERR_NONFINITE";
+        case GDM_ERR_SINGULAR: return "GDM_ERR_SINGULAR";
+        case GDM_ERR_NOT_CONVERGED: return "GDM_ERR_NOT_CONVERGED";
+        case GDM_ERR_OOM: return "GDM_ERR_OOM";
+        case GDM_ERR_CUDA: return "GDM_ERR_CUDA";
+        case GDM_ERR_TIMEOUT: return "GDM_ERR_TIMEOUT";
+        case GDM_ERR_UNSUPPORTED: return "GDM_ERR_UNSUPPORTED";
+    }
+    return "GDM_ERR_UNKNOWN";
+}
+
+const char *gdm_last_error(gdm_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+int64_t gdm_launch_count(gdm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+gdm_status gdm_create(gdm_ctx **out, int device, void *stream) {
+    if (!out) return GDM_ERR_INVALID_ARG;
+    *out = nullptr;
+    gdm_ctx *ctx = new (std::nothrow) gdm_ctx();
+    if (!ctx) return GDM_ERR_OOM;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return GDM_ERR_CUDA;
+    }
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    e = cudaMalloc(&ctx->dflags, GDM_NFLAGS * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->dflags, 0, GDM_NFLAGS * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dparams, GDM_PARAM_BYTES);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev2);
+    if (e != cudaSuccess) {
+        gdm_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? GDM_ERR_OOM : GDM_ERR_CUDA;
+    }
+    *out = ctx;
+    return GDM_OK;
+}
+
+gdm_status gdm_destroy(gdm_ctx *ctx) {
+    if (!ctx) return GDM_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream || ctx->ws) cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->dflags) cudaFree(ctx->dflags);
+    if (ctx->dparams) cudaFree(ctx->dparams);
+    if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->ev2) cudaEventDestroy(ctx->ev2);
+    delete ctx;
+    return GDM_OK;
+}
+
+gdm_status gdm_set_stream(gdm_ctx *ctx, void *stream) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return GDM_OK;
+}
+
+gdm_status gdm_ctx_check(gdm_ctx *ctx) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    int h[2] = {0, 0};
+    GDM_CUDA_TRY(ctx, cudaMemcpyAsync(h, ctx->dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    GDM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dflags, 0, 2 * sizeof(int), ctx->stream));
+    if (h[0] != 0)
+        return gdm_fail(ctx, (gdm_status)h[0], "device reported %s (detail %d)", gdm_status_string((gdm_status)h[0]),
+                        h[1]);
+    return GDM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ validation
+static gdm_status check_problem(gdm_ctx *ctx, const gdm_problem *p) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    if (!p) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "problem is NULL");
+    if (p->n < 1) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n must be >= 1 (got %lld)", (long long)p->n);
+    if (p->kind != 3 && p->kind != 6) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "kind must be 3 or 6");
+    if (!p->pos) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "pos is NULL");
+    if (!(p->wavelength > 0.0) || !isfinite(p->wavelength))
+        return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "wavelength must be finite and > 0");
+    if (!(p->eps_env > 0.0) || !isfinite(p->eps_env))
+        return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "eps_env must be finite and > 0");
+    if (p->kind == 3) {
+        if (!p->eps) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "kind 3 needs eps");
+        if (!(p->step > 0.0) || !isfinite(p->step))
+            return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "kind 3 needs a finite mesh step > 0");
+    } else {
+        if (!p->alpha6) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "kind 6 needs alpha6");
+        if (p->eps_env != 1.0) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "kind 6 is implemented for vacuum only");
+    }
+    if (p->n * p->kind > (int64_t)1 << 30) return gdm_fail(ctx, GDM_ERR_SHAPE, "system too large");
+    return GDM_OK;
+}
+
+static gdm_status check_prec(gdm_ctx *ctx, gdm_precision prec) {
+    if (prec != GDM_FP64 && prec != GDM_FP32 && prec != GDM_TF32_REFINE)
+        return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    return GDM_OK;
+}
+
+static gdm_status check_lda(gdm_ctx *ctx, int64_t n_sys, int64_t lda) {
+    if (lda < n_sys) return gdm_fail(ctx, GDM_ERR_SHAPE, "lda %lld < system size %lld", (long long)lda, (long long)n_sys);
+    if (lda % 2) return gdm_fail(ctx, GDM_ERR_SHAPE, "lda must be even (16-byte aligned columns)");
+    return GDM_OK;
+}
+
+extern "C" {
+
+gdm_status gdm_workspace_size(const gdm_problem *p, int n_rhs, gdm_precision prec, size_t *bytes) {
+    if (!p || !bytes || n_rhs < 1) return GDM_ERR_INVALID_ARG;
+    int64_t ns = p->n * p->kind;
+    size_t vec = (size_t)ns * n_rhs * 16;
+    size_t b = 6 * vec + 64 * 1024;
+    if (prec != GDM_FP64) {
+        // tensor-core operand copies: L panel (hi/lo, 2x embedded) and U row block (hi/lo)
+        b += (size_t)ns * 256 * 4 * 4 + (size_t)ns * 512 * 4 * 2 + (size_t)ns * n_rhs * 8;
+    }
+    b += (size_t)ns * 64 * 16;  // panel factorisation candidates and pivots
+    *bytes = b;
+    return GDM_OK;
+}
+
+gdm_status gdm_incident_planewave(gdm_ctx *ctx, const double *r, int64_t m, double wavelength, double eps_env,
+                                  const double *e0, const double *khat, int n_rhs, int kind_out, double *F0) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    if (!r || !e0 || !khat || !F0) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (m < 1 || n_rhs < 1) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "m and n_rhs must be >= 1");
+    if (kind_out != 3 && kind_out != 6) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "kind_out must be 3 or 6");
+    if (!(wavelength > 0) || !(eps_env > 0)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "bad wavelength/eps_env");
+    double kn = 0;
+    for (int c = 0; c < 3; c++) kn += khat[c] * khat[c];
+    if (fabs(kn - 1.0) > 1e-9) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "khat must be a unit vector");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    double n_env = sqrt(eps_env);
+    double k = n_env * 2.0 * 3.14159265358979323846 / wavelength;
+    return gdm_launch_planewave(ctx, r, m, k, n_env, e0, khat, n_rhs, kind_out, F0);
+}
+
+gdm_status gdm_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda) {
+    GDM_TRY(check_problem(ctx, p));
+    GDM_TRY(check_prec(ctx, prec));
+    if (!A) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "A is NULL");
+    GDM_TRY(check_lda(ctx, p->n * p->kind, lda));
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return gdm_launch_assemble(ctx, p, prec, A, lda);
+}
+
+gdm_status gdm_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda, int32_t *ipiv,
+                     const double *F0, double *F, int n_rhs, const gdm_solve_opts *opts, gdm_solve_info *info) {
+    GDM_TRY(check_problem(ctx, p));
+    GDM_TRY(check_prec(ctx, prec));
+    if (!A || !ipiv || !F0 || !F) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n_rhs must be in [1, 64]");
+    int64_t ns = p->n * p->kind;
+    GDM_TRY(check_lda(ctx, ns, lda));
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    gdm_solve_opts o = {0, 0, 0.0};
+    if (opts) o = *opts;
+    if (o.max_iter <= 0) o.max_iter = (prec == GDM_FP64) ? 3 : 40;
+    if (!(o.tol > 0)) o.tol = 1e-12;
+    if (info) memset(info, 0, sizeof(*info));
+    float fms = 0.f;
+    if (!(o.flags & GDM_SOLVE_FACTORED)) {
+        if (info) GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+        GDM_TRY(gdm_lu_factor(ctx, prec, A, ns, lda, ipiv));
+        if (info) {
+            GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
+            GDM_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev1));
+            GDM_CUDA_TRY(ctx, cudaEventElapsedTime(&fms, ctx->ev0, ctx->ev1));
+        }
+    }
+    gdm_status s = gdm_refined_solve(ctx, p, prec, A, lda, ipiv, F0, F, n_rhs, 0, &o, info);
+    if (info) info->factor_ms = fms;
+    return s;
+}
+
+gdm_status gdm_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, const double *r_eval, int64_t m,
+                         const double *F0_eval, int n_rhs, double *E_out, double *H_out) {
+    GDM_TRY(check_problem(ctx, p));
+    if (!F || !r_eval || !E_out) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (m < 1 || n_rhs < 1) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "m and n_rhs must be >= 1");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return gdm_launch_nearfield(ctx, p, F, r_eval, m, F0_eval, n_rhs, E_out, H_out);
+}
+
+gdm_status gdm_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F, int n_rhs,
+                              const double *e0_norm2, double *ext, double *sca, double *abs) {
+    GDM_TRY(check_problem(ctx, p));
+    if (!F0 || !F || !e0_norm2) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n_rhs must be in [1, 64]");
+    for (int r = 0; r < n_rhs; r++)
+        if (!(e0_norm2[r] > 0)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "|E0|^2 must be > 0");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return gdm_launch_cross_sections(ctx, p, F0, F, n_rhs, e0_norm2, ext, sca, abs);
+}
+
+gdm_status gdm_backward(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
+                        const int32_t *ipiv, const double *F, int n_rhs, const double *e0, const double *khat,
+                        const double *gF, const double *g_sigma, double *grad_pos, double *grad_eps,
+                        double *grad_wavelength, gdm_solve_info *info) {
+    GDM_TRY(check_problem(ctx, p));
+    GDM_TRY(check_prec(ctx, prec));
+    if (p->kind != 3) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "gdm_backward is implemented for kind 3");
+    if (!A || !ipiv || !F || !e0 || !khat) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n_rhs must be in [1, 64]");
+    GDM_TRY(check_lda(ctx, p->n * p->kind, lda));
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return gdm_launch_backward(ctx, p, prec, A, lda, ipiv, F, n_rhs, e0, khat, gF, g_sigma, grad_pos, grad_eps,
+                               grad_wavelength, info);
+}
+
+gdm_status gdm_nearfield_backward(gdm_ctx *ctx, const gdm_problem *p, const double *F, const double *r_eval,
+                                  int64_t m, int n_rhs, const double *e0, const double *khat, const double *gE,
+                                  double *gF_accum, double *grad_pos, double *grad_eps, double *grad_wavelength) {
+    GDM_TRY(check_problem(ctx, p));
+    if (p->kind != 3) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "gdm_nearfield_backward is implemented for kind 3");
+    if (!F || !r_eval || !e0 || !khat || !gE) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (m < 1 || n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "bad m or n_rhs");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return gdm_launch_nearfield_backward(ctx, p, F, r_eval, m, n_rhs, e0, khat, gE, gF_accum, grad_pos, grad_eps,
+                                         grad_wavelength);
+}
+
+}  // extern "C"

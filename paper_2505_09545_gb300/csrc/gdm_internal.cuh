@@ -1,0 +1,183 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the public C ABI (include/gdm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/gdm.h"
+
+// ------------------------------------------------------------------ context
+struct gdm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    int max_smem_optin = 0;
+    char err[512] = {0};
+    int64_t launches = 0;
+    // grow-only scratch arena owned by the context
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    // device-side error record: [0] first gdm_status, [1] detail, [2..3] grid-barrier counters
+    int *dflags = nullptr;
+    // pinned host mirror for synchronous reads of small device results
+    void *hpinned = nullptr;
+    size_t hpinned_bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    // small parameter arrays copied from the host (stream-ordered); offset reset per API call
+    char *dparams = nullptr;
+    size_t param_off = 0;
+};
+#define GDM_PARAM_BYTES (1 << 16)
+
+// set the context error string, return the status
+gdm_status gdm_fail(gdm_ctx *ctx, gdm_status s, const char *fmt, ...);
+
+#define GDM_CUDA_TRY(ctx, call)                                                                       \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return gdm_fail((ctx), (e_ == cudaErrorMemoryAllocation) ? GDM_ERR_OOM : GDM_ERR_CUDA,    \
+                            "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+#define GDM_TRY(...)                       \
+    do {                                   \
+        gdm_status s_ = (__VA_ARGS__);     \
+        if (s_ != GDM_OK) return s_;       \
+    } while (0)
+
+// check the last kernel launch, count it
+gdm_status gdm_after_launch(gdm_ctx *ctx, const char *what);
+#define GDM_LAUNCHED(ctx, what) GDM_TRY(gdm_after_launch((ctx), (what)))
+
+// scratch arena: returns a pointer to >= bytes of device memory (256-B aligned),
+// invalidating earlier pointers if it has to grow (it synchronises first).
+gdm_status gdm_scratch(gdm_ctx *ctx, size_t bytes, void **ptr);
+gdm_status gdm_pinned(gdm_ctx *ctx, size_t bytes, void **ptr);
+// copy a small host array into the context's parameter buffer (stream-ordered); call
+// gdm_params_reset at the start of each API call.
+gdm_status gdm_upload(gdm_ctx *ctx, const void *host, size_t bytes, void **dev);
+static inline void gdm_params_reset(gdm_ctx *ctx) { ctx->param_off = 0; }
+
+// carve sub-buffers out of one scratch block
+struct ScratchCarver {
+    char *base;
+    size_t off = 0;
+    explicit ScratchCarver(void *b) : base((char *)b) {}
+    template <class T> T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = (T *)(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+    static size_t round(size_t b) { return (b + 255) & ~size_t(255); }
+};
+
+// ------------------------------------------------------------------ device error flags
+#define GDM_FLAG_STATUS 0
+#define GDM_FLAG_DETAIL 1
+#define GDM_FLAG_BAR_COUNT 2
+#define GDM_FLAG_BAR_GEN 3
+#define GDM_NFLAGS 8
+
+__device__ __forceinline__ void gdm_dev_error(int *flags, int status, int detail) {
+    if (atomicCAS(&flags[GDM_FLAG_STATUS], 0, status) == 0) flags[GDM_FLAG_DETAIL] = detail;
+}
+
+// bounded spin limit for device waits (~ a second with nanosleep backoff)
+#define GDM_SPIN_LIMIT (1 << 24)
+
+// ------------------------------------------------------------------ complex helpers
+struct cd {
+    double x, y;
+};
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {  // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+// a += b * c
+__host__ __device__ __forceinline__ void cfma(double2 &a, double2 b, double2 c) {
+    a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));
+    a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
+}
+__host__ __device__ __forceinline__ void cfma(float2 &a, float2 b, float2 c) {
+    a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+    a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
+}
+// a -= b * c
+__host__ __device__ __forceinline__ void cfms(double2 &a, double2 b, double2 c) {
+    a.x = fma(-b.x, c.x, fma(b.y, c.y, a.x));
+    a.y = fma(-b.x, c.y, fma(-b.y, c.x, a.y));
+}
+__host__ __device__ __forceinline__ void cfms(float2 &a, float2 b, float2 c) {
+    a.x = fmaf(-b.x, c.x, fmaf(b.y, c.y, a.x));
+    a.y = fmaf(-b.x, c.y, fmaf(-b.y, c.x, a.y));
+}
+__host__ __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+__host__ __device__ __forceinline__ float cabs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+__host__ __device__ __forceinline__ double2 crecip(double2 a) {
+    double d = a.x * a.x + a.y * a.y;
+    return make_double2(a.x / d, -a.y / d);
+}
+__host__ __device__ __forceinline__ float2 crecip(float2 a) {
+    // scaled to avoid overflow of |a|^2 for large entries
+    float s = fmaxf(fabsf(a.x), fabsf(a.y));
+    float ax = a.x / s, ay = a.y / s;
+    float d = ax * ax + ay * ay;
+    return make_float2(ax / (d * s), -ay / (d * s));
+}
+
+template <class T> struct cplx;
+template <> struct cplx<float> { typedef float2 t; };
+template <> struct cplx<double> { typedef double2 t; };
+
+// ------------------------------------------------------------------ internal launchers (defined per .cu)
+// green.cu
+gdm_status gdm_launch_planewave(gdm_ctx *ctx, const double *r, int64_t m, double k, double n_env, const double *e0,
+                                const double *khat, int n_rhs, int kind_out, double *F0);
+gdm_status gdm_launch_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda);
+// residual r = F0 - A F (mode 0) or the adjoint residual r = g - A^H mu (mode 1), FP64 matrix-free.
+// Writes r (kN x n_rhs) and, if norms != NULL, per-RHS ||r||^2 into norms[0..n_rhs).
+gdm_status gdm_launch_residual(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
+                               int adjoint, double *r, double *norms2);
+gdm_status gdm_launch_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, const double *r_eval, int64_t m,
+                                const double *F0_eval, int n_rhs, double *E_out, double *H_out);
+gdm_status gdm_launch_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F, int n_rhs,
+                                     const double *e0_norm2, double *ext, double *sca, double *abs);
+// linear algebra (lu.cu)
+gdm_status gdm_lu_factor(gdm_ctx *ctx, gdm_precision prec, void *A, int64_t n, int64_t lda, int32_t *ipiv);
+// solve op(A) X = B in place on B (complex of the factor precision, n x n_rhs, ldb);
+// conj_trans = 0: A X = B using P, L, U; conj_trans = 1: A^H X = B.
+gdm_status gdm_lu_solve(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda, const int32_t *ipiv,
+                        void *B, int64_t ldb, int n_rhs, int conj_trans);
+// refine.cu
+gdm_status gdm_refined_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
+                             const int32_t *ipiv, const double *rhs, double *X, int n_rhs, int adjoint,
+                             const gdm_solve_opts *opts, gdm_solve_info *info);
+// backward.cu
+gdm_status gdm_launch_backward(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
+                               const int32_t *ipiv, const double *F, int n_rhs, const double *e0, const double *khat,
+                               const double *gF, const double *g_sigma, double *grad_pos, double *grad_eps,
+                               double *grad_wavelength, gdm_solve_info *info);
+gdm_status gdm_launch_nearfield_backward(gdm_ctx *ctx, const gdm_problem *p, const double *F, const double *r_eval,
+                                         int64_t m, int n_rhs, const double *e0, const double *khat, const double *gE,
+                                         double *gF_accum, double *grad_pos, double *grad_eps,
+                                         double *grad_wavelength);
+
+// problem helpers
+static inline double gdm_k0(const gdm_problem *p) { return 2.0 * 3.14159265358979323846 / p->wavelength; }

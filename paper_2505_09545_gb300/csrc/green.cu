@@ -1,0 +1,851 @@
+// Green-dyad kernels of the GDM hot path:
+//   * plane-wave illumination,
+//   * pair-tiled assembly of A = I - G alpha (complex64 with a double-float phase, or complex128),
+//   * FP64 matrix-free Green sums: refinement residual F0 - A F (and the adjoint A^H form), near field,
+//   * FP64 cross-section reductions.
+//
+// Physics (Gaussian units, exp(-i w t)), following the paper's Eq. (superprop_G) blocks:
+//   G^Ep(R) = e^{ikR}/eps_env [ (k^2/R + ik/R^2 - 1/R^3) I + (-k^2/R - 3ik/R^2 + 3/R^3) u u^T ]
+//   G^Hp(R) = k0 k e^{ikR} (1/R + i/(k R^2)) [u]_x          ([u]_x v = u x v)
+//   vacuum ED/MD dyad: G^Em = -G^Hp, G^Hm = G^Ep.
+// Cells (kind 3): alpha = (eps - eps_env) d^3/(4 pi), self-term S = -4 pi/(3 eps_env d^3) I
+// (Sec. "Volume discretization polarizabilities", Eq. selfterm_SEp_cubic).
+#include <math.h>
+
+#include "gdm_internal.cuh"
+
+#define PI_D 3.14159265358979323846
+
+// ================================================================== double-float (FP32 pair) arithmetic
+// Error-free transformations (Knuth two-sum, FMA two-product) give ~48-bit precision on the FP32
+// pipes, which on GB300 run ~64x faster than FP64. Used for the phase k R of the assembled matrix.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = two_sum(x.hi, y.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, e);
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_sqr(ff x) {
+    float p = __fmul_rn(x.hi, x.hi);
+    float e = fmaf(x.hi, x.hi, -p);
+    e = fmaf(2.0f * x.hi, x.lo, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_sqrt(ff x) {
+    float r = sqrtf(x.hi);
+    float p = __fmul_rn(r, r);
+    float e = fmaf(r, r, -p);
+    float res = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), e), x.lo);
+    return fast_two_sum(r, __fdiv_rn(res, 2.0f * r));
+}
+// x - y for two FP32-pair coordinates
+__device__ __forceinline__ ff ff_diff(float xh, float xl, float yh, float yl) {
+    ff s = two_sum(xh, -yh);
+    float e = __fadd_rn(s.lo, __fsub_rn(xl, yl));
+    return fast_two_sum(s.hi, e);
+}
+
+// 2 pi = C1 + C2 + C3: C1 and C2 carry 12 significant bits each (so n*C1, n*C2 are exact FP32
+// products for |n| < 4096), C3 is the FP32-rounded remainder. Split of the number 2 pi computed
+// with 50-digit arithmetic (Cody-Waite style argument reduction).
+#define TWO_PI_C1 6.283203125f
+#define TWO_PI_C2 (-1.7814338207244873e-05f)
+#define TWO_PI_C3 (-3.4822063010864213e-09f)
+#define INV_TWO_PI_F 0.15915494309189535f
+
+// e^{i x} for a double-float phase x >= 0 (|x| < 2.5e4): reduce to [-pi, pi] keeping the low part,
+// then FP32 sincos of the high part with a first-order correction for the low part.
+__device__ __forceinline__ float2 ff_expi(ff x) {
+    float n = rintf(x.hi * INV_TWO_PI_F);
+    float t1 = fmaf(-n, TWO_PI_C1, x.hi);  // exact
+    ff s = two_sum(t1, -n * TWO_PI_C2);    // -n*C2 exact
+    float lo = fmaf(-n, TWO_PI_C3, __fadd_rn(s.lo, x.lo));
+    ff th = fast_two_sum(s.hi, lo);
+    float sn, cs;
+    sincosf(th.hi, &sn, &cs);
+    return make_float2(fmaf(-sn, th.lo, cs), fmaf(cs, th.lo, sn));
+}
+
+// ================================================================== plane wave
+__global__ void k_planewave(const double *__restrict__ r, int64_t m, double k, double n_env, const double *__restrict__ e0,
+                            double kx, double ky, double kz, int n_rhs, int kind_out, double2 *__restrict__ F0) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double ph = k * (kx * r[3 * i] + ky * r[3 * i + 1] + kz * r[3 * i + 2]);
+    double s, c;
+    sincos(ph, &s, &c);
+    double2 e = make_double2(c, s);
+    int64_t ld = (int64_t)kind_out * m;
+    for (int q = 0; q < n_rhs; q++) {
+        double2 E[3];
+        for (int a = 0; a < 3; a++) E[a] = cmul(make_double2(e0[6 * q + 2 * a], e0[6 * q + 2 * a + 1]), e);
+        double2 *out = F0 + q * ld + (int64_t)kind_out * i;
+        for (int a = 0; a < 3; a++) out[a] = E[a];
+        if (kind_out == 6) {
+            // H0 = n_env khat x E0
+            out[3] = cscale(csub(cscale(E[2], ky), cscale(E[1], kz)), n_env);
+            out[4] = cscale(csub(cscale(E[0], kz), cscale(E[2], kx)), n_env);
+            out[5] = cscale(csub(cscale(E[1], kx), cscale(E[0], ky)), n_env);
+        }
+    }
+}
+
+gdm_status gdm_launch_planewave(gdm_ctx *ctx, const double *r, int64_t m, double k, double n_env, const double *e0,
+                                const double *khat, int n_rhs, int kind_out, double *F0) {
+    double *de0;
+    GDM_TRY(gdm_upload(ctx, e0, sizeof(double) * 6 * n_rhs, (void **)&de0));
+    int bs = 256;
+    k_planewave<<<(unsigned)((m + bs - 1) / bs), bs, 0, ctx->stream>>>(r, m, k, n_env, de0, khat[0], khat[1], khat[2],
+                                                                       n_rhs, kind_out, (double2 *)F0);
+    GDM_LAUNCHED(ctx, "planewave");
+    return GDM_OK;
+}
+
+
+// ================================================================== per-dipole preparation
+// FP32 assembly operands: positions split into (hi, lo) FP32 pairs so that r_i - r_j keeps ~48 bits,
+// alpha_j rounded to complex64, and the diagonal block value 1 - S alpha_j (kind 3).
+struct DipF {
+    float xh, yh, zh, xl, yl, zl;
+    float2 alpha;
+    float2 diag;
+    float pad[2];
+};
+static_assert(sizeof(DipF) == 48, "DipF layout");
+
+__global__ void k_prep_dipf(const double *__restrict__ pos, const double2 *__restrict__ eps, int64_t n, double eps_env,
+                            double d3_4pi, DipF *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    DipF d;
+    double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    d.xh = (float)x;
+    d.yh = (float)y;
+    d.zh = (float)z;
+    d.xl = (float)(x - (double)d.xh);
+    d.yl = (float)(y - (double)d.yh);
+    d.zl = (float)(z - (double)d.zh);
+    d.alpha = make_float2(0.f, 0.f);
+    d.diag = make_float2(1.f, 0.f);
+    if (eps) {
+        double2 e = eps[i];
+        double ar = (e.x - eps_env) * d3_4pi, ai = e.y * d3_4pi;
+        d.alpha = make_float2((float)ar, (float)ai);
+        // 1 - S alpha with S = -4 pi / (3 eps_env d^3): 1 + (eps - eps_env) / (3 eps_env)
+        d.diag = make_float2((float)(1.0 + (e.x - eps_env) / (3.0 * eps_env)), (float)(e.y / (3.0 * eps_env)));
+    }
+    d.pad[0] = d.pad[1] = 0.f;
+    out[i] = d;
+}
+
+// FP64 cell polarisabilities alpha_j = (eps_j - eps_env) d^3 / (4 pi)
+__global__ void k_alpha3_f64(const double2 *__restrict__ eps, int64_t n, double eps_env, double d3_4pi,
+                             double2 *__restrict__ alpha) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 e = eps[i];
+    alpha[i] = make_double2((e.x - eps_env) * d3_4pi, e.y * d3_4pi);
+}
+
+__global__ void k_alpha6_f32(const double2 *__restrict__ a6, int64_t count, float2 *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    out[i] = make_float2((float)a6[i].x, (float)a6[i].y);
+}
+
+// ================================================================== assembly
+// Green coefficients of one ordered pair: G^Ep = a I + b u u^T, G^Hp = c [u]_x.
+template <class T> struct PairG {
+    typename cplx<T>::t a, b, c;
+    T ux, uy, uz;
+};
+
+// FP32 with a double-float phase: the phase k R needs ~1e-9 absolute accuracy for kR up to ~1e3,
+// the amplitudes 1/R^n only FP32 relative accuracy.
+__device__ __forceinline__ PairG<float> pair_green_f32(const DipF &ti, const DipF &sj, ff kff, float kf, float k2,
+                                                       float k0k, float inv_eps, bool need_c) {
+    ff dx = ff_diff(ti.xh, ti.xl, sj.xh, sj.xl);
+    ff dy = ff_diff(ti.yh, ti.yl, sj.yh, sj.yl);
+    ff dz = ff_diff(ti.zh, ti.zl, sj.zh, sj.zl);
+    ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+    ff r = ff_sqrt(r2);
+    float r1 = 1.0f / r.hi;
+    float r2i = r1 * r1, r3i = r2i * r1;
+    float2 e = ff_expi(ff_mul(kff, r));
+    PairG<float> g;
+    if (need_c) g.c = cmul(e, make_float2(k0k * r1, k0k * r2i / kf));
+    e = cscale(e, inv_eps);
+    g.a = cmul(e, make_float2(k2 * r1 - r3i, kf * r2i));
+    g.b = cmul(e, make_float2(3.0f * r3i - k2 * r1, -3.0f * kf * r2i));
+    g.ux = dx.hi * r1;
+    g.uy = dy.hi * r1;
+    g.uz = dz.hi * r1;
+    return g;
+}
+
+__device__ __forceinline__ PairG<double> pair_green_f64(double dx, double dy, double dz, double k, double k2,
+                                                        double k0k, double inv_eps, bool need_c) {
+    double r2 = dx * dx + dy * dy + dz * dz;
+    double r1 = rsqrt(r2);
+    double r = r2 * r1;
+    double r2i = r1 * r1, r3i = r2i * r1;
+    double s, c;
+    sincos(k * r, &s, &c);
+    double2 e = make_double2(c, s);
+    PairG<double> g;
+    if (need_c) g.c = cmul(e, make_double2(k0k * r1, k0k * r2i / k));
+    e = cscale(e, inv_eps);
+    g.a = cmul(e, make_double2(k2 * r1 - r3i, k * r2i));
+    g.b = cmul(e, make_double2(3.0 * r3i - k2 * r1, -3.0 * k * r2i));
+    g.ux = dx * r1;
+    g.uy = dy * r1;
+    g.uz = dz * r1;
+    return g;
+}
+
+// y = G^Ep x = a x + b u (u.x)
+template <class C, class T>
+__device__ __forceinline__ void apply_gep(const PairG<T> &g, const C *x, C *y) {
+    C ud;
+    ud.x = g.ux * x[0].x + g.uy * x[1].x + g.uz * x[2].x;
+    ud.y = g.ux * x[0].y + g.uy * x[1].y + g.uz * x[2].y;
+    C bu = cmul(g.b, ud);
+    y[0] = cadd(cmul(g.a, x[0]), cscale(bu, g.ux));
+    y[1] = cadd(cmul(g.a, x[1]), cscale(bu, g.uy));
+    y[2] = cadd(cmul(g.a, x[2]), cscale(bu, g.uz));
+}
+// y = c (u x x)
+template <class C, class T>
+__device__ __forceinline__ void apply_ghp(const PairG<T> &g, const C *x, C *y) {
+    C v0, v1, v2;
+    v0.x = g.uy * x[2].x - g.uz * x[1].x;
+    v0.y = g.uy * x[2].y - g.uz * x[1].y;
+    v1.x = g.uz * x[0].x - g.ux * x[2].x;
+    v1.y = g.uz * x[0].y - g.ux * x[2].y;
+    v2.x = g.ux * x[1].x - g.uy * x[0].x;
+    v2.y = g.ux * x[1].y - g.uy * x[0].y;
+    y[0] = cmul(g.c, v0);
+    y[1] = cmul(g.c, v1);
+    y[2] = cmul(g.c, v2);
+}
+// 6x6 vacuum dyad on (x_e, x_m): (G x_e - C x_m, C x_e + G x_m)
+template <class C, class T>
+__device__ __forceinline__ void apply_g6(const PairG<T> &g, const C *x, C *y) {
+    C ge[3], gm[3], ce[3], cm[3];
+    apply_gep(g, x, ge);
+    apply_gep(g, x + 3, gm);
+    apply_ghp(g, x, ce);
+    apply_ghp(g, x + 3, cm);
+    for (int a = 0; a < 3; a++) {
+        y[a] = csub(ge[a], cm[a]);
+        y[3 + a] = cadd(ce[a], gm[a]);
+    }
+}
+
+#define ASM_TI 128
+#define ASM_TJ3 16
+#define ASM_TJ6 4
+
+// kind 3, complex64 output. Block (128 targets i) x (16 sources j). Column-major A, lda in complex.
+__global__ void __launch_bounds__(ASM_TI) k_assemble3_f32(float2 *__restrict__ A, int64_t lda, int64_t n,
+                                                         const DipF *__restrict__ dip, float khi, float klo,
+                                                         float inv_eps) {
+    __shared__ DipF sj[ASM_TJ3];
+    int64_t j0 = (int64_t)blockIdx.y * ASM_TJ3;
+    if (threadIdx.x < ASM_TJ3 && j0 + threadIdx.x < n) sj[threadIdx.x] = dip[j0 + threadIdx.x];
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * ASM_TI + threadIdx.x;
+    if (i >= n) return;
+    const DipF ti = dip[i];
+    ff kff = {khi, klo};
+    float kf = khi, k2 = khi * khi;
+    int jn = (int)min((int64_t)ASM_TJ3, n - j0);
+    for (int jj = 0; jj < jn; jj++) {
+        int64_t j = j0 + jj;
+        float2 *col = A + (3 * j) * lda + 3 * i;
+        if (j == i) {
+            float2 dg = sj[jj].diag;
+            float2 z = make_float2(0.f, 0.f);
+            col[0] = dg; col[1] = z; col[2] = z;
+            col += lda;
+            col[0] = z; col[1] = dg; col[2] = z;
+            col += lda;
+            col[0] = z; col[1] = z; col[2] = dg;
+            continue;
+        }
+        PairG<float> g = pair_green_f32(ti, sj[jj], kff, kf, k2, 0.f, inv_eps, false);
+        float2 al = sj[jj].alpha;
+        float2 na = cmul(g.a, al), nb = cmul(g.b, al);
+        na = make_float2(-na.x, -na.y);
+        nb = make_float2(-nb.x, -nb.y);
+        float u[3] = {g.ux, g.uy, g.uz};
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            float2 v0 = cscale(nb, u[0] * u[b]);
+            float2 v1 = cscale(nb, u[1] * u[b]);
+            float2 v2 = cscale(nb, u[2] * u[b]);
+            if (b == 0) v0 = cadd(v0, na);
+            if (b == 1) v1 = cadd(v1, na);
+            if (b == 2) v2 = cadd(v2, na);
+            col[0] = v0; col[1] = v1; col[2] = v2;
+            col += lda;
+        }
+    }
+}
+
+// kind 3, complex128 output (plain FP64 path)
+__global__ void __launch_bounds__(ASM_TI) k_assemble3_f64(double2 *__restrict__ A, int64_t lda, int64_t n,
+                                                         const double *__restrict__ pos,
+                                                         const double2 *__restrict__ alpha, double self_fac, double k,
+                                                         double inv_eps) {
+    __shared__ double sp[ASM_TJ3][3];
+    __shared__ double2 sa[ASM_TJ3];
+    int64_t j0 = (int64_t)blockIdx.y * ASM_TJ3;
+    if (threadIdx.x < ASM_TJ3 && j0 + threadIdx.x < n) {
+        int64_t j = j0 + threadIdx.x;
+        sp[threadIdx.x][0] = pos[3 * j];
+        sp[threadIdx.x][1] = pos[3 * j + 1];
+        sp[threadIdx.x][2] = pos[3 * j + 2];
+        sa[threadIdx.x] = alpha[j];
+    }
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * ASM_TI + threadIdx.x;
+    if (i >= n) return;
+    double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+    double k2 = k * k;
+    int jn = (int)min((int64_t)ASM_TJ3, n - j0);
+    for (int jj = 0; jj < jn; jj++) {
+        int64_t j = j0 + jj;
+        double2 *col = A + (3 * j) * lda + 3 * i;
+        double2 al = sa[jj];
+        if (j == i) {
+            // 1 - S alpha with the cubic self-term S = -4 pi / (3 eps_env d^3) = -self_fac
+            double2 dg = make_double2(1.0 + self_fac * al.x, self_fac * al.y);
+            double2 z = make_double2(0.0, 0.0);
+            col[0] = dg; col[1] = z; col[2] = z;
+            col += lda;
+            col[0] = z; col[1] = dg; col[2] = z;
+            col += lda;
+            col[0] = z; col[1] = z; col[2] = dg;
+            continue;
+        }
+        PairG<double> g = pair_green_f64(xi - sp[jj][0], yi - sp[jj][1], zi - sp[jj][2], k, k2, 0.0, inv_eps, false);
+        double2 na = cmul(g.a, al), nb = cmul(g.b, al);
+        na = make_double2(-na.x, -na.y);
+        nb = make_double2(-nb.x, -nb.y);
+        double u[3] = {g.ux, g.uy, g.uz};
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            double2 v0 = cscale(nb, u[0] * u[b]);
+            double2 v1 = cscale(nb, u[1] * u[b]);
+            double2 v2 = cscale(nb, u[2] * u[b]);
+            if (b == 0) v0 = cadd(v0, na);
+            if (b == 1) v1 = cadd(v1, na);
+            if (b == 2) v2 = cadd(v2, na);
+            col[0] = v0; col[1] = v1; col[2] = v2;
+            col += lda;
+        }
+    }
+}
+
+// kind 6 (vacuum ED/MD dipoles), generic 6x6 alpha_j. Block (128 targets) x (4 sources).
+template <class T>
+__global__ void __launch_bounds__(ASM_TI) k_assemble6(typename cplx<T>::t *__restrict__ A, int64_t lda, int64_t n,
+                                                     const DipF *__restrict__ dipf, const double *__restrict__ pos,
+                                                     const typename cplx<T>::t *__restrict__ alpha6, float khi,
+                                                     float klo, double k) {
+    typedef typename cplx<T>::t C;
+    __shared__ C sa[ASM_TJ6][36];
+    __shared__ DipF sjf[ASM_TJ6];
+    __shared__ double sjp[ASM_TJ6][3];
+    int64_t j0 = (int64_t)blockIdx.y * ASM_TJ6;
+    int jn = (int)min((int64_t)ASM_TJ6, n - j0);
+    for (int t = threadIdx.x; t < jn * 36; t += blockDim.x) sa[t / 36][t % 36] = alpha6[(j0 + t / 36) * 36 + t % 36];
+    if (threadIdx.x < jn) {
+        if (sizeof(T) == 4) sjf[threadIdx.x] = dipf[j0 + threadIdx.x];
+        else {
+            for (int c = 0; c < 3; c++) sjp[threadIdx.x][c] = pos[3 * (j0 + threadIdx.x) + c];
+        }
+    }
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * ASM_TI + threadIdx.x;
+    if (i >= n) return;
+    for (int jj = 0; jj < jn; jj++) {
+        int64_t j = j0 + jj;
+        C *col = A + (6 * j) * lda + 6 * i;
+        if (j == i) {
+            for (int q = 0; q < 6; q++) {
+                for (int a = 0; a < 6; a++) {
+                    C v;
+                    v.x = (a == q) ? (T)1 : (T)0;
+                    v.y = (T)0;
+                    col[a] = v;
+                }
+                col += lda;
+            }
+            continue;
+        }
+        PairG<T> g;
+        if constexpr (sizeof(T) == 4) {
+            const DipF ti = dipf[i];
+            ff kff = {khi, klo};
+            g = pair_green_f32(ti, sjf[jj], kff, khi, khi * khi, khi * khi, 1.0f, true);
+        } else {
+            g = pair_green_f64(pos[3 * i] - sjp[jj][0], pos[3 * i + 1] - sjp[jj][1], pos[3 * i + 2] - sjp[jj][2], k,
+                               k * k, k * k, 1.0, true);
+        }
+        for (int q = 0; q < 6; q++) {
+            C x[6], y[6];
+            for (int a = 0; a < 6; a++) x[a] = sa[jj][a * 6 + q];
+            apply_g6(g, x, y);
+            for (int a = 0; a < 6; a++) {
+                C v;
+                v.x = -y[a].x;
+                v.y = -y[a].y;
+                col[a] = v;
+            }
+            col += lda;
+        }
+    }
+}
+
+gdm_status gdm_launch_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda) {
+    int64_t n = p->n;
+    double k0 = gdm_k0(p);
+    double k = sqrt(p->eps_env) * k0;
+    double d3_4pi = p->kind == 3 ? p->step * p->step * p->step / (4.0 * PI_D) : 0.0;
+    size_t need = ScratchCarver::round(n * sizeof(DipF)) + ScratchCarver::round(n * sizeof(double2)) +
+                  (p->kind == 6 ? ScratchCarver::round(n * 36 * sizeof(float2)) : 0) + 1024;
+    void *ws;
+    GDM_TRY(gdm_scratch(ctx, need, &ws));
+    ScratchCarver sc(ws);
+    DipF *dipf = sc.take<DipF>(n);
+    double2 *alpha = sc.take<double2>(n);
+    int bs = 256;
+    unsigned nb = (unsigned)((n + bs - 1) / bs);
+    float khi = (float)k, klo = (float)(k - (double)khi);
+    dim3 blk(ASM_TI);
+    if (p->kind == 3) {
+        if (prec == GDM_FP64) {
+            k_alpha3_f64<<<nb, bs, 0, ctx->stream>>>((const double2 *)p->eps, n, p->eps_env, d3_4pi, alpha);
+            GDM_LAUNCHED(ctx, "alpha3_f64");
+            dim3 grid((unsigned)((n + ASM_TI - 1) / ASM_TI), (unsigned)((n + ASM_TJ3 - 1) / ASM_TJ3));
+            double self_fac = 4.0 * PI_D / (3.0 * p->eps_env * p->step * p->step * p->step);
+            k_assemble3_f64<<<grid, blk, 0, ctx->stream>>>((double2 *)A, lda, n, p->pos, alpha, self_fac, k,
+                                                          1.0 / p->eps_env);
+            GDM_LAUNCHED(ctx, "assemble3_f64");
+        } else {
+            k_prep_dipf<<<nb, bs, 0, ctx->stream>>>(p->pos, (const double2 *)p->eps, n, p->eps_env, d3_4pi, dipf);
+            GDM_LAUNCHED(ctx, "prep_dipf");
+            dim3 grid((unsigned)((n + ASM_TI - 1) / ASM_TI), (unsigned)((n + ASM_TJ3 - 1) / ASM_TJ3));
+            k_assemble3_f32<<<grid, blk, 0, ctx->stream>>>((float2 *)A, lda, n, dipf, khi, klo,
+                                                          (float)(1.0 / p->eps_env));
+            GDM_LAUNCHED(ctx, "assemble3_f32");
+        }
+    } else {
+        dim3 grid((unsigned)((n + ASM_TI - 1) / ASM_TI), (unsigned)((n + ASM_TJ6 - 1) / ASM_TJ6));
+        if (prec == GDM_FP64) {
+            k_assemble6<double><<<grid, blk, 0, ctx->stream>>>((double2 *)A, lda, n, nullptr, p->pos,
+                                                              (const double2 *)p->alpha6, khi, klo, k);
+            GDM_LAUNCHED(ctx, "assemble6_f64");
+        } else {
+            float2 *a6 = sc.take<float2>(n * 36);
+            k_prep_dipf<<<nb, bs, 0, ctx->stream>>>(p->pos, nullptr, n, 1.0, 0.0, dipf);
+            GDM_LAUNCHED(ctx, "prep_dipf");
+            k_alpha6_f32<<<(unsigned)((n * 36 + bs - 1) / bs), bs, 0, ctx->stream>>>((const double2 *)p->alpha6,
+                                                                                     n * 36, a6);
+            GDM_LAUNCHED(ctx, "alpha6_f32");
+            k_assemble6<float><<<grid, blk, 0, ctx->stream>>>((float2 *)A, lda, n, dipf, p->pos, a6, khi, klo, k);
+            GDM_LAUNCHED(ctx, "assemble6_f32");
+        }
+    }
+    return GDM_OK;
+}
+
+// ================================================================== FP64 matrix-free Green sums
+// Dipole moments P = alpha X (forward) or P = conj(X) (adjoint sources, kind 3); (kind*n) x n_rhs.
+__global__ void k_moments(const double2 *__restrict__ X, int64_t n, int kind, int n_rhs, const double2 *__restrict__ eps,
+                          double eps_env, double d3_4pi, const double2 *__restrict__ alpha6, int conj_only,
+                          double2 *__restrict__ P) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int q = blockIdx.y;
+    if (i >= n || q >= n_rhs) return;
+    int64_t ld = kind * n;
+    const double2 *x = X + q * ld + kind * i;
+    double2 *o = P + q * ld + kind * i;
+    if (conj_only) {
+        for (int a = 0; a < kind; a++) o[a] = conjd(x[a]);
+        return;
+    }
+    if (kind == 3) {
+        double2 al = make_double2((eps[i].x - eps_env) * d3_4pi, eps[i].y * d3_4pi);
+        for (int a = 0; a < 3; a++) o[a] = cmul(al, x[a]);
+    } else {
+        const double2 *al = alpha6 + 36 * i;
+        for (int a = 0; a < 6; a++) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int b = 0; b < 6; b++) cfma(s, al[6 * a + b], x[b]);
+            o[a] = s;
+        }
+    }
+}
+
+#define GS_T 128
+#define GS_S 32
+
+// partial[c][q][t][OUT] = sum over sources j of chunk c of G(r_t - r_j) P_j  (q < NR RHS of this group)
+// OUT = 3 (G^Ep only), or 6 (G^Ep and G^Hp for kind 3 near fields / full 6x6 dyad for kind 6).
+template <int KIND, int OUT, int NR>
+__global__ void __launch_bounds__(GS_T) k_green_sum(const double *__restrict__ tpos, int64_t m,
+                                                   const double *__restrict__ spos, const double2 *__restrict__ P,
+                                                   int64_t n, int rhs0, int nr_here, double k, double k0,
+                                                   double inv_eps, int64_t chunk, int self_exclude,
+                                                   double2 *__restrict__ partial) {
+    __shared__ double sp[GS_S][3];
+    __shared__ double2 sm[GS_S][KIND][NR];
+    const int64_t t = (int64_t)blockIdx.x * GS_T + threadIdx.x;
+    const bool valid = t < m;
+    const int64_t c = blockIdx.y;
+    const int64_t jb = c * chunk, je = min(n, jb + chunk);
+    double tx = 0, ty = 0, tz = 0;
+    if (valid) {
+        tx = tpos[3 * t];
+        ty = tpos[3 * t + 1];
+        tz = tpos[3 * t + 2];
+    }
+    double2 acc[NR][OUT];
+#pragma unroll
+    for (int q = 0; q < NR; q++)
+#pragma unroll
+        for (int a = 0; a < OUT; a++) acc[q][a] = make_double2(0.0, 0.0);
+    const double k2 = k * k, k0k = k0 * k;
+    const int64_t ldp = (int64_t)KIND * n;
+    for (int64_t s0 = jb; s0 < je; s0 += GS_S) {
+        int sn = (int)min((int64_t)GS_S, je - s0);
+        for (int e = threadIdx.x; e < sn * 3; e += GS_T) sp[e / 3][e % 3] = spos[3 * s0 + e];
+        for (int e = threadIdx.x; e < sn * KIND * NR; e += GS_T) {
+            int jj = e / (KIND * NR), rem = e % (KIND * NR), a = rem / NR, q = rem % NR;
+            double2 v = make_double2(0.0, 0.0);
+            if (q < nr_here) v = P[(rhs0 + q) * ldp + KIND * (s0 + jj) + a];
+            sm[jj][a][q] = v;
+        }
+        __syncthreads();
+        if (valid) {
+            for (int jj = 0; jj < sn; jj++) {
+                if (self_exclude && s0 + jj == t) continue;
+                PairG<double> g = pair_green_f64(tx - sp[jj][0], ty - sp[jj][1], tz - sp[jj][2], k, k2, k0k, inv_eps,
+                                                 OUT == 6);
+#pragma unroll
+                for (int q = 0; q < NR; q++) {
+                    double2 x[KIND], y[OUT];
+#pragma unroll
+                    for (int a = 0; a < KIND; a++) x[a] = sm[jj][a][q];
+                    if constexpr (KIND == 6) {
+                        apply_g6(g, x, y);
+                    } else {
+                        apply_gep(g, x, y);
+                        if constexpr (OUT == 6) apply_ghp(g, x, y + 3);
+                    }
+#pragma unroll
+                    for (int a = 0; a < OUT; a++) acc[q][a] = cadd(acc[q][a], y[a]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!valid) return;
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+        if (q >= nr_here) break;
+        double2 *o = partial + ((c * NR + q) * m + t) * OUT;
+#pragma unroll
+        for (int a = 0; a < OUT; a++) o[a] = acc[q][a];
+    }
+}
+
+// r = rhs - X + (G P)  [forward, P = alpha X, self-term S P_t for cells]
+// r = rhs - X + conj(alpha_t) conj(G P)  [adjoint kind 3, P = conj(X): (A^H X)_t = X_t - conj(alpha_t (G conj X)_t)]
+template <int KIND, int NR>
+__global__ void k_residual_finalize(const double2 *__restrict__ partial, int nchunks, int64_t n, int rhs0, int nr_here,
+                                    const double2 *__restrict__ rhs, const double2 *__restrict__ X,
+                                    const double2 *__restrict__ P, double self_S, int adjoint,
+                                    const double2 *__restrict__ eps, double eps_env, double d3_4pi,
+                                    double2 *__restrict__ r, double *__restrict__ norms2) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double nrm[NR];
+#pragma unroll
+    for (int q = 0; q < NR; q++) nrm[q] = 0.0;
+    if (t < n) {
+        const int64_t ld = (int64_t)KIND * n;
+        double2 al = make_double2(0.0, 0.0);
+        if (adjoint && KIND == 3) al = make_double2((eps[t].x - eps_env) * d3_4pi, eps[t].y * d3_4pi);
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            if (q >= nr_here) break;
+            int64_t col = (int64_t)(rhs0 + q) * ld + KIND * t;
+            for (int a = 0; a < KIND; a++) {
+                double2 s = make_double2(0.0, 0.0);
+                for (int c = 0; c < nchunks; c++) s = cadd(s, partial[((c * NR + q) * n + t) * KIND + a]);
+                if (KIND == 3) s = cadd(s, cscale(P[col + a], self_S));
+                double2 v;
+                if (adjoint) v = cadd(csub(rhs[col + a], X[col + a]), cmul(conjd(al), conjd(s)));
+                else v = cadd(csub(rhs[col + a], X[col + a]), s);
+                r[col + a] = v;
+                nrm[q] += v.x * v.x + v.y * v.y;
+            }
+        }
+    }
+    // block reduction of the squared norms
+    __shared__ double red[NR][32];
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+        double v = nrm[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && norms2) {
+        int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            double v = threadIdx.x < nw ? red[q][threadIdx.x] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (threadIdx.x == 0 && q < nr_here) atomicAdd(&norms2[rhs0 + q], v);
+        }
+    }
+}
+
+static void green_grid(gdm_ctx *ctx, int64_t m, int64_t n, int64_t *chunk, int *nchunks) {
+    int64_t tb = (m + GS_T - 1) / GS_T;
+    int64_t want = (4 * (int64_t)ctx->sm_count + tb - 1) / tb;
+    int64_t maxc = (n + GS_S - 1) / GS_S;
+    int64_t nc = want < 1 ? 1 : (want > maxc ? maxc : want);
+    if (nc > 64) nc = 64;
+    int64_t ch = (n + nc - 1) / nc;
+    ch = (ch + GS_S - 1) / GS_S * GS_S;
+    *chunk = ch;
+    *nchunks = (int)((n + ch - 1) / ch);
+}
+
+size_t gdm_green_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n, int out) {
+    int64_t chunk;
+    int nc;
+    green_grid(ctx, m, n, &chunk, &nc);
+    return (size_t)nc * 2 * m * out * sizeof(double2);
+}
+
+template <int KIND, int OUT>
+static gdm_status launch_green_sum(gdm_ctx *ctx, const double *tpos, int64_t m, const double *spos,
+                                   const double2 *P, int64_t n, int rhs0, int nr_here, double k, double k0,
+                                   double inv_eps, int self_exclude, double2 *partial, int *nchunks_out) {
+    int64_t chunk;
+    int nc;
+    green_grid(ctx, m, n, &chunk, &nc);
+    dim3 grid((unsigned)((m + GS_T - 1) / GS_T), (unsigned)nc);
+    k_green_sum<KIND, OUT, 2><<<grid, GS_T, 0, ctx->stream>>>(tpos, m, spos, P, n, rhs0, nr_here, k, k0, inv_eps,
+                                                              chunk, self_exclude, partial);
+    GDM_LAUNCHED(ctx, "green_sum");
+    *nchunks_out = nc;
+    return GDM_OK;
+}
+
+// residual of the FP64 system (matrix-free); scratch: P (kN x n_rhs) + partial buffer
+gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
+                                  int adjoint, double *r, double *norms2, double2 *Pbuf, double2 *partial) {
+    const int64_t n = p->n;
+    const int kind = p->kind;
+    if (adjoint && kind != 3) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "adjoint residual implemented for kind 3");
+    double k0 = gdm_k0(p), k = sqrt(p->eps_env) * k0;
+    double d3_4pi = kind == 3 ? p->step * p->step * p->step / (4.0 * PI_D) : 0.0;
+    double S = kind == 3 ? -4.0 * PI_D / (3.0 * p->eps_env * p->step * p->step * p->step) : 0.0;
+    dim3 g1((unsigned)((n + 127) / 128), (unsigned)n_rhs);
+    k_moments<<<g1, 128, 0, ctx->stream>>>((const double2 *)X, n, kind, n_rhs, (const double2 *)p->eps, p->eps_env,
+                                            d3_4pi, (const double2 *)p->alpha6, adjoint, Pbuf);
+    GDM_LAUNCHED(ctx, "moments");
+    if (norms2) GDM_CUDA_TRY(ctx, cudaMemsetAsync(norms2, 0, sizeof(double) * n_rhs, ctx->stream));
+    for (int q0 = 0; q0 < n_rhs; q0 += 2) {
+        int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
+        int nc;
+        if (kind == 3)
+            GDM_TRY(launch_green_sum<3, 3>(ctx, p->pos, n, p->pos, Pbuf, n, q0, nr, k, k0, 1.0 / p->eps_env, 1,
+                                           partial, &nc));
+        else
+            GDM_TRY(launch_green_sum<6, 6>(ctx, p->pos, n, p->pos, Pbuf, n, q0, nr, k, k0, 1.0, 1, partial, &nc));
+        unsigned nb = (unsigned)((n + 255) / 256);
+        if (kind == 3)
+            k_residual_finalize<3, 2><<<nb, 256, 0, ctx->stream>>>(
+                partial, nc, n, q0, nr, (const double2 *)rhs, (const double2 *)X, Pbuf, S, adjoint,
+                (const double2 *)p->eps, p->eps_env, d3_4pi, (double2 *)r, norms2);
+        else
+            k_residual_finalize<6, 2><<<nb, 256, 0, ctx->stream>>>(
+                partial, nc, n, q0, nr, (const double2 *)rhs, (const double2 *)X, Pbuf, 0.0, 0, nullptr, 1.0, 0.0,
+                (double2 *)r, norms2);
+        GDM_LAUNCHED(ctx, "residual_finalize");
+    }
+    return GDM_OK;
+}
+
+// ================================================================== near field
+template <int OUT>
+__global__ void k_nearfield_finalize(const double2 *__restrict__ partial, int nchunks, int64_t m, int rhs0, int nr_here,
+                                     const double2 *__restrict__ F0e, int n_rhs_total, double2 *__restrict__ E,
+                                     double2 *__restrict__ H) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    for (int q = 0; q < nr_here; q++) {
+        int qq = rhs0 + q;
+        for (int a = 0; a < OUT; a++) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int c = 0; c < nchunks; c++) s = cadd(s, partial[((c * 2 + q) * m + t) * OUT + a]);
+            if (F0e) s = cadd(s, F0e[(int64_t)qq * 6 * m + 6 * t + a]);
+            if (a < 3) E[(int64_t)qq * 3 * m + 3 * t + a] = s;
+            else if (H) H[(int64_t)qq * 3 * m + 3 * t + a - 3] = s;
+        }
+    }
+}
+
+gdm_status gdm_launch_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, const double *r_eval, int64_t m,
+                                const double *F0_eval, int n_rhs, double *E_out, double *H_out) {
+    const int64_t n = p->n;
+    const int kind = p->kind;
+    double k0 = gdm_k0(p), k = sqrt(p->eps_env) * k0;
+    double d3_4pi = kind == 3 ? p->step * p->step * p->step / (4.0 * PI_D) : 0.0;
+    size_t need = ScratchCarver::round((size_t)kind * n * n_rhs * sizeof(double2)) +
+                  ScratchCarver::round(gdm_green_partial_bytes(ctx, m, n, 6)) + 1024;
+    void *ws;
+    GDM_TRY(gdm_scratch(ctx, need, &ws));
+    ScratchCarver sc(ws);
+    double2 *Pbuf = sc.take<double2>((size_t)kind * n * n_rhs);
+    double2 *partial = sc.take<double2>(gdm_green_partial_bytes(ctx, m, n, 6) / sizeof(double2));
+    dim3 g1((unsigned)((n + 127) / 128), (unsigned)n_rhs);
+    k_moments<<<g1, 128, 0, ctx->stream>>>((const double2 *)F, n, kind, n_rhs, (const double2 *)p->eps, p->eps_env,
+                                            d3_4pi, (const double2 *)p->alpha6, 0, Pbuf);
+    GDM_LAUNCHED(ctx, "moments");
+    for (int q0 = 0; q0 < n_rhs; q0 += 2) {
+        int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
+        int nc;
+        if (kind == 3)
+            GDM_TRY(launch_green_sum<3, 6>(ctx, r_eval, m, p->pos, Pbuf, n, q0, nr, k, k0, 1.0 / p->eps_env, 0,
+                                           partial, &nc));
+        else
+            GDM_TRY(launch_green_sum<6, 6>(ctx, r_eval, m, p->pos, Pbuf, n, q0, nr, k, k0, 1.0, 0, partial, &nc));
+        k_nearfield_finalize<6><<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(
+            partial, nc, m, q0, nr, (const double2 *)F0_eval, n_rhs, (double2 *)E_out, (double2 *)H_out);
+        GDM_LAUNCHED(ctx, "nearfield_finalize");
+    }
+    return GDM_OK;
+}
+
+// ================================================================== cross sections
+#define XS_BS 256
+__global__ void k_xsec_partial(const double2 *__restrict__ F0, const double2 *__restrict__ F, int64_t n, int kind,
+                               const double2 *__restrict__ eps, double eps_env, double d3_4pi,
+                               const double2 *__restrict__ alpha6, double rad, double *__restrict__ part) {
+    int q = blockIdx.y;
+    int64_t i = blockIdx.x * (int64_t)XS_BS + threadIdx.x;
+    double se = 0.0, sa = 0.0;
+    if (i < n) {
+        int64_t off = (int64_t)q * kind * n + kind * i;
+        const double2 *f0 = F0 + off;
+        const double2 *f = F + off;
+        double2 pm[6];
+        if (kind == 3) {
+            double2 al = make_double2((eps[i].x - eps_env) * d3_4pi, eps[i].y * d3_4pi);
+            for (int a = 0; a < 3; a++) pm[a] = cmul(al, f[a]);
+        } else {
+            const double2 *al = alpha6 + 36 * i;
+            for (int a = 0; a < 6; a++) {
+                double2 s = make_double2(0.0, 0.0);
+                for (int b = 0; b < 6; b++) cfma(s, al[6 * a + b], f[b]);
+                pm[a] = s;
+            }
+        }
+        for (int a = 0; a < kind; a++) {
+            se += cconjmul(f0[a], pm[a]).y;
+            sa += cconjmul(f[a], pm[a]).y;
+            if (kind == 6) sa -= rad * (pm[a].x * pm[a].x + pm[a].y * pm[a].y);
+        }
+    }
+    __shared__ double red[2][XS_BS / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        se += __shfl_down_sync(0xffffffffu, se, o);
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = se;
+        red[1][threadIdx.x >> 5] = sa;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int w = 0; w < XS_BS / 32; w++) {
+            a0 += red[0][w];
+            a1 += red[1][w];
+        }
+        part[((int64_t)q * gridDim.x + blockIdx.x) * 2] = a0;
+        part[((int64_t)q * gridDim.x + blockIdx.x) * 2 + 1] = a1;
+    }
+}
+
+__global__ void k_xsec_final(const double *__restrict__ part, int nblocks, int n_rhs, const double *__restrict__ pref,
+                             double *ext, double *sca, double *abs_) {
+    int q = blockIdx.x;
+    if (q >= n_rhs) return;
+    double a0 = 0.0, a1 = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 32) {
+        a0 += part[((int64_t)q * nblocks + b) * 2];
+        a1 += part[((int64_t)q * nblocks + b) * 2 + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_down_sync(0xffffffffu, a0, o);
+        a1 += __shfl_down_sync(0xffffffffu, a1, o);
+    }
+    if (threadIdx.x == 0) {
+        double e = pref[q] * a0, ab = pref[q] * a1;
+        if (ext) ext[q] = e;
+        if (abs_) abs_[q] = ab;
+        if (sca) sca[q] = e - ab;
+    }
+}
+
+gdm_status gdm_launch_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F, int n_rhs,
+                                     const double *e0_norm2, double *ext, double *sca, double *abs) {
+    const int64_t n = p->n;
+    double k = sqrt(p->eps_env) * gdm_k0(p);
+    double d3_4pi = p->kind == 3 ? p->step * p->step * p->step / (4.0 * PI_D) : 0.0;
+    double pref[64];
+    for (int q = 0; q < n_rhs; q++) pref[q] = 4.0 * PI_D * k / (p->eps_env * e0_norm2[q]);
+    double *dpref;
+    GDM_TRY(gdm_upload(ctx, pref, sizeof(double) * n_rhs, (void **)&dpref));
+    unsigned nb = (unsigned)((n + XS_BS - 1) / XS_BS);
+    void *ws;
+    GDM_TRY(gdm_scratch(ctx, (size_t)nb * n_rhs * 2 * sizeof(double) + 256, &ws));
+    double *part = (double *)ws;
+    double rad = (2.0 / 3.0) * k * k * k;
+    k_xsec_partial<<<dim3(nb, n_rhs), XS_BS, 0, ctx->stream>>>((const double2 *)F0, (const double2 *)F, n, p->kind,
+                                                               (const double2 *)p->eps, p->eps_env, d3_4pi,
+                                                               (const double2 *)p->alpha6, rad, part);
+    GDM_LAUNCHED(ctx, "xsec_partial");
+    k_xsec_final<<<n_rhs, 32, 0, ctx->stream>>>(part, (int)nb, n_rhs, dpref, ext, sca, abs);
+    GDM_LAUNCHED(ctx, "xsec_final");
+    return GDM_OK;
+}

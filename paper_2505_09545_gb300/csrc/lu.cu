@@ -1,0 +1,673 @@
+// Blocked complex LU factorisation with partial pivoting and blocked triangular solves
+// (Sec. "Numerical solution": the GDM system is solved by LU decomposition).
+//
+// Storage: column-major complex (float2 or double2), leading dimension lda.
+// Algorithm: right-looking blocked LU with outer block NB and panels of width NBP:
+//   for each outer block [b0, b0+nb):
+//     for each panel [c0, c0+w) inside the block:
+//       factor the tall panel rows [c0, n) with partial pivoting (cooperative kernel: the panel rows
+//         live in the shared memory of up to one CTA per SM, one bounded grid barrier per column);
+//       swap the same rows in the other columns of the block; triangular solve + GEMM update of the
+//         block's remaining columns;
+//     swap the block's pivot rows in the trailing columns, U12 = L11^{-1} A12, A22 -= A21 U12.
+// Left-of-block columns are never swapped: the forward solve applies each block's row swaps to the
+// right-hand side just before using that block's columns of L, which is equivalent.
+// For the FP32 precisions the trailing update A22 -= A21 U12 runs on the tcgen05 tensor cores
+// (lu_tc.cu); everything else uses the SIMT kernels of this file.
+#include <cooperative_groups.h>
+
+#include "gdm_internal.cuh"
+
+#define NBP 32        // panel width (columns per cooperative panel factorisation)
+#define PANEL_THREADS 256
+
+// tensor-core trailing update (lu_tc.cu); returns GDM_ERR_UNSUPPORTED when not applicable
+gdm_status gdm_tc_trailing_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t b0,
+                                  int64_t nb, void *ws, size_t ws_bytes);
+size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec);
+int gdm_lu_block(gdm_precision prec);
+
+// ------------------------------------------------------------------ bounded grid barrier
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All CTAs of a cooperative launch meet here. Gives up after ~2 s (sets GDM_ERR_TIMEOUT and
+// returns false) instead of spinning forever.
+__device__ bool grid_barrier(int *flags, unsigned nblocks) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile int *vgen = flags + GDM_FLAG_BAR_GEN;
+        int g = *vgen;
+        __threadfence();
+        int arrived = atomicAdd(flags + GDM_FLAG_BAR_COUNT, 1);
+        if (arrived == (int)nblocks - 1) {
+            atomicExch(flags + GDM_FLAG_BAR_COUNT, 0);
+            __threadfence();
+            atomicAdd(flags + GDM_FLAG_BAR_GEN, 1);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            unsigned it = 0;
+            while (*vgen == g) {
+                __nanosleep(32);
+                if ((++it & 1023) == 0 && (globaltimer_ns() - t0 > 2000000000ull || it > (1u << 26))) {
+                    gdm_dev_error(flags, GDM_ERR_TIMEOUT, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// ------------------------------------------------------------------ panel factorisation
+template <class C> struct PanelScratch {
+    double *cand_val;  // [2][P]
+    int64_t *cand_row; // [2][P]
+    C *cand_vals;      // [2][P][NBP]
+    C *top_row;        // [2][NBP]
+};
+
+template <class T> __device__ __forceinline__ T ld_cg(const T *p);
+template <> __device__ __forceinline__ float2 ld_cg<float2>(const float2 *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ double2 ld_cg<double2>(const double2 *p) { return __ldcg(p); }
+
+// Factor rows [c0, n) x cols [c0, c0+w) in place. CTA b owns rows [c0 + b*rpc, c0 + (b+1)*rpc).
+template <class C>
+__global__ void __launch_bounds__(PANEL_THREADS) k_panel(C *__restrict__ A, int64_t lda, int64_t n, int64_t c0, int w,
+                                                         int rpc, int32_t *__restrict__ ipiv, PanelScratch<C> ps,
+                                                         int *flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = (C *)smem_raw;  // [NBP][rpc], column-major
+    __shared__ C prow[NBP];
+    __shared__ double wv[PANEL_THREADS / 32];
+    __shared__ int64_t wr[PANEL_THREADS / 32];
+    __shared__ int64_t s_wrow;
+    __shared__ double s_wval;
+    __shared__ int s_wcta;
+    const unsigned P = gridDim.x;
+    const int b = blockIdx.x;
+    const int64_t r0 = c0 + (int64_t)b * rpc;
+    const int nr = (int)max((int64_t)0, min((int64_t)rpc, n - r0));
+    // load
+    for (int c = 0; c < w; c++)
+        for (int lr = threadIdx.x; lr < nr; lr += PANEL_THREADS) tile[c * rpc + lr] = A[(c0 + c) * lda + r0 + lr];
+    __syncthreads();
+    for (int t = 0; t < w; t++) {
+        const int par = t & 1;
+        // 1. local argmax of |re| + |im| over eligible rows (global row >= c0 + t)
+        int lstart = (b == 0) ? t : 0;
+        double best = -1.0;
+        int64_t brow = INT64_MAX;
+        for (int lr = lstart + threadIdx.x; lr < nr; lr += PANEL_THREADS) {
+            double v = (double)cabs1(tile[t * rpc + lr]);
+            if (v > best) {
+                best = v;
+                brow = r0 + lr;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_down_sync(0xffffffffu, best, o);
+            int64_t orow = __shfl_down_sync(0xffffffffu, brow, o);
+            if (ov > best || (ov == best && orow < brow)) {
+                best = ov;
+                brow = orow;
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+            wv[threadIdx.x >> 5] = best;
+            wr[threadIdx.x >> 5] = brow;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 1; k < PANEL_THREADS / 32; k++)
+                if (wv[k] > best || (wv[k] == best && wr[k] < brow)) {
+                    best = wv[k];
+                    brow = wr[k];
+                }
+            s_wval = best;
+            s_wrow = brow;
+        }
+        __syncthreads();
+        best = s_wval;
+        brow = s_wrow;
+        if (P > 1) {
+            // 2. publish candidate (and the current top row from CTA 0)
+            if (threadIdx.x == 0) {
+                ps.cand_val[par * P + b] = best;
+                ps.cand_row[par * P + b] = (best >= 0.0) ? brow : INT64_MAX;
+            }
+            if (threadIdx.x < w) {
+                if (best >= 0.0) ps.cand_vals[((size_t)par * P + b) * NBP + threadIdx.x] = tile[threadIdx.x * rpc + (brow - r0)];
+                if (b == 0) ps.top_row[par * NBP + threadIdx.x] = tile[threadIdx.x * rpc + t];
+            }
+            // 3. all CTAs meet
+            if (!grid_barrier(flags, P)) return;
+            // 4. global winner (max value, lowest row on ties)
+            if (threadIdx.x < 32) {
+                double v = -2.0;
+                int64_t rr = INT64_MAX;
+                int cb = 0;
+                for (int k = threadIdx.x; k < (int)P; k += 32) {
+                    double kv = __ldcg(ps.cand_val + par * P + k);
+                    int64_t kr = __ldcg((const long long *)(ps.cand_row + par * P + k));
+                    if (kv > v || (kv == v && kr < rr)) {
+                        v = kv;
+                        rr = kr;
+                        cb = k;
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    double ov = __shfl_down_sync(0xffffffffu, v, o);
+                    int64_t orr = __shfl_down_sync(0xffffffffu, rr, o);
+                    int ocb = __shfl_down_sync(0xffffffffu, cb, o);
+                    if (ov > v || (ov == v && orr < rr)) {
+                        v = ov;
+                        rr = orr;
+                        cb = ocb;
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    s_wval = v;
+                    s_wrow = rr;
+                    s_wcta = cb;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < w) prow[threadIdx.x] = ld_cg(ps.cand_vals + ((size_t)par * P + s_wcta) * NBP + threadIdx.x);
+        } else {
+            if (threadIdx.x < w) prow[threadIdx.x] = tile[threadIdx.x * rpc + (brow - r0)];
+        }
+        __syncthreads();
+        const int64_t wrow = s_wrow;
+        const double wval = s_wval;
+        const int64_t prow_g = c0 + t;
+        if (b == 0 && threadIdx.x == 0) {
+            ipiv[prow_g] = (int32_t)wrow;
+            if (!(wval > 0.0)) gdm_dev_error(flags, GDM_ERR_SINGULAR, (int)prow_g);
+        }
+        // 5. swap rows prow_g <-> wrow inside the panel
+        if (wrow != prow_g) {
+            int64_t owner = (wrow - c0) / rpc;
+            if (owner == b && threadIdx.x < w) {
+                C old = (P > 1) ? ld_cg(ps.top_row + par * NBP + threadIdx.x) : tile[threadIdx.x * rpc + t];
+                tile[threadIdx.x * rpc + (wrow - r0)] = old;
+            }
+            __syncthreads();
+            if (b == 0 && threadIdx.x < w) tile[threadIdx.x * rpc + t] = prow[threadIdx.x];
+        }
+        __syncthreads();
+        // 6. scale the pivot column and update the rest of the panel
+        C pv = prow[t];
+        C inv;
+        if (cabs1(pv) > 0) inv = crecip(pv);
+        else {
+            inv.x = 0;
+            inv.y = 0;
+        }
+        int ustart = (b == 0) ? t + 1 : 0;
+        for (int lr = ustart + threadIdx.x; lr < nr; lr += PANEL_THREADS) {
+            C l = cmul(tile[t * rpc + lr], inv);
+            tile[t * rpc + lr] = l;
+            for (int c = t + 1; c < w; c++) cfms(tile[c * rpc + lr], l, prow[c]);
+        }
+        __syncthreads();
+    }
+    for (int c = 0; c < w; c++)
+        for (int lr = threadIdx.x; lr < nr; lr += PANEL_THREADS) A[(c0 + c) * lda + r0 + lr] = tile[c * rpc + lr];
+}
+
+// ------------------------------------------------------------------ row interchanges
+// Apply pivots ipiv[k_begin..k_end) in order to columns [cb, ce) (one thread per column).
+template <class C>
+__global__ void k_laswp(C *__restrict__ A, int64_t lda, int64_t cb, int64_t ce, const int32_t *__restrict__ ipiv,
+                        int64_t k_begin, int64_t k_end) {
+    __shared__ int32_t sp[256];
+    int64_t col = cb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int nk = (int)(k_end - k_begin);
+    for (int t = threadIdx.x; t < nk; t += blockDim.x) sp[t] = ipiv[k_begin + t];
+    __syncthreads();
+    if (col >= ce) return;
+    C *a = A + col * lda;
+    for (int t = 0; t < nk; t++) {
+        int64_t r1 = k_begin + t, r2 = sp[t];
+        if (r2 != r1) {
+            C x = a[r1], y = a[r2];
+            a[r1] = y;
+            a[r2] = x;
+        }
+    }
+}
+
+// Same for a right-hand-side block B (ldb) with n_rhs columns; reverse order for the transpose.
+template <class C>
+__global__ void k_laswp_rhs(C *__restrict__ B, int64_t ldb, int n_rhs, const int32_t *__restrict__ ipiv,
+                            int64_t k_begin, int64_t k_end, int reverse) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_rhs) return;
+    C *b = B + q * ldb;
+    int nk = (int)(k_end - k_begin);
+    for (int s = 0; s < nk; s++) {
+        int t = reverse ? nk - 1 - s : s;
+        int64_t r1 = k_begin + t, r2 = ipiv[k_begin + t];
+        if (r2 != r1) {
+            C x = b[r1], y = b[r2];
+            b[r1] = y;
+            b[r2] = x;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ small triangular solves
+// X = L^{-1} B in place, L unit lower w x w at A[c0, c0]; B = A[c0 .. c0+w, cb .. ce) (one warp per column).
+template <class C>
+__global__ void k_trsm_small(C *__restrict__ A, int64_t lda, int64_t c0, int w, int64_t cb, int64_t ce) {
+    __shared__ C L[NBP][NBP + 1];
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int r = e % w, c = e / w;
+        L[r][c] = A[(c0 + c) * lda + c0 + r];
+    }
+    __syncthreads();
+    int lane = threadIdx.x & 31;
+    int64_t col = cb + (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (col >= ce) return;
+    C *bcol = A + col * lda + c0;
+    C v;
+    v.x = 0;
+    v.y = 0;
+    if (lane < w) v = bcol[lane];
+    for (int i = 0; i < w; i++) {
+        C xi;
+        xi.x = __shfl_sync(0xffffffffu, v.x, i);
+        xi.y = __shfl_sync(0xffffffffu, v.y, i);
+        if (lane > i && lane < w) cfms(v, L[lane][i], xi);
+    }
+    if (lane < w) bcol[lane] = v;
+}
+
+// ------------------------------------------------------------------ SIMT complex GEMM  C -= A * B
+#define GM_BM 64
+#define GM_BN 64
+#define GM_BK 16
+// C: M x N at Cp (ldc); A: M x K at Ap (lda); B: K x N at Bp (ldb); all column-major complex.
+template <class C>
+__global__ void __launch_bounds__(256) k_gemm_sub(C *__restrict__ Cp, int64_t ldc, const C *__restrict__ Ap,
+                                                  int64_t lda, const C *__restrict__ Bp, int64_t ldb, int64_t M,
+                                                  int64_t N, int64_t K) {
+    __shared__ C As[GM_BK][GM_BM + 1];
+    __shared__ C Bs[GM_BK][GM_BN + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t m0 = (int64_t)blockIdx.x * GM_BM, n0 = (int64_t)blockIdx.y * GM_BN;
+    C acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            acc[i][j].x = 0;
+            acc[i][j].y = 0;
+        }
+    for (int64_t k0 = 0; k0 < K; k0 += GM_BK) {
+        for (int e = threadIdx.x; e < GM_BK * GM_BM; e += 256) {
+            int mm = e % GM_BM, kk = e / GM_BM;
+            C v;
+            v.x = 0;
+            v.y = 0;
+            if (m0 + mm < M && k0 + kk < K) v = Ap[(k0 + kk) * lda + m0 + mm];
+            As[kk][mm] = v;
+        }
+        for (int e = threadIdx.x; e < GM_BK * GM_BN; e += 256) {
+            int kk = e % GM_BK, nn = e / GM_BK;
+            C v;
+            v.x = 0;
+            v.y = 0;
+            if (n0 + nn < N && k0 + kk < K) v = Bp[(n0 + nn) * ldb + k0 + kk];
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GM_BK; kk++) {
+            C a[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) bv[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) cfma(acc[i][j], a[i], bv[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        int64_t nn = n0 + ty + 16 * j;
+        if (nn >= N) continue;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            int64_t mm = m0 + tx + 16 * i;
+            if (mm >= M) continue;
+            C *c = Cp + nn * ldc + mm;
+            *c = csub(*c, acc[i][j]);
+        }
+    }
+}
+
+template <class C>
+static gdm_status gemm_sub(gdm_ctx *ctx, C *Cp, int64_t ldc, const C *Ap, int64_t lda, const C *Bp, int64_t ldb,
+                           int64_t M, int64_t N, int64_t K) {
+    if (M <= 0 || N <= 0 || K <= 0) return GDM_OK;
+    dim3 grid((unsigned)((M + GM_BM - 1) / GM_BM), (unsigned)((N + GM_BN - 1) / GM_BN));
+    if (grid.y > 65535) return gdm_fail(ctx, GDM_ERR_SHAPE, "gemm grid too large");
+    k_gemm_sub<C><<<grid, 256, 0, ctx->stream>>>(Cp, ldc, Ap, lda, Bp, ldb, M, N, K);
+    GDM_LAUNCHED(ctx, "gemm_sub");
+    return GDM_OK;
+}
+
+// ------------------------------------------------------------------ factorisation driver
+template <class C>
+static gdm_status panel_factor(gdm_ctx *ctx, C *A, int64_t lda, int64_t n, int64_t c0, int w, int32_t *ipiv,
+                               PanelScratch<C> ps, int pmax) {
+    int64_t m = n - c0;
+    int P = (int)((m + 255) / 256);
+    if (P > pmax) P = pmax;
+    if (P < 1) P = 1;
+    int rpc = (int)((m + P - 1) / P);
+    if (rpc < w) rpc = w;
+    P = (int)((m + rpc - 1) / rpc);
+    size_t smem = (size_t)NBP * rpc * sizeof(C);
+    if (smem > (size_t)ctx->max_smem_optin - 4096)
+        return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "panel of %lld rows does not fit the cooperative panel kernel",
+                        (long long)m);
+    static bool attr_set[2] = {false, false};
+    int slot = sizeof(C) == 8 ? 0 : 1;
+    if (!attr_set[slot]) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_panel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               ctx->max_smem_optin - 4096));
+        attr_set[slot] = true;
+    }
+    if (P > 1) GDM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dflags + GDM_FLAG_BAR_COUNT, 0, sizeof(int), ctx->stream));
+    int *flags = ctx->dflags;
+    void *args[] = {&A, &lda, &n, &c0, &w, &rpc, &ipiv, &ps, &flags};
+    if (P > 1) {
+        GDM_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void *)k_panel<C>, dim3(P), dim3(PANEL_THREADS), args, smem,
+                                                      ctx->stream));
+    } else {
+        k_panel<C><<<1, PANEL_THREADS, smem, ctx->stream>>>(A, lda, n, c0, w, rpc, ipiv, ps, flags);
+    }
+    GDM_LAUNCHED(ctx, "panel");
+    return GDM_OK;
+}
+
+template <class C>
+static gdm_status laswp(gdm_ctx *ctx, C *A, int64_t lda, int64_t cb, int64_t ce, const int32_t *ipiv, int64_t kb,
+                        int64_t ke) {
+    if (ce <= cb || ke <= kb) return GDM_OK;
+    if (ke - kb > 256) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "laswp block too large");
+    unsigned nb = (unsigned)((ce - cb + 127) / 128);
+    k_laswp<C><<<nb, 128, 0, ctx->stream>>>(A, lda, cb, ce, ipiv, kb, ke);
+    GDM_LAUNCHED(ctx, "laswp");
+    return GDM_OK;
+}
+
+template <class C>
+static gdm_status trsm_small(gdm_ctx *ctx, C *A, int64_t lda, int64_t c0, int w, int64_t cb, int64_t ce) {
+    if (ce <= cb) return GDM_OK;
+    const int wpb = 8;
+    unsigned nb = (unsigned)((ce - cb + wpb - 1) / wpb);
+    k_trsm_small<C><<<nb, wpb * 32, 0, ctx->stream>>>(A, lda, c0, w, cb, ce);
+    GDM_LAUNCHED(ctx, "trsm_small");
+    return GDM_OK;
+}
+
+int gdm_lu_block(gdm_precision prec) { return prec == GDM_FP64 ? 128 : 256; }
+
+template <class C>
+static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n, int64_t lda, int32_t *ipiv) {
+    const int NB = gdm_lu_block(prec);
+    int pmax = ctx->sm_count;
+    // scratch: panel candidates + tensor-core operand buffers
+    size_t pbytes = ScratchCarver::round(2 * pmax * sizeof(double)) + ScratchCarver::round(2 * pmax * sizeof(int64_t)) +
+                    ScratchCarver::round((size_t)2 * pmax * NBP * sizeof(C)) +
+                    ScratchCarver::round(2 * NBP * sizeof(C));
+    size_t tcbytes = (sizeof(C) == 8) ? gdm_tc_workspace_bytes(n, NB, prec) : 0;
+    void *ws;
+    GDM_TRY(gdm_scratch(ctx, pbytes + tcbytes + 1024, &ws));
+    ScratchCarver sc(ws);
+    PanelScratch<C> ps;
+    ps.cand_val = sc.take<double>(2 * pmax);
+    ps.cand_row = sc.take<int64_t>(2 * pmax);
+    ps.cand_vals = sc.take<C>((size_t)2 * pmax * NBP);
+    ps.top_row = sc.take<C>(2 * NBP);
+    void *tcws = tcbytes ? sc.take<char>(tcbytes) : nullptr;
+    for (int64_t b0 = 0; b0 < n; b0 += NB) {
+        int64_t nb = n - b0 < NB ? n - b0 : NB;
+        int64_t be = b0 + nb;
+        for (int64_t c0 = b0; c0 < be; c0 += NBP) {
+            int w = (int)(be - c0 < NBP ? be - c0 : NBP);
+            GDM_TRY(panel_factor<C>(ctx, A, lda, n, c0, w, ipiv, ps, pmax));
+            GDM_TRY(laswp<C>(ctx, A, lda, b0, c0, ipiv, c0, c0 + w));
+            GDM_TRY(laswp<C>(ctx, A, lda, c0 + w, be, ipiv, c0, c0 + w));
+            if (c0 + w < be) {
+                GDM_TRY(trsm_small<C>(ctx, A, lda, c0, w, c0 + w, be));
+                GDM_TRY(gemm_sub<C>(ctx, A + (c0 + w) * lda + c0 + w, lda, A + c0 * lda + c0 + w, lda,
+                                    A + (c0 + w) * lda + c0, lda, n - c0 - w, be - c0 - w, w));
+            }
+        }
+        if (be < n) {
+            GDM_TRY(laswp<C>(ctx, A, lda, be, n, ipiv, b0, be));
+            // U12 = L11^{-1} A12, blocked by panels
+            for (int64_t c0 = b0; c0 < be; c0 += NBP) {
+                int w = (int)(be - c0 < NBP ? be - c0 : NBP);
+                GDM_TRY(trsm_small<C>(ctx, A, lda, c0, w, be, n));
+                if (c0 + w < be)
+                    GDM_TRY(gemm_sub<C>(ctx, A + be * lda + c0 + w, lda, A + c0 * lda + c0 + w, lda, A + be * lda + c0,
+                                        lda, be - c0 - w, n - be, w));
+            }
+            // A22 -= A21 U12
+            gdm_status s = GDM_ERR_UNSUPPORTED;
+            if (sizeof(C) == 8 && tcws)
+                s = gdm_tc_trailing_update(ctx, prec, (float2 *)A, lda, n, b0, nb, tcws, tcbytes);
+            if (s == GDM_ERR_UNSUPPORTED)
+                s = gemm_sub<C>(ctx, A + be * lda + be, lda, A + b0 * lda + be, lda, A + be * lda + b0, lda, n - be,
+                                n - be, nb);
+            GDM_TRY(s);
+        }
+    }
+    return GDM_OK;
+}
+
+gdm_status gdm_lu_factor(gdm_ctx *ctx, gdm_precision prec, void *A, int64_t n, int64_t lda, int32_t *ipiv) {
+    if (prec == GDM_FP64) return lu_factor_t<double2>(ctx, prec, (double2 *)A, n, lda, ipiv);
+    return lu_factor_t<float2>(ctx, prec, (float2 *)A, n, lda, ipiv);
+}
+
+// ------------------------------------------------------------------ triangular solves on right-hand sides
+// Diagonal-block solve for one panel (w <= NBP): lower unit (forward) or upper non-unit (backward);
+// conj = 1 solves with the conjugate transpose of the stored triangle. One warp per RHS column.
+template <class C>
+__global__ void k_trsv_diag(const C *__restrict__ A, int64_t lda, int64_t c0, int w, C *__restrict__ B, int64_t ldb,
+                            int n_rhs, int upper, int conj) {
+    __shared__ C T[NBP][NBP + 1];
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int r = e % w, c = e / w;
+        C v = A[(c0 + c) * lda + c0 + r];
+        if (conj) {
+            v.y = -v.y;
+            T[c][r] = v;  // transpose
+        } else
+            T[r][c] = v;
+    }
+    __syncthreads();
+    int lane = threadIdx.x & 31;
+    int q = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (q >= n_rhs) return;
+    C *b = B + q * ldb + c0;
+    C v;
+    v.x = 0;
+    v.y = 0;
+    if (lane < w) v = b[lane];
+    // effective triangle after the optional conjugate transpose
+    bool eff_upper = conj ? !upper : upper;
+    bool unit = !upper;  // L is unit diagonal, U is not (transpose keeps the diagonal)
+    if (!eff_upper) {
+        for (int i = 0; i < w; i++) {
+            if (!unit && lane == i) v = cmul(v, crecip(T[i][i]));
+            C xi;
+            xi.x = __shfl_sync(0xffffffffu, v.x, i);
+            xi.y = __shfl_sync(0xffffffffu, v.y, i);
+            if (lane > i && lane < w) cfms(v, T[lane][i], xi);
+        }
+    } else {
+        for (int i = w - 1; i >= 0; i--) {
+            if (!unit && lane == i) v = cmul(v, crecip(T[i][i]));
+            C xi;
+            xi.x = __shfl_sync(0xffffffffu, v.x, i);
+            xi.y = __shfl_sync(0xffffffffu, v.y, i);
+            if (lane < i) cfms(v, T[lane][i], xi);
+        }
+    }
+    if (lane < w) b[lane] = v;
+}
+
+// y[r0:r1] -= M[r0:r1, c0:c0+w] * y[c0:c0+w]   (thread per row, loop over RHS)
+template <class C>
+__global__ void k_gemv_sub(const C *__restrict__ A, int64_t lda, int64_t r0, int64_t r1, int64_t c0, int w,
+                           C *__restrict__ B, int64_t ldb, int n_rhs) {
+    __shared__ C xs[NBP][8];
+    int64_t r = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int q0 = 0; q0 < n_rhs; q0 += 8) {
+        int nq = n_rhs - q0 < 8 ? n_rhs - q0 : 8;
+        __syncthreads();
+        for (int e = threadIdx.x; e < w * nq; e += blockDim.x) xs[e % w][e / w] = B[(q0 + e / w) * ldb + c0 + e % w];
+        __syncthreads();
+        if (r < r1) {
+            C acc[8];
+            for (int q = 0; q < 8; q++) {
+                acc[q].x = 0;
+                acc[q].y = 0;
+            }
+            for (int c = 0; c < w; c++) {
+                C a = A[(c0 + c) * lda + r];
+                for (int q = 0; q < nq; q++) cfma(acc[q], a, xs[c][q]);
+            }
+            for (int q = 0; q < nq; q++) {
+                C *y = B + (q0 + q) * ldb + r;
+                *y = csub(*y, acc[q]);
+            }
+        }
+    }
+}
+
+// y[c0:c0+w] -= M[r0:r1, c0:c0+w]^H * y[r0:r1]   (block per column of M, reduction over rows)
+template <class C>
+__global__ void k_gemv_h_sub(const C *__restrict__ A, int64_t lda, int64_t r0, int64_t r1, int64_t c0,
+                             C *__restrict__ B, int64_t ldb, int n_rhs) {
+    int c = blockIdx.x;
+    int q = blockIdx.y;
+    const C *a = A + (c0 + c) * lda;
+    const C *y = B + q * ldb;
+    double sx = 0, sy = 0;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        C m = a[r], v = y[r];
+        // conj(m) * v
+        sx += (double)m.x * v.x + (double)m.y * v.y;
+        sy += (double)m.x * v.y - (double)m.y * v.x;
+    }
+    __shared__ double rx[32], ry[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rx[threadIdx.x >> 5] = sx;
+        ry[threadIdx.x >> 5] = sy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+            sx += rx[k];
+            sy += ry[k];
+        }
+        C *o = B + q * ldb + c0 + c;
+        o->x -= sx;
+        o->y -= sy;
+    }
+}
+
+template <class C>
+static gdm_status lu_solve_t(gdm_ctx *ctx, gdm_precision prec, const C *A, int64_t n, int64_t lda,
+                             const int32_t *ipiv, C *B, int64_t ldb, int n_rhs, int conj_trans) {
+    const int NB = gdm_lu_block(prec);
+    const int wpb = 4;
+    unsigned nbq = (unsigned)((n_rhs + wpb - 1) / wpb);
+    if (!conj_trans) {
+        for (int64_t b0 = 0; b0 < n; b0 += NB) {
+            int64_t be = b0 + NB < n ? b0 + NB : n;
+            k_laswp_rhs<C><<<(n_rhs + 31) / 32, 32, 0, ctx->stream>>>(B, ldb, n_rhs, ipiv, b0, be, 0);
+            GDM_LAUNCHED(ctx, "laswp_rhs");
+            for (int64_t c0 = b0; c0 < be; c0 += NBP) {
+                int w = (int)(be - c0 < NBP ? be - c0 : NBP);
+                k_trsv_diag<C><<<nbq, wpb * 32, 0, ctx->stream>>>(A, lda, c0, w, B, ldb, n_rhs, 0, 0);
+                GDM_LAUNCHED(ctx, "trsv_diag");
+                if (c0 + w < n) {
+                    k_gemv_sub<C><<<(unsigned)((n - c0 - w + 255) / 256), 256, 0, ctx->stream>>>(A, lda, c0 + w, n, c0,
+                                                                                                w, B, ldb, n_rhs);
+                    GDM_LAUNCHED(ctx, "gemv_sub");
+                }
+            }
+        }
+        for (int64_t c0 = ((n - 1) / NBP) * NBP; c0 >= 0; c0 -= NBP) {
+            int w = (int)(n - c0 < NBP ? n - c0 : NBP);
+            k_trsv_diag<C><<<nbq, wpb * 32, 0, ctx->stream>>>(A, lda, c0, w, B, ldb, n_rhs, 1, 0);
+            GDM_LAUNCHED(ctx, "trsv_diag");
+            if (c0 > 0) {
+                k_gemv_sub<C><<<(unsigned)((c0 + 255) / 256), 256, 0, ctx->stream>>>(A, lda, 0, c0, c0, w, B, ldb,
+                                                                                     n_rhs);
+                GDM_LAUNCHED(ctx, "gemv_sub");
+            }
+        }
+    } else {
+        // A^{-H} = P_1^T L_1^{-H} ... P_S^T L_S^{-H} U^{-H}: first U^H z = b (forward), then per block
+        // (last to first): z_b -= L21^H z_rest; z_b = L_bb^{-H} z_b; undo the block's row swaps.
+        for (int64_t c0 = 0; c0 < n; c0 += NBP) {
+            int w = (int)(n - c0 < NBP ? n - c0 : NBP);
+            if (c0 > 0) {
+                k_gemv_h_sub<C><<<dim3(w, n_rhs), 256, 0, ctx->stream>>>(A, lda, 0, c0, c0, B, ldb, n_rhs);
+                GDM_LAUNCHED(ctx, "gemv_h_sub");
+            }
+            k_trsv_diag<C><<<nbq, wpb * 32, 0, ctx->stream>>>(A, lda, c0, w, B, ldb, n_rhs, 1, 1);
+            GDM_LAUNCHED(ctx, "trsv_diag");
+        }
+        int64_t last_b0 = ((n - 1) / NB) * NB;
+        for (int64_t b0 = last_b0; b0 >= 0; b0 -= NB) {
+            int64_t be = b0 + NB < n ? b0 + NB : n;
+            int64_t last_c0 = b0 + ((be - 1 - b0) / NBP) * NBP;
+            for (int64_t c0 = last_c0; c0 >= b0; c0 -= NBP) {
+                int w = (int)(be - c0 < NBP ? be - c0 : NBP);
+                if (c0 + w < n) {
+                    k_gemv_h_sub<C><<<dim3(w, n_rhs), 256, 0, ctx->stream>>>(A, lda, c0 + w, n, c0, B, ldb, n_rhs);
+                    GDM_LAUNCHED(ctx, "gemv_h_sub");
+                }
+                k_trsv_diag<C><<<nbq, wpb * 32, 0, ctx->stream>>>(A, lda, c0, w, B, ldb, n_rhs, 0, 1);
+                GDM_LAUNCHED(ctx, "trsv_diag");
+            }
+            k_laswp_rhs<C><<<(n_rhs + 31) / 32, 32, 0, ctx->stream>>>(B, ldb, n_rhs, ipiv, b0, be, 1);
+            GDM_LAUNCHED(ctx, "laswp_rhs");
+        }
+    }
+    return GDM_OK;
+}
+
+gdm_status gdm_lu_solve(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda, const int32_t *ipiv,
+                        void *B, int64_t ldb, int n_rhs, int conj_trans) {
+    if (prec == GDM_FP64)
+        return lu_solve_t<double2>(ctx, prec, (const double2 *)A, n, lda, ipiv, (double2 *)B, ldb, n_rhs, conj_trans);
+    return lu_solve_t<float2>(ctx, prec, (const float2 *)A, n, lda, ipiv, (float2 *)B, ldb, n_rhs, conj_trans);
+}

@@ -1,0 +1,183 @@
+// Mixed-precision iterative refinement of the GDM solve.
+//
+// X_0 = LU^{-1} b in the factor precision; then repeat
+//   r = b - A X          (FP64, matrix-free: the Green dyads are regenerated in FP64 per pair)
+//   d = LU^{-1} r        (factor precision)
+//   X = X + d            (FP64)
+// until max_q ||d_q|| / ||X_q|| <= tol. The adjoint variant solves A^H X = b with the same factors
+// (conjugate-transposed triangular solves) and the matrix-free residual b - A^H X.
+#include <math.h>
+
+#include "gdm_internal.cuh"
+
+gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
+                                  int adjoint, double *r, double *norms2, double2 *Pbuf, double2 *partial);
+size_t gdm_green_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n, int out);
+
+template <class C>
+__global__ void k_to_work(const double2 *__restrict__ src, C *__restrict__ dst, int64_t count, double scale) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    C v;
+    v.x = src[i].x * scale;
+    v.y = src[i].y * scale;
+    dst[i] = v;
+}
+
+// X (+)= d/scale ; accumulate ||d||^2 and ||X||^2 per RHS; flag non-finite values
+template <class C>
+__global__ void k_update(double2 *__restrict__ X, const C *__restrict__ d, int64_t ld, int n_rhs, int accumulate,
+                         double inv_scale, double *__restrict__ norms, int *flags) {
+    int q = blockIdx.y;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double dn = 0.0, xn = 0.0;
+    if (i < ld) {
+        C dv = d[q * ld + i];
+        double dx = dv.x * inv_scale, dy = dv.y * inv_scale;
+        double2 x = accumulate ? X[q * ld + i] : make_double2(0.0, 0.0);
+        x.x += dx;
+        x.y += dy;
+        X[q * ld + i] = x;
+        dn = dx * dx + dy * dy;
+        xn = x.x * x.x + x.y * x.y;
+        if (!isfinite(xn)) gdm_dev_error(flags, GDM_ERR_NONFINITE, (int)i);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dn += __shfl_down_sync(0xffffffffu, dn, o);
+        xn += __shfl_down_sync(0xffffffffu, xn, o);
+    }
+    __shared__ double rd[32], rx[32];
+    if ((threadIdx.x & 31) == 0) {
+        rd[threadIdx.x >> 5] = dn;
+        rx[threadIdx.x >> 5] = xn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            dn += rd[w];
+            xn += rx[w];
+        }
+        atomicAdd(&norms[2 * q], dn);
+        atomicAdd(&norms[2 * q + 1], xn);
+    }
+}
+
+__global__ void k_norm2(const double2 *__restrict__ v, int64_t ld, double *__restrict__ out) {
+    int q = blockIdx.y;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (i < ld) {
+        double2 x = v[q * ld + i];
+        s = x.x * x.x + x.y * x.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ double r[32];
+    if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) s += r[w];
+        atomicAdd(&out[q], s);
+    }
+}
+
+template <class C>
+static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
+                            const int32_t *ipiv, const double *rhs, double *X, int n_rhs, int adjoint,
+                            const gdm_solve_opts *opts, gdm_solve_info *info) {
+    const int64_t ns = p->n * p->kind;
+    const int64_t cnt = ns * n_rhs;
+    size_t need = ScratchCarver::round(cnt * sizeof(double2)) * 2 + ScratchCarver::round(cnt * sizeof(C)) +
+                  ScratchCarver::round(gdm_green_partial_bytes(ctx, p->n, p->n, p->kind)) +
+                  ScratchCarver::round(sizeof(double) * 4 * n_rhs) + 4096;
+    // the LU scratch is not needed any more: the refinement reuses the arena
+    void *ws;
+    GDM_TRY(gdm_scratch(ctx, need, &ws));
+    ScratchCarver sc(ws);
+    double2 *r = sc.take<double2>(cnt);
+    double2 *Pbuf = sc.take<double2>(cnt);
+    C *w = sc.take<C>(cnt);
+    double2 *partial = sc.take<double2>(gdm_green_partial_bytes(ctx, p->n, p->n, p->kind) / sizeof(double2));
+    double *dnorm = sc.take<double>(4 * n_rhs);
+    double *hn;
+    GDM_TRY(gdm_pinned(ctx, sizeof(double) * 4 * n_rhs, (void **)&hn));
+    const unsigned nb = (unsigned)((ns + 255) / 256);
+    const dim3 gq(nb, (unsigned)n_rhs);
+    // ||b||^2 for the relative residual
+    GDM_CUDA_TRY(ctx, cudaMemsetAsync(dnorm, 0, sizeof(double) * 4 * n_rhs, ctx->stream));
+    k_norm2<<<gq, 256, 0, ctx->stream>>>((const double2 *)rhs, ns, dnorm + 3 * n_rhs);
+    GDM_LAUNCHED(ctx, "norm2");
+    if (info) GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
+    // initial solve
+    k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>((const double2 *)rhs, w, cnt, 1.0);
+    GDM_LAUNCHED(ctx, "to_work");
+    GDM_TRY(gdm_lu_solve(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint));
+    k_update<C><<<gq, 256, 0, ctx->stream>>>((double2 *)X, w, ns, n_rhs, 0, 1.0, dnorm, ctx->dflags);
+    GDM_LAUNCHED(ctx, "update");
+    int it = 0;
+    double relc = 1.0, relr = -1.0;
+    if (!(opts->flags & GDM_SOLVE_NO_REFINE)) {
+        for (it = 1; it <= opts->max_iter; it++) {
+            GDM_CUDA_TRY(ctx, cudaMemsetAsync(dnorm, 0, sizeof(double) * 3 * n_rhs, ctx->stream));
+            GDM_TRY(gdm_launch_residual_ws(ctx, p, rhs, X, n_rhs, adjoint, (double *)r, dnorm + 2 * n_rhs, Pbuf,
+                                           partial));
+            // scale the residual into a safe FP32 range before the low-precision solve
+            k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(r, w, cnt, 1.0);
+            GDM_LAUNCHED(ctx, "to_work");
+            GDM_TRY(gdm_lu_solve(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint));
+            k_update<C><<<gq, 256, 0, ctx->stream>>>((double2 *)X, w, ns, n_rhs, 1, 1.0, dnorm, ctx->dflags);
+            GDM_LAUNCHED(ctx, "update");
+            GDM_CUDA_TRY(ctx, cudaMemcpyAsync(hn, dnorm, sizeof(double) * 4 * n_rhs, cudaMemcpyDeviceToHost,
+                                              ctx->stream));
+            GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            relc = 0.0;
+            relr = 0.0;
+            bool finite = true;
+            for (int q = 0; q < n_rhs; q++) {
+                double dq = hn[2 * q], xq = hn[2 * q + 1], rq = hn[2 * n_rhs + q], bq = hn[3 * n_rhs + q];
+                if (!isfinite(dq) || !isfinite(xq) || !isfinite(rq)) finite = false;
+                double c = xq > 0 ? sqrt(dq / xq) : (dq > 0 ? INFINITY : 0.0);
+                double rr = bq > 0 ? sqrt(rq / bq) : 0.0;
+                if (c > relc) relc = c;
+                if (rr > relr) relr = rr;
+            }
+            if (!finite) {
+                if (info) {
+                    info->iterations = it;
+                    info->status = GDM_ERR_NONFINITE;
+                }
+                return gdm_fail(ctx, GDM_ERR_NONFINITE, "non-finite values in the refined solution");
+            }
+            if (relc <= opts->tol) break;
+        }
+        if (it > opts->max_iter) it = opts->max_iter;
+    }
+    if (info) {
+        GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, ctx->stream));
+        GDM_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev2));
+        float ms = 0.f;
+        GDM_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev1, ctx->ev2));
+        info->refine_ms = ms;
+        info->iterations = (opts->flags & GDM_SOLVE_NO_REFINE) ? 0 : it;
+        info->rel_correction = relc;
+        info->rel_residual = relr;
+    }
+    if (!(opts->flags & GDM_SOLVE_NO_REFINE)) {
+        // the loop synchronised the stream already: collect device-side errors of the whole solve
+        gdm_status dev = gdm_ctx_check(ctx);
+        if (info) info->status = dev;
+        if (dev != GDM_OK) return dev;
+        if (relc > opts->tol) {
+            if (info) info->status = GDM_ERR_NOT_CONVERGED;
+            return gdm_fail(ctx, GDM_ERR_NOT_CONVERGED, "refinement stopped at relative correction %.3e > tol %.3e",
+                            relc, opts->tol);
+        }
+    }
+    return GDM_OK;
+}
+
+gdm_status gdm_refined_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
+                             const int32_t *ipiv, const double *rhs, double *X, int n_rhs, int adjoint,
+                             const gdm_solve_opts *opts, gdm_solve_info *info) {
+    if (prec == GDM_FP64) return refined_t<double2>(ctx, p, prec, A, lda, ipiv, rhs, X, n_rhs, adjoint, opts, info);
+    return refined_t<float2>(ctx, p, prec, A, lda, ipiv, rhs, X, n_rhs, adjoint, opts, info);
+}

@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU FP64 oracle.
+
+Tolerances (stated by the method's target accuracy):
+* assembled matrix, complex64: |dA| <= 1e-6 * max|entry of the 3x3 (6x6) block| per block;
+* assembled matrix, complex128: 1e-12 relative per block;
+* refined fields: ||dF_q|| / ||F_q|| <= 1e-9 per illumination;
+* near fields and cross sections: 1e-9 relative (absolute floor 1e-9 * max value).
+Sizes span several tiles with ragged tails (3N not a multiple of any tile size).
+"""
+import numpy as np
+import pytest
+import torch
+
+import gdm_workloads as W
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+@pytest.fixture(scope="module")
+def G():
+    import paper_2505_09545_gb300 as G
+    return G
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    c = G.Context(0)
+    yield c
+    c.close()
+
+
+def t(x):
+    return torch.tensor(np.ascontiguousarray(x), device=DEV)
+
+
+def gpu_problem(G, s, lam):
+    if s.kind == 3:
+        return G.GDMProblem(t(s.pos), lam, 3, eps=t(s.eps), step=s.step)
+    al = O.lorentz_alpha6(s.omega0_e, s.omega0_m, s.gamma_ev, s.amp_nm, lam)
+    return G.GDMProblem(t(s.pos), lam, 6, alpha6=t(al))
+
+
+def oracle_problem(s, lam):
+    if s.kind == 3:
+        return O.Problem(s.pos, lam, 3, eps=s.eps, step=s.step)
+    return O.Problem(s.pos, lam, 6, alpha6=O.lorentz_alpha6(s.omega0_e, s.omega0_m, s.gamma_ev, s.amp_nm, lam))
+
+
+def block_errors(Ag, Ao, kind):
+    """max over blocks of max|dA_block| / max|A_block|."""
+    n = Ao.shape[0] // kind
+    d = np.abs(Ag - Ao).reshape(n, kind, n, kind).max(axis=(1, 3))
+    m = np.abs(Ao).reshape(n, kind, n, kind).max(axis=(1, 3))
+    return (d / m).max()
+
+
+def structures():
+    return [W.random_cells(150, seed=1), W.random_cells(61, seed=2, lossy=False)]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp64", 1e-12)])
+def test_assembly_cells(G, ctx, prec, tol):
+    for s in structures():
+        lam = float(s.wavelengths[0])
+        A = G.assemble(ctx, gpu_problem(G, s, lam), prec)
+        ns = 3 * s.n
+        Ag = A.cpu().numpy()[:, :ns].T
+        Ao = oracle_problem(s, lam).matrix()
+        assert block_errors(Ag, Ao, 3) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp64", 1e-12)])
+def test_assembly_edmd(G, ctx, prec, tol):
+    s = W.metasurface_edmd(nx=7, ny=5, pitch=400.0)
+    lam = 640.0
+    A = G.assemble(ctx, gpu_problem(G, s, lam), prec)
+    Ag = A.cpu().numpy()[:, :6 * s.n].T
+    Ao = oracle_problem(s, lam).matrix()
+    assert block_errors(Ag, Ao, 6) < tol
+
+
+def test_assembly_large_phase(G, ctx):
+    """Config-4 extent: kR up to ~450 rad needs the double-float phase."""
+    s = W.metasurface_edmd(nx=64, ny=64, pitch=400.0)
+    rng = np.random.default_rng(0)
+    sub = np.sort(rng.choice(s.n, 40, replace=False))
+    s.pos = s.pos[sub]
+    s.omega0_e, s.omega0_m = s.omega0_e[sub], s.omega0_m[sub]
+    lam = 500.0
+    A = G.assemble(ctx, gpu_problem(G, s, lam), "fp32")
+    Ag = A.cpu().numpy()[:, :6 * s.n].T
+    Ao = oracle_problem(s, lam).matrix()
+    assert block_errors(Ag, Ao, 6) < 1e-6
+
+
+def test_planewave(G, ctx):
+    s = W.random_cells(70, seed=4)
+    F0 = G.incident_planewave(ctx, t(s.pos), 530.0, W.XYPOL, kind_out=6)
+    ref = O.plane_wave(s.pos, 2 * np.pi / 530.0, 1.0, W.XYPOL, (0, 0, 1.0), 6)
+    np.testing.assert_allclose(F0.cpu().numpy().T, ref, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+def test_solve_cells(G, ctx, prec):
+    for s in structures():
+        lam = float(s.wavelengths[0])
+        prob = gpu_problem(G, s, lam)
+        F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0)
+        A = G.assemble(ctx, prob, prec)
+        F, ipiv, info = G.solve(ctx, prob, A, F0, prec)
+        pr = oracle_problem(s, lam)
+        Fo = pr.solve(pr.plane_wave(s.e0))
+        err = np.linalg.norm(F.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+        assert np.all(err < 1e-9), (prec, err, info)
+
+
+def test_solve_sphere_config(G, ctx):
+    """The plain-FP64 sphere workload (N = 925, 3N = 2775): fields, near field on the 968-point grid,
+    cross sections."""
+    s = W.sphere_plain_fp64()
+    lam = float(s.wavelengths[0])
+    prob = gpu_problem(G, s, lam)
+    F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0)
+    A = G.assemble(ctx, prob, "fp64")
+    F, ipiv, info = G.solve(ctx, prob, A, F0, "fp64")
+    r_eval = t(s.r_eval)
+    F0e = G.incident_planewave(ctx, r_eval, lam, s.e0, kind_out=6)
+    E, H = G.nearfield(ctx, prob, F, r_eval, F0e)
+    ext, sca, ab = G.cross_sections(ctx, prob, F0, F, np.ones(s.n_rhs))
+    pr = oracle_problem(s, lam)
+    F0o = pr.plane_wave(s.e0)
+    Fo = pr.solve(F0o)
+    err = np.linalg.norm(F.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+    assert np.all(err < 1e-9), err
+    Eo, Ho = pr.nearfield(Fo, s.r_eval, s.e0)
+    for g, o in ((E, Eo), (H, Ho)):
+        go = g.cpu().numpy().T.reshape(-1, 3, s.n_rhs)
+        np.testing.assert_allclose(go.reshape(o.shape), o, rtol=1e-9, atol=1e-9 * np.abs(o).max())
+    xo = pr.cross_sections(F0o, Fo, s.e0)
+    for g, o in zip((ext, sca, ab), xo):
+        np.testing.assert_allclose(g.cpu().numpy(), o, rtol=1e-9, atol=1e-9 * abs(xo[0]).max())
+
+
+def test_nearfield_kernel_isolated(G, ctx):
+    """Near field from the oracle's own fields (isolates the repropagation kernel), kinds 3 and 6."""
+    for s, lam in ((W.random_cells(90, seed=8), 555.0), (W.metasurface_edmd(nx=6, ny=6), 700.0)):
+        pr = oracle_problem(s, lam)
+        Fo = pr.solve(pr.plane_wave(s.e0))
+        rng = np.random.default_rng(1)
+        r_eval = rng.uniform(-2000, 2000, (300, 3)) + np.array([0, 0, 3000.0])
+        E, H = G.nearfield(ctx, gpu_problem(G, s, lam), t(Fo.T), t(r_eval), None)
+        Eo, Ho = pr.nearfield(Fo, r_eval, s.e0, with_incident=False)
+        np.testing.assert_allclose(E.cpu().numpy().T.reshape(Eo.shape[0], 3, -1), Eo, rtol=1e-10,
+                                   atol=1e-10 * np.abs(Eo).max())
+        np.testing.assert_allclose(H.cpu().numpy().T.reshape(Ho.shape[0], 3, -1), Ho, rtol=1e-10,
+                                   atol=1e-10 * np.abs(Ho).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_solve_edmd(G, ctx, prec):
+    s = W.metasurface_edmd(nx=9, ny=7, pitch=400.0)
+    lam = 610.0
+    prob = gpu_problem(G, s, lam)
+    F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0, kind_out=6)
+    A = G.assemble(ctx, prob, prec)
+    F, ipiv, info = G.solve(ctx, prob, A, F0, prec)
+    pr = oracle_problem(s, lam)
+    F0o = pr.plane_wave(s.e0)
+    Fo = pr.solve(F0o)
+    err = np.linalg.norm(F.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+    assert np.all(err < 1e-9), err
+    ext, sca, ab = G.cross_sections(ctx, prob, F0, F, np.ones(s.n_rhs))
+    xo = pr.cross_sections(F0o, Fo, s.e0)
+    for g, o in zip((ext, sca, ab), xo):
+        np.testing.assert_allclose(g.cpu().numpy(), o, rtol=1e-9, atol=1e-9 * abs(xo[0]).max())
+
+
+def test_single_dipole_and_single_cell(G, ctx):
+    """Degenerate sizes: one cell (N = 1) and one effective dipole."""
+    s = W.Structure(name="one", kind=3, pos=np.zeros((1, 3)), step=7.0, eps=np.array([4.0 + 1.0j]),
+                    wavelengths=np.array([500.0]), e0=W.XYPOL.copy())
+    prob = gpu_problem(G, s, 500.0)
+    F0 = G.incident_planewave(ctx, prob.pos, 500.0, s.e0)
+    for prec in ("fp64", "fp32"):
+        A = G.assemble(ctx, prob, prec)
+        F, _, _ = G.solve(ctx, prob, A, F0, prec)
+        np.testing.assert_allclose(F.cpu().numpy(), F0.cpu().numpy() * 3 / (4.0 + 1.0j + 2), rtol=1e-12)
+
+
+def test_invalid_arguments(G, ctx):
+    s = W.random_cells(10, seed=3)
+    prob = gpu_problem(G, s, 500.0)
+    with pytest.raises(G.GDMError):
+        G.assemble(ctx, prob, "fp32", lda=29)        # odd / too small leading dimension
+    bad = G.GDMProblem(prob.pos, -1.0, 3, eps=prob.eps, step=10.0)
+    with pytest.raises(G.GDMError):
+        G.assemble(ctx, bad, "fp32")
