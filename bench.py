@@ -1,0 +1,292 @@
+"""Benchmark of the GDM hot path on GB300.
+
+One step = assemble A = I - G alpha + LU factorisation + FP64-refined solve of both plane-wave
+illuminations for the 40 x 30 x 10 cell cuboid (N = 12,000, 3N = 36,000, lambda = 500 nm).
+The metric is seconds per (lambda, N) solve (lower is better).
+
+    python bench.py [--gpus N --steps K --warmup W --precision tf32|fp32|fp64 --impl ours|reference]
+
+Under torchrun each rank solves its own copy of the problem (independent units, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GDM assemble+solve s per (λ,N) vs FP64 GPU path at 1e-9 rel err; adjoint grad s"
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop/FMA x max clock
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r[0] for r in rows if r[2] > 300.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_oracle_sample(nx=18, ny=14, nz=10, target_n=12000):
+    """The CPU FP64 oracle as it stands on a bounded sample of the workload: the same cuboid
+    recipe at nx*ny*nz cells, assembly + dense solve, scaled to N = target_n by N^2 (assembly)
+    and N^3 (solve)."""
+    import numpy as np
+    import gdm_workloads as W
+    import oracle as O
+    s = W.cuboid_precision(nx, ny, nz)
+    pr = O.Problem(s.pos, float(s.wavelengths[0]), 3, eps=s.eps, step=s.step)
+    t0 = time.perf_counter()
+    A = pr.matrix()
+    F0 = pr.plane_wave(s.e0)
+    t1 = time.perf_counter()
+    np.linalg.solve(A, F0)
+    t2 = time.perf_counter()
+    ratio = target_n / s.n
+    est = (t1 - t0) * ratio ** 2 + (t2 - t1) * ratio ** 3
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": est, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle assemble+solve of the same cuboid recipe at {nx}x{ny}x{nz} cells (N={s.n}, "
+                      f"{t2 - t0:.2f} s measured: assembly {t1 - t0:.2f} s, solve {t2 - t1:.2f} s), "
+                      f"scaled to N={target_n} by N^2 (assembly) and N^3 (solve)"}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return
+    cpu_oracle_sample(8, 6, 5)  # warm numpy / BLAS
+    times = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        last = cpu_oracle_sample()
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(last["value"])
+    v = statistics.mean(times)
+    cb = dict(last)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_config(args):
+    return {"workload": "cuboid 40x30x10 cells, d=10 nm, N=12000 (3N=36000), eps~U[2,16]+iU[0,0.5] seed 2, "
+                        "lambda=500 nm, x- and y-polarised plane waves; assemble + LU + FP64-refined solve",
+            "precision": args.precision, "n_rhs": 2,
+            "l2": "inputs larger than L2 (10.4 GB complex64 matrix rewritten every step)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import gdm_workloads as W
+    import paper_2505_09545_gb300 as G
+
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cpu_base = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu_base = cpu_oracle_sample()  # before any GPU work of this process
+
+    s = W.cuboid_precision()
+    lam = float(s.wavelengths[0])
+    ctx = G.Context(local)
+    pos = torch.tensor(s.pos, device=dev)
+    eps = torch.tensor(s.eps, device=dev)
+    prob = G.GDMProblem(pos, lam, 3, eps=eps, step=s.step)
+    ns = prob.size
+    A = torch.empty((ns, G.padded_lda(ns)), dtype=torch.complex128 if args.precision == "fp64" else torch.complex64,
+                    device=dev)
+    ipiv = torch.empty(ns, dtype=torch.int32, device=dev)
+    F0 = G.incident_planewave(ctx, pos, lam, s.e0)
+    F = torch.empty_like(F0)
+
+    def step():
+        G.assemble(ctx, prob, args.precision, out=A)
+        return G.solve(ctx, prob, A, F0, args.precision, ipiv=ipiv, F=F)[2]
+
+    for _ in range(max(3, args.warmup)):
+        info = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clk = ClockSampler(local)
+    barrier()
+    clk.start()
+    ctx.profile(True)
+    l0 = ctx.launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    infos = []
+    for _ in range(args.steps):
+        infos.append(step())
+    e1.record()
+    barrier()
+    launches = ctx.launches - l0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public API: host inputs -> device, solve, fields back to the host
+    h_pos = torch.tensor(s.pos).pin_memory()
+    h_eps = torch.tensor(s.eps).pin_memory()
+    h_F = torch.empty(F.shape, dtype=F.dtype).pin_memory()
+    d_pos = torch.empty_like(pos)
+    d_eps = torch.empty_like(eps)
+
+    def e2e_step():
+        d_pos.copy_(h_pos, non_blocking=True)
+        d_eps.copy_(h_eps, non_blocking=True)
+        pr2 = G.GDMProblem(d_pos, lam, 3, eps=d_eps, step=s.step)
+        f0 = G.incident_planewave(ctx, d_pos, lam, s.e0)
+        G.assemble(ctx, pr2, args.precision, out=A)
+        G.solve(ctx, pr2, A, f0, args.precision, ipiv=ipiv, F=F)
+        h_F.copy_(F, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    k_e2e = max(1, min(3, args.steps))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    peaks, peak_src = load_peaks()
+    per_launch_ms = prof["ms"] / max(1, prof["launches"])
+    flops_per_launch = prof["flops"] / max(1, prof["launches"])
+    if args.precision == "fp64":
+        rl = {"bound": "alu", "peak": 1.05, "peak_src": "FP64 rate measured with torch float64 matmul on GB300"}
+    elif os.environ.get("GDM_TC_DISABLE") or prof.get("tc", True) is False:
+        rl = {"bound": "alu", "peak": FP32_SIMT_PEAK_TFLOPS, "peak_src": "FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+    else:
+        rl = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"] * NOMINAL_TF32_OVER_BF16,
+              "peak_src": f"{peak_src} sustained bf16 x nominal TF32/BF16 ratio 1.1/2.25"}
+    achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12 if per_launch_ms > 0 else 0.0
+    roofline = {"bound": rl["bound"], "achieved": achieved, "peak": rl["peak"], "unit": "TFLOP/s",
+                "frac": achieved / rl["peak"], "traffic": None, "kernel": "LU trailing update A22 -= A21 U12",
+                "launches_per_step": prof["launches"] / args.steps, "ms_per_step_in_kernel": prof["ms"] / args.steps,
+                "peak_source": rl["peak_src"]}
+    units = ws * 1
+    value = ms / 1e3 / units
+    it = infos[-1]
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64-tf32+f64" if args.precision == "tf32" else
+            ("c64-3xtf32+f64" if args.precision == "fp32" else "f64"),
+            "data": "synthetic", "config": workload_config(args),
+            "accuracy": {"refine_iters": it["iterations"], "rel_correction": it["rel_correction"],
+                         "rel_residual_fp64": it["rel_residual"], "factor_ms": it["factor_ms"],
+                         "refine_ms": it["refine_ms"]},
+            "roofline": roofline, "gpu_launches": launches,
+            "e2e": {"value": e2e_s / units, "unit": "s", "h2d_bytes_per_step": int(h_pos.numel() * 8 + h_eps.numel() * 16),
+                    "d2h_bytes_per_step": int(h_F.numel() * 16)},
+            "clocks": clocks, "cpu_baseline": cpu_base}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

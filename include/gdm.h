@@ -200,6 +200,17 @@ gdm_status gdm_nearfield_backward(gdm_ctx *ctx, const gdm_problem *p, const doub
                                   int64_t m, int n_rhs, const double *e0, const double *khat, const double *gE,
                                   double *gF_accum, double *grad_pos, double *grad_eps, double *grad_wavelength);
 
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Time every launch of the dominant kernel of the factorisation (the trailing update
+ * A22 -= A21 U12 of the LU) with CUDA events on the context stream. enable = 1 clears the
+ * record and starts recording; enable = 0 stops. Adds no synchronisation. */
+gdm_status gdm_profile_enable(gdm_ctx *ctx, int enable);
+/* Number of recorded launches, their summed device time (ms), summed algorithmic flops
+ * (8 M N K per complex M x N x K update) and algorithmic bytes (read A21, U12, C; write C).
+ * Synchronises the context stream. Any output pointer may be NULL. */
+gdm_status gdm_profile_read(gdm_ctx *ctx, int64_t *launches, double *total_ms, double *flops, double *bytes);
+
 #ifdef __cplusplus
 }
 #endif

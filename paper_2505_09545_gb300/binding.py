@@ -77,6 +77,8 @@ _SIGS = {
     "gdm_backward": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, C.c_int, PD, PD, P, PD, P, P, P,
                       C.POINTER(SolveInfo)], C.c_int),
     "gdm_nearfield_backward": ([P, C.POINTER(Problem), P, P, I64, C.c_int, PD, PD, P, P, P, P, P], C.c_int),
+    "gdm_profile_enable": ([P, C.c_int], C.c_int),
+    "gdm_profile_read": ([P, C.POINTER(I64), PD, PD, PD], C.c_int),
 }
 
 
@@ -149,6 +151,17 @@ class Context:
     @property
     def launches(self):
         return int(lib().gdm_launch_count(self.h))
+
+    def profile(self, enable=True):
+        """Start (or stop) CUDA-event timing of the LU trailing-update kernel launches."""
+        self._check(lib().gdm_profile_enable(self.h, 1 if enable else 0), "gdm_profile_enable")
+
+    def profile_read(self):
+        n = I64(0)
+        ms, fl, by = D(0), D(0), D(0)
+        self._check(lib().gdm_profile_read(self.h, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)),
+                    "gdm_profile_read")
+        return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
 
 
 class GDMProblem:

@@ -63,7 +63,57 @@ gdm_status gdm_upload(gdm_ctx *ctx, const void *host, size_t bytes, void **dev) 
     return GDM_OK;
 }
 
+gdm_status gdm_prof_begin(gdm_ctx *ctx, int *slot) {
+    *slot = -1;
+    if (!ctx->prof_on || ctx->prof_n >= GDM_PROF_MAX) return GDM_OK;
+    if (!ctx->prof_ev) {
+        ctx->prof_ev = new (std::nothrow) cudaEvent_t[2 * GDM_PROF_MAX];
+        if (!ctx->prof_ev) return gdm_fail(ctx, GDM_ERR_OOM, "profile events");
+        for (int i = 0; i < 2 * GDM_PROF_MAX; i++) GDM_CUDA_TRY(ctx, cudaEventCreate(&ctx->prof_ev[i]));
+    }
+    *slot = ctx->prof_n;
+    GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->prof_ev[2 * *slot], ctx->stream));
+    return GDM_OK;
+}
+
+gdm_status gdm_prof_end(gdm_ctx *ctx, int slot, double flops, double bytes) {
+    if (slot < 0) return GDM_OK;
+    GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->prof_ev[2 * slot + 1], ctx->stream));
+    ctx->prof_n = slot + 1;
+    ctx->prof_flops += flops;
+    ctx->prof_bytes += bytes;
+    return GDM_OK;
+}
+
 extern "C" {
+
+gdm_status gdm_profile_enable(gdm_ctx *ctx, int enable) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    ctx->prof_on = enable ? 1 : 0;
+    if (enable) {
+        ctx->prof_n = 0;
+        ctx->prof_flops = 0.0;
+        ctx->prof_bytes = 0.0;
+    }
+    return GDM_OK;
+}
+
+gdm_status gdm_profile_read(gdm_ctx *ctx, int64_t *launches, double *total_ms, double *flops, double *bytes) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    double ms = 0.0;
+    for (int i = 0; i < ctx->prof_n; i++) {
+        float t = 0.f;
+        GDM_CUDA_TRY(ctx, cudaEventElapsedTime(&t, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
+        ms += t;
+    }
+    if (launches) *launches = ctx->prof_n;
+    if (total_ms) *total_ms = ms;
+    if (flops) *flops = ctx->prof_flops;
+    if (bytes) *bytes = ctx->prof_bytes;
+    return GDM_OK;
+}
 
 const char *gdm_status_string(gdm_status s) {
     switch (s) {
@@ -124,6 +174,10 @@ gdm_status gdm_destroy(gdm_ctx *ctx) {
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
+    if (ctx->prof_ev) {
+        for (int i = 0; i < 2 * GDM_PROF_MAX; i++) cudaEventDestroy(ctx->prof_ev[i]);
+        delete[] ctx->prof_ev;
+    }
     delete ctx;
     return GDM_OK;
 }

@@ -29,7 +29,16 @@ struct gdm_ctx {
     // small parameter arrays copied from the host (stream-ordered); offset reset per API call
     char *dparams = nullptr;
     size_t param_off = 0;
+    // optional event timing of the dominant kernel (gdm_profile_enable)
+    int prof_on = 0;
+    int prof_n = 0;
+    cudaEvent_t *prof_ev = nullptr;  // 2 * GDM_PROF_MAX events, created lazily
+    double prof_flops = 0.0, prof_bytes = 0.0;
 };
+#define GDM_PROF_MAX 4096
+// bracket one launch of the profiled kernel (no-ops unless profiling is on)
+gdm_status gdm_prof_begin(gdm_ctx *ctx, int *slot);
+gdm_status gdm_prof_end(gdm_ctx *ctx, int slot, double flops, double bytes);
 #define GDM_PARAM_BYTES (1 << 16)
 
 // set the context error string, return the status

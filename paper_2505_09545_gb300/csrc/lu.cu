@@ -474,9 +474,15 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
             gdm_status s = GDM_ERR_UNSUPPORTED;
             if (sizeof(C) == 8 && tcws)
                 s = gdm_tc_trailing_update(ctx, prec, (float2 *)A, lda, n, b0, nb, tcws, tcbytes);
-            if (s == GDM_ERR_UNSUPPORTED)
+            if (s == GDM_ERR_UNSUPPORTED) {
+                int slot;
+                GDM_TRY(gdm_prof_begin(ctx, &slot));
                 s = gemm_sub<C>(ctx, A + be * lda + be, lda, A + b0 * lda + be, lda, A + be * lda + b0, lda, n - be,
                                 n - be, nb);
+                double mm = (double)(n - be);
+                GDM_TRY(gdm_prof_end(ctx, slot, 8.0 * mm * mm * nb,
+                                     sizeof(C) * (2.0 * mm * mm + 2.0 * mm * nb)));
+            }
             GDM_TRY(s);
         }
     }
