@@ -94,8 +94,15 @@ typedef struct {
     double tol;             /* stop when max_r ||dF_r|| / ||F_r|| <= tol (default 1e-12) */
 } gdm_solve_opts;
 
-#define GDM_SOLVE_FACTORED 1  /* A already holds this problem's factors and ipiv its pivots */
-#define GDM_SOLVE_NO_REFINE 2 /* return the plain triangular-solve result */
+#define GDM_SOLVE_FACTORED 1      /* A already holds this problem's factors and ipiv its pivots */
+#define GDM_SOLVE_NO_REFINE 2     /* return the plain triangular-solve result */
+#define GDM_SOLVE_GLOBAL_PIVOT 4  /* always search pivots over the whole column (partial pivoting) */
+/* Pivoting: by default each 32-column panel searches its pivots among the rows of its 32 x 32
+ * diagonal block and certifies the choice against all rows below. If some row below exceeds its
+ * pivot by more than GDM_PIVOT_GROWTH_LIMIT, gdm_solve re-assembles A from the problem and factors
+ * again with partial pivoting over whole columns; a certificate <= 1 means the factors are exactly
+ * those of partial pivoting. */
+#define GDM_PIVOT_GROWTH_LIMIT 4.0
 
 typedef struct {
     int32_t iterations;          /* refinement steps taken */
@@ -104,6 +111,9 @@ typedef struct {
     double rel_residual;         /* last max_r ||F0_r - A F_r|| / ||F0_r|| (FP64, matrix-free) */
     double factor_ms;            /* device time of the factorisation (0 if skipped) */
     double refine_ms;            /* device time of solves + refinement */
+    double pivot_growth;         /* largest |entry below| / |pivot| seen by the panels (<= 1: partial pivoting) */
+    int32_t refactored;          /* 1 if the factorisation was redone with whole-column pivoting */
+    int32_t reserved;
 } gdm_solve_info;
 
 /* ---------------------------------------------------------------- context */

@@ -27,6 +27,7 @@ STATUS = {0: "GDM_OK", 1: "GDM_ERR_INVALID_ARG", 2: "GDM_ERR_SHAPE", 3: "GDM_ERR
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2}
 SOLVE_FACTORED = 1
 SOLVE_NO_REFINE = 2
+SOLVE_GLOBAL_PIVOT = 4
 
 
 class GDMError(RuntimeError):
@@ -47,7 +48,8 @@ class SolveOpts(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("rel_correction", C.c_double),
-                ("rel_residual", C.c_double), ("factor_ms", C.c_double), ("refine_ms", C.c_double)]
+                ("rel_residual", C.c_double), ("factor_ms", C.c_double), ("refine_ms", C.c_double),
+                ("pivot_growth", C.c_double), ("refactored", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -224,7 +226,7 @@ def assemble(ctx: Context, prob: GDMProblem, precision="fp32", lda=None, out=Non
 
 
 def solve(ctx: Context, prob: GDMProblem, A, F0, precision="fp32", ipiv=None, factored=False, max_iter=0, tol=0.0,
-          no_refine=False, info=True, F=None):
+          no_refine=False, info=True, F=None, global_pivot=False):
     """Factor A in place (unless factored) and solve A F = F0 with FP64 refinement.
     F0: (n_rhs, n_sys) complex128. Returns (F, ipiv, info dict or None)."""
     ns = prob.size
@@ -234,7 +236,8 @@ def solve(ctx: Context, prob: GDMProblem, A, F0, precision="fp32", ipiv=None, fa
     if F is None:
         F = torch.empty_like(F0)
     n_rhs = F0.shape[0]
-    flags = (SOLVE_FACTORED if factored else 0) | (SOLVE_NO_REFINE if no_refine else 0)
+    flags = ((SOLVE_FACTORED if factored else 0) | (SOLVE_NO_REFINE if no_refine else 0)
+             | (SOLVE_GLOBAL_PIVOT if global_pivot else 0))
     opts = SolveOpts(int(max_iter), flags, float(tol))
     inf = SolveInfo() if info else None
     s = prob.struct()

@@ -294,9 +294,18 @@ gdm_status gdm_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, voi
     if (!(o.tol > 0)) o.tol = 1e-12;
     if (info) memset(info, 0, sizeof(*info));
     float fms = 0.f;
+    float growth = 1.f;
+    int refactored = 0;
     if (!(o.flags & GDM_SOLVE_FACTORED)) {
         if (info) GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
-        GDM_TRY(gdm_lu_factor(ctx, prec, A, ns, lda, ipiv));
+        int global = (o.flags & GDM_SOLVE_GLOBAL_PIVOT) ? 1 : 0;
+        GDM_TRY(gdm_lu_factor(ctx, prec, A, ns, lda, ipiv, global, &growth));
+        if (!global && !(growth <= (float)GDM_PIVOT_GROWTH_LIMIT)) {
+            // the in-block pivots are not safe for this matrix: rebuild A and pivot over whole columns
+            GDM_TRY(gdm_launch_assemble(ctx, p, prec, A, lda));
+            GDM_TRY(gdm_lu_factor(ctx, prec, A, ns, lda, ipiv, 1, &growth));
+            refactored = 1;
+        }
         if (info) {
             GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
             GDM_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev1));
@@ -304,7 +313,11 @@ gdm_status gdm_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, voi
         }
     }
     gdm_status s = gdm_refined_solve(ctx, p, prec, A, lda, ipiv, F0, F, n_rhs, 0, &o, info);
-    if (info) info->factor_ms = fms;
+    if (info) {
+        info->factor_ms = fms;
+        info->pivot_growth = growth;
+        info->refactored = refactored;
+    }
     return s;
 }
 

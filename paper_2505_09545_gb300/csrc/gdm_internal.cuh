@@ -90,6 +90,7 @@ struct ScratchCarver {
 #define GDM_FLAG_DETAIL 1
 #define GDM_FLAG_BAR_COUNT 2
 #define GDM_FLAG_BAR_GEN 3
+#define GDM_FLAG_GROWTH 4
 #define GDM_NFLAGS 8
 
 __device__ __forceinline__ void gdm_dev_error(int *flags, int status, int detail) {
@@ -169,7 +170,11 @@ gdm_status gdm_launch_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double
 gdm_status gdm_launch_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F, int n_rhs,
                                      const double *e0_norm2, double *ext, double *sca, double *abs);
 // linear algebra (lu.cu)
-gdm_status gdm_lu_factor(gdm_ctx *ctx, gdm_precision prec, void *A, int64_t n, int64_t lda, int32_t *ipiv);
+// Factor A in place. global_pivot = 0: pivots searched inside each 32 x 32 diagonal block, with the
+// largest |row below| / |pivot| ratio returned in *growth_out (<= 1: identical to partial pivoting);
+// global_pivot = 1: partial pivoting over the whole column (cooperative panel kernel).
+gdm_status gdm_lu_factor(gdm_ctx *ctx, gdm_precision prec, void *A, int64_t n, int64_t lda, int32_t *ipiv,
+                         int global_pivot, float *growth_out);
 // solve op(A) X = B in place on B (complex of the factor precision, n x n_rhs, ldb);
 // conj_trans = 0: A X = B using P, L, U; conj_trans = 1: A^H X = B.
 gdm_status gdm_lu_solve(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda, const int32_t *ipiv,

@@ -224,6 +224,116 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(C *__restrict__ A, int6
         for (int lr = threadIdx.x; lr < nr; lr += PANEL_THREADS) A[(c0 + c) * lda + r0 + lr] = tile[c * rpc + lr];
 }
 
+// ------------------------------------------------------------------ panel with pivoting inside the diagonal block
+// Factor rows [c0, n) x cols [c0, c0+w): every CTA factors the w x w diagonal block D with partial pivoting
+// among D's own rows (so the rows below never move), then solves its share of the rows below:
+// L21 = A21 U11^{-1}. No grid-wide synchronisation. Certificate: for every row below and column k the
+// updated entry (before division by the pivot) is compared with the pivot in |re|+|im|; the largest ratio
+// is recorded in growth[0] (as float bits). A ratio <= 1 means the pivots are exactly those of partial
+// pivoting over the whole column (rows of D win ties, as they have the lower index).
+template <class C>
+__global__ void __launch_bounds__(256) k_panel_local(C *__restrict__ A, int64_t lda, int64_t n, int64_t c0, int w,
+                                                     int32_t *__restrict__ ipiv, unsigned *growth, int *flags) {
+    typedef decltype(C().x) T;
+    __shared__ C D[NBP][NBP + 1];
+    __shared__ int s_piv;
+    for (int e = threadIdx.x; e < NBP * NBP; e += blockDim.x) {
+        int r = e % NBP, c = e / NBP;
+        C v;
+        v.x = 0;
+        v.y = 0;
+        if (r < w && c < w) v = A[(c0 + c) * lda + c0 + r];
+        D[r][c] = v;
+    }
+    __syncthreads();
+    for (int t = 0; t < w; t++) {
+        if (threadIdx.x < 32) {
+            int r = threadIdx.x;
+            double v = (r >= t && r < w) ? (double)cabs1(D[r][t]) : -1.0;
+            int rr = r;
+            for (int o = 16; o > 0; o >>= 1) {
+                double ov = __shfl_down_sync(0xffffffffu, v, o);
+                int orr = __shfl_down_sync(0xffffffffu, rr, o);
+                if (ov > v || (ov == v && orr < rr)) {
+                    v = ov;
+                    rr = orr;
+                }
+            }
+            if (threadIdx.x == 0) {
+                s_piv = rr;
+                if (blockIdx.x == 0) {
+                    ipiv[c0 + t] = (int32_t)(c0 + rr);
+                    if (!(v > 0.0)) gdm_dev_error(flags, GDM_ERR_SINGULAR, (int)(c0 + t));
+                }
+            }
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != t && threadIdx.x < w) {
+            C a = D[t][threadIdx.x];
+            D[t][threadIdx.x] = D[p][threadIdx.x];
+            D[p][threadIdx.x] = a;
+        }
+        __syncthreads();
+        C pv = D[t][t];
+        C inv;
+        if (cabs1(pv) > 0) inv = crecip(pv);
+        else {
+            inv.x = 0;
+            inv.y = 0;
+        }
+        // rows t+1..w-1: multiplier, then rank-1 update of columns t+1..w-1
+        const int nr = w - t - 1;
+        for (int e = threadIdx.x; e < nr * (nr + 1); e += blockDim.x) {
+            int r = t + 1 + e / (nr + 1), c = t + e % (nr + 1);  // c == t: multiplier column
+            if (c == t) continue;
+            C l = cmul(D[r][t], inv);
+            cfms(D[r][c], l, D[t][c]);
+        }
+        __syncthreads();
+        for (int r = t + 1 + threadIdx.x; r < w; r += blockDim.x) D[r][t] = cmul(D[r][t], inv);
+        __syncthreads();
+    }
+    if (blockIdx.x == 0)
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+            int r = e % w, c = e / w;
+            A[(c0 + c) * lda + c0 + r] = D[r][c];
+        }
+    // rows below the diagonal block: x <- x U^{-1}, one thread per row
+    float worst = 0.f;
+    for (int64_t r = c0 + w + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        C x[NBP];
+#pragma unroll
+        for (int k = 0; k < NBP; k++)
+            if (k < w) x[k] = A[(c0 + k) * lda + r];
+#pragma unroll
+        for (int k = 0; k < NBP; k++) {
+            if (k < w) {
+                C num = x[k];
+#pragma unroll
+                for (int j = 0; j < NBP; j++)
+                    if (j < k) cfms(num, x[j], D[j][k]);
+                T pa = cabs1(D[k][k]);
+                T na = cabs1(num);
+                if (pa > 0) {
+                    float ratio = (float)(na / pa);
+                    worst = fmaxf(worst, ratio);
+                    x[k] = cmul(num, crecip(D[k][k]));
+                } else {
+                    x[k].x = 0;
+                    x[k].y = 0;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NBP; k++)
+            if (k < w) A[(c0 + k) * lda + r] = x[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_down_sync(0xffffffffu, worst, o));
+    if ((threadIdx.x & 31) == 0 && worst > 0.f) atomicMax(growth, __float_as_uint(worst));
+}
+
 // ------------------------------------------------------------------ row interchanges
 // Apply pivots ipiv[k_begin..k_end) in order to columns [cb, ce) (one thread per column).
 template <class C>
@@ -429,7 +539,20 @@ static gdm_status trsm_small(gdm_ctx *ctx, C *A, int64_t lda, int64_t c0, int w,
 int gdm_lu_block(gdm_precision prec) { return prec == GDM_FP64 ? 128 : 256; }
 
 template <class C>
-static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n, int64_t lda, int32_t *ipiv) {
+static gdm_status panel_local(gdm_ctx *ctx, C *A, int64_t lda, int64_t n, int64_t c0, int w, int32_t *ipiv,
+                              unsigned *growth) {
+    int64_t below = n - c0 - w;
+    int blocks = (int)((below + 255) / 256);
+    if (blocks < 1) blocks = 1;
+    if (blocks > 4 * ctx->sm_count) blocks = 4 * ctx->sm_count;
+    k_panel_local<C><<<blocks, 256, 0, ctx->stream>>>(A, lda, n, c0, w, ipiv, growth, ctx->dflags);
+    GDM_LAUNCHED(ctx, "panel_local");
+    return GDM_OK;
+}
+
+template <class C>
+static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n, int64_t lda, int32_t *ipiv,
+                              int global_pivot, unsigned *growth) {
     const int NB = gdm_lu_block(prec);
     int pmax = ctx->sm_count;
     // scratch: panel candidates + tensor-core operand buffers
@@ -451,7 +574,8 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
         int64_t be = b0 + nb;
         for (int64_t c0 = b0; c0 < be; c0 += NBP) {
             int w = (int)(be - c0 < NBP ? be - c0 : NBP);
-            GDM_TRY(panel_factor<C>(ctx, A, lda, n, c0, w, ipiv, ps, pmax));
+            if (global_pivot) GDM_TRY(panel_factor<C>(ctx, A, lda, n, c0, w, ipiv, ps, pmax));
+            else GDM_TRY(panel_local<C>(ctx, A, lda, n, c0, w, ipiv, growth));
             GDM_TRY(laswp<C>(ctx, A, lda, b0, c0, ipiv, c0, c0 + w));
             GDM_TRY(laswp<C>(ctx, A, lda, c0 + w, be, ipiv, c0, c0 + w));
             if (c0 + w < be) {
@@ -489,9 +613,24 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
     return GDM_OK;
 }
 
-gdm_status gdm_lu_factor(gdm_ctx *ctx, gdm_precision prec, void *A, int64_t n, int64_t lda, int32_t *ipiv) {
-    if (prec == GDM_FP64) return lu_factor_t<double2>(ctx, prec, (double2 *)A, n, lda, ipiv);
-    return lu_factor_t<float2>(ctx, prec, (float2 *)A, n, lda, ipiv);
+gdm_status gdm_lu_factor(gdm_ctx *ctx, gdm_precision prec, void *A, int64_t n, int64_t lda, int32_t *ipiv,
+                         int global_pivot, float *growth_out) {
+    // the growth record lives in the flags allocation (slot GDM_FLAG_GROWTH)
+    unsigned *growth = (unsigned *)(ctx->dflags + GDM_FLAG_GROWTH);
+    GDM_CUDA_TRY(ctx, cudaMemsetAsync(growth, 0, sizeof(unsigned), ctx->stream));
+    gdm_status s = (prec == GDM_FP64) ? lu_factor_t<double2>(ctx, prec, (double2 *)A, n, lda, ipiv, global_pivot, growth)
+                                      : lu_factor_t<float2>(ctx, prec, (float2 *)A, n, lda, ipiv, global_pivot, growth);
+    if (s != GDM_OK) return s;
+    if (growth_out) {
+        unsigned *h;
+        GDM_TRY(gdm_pinned(ctx, 64, (void **)&h));
+        GDM_CUDA_TRY(ctx, cudaMemcpyAsync(h, growth, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+        GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        float g;
+        memcpy(&g, h, sizeof(float));
+        *growth_out = global_pivot ? 1.0f : g;
+    }
+    return GDM_OK;
 }
 
 // ------------------------------------------------------------------ triangular solves on right-hand sides

@@ -1,9 +1,503 @@
-// tcgen05 tensor-core trailing update for the FP32 LU (filled in below).
+// Tensor-core trailing update of the FP32 LU on GB300: A22 -= A21 U12 with tcgen05 (TF32 inputs,
+// FP32 accumulation in tensor memory), operands staged by TMA.
+//
+// Complex -> real embedding. With L = A21 (m x nb complex) and U = U12 (nb x m complex), column-major
+// interleaved storage makes the trailing block a real (2m) x m matrix C (row 2i+c = component c of
+// complex row i). Then
+//     C -= Lx * Ur,   Lx = (2m) x (2nb) real, rows 2i: [Lr, -Li, ...], rows 2i+1: [Li, Lr, ...],
+//                     Ur = (2nb) x m real = U12 seen as reals (column j = [Ur0, Ui0, Ur1, Ui1, ...]),
+// a single real GEMM with M' = 2m, N = m, K' = 2nb and exactly the complex flop count 8 m^2 nb.
+// Both operands are K-major: Lx is written K-major by a small preparation kernel, Ur is read directly
+// from the matrix (each column of U12 is contiguous in K'). C is updated in place by the epilogue.
+//
+// Precision modes:  TF32_REFINE: one product per step (TF32 inputs).
+//                   FP32:        three products hi*hi + hi*lo + lo*hi of TF32 hi/lo splits (x = hi + lo,
+//                                hi = x rounded to TF32), which carries ~21 significant bits.
+//
+// Kernel structure (persistent, one CTA per SM, 192 threads):
+//   warp 0: TMA producer (one elected lane) -> smem ring of STAGES stages (mbarrier full/empty),
+//   warp 1: TMEM allocation + MMA issuer (one lane): 128 x BN accumulator per tile, two accumulators
+//           (double buffered) so the epilogue of tile t overlaps the main loop of tile t+1,
+//   warps 2-5: epilogue: tcgen05.ld of the accumulator (each warp its 32-lane quarter), C -= acc with
+//           coalesced column accesses (32 consecutive rows per warp per column).
+// Every wait is bounded (~2 s): on timeout the kernel records GDM_ERR_TIMEOUT, drains what it issued,
+// frees its tensor memory and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <stdlib.h>
+
 #include "gdm_internal.cuh"
 
-size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec) { return 0; }
+namespace {
 
+constexpr int BM = 128;          // rows of the real embedding per tile (UMMA M)
+constexpr int BK = 32;           // K' floats per stage = 128 bytes = one 128B swizzle row
+constexpr int NTHREADS = 192;
+
+template <int BN, int SPLIT> struct Cfg {
+    static constexpr int NP = (SPLIT == 3) ? 2 : 1;  // operand planes per stage (hi[, lo])
+    static constexpr int A_BYTES = BM * BK * 4;
+    static constexpr int B_BYTES = BN * BK * 4;
+    static constexpr int STAGE_BYTES = NP * (A_BYTES + B_BYTES);
+    static constexpr int STAGES = (SPLIT == 3) ? 3 : 4;
+    static constexpr int TMEM_COLS = 2 * BN;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 512 /*barriers*/;
+    // instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = BN
+    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(BM >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of the given parity. Returns false if the CTA is aborting or after
+// ~2 s (then records GDM_ERR_TIMEOUT and raises the CTA's abort flag).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *gflags) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = gtimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > 2000000000ull) {
+                gdm_dev_error(gflags, GDM_ERR_TIMEOUT, 2);
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core groups 1024 B apart
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;               // descriptor version
+    d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+    return d;
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+            dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+struct TileMap {
+    int num_m, num_n, group;
+    __device__ __forceinline__ void get(int t, int &m, int &n) const {
+        // groups of `group` column tiles; inside a group the row tile varies slowest across the
+        // group's columns so that concurrently running CTAs share operand tiles in L2
+        int per_group = num_m * group;
+        int g = t / per_group;
+        int idx = t - g * per_group;
+        int gn = min(group, num_n - g * group);
+        n = g * group + idx % gn;
+        m = idx / gn;
+    }
+};
+
+template <int BN, int SPLIT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc_update(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+                const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
+                float *__restrict__ Cm, int64_t ldc, int M, int N, int K, int bx0, int by0, int *gflags) {
+    using CF = Cfg<BN, SPLIT>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(base + CF::STAGES * CF::STAGE_BYTES);
+    uint64_t *full = bars;                       // [STAGES]
+    uint64_t *empty = bars + CF::STAGES;         // [STAGES]
+    uint64_t *tfull = bars + 2 * CF::STAGES;     // [2]
+    uint64_t *tempty = tfull + 2;                // [2]
+    uint64_t *drain = tempty + 2;                // [1]
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (K + BK - 1) / BK;
+    TileMap tm{(M + BM - 1) / BM, (N + BN - 1) / BN, 8};
+    const int ntiles = tm.num_m * tm.num_n;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CF::STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)CF::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int issued = 0;  // stages issued and not yet known complete (for the drain on abort)
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                int mt, nt;
+                tm.get(t, mt, nt);
+                for (int kc = 0; kc < nk; kc++) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, gflags)) break;
+                    unsigned char *st = base + s * CF::STAGE_BYTES;
+                    mbar_expect_tx(&full[s], CF::STAGE_BYTES);
+                    tma_load_2d(st, &tmA0, kc * BK, mt * BM, &full[s]);
+                    tma_load_2d(st + CF::A_BYTES, &tmB0, bx0 + kc * BK, by0 + nt * BN, &full[s]);
+                    if (SPLIT == 3) {
+                        tma_load_2d(st + CF::A_BYTES + CF::B_BYTES, &tmA1, kc * BK, mt * BM, &full[s]);
+                        tma_load_2d(st + 2 * CF::A_BYTES + CF::B_BYTES, &tmB1, bx0 + kc * BK, by0 + nt * BN, &full[s]);
+                    }
+                    issued++;
+                    if (++s == CF::STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            if (*abort_flag) {
+                // let the copies already issued land before the CTA's shared memory goes away
+                int s2 = s, ph2 = ph;
+                for (int i = 0; i < CF::STAGES && i < issued; i++) {
+                    if (--s2 < 0) {
+                        s2 = CF::STAGES - 1;
+                        ph2 ^= 1;
+                    }
+                    uint64_t t0 = gtimer();
+                    while (!mbar_try_wait(&full[s2], ph2) && gtimer() - t0 < 2000000000ull) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int lt = 0;
+            bool issued_any = false;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, lt++) {
+                const int b = lt & 1;
+                const uint32_t tph = (lt >> 1) & 1;
+                if (!mbar_wait(&tempty[b], tph ^ 1, abort_flag, gflags)) break;
+                tc_fence_after();
+                const uint32_t dt = tmem_base + (uint32_t)(b * BN);
+                bool ok = true;
+                for (int kc = 0; kc < nk; kc++) {
+                    if (!mbar_wait(&full[s], ph, abort_flag, gflags)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(base + s * CF::STAGE_BYTES);
+                    const uint64_t a0 = desc_sw128(sa);
+                    const uint64_t b0 = desc_sw128(sa + CF::A_BYTES);
+#pragma unroll
+                    for (int k = 0; k < BK / 8; k++) {
+                        // advance 8 TF32 = 32 bytes along K inside the swizzled row: +2 in the 16-B address field
+                        const uint64_t ko = (uint64_t)(2 * k);
+                        umma_tf32(dt, a0 + ko, b0 + ko, CF::IDESC, (kc | k) ? 1u : 0u);
+                        if (SPLIT == 3) {
+                            const uint64_t a1 = desc_sw128(sa + CF::A_BYTES + CF::B_BYTES);
+                            const uint64_t b1 = desc_sw128(sa + 2 * CF::A_BYTES + CF::B_BYTES);
+                            umma_tf32(dt, a0 + ko, b1 + ko, CF::IDESC, 1u);
+                            umma_tf32(dt, a1 + ko, b0 + ko, CF::IDESC, 1u);
+                        }
+                    }
+                    issued_any = true;
+                    umma_commit(&empty[s]);
+                    if (++s == CF::STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(&tfull[b]);
+            }
+            if (issued_any) {
+                // all MMAs of this CTA complete before tensor memory is released
+                umma_commit(drain);
+                uint64_t t0 = gtimer();
+                while (!mbar_try_wait(drain, 0) && gtimer() - t0 < 2000000000ull) {
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5 cover the four 32-lane quarters of tensor memory
+        const int q = warp & 3;
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, lt++) {
+            const int b = lt & 1;
+            const uint32_t tph = (lt >> 1) & 1;
+            if (!mbar_wait(&tfull[b], tph, abort_flag, gflags)) break;
+            tc_fence_after();
+            int mt, nt;
+            tm.get(t, mt, nt);
+            const int row = mt * BM + q * 32 + lane;
+            const bool rok = row < M;
+            float *cp = Cm + row;
+            const int col_base = nt * BN;
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ch++) {
+                float v[32];
+                tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + ch * 32), v);
+                const int c0 = col_base + ch * 32;
+                if (rok) {
+                    float old[32];
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        if (c0 + j < N) old[j] = cp[(int64_t)(c0 + j) * ldc];
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        if (c0 + j < N) cp[(int64_t)(c0 + j) * ldc] = old[j] - v[j];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"((uint32_t)CF::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- operand preparation
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Lx[(2i+c) * K' + 2k + c'] from L = A21 (complex column-major at L, ld lda), rows i < m, cols k < nb.
+// SPLIT = 3 writes the TF32 hi part to Lx and the remainder to Llo.
+template <int SPLIT>
+__global__ void k_prep_lx(const float2 *__restrict__ L, int64_t lda, int m, int nb, float *__restrict__ Lx,
+                          float *__restrict__ Llo) {
+    __shared__ float2 tile[32][33];
+    const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    for (int kk = ty; kk < 32; kk += 8) {
+        int i = i0 + tx, k = k0 + kk;
+        float2 v = make_float2(0.f, 0.f);
+        if (i < m && k < nb) v = L[(int64_t)k * lda + i];
+        tile[kk][tx] = v;
+    }
+    __syncthreads();
+    const int K2 = 2 * nb;
+    for (int ii = ty; ii < 32; ii += 8) {
+        int i = i0 + ii, k = k0 + tx;
+        if (i >= m || k >= nb) continue;
+        float2 l = tile[tx][ii];
+        float2 r0 = make_float2(l.x, -l.y), r1 = make_float2(l.y, l.x);
+        float2 *o0 = (float2 *)(Lx + (int64_t)(2 * i) * K2 + 2 * k);
+        float2 *o1 = (float2 *)(Lx + (int64_t)(2 * i + 1) * K2 + 2 * k);
+        if (SPLIT == 3) {
+            float2 h0 = make_float2(tf32_round(r0.x), tf32_round(r0.y));
+            float2 h1 = make_float2(tf32_round(r1.x), tf32_round(r1.y));
+            *o0 = h0;
+            *o1 = h1;
+            *(float2 *)(Llo + (int64_t)(2 * i) * K2 + 2 * k) = make_float2(r0.x - h0.x, r0.y - h0.y);
+            *(float2 *)(Llo + (int64_t)(2 * i + 1) * K2 + 2 * k) = make_float2(r1.x - h1.x, r1.y - h1.y);
+        } else {
+            *o0 = r0;
+            *o1 = r1;
+        }
+    }
+}
+
+// U12 (complex nb x m at U, ld lda) -> K-major real planes Uhi/Ulo [j][2nb]
+__global__ void k_split_u(const float2 *__restrict__ U, int64_t lda, int nb, int m, float *__restrict__ Uhi,
+                          float *__restrict__ Ulo) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nb * m) return;
+    int j = (int)(e / nb), k = (int)(e % nb);
+    float2 v = U[(int64_t)j * lda + k];
+    float2 h = make_float2(tf32_round(v.x), tf32_round(v.y));
+    *(float2 *)(Uhi + (int64_t)j * 2 * nb + 2 * k) = h;
+    *(float2 *)(Ulo + (int64_t)j * 2 * nb + 2 * k) = make_float2(v.x - h.x, v.y - h.y);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2D FP32 tensor map: inner extent `inner` (contiguous), `outer` rows with row pitch `pitch_floats`,
+// box 32 x box_rows, 128-byte swizzle, zero fill out of bounds.
+bool make_map(CUtensorMap *map, const float *gptr, uint64_t inner, uint64_t outer, uint64_t pitch_floats,
+              uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {pitch_floats * 4};
+    cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)gptr, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int BN, int SPLIT>
+gdm_status launch_update(gdm_ctx *ctx, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
+                         const CUtensorMap &b1, float *C, int64_t ldc, int M, int N, int K, int bx0, int by0) {
+    using CF = Cfg<BN, SPLIT>;
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_update<BN, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               CF::SMEM));
+        attr = true;
+    }
+    int ntiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    int grid = ntiles < ctx->sm_count ? ntiles : ctx->sm_count;
+    k_tc_update<BN, SPLIT><<<grid, NTHREADS, CF::SMEM, ctx->stream>>>(a0, a1, b0, b1, C, ldc, M, N, K, bx0, by0,
+                                                                       ctx->dflags);
+    GDM_LAUNCHED(ctx, "tc_update");
+    return GDM_OK;
+}
+
+}  // namespace
+
+size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec) {
+    if (prec == GDM_FP64) return 0;
+    size_t lx = (size_t)2 * n * 2 * nb * sizeof(float);  // Lx: (2m) x (2nb)
+    size_t u = (size_t)n * 2 * nb * sizeof(float);       // one U plane: m x (2nb)
+    return prec == GDM_FP32 ? 2 * lx + 2 * u + 4096 : lx + 4096;
+}
+
+// A22 -= A21 U12 for the block [b0, b0+nb) of the complex64 matrix A (n x n, lda).
 gdm_status gdm_tc_trailing_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t b0,
                                   int64_t nb, void *ws, size_t ws_bytes) {
-    return GDM_ERR_UNSUPPORTED;
+    if (prec == GDM_FP64) return GDM_ERR_UNSUPPORTED;
+    const int64_t be = b0 + nb;
+    const int64_t m = n - be;
+    if (m < 64 || getenv("GDM_TC_DISABLE")) return GDM_ERR_UNSUPPORTED;
+    if (((uintptr_t)A & 15) || (lda & 1)) return GDM_ERR_UNSUPPORTED;
+    const int split = (prec == GDM_FP32) ? 3 : 1;
+    const int M = (int)(2 * m), N = (int)m, K = (int)(2 * nb);
+    ScratchCarver sc(ws);
+    float *Lx = sc.take<float>((size_t)M * K);
+    float *Llo = split == 3 ? sc.take<float>((size_t)M * K) : nullptr;
+    float *Uhi = split == 3 ? sc.take<float>((size_t)N * K) : nullptr;
+    float *Ulo = split == 3 ? sc.take<float>((size_t)N * K) : nullptr;
+    if (sc.off > ws_bytes) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "tensor-core workspace too small");
+    const float2 *L = A + b0 * lda + be;
+    dim3 pg((unsigned)((m + 31) / 32), (unsigned)((nb + 31) / 32));
+    if (split == 3) {
+        k_prep_lx<3><<<pg, 256, 0, ctx->stream>>>(L, lda, (int)m, (int)nb, Lx, Llo);
+        GDM_LAUNCHED(ctx, "prep_lx");
+        int64_t cnt = nb * m;
+        k_split_u<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(A + be * lda + b0, lda, (int)nb, (int)m, Uhi,
+                                                                          Ulo);
+        GDM_LAUNCHED(ctx, "split_u");
+    } else {
+        k_prep_lx<1><<<pg, 256, 0, ctx->stream>>>(L, lda, (int)m, (int)nb, Lx, nullptr);
+        GDM_LAUNCHED(ctx, "prep_lx");
+    }
+    CUtensorMap ta0, ta1, tb0, tb1;
+    float *C = (float *)(A + be * lda + be);
+    const int64_t ldc = 2 * lda;
+    bool ok = make_map(&ta0, Lx, K, M, K, BM);
+    int slot;
+    double fl = 8.0 * (double)m * (double)m * (double)nb;
+    double by = 16.0 * (double)m * m + 4.0 * ((double)M * K + (double)N * K) * (split == 3 ? 2 : 1);
+    if (split == 3) {
+        ok = ok && make_map(&ta1, Llo, K, M, K, BM) && make_map(&tb0, Uhi, K, N, K, 128) &&
+             make_map(&tb1, Ulo, K, N, K, 128);
+        if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        GDM_TRY(gdm_prof_begin(ctx, &slot));
+        GDM_TRY(launch_update<128, 3>(ctx, ta0, ta1, tb0, tb1, C, ldc, M, N, K, 0, 0));
+    } else {
+        // U12 straight from the matrix: real rows [2 b0, 2 b0 + K) of columns [be, n)
+        ok = ok && make_map(&tb0, (const float *)A, (uint64_t)2 * lda, (uint64_t)n, (uint64_t)2 * lda, 256);
+        if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        GDM_TRY(gdm_prof_begin(ctx, &slot));
+        GDM_TRY(launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, C, ldc, M, N, K, (int)(2 * b0), (int)be));
+    }
+    GDM_TRY(gdm_prof_end(ctx, slot, fl, by));
+    return GDM_OK;
 }

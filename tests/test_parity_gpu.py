@@ -198,3 +198,50 @@ def test_invalid_arguments(G, ctx):
     bad = G.GDMProblem(prob.pos, -1.0, 3, eps=prob.eps, step=10.0)
     with pytest.raises(G.GDMError):
         G.assemble(ctx, bad, "fp32")
+
+
+@pytest.mark.parametrize("prec,tol_plain,max_iters", [("tf32", 5e-2, 16), ("fp32", 1e-4, 5), ("fp64", 1e-11, 2)])
+def test_lu_factor_quality(G, ctx, prec, tol_plain, max_iters):
+    """The factors themselves (no refinement) solve the system to the precision's level, so a wrong
+    trailing update cannot hide behind the FP64 refinement. 3N = 2100: eight outer blocks, the
+    tensor-core update runs with trailing sizes 1844 ... 52 (ragged tiles)."""
+    s = W.random_cells(700, seed=12)
+    lam = float(s.wavelengths[0])
+    prob = gpu_problem(G, s, lam)
+    F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0)
+    A = G.assemble(ctx, prob, prec)
+    F1, ipiv, _ = G.solve(ctx, prob, A, F0, prec, no_refine=True)
+    pr = oracle_problem(s, lam)
+    Fo = pr.solve(pr.plane_wave(s.e0))
+    e1 = np.linalg.norm(F1.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+    assert np.all(e1 < tol_plain), e1
+    F2, _, info = G.solve(ctx, prob, A, F0, prec, ipiv=ipiv, factored=True)
+    e2 = np.linalg.norm(F2.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+    assert np.all(e2 < 1e-9) and info["iterations"] <= max_iters, (e1, e2, info)
+
+
+@pytest.mark.parametrize("eps,expect_refactor", [(12.25 + 0.0j, False), (-8.0 + 0.5j, False), (-2.2 + 0.3j, True)])
+def test_pivoting_certificate_and_fallback(G, ctx, eps, expect_refactor):
+    """Pivots are searched inside each 32 x 32 diagonal block and certified against the rows below.
+    Dielectric cells: certificate <= 1 (identical to partial pivoting). Metallic cells near the plasmon
+    resonance: the certificate exceeds the limit and the solve refactors with whole-column pivoting.
+    Either way the refined fields match the oracle."""
+    s = W.random_cells(120, seed=3)
+    s.eps = np.full(s.n, eps, complex)
+    lam = 500.0
+    prob = gpu_problem(G, s, lam)
+    F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0)
+    pr = oracle_problem(s, lam)
+    Fo = pr.solve(pr.plane_wave(s.e0))
+    for prec in ("fp32", "fp64"):
+        A = G.assemble(ctx, prob, prec)
+        F, _, info = G.solve(ctx, prob, A, F0, prec)
+        err = np.linalg.norm(F.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+        assert np.all(err < 1e-9), (err, info)
+        assert bool(info["refactored"]) == expect_refactor, info
+        if eps.real > 0:
+            assert info["pivot_growth"] <= 1.0
+        A = G.assemble(ctx, prob, prec)
+        F, _, info = G.solve(ctx, prob, A, F0, prec, global_pivot=True)
+        err = np.linalg.norm(F.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+        assert np.all(err < 1e-9) and not info["refactored"]
