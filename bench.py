@@ -139,7 +139,9 @@ def run_reference(args):
 
 
 def workload_config(args):
-    return {"workload": "cuboid 40x30x10 cells, d=10 nm, N=12000 (3N=36000), eps~U[2,16]+iU[0,0.5] seed 2, "
+    nx, ny, nz = (int(v) for v in getattr(args, "cuboid", "40x30x10").split("x"))
+    n = nx * ny * nz
+    return {"workload": f"cuboid {nx}x{ny}x{nz} cells, d=10 nm, N={n} (3N={3 * n}), eps~U[2,16]+iU[0,0.5] seed 2, "
                         "lambda=500 nm, x- and y-polarised plane waves; assemble + LU + FP64-refined solve",
             "precision": args.precision, "n_rhs": 2,
             "l2": "inputs larger than L2 (10.4 GB complex64 matrix rewritten every step)"}
@@ -153,6 +155,8 @@ def main():
     ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cuboid", default="40x30x10",
+                    help="cells per axis of the cuboid workload (smaller cases are for profiling only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -173,7 +177,8 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu_base = cpu_oracle_sample()  # before any GPU work of this process
 
-    s = W.cuboid_precision()
+    nx, ny, nz = (int(v) for v in args.cuboid.split("x"))
+    s = W.cuboid_precision(nx, ny, nz)
     lam = float(s.wavelengths[0])
     ctx = G.Context(local)
     pos = torch.tensor(s.pos, device=dev)
@@ -206,11 +211,13 @@ def main():
     l0 = ctx.launches
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record()
     infos = []
     for _ in range(args.steps):
         infos.append(step())
     e1.record()
+    torch.cuda.nvtx.range_pop()
     barrier()
     launches = ctx.launches - l0
     prof = ctx.profile_read()

@@ -179,6 +179,12 @@ gdm_status gdm_lu_factor(gdm_ctx *ctx, gdm_precision prec, void *A, int64_t n, i
 // conj_trans = 0: A X = B using P, L, U; conj_trans = 1: A^H X = B.
 gdm_status gdm_lu_solve(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda, const int32_t *ipiv,
                         void *B, int64_t ldb, int n_rhs, int conj_trans);
+// trsv.cu: persistent blocked solves (pivots must stay inside their row blocks) and the check for that
+size_t gdm_trsv_sync_bytes(int64_t n);
+gdm_status gdm_pivots_local(gdm_ctx *ctx, const int32_t *ipiv, int64_t n, int nbs, int *sync_buf, int *local);
+gdm_status gdm_trsv_persistent(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda,
+                               const int32_t *ipiv, void *B, int64_t ldb, int n_rhs, int conj_trans, int *sync_buf);
+int gdm_lu_block(gdm_precision prec);
 // refine.cu
 gdm_status gdm_refined_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
                              const int32_t *ipiv, const double *rhs, double *X, int n_rhs, int adjoint,

@@ -7,6 +7,7 @@
 // until max_q ||d_q|| / ||X_q|| <= tol. The adjoint variant solves A^H X = b with the same factors
 // (conjugate-transposed triangular solves) and the matrix-free residual b - A^H X.
 #include <math.h>
+#include <stdlib.h>
 
 #include "gdm_internal.cuh"
 
@@ -88,7 +89,8 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     const int64_t cnt = ns * n_rhs;
     size_t need = ScratchCarver::round(cnt * sizeof(double2)) * 2 + ScratchCarver::round(cnt * sizeof(C)) +
                   ScratchCarver::round(gdm_green_partial_bytes(ctx, p->n, p->n, p->kind)) +
-                  ScratchCarver::round(sizeof(double) * 4 * n_rhs) + 4096;
+                  ScratchCarver::round(sizeof(double) * 4 * n_rhs) + ScratchCarver::round(gdm_trsv_sync_bytes(ns)) +
+                  4096;
     // the LU scratch is not needed any more: the refinement reuses the arena
     void *ws;
     GDM_TRY(gdm_scratch(ctx, need, &ws));
@@ -98,6 +100,7 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     C *w = sc.take<C>(cnt);
     double2 *partial = sc.take<double2>(gdm_green_partial_bytes(ctx, p->n, p->n, p->kind) / sizeof(double2));
     double *dnorm = sc.take<double>(4 * n_rhs);
+    int *tsync = sc.take<int>(gdm_trsv_sync_bytes(ns) / sizeof(int));
     double *hn;
     GDM_TRY(gdm_pinned(ctx, sizeof(double) * 4 * n_rhs, (void **)&hn));
     const unsigned nb = (unsigned)((ns + 255) / 256);
@@ -106,11 +109,18 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     GDM_CUDA_TRY(ctx, cudaMemsetAsync(dnorm, 0, sizeof(double) * 4 * n_rhs, ctx->stream));
     k_norm2<<<gq, 256, 0, ctx->stream>>>((const double2 *)rhs, ns, dnorm + 3 * n_rhs);
     GDM_LAUNCHED(ctx, "norm2");
+    // persistent block solves when every pivot stays inside its row block
+    int local = 0;
+    if (!getenv("GDM_TRSV_LAUNCHES")) GDM_TRY(gdm_pivots_local(ctx, ipiv, ns, gdm_lu_block(prec), tsync, &local));
+    auto lu_solve = [&](void *w) -> gdm_status {
+        if (local) return gdm_trsv_persistent(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint, tsync);
+        return gdm_lu_solve(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint);
+    };
     if (info) GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     // initial solve
     k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>((const double2 *)rhs, w, cnt, 1.0);
     GDM_LAUNCHED(ctx, "to_work");
-    GDM_TRY(gdm_lu_solve(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint));
+    GDM_TRY(lu_solve(w));
     k_update<C><<<gq, 256, 0, ctx->stream>>>((double2 *)X, w, ns, n_rhs, 0, 1.0, dnorm, ctx->dflags);
     GDM_LAUNCHED(ctx, "update");
     int it = 0;
@@ -123,7 +133,7 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
             // scale the residual into a safe FP32 range before the low-precision solve
             k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(r, w, cnt, 1.0);
             GDM_LAUNCHED(ctx, "to_work");
-            GDM_TRY(gdm_lu_solve(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint));
+            GDM_TRY(lu_solve(w));
             k_update<C><<<gq, 256, 0, ctx->stream>>>((double2 *)X, w, ns, n_rhs, 1, 1.0, dnorm, ctx->dflags);
             GDM_LAUNCHED(ctx, "update");
             GDM_CUDA_TRY(ctx, cudaMemcpyAsync(hn, dnorm, sizeof(double) * 4 * n_rhs, cudaMemcpyDeviceToHost,
