@@ -166,6 +166,13 @@ gdm_status gdm_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, voi
                      int32_t *ipiv, const double *F0, double *F, int n_rhs, const gdm_solve_opts *opts,
                      gdm_solve_info *info);
 
+/* Residual r = F0 - A F of problem p for given fields F (FP64 result), computed matrix-free: the
+ * Green dyads are regenerated for every pair (double-float arithmetic for cells, FP64 for ED/MD dipoles),
+ * no stored matrix. This is the residual that drives gdm_solve's refinement (Eq. GDM_system_of_equations).
+ * F0, F, r: device (kind*n) x n_rhs complex128; norms2: device n_rhs doubles receiving ||r_q||^2, or NULL. */
+gdm_status gdm_residual(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F, int n_rhs, double *r,
+                        double *norms2);
+
 /* Near field by repropagation (Sec. "Observables"): at m points r_eval (device,
  * m x 3, none on a dipole), E = E0 + sum_j [G^Ep p_j + G^Em m_j] and
  * H = H0 + sum_j [G^Hp p_j + G^Hm m_j] with (p, m)_j = alpha_j F_j.

@@ -4,7 +4,7 @@ The compute lives in the CUDA library libgdm.so (C ABI: include/gdm.h); this
 package only builds/loads it and marshals arguments (see `binding`)."""
 from . import autograd  # noqa: F401
 from .binding import (Context, GDMError, GDMProblem, assemble, backward, cross_sections, incident_planewave, lib,
-                      nearfield, nearfield_backward, padded_lda, solve)
+                      nearfield, nearfield_backward, padded_lda, residual, solve)
 
 __all__ = ["Context", "GDMError", "GDMProblem", "assemble", "backward", "cross_sections", "incident_planewave",
-           "lib", "nearfield", "nearfield_backward", "padded_lda", "solve"]
+           "lib", "nearfield", "nearfield_backward", "padded_lda", "residual", "solve"]

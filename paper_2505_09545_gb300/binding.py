@@ -75,6 +75,7 @@ _SIGS = {
     "gdm_solve": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, P, C.c_int, C.POINTER(SolveOpts),
                    C.POINTER(SolveInfo)], C.c_int),
     "gdm_nearfield": ([P, C.POINTER(Problem), P, P, I64, P, C.c_int, P, P], C.c_int),
+    "gdm_residual": ([P, C.POINTER(Problem), P, P, C.c_int, P, P], C.c_int),
     "gdm_cross_sections": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
     "gdm_backward": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, C.c_int, PD, PD, P, PD, P, P, P,
                       C.POINTER(SolveInfo)], C.c_int),
@@ -245,6 +246,17 @@ def solve(ctx: Context, prob: GDMProblem, A, F0, precision="fp32", ipiv=None, fa
     ctx._check(lib().gdm_solve(ctx.h, C.byref(s), PRECISION[precision], _ptr(A), lda, _ptr(ipiv), _ptr(F0.contiguous()),
                                _ptr(F), n_rhs, C.byref(opts), C.byref(inf) if info else None), "gdm_solve")
     return F, ipiv, (inf.as_dict() if info else None)
+
+
+def residual(ctx: Context, prob: GDMProblem, F0, F):
+    """FP64 matrix-free residual F0 - A F: returns (r, ||r_q||^2) with r shaped like F."""
+    r = torch.empty_like(F)
+    n2 = torch.zeros(F.shape[0], dtype=torch.float64, device=F.device)
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_residual(ctx.h, C.byref(s), _ptr(F0.contiguous()), _ptr(F.contiguous()), F.shape[0], _ptr(r),
+                                  _ptr(n2)), "gdm_residual")
+    return r, n2
 
 
 def nearfield(ctx: Context, prob: GDMProblem, F, r_eval, F0_eval=None, with_h=True):

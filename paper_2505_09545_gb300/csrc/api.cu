@@ -6,6 +6,14 @@
 
 #include "gdm_internal.cuh"
 
+#include <stdlib.h>
+
+size_t gdm_ff_scratch_bytes(int64_t n);
+size_t gdm_green_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n, int out);
+gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
+                                  int adjoint, double *r, double *norms2, double2 *Pbuf, double2 *partial, void *ffws,
+                                  int ff_prepare);
+
 gdm_status gdm_fail(gdm_ctx *ctx, gdm_status s, const char *fmt, ...) {
     if (ctx) {
         va_list ap;
@@ -319,6 +327,27 @@ gdm_status gdm_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, voi
         info->refactored = refactored;
     }
     return s;
+}
+
+gdm_status gdm_residual(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F, int n_rhs, double *r,
+                        double *norms2) {
+    GDM_TRY(check_problem(ctx, p));
+    if (!F0 || !F || !r) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n_rhs must be in [1, 64]");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    gdm_params_reset(ctx);
+    const int64_t cnt = p->n * p->kind * n_rhs;
+    const bool ff = (p->kind == 3 && !getenv("GDM_RESIDUAL_FP64"));
+    size_t pb = gdm_green_partial_bytes(ctx, p->n, p->n, p->kind);
+    size_t need = ScratchCarver::round(cnt * sizeof(double2)) + ScratchCarver::round(pb) +
+                  ScratchCarver::round(gdm_ff_scratch_bytes(p->n)) + 1024;
+    void *ws;
+    GDM_TRY(gdm_scratch(ctx, need, &ws));
+    ScratchCarver sc(ws);
+    double2 *Pbuf = sc.take<double2>(cnt);
+    double2 *partial = sc.take<double2>(pb / sizeof(double2));
+    void *ffws = ff ? sc.take<char>(gdm_ff_scratch_bytes(p->n)) : nullptr;
+    return gdm_launch_residual_ws(ctx, p, F0, F, n_rhs, 0, r, norms2, Pbuf, partial, ffws, 1);
 }
 
 gdm_status gdm_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, const double *r_eval, int64_t m,

@@ -17,8 +17,7 @@
 #define PI_D 3.14159265358979323846
 
 size_t gdm_green_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n, int out);
-gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
-                                  int adjoint, double *r, double *norms2, double2 *Pbuf, double2 *partial);
+
 
 namespace {
 

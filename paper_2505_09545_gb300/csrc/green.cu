@@ -668,9 +668,14 @@ static gdm_status launch_green_sum(gdm_ctx *ctx, const double *tpos, int64_t m, 
     return GDM_OK;
 }
 
-// residual of the FP64 system (matrix-free); scratch: P (kN x n_rhs) + partial buffer
+gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const double2 *P, int rhs0, int nr,
+                                   int64_t chunk, int nchunks, void *ffws, double2 *partial, int prepare);
+
+// residual of the FP64 system (matrix-free); scratch: P (kN x n_rhs) + partial buffer; ffws (nullable):
+// double-float workspace (gdm_ff_scratch_bytes) selecting the double-float pair kernel for cells.
 gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
-                                  int adjoint, double *r, double *norms2, double2 *Pbuf, double2 *partial) {
+                                  int adjoint, double *r, double *norms2, double2 *Pbuf, double2 *partial, void *ffws,
+                                  int ff_prepare) {
     const int64_t n = p->n;
     const int kind = p->kind;
     if (adjoint && kind != 3) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "adjoint residual implemented for kind 3");
@@ -685,7 +690,11 @@ gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const doub
     for (int q0 = 0; q0 < n_rhs; q0 += 2) {
         int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
         int nc;
-        if (kind == 3)
+        if (kind == 3 && ffws) {
+            int64_t chunk;
+            green_grid(ctx, n, n, &chunk, &nc);
+            GDM_TRY(gdm_launch_green_sum_ff(ctx, p, Pbuf, q0, nr, chunk, nc, ffws, partial, ff_prepare && q0 == 0));
+        } else if (kind == 3)
             GDM_TRY(launch_green_sum<3, 3>(ctx, p->pos, n, p->pos, Pbuf, n, q0, nr, k, k0, 1.0 / p->eps_env, 1,
                                            partial, &nc));
         else

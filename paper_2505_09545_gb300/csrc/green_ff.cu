@@ -1,0 +1,280 @@
+// Matrix-free refinement residual in double-float arithmetic (cells, kind 3).
+//
+// The residual r = F0 - A F of the FP64 refinement needs the Green dyad G^Ep of every pair to ~1e-13
+// relative. GB300 runs FP64 at ~1/64 of its FP32 rate, so this kernel regenerates G in double-float
+// (FP32 pairs, ~48 significant bits: Knuth two-sum, FMA two-product) on the FP32 pipes:
+//   * r_i - r_j from FP32 (hi, lo) position pairs; R, 1/R, R-hat in double-float;
+//   * phase k R reduced modulo 2 pi with a three-part split of 2 pi;
+//   * e^{i theta}: table of cos/sin at multiples of pi/128 (double-float entries computed on the host in
+//     double precision) times cos/sin of the remainder |delta| <= pi/256 from its Taylor series
+//     (cos: 1 - d^2/2 + d^4/24 - d^6/720, sin: d - d^3/6 + d^5/120; the neglected terms are < 1e-15);
+//   * G s = a s + b u (u.s), accumulated in double-float, written as FP64 partial sums for the FP64 finalize.
+#include <math.h>
+
+#include "gdm_internal.cuh"
+
+namespace {
+
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff mk(float h, float l) { return {h, l}; }
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff add(ff x, ff y) {
+    ff s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ ff neg(ff x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ ff sub(ff x, ff y) { return add(x, neg(y)); }
+__device__ __forceinline__ ff mul(ff x, ff y) {
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff mulf(ff x, float y) {
+    float p = __fmul_rn(x.hi, y);
+    float e = fmaf(x.hi, y, -p);
+    e = fmaf(x.lo, y, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff sqr(ff x) {
+    float p = __fmul_rn(x.hi, x.hi);
+    float e = fmaf(x.hi, x.hi, -p);
+    e = fmaf(2.0f * x.hi, x.lo, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ffsqrt(ff x) {
+    float r = sqrtf(x.hi);
+    float p = __fmul_rn(r, r);
+    float e = fmaf(r, r, -p);
+    float res = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), e), x.lo);
+    return fast_two_sum(r, __fdiv_rn(res, 2.0f * r));
+}
+__device__ __forceinline__ ff recip(ff x) {
+    float r = __fdiv_rn(1.0f, x.hi);
+    // d = 1 - x r (in double-float), y = r + r d
+    float p = __fmul_rn(x.hi, r);
+    float ep = fmaf(x.hi, r, -p);
+    ep = fmaf(x.lo, r, ep);
+    float d = __fsub_rn(__fsub_rn(1.0f, p), ep);
+    return fast_two_sum(r, __fmul_rn(r, d));
+}
+struct cff {
+    ff re, im;
+};
+__device__ __forceinline__ cff cmulff(cff a, cff b) {
+    return {sub(mul(a.re, b.re), mul(a.im, b.im)), add(mul(a.re, b.im), mul(a.im, b.re))};
+}
+__device__ __forceinline__ cff caddff(cff a, cff b) { return {add(a.re, b.re), add(a.im, b.im)}; }
+__device__ __forceinline__ cff cscaleff(cff a, ff s) { return {mul(a.re, s), mul(a.im, s)}; }
+
+#define TWO_PI_C1 6.283203125f
+#define TWO_PI_C2 (-1.7814338207244873e-05f)
+#define TWO_PI_C3 (-3.4822063010864213e-09f)
+#define INV_TWO_PI_F 0.15915494309189535f
+// pi/128 = P1 + P2 + P3, P1 and P2 with 16 significant bits (i * P1, i * P2 exact for |i| <= 128)
+#define PI128_P1 0.02454376220703125f
+#define PI128_P2 (-6.95999915478751e-08f)
+#define PI128_P3 (-8.694424303776205e-13f)
+#define INV_PI128_F 40.7436637878418f
+
+// e^{i x} for a double-float phase x >= 0; tab[i + 128] = (cos_hi, cos_lo, sin_hi, sin_lo) at i pi/128
+__device__ __forceinline__ cff expi_ff(ff x, const float4 *tab) {
+    float n = rintf(x.hi * INV_TWO_PI_F);
+    float t1 = fmaf(-n, TWO_PI_C1, x.hi);
+    ff s = two_sum(t1, -n * TWO_PI_C2);
+    ff th = fast_two_sum(s.hi, fmaf(-n, TWO_PI_C3, __fadd_rn(s.lo, x.lo)));
+    float fi = rintf(th.hi * INV_PI128_F);
+    fi = fminf(fmaxf(fi, -128.f), 128.f);
+    float u1 = fmaf(-fi, PI128_P1, th.hi);
+    ff s2 = two_sum(u1, -fi * PI128_P2);
+    ff d = fast_two_sum(s2.hi, fmaf(-fi, PI128_P3, __fadd_rn(s2.lo, th.lo)));
+    ff d2 = sqr(d);
+    float d2f = d2.hi;
+    // cos d = 1 - d^2/2 + (d^4/24 - d^6/720);  sin d = d - d^3/6 + d^5/120
+    ff cd = sub(mk(1.0f, 0.0f), mulf(d2, 0.5f));
+    cd = add(cd, mk(d2f * d2f * (1.0f / 24.0f - d2f * (1.0f / 720.0f)), 0.0f));
+    ff d3 = mul(d2, d);
+    ff sd = sub(d, mul(d3, mk(0.16666667163372040f, -4.967053879312289e-09f)));  // 1/6 in double-float
+    sd = add(sd, mk(d3.hi * d2f * (1.0f / 120.0f), 0.0f));
+    float4 t = tab[(int)fi + 128];
+    ff c0 = mk(t.x, t.y), s0 = mk(t.z, t.w);
+    return {sub(mul(c0, cd), mul(s0, sd)), add(mul(s0, cd), mul(c0, sd))};
+}
+
+struct DipF {
+    float xh, yh, zh, xl, yl, zl;
+    float2 alpha;
+    float2 diag;
+    float pad[2];
+};
+
+#define RF_T 128
+#define RF_S 32
+
+// partial[c][q][t][3] (FP64) = sum over sources j != t of chunk c of G^Ep(r_t - r_j) P_j
+template <int NR>
+__global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ dip, int64_t n,
+                                                      const double2 *__restrict__ P, int rhs0, int nr_here, float khi,
+                                                      float klo, float k2hi, float k2lo, float ie_hi, float ie_lo,
+                                                      const float4 *__restrict__ gtab, int64_t chunk,
+                                                      double2 *__restrict__ partial) {
+    __shared__ float4 tab[257];
+    __shared__ float sxyz[RF_S][6];
+    __shared__ float4 sm[RF_S][3][NR];  // (re_hi, re_lo, im_hi, im_lo)
+    for (int e = threadIdx.x; e < 257; e += RF_T) tab[e] = gtab[e];
+    const int64_t t = (int64_t)blockIdx.x * RF_T + threadIdx.x;
+    const bool valid = t < n;
+    const int64_t c = blockIdx.y;
+    const int64_t jb = c * chunk, je = min(n, jb + chunk);
+    DipF ti = valid ? dip[t] : dip[0];
+    const ff kf = mk(khi, klo), k2 = mk(k2hi, k2lo), ie = mk(ie_hi, ie_lo);
+    cff acc[NR][3];
+#pragma unroll
+    for (int q = 0; q < NR; q++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) acc[q][a] = {mk(0, 0), mk(0, 0)};
+    const int64_t ld = 3 * n;
+    for (int64_t s0 = jb; s0 < je; s0 += RF_S) {
+        const int sn = (int)min((int64_t)RF_S, je - s0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < sn; e += RF_T) {
+            DipF d = dip[s0 + e];
+            sxyz[e][0] = d.xh;
+            sxyz[e][1] = d.yh;
+            sxyz[e][2] = d.zh;
+            sxyz[e][3] = d.xl;
+            sxyz[e][4] = d.yl;
+            sxyz[e][5] = d.zl;
+        }
+        for (int e = threadIdx.x; e < sn * 3 * NR; e += RF_T) {
+            int jj = e / (3 * NR), rem = e % (3 * NR), a = rem / NR, q = rem % NR;
+            double2 v = make_double2(0.0, 0.0);
+            if (q < nr_here) v = P[(rhs0 + q) * ld + 3 * (s0 + jj) + a];
+            float rh = (float)v.x, ih = (float)v.y;
+            sm[jj][a][q] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int jj = 0; jj < sn; jj++) {
+            if (s0 + jj == t) continue;
+            ff dx = add(two_sum(ti.xh, -sxyz[jj][0]), mk(__fsub_rn(ti.xl, sxyz[jj][3]), 0.f));
+            ff dy = add(two_sum(ti.yh, -sxyz[jj][1]), mk(__fsub_rn(ti.yl, sxyz[jj][4]), 0.f));
+            ff dz = add(two_sum(ti.zh, -sxyz[jj][2]), mk(__fsub_rn(ti.zl, sxyz[jj][5]), 0.f));
+            ff r2 = add(add(sqr(dx), sqr(dy)), sqr(dz));
+            ff r = ffsqrt(r2);
+            ff r1 = recip(r);
+            ff ri2 = sqr(r1);
+            ff ri3 = mul(ri2, r1);
+            ff u[3] = {mul(dx, r1), mul(dy, r1), mul(dz, r1)};
+            cff e = expi_ff(mul(kf, r), tab);
+            e = cscaleff(e, ie);
+            ff k2r1 = mul(k2, r1);
+            ff kri2 = mul(kf, ri2);
+            // a = e (k^2/R - 1/R^3 + i k/R^2),  b = e (3/R^3 - k^2/R - 3 i k/R^2)
+            cff ca = {sub(k2r1, ri3), kri2};
+            cff cb = {sub(mulf(ri3, 3.0f), k2r1), neg(mulf(kri2, 3.0f))};
+            cff a = cmulff(e, ca), b = cmulff(e, cb);
+#pragma unroll
+            for (int q = 0; q < NR; q++) {
+                cff s[3];
+#pragma unroll
+                for (int aa = 0; aa < 3; aa++) {
+                    float4 v = sm[jj][aa][q];
+                    s[aa] = {mk(v.x, v.y), mk(v.z, v.w)};
+                }
+                cff us = {add(add(mul(u[0], s[0].re), mul(u[1], s[1].re)), mul(u[2], s[2].re)),
+                          add(add(mul(u[0], s[0].im), mul(u[1], s[1].im)), mul(u[2], s[2].im))};
+                cff bus = cmulff(b, us);
+#pragma unroll
+                for (int aa = 0; aa < 3; aa++) {
+                    cff v = caddff(cmulff(a, s[aa]), cscaleff(bus, u[aa]));
+                    acc[q][aa] = caddff(acc[q][aa], v);
+                }
+            }
+        }
+    }
+    if (!valid) return;
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+        if (q >= nr_here) break;
+        double2 *o = partial + ((c * 2 + q) * n + t) * 3;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            o[a] = make_double2((double)acc[q][a].re.hi + (double)acc[q][a].re.lo,
+                                (double)acc[q][a].im.hi + (double)acc[q][a].im.lo);
+    }
+}
+
+__global__ void k_prep_dipf_pos(const double *__restrict__ pos, int64_t n, DipF *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    DipF d;
+    double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    d.xh = (float)x;
+    d.yh = (float)y;
+    d.zh = (float)z;
+    d.xl = (float)(x - (double)d.xh);
+    d.yl = (float)(y - (double)d.yh);
+    d.zl = (float)(z - (double)d.zh);
+    d.alpha = make_float2(0.f, 0.f);
+    d.diag = make_float2(0.f, 0.f);
+    d.pad[0] = d.pad[1] = 0.f;
+    out[i] = d;
+}
+
+void split(double v, float *h, float *l) {
+    *h = (float)v;
+    *l = (float)(v - (double)*h);
+}
+
+}  // namespace
+
+size_t gdm_ff_scratch_bytes(int64_t n) { return ScratchCarver::round(n * sizeof(DipF)) + 257 * 16 + 512; }
+
+// Same output as the FP64 Green sum used by the residual (partial sums per chunk, two RHS per launch).
+gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const double2 *P, int rhs0, int nr,
+                                   int64_t chunk, int nchunks, void *ffws, double2 *partial, int prepare) {
+    const int64_t n = p->n;
+    ScratchCarver sc(ffws);
+    DipF *dip = sc.take<DipF>(n);
+    float4 *tab = sc.take<float4>(257);
+    if (prepare) {
+        k_prep_dipf_pos<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(p->pos, n, dip);
+        GDM_LAUNCHED(ctx, "prep_dipf_pos");
+        float4 h[257];
+        for (int i = -128; i <= 128; i++) {
+            double a = i * (3.14159265358979323846 / 128.0);
+            float ch, cl, sh, sl;
+            split(cos(a), &ch, &cl);
+            split(sin(a), &sh, &sl);
+            h[i + 128] = make_float4(ch, cl, sh, sl);
+        }
+        GDM_CUDA_TRY(ctx, cudaMemcpyAsync(tab, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+        GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // h is a stack array
+    }
+    const double k = sqrt(p->eps_env) * gdm_k0(p);
+    float khi, klo, k2hi, k2lo, iehi, ielo;
+    split(k, &khi, &klo);
+    split(k * k, &k2hi, &k2lo);
+    split(1.0 / p->eps_env, &iehi, &ielo);
+    dim3 grid((unsigned)((n + RF_T - 1) / RF_T), (unsigned)nchunks);
+    if (nr == 1)
+        k_green_sum_ff<1><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo, tab,
+                                                          chunk, partial);
+    else
+        k_green_sum_ff<2><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo, tab,
+                                                          chunk, partial);
+    GDM_LAUNCHED(ctx, "green_sum_ff");
+    return GDM_OK;
+}

@@ -12,7 +12,9 @@
 #include "gdm_internal.cuh"
 
 gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
-                                  int adjoint, double *r, double *norms2, double2 *Pbuf, double2 *partial);
+                                  int adjoint, double *r, double *norms2, double2 *Pbuf, double2 *partial, void *ffws,
+                                  int ff_prepare);
+size_t gdm_ff_scratch_bytes(int64_t n);
 size_t gdm_green_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n, int out);
 
 template <class C>
@@ -90,6 +92,7 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     size_t need = ScratchCarver::round(cnt * sizeof(double2)) * 2 + ScratchCarver::round(cnt * sizeof(C)) +
                   ScratchCarver::round(gdm_green_partial_bytes(ctx, p->n, p->n, p->kind)) +
                   ScratchCarver::round(sizeof(double) * 4 * n_rhs) + ScratchCarver::round(gdm_trsv_sync_bytes(ns)) +
+                  ScratchCarver::round(gdm_trsv_inv_bytes(ns)) + ScratchCarver::round(gdm_ff_scratch_bytes(p->n)) +
                   4096;
     // the LU scratch is not needed any more: the refinement reuses the arena
     void *ws;
@@ -101,6 +104,9 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     double2 *partial = sc.take<double2>(gdm_green_partial_bytes(ctx, p->n, p->n, p->kind) / sizeof(double2));
     double *dnorm = sc.take<double>(4 * n_rhs);
     int *tsync = sc.take<int>(gdm_trsv_sync_bytes(ns) / sizeof(int));
+    void *dinv = sc.take<char>(gdm_trsv_inv_bytes(ns));
+    // double-float residual for cells unless GDM_RESIDUAL_FP64 is set
+    void *ffws = (p->kind == 3 && !getenv("GDM_RESIDUAL_FP64")) ? sc.take<char>(gdm_ff_scratch_bytes(p->n)) : nullptr;
     double *hn;
     GDM_TRY(gdm_pinned(ctx, sizeof(double) * 4 * n_rhs, (void **)&hn));
     const unsigned nb = (unsigned)((ns + 255) / 256);
@@ -112,8 +118,9 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     // persistent block solves when every pivot stays inside its row block
     int local = 0;
     if (!getenv("GDM_TRSV_LAUNCHES")) GDM_TRY(gdm_pivots_local(ctx, ipiv, ns, gdm_lu_block(prec), tsync, &local));
+    if (local) GDM_TRY(gdm_trsv_prepare(ctx, prec, A, ns, lda, dinv));
     auto lu_solve = [&](void *w) -> gdm_status {
-        if (local) return gdm_trsv_persistent(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint, tsync);
+        if (local) return gdm_trsv_persistent(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint, tsync, dinv);
         return gdm_lu_solve(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint);
     };
     if (info) GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
@@ -129,7 +136,7 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
         for (it = 1; it <= opts->max_iter; it++) {
             GDM_CUDA_TRY(ctx, cudaMemsetAsync(dnorm, 0, sizeof(double) * 3 * n_rhs, ctx->stream));
             GDM_TRY(gdm_launch_residual_ws(ctx, p, rhs, X, n_rhs, adjoint, (double *)r, dnorm + 2 * n_rhs, Pbuf,
-                                           partial));
+                                           partial, ffws, it == 1));
             // scale the residual into a safe FP32 range before the low-precision solve
             k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(r, w, cnt, 1.0);
             GDM_LAUNCHED(ctx, "to_work");

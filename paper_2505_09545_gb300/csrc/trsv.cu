@@ -66,7 +66,7 @@ template <class C, int NBS, int NR>
 __global__ void __launch_bounds__(2 * NBS) k_trsv_persistent(const C *__restrict__ A, int64_t lda, int64_t n,
                                                              const int32_t *__restrict__ ipiv, C *__restrict__ B,
                                                              int64_t ldb, int rhs0, int nr_here, int mode,
-                                                             int *sync_buf, int *gflags) {
+                                                             const C *__restrict__ dinv, int *sync_buf, int *gflags) {
     constexpr int NT = 2 * NBS;
     constexpr int NW = NT / 32;
     __shared__ C acc[NBS][NR];
@@ -95,9 +95,20 @@ __global__ void __launch_bounds__(2 * NBS) k_trsv_persistent(const C *__restrict
     // -------- contributions of the solved blocks
     for (int s = 0; s < tk; s++) {
         const int k = fwd ? s : nblk - 1 - s;
-        if (!wait_flag(flags + k, abort_flag, gflags)) return;
         const int64_t k0 = (int64_t)k * NBS;
         const int nk = (int)min((int64_t)NBS, n - k0);
+        {
+            // pull this dependency block into L2 while (possibly) waiting for its solution
+            const int64_t cb = (mode <= 1) ? k0 : r0;  // first column of the block read below
+            const int64_t rb = (mode <= 1) ? r0 : k0;  // first row
+            const int ncol = (mode <= 1) ? nk : nr, nrow = (mode <= 1) ? nr : nk;
+            const int lines_per_col = (int)((nrow * sizeof(C) + 127) / 128);
+            for (int e = tid; e < ncol * lines_per_col; e += NT) {
+                const char *ptr = (const char *)(A + (cb + e / lines_per_col) * lda + rb) + (e % lines_per_col) * 128;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+            }
+        }
+        if (!wait_flag(flags + k, abort_flag, gflags)) return;
         for (int e = tid; e < NBS * NR; e += NT) {
             int r = e / NR, q = e % NR;
             yk[r][q] = (r < nk && q < nr_here) ? __ldcg(B + (int64_t)(rhs0 + q) * ldb + k0 + r) : cz<C>();
@@ -112,7 +123,7 @@ __global__ void __launch_bounds__(2 * NBS) k_trsv_persistent(const C *__restrict
             if (r < nr) {
                 const C *col = A + (k0 + h * (NBS / 2)) * lda + r0 + r;
                 const int cend = min(NBS / 2, nk - h * (NBS / 2));
-#pragma unroll 8
+#pragma unroll 16
                 for (int c = 0; c < cend; c++) {
                     C m = col[(int64_t)c * lda];
 #pragma unroll
@@ -166,71 +177,50 @@ __global__ void __launch_bounds__(2 * NBS) k_trsv_persistent(const C *__restrict
         }
     }
     __syncthreads();
-    // column-oriented substitution in sub-blocks of 32: solve the 32 x 32 diagonal piece with one warp per
-    // right-hand side (shuffles), then update the remaining rows of the block
+    // diagonal block in pieces of 32: x_s = inv(T_ss) acc_s with the precomputed 32 x 32 inverses of the
+    // factors' diagonal pieces (conjugate-transposed for the adjoint modes), then update the remaining rows
     const bool lower_like = (mode == 0 || mode == 2);
     const int nsub = (nr + 31) / 32;
+    const int use_u = (mode == 1 || mode == 2);
+    const bool herm = (mode >= 2);
     for (int si = 0; si < nsub; si++) {
         const int sb = lower_like ? si : nsub - 1 - si;
         const int c0 = sb * 32;
         const int w = min(32, nr - c0);
-        const int wi = tid / 32, lane = tid % 32;
-        if (wi < NR && wi < nr_here) {
-            // T[lane][i]: entry (c0+lane, c0+i) of the effective triangle
-            C T[32];
+        const C *Ti = dinv + ((int64_t)2 * ((r0 + c0) / 32) + use_u) * 1024;
+        __syncthreads();
+        // x[row][q] = sum_i Tinv_eff[row][i] acc[c0+i][q]; one thread per (row, q)
+        C xv = cz<C>();
+        const int row = tid % 32, q = tid / 32;
+        if (q < NR && row < w) {
+            C m[32];
 #pragma unroll
-            for (int i = 0; i < 32; i++) {
-                C v = cz<C>();
-                if (lane < w && i < w) {
-                    if (mode <= 1) v = D[(int64_t)(c0 + i) * lda + c0 + lane];
-                    else v = conjc(D[(int64_t)(c0 + lane) * lda + c0 + i]);
-                }
-                T[i] = v;
-            }
-            C v = lane < w ? acc[c0 + lane][wi] : cz<C>();
-            const bool unit = (mode == 0 || mode == 3);
-            if (lower_like) {
+            for (int i = 0; i < 32; i++) m[i] = herm ? conjc(Ti[i * 32 + row]) : Ti[row * 32 + i];
 #pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    if (i < w) {
-                        if (!unit && lane == i) v = cmul(v, crecip(T[i]));
-                        C xi;
-                        xi.x = __shfl_sync(0xffffffffu, v.x, i);
-                        xi.y = __shfl_sync(0xffffffffu, v.y, i);
-                        if (lane > i && lane < w) cfms(v, T[i], xi);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int i = 31; i >= 0; i--) {
-                    if (i < w) {
-                        if (!unit && lane == i) v = cmul(v, crecip(T[i]));
-                        C xi;
-                        xi.x = __shfl_sync(0xffffffffu, v.x, i);
-                        xi.y = __shfl_sync(0xffffffffu, v.y, i);
-                        if (lane < i) cfms(v, T[i], xi);
-                    }
-                }
-            }
-            if (lane < w) acc[c0 + lane][wi] = v;
+            for (int i = 0; i < 32; i++)
+                if (i < w) cfma(xv, m[i], acc[c0 + i][q]);
         }
         __syncthreads();
-        // update rows of the block not yet solved with the 32 solved values
+        if (q < NR && row < w) acc[c0 + row][q] = xv;
+        __syncthreads();
         const int ub = lower_like ? c0 + w : 0;
         const int ue = lower_like ? nr : c0;
         for (int r = ub + tid; r < ue; r += NT) {
             C sum[NR];
 #pragma unroll
-            for (int q = 0; q < NR; q++) sum[q] = cz<C>();
-            for (int i = 0; i < w; i++) {
-                C m;
-                if (mode <= 1) m = D[(int64_t)(c0 + i) * lda + r];
-                else m = conjc(D[(int64_t)r * lda + c0 + i]);
+            for (int qq = 0; qq < NR; qq++) sum[qq] = cz<C>();
+            C m[32];
 #pragma unroll
-                for (int q = 0; q < NR; q++) cfma(sum[q], m, acc[c0 + i][q]);
+            for (int i = 0; i < 32; i++) {
+                if (i < w) m[i] = (mode <= 1) ? D[(int64_t)(c0 + i) * lda + r] : conjc(D[(int64_t)r * lda + c0 + i]);
             }
 #pragma unroll
-            for (int q = 0; q < NR; q++) acc[r][q] = csub(acc[r][q], sum[q]);
+            for (int i = 0; i < 32; i++)
+                if (i < w)
+#pragma unroll
+                    for (int qq = 0; qq < NR; qq++) cfma(sum[qq], m[i], acc[c0 + i][qq]);
+#pragma unroll
+            for (int qq = 0; qq < NR; qq++) acc[r][qq] = csub(acc[r][qq], sum[qq]);
         }
         __syncthreads();
     }
@@ -254,6 +244,60 @@ __global__ void __launch_bounds__(2 * NBS) k_trsv_persistent(const C *__restrict
     if (tid == 0) atomicExch((int *)(flags + j), 1);
 }
 
+// Inverses of the 32 x 32 diagonal pieces of L (unit lower) and U (upper) of every panel:
+// inv[(2*p + 0)*1024 + r*32 + c] = (L_pp^{-1})[r][c], inv[(2*p + 1)*1024 + r*32 + c] = (U_pp^{-1})[r][c].
+// One warp per triangle; lane c computes column c of the inverse by substitution on e_c.
+template <class C>
+__global__ void k_diag_inverses(const C *__restrict__ A, int64_t lda, int64_t n, C *__restrict__ inv) {
+    // one warp (block) per triangle
+    const int warp = blockIdx.x, lane = threadIdx.x & 31;
+    const int np = (int)((n + 31) / 32);
+    if (warp >= 2 * np) return;
+    const int p = warp / 2, up = warp & 1;
+    const int64_t c0 = (int64_t)p * 32;
+    const int w = (int)min((int64_t)32, n - c0);
+    __shared__ C t[32][33];
+    for (int r = 0; r < 32; r++) {
+        C v = cz<C>();
+        if (r < w && lane < w) v = A[(c0 + lane) * lda + c0 + r];
+        t[r][lane] = v;  // t[row][col]
+    }
+    __syncwarp();
+    C x[32];
+#pragma unroll
+    for (int r = 0; r < 32; r++) x[r] = cz<C>();
+    if (lane < w) {
+        if (!up) {
+            // L x = e_lane, unit lower: forward
+#pragma unroll
+            for (int r = 0; r < 32; r++) {
+                if (r < w) {
+                    C v = (r == lane) ? C{1, 0} : cz<C>();
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        if (j < r) cfms(v, t[r][j], x[j]);
+                    x[r] = v;
+                }
+            }
+        } else {
+            // U x = e_lane: backward with division by the diagonal
+#pragma unroll
+            for (int r = 31; r >= 0; r--) {
+                if (r < w) {
+                    C v = (r == lane) ? C{1, 0} : cz<C>();
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        if (j > r && j < w) cfms(v, t[r][j], x[j]);
+                    x[r] = cmul(v, crecip(t[r][r]));
+                }
+            }
+        }
+    }
+    C *o = inv + ((int64_t)2 * p + up) * 1024;
+#pragma unroll
+    for (int r = 0; r < 32; r++) o[r * 32 + lane] = x[r];
+}
+
 // every pivot inside its own block of NBS rows?
 __global__ void k_pivots_local(const int32_t *__restrict__ ipiv, int64_t n, int nbs, int *bad) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -263,14 +307,14 @@ __global__ void k_pivots_local(const int32_t *__restrict__ ipiv, int64_t n, int 
 
 template <class C, int NBS>
 gdm_status launch_modes(gdm_ctx *ctx, const C *A, int64_t lda, int64_t n, const int32_t *ipiv, C *B, int64_t ldb,
-                        int n_rhs, const int *modes, int nmodes, int *sync_buf) {
+                        int n_rhs, const int *modes, int nmodes, int *sync_buf, C *dinv) {
     const int nblk = (int)((n + NBS - 1) / NBS);
     for (int mi = 0; mi < nmodes; mi++) {
         for (int q0 = 0; q0 < n_rhs; q0 += 2) {
             int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
             GDM_CUDA_TRY(ctx, cudaMemsetAsync(sync_buf, 0, sizeof(int) * (nblk + 2), ctx->stream));
             k_trsv_persistent<C, NBS, 2><<<nblk, 2 * NBS, 0, ctx->stream>>>(A, lda, n, ipiv, B, ldb, q0, nr, modes[mi],
-                                                                            sync_buf, ctx->dflags);
+                                                                            dinv, sync_buf, ctx->dflags);
             GDM_LAUNCHED(ctx, "trsv_persistent");
         }
     }
@@ -280,6 +324,20 @@ gdm_status launch_modes(gdm_ctx *ctx, const C *A, int64_t lda, int64_t n, const 
 }  // namespace
 
 size_t gdm_trsv_sync_bytes(int64_t n) { return sizeof(int) * ((n + 127) / 128 + 8); }
+
+// bytes of the diagonal-piece inverses (complex128 size, enough for both precisions)
+size_t gdm_trsv_inv_bytes(int64_t n) { return (size_t)2 * ((n + 31) / 32) * 1024 * sizeof(double2); }
+
+gdm_status gdm_trsv_prepare(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda, void *dinv) {
+    const int np = (int)((n + 31) / 32);
+    const unsigned blocks = (unsigned)(2 * np);
+    if (prec == GDM_FP64)
+        k_diag_inverses<double2><<<blocks, 32, 0, ctx->stream>>>((const double2 *)A, lda, n, (double2 *)dinv);
+    else
+        k_diag_inverses<float2><<<blocks, 32, 0, ctx->stream>>>((const float2 *)A, lda, n, (float2 *)dinv);
+    GDM_LAUNCHED(ctx, "diag_inverses");
+    return GDM_OK;
+}
 
 // 1 if all pivots stay inside their NBS-row block (synchronises)
 gdm_status gdm_pivots_local(gdm_ctx *ctx, const int32_t *ipiv, int64_t n, int nbs, int *sync_buf, int *local) {
@@ -296,11 +354,13 @@ gdm_status gdm_pivots_local(gdm_ctx *ctx, const int32_t *ipiv, int64_t n, int nb
 
 // solve with the factors: conj_trans = 0: U^{-1} L^{-1} P b; conj_trans = 1: P^T L^{-H} U^{-H} b
 gdm_status gdm_trsv_persistent(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda,
-                               const int32_t *ipiv, void *B, int64_t ldb, int n_rhs, int conj_trans, int *sync_buf) {
+                               const int32_t *ipiv, void *B, int64_t ldb, int n_rhs, int conj_trans, int *sync_buf,
+                               const void *dinv) {
     static const int fwd[2] = {0, 1}, adj[2] = {2, 3};
     const int *modes = conj_trans ? adj : fwd;
     if (prec == GDM_FP64)
         return launch_modes<double2, 128>(ctx, (const double2 *)A, lda, n, ipiv, (double2 *)B, ldb, n_rhs, modes, 2,
-                                          sync_buf);
-    return launch_modes<float2, 256>(ctx, (const float2 *)A, lda, n, ipiv, (float2 *)B, ldb, n_rhs, modes, 2, sync_buf);
+                                          sync_buf, (double2 *)dinv);
+    return launch_modes<float2, 256>(ctx, (const float2 *)A, lda, n, ipiv, (float2 *)B, ldb, n_rhs, modes, 2, sync_buf,
+                                     (float2 *)dinv);
 }

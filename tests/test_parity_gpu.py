@@ -245,3 +245,21 @@ def test_pivoting_certificate_and_fallback(G, ctx, eps, expect_refactor):
         F, _, info = G.solve(ctx, prob, A, F0, prec, global_pivot=True)
         err = np.linalg.norm(F.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
         assert np.all(err < 1e-9) and not info["refactored"]
+
+
+@pytest.mark.parametrize("lossy", [True, False])
+def test_residual_matches_oracle(G, ctx, lossy):
+    """gdm_residual (double-float pair sums for cells) = the oracle's F0 - A F, row by row, for arbitrary
+    (not solved) fields, to 1e-13 of the largest term."""
+    s = W.random_cells(300, seed=31, lossy=lossy)
+    lam = 530.0
+    prob = gpu_problem(G, s, lam)
+    rng = np.random.default_rng(2)
+    F = rng.standard_normal((2, 3 * s.n)) + 1j * rng.standard_normal((2, 3 * s.n))
+    F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0)
+    r, n2 = G.residual(ctx, prob, F0, t(F))
+    pr = oracle_problem(s, lam)
+    ro = O.residual_rows(pr, F0.cpu().numpy().T, F.T, np.arange(s.n)).reshape(3 * s.n, 2)
+    scale = np.abs(pr.matrix()).max() * np.abs(F).max()
+    assert np.abs(r.cpu().numpy().T - ro).max() <= 1e-13 * scale
+    np.testing.assert_allclose(n2.cpu().numpy(), np.sum(np.abs(ro) ** 2, axis=0), rtol=1e-10)
