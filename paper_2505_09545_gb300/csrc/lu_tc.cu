@@ -39,9 +39,12 @@ template <int BN, int SPLIT> struct Cfg {
     static constexpr int A_BYTES = BM * BK * 4;
     static constexpr int B_BYTES = BN * BK * 4;
     static constexpr int STAGE_BYTES = NP * (A_BYTES + B_BYTES);
-    static constexpr int STAGES = (SPLIT == 3) ? 3 : 4;
+    static constexpr int STAGES = 3;
     static constexpr int TMEM_COLS = 2 * BN;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 512 /*barriers*/;
+    static constexpr int NCB = (SPLIT == 3) ? 2 : 4;         // C staging buffers (128 rows x 32 columns each)
+    static constexpr int CB_BYTES = BM * 32 * 4;
+    static constexpr int LOOK = NCB / 2;                      // C chunks loaded ahead
+    static constexpr int SMEM = STAGES * STAGE_BYTES + NCB * CB_BYTES + 1024 /*alignment*/ + 512 /*barriers*/;
     // instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = BN
     static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(BM >> 4) << 24);
@@ -98,6 +101,18 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"((uint64_t)map),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core groups 1024 B apart
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
@@ -157,7 +172,8 @@ template <int BN, int SPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_update(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                 const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
-                float *__restrict__ Cm, int64_t ldc, int M, int N, int K, int bx0, int by0, int *gflags) {
+                const __grid_constant__ CUtensorMap tmC, int cx0, int cy0, int M, int N, int K, int bx0, int by0,
+                int *gflags) {
     using CF = Cfg<BN, SPLIT>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -167,7 +183,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint64_t *tfull = bars + 2 * CF::STAGES;     // [2]
     uint64_t *tempty = tfull + 2;                // [2]
     uint64_t *drain = tempty + 2;                // [1]
-    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    uint64_t *cbar = drain + 1;                  // [NCB] C chunk loads
+    float *cbuf = (float *)(base + CF::STAGES * CF::STAGE_BYTES + 512);  // NCB x (32 cols x 128 rows)
+    uint32_t *tmem_slot = (uint32_t *)(cbar + CF::NCB);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -185,6 +203,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&tempty[b], 4);
         }
         mbar_init(drain, 1);
+        for (int b = 0; b < CF::NCB; b++) mbar_init(&cbar[b], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -293,39 +312,88 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         }
     } else {
-        // ---------------- epilogue: warps 2..5 cover the four 32-lane quarters of tensor memory
+        // ---------------- epilogue: warps 2..5 cover the four 32-lane quarters of tensor memory.
+        // C streams through shared memory in 128 x 32 chunks: TMA loads run LOOK chunks ahead into a ring of
+        // NCB buffers, every thread subtracts its accumulator row, one thread issues the TMA store.
         const int q = warp & 3;
+        const int et = threadIdx.x - 64;  // 0..127
+        const bool leader = (et == 0);
+        constexpr int CPT = BN / 32;      // chunks per tile
+        const int my_tiles = (blockIdx.x < ntiles) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+        const int total = my_tiles * CPT;
+        auto coords = [&](int g, int &x, int &y) {
+            int lt2 = g / CPT, ch = g % CPT, mt, nt;
+            tm.get(blockIdx.x + lt2 * gridDim.x, mt, nt);
+            x = cx0 + mt * BM;
+            y = cy0 + nt * BN + ch * 32;
+        };
+        auto issue_load = [&](int g) {
+            int x, y;
+            coords(g, x, y);
+            const int b = g % CF::NCB;
+            mbar_expect_tx(&cbar[b], CF::CB_BYTES);
+            tma_load_2d(cbuf + (size_t)b * (CF::CB_BYTES / 4), &tmC, x, y, &cbar[b]);
+        };
+        if (leader)
+            for (int g = 0; g < CF::LOOK && g < total; g++) issue_load(g);
+        const int row = q * 32 + lane;
+        // Only the leader waits on mbarriers; it publishes each outcome in dec[] (two parity slots) before a
+        // named barrier of the four epilogue warps, so all of them take the same branch (no divergent exit).
+        volatile int *dec = (volatile int *)(abort_flag + 1);
+        int dc = 0;
+        auto agree = [&](bool leader_ok) -> bool {
+            if (leader) dec[dc & 1] = leader_ok ? 1 : 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            bool r = dec[dc & 1] != 0;
+            dc++;
+            return r;
+        };
         int lt = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, lt++) {
             const int b = lt & 1;
             const uint32_t tph = (lt >> 1) & 1;
-            if (!mbar_wait(&tfull[b], tph, abort_flag, gflags)) break;
+            bool ok = true;
+            if (leader) ok = mbar_wait(&tfull[b], tph, abort_flag, gflags);
+            if (!agree(ok)) break;
             tc_fence_after();
-            int mt, nt;
-            tm.get(t, mt, nt);
-            const int row = mt * BM + q * 32 + lane;
-            const bool rok = row < M;
-            float *cp = Cm + row;
-            const int col_base = nt * BN;
+            bool alive = true;
 #pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ch++) {
+            for (int ch = 0; ch < CPT; ch++) {
+                const int g = lt * CPT + ch;
+                const int cb = g % CF::NCB;
+                ok = true;
+                if (leader) {
+                    if (g + CF::LOOK < total) {
+                        // the buffer's previous chunk (g + LOOK - NCB) must have been read out by its store
+                        bulk_wait_read<CF::NCB - CF::LOOK - 1>();
+                        issue_load(g + CF::LOOK);
+                    }
+                    ok = mbar_wait(&cbar[cb], (uint32_t)((g / CF::NCB) & 1), abort_flag, gflags);
+                }
                 float v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + ch * 32), v);
-                const int c0 = col_base + ch * 32;
-                if (rok) {
-                    float old[32];
+                if (!agree(ok)) {
+                    alive = false;
+                    break;
+                }
+                float *buf = cbuf + (size_t)cb * (CF::CB_BYTES / 4);
 #pragma unroll
-                    for (int j = 0; j < 32; j++)
-                        if (c0 + j < N) old[j] = cp[(int64_t)(c0 + j) * ldc];
-#pragma unroll
-                    for (int j = 0; j < 32; j++)
-                        if (c0 + j < N) cp[(int64_t)(c0 + j) * ldc] = old[j] - v[j];
+                for (int j = 0; j < 32; j++) buf[j * BM + row] -= v[j];
+                fence_proxy_async_smem();
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (leader) {
+                    int x, y;
+                    coords(g, x, y);
+                    tma_store_2d(&tmC, buf, x, y);
+                    bulk_commit();
                 }
             }
+            if (!alive) break;
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
         }
+        if (leader) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();
@@ -422,9 +490,25 @@ bool make_map(CUtensorMap *map, const float *gptr, uint64_t inner, uint64_t oute
     return r == CUDA_SUCCESS;
 }
 
+// 2D FP32 tensor map for the C chunks: inner extent `inner` (real rows), `outer` columns with pitch
+// pitch_floats, box 128 rows x 32 columns, no swizzle (rows contiguous in shared memory).
+bool make_map_c(CUtensorMap *map, const float *gptr, uint64_t inner, uint64_t outer, uint64_t pitch_floats) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {pitch_floats * 4};
+    cuuint32_t box[2] = {(cuuint32_t)BM, 32};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)gptr, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 template <int BN, int SPLIT>
 gdm_status launch_update(gdm_ctx *ctx, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
-                         const CUtensorMap &b1, float *C, int64_t ldc, int M, int N, int K, int bx0, int by0) {
+                         const CUtensorMap &b1, const CUtensorMap &cm, int cx0, int cy0, int M, int N, int K, int bx0,
+                         int by0) {
     using CF = Cfg<BN, SPLIT>;
     static bool attr = false;
     if (!attr) {
@@ -434,8 +518,8 @@ gdm_status launch_update(gdm_ctx *ctx, const CUtensorMap &a0, const CUtensorMap 
     }
     int ntiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     int grid = ntiles < ctx->sm_count ? ntiles : ctx->sm_count;
-    k_tc_update<BN, SPLIT><<<grid, NTHREADS, CF::SMEM, ctx->stream>>>(a0, a1, b0, b1, C, ldc, M, N, K, bx0, by0,
-                                                                       ctx->dflags);
+    k_tc_update<BN, SPLIT><<<grid, NTHREADS, CF::SMEM, ctx->stream>>>(a0, a1, b0, b1, cm, cx0, cy0, M, N, K, bx0,
+                                                                       by0, ctx->dflags);
     GDM_LAUNCHED(ctx, "tc_update");
     return GDM_OK;
 }
@@ -478,10 +562,9 @@ gdm_status gdm_tc_trailing_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, i
         k_prep_lx<1><<<pg, 256, 0, ctx->stream>>>(L, lda, (int)m, (int)nb, Lx, nullptr);
         GDM_LAUNCHED(ctx, "prep_lx");
     }
-    CUtensorMap ta0, ta1, tb0, tb1;
-    float *C = (float *)(A + be * lda + be);
-    const int64_t ldc = 2 * lda;
-    bool ok = make_map(&ta0, Lx, K, M, K, BM);
+    CUtensorMap ta0, ta1, tb0, tb1, tc;
+    bool ok = make_map(&ta0, Lx, K, M, K, BM) &&
+              make_map_c(&tc, (const float *)A, (uint64_t)2 * n, (uint64_t)n, (uint64_t)2 * lda);
     int slot;
     double fl = 8.0 * (double)m * (double)m * (double)nb;
     double by = 16.0 * (double)m * m + 4.0 * ((double)M * K + (double)N * K) * (split == 3 ? 2 : 1);
@@ -490,13 +573,14 @@ gdm_status gdm_tc_trailing_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, i
              make_map(&tb1, Ulo, K, N, K, 128);
         if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         GDM_TRY(gdm_prof_begin(ctx, &slot));
-        GDM_TRY(launch_update<128, 3>(ctx, ta0, ta1, tb0, tb1, C, ldc, M, N, K, 0, 0));
+        GDM_TRY(launch_update<128, 3>(ctx, ta0, ta1, tb0, tb1, tc, (int)(2 * be), (int)be, M, N, K, 0, 0));
     } else {
         // U12 straight from the matrix: real rows [2 b0, 2 b0 + K) of columns [be, n)
         ok = ok && make_map(&tb0, (const float *)A, (uint64_t)2 * lda, (uint64_t)n, (uint64_t)2 * lda, 256);
         if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         GDM_TRY(gdm_prof_begin(ctx, &slot));
-        GDM_TRY(launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, C, ldc, M, N, K, (int)(2 * b0), (int)be));
+        GDM_TRY(launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, tc, (int)(2 * be), (int)be, M, N, K, (int)(2 * b0),
+                                      (int)be));
     }
     GDM_TRY(gdm_prof_end(ctx, slot, fl, by));
     return GDM_OK;
