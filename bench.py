@@ -229,6 +229,11 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
 
+    # one extra (untimed) step with per-phase device-time accounting
+    ctx.phases(True)
+    step()
+    phases = {k: round(v, 2) for k, v in ctx.phases(False).items()}
+
     # end to end through the public API: host inputs -> device, solve, fields back to the host
     h_pos = torch.tensor(s.pos).pin_memory()
     h_eps = torch.tensor(s.eps).pin_memory()
@@ -284,7 +289,7 @@ def main():
             "accuracy": {"refine_iters": it["iterations"], "rel_correction": it["rel_correction"],
                          "rel_residual_fp64": it["rel_residual"], "factor_ms": it["factor_ms"],
                          "refine_ms": it["refine_ms"]},
-            "roofline": roofline, "gpu_launches": launches,
+            "roofline": roofline, "gpu_launches": launches, "phases_ms": phases,
             "e2e": {"value": e2e_s / units, "unit": "s", "h2d_bytes_per_step": int(h_pos.numel() * 8 + h_eps.numel() * 16),
                     "d2h_bytes_per_step": int(h_F.numel() * 16)},
             "clocks": clocks, "cpu_baseline": cpu_base}

@@ -228,6 +228,13 @@ gdm_status gdm_profile_enable(gdm_ctx *ctx, int enable);
  * Synchronises the context stream. Any output pointer may be NULL. */
 gdm_status gdm_profile_read(gdm_ctx *ctx, int64_t *launches, double *total_ms, double *flops, double *bytes);
 
+/* Phase accounting: with enable = 1 subsequent calls record device time per phase of the solve
+ * (CUDA events around each phase; adds host overhead, for diagnostics only). ms_out (host, 9 doubles,
+ * nullable) receives the times recorded since the previous call, in the order: panel factorisation,
+ * row interchanges, small triangular solves, in-block updates, U12 updates, trailing update,
+ * correction solves, refinement residual, other. Synchronises the stream when ms_out != NULL. */
+gdm_status gdm_profile_phases(gdm_ctx *ctx, int enable, double *ms_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,7 +82,10 @@ _SIGS = {
     "gdm_nearfield_backward": ([P, C.POINTER(Problem), P, P, I64, C.c_int, PD, PD, P, P, P, P, P], C.c_int),
     "gdm_profile_enable": ([P, C.c_int], C.c_int),
     "gdm_profile_read": ([P, C.POINTER(I64), PD, PD, PD], C.c_int),
+    "gdm_profile_phases": ([P, C.c_int, PD], C.c_int),
 }
+PHASES = ["panel", "laswp", "trsm_small", "inblock_update", "u12_update", "trailing_update", "correction_solves",
+          "residual", "other"]
 
 
 def lib():
@@ -158,6 +161,12 @@ class Context:
     def profile(self, enable=True):
         """Start (or stop) CUDA-event timing of the LU trailing-update kernel launches."""
         self._check(lib().gdm_profile_enable(self.h, 1 if enable else 0), "gdm_profile_enable")
+
+    def phases(self, enable=True):
+        """Read (and reset) the per-phase device times, then enable/disable phase accounting."""
+        out = (C.c_double * len(PHASES))()
+        self._check(lib().gdm_profile_phases(self.h, 1 if enable else 0, out), "gdm_profile_phases")
+        return {k: out[i] for i, k in enumerate(PHASES)}
 
     def profile_read(self):
         n = I64(0)

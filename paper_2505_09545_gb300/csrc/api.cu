@@ -93,7 +93,45 @@ gdm_status gdm_prof_end(gdm_ctx *ctx, int slot, double flops, double bytes) {
     return GDM_OK;
 }
 
+gdm_status gdm_phase_begin(gdm_ctx *ctx, int phase) {
+    if (!ctx->ph_on || ctx->ph_n >= GDM_PH_MAX) return GDM_OK;
+    if (!ctx->ph_ev) {
+        ctx->ph_ev = new (std::nothrow) cudaEvent_t[2 * GDM_PH_MAX];
+        ctx->ph_id = new (std::nothrow) int[GDM_PH_MAX];
+        if (!ctx->ph_ev || !ctx->ph_id) return gdm_fail(ctx, GDM_ERR_OOM, "phase events");
+        for (int i = 0; i < 2 * GDM_PH_MAX; i++) GDM_CUDA_TRY(ctx, cudaEventCreate(&ctx->ph_ev[i]));
+    }
+    ctx->ph_id[ctx->ph_n] = phase;
+    GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ph_ev[2 * ctx->ph_n], ctx->stream));
+    return GDM_OK;
+}
+
+gdm_status gdm_phase_end(gdm_ctx *ctx, int phase) {
+    if (!ctx->ph_on || ctx->ph_n >= GDM_PH_MAX) return GDM_OK;
+    (void)phase;
+    GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ph_ev[2 * ctx->ph_n + 1], ctx->stream));
+    ctx->ph_n++;
+    return GDM_OK;
+}
+
 extern "C" {
+
+gdm_status gdm_profile_phases(gdm_ctx *ctx, int enable, double *ms_out) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    if (ms_out) {
+        GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+        GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int p = 0; p < GDM_NPHASES; p++) ms_out[p] = 0.0;
+        for (int i = 0; i < ctx->ph_n; i++) {
+            float t = 0.f;
+            GDM_CUDA_TRY(ctx, cudaEventElapsedTime(&t, ctx->ph_ev[2 * i], ctx->ph_ev[2 * i + 1]));
+            ms_out[ctx->ph_id[i]] += t;
+        }
+    }
+    ctx->ph_on = enable ? 1 : 0;
+    ctx->ph_n = 0;
+    return GDM_OK;
+}
 
 gdm_status gdm_profile_enable(gdm_ctx *ctx, int enable) {
     if (!ctx) return GDM_ERR_INVALID_ARG;
@@ -185,6 +223,11 @@ gdm_status gdm_destroy(gdm_ctx *ctx) {
     if (ctx->prof_ev) {
         for (int i = 0; i < 2 * GDM_PROF_MAX; i++) cudaEventDestroy(ctx->prof_ev[i]);
         delete[] ctx->prof_ev;
+    }
+    if (ctx->ph_ev) {
+        for (int i = 0; i < 2 * GDM_PH_MAX; i++) cudaEventDestroy(ctx->ph_ev[i]);
+        delete[] ctx->ph_ev;
+        delete[] ctx->ph_id;
     }
     delete ctx;
     return GDM_OK;

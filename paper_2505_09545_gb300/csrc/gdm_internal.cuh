@@ -34,8 +34,20 @@ struct gdm_ctx {
     int prof_n = 0;
     cudaEvent_t *prof_ev = nullptr;  // 2 * GDM_PROF_MAX events, created lazily
     double prof_flops = 0.0, prof_bytes = 0.0;
+    // phase accounting
+    int ph_on = 0;
+    int ph_n = 0;
+    cudaEvent_t *ph_ev = nullptr;  // 2 * GDM_PH_MAX events
+    int *ph_id = nullptr;
 };
+#define GDM_PH_MAX 32768
 #define GDM_PROF_MAX 4096
+// phase accounting (diagnostics): device time per phase, summed over bracketed regions
+enum { GDM_PH_PANEL = 0, GDM_PH_LASWP, GDM_PH_TRSM, GDM_PH_INBLOCK, GDM_PH_U12, GDM_PH_TRAILING, GDM_PH_TRSV,
+       GDM_PH_RESIDUAL, GDM_PH_OTHER, GDM_NPHASES };
+struct gdm_phase_rec;
+gdm_status gdm_phase_begin(gdm_ctx *ctx, int phase);
+gdm_status gdm_phase_end(gdm_ctx *ctx, int phase);
 // bracket one launch of the profiled kernel (no-ops unless profiling is on)
 gdm_status gdm_prof_begin(gdm_ctx *ctx, int *slot);
 gdm_status gdm_prof_end(gdm_ctx *ctx, int slot, double flops, double bytes);
@@ -186,7 +198,8 @@ gdm_status gdm_trsv_persistent(gdm_ctx *ctx, gdm_precision prec, const void *A, 
                                const int32_t *ipiv, void *B, int64_t ldb, int n_rhs, int conj_trans, int *sync_buf,
                                const void *dinv);
 size_t gdm_trsv_inv_bytes(int64_t n);
-gdm_status gdm_trsv_prepare(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda, void *dinv);
+gdm_status gdm_trsv_prepare(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda,
+                            const int32_t *ipiv, void *dinv);
 int gdm_lu_block(gdm_precision prec);
 // refine.cu
 gdm_status gdm_refined_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,

@@ -10,11 +10,13 @@
 //       swap the same rows in the other columns of the block; triangular solve + GEMM update of the
 //         block's remaining columns;
 //     swap the block's pivot rows in the trailing columns, U12 = L11^{-1} A12, A22 -= A21 U12.
-// Left-of-block columns are never swapped: the forward solve applies each block's row swaps to the
-// right-hand side just before using that block's columns of L, which is equivalent.
+// Columns to the left of a panel are never swapped: L is kept in the row order of the step that produced
+// it, and the forward solve applies each panel's row swaps to the right-hand side just before using that
+// panel's columns of L (the product form y = L_S^{-1} P_S ... L_1^{-1} P_1 b at panel granularity).
 // For the FP32 precisions the trailing update A22 -= A21 U12 runs on the tcgen05 tensor cores
 // (lu_tc.cu); everything else uses the SIMT kernels of this file.
 #include <cooperative_groups.h>
+#include <stdlib.h>
 
 #include "gdm_internal.cuh"
 
@@ -25,6 +27,8 @@
 gdm_status gdm_tc_trailing_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t b0,
                                   int64_t nb, void *ws, size_t ws_bytes);
 size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec);
+gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t r0, int64_t c0,
+                         int64_t k0, int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof);
 int gdm_lu_block(gdm_precision prec);
 
 // ------------------------------------------------------------------ bounded grid barrier
@@ -235,8 +239,8 @@ template <class C>
 __global__ void __launch_bounds__(256) k_panel_local(C *__restrict__ A, int64_t lda, int64_t n, int64_t c0, int w,
                                                      int32_t *__restrict__ ipiv, unsigned *growth, int *flags) {
     typedef decltype(C().x) T;
-    __shared__ C D[NBP][NBP + 1];
-    __shared__ int s_piv;
+    __shared__ C D[NBP][NBP + 1];   // diagonal block, factored in place (L strictly below, U on and above)
+    __shared__ C Ui[NBP][NBP + 1];  // U^{-1}
     for (int e = threadIdx.x; e < NBP * NBP; e += blockDim.x) {
         int r = e % NBP, c = e / NBP;
         C v;
@@ -246,89 +250,84 @@ __global__ void __launch_bounds__(256) k_panel_local(C *__restrict__ A, int64_t 
         D[r][c] = v;
     }
     __syncthreads();
-    for (int t = 0; t < w; t++) {
-        if (threadIdx.x < 32) {
-            int r = threadIdx.x;
-            double v = (r >= t && r < w) ? (double)cabs1(D[r][t]) : -1.0;
-            int rr = r;
+    if (threadIdx.x < 32) {
+        // one warp: partial pivoting among the block's rows; lane = row for the search, column for the swap
+        const int lane = threadIdx.x;
+        for (int t = 0; t < w; t++) {
+            double v = (lane >= t && lane < w) ? (double)cabs1(D[lane][t]) : -1.0;
+            int idx = lane;
             for (int o = 16; o > 0; o >>= 1) {
                 double ov = __shfl_down_sync(0xffffffffu, v, o);
-                int orr = __shfl_down_sync(0xffffffffu, rr, o);
-                if (ov > v || (ov == v && orr < rr)) {
+                int oi = __shfl_down_sync(0xffffffffu, idx, o);
+                if (ov > v || (ov == v && oi < idx)) {
                     v = ov;
-                    rr = orr;
+                    idx = oi;
                 }
             }
-            if (threadIdx.x == 0) {
-                s_piv = rr;
-                if (blockIdx.x == 0) {
-                    ipiv[c0 + t] = (int32_t)(c0 + rr);
-                    if (!(v > 0.0)) gdm_dev_error(flags, GDM_ERR_SINGULAR, (int)(c0 + t));
-                }
+            const int p = __shfl_sync(0xffffffffu, idx, 0);
+            const double pv = __shfl_sync(0xffffffffu, v, 0);
+            if (blockIdx.x == 0 && lane == 0) {
+                ipiv[c0 + t] = (int32_t)(c0 + p);
+                if (!(pv > 0.0)) gdm_dev_error(flags, GDM_ERR_SINGULAR, (int)(c0 + t));
+            }
+            if (p != t && lane < w) {
+                C a = D[t][lane];
+                D[t][lane] = D[p][lane];
+                D[p][lane] = a;
+            }
+            __syncwarp();
+            C piv = D[t][t];
+            C inv;
+            if (cabs1(piv) > 0) inv = crecip(piv);
+            else {
+                inv.x = 0;
+                inv.y = 0;
+            }
+            if (lane > t && lane < w) {
+                C l = cmul(D[lane][t], inv);
+                D[lane][t] = l;
+                for (int c = t + 1; c < w; c++) cfms(D[lane][c], l, D[t][c]);
+            }
+            __syncwarp();
+        }
+        // U^{-1}, one column per lane (back substitution)
+        if (lane < w) {
+            for (int r = w - 1; r >= 0; r--) {
+                C sacc;
+                sacc.x = (r == lane) ? 1 : 0;
+                sacc.y = 0;
+                for (int j = r + 1; j < w; j++) cfms(sacc, D[r][j], Ui[j][lane]);
+                C d = D[r][r];
+                Ui[r][lane] = cabs1(d) > 0 ? cmul(sacc, crecip(d)) : sacc;
             }
         }
-        __syncthreads();
-        const int p = s_piv;
-        if (p != t && threadIdx.x < w) {
-            C a = D[t][threadIdx.x];
-            D[t][threadIdx.x] = D[p][threadIdx.x];
-            D[p][threadIdx.x] = a;
-        }
-        __syncthreads();
-        C pv = D[t][t];
-        C inv;
-        if (cabs1(pv) > 0) inv = crecip(pv);
-        else {
-            inv.x = 0;
-            inv.y = 0;
-        }
-        // rows t+1..w-1: multiplier, then rank-1 update of columns t+1..w-1
-        const int nr = w - t - 1;
-        for (int e = threadIdx.x; e < nr * (nr + 1); e += blockDim.x) {
-            int r = t + 1 + e / (nr + 1), c = t + e % (nr + 1);  // c == t: multiplier column
-            if (c == t) continue;
-            C l = cmul(D[r][t], inv);
-            cfms(D[r][c], l, D[t][c]);
-        }
-        __syncthreads();
-        for (int r = t + 1 + threadIdx.x; r < w; r += blockDim.x) D[r][t] = cmul(D[r][t], inv);
-        __syncthreads();
     }
+    __syncthreads();
     if (blockIdx.x == 0)
         for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
             int r = e % w, c = e / w;
             A[(c0 + c) * lda + c0 + r] = D[r][c];
         }
-    // rows below the diagonal block: x <- x U^{-1}, one thread per row
+    // rows below the diagonal block: L21 = A21 U^{-1}; certificate from l_k U_kk (the updated entry that
+    // partial pivoting would have compared with the pivot U_kk)
     float worst = 0.f;
     for (int64_t r = c0 + w + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
         C x[NBP];
 #pragma unroll
-        for (int k = 0; k < NBP; k++)
-            if (k < w) x[k] = A[(c0 + k) * lda + r];
+        for (int j = 0; j < NBP; j++)
+            if (j < w) x[j] = A[(c0 + j) * lda + r];
+        for (int k = 0; k < w; k++) {
+            C l;
+            l.x = 0;
+            l.y = 0;
 #pragma unroll
-        for (int k = 0; k < NBP; k++) {
-            if (k < w) {
-                C num = x[k];
-#pragma unroll
-                for (int j = 0; j < NBP; j++)
-                    if (j < k) cfms(num, x[j], D[j][k]);
-                T pa = cabs1(D[k][k]);
-                T na = cabs1(num);
-                if (pa > 0) {
-                    float ratio = (float)(na / pa);
-                    worst = fmaxf(worst, ratio);
-                    x[k] = cmul(num, crecip(D[k][k]));
-                } else {
-                    x[k].x = 0;
-                    x[k].y = 0;
-                }
-            }
+            for (int j = 0; j < NBP; j++)
+                if (j <= k) cfma(l, x[j], Ui[j][k]);
+            T pa = cabs1(D[k][k]);
+            if (pa > 0) worst = fmaxf(worst, (float)(cabs1(cmul(l, D[k][k])) / pa));
+            A[(c0 + k) * lda + r] = l;
         }
-#pragma unroll
-        for (int k = 0; k < NBP; k++)
-            if (k < w) A[(c0 + k) * lda + r] = x[k];
     }
     for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_down_sync(0xffffffffu, worst, o));
     if ((threadIdx.x & 31) == 0 && worst > 0.f) atomicMax(growth, __float_as_uint(worst));
@@ -339,7 +338,7 @@ __global__ void __launch_bounds__(256) k_panel_local(C *__restrict__ A, int64_t 
 template <class C>
 __global__ void k_laswp(C *__restrict__ A, int64_t lda, int64_t cb, int64_t ce, const int32_t *__restrict__ ipiv,
                         int64_t k_begin, int64_t k_end) {
-    __shared__ int32_t sp[256];
+    __shared__ int32_t sp[1024];
     int64_t col = cb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int nk = (int)(k_end - k_begin);
     for (int t = threadIdx.x; t < nk; t += blockDim.x) sp[t] = ipiv[k_begin + t];
@@ -519,7 +518,7 @@ template <class C>
 static gdm_status laswp(gdm_ctx *ctx, C *A, int64_t lda, int64_t cb, int64_t ce, const int32_t *ipiv, int64_t kb,
                         int64_t ke) {
     if (ce <= cb || ke <= kb) return GDM_OK;
-    if (ke - kb > 256) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "laswp block too large");
+    if (ke - kb > 1024) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "laswp block too large");
     unsigned nb = (unsigned)((ce - cb + 127) / 128);
     k_laswp<C><<<nb, 128, 0, ctx->stream>>>(A, lda, cb, ce, ipiv, kb, ke);
     GDM_LAUNCHED(ctx, "laswp");
@@ -536,7 +535,26 @@ static gdm_status trsm_small(gdm_ctx *ctx, C *A, int64_t lda, int64_t c0, int w,
     return GDM_OK;
 }
 
-int gdm_lu_block(gdm_precision prec) { return prec == GDM_FP64 ? 128 : 256; }
+int gdm_lu_block(gdm_precision prec) {
+    if (prec == GDM_FP64) return 128;
+    const char *e = getenv("GDM_LU_NB");
+    int nb = e ? atoi(e) : 512;
+    if (nb < 64 || nb > 1024 || nb % 32) nb = 512;
+    return nb;
+}
+
+// sub-block update C -= L U inside the matrix: tensor cores for the FP32 precisions, SIMT otherwise
+template <class C>
+static gdm_status update(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t lda, int64_t n, int64_t r0, int64_t c0,
+                         int64_t k0, int64_t Mc, int64_t Nc, int64_t Kc, void *tcws, size_t tcbytes) {
+    if (Mc <= 0 || Nc <= 0 || Kc <= 0) return GDM_OK;
+    gdm_status s = GDM_ERR_UNSUPPORTED;
+    if (sizeof(C) == 8 && tcws)
+        s = gdm_tc_update(ctx, prec, (float2 *)A, lda, n, r0, c0, k0, Mc, Nc, Kc, tcws, tcbytes, 0);
+    if (s == GDM_ERR_UNSUPPORTED)
+        s = gemm_sub<C>(ctx, A + c0 * lda + r0, lda, A + k0 * lda + r0, lda, A + c0 * lda + k0, lda, Mc, Nc, Kc);
+    return s;
+}
 
 template <class C>
 static gdm_status panel_local(gdm_ctx *ctx, C *A, int64_t lda, int64_t n, int64_t c0, int w, int32_t *ipiv,
@@ -553,7 +571,8 @@ static gdm_status panel_local(gdm_ctx *ctx, C *A, int64_t lda, int64_t n, int64_
 template <class C>
 static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n, int64_t lda, int32_t *ipiv,
                               int global_pivot, unsigned *growth) {
-    const int NB = gdm_lu_block(prec);
+    // whole-column pivoting moves rows below the block, so it factors one 32-column panel per block
+    const int NB = global_pivot ? NBP : gdm_lu_block(prec);
     int pmax = ctx->sm_count;
     // scratch: panel candidates + tensor-core operand buffers
     size_t pbytes = ScratchCarver::round(2 * pmax * sizeof(double)) + ScratchCarver::round(2 * pmax * sizeof(int64_t)) +
@@ -574,27 +593,41 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
         int64_t be = b0 + nb;
         for (int64_t c0 = b0; c0 < be; c0 += NBP) {
             int w = (int)(be - c0 < NBP ? be - c0 : NBP);
+            GDM_TRY(gdm_phase_begin(ctx, GDM_PH_PANEL));
             if (global_pivot) GDM_TRY(panel_factor<C>(ctx, A, lda, n, c0, w, ipiv, ps, pmax));
             else GDM_TRY(panel_local<C>(ctx, A, lda, n, c0, w, ipiv, growth));
-            GDM_TRY(laswp<C>(ctx, A, lda, b0, c0, ipiv, c0, c0 + w));
+            GDM_TRY(gdm_phase_end(ctx, GDM_PH_PANEL));
+            GDM_TRY(gdm_phase_begin(ctx, GDM_PH_LASWP));
             GDM_TRY(laswp<C>(ctx, A, lda, c0 + w, be, ipiv, c0, c0 + w));
+            GDM_TRY(gdm_phase_end(ctx, GDM_PH_LASWP));
             if (c0 + w < be) {
+                GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRSM));
                 GDM_TRY(trsm_small<C>(ctx, A, lda, c0, w, c0 + w, be));
-                GDM_TRY(gemm_sub<C>(ctx, A + (c0 + w) * lda + c0 + w, lda, A + c0 * lda + c0 + w, lda,
-                                    A + (c0 + w) * lda + c0, lda, n - c0 - w, be - c0 - w, w));
+                GDM_TRY(gdm_phase_end(ctx, GDM_PH_TRSM));
+                GDM_TRY(gdm_phase_begin(ctx, GDM_PH_INBLOCK));
+                GDM_TRY(update<C>(ctx, prec, A, lda, n, c0 + w, c0 + w, c0, n - c0 - w, be - c0 - w, w, tcws, tcbytes));
+                GDM_TRY(gdm_phase_end(ctx, GDM_PH_INBLOCK));
             }
         }
         if (be < n) {
-            GDM_TRY(laswp<C>(ctx, A, lda, be, n, ipiv, b0, be));
-            // U12 = L11^{-1} A12, blocked by panels
+            // U12 = L11^{-1} A12 panel by panel; each panel's interchanges reach the trailing columns just
+            // before its triangular solve (L rows of later panels are still in their pre-interchange order)
             for (int64_t c0 = b0; c0 < be; c0 += NBP) {
                 int w = (int)(be - c0 < NBP ? be - c0 : NBP);
+                GDM_TRY(gdm_phase_begin(ctx, GDM_PH_LASWP));
+                GDM_TRY(laswp<C>(ctx, A, lda, be, n, ipiv, c0, c0 + w));
+                GDM_TRY(gdm_phase_end(ctx, GDM_PH_LASWP));
+                GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRSM));
                 GDM_TRY(trsm_small<C>(ctx, A, lda, c0, w, be, n));
-                if (c0 + w < be)
-                    GDM_TRY(gemm_sub<C>(ctx, A + be * lda + c0 + w, lda, A + c0 * lda + c0 + w, lda, A + be * lda + c0,
-                                        lda, be - c0 - w, n - be, w));
+                GDM_TRY(gdm_phase_end(ctx, GDM_PH_TRSM));
+                if (c0 + w < be) {
+                    GDM_TRY(gdm_phase_begin(ctx, GDM_PH_U12));
+                    GDM_TRY(update<C>(ctx, prec, A, lda, n, c0 + w, be, c0, be - c0 - w, n - be, w, tcws, tcbytes));
+                    GDM_TRY(gdm_phase_end(ctx, GDM_PH_U12));
+                }
             }
             // A22 -= A21 U12
+            GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRAILING));
             gdm_status s = GDM_ERR_UNSUPPORTED;
             if (sizeof(C) == 8 && tcws)
                 s = gdm_tc_trailing_update(ctx, prec, (float2 *)A, lda, n, b0, nb, tcws, tcbytes);
@@ -608,6 +641,7 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
                                      sizeof(C) * (2.0 * mm * mm + 2.0 * mm * nb)));
             }
             GDM_TRY(s);
+            GDM_TRY(gdm_phase_end(ctx, GDM_PH_TRAILING));
         }
     }
     return GDM_OK;
@@ -752,9 +786,10 @@ static gdm_status lu_solve_t(gdm_ctx *ctx, gdm_precision prec, const C *A, int64
     const int NB = gdm_lu_block(prec);
     const int wpb = 4;
     unsigned nbq = (unsigned)((n_rhs + wpb - 1) / wpb);
+    (void)NB;
     if (!conj_trans) {
-        for (int64_t b0 = 0; b0 < n; b0 += NB) {
-            int64_t be = b0 + NB < n ? b0 + NB : n;
+        for (int64_t b0 = 0; b0 < n; b0 += NBP) {
+            int64_t be = b0 + NBP < n ? b0 + NBP : n;
             k_laswp_rhs<C><<<(n_rhs + 31) / 32, 32, 0, ctx->stream>>>(B, ldb, n_rhs, ipiv, b0, be, 0);
             GDM_LAUNCHED(ctx, "laswp_rhs");
             for (int64_t c0 = b0; c0 < be; c0 += NBP) {
@@ -790,9 +825,9 @@ static gdm_status lu_solve_t(gdm_ctx *ctx, gdm_precision prec, const C *A, int64
             k_trsv_diag<C><<<nbq, wpb * 32, 0, ctx->stream>>>(A, lda, c0, w, B, ldb, n_rhs, 1, 1);
             GDM_LAUNCHED(ctx, "trsv_diag");
         }
-        int64_t last_b0 = ((n - 1) / NB) * NB;
-        for (int64_t b0 = last_b0; b0 >= 0; b0 -= NB) {
-            int64_t be = b0 + NB < n ? b0 + NB : n;
+        int64_t last_b0 = ((n - 1) / NBP) * NBP;
+        for (int64_t b0 = last_b0; b0 >= 0; b0 -= NBP) {
+            int64_t be = b0 + NBP < n ? b0 + NBP : n;
             int64_t last_c0 = b0 + ((be - 1 - b0) / NBP) * NBP;
             for (int64_t c0 = last_c0; c0 >= b0; c0 -= NBP) {
                 int w = (int)(be - c0 < NBP ? be - c0 : NBP);

@@ -533,55 +533,66 @@ size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec) {
     return prec == GDM_FP32 ? 2 * lx + 2 * u + 4096 : lx + 4096;
 }
 
-// A22 -= A21 U12 for the block [b0, b0+nb) of the complex64 matrix A (n x n, lda).
-gdm_status gdm_tc_trailing_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t b0,
-                                  int64_t nb, void *ws, size_t ws_bytes) {
+// General update of a sub-block of the complex64 matrix A (n x n, lda):
+//   A[r0 : r0+Mc, c0 : c0+Nc] -= A[r0 : r0+Mc, k0 : k0+Kc] * A[k0 : k0+Kc, c0 : c0+Nc].
+// The C chunks are clipped to the sub-block through the tensor-map extents (rows < r0+Mc, columns
+// < c0+Nc), so columns and rows outside it are never written. prof = 1 records the launch as the
+// factorisation's dominant kernel (gdm_profile_enable).
+gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t r0, int64_t c0,
+                         int64_t k0, int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof) {
     if (prec == GDM_FP64) return GDM_ERR_UNSUPPORTED;
-    const int64_t be = b0 + nb;
-    const int64_t m = n - be;
-    if (m < 64 || getenv("GDM_TC_DISABLE")) return GDM_ERR_UNSUPPORTED;
-    if (((uintptr_t)A & 15) || (lda & 1)) return GDM_ERR_UNSUPPORTED;
+    if (Mc <= 0 || Nc <= 0 || Kc <= 0) return GDM_OK;
+    if (getenv("GDM_TC_DISABLE")) return GDM_ERR_UNSUPPORTED;
+    if (((uintptr_t)A & 15) || (lda & 1) || (r0 & 1) || (k0 & 1)) return GDM_ERR_UNSUPPORTED;
     const int split = (prec == GDM_FP32) ? 3 : 1;
-    const int M = (int)(2 * m), N = (int)m, K = (int)(2 * nb);
+    const int M = (int)(2 * Mc), N = (int)Nc, K = (int)(2 * Kc);
     ScratchCarver sc(ws);
     float *Lx = sc.take<float>((size_t)M * K);
     float *Llo = split == 3 ? sc.take<float>((size_t)M * K) : nullptr;
     float *Uhi = split == 3 ? sc.take<float>((size_t)N * K) : nullptr;
     float *Ulo = split == 3 ? sc.take<float>((size_t)N * K) : nullptr;
     if (sc.off > ws_bytes) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "tensor-core workspace too small");
-    const float2 *L = A + b0 * lda + be;
-    dim3 pg((unsigned)((m + 31) / 32), (unsigned)((nb + 31) / 32));
+    const float2 *L = A + k0 * lda + r0;
+    dim3 pg((unsigned)((Mc + 31) / 32), (unsigned)((Kc + 31) / 32));
     if (split == 3) {
-        k_prep_lx<3><<<pg, 256, 0, ctx->stream>>>(L, lda, (int)m, (int)nb, Lx, Llo);
+        k_prep_lx<3><<<pg, 256, 0, ctx->stream>>>(L, lda, (int)Mc, (int)Kc, Lx, Llo);
         GDM_LAUNCHED(ctx, "prep_lx");
-        int64_t cnt = nb * m;
-        k_split_u<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(A + be * lda + b0, lda, (int)nb, (int)m, Uhi,
+        int64_t cnt = Kc * Nc;
+        k_split_u<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(A + c0 * lda + k0, lda, (int)Kc, (int)Nc, Uhi,
                                                                           Ulo);
         GDM_LAUNCHED(ctx, "split_u");
     } else {
-        k_prep_lx<1><<<pg, 256, 0, ctx->stream>>>(L, lda, (int)m, (int)nb, Lx, nullptr);
+        k_prep_lx<1><<<pg, 256, 0, ctx->stream>>>(L, lda, (int)Mc, (int)Kc, Lx, nullptr);
         GDM_LAUNCHED(ctx, "prep_lx");
     }
     CUtensorMap ta0, ta1, tb0, tb1, tc;
     bool ok = make_map(&ta0, Lx, K, M, K, BM) &&
-              make_map_c(&tc, (const float *)A, (uint64_t)2 * n, (uint64_t)n, (uint64_t)2 * lda);
-    int slot;
-    double fl = 8.0 * (double)m * (double)m * (double)nb;
-    double by = 16.0 * (double)m * m + 4.0 * ((double)M * K + (double)N * K) * (split == 3 ? 2 : 1);
+              make_map_c(&tc, (const float *)A, (uint64_t)(2 * (r0 + Mc)), (uint64_t)(c0 + Nc), (uint64_t)2 * lda);
+    int slot = -1;
+    double fl = 8.0 * (double)Mc * (double)Nc * (double)Kc;
+    double by = 16.0 * (double)Mc * Nc + 4.0 * ((double)M * K + (double)N * K) * (split == 3 ? 2 : 1);
     if (split == 3) {
         ok = ok && make_map(&ta1, Llo, K, M, K, BM) && make_map(&tb0, Uhi, K, N, K, 128) &&
              make_map(&tb1, Ulo, K, N, K, 128);
         if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-        GDM_TRY(gdm_prof_begin(ctx, &slot));
-        GDM_TRY(launch_update<128, 3>(ctx, ta0, ta1, tb0, tb1, tc, (int)(2 * be), (int)be, M, N, K, 0, 0));
+        if (prof) GDM_TRY(gdm_prof_begin(ctx, &slot));
+        GDM_TRY(launch_update<128, 3>(ctx, ta0, ta1, tb0, tb1, tc, (int)(2 * r0), (int)c0, M, N, K, 0, 0));
     } else {
-        // U12 straight from the matrix: real rows [2 b0, 2 b0 + K) of columns [be, n)
-        ok = ok && make_map(&tb0, (const float *)A, (uint64_t)2 * lda, (uint64_t)n, (uint64_t)2 * lda, 256);
+        // U straight from the matrix: real rows [2 k0, 2 k0 + K) of columns [c0, c0 + Nc) (zero beyond)
+        ok = ok && make_map(&tb0, (const float *)A, (uint64_t)2 * lda, (uint64_t)(c0 + Nc), (uint64_t)2 * lda, 256);
         if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-        GDM_TRY(gdm_prof_begin(ctx, &slot));
-        GDM_TRY(launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, tc, (int)(2 * be), (int)be, M, N, K, (int)(2 * b0),
-                                      (int)be));
+        if (prof) GDM_TRY(gdm_prof_begin(ctx, &slot));
+        GDM_TRY(launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * k0),
+                                      (int)c0));
     }
-    GDM_TRY(gdm_prof_end(ctx, slot, fl, by));
+    if (prof) GDM_TRY(gdm_prof_end(ctx, slot, fl, by));
     return GDM_OK;
+}
+
+// A22 -= A21 U12 for the block [b0, b0+nb) of the complex64 matrix A (n x n, lda).
+gdm_status gdm_tc_trailing_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t b0,
+                                  int64_t nb, void *ws, size_t ws_bytes) {
+    const int64_t be = b0 + nb, m = n - be;
+    if (m < 64) return GDM_ERR_UNSUPPORTED;
+    return gdm_tc_update(ctx, prec, A, lda, n, be, be, b0, m, m, nb, ws, ws_bytes, 1);
 }

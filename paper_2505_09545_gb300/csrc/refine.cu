@@ -117,11 +117,14 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     GDM_LAUNCHED(ctx, "norm2");
     // persistent block solves when every pivot stays inside its row block
     int local = 0;
-    if (!getenv("GDM_TRSV_LAUNCHES")) GDM_TRY(gdm_pivots_local(ctx, ipiv, ns, gdm_lu_block(prec), tsync, &local));
-    if (local) GDM_TRY(gdm_trsv_prepare(ctx, prec, A, ns, lda, dinv));
+    if (prec != GDM_FP64 && !getenv("GDM_TRSV_LAUNCHES")) GDM_TRY(gdm_pivots_local(ctx, ipiv, ns, 32, tsync, &local));
+    if (local) GDM_TRY(gdm_trsv_prepare(ctx, prec, A, ns, lda, ipiv, dinv));
     auto lu_solve = [&](void *w) -> gdm_status {
-        if (local) return gdm_trsv_persistent(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint, tsync, dinv);
-        return gdm_lu_solve(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint);
+        GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRSV));
+        gdm_status st = local ? gdm_trsv_persistent(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint, tsync, dinv)
+                              : gdm_lu_solve(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint);
+        GDM_TRY(st);
+        return gdm_phase_end(ctx, GDM_PH_TRSV);
     };
     if (info) GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     // initial solve
@@ -135,8 +138,10 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     if (!(opts->flags & GDM_SOLVE_NO_REFINE)) {
         for (it = 1; it <= opts->max_iter; it++) {
             GDM_CUDA_TRY(ctx, cudaMemsetAsync(dnorm, 0, sizeof(double) * 3 * n_rhs, ctx->stream));
+            GDM_TRY(gdm_phase_begin(ctx, GDM_PH_RESIDUAL));
             GDM_TRY(gdm_launch_residual_ws(ctx, p, rhs, X, n_rhs, adjoint, (double *)r, dnorm + 2 * n_rhs, Pbuf,
                                            partial, ffws, it == 1));
+            GDM_TRY(gdm_phase_end(ctx, GDM_PH_RESIDUAL));
             // scale the residual into a safe FP32 range before the low-precision solve
             k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(r, w, cnt, 1.0);
             GDM_LAUNCHED(ctx, "to_work");

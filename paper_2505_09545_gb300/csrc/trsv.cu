@@ -1,17 +1,28 @@
-// Persistent blocked triangular solves with the LU factors (right-hand sides of the refinement and
-// of the adjoint). One CTA per row block of NBS rows (NBS = the factorisation's outer block). A CTA
-// takes a ticket in dependency order, subtracts the contributions of the already solved blocks as
-// they are published (bounded waits on per-block flags; a CTA only ever waits for lower tickets, which
-// are already running), solves its diagonal block and publishes its rows.
-//
-//   mode 0  L   : y_j = L_jj^{-1} P_j (b_j - sum_{k<j} L_jk y_k)       (forward, pivots inside block j)
-//   mode 1  U   : y_j = U_jj^{-1} (b_j - sum_{k>j} U_jk y_k)           (backward)
-//   mode 2  U^H : y_j = U_jj^{-H} (b_j - sum_{k<j} U_kj^H y_k)         (forward)
-//   mode 3  L^H : y_j = P_j^T L_jj^{-H} (b_j - sum_{k>j} L_kj^H y_k)   (backward)
-//
-// Valid when every pivot stays inside its own row block (the factorisation with pivots searched inside
-// the diagonal blocks); otherwise the launch-per-panel solver of lu.cu is used.
+// Persistent blocked triangular solves with the FP32 LU factors (correction solves of the refinement and
+// the adjoint solve). The rows are cut into blocks of 128 rows. Once per factorisation, the solve operator
+// of every diagonal block is formed explicitly:
+//   M_j  = L_pK^{-1} P_pK ... L_p1^{-1} P_p1 restricted to block j  (its 32-row panels p1..pK, with their
+//          row interchanges, in the product form the factorisation produced),
+//   Ui_j = U_jj^{-1}.
+// A solve is then one kernel per triangle: one CTA per row block takes a ticket in dependency order,
+// subtracts the contributions of the already published blocks (bounded waits on per-block flags; a CTA
+// only waits for lower tickets, which are already running), applies its block operator and publishes its
+// rows:
+//   mode 0  L   : y_j = M_j (b_j - sum_{k<j} L_jk y_k)             (forward)
+//   mode 1  U   : y_j = Ui_j (b_j - sum_{k>j} U_jk y_k)            (backward)
+//   mode 2  U^H : y_j = Ui_j^H (b_j - sum_{k<j} U_kj^H y_k)        (forward)
+//   mode 3  L^H : y_j = M_j^H (b_j - sum_{k>j} L_kj^H y_k)         (backward)
+// The matrix blocks and operators reach shared memory through the TMA engine (a producer warp and a ring
+// of stages), which is what keeps one CTA's stream of 128 KB blocks at bandwidth: ordinary loads from
+// 256 threads capped it near 17 GB/s per SM. Valid when every pivot stays inside its own 32-row panel
+// (pivots searched inside the diagonal blocks); otherwise, and for the FP64 factors, the launch-per-panel
+// solver of lu.cu is used.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "gdm_internal.cuh"
+
+#define TRSV_NBS_F32 128
 
 namespace {
 
@@ -27,57 +38,148 @@ template <class C> __device__ __forceinline__ C cz() {
     v.y = 0;
     return v;
 }
-template <class C> __device__ __forceinline__ C conjc(C a) {
-    a.y = -a.y;
-    return a;
-}
 
-// thread 0 waits for flag[k] (or a global abort); returns false on abort/timeout
-__device__ bool wait_flag(volatile int *flag, volatile int *abort_flag, int *gflags) {
-    __shared__ int ok;
-    if (threadIdx.x == 0) {
-        ok = 1;
-        if (*flag == 0) {
-            uint64_t t0 = gtimer_t();
-            unsigned it = 0;
-            while (*flag == 0) {
-                __nanosleep(64);
-                if ((++it & 255) == 0) {
-                    if (*abort_flag) {
-                        ok = 0;
-                        break;
-                    }
-                    if (gtimer_t() - t0 > 2000000000ull) {
-                        gdm_dev_error(gflags, GDM_ERR_TIMEOUT, 3);
-                        *abort_flag = 1;
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-        }
-        __threadfence();
+// ------------------------------------------------------------------ block operators
+// One CTA per (row block j, triangle): X = I, then the block's panel sequence (L) or back substitution (U)
+// applied to the columns of X (one thread per column), stored column-major and row-major.
+template <class C, int NBS>
+__global__ void __launch_bounds__(NBS) k_block_ops(const C *__restrict__ A, int64_t lda, int64_t n,
+                                                   const int32_t *__restrict__ ipiv, C *__restrict__ ops) {
+    extern __shared__ __align__(16) unsigned char xsm[];
+    C(*X)[NBS + 1] = (C(*)[NBS + 1])xsm;  // X[r][c]
+    const int j = blockIdx.x >> 1, tri = blockIdx.x & 1;
+    const int64_t r0 = (int64_t)j * NBS;
+    if (r0 >= n) return;
+    const int nr = (int)min((int64_t)NBS, n - r0);
+    const int c = threadIdx.x;
+    for (int r = 0; r < NBS; r++) {
+        C v = cz<C>();
+        if (r == c && c < nr) v.x = 1;
+        X[r][c] = v;
     }
     __syncthreads();
-    return ok != 0;
+    const C *D = A + r0 * lda + r0;  // D[r + k*lda]
+    if (c < nr) {
+        if (tri == 0) {
+            for (int p0 = 0; p0 < nr; p0 += 32) {
+                const int w = min(32, nr - p0);
+                for (int t = 0; t < w; t++) {
+                    int q = (int)(ipiv[r0 + p0 + t] - r0);
+                    if (q != p0 + t && q >= p0 && q < p0 + w) {
+                        C a = X[p0 + t][c];
+                        X[p0 + t][c] = X[q][c];
+                        X[q][c] = a;
+                    }
+                }
+                // rows of the panel: unit lower substitution; rows below: subtract L[r][panel] x_panel
+                for (int t = 0; t < w; t++) {
+                    C xt = X[p0 + t][c];
+                    for (int r = p0 + t + 1; r < nr; r++) cfms(X[r][c], D[(int64_t)(p0 + t) * lda + r], xt);
+                }
+            }
+        } else {
+            for (int r = nr - 1; r >= 0; r--) {
+                C s = X[r][c];
+                for (int k = r + 1; k < nr; k++) cfms(s, D[(int64_t)k * lda + r], X[k][c]);
+                C d = D[(int64_t)r * lda + r];
+                X[r][c] = cabs1(d) > 0 ? cmul(s, crecip(d)) : s;
+            }
+        }
+    }
+    __syncthreads();
+    // two layouts of the operator: column-major (coalesced for y = X acc) and row-major (for y = X^H acc)
+    C *ocm = ops + (int64_t)(4 * j + 2 * tri) * NBS * NBS;
+    C *orm = ocm + (int64_t)NBS * NBS;
+    for (int r = 0; r < NBS; r++) {
+        orm[r * NBS + c] = X[r][c];
+        ocm[c * NBS + r] = X[r][c];
+    }
 }
 
-template <class C, int NBS, int NR>
-__global__ void __launch_bounds__(2 * NBS) k_trsv_persistent(const C *__restrict__ A, int64_t lda, int64_t n,
-                                                             const int32_t *__restrict__ ipiv, C *__restrict__ B,
-                                                             int64_t ldb, int rhs0, int nr_here, int mode,
-                                                             const C *__restrict__ dinv, int *sync_buf, int *gflags) {
-    constexpr int NT = 2 * NBS;
-    constexpr int NW = NT / 32;
-    __shared__ C acc[NBS][NR];
-    __shared__ C yk[NBS][NR];
-    __shared__ C part[NBS][NR];
-    __shared__ int s_ticket;
+// ------------------------------------------------------------------ TMA-fed persistent solve
+// Per CTA (row block j): warps 0..7 compute, warp 8 streams data with the TMA engine into a ring of
+// NSTAGE shared-memory stages of HALF = NBS/2 columns x NBS rows (one half of a 128 x 128 block):
+// first the dependency blocks in processing order, then the block operator. Only the short solution
+// vectors of the dependencies go through ordinary loads.
+#define TS_NBS 128
+#define TS_HALF 64
+#define TS_NSTAGE 3
+#define TS_STAGE_BYTES (TS_HALF * TS_NBS * 8)  // 64 KB of complex64
+
+__device__ __forceinline__ uint32_t smem_u32t(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void tmbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32t(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void tmbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32t(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tmbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32t(bar)) : "memory");
+}
+__device__ __forceinline__ bool tmbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_u32t(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// bounded wait (~2 s) on an mbarrier phase; false on timeout or when the CTA is aborting
+__device__ bool tmbar_wait(uint64_t *bar, uint32_t parity, volatile int *cta_abort, int *gflags) {
+    if (tmbar_try(bar, parity)) return true;
+    uint64_t t0 = gtimer_t();
+    for (uint32_t it = 1;; ++it) {
+        if (tmbar_try(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*cta_abort) return false;
+            if (gtimer_t() - t0 > 2000000000ull) {
+                gdm_dev_error(gflags, GDM_ERR_TIMEOUT, 4);
+                *cta_abort = 1;
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void tma2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32t(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32t(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32t(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32t(bar))
+                 : "memory");
+}
+
+template <int NR>
+__global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUtensorMap tmA, int64_t n,
+                                                   float2 *__restrict__ B, int64_t ldb, int rhs0, int nr_here,
+                                                   int mode, const float2 *__restrict__ ops, int *sync_buf,
+                                                   int *gflags) {
+    constexpr int NBS = TS_NBS, HALF = TS_HALF;
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    float2 *ring = (float2 *)tsm;  // [NSTAGE][HALF][NBS]
+    __shared__ __align__(8) uint64_t full[TS_NSTAGE], empty[TS_NSTAGE];
+    __shared__ float2 acc[NBS][NR], yk[NBS][NR], part[NBS][NR];
+    __shared__ int s_ticket, s_dec[2];
+    __shared__ volatile int cta_abort;
     const int nblk = (int)((n + NBS - 1) / NBS);
     int *ticket = sync_buf;
-    volatile int *abort_flag = (volatile int *)(sync_buf + 1);
+    volatile int *gabort = (volatile int *)(sync_buf + 1);
     volatile int *flags = (volatile int *)(sync_buf + 2);
-    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1);
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    if (tid == 0) {
+        s_ticket = atomicAdd(ticket, 1);
+        for (int st = 0; st < TS_NSTAGE; st++) {
+            tmbar_init(&full[st], 1);
+            tmbar_init(&empty[st], 8);
+        }
+        cta_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
     const int tk = s_ticket;
     if (tk >= nblk) return;
@@ -85,261 +187,253 @@ __global__ void __launch_bounds__(2 * NBS) k_trsv_persistent(const C *__restrict
     const int j = fwd ? tk : nblk - 1 - tk;
     const int64_t r0 = (int64_t)j * NBS;
     const int nr = (int)min((int64_t)NBS, n - r0);
-    const int tid = threadIdx.x;
-    // initial acc = b_j
-    for (int e = tid; e < NBS * NR; e += NT) {
-        int r = e / NR, q = e % NR;
-        acc[r][q] = (r < nr && q < nr_here) ? B[(int64_t)(rhs0 + q) * ldb + r0 + r] : cz<C>();
-    }
-    __syncthreads();
-    // -------- contributions of the solved blocks
-    for (int s = 0; s < tk; s++) {
-        const int k = fwd ? s : nblk - 1 - s;
-        const int64_t k0 = (int64_t)k * NBS;
-        const int nk = (int)min((int64_t)NBS, n - k0);
-        {
-            // pull this dependency block into L2 while (possibly) waiting for its solution
-            const int64_t cb = (mode <= 1) ? k0 : r0;  // first column of the block read below
-            const int64_t rb = (mode <= 1) ? r0 : k0;  // first row
-            const int ncol = (mode <= 1) ? nk : nr, nrow = (mode <= 1) ? nr : nk;
-            const int lines_per_col = (int)((nrow * sizeof(C) + 127) / 128);
-            for (int e = tid; e < ncol * lines_per_col; e += NT) {
-                const char *ptr = (const char *)(A + (cb + e / lines_per_col) * lda + rb) + (e % lines_per_col) * 128;
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
-            }
-        }
-        if (!wait_flag(flags + k, abort_flag, gflags)) return;
-        for (int e = tid; e < NBS * NR; e += NT) {
-            int r = e / NR, q = e % NR;
-            yk[r][q] = (r < nk && q < nr_here) ? __ldcg(B + (int64_t)(rhs0 + q) * ldb + k0 + r) : cz<C>();
-        }
-        __syncthreads();
-        if (mode <= 1) {
-            // acc[r] -= sum_c M[r0+r][k0+c] yk[c]; two threads per row, each half the columns
-            const int r = tid % NBS, h = tid / NBS;
-            C sum[NR];
-#pragma unroll
-            for (int q = 0; q < NR; q++) sum[q] = cz<C>();
-            if (r < nr) {
-                const C *col = A + (k0 + h * (NBS / 2)) * lda + r0 + r;
-                const int cend = min(NBS / 2, nk - h * (NBS / 2));
-#pragma unroll 16
-                for (int c = 0; c < cend; c++) {
-                    C m = col[(int64_t)c * lda];
-#pragma unroll
-                    for (int q = 0; q < NR; q++) cfma(sum[q], m, yk[h * (NBS / 2) + c][q]);
+    const int nitems = 2 * tk + 2;  // halves of the dependency blocks, then the two halves of the operator
+    const float2 *opm = ops + (int64_t)(4 * j + 2 * ((mode == 1 || mode == 2) ? 1 : 0) + (mode >= 2 ? 1 : 0)) * NBS * NBS;
+
+    if (warp == 8) {
+        // ---------------- producer
+        if (lane == 0) {
+            int issued = 0;
+            for (int it = 0; it < nitems; it++) {
+                const int st = it % TS_NSTAGE;
+                const uint32_t ph = (uint32_t)((it / TS_NSTAGE) & 1);
+                if (!tmbar_wait(&empty[st], ph ^ 1, &cta_abort, gflags)) break;
+                issued = it + 1;
+                float2 *dst = ring + (size_t)st * HALF * NBS;
+                tmbar_expect_tx(&full[st], TS_STAGE_BYTES);
+                const int half = it & 1;
+                if (it < 2 * tk) {
+                    const int s = it / 2;
+                    const int k = fwd ? s : nblk - 1 - s;
+                    const int64_t k0 = (int64_t)k * NBS;
+                    // no-trans: columns of block k, rows of block j; conj-trans: columns of block j, rows of block k
+                    const int x = (int)(2 * ((mode <= 1) ? r0 : k0));
+                    const int y = (int)(((mode <= 1) ? k0 : r0) + half * HALF);
+                    tma2d(dst, &tmA, x, y, &full[st]);
+                } else {
+                    bulk1d(dst, opm + (size_t)half * HALF * NBS, TS_STAGE_BYTES, &full[st]);
                 }
             }
-            if (h == 1)
+            // on an abort, let the copies still in flight land before the CTA (and its shared memory) goes away;
+            // the most recent NSTAGE items are the latest phase of each stage
+            if (cta_abort) {
+                for (int it = max(0, issued - TS_NSTAGE); it < issued; it++) {
+                    uint64_t *bar = &full[it % TS_NSTAGE];
+                    const uint32_t ph = (uint32_t)((it / TS_NSTAGE) & 1);
+                    uint64_t t0 = gtimer_t();
+                    while (!tmbar_try(bar, ph) && gtimer_t() - t0 < 2000000000ull) {
+                    }
+                }
+            }
+        }
+        return;
+    }
+    // ---------------- consumers (warps 0..7, 256 threads); thread 0 takes every wait and publishes the
+    // outcome before a named barrier so all consumer warps branch alike
+    int dc = 0;
+    auto agree = [&](bool ok0) -> bool {
+        if (tid == 0) s_dec[dc & 1] = ok0 ? 1 : 0;
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        bool r = s_dec[dc & 1] != 0;
+        dc++;
+        return r;
+    };
+    for (int e = tid; e < NBS * NR; e += 256) {
+        int r = e / NR, q = e % NR;
+        acc[r][q] = (r < nr && q < nr_here) ? B[(int64_t)(rhs0 + q) * ldb + r0 + r] : make_float2(0.f, 0.f);
+    }
+    const int r = tid % NBS, hh = tid / NBS;  // row and which 32-column quarter pair (no-trans)
+    int it = 0;
+    for (int s = 0; s <= tk; s++) {
+        const bool is_op = (s == tk);
+        if (!is_op) {
+            const int k = fwd ? s : nblk - 1 - s;
+            const int64_t k0 = (int64_t)k * NBS;
+            const int nk = (int)min((int64_t)NBS, n - k0);
+            bool ok0 = true;
+            if (tid == 0) {
+                if (flags[k] == 0) {
+                    uint64_t t0 = gtimer_t();
+                    unsigned w = 0;
+                    while (flags[k] == 0) {
+                        if ((++w & 255) == 0) {
+                            if (*gabort || cta_abort) {
+                                ok0 = false;
+                                break;
+                            }
+                            if (gtimer_t() - t0 > 2000000000ull) {
+                                gdm_dev_error(gflags, GDM_ERR_TIMEOUT, 3);
+                                *gabort = 1;
+                                ok0 = false;
+                                break;
+                            }
+                        }
+                    }
+                }
+                __threadfence();
+            }
+            if (!agree(ok0)) {
+                cta_abort = 1;
+                return;
+            }
+            for (int e = tid; e < NBS * NR; e += 256) {
+                int rr = e / NR, q = e % NR;
+                yk[rr][q] = (rr < nk && q < nr_here) ? __ldcg(B + (int64_t)(rhs0 + q) * ldb + k0 + rr)
+                                                     : make_float2(0.f, 0.f);
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+        }
+        float2 sum[NR];
 #pragma unroll
-                for (int q = 0; q < NR; q++) part[r][q] = sum[q];
-            __syncthreads();
-            if (h == 0 && r < nr)
+        for (int q = 0; q < NR; q++) sum[q] = make_float2(0.f, 0.f);
+        for (int half = 0; half < 2; half++, it++) {
+            const int st = it % TS_NSTAGE;
+            bool ok0 = true;
+            if (tid == 0) ok0 = tmbar_wait(&full[st], (uint32_t)((it / TS_NSTAGE) & 1), &cta_abort, gflags);
+            if (!agree(ok0)) {
+                cta_abort = 1;
+                return;
+            }
+            const float2 *sb = ring + (size_t)st * HALF * NBS;  // sb[c * NBS + row]
+            const float2(*src)[NR] = is_op ? acc : yk;
+            if (mode <= 1 || is_op) {
+                // y_r -= sum_c M[r][c] v[c] (operator: y_r = sum_c Op[r][c] acc[c]); thread (r, hh) takes 32 columns
+                const bool herm = is_op && mode >= 2;
+#pragma unroll 8
+                for (int c = hh * 32; c < hh * 32 + 32; c++) {
+                    float2 m = sb[c * NBS + r];
+                    if (herm) m.y = -m.y;
+                    const int cc = half * HALF + c;
 #pragma unroll
-                for (int q = 0; q < NR; q++) acc[r][q] = csub(acc[r][q], cadd(sum[q], part[r][q]));
-        } else {
-            // acc[c] -= sum_rr conj(M[k0+rr][r0+c]) yk[rr]; one warp per column (rows across lanes)
-            const int w = tid / 32, lane = tid % 32;
-            for (int c = w; c < nr; c += NW) {
-                const C *col = A + (r0 + c) * lda + k0;
-                C sum[NR];
+                    for (int q = 0; q < NR; q++) cfma(sum[q], m, src[cc][q]);
+                }
+            } else {
+                // acc[c] -= sum_rr conj(M[k0+rr][r0+c]) yk[rr]: 4 threads per column of this half, rows rotated
+                const int c = tid / 4, p = tid % 4;
+                float2 cs[NR];
 #pragma unroll
-                for (int q = 0; q < NR; q++) sum[q] = cz<C>();
-                for (int rr = lane; rr < nk; rr += 32) {
-                    C m = conjc(col[rr]);
+                for (int q = 0; q < NR; q++) cs[q] = make_float2(0.f, 0.f);
+#pragma unroll 8
+                for (int i = 0; i < NBS / 4; i++) {
+                    const int rr = (p + 4 * i + 4 * c) & (NBS - 1);
+                    float2 m = sb[c * NBS + rr];
+                    m.y = -m.y;
 #pragma unroll
-                    for (int q = 0; q < NR; q++) cfma(sum[q], m, yk[rr][q]);
+                    for (int q = 0; q < NR; q++) cfma(cs[q], m, yk[rr][q]);
                 }
 #pragma unroll
                 for (int q = 0; q < NR; q++)
-                    for (int o = 16; o > 0; o >>= 1) {
-                        sum[q].x += __shfl_down_sync(0xffffffffu, sum[q].x, o);
-                        sum[q].y += __shfl_down_sync(0xffffffffu, sum[q].y, o);
+                    for (int o = 1; o < 4; o <<= 1) {
+                        cs[q].x += __shfl_xor_sync(0xffffffffu, cs[q].x, o);
+                        cs[q].y += __shfl_xor_sync(0xffffffffu, cs[q].y, o);
                     }
-                if (lane == 0)
+                if (p == 0 && half * HALF + c < nr)
 #pragma unroll
-                    for (int q = 0; q < NR; q++) acc[c][q] = csub(acc[c][q], sum[q]);
+                    for (int q = 0; q < NR; q++) acc[half * HALF + c][q] = csub(acc[half * HALF + c][q], cs[q]);
+            }
+            __syncwarp();
+            if (lane == 0) tmbar_arrive(&empty[st]);
+        }
+        if (mode <= 1 || is_op) {
+            if (hh == 1)
+#pragma unroll
+                for (int q = 0; q < NR; q++) part[r][q] = sum[q];
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (hh == 0 && r < nr) {
+                if (is_op) {
+                    for (int q = 0; q < NR; q++)
+                        if (q < nr_here) B[(int64_t)(rhs0 + q) * ldb + r0 + r] = cadd(sum[q], part[r][q]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NR; q++) acc[r][q] = csub(acc[r][q], cadd(sum[q], part[r][q]));
+                }
             }
         }
-        __syncthreads();
-    }
-    // -------- diagonal block
-    const C *D = A + r0 * lda + r0;  // D[r + c*lda]
-    if (mode == 0 && tid < NR) {
-        // apply the block's row interchanges in order (partners are inside the block)
-        for (int t = 0; t < nr; t++) {
-            int p = ipiv[r0 + t] - (int)r0;
-            if (p != t) {
-                C a = acc[t][tid];
-                acc[t][tid] = acc[p][tid];
-                acc[p][tid] = a;
-            }
-        }
-    }
-    __syncthreads();
-    // diagonal block in pieces of 32: x_s = inv(T_ss) acc_s with the precomputed 32 x 32 inverses of the
-    // factors' diagonal pieces (conjugate-transposed for the adjoint modes), then update the remaining rows
-    const bool lower_like = (mode == 0 || mode == 2);
-    const int nsub = (nr + 31) / 32;
-    const int use_u = (mode == 1 || mode == 2);
-    const bool herm = (mode >= 2);
-    for (int si = 0; si < nsub; si++) {
-        const int sb = lower_like ? si : nsub - 1 - si;
-        const int c0 = sb * 32;
-        const int w = min(32, nr - c0);
-        const C *Ti = dinv + ((int64_t)2 * ((r0 + c0) / 32) + use_u) * 1024;
-        __syncthreads();
-        // x[row][q] = sum_i Tinv_eff[row][i] acc[c0+i][q]; one thread per (row, q)
-        C xv = cz<C>();
-        const int row = tid % 32, q = tid / 32;
-        if (q < NR && row < w) {
-            C m[32];
-#pragma unroll
-            for (int i = 0; i < 32; i++) m[i] = herm ? conjc(Ti[i * 32 + row]) : Ti[row * 32 + i];
-#pragma unroll
-            for (int i = 0; i < 32; i++)
-                if (i < w) cfma(xv, m[i], acc[c0 + i][q]);
-        }
-        __syncthreads();
-        if (q < NR && row < w) acc[c0 + row][q] = xv;
-        __syncthreads();
-        const int ub = lower_like ? c0 + w : 0;
-        const int ue = lower_like ? nr : c0;
-        for (int r = ub + tid; r < ue; r += NT) {
-            C sum[NR];
-#pragma unroll
-            for (int qq = 0; qq < NR; qq++) sum[qq] = cz<C>();
-            C m[32];
-#pragma unroll
-            for (int i = 0; i < 32; i++) {
-                if (i < w) m[i] = (mode <= 1) ? D[(int64_t)(c0 + i) * lda + r] : conjc(D[(int64_t)r * lda + c0 + i]);
-            }
-#pragma unroll
-            for (int i = 0; i < 32; i++)
-                if (i < w)
-#pragma unroll
-                    for (int qq = 0; qq < NR; qq++) cfma(sum[qq], m[i], acc[c0 + i][qq]);
-#pragma unroll
-            for (int qq = 0; qq < NR; qq++) acc[r][qq] = csub(acc[r][qq], sum[qq]);
-        }
-        __syncthreads();
-    }
-    if (mode == 3 && tid < NR) {
-        for (int t = nr - 1; t >= 0; t--) {
-            int p = ipiv[r0 + t] - (int)r0;
-            if (p != t) {
-                C a = acc[t][tid];
-                acc[t][tid] = acc[p][tid];
-                acc[p][tid] = a;
-            }
-        }
-    }
-    __syncthreads();
-    for (int e = tid; e < nr * NR; e += NT) {
-        int r = e / NR, q = e % NR;
-        if (q < nr_here) B[(int64_t)(rhs0 + q) * ldb + r0 + r] = acc[r][q];
+        asm volatile("bar.sync 1, 256;" ::: "memory");
     }
     __threadfence();
-    __syncthreads();
+    asm volatile("bar.sync 1, 256;" ::: "memory");
     if (tid == 0) atomicExch((int *)(flags + j), 1);
 }
 
-// Inverses of the 32 x 32 diagonal pieces of L (unit lower) and U (upper) of every panel:
-// inv[(2*p + 0)*1024 + r*32 + c] = (L_pp^{-1})[r][c], inv[(2*p + 1)*1024 + r*32 + c] = (U_pp^{-1})[r][c].
-// One warp per triangle; lane c computes column c of the inverse by substitution on e_c.
-template <class C>
-__global__ void k_diag_inverses(const C *__restrict__ A, int64_t lda, int64_t n, C *__restrict__ inv) {
-    // one warp (block) per triangle
-    const int warp = blockIdx.x, lane = threadIdx.x & 31;
-    const int np = (int)((n + 31) / 32);
-    if (warp >= 2 * np) return;
-    const int p = warp / 2, up = warp & 1;
-    const int64_t c0 = (int64_t)p * 32;
-    const int w = (int)min((int64_t)32, n - c0);
-    __shared__ C t[32][33];
-    for (int r = 0; r < 32; r++) {
-        C v = cz<C>();
-        if (r < w && lane < w) v = A[(c0 + lane) * lda + c0 + r];
-        t[r][lane] = v;  // t[row][col]
-    }
-    __syncwarp();
-    C x[32];
-#pragma unroll
-    for (int r = 0; r < 32; r++) x[r] = cz<C>();
-    if (lane < w) {
-        if (!up) {
-            // L x = e_lane, unit lower: forward
-#pragma unroll
-            for (int r = 0; r < 32; r++) {
-                if (r < w) {
-                    C v = (r == lane) ? C{1, 0} : cz<C>();
-#pragma unroll
-                    for (int j = 0; j < 32; j++)
-                        if (j < r) cfms(v, t[r][j], x[j]);
-                    x[r] = v;
-                }
-            }
-        } else {
-            // U x = e_lane: backward with division by the diagonal
-#pragma unroll
-            for (int r = 31; r >= 0; r--) {
-                if (r < w) {
-                    C v = (r == lane) ? C{1, 0} : cz<C>();
-#pragma unroll
-                    for (int j = 0; j < 32; j++)
-                        if (j > r && j < w) cfms(v, t[r][j], x[j]);
-                    x[r] = cmul(v, crecip(t[r][r]));
-                }
-            }
-        }
-    }
-    C *o = inv + ((int64_t)2 * p + up) * 1024;
-#pragma unroll
-    for (int r = 0; r < 32; r++) o[r * 32 + lane] = x[r];
-}
-
-// every pivot inside its own block of NBS rows?
+// every pivot inside its own block of nbs rows?
 __global__ void k_pivots_local(const int32_t *__restrict__ ipiv, int64_t n, int nbs, int *bad) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (ipiv[i] / nbs != i / nbs) atomicExch(bad, 1);
 }
 
-template <class C, int NBS>
-gdm_status launch_modes(gdm_ctx *ctx, const C *A, int64_t lda, int64_t n, const int32_t *ipiv, C *B, int64_t ldb,
-                        int n_rhs, const int *modes, int nmodes, int *sync_buf, C *dinv) {
-    const int nblk = (int)((n + NBS - 1) / NBS);
+PFN_cuTensorMapEncodeTiled_v12000 trsv_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+gdm_status launch_modes_f32(gdm_ctx *ctx, const float2 *A, int64_t lda, int64_t n, float2 *B, int64_t ldb, int n_rhs,
+                            const int *modes, int nmodes, int *sync_buf, const float2 *ops) {
+    const int nblk = (int)((n + TS_NBS - 1) / TS_NBS);
+    auto fn = trsv_encode_fn();
+    if (!fn) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * n), (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)(2 * lda * 4)};
+    cuuint32_t box[2] = {2 * TS_NBS, TS_HALF};
+    cuuint32_t es[2] = {1, 1};
+    if (fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)A, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed (solve)");
+    const int smem = TS_NSTAGE * TS_STAGE_BYTES;
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsv_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+    }
     for (int mi = 0; mi < nmodes; mi++) {
         for (int q0 = 0; q0 < n_rhs; q0 += 2) {
             int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
             GDM_CUDA_TRY(ctx, cudaMemsetAsync(sync_buf, 0, sizeof(int) * (nblk + 2), ctx->stream));
-            k_trsv_persistent<C, NBS, 2><<<nblk, 2 * NBS, 0, ctx->stream>>>(A, lda, n, ipiv, B, ldb, q0, nr, modes[mi],
-                                                                            dinv, sync_buf, ctx->dflags);
-            GDM_LAUNCHED(ctx, "trsv_persistent");
+            k_trsv_tma<2><<<nblk, 288, smem, ctx->stream>>>(map, n, B, ldb, q0, nr, modes[mi], ops, sync_buf,
+                                                            ctx->dflags);
+            GDM_LAUNCHED(ctx, "trsv_tma");
         }
     }
     return GDM_OK;
 }
 
-}  // namespace
-
-size_t gdm_trsv_sync_bytes(int64_t n) { return sizeof(int) * ((n + 127) / 128 + 8); }
-
-// bytes of the diagonal-piece inverses (complex128 size, enough for both precisions)
-size_t gdm_trsv_inv_bytes(int64_t n) { return (size_t)2 * ((n + 31) / 32) * 1024 * sizeof(double2); }
-
-gdm_status gdm_trsv_prepare(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda, void *dinv) {
-    const int np = (int)((n + 31) / 32);
-    const unsigned blocks = (unsigned)(2 * np);
-    if (prec == GDM_FP64)
-        k_diag_inverses<double2><<<blocks, 32, 0, ctx->stream>>>((const double2 *)A, lda, n, (double2 *)dinv);
-    else
-        k_diag_inverses<float2><<<blocks, 32, 0, ctx->stream>>>((const float2 *)A, lda, n, (float2 *)dinv);
-    GDM_LAUNCHED(ctx, "diag_inverses");
+template <class C, int NBS> gdm_status launch_ops(gdm_ctx *ctx, const C *A, int64_t lda, int64_t n, const int32_t *ipiv,
+                                                  C *ops) {
+    const size_t smem = sizeof(C) * NBS * (NBS + 1);
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_block_ops<C, NBS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        attr = true;
+    }
+    const int nblk = (int)((n + NBS - 1) / NBS);
+    k_block_ops<C, NBS><<<2 * nblk, NBS, smem, ctx->stream>>>(A, lda, n, ipiv, ops);
+    GDM_LAUNCHED(ctx, "block_ops");
     return GDM_OK;
 }
 
-// 1 if all pivots stay inside their NBS-row block (synchronises)
+}  // namespace
+
+size_t gdm_trsv_sync_bytes(int64_t n) { return sizeof(int) * ((n + 31) / 32 + 8); }
+
+// bytes of the FP32 block operators (4 planes of 128 x 128 per row block)
+size_t gdm_trsv_inv_bytes(int64_t n) {
+    const int64_t nb32 = (n + TRSV_NBS_F32 - 1) / TRSV_NBS_F32;
+    return (size_t)4 * nb32 * TRSV_NBS_F32 * TRSV_NBS_F32 * sizeof(float2);
+}
+
+// 1 if all pivots stay inside their nbs-row block (synchronises)
 gdm_status gdm_pivots_local(gdm_ctx *ctx, const int32_t *ipiv, int64_t n, int nbs, int *sync_buf, int *local) {
     GDM_CUDA_TRY(ctx, cudaMemsetAsync(sync_buf, 0, sizeof(int), ctx->stream));
     k_pivots_local<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ipiv, n, nbs, sync_buf);
@@ -352,15 +446,20 @@ gdm_status gdm_pivots_local(gdm_ctx *ctx, const int32_t *ipiv, int64_t n, int nb
     return GDM_OK;
 }
 
+gdm_status gdm_trsv_prepare(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda,
+                            const int32_t *ipiv, void *ops) {
+    if (prec == GDM_FP64) return GDM_ERR_UNSUPPORTED;  // the FP64 path uses the launch-per-panel solver
+    return launch_ops<float2, TRSV_NBS_F32>(ctx, (const float2 *)A, lda, n, ipiv, (float2 *)ops);
+}
+
 // solve with the factors: conj_trans = 0: U^{-1} L^{-1} P b; conj_trans = 1: P^T L^{-H} U^{-H} b
 gdm_status gdm_trsv_persistent(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda,
                                const int32_t *ipiv, void *B, int64_t ldb, int n_rhs, int conj_trans, int *sync_buf,
-                               const void *dinv) {
+                               const void *ops) {
+    (void)ipiv;
     static const int fwd[2] = {0, 1}, adj[2] = {2, 3};
     const int *modes = conj_trans ? adj : fwd;
-    if (prec == GDM_FP64)
-        return launch_modes<double2, 128>(ctx, (const double2 *)A, lda, n, ipiv, (double2 *)B, ldb, n_rhs, modes, 2,
-                                          sync_buf, (double2 *)dinv);
-    return launch_modes<float2, 256>(ctx, (const float2 *)A, lda, n, ipiv, (float2 *)B, ldb, n_rhs, modes, 2, sync_buf,
-                                     (float2 *)dinv);
+    if (prec == GDM_FP64) return GDM_ERR_UNSUPPORTED;  // the FP64 path uses the launch-per-panel solver
+    return launch_modes_f32(ctx, (const float2 *)A, lda, n, (float2 *)B, ldb, n_rhs, modes, 2, sync_buf,
+                            (const float2 *)ops);
 }
