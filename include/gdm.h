@@ -193,6 +193,28 @@ gdm_status gdm_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, co
 gdm_status gdm_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,
                               int n_rhs, const double *e0_norm2, double *ext, double *sca, double *abs);
 
+/* Largest ceil(n/256) * n_rhs that gdm_cross_sections_noalloc accepts: its fixed device
+ * scratch holds this many (ext, abs) partial-sum pairs, 1 MiB per device. */
+#define GDM_XSEC_NOALLOC_MAX_PARTS 65536
+
+/* gdm_cross_sections without any device allocation. The paper has no counterpart: this is a
+ * deployment variant with the same arguments and results as gdm_cross_sections (same
+ * partial-sum kernel, same summation order). It is for callers that must not allocate device
+ * memory: a step running while another allocator (a PyTorch caching allocator at its limit,
+ * say) holds the free memory, or a latency-bound loop that cannot afford cudaMalloc/cudaFree,
+ * which may synchronise the whole device. The partial sums live in one fixed file-scope device
+ * buffer per device (GDM_XSEC_NOALLOC_MAX_PARTS pairs), and the prefactors are passed as a
+ * kernel argument. The first call on each device looks up that buffer's address
+ * (cudaGetSymbolAddress, with the context's device current); make it before any stream capture.
+ * Nothing in the buffer needs to start at zero: every slot read is written earlier in the same
+ * call. The buffer is shared by every context and stream of a device, so calls that overlap on
+ * the GPU race on it: order them on one stream or synchronise in between.
+ * Errors: as gdm_cross_sections, plus GDM_ERR_SHAPE when ceil(n/256) * n_rhs exceeds
+ * GDM_XSEC_NOALLOC_MAX_PARTS (nothing is launched), and GDM_ERR_CUDA if the address lookup fails. */
+gdm_status gdm_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,
+                                      int n_rhs, const double *e0_norm2, double *ext, double *sca,
+                                      double *abs);
+
 /* Adjoint backward of gdm_solve + gdm_cross_sections for plane-wave illumination
  * (kind 3). Given the upstream gradient gF = dL/dF^* (device (3n) x n_rhs
  * complex128, conjugate Wirtinger derivative, may be NULL) and g_sigma (host

@@ -77,6 +77,7 @@ _SIGS = {
     "gdm_nearfield": ([P, C.POINTER(Problem), P, P, I64, P, C.c_int, P, P], C.c_int),
     "gdm_residual": ([P, C.POINTER(Problem), P, P, C.c_int, P, P], C.c_int),
     "gdm_cross_sections": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
+    "gdm_cross_sections_noalloc": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
     "gdm_backward": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, C.c_int, PD, PD, P, PD, P, P, P,
                       C.POINTER(SolveInfo)], C.c_int),
     "gdm_nearfield_backward": ([P, C.POINTER(Problem), P, P, I64, C.c_int, PD, PD, P, P, P, P, P], C.c_int),
@@ -291,6 +292,22 @@ def cross_sections(ctx: Context, prob: GDMProblem, F0, F, e0_norm2):
     ctx._sync_stream()
     ctx._check(lib().gdm_cross_sections(ctx.h, C.byref(s), _ptr(F0.contiguous()), _ptr(F.contiguous()), n_rhs, npp,
                                         _ptr(out[0]), _ptr(out[1]), _ptr(out[2])), "gdm_cross_sections")
+    return out[0], out[1], out[2]
+
+
+def cross_sections_noalloc(ctx: Context, prob: GDMProblem, F0, F, e0_norm2, out):
+    """gdm_cross_sections_noalloc: writes (ext, sca, abs) into the caller's (3, n_rhs) float64 device tensor
+    `out`; the library allocates nothing."""
+    n_rhs = F.shape[0]
+    if out.shape != (3, n_rhs) or out.dtype != torch.float64 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous (3, n_rhs) float64 tensor")
+    if not (F0.is_contiguous() and F.is_contiguous()):
+        raise ValueError("F0 and F must be contiguous")
+    na, npp = _dbl_array(e0_norm2)
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_cross_sections_noalloc(ctx.h, C.byref(s), _ptr(F0), _ptr(F), n_rhs, npp, _ptr(out[0]),
+                                                _ptr(out[1]), _ptr(out[2])), "gdm_cross_sections_noalloc")
     return out[0], out[1], out[2]
 
 

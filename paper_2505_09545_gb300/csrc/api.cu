@@ -413,6 +413,17 @@ gdm_status gdm_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *
     return gdm_launch_cross_sections(ctx, p, F0, F, n_rhs, e0_norm2, ext, sca, abs);
 }
 
+gdm_status gdm_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,
+                                      int n_rhs, const double *e0_norm2, double *ext, double *sca, double *abs) {
+    GDM_TRY(check_problem(ctx, p));
+    if (!F0 || !F || !e0_norm2) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n_rhs must be in [1, 64]");
+    for (int r = 0; r < n_rhs; r++)
+        if (!(e0_norm2[r] > 0)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "|E0|^2 must be > 0");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return gdm_launch_cross_sections_noalloc(ctx, p, F0, F, n_rhs, e0_norm2, ext, sca, abs);
+}
+
 gdm_status gdm_backward(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
                         const int32_t *ipiv, const double *F, int n_rhs, const double *e0, const double *khat,
                         const double *gF, const double *g_sigma, double *grad_pos, double *grad_eps,

@@ -181,6 +181,9 @@ gdm_status gdm_launch_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double
                                 const double *F0_eval, int n_rhs, double *E_out, double *H_out);
 gdm_status gdm_launch_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F, int n_rhs,
                                      const double *e0_norm2, double *ext, double *sca, double *abs);
+gdm_status gdm_launch_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,
+                                             int n_rhs, const double *e0_norm2, double *ext, double *sca,
+                                             double *abs);
 // linear algebra (lu.cu)
 // Factor A in place. global_pivot = 0: pivots searched inside each 32 x 32 diagonal block, with the
 // largest |row below| / |pivot| ratio returned in *growth_out (<= 1: identical to partial pivoting);

@@ -12,6 +12,8 @@
 // (Sec. "Volume discretization polarizabilities", Eq. selfterm_SEp_cubic).
 #include <math.h>
 
+#include <mutex>
+
 #include "gdm_internal.cuh"
 
 #define PI_D 3.14159265358979323846
@@ -856,5 +858,88 @@ gdm_status gdm_launch_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const d
     GDM_LAUNCHED(ctx, "xsec_partial");
     k_xsec_final<<<n_rhs, 32, 0, ctx->stream>>>(part, (int)nb, n_rhs, dpref, ext, sca, abs);
     GDM_LAUNCHED(ctx, "xsec_final");
+    return GDM_OK;
+}
+
+// ------------------------------------------------------------------ cross sections without allocation
+// A variant of the launcher above for callers that must not allocate device memory: a step that runs
+// while another allocator (a PyTorch caching allocator at its limit, say) holds the free memory, or a
+// latency-bound loop that cannot afford cudaMalloc/cudaFree, which may synchronise the whole device.
+// The partial sums go to one fixed file-scope buffer per device instead of the context's growing
+// workspace, and the prefactors travel as a kernel argument instead of through the parameter buffer.
+// Every slot the final kernel reads is written earlier on the same stream by k_xsec_partial, so nothing
+// in the buffer needs to start at zero. The buffer is shared by all contexts and streams of a device:
+// calls that overlap on the GPU race on it.
+static __device__ __align__(256) double g_xsec_static_part[2 * GDM_XSEC_NOALLOC_MAX_PARTS];
+
+namespace {
+struct XsecPref {
+    double v[64];
+};
+
+__global__ void k_xsec_final_pref(const double *__restrict__ part, int nblocks, int n_rhs, XsecPref pref, double *ext,
+                                  double *sca, double *abs_) {
+    int q = blockIdx.x;
+    if (q >= n_rhs) return;
+    double a0 = 0.0, a1 = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 32) {
+        a0 += part[((int64_t)q * nblocks + b) * 2];
+        a1 += part[((int64_t)q * nblocks + b) * 2 + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_down_sync(0xffffffffu, a0, o);
+        a1 += __shfl_down_sync(0xffffffffu, a1, o);
+    }
+    if (threadIdx.x == 0) {
+        double e = pref.v[q] * a0, ab = pref.v[q] * a1;
+        if (ext) ext[q] = e;
+        if (abs_) abs_[q] = ab;
+        if (sca) sca[q] = e - ab;
+    }
+}
+
+// device address of g_xsec_static_part, looked up once per device (with that device current)
+#define GDM_XSEC_MAX_DEVICES 64
+std::mutex g_xsec_mu;
+double *g_xsec_ptr[GDM_XSEC_MAX_DEVICES];
+}  // namespace
+
+gdm_status gdm_launch_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,
+                                             int n_rhs, const double *e0_norm2, double *ext, double *sca,
+                                             double *abs) {
+    const int64_t n = p->n;
+    const int64_t nb = (n + XS_BS - 1) / XS_BS;
+    if (nb * n_rhs > GDM_XSEC_NOALLOC_MAX_PARTS)
+        return gdm_fail(ctx, GDM_ERR_SHAPE,
+                        "gdm_cross_sections_noalloc: ceil(n/%d) * n_rhs = %lld exceeds its fixed scratch of %d "
+                        "partial sums (n = %lld, n_rhs = %d); use gdm_cross_sections",
+                        XS_BS, (long long)(nb * n_rhs), GDM_XSEC_NOALLOC_MAX_PARTS, (long long)n, n_rhs);
+    if (ctx->device < 0 || ctx->device >= GDM_XSEC_MAX_DEVICES)
+        return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "gdm_cross_sections_noalloc: device ordinal %d >= %d", ctx->device,
+                        GDM_XSEC_MAX_DEVICES);
+    double *part;
+    {
+        std::lock_guard<std::mutex> lock(g_xsec_mu);
+        if (!g_xsec_ptr[ctx->device]) {
+            void *addr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&addr, g_xsec_static_part);
+            if (e != cudaSuccess || !addr)
+                return gdm_fail(ctx, GDM_ERR_CUDA, "gdm_cross_sections_noalloc: cudaGetSymbolAddress failed: %s",
+                                cudaGetErrorString(e));
+            g_xsec_ptr[ctx->device] = (double *)addr;
+        }
+        part = g_xsec_ptr[ctx->device];
+    }
+    const double k = sqrt(p->eps_env) * gdm_k0(p);
+    const double d3_4pi = p->kind == 3 ? p->step * p->step * p->step / (4.0 * PI_D) : 0.0;
+    XsecPref pref;
+    for (int q = 0; q < n_rhs; q++) pref.v[q] = 4.0 * PI_D * k / (p->eps_env * e0_norm2[q]);
+    const double rad = (2.0 / 3.0) * k * k * k;
+    k_xsec_partial<<<dim3((unsigned)nb, n_rhs), XS_BS, 0, ctx->stream>>>(
+        (const double2 *)F0, (const double2 *)F, n, p->kind, (const double2 *)p->eps, p->eps_env, d3_4pi,
+        (const double2 *)p->alpha6, rad, part);
+    GDM_LAUNCHED(ctx, "xsec_partial");
+    k_xsec_final_pref<<<n_rhs, 32, 0, ctx->stream>>>(part, (int)nb, n_rhs, pref, ext, sca, abs);
+    GDM_LAUNCHED(ctx, "xsec_final_pref");
     return GDM_OK;
 }
