@@ -14,6 +14,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -107,6 +108,111 @@ def cpu_oracle_sample(nx=18, ny=14, nz=10, target_n=12000):
                       f"scaled to N={target_n} by N^2 (assembly) and N^3 (solve)"}
 
 
+def adjoint_leg(G, ctx, dev, precision, warmup, steps):
+    """Differentiation workload: dielectric cylinder r = 80 nm, h = 100 nm, d = 10 nm, eps = 12.25 + 0.05i,
+    8 wavelengths 450-800 nm, x-polarised plane wave; L = sum over the wavelengths of |E|^2 at a probe
+    50 nm above the top face plus sigma_sca; gradients with respect to every cell position, every cell
+    eps and each wavelength through the autograd wrappers (forward solve + adjoint backward)."""
+    import torch
+    import gdm_workloads as W
+    from paper_2505_09545_gb300 import autograd as AG
+    cyl = W.cylinder_diff()
+    pos = torch.tensor(cyl.pos, device=dev, requires_grad=True)
+    eps = torch.tensor(cyl.eps, device=dev, requires_grad=True)
+    rp = torch.tensor(cyl.r_eval, device=dev)
+    lams = [torch.tensor(float(l), dtype=torch.float64, device=dev, requires_grad=True) for l in cyl.wavelengths]
+
+    def run():
+        pos.grad = None
+        eps.grad = None
+        for wl in lams:
+            wl.grad = None
+        t0 = time.perf_counter()
+        L = 0.0
+        for wl in lams:
+            F, sig = AG.scatter(pos, eps, wl, ctx, cyl.step, cyl.e0, precision=precision)
+            E = AG.nearfield(pos, eps, wl, F, rp, ctx, cyl.step, cyl.e0)
+            L = L + (E.abs() ** 2).sum() + sig[:, 1].sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        L.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1
+
+    for _ in range(max(3, warmup)):
+        run()
+    fw, bw = [], []
+    for _ in range(max(1, steps)):
+        a, b = run()
+        fw.append(a)
+        bw.append(b)
+    f, b = statistics.median(fw), statistics.median(bw)
+    return {"value": f + b, "unit": "s", "forward_s": f, "backward_s": b, "precision": precision,
+            "workload": f"cylinder r=80 h=100 d=10 nm (N={cyl.n}), eps=12.25+0.05i, {len(lams)} wavelengths "
+                        "450-800 nm, x-pol; L = sum |E(probe)|^2 + sigma_sca; grads wrt all positions, eps, lambda",
+            "timing": "wall clock with device synchronisation, median of the timed repetitions"}
+
+
+def fp64_compare(G, ctx, dev, precision, cuboid):
+    """The plain FP64 GPU path (FP64 assembly, FP64 LU, FP64 solve) against the mixed-precision path on
+    the same cuboid: seconds per assemble+solve and the relative field difference between the two."""
+    import torch
+    import gdm_workloads as W
+    nx, ny, nz = (int(v) for v in cuboid.split("x"))
+    s = W.cuboid_precision(nx, ny, nz)
+    lam = float(s.wavelengths[0])
+    pos = torch.tensor(s.pos, device=dev)
+    prob = G.GDMProblem(pos, lam, 3, eps=torch.tensor(s.eps, device=dev), step=s.step)
+    F0 = G.incident_planewave(ctx, pos, lam, s.e0)
+    out = {}
+    fields = {}
+    for prec in ("fp64", precision):
+        A = torch.empty((prob.size, G.padded_lda(prob.size)),
+                        dtype=torch.complex128 if prec == "fp64" else torch.complex64, device=dev)
+        ipiv = torch.empty(prob.size, dtype=torch.int32, device=dev)
+        F = torch.empty_like(F0)
+        reps = 1 if prec == "fp64" else 3
+        G.assemble(ctx, prob, prec, out=A)
+        G.solve(ctx, prob, A, F0, prec, ipiv=ipiv, F=F)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            G.assemble(ctx, prob, prec, out=A)
+            G.solve(ctx, prob, A, F0, prec, ipiv=ipiv, F=F)
+        e1.record()
+        torch.cuda.synchronize()
+        out[prec] = e0.elapsed_time(e1) / reps / 1e3
+        fields[prec] = F.clone()
+        del A
+    d = (fields[precision] - fields["fp64"]).norm(dim=1) / fields["fp64"].norm(dim=1)
+    return {"workload": f"cuboid {nx}x{ny}x{nz} (3N={3 * s.n})", "fp64_s": out["fp64"],
+            f"{precision}_s": out[precision], "speedup": out["fp64"] / out[precision],
+            "rel_field_diff_vs_fp64": float(d.max()),
+            "timing": "CUDA events; FP64 one timed repetition after one warm-up, mixed precision three"}
+
+
+def traffic_record(kernel_src):
+    """Per-launch DRAM traffic of the trailing update from the committed ncu summary, if it was taken on
+    the kernel source as it is now (sha256 of the file); else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "tc_update_tf32_cuboid40x30x10_traffic.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = dict(re.findall(r"^- (\w+): (\S+)$", txt, flags=re.M))
+    src = os.path.join(ROOT, "paper_2505_09545_gb300", "csrc", kernel_src)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if vals.get("source_sha256") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -157,6 +263,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cuboid", default="40x30x10",
                     help="cells per axis of the cuboid workload (smaller cases are for profiling only)")
+    ap.add_argument("--fp64-cuboid", default="20x15x10",
+                    help="cuboid of the FP64-GPU-path comparison (40x30x10 = the full workload, ~2 min)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint leg and the FP64 comparison (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -263,6 +373,23 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    # assembly kernel alone against HBM: (3N)^2 complex entries written once
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    G.assemble(ctx, prob, args.precision, out=A)
+    torch.cuda.synchronize()
+    ea.record()
+    for _ in range(5):
+        G.assemble(ctx, prob, args.precision, out=A)
+    eb.record()
+    torch.cuda.synchronize()
+    asm_ms = ea.elapsed_time(eb) / 5
+    asm_bytes = float(ns) * ns * A.element_size()
+
+    extras = {}
+    if not args.no_extras:
+        extras["adjoint"] = adjoint_leg(G, ctx, dev, args.precision, args.warmup, args.steps)
+        extras["fp64_gpu_path"] = fp64_compare(G, ctx, dev, args.precision, args.fp64_cuboid)
+
     peaks, peak_src = load_peaks()
     per_launch_ms = prof["ms"] / max(1, prof["launches"])
     flops_per_launch = prof["flops"] / max(1, prof["launches"])
@@ -274,10 +401,18 @@ def main():
         rl = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"] * NOMINAL_TF32_OVER_BF16,
               "peak_src": f"{peak_src} sustained bf16 x nominal TF32/BF16 ratio 1.1/2.25"}
     achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12 if per_launch_ms > 0 else 0.0
+    traffic = traffic_record("lu_tc.cu") if (rl["bound"] == "tensor" and args.precision == "tf32"
+                                             and args.cuboid == "40x30x10") else None
     roofline = {"bound": rl["bound"], "achieved": achieved, "peak": rl["peak"], "unit": "TFLOP/s",
-                "frac": achieved / rl["peak"], "traffic": None, "kernel": "LU trailing update A22 -= A21 U12",
+                "frac": achieved / rl["peak"], "traffic": traffic, "kernel": "LU trailing update A22 -= A21 U12",
+                "algorithmic_bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
+                "flops_per_launch": flops_per_launch,
                 "launches_per_step": prof["launches"] / args.steps, "ms_per_step_in_kernel": prof["ms"] / args.steps,
                 "peak_source": rl["peak_src"]}
+    assembly = {"bound": "hbm", "achieved": asm_bytes / (asm_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": asm_bytes / (asm_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "ms": asm_ms,
+                "bytes": asm_bytes, "peak_source": f"{peak_src} copy bandwidth",
+                "kernel": "assemble A = I - G alpha (one launch, every entry written once)"}
     units = ws * 1
     value = ms / 1e3 / units
     it = infos[-1]
@@ -289,7 +424,8 @@ def main():
             "accuracy": {"refine_iters": it["iterations"], "rel_correction": it["rel_correction"],
                          "rel_residual_fp64": it["rel_residual"], "factor_ms": it["factor_ms"],
                          "refine_ms": it["refine_ms"]},
-            "roofline": roofline, "gpu_launches": launches, "phases_ms": phases,
+            "roofline": roofline, "assembly_roofline": assembly, **extras,
+            "gpu_launches": launches, "phases_ms": phases,
             "e2e": {"value": e2e_s / units, "unit": "s", "h2d_bytes_per_step": int(h_pos.numel() * 8 + h_eps.numel() * 16),
                     "d2h_bytes_per_step": int(h_F.numel() * 16)},
             "clocks": clocks, "cpu_baseline": cpu_base}

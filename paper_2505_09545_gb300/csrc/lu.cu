@@ -235,6 +235,26 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(C *__restrict__ A, int6
 // updated entry (before division by the pivot) is compared with the pivot in |re|+|im|; the largest ratio
 // is recorded in growth[0] (as float bits). A ratio <= 1 means the pivots are exactly those of partial
 // pivoting over the whole column (rows of D win ties, as they have the lower index).
+// Every CTA of a panel launch reads the unfactored diagonal block from A at its start, so the factored
+// block may only be stored once no CTA can still read it: the last CTA to finish (ticket in the flags)
+// stores its own copy and returns the ticket to 0 for the next launch.
+template <class C>
+__device__ void panel_store_diag_last(C *A, int64_t lda, int64_t c0, int w, const C *D, int ldd, int *flags) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&flags[GDM_FLAG_PANEL_TICKET], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int r = e % w, c = e / w;
+        A[(c0 + c) * lda + c0 + r] = D[r * ldd + c];
+    }
+    if (threadIdx.x == 0) atomicExch(&flags[GDM_FLAG_PANEL_TICKET], 0);
+}
+
 template <class C>
 __global__ void __launch_bounds__(256) k_panel_local(C *__restrict__ A, int64_t lda, int64_t n, int64_t c0, int w,
                                                      int32_t *__restrict__ ipiv, unsigned *growth, int *flags) {
@@ -303,11 +323,6 @@ __global__ void __launch_bounds__(256) k_panel_local(C *__restrict__ A, int64_t 
         }
     }
     __syncthreads();
-    if (blockIdx.x == 0)
-        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-            int r = e % w, c = e / w;
-            A[(c0 + c) * lda + c0 + r] = D[r][c];
-        }
     // rows below the diagonal block: L21 = A21 U^{-1}; certificate from l_k U_kk (the updated entry that
     // partial pivoting would have compared with the pivot U_kk)
     float worst = 0.f;
@@ -331,6 +346,113 @@ __global__ void __launch_bounds__(256) k_panel_local(C *__restrict__ A, int64_t 
     }
     for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_down_sync(0xffffffffu, worst, o));
     if ((threadIdx.x & 31) == 0 && worst > 0.f) atomicMax(growth, __float_as_uint(worst));
+    panel_store_diag_last(A, lda, c0, w, &D[0][0], NBP + 1, flags);
+}
+
+// FP32 version of the same panel with the diagonal block held in registers: lane q of warp 0 keeps row q
+// of D. Instead of moving rows, each lane tracks the position its row occupies in the LAPACK-style swap
+// sequence (pos), so the pivot of step t is the largest |re|+|im| in column t among the rows not yet
+// chosen, ties going to the lowest current position, exactly as with explicit swaps (two warp
+// reductions: the maximum of the magnitudes' bit patterns, then the lowest position attaining it);
+// ipiv[t] is the position the chosen row occupied. The chosen row publishes itself in shared memory
+// (double-buffered by step parity, so one warp barrier per step suffices) and the other rows take the
+// multiplier and update their remaining columns from it. The rows below then solve x U = a by forward
+// substitution against U in shared memory (independent updates of the remaining columns), with the
+// same certificate as above.
+__global__ void __launch_bounds__(128) k_panel_local_f32(float2 *__restrict__ A, int64_t lda, int64_t n, int64_t c0,
+                                                         int w, int32_t *__restrict__ ipiv, unsigned *growth,
+                                                         int *flags) {
+    __shared__ float2 U[NBP][NBP + 1];  // factored diagonal block in position order
+    __shared__ float2 invd[NBP];
+    __shared__ float2 prow[2][NBP];     // pivot row of the current step
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t r_first = c0 + w + blockIdx.x * (int64_t)blockDim.x + tid;
+    const int64_t r_step = (int64_t)gridDim.x * blockDim.x;
+    if (tid < 32) {
+        float2 row[NBP];
+#pragma unroll
+        for (int c = 0; c < NBP; c++) {
+            row[c] = make_float2(0.f, 0.f);
+            if (c < w && lane < w) row[c] = A[(c0 + c) * lda + c0 + lane];
+        }
+        int pos = lane;         // current position of this lane's row
+        bool done = lane >= w;  // chosen as a pivot row already (or outside the block)
+#pragma unroll
+        for (int t = 0; t < NBP; t++) {
+            if (t < w) {
+                // |re|+|im| >= 0, so its bit pattern orders like the value
+                const unsigned vb = done ? 0u : __float_as_uint(fabsf(row[t].x) + fabsf(row[t].y));
+                const unsigned m = __reduce_max_sync(0xffffffffu, vb);
+                const unsigned key = __reduce_min_sync(0xffffffffu, (!done && vb == m) ? (unsigned)pos : 0xffffffffu);
+                if (blockIdx.x == 0 && lane == 0) {
+                    ipiv[c0 + t] = (int32_t)(c0 + key);
+                    if (!(__uint_as_float(m) > 0.f)) gdm_dev_error(flags, GDM_ERR_SINGULAR, (int)(c0 + t));
+                }
+                const bool is_p = !done && pos == (int)key;
+                float2 *P = prow[t & 1];
+                if (is_p) {
+#pragma unroll
+                    for (int c = t; c < NBP; c++) P[c] = row[c];
+                }
+                // the row at position t moves to the pivot's old position
+                if (pos == t) pos = (int)key;
+                if (is_p) {
+                    pos = t;
+                    done = true;
+                }
+                __syncwarp();
+                if (!done) {
+                    const float2 piv = P[t];
+                    float2 l = make_float2(0.f, 0.f);
+                    const float sc = fmaxf(fabsf(piv.x), fabsf(piv.y));
+                    if (sc > 0.f) {
+                        // 1/piv = conj(piv/sc) / (|piv/sc|^2 sc), scaled against overflow
+                        const float is = __frcp_rn(sc);
+                        const float ax = piv.x * is, ay = piv.y * is;
+                        const float rr = __frcp_rn(fmaf(ax, ax, ay * ay) * sc);
+                        l = cmul(row[t], make_float2(ax * rr, -ay * rr));
+                    }
+                    row[t] = l;
+#pragma unroll
+                    for (int c = t + 1; c < NBP; c++) cfms(row[c], l, P[c]);
+                }
+            }
+        }
+        if (lane < w) {
+#pragma unroll
+            for (int c = 0; c < NBP; c++) U[pos][c] = row[c];
+        }
+    }
+    __syncthreads();
+    if (tid < w) {
+        const float2 d = U[tid][tid];
+        invd[tid] = (fabsf(d.x) + fabsf(d.y) > 0.f) ? crecip(d) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float worst = 0.f;
+    for (int64_t r = r_first; r < n; r += r_step) {
+        float2 x[NBP];
+#pragma unroll
+        for (int c = 0; c < NBP; c++) x[c] = (c < w) ? A[(c0 + c) * lda + r] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < NBP; k++) {
+            if (k < w) {
+                const float2 ukk = U[k][k];
+                const float pa = fabsf(ukk.x) + fabsf(ukk.y);
+                if (pa > 0.f) worst = fmaxf(worst, (fabsf(x[k].x) + fabsf(x[k].y)) / pa);
+                const float2 l = cmul(x[k], invd[k]);
+                x[k] = l;
+#pragma unroll
+                for (int c = k + 1; c < NBP; c++) cfms(x[c], l, U[k][c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NBP; c++)
+            if (c < w) A[(c0 + c) * lda + r] = x[c];
+    }
+    for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_down_sync(0xffffffffu, worst, o));
+    if (lane == 0 && worst > 0.f) atomicMax(growth, __float_as_uint(worst));
+    panel_store_diag_last(A, lda, c0, w, &U[0][0], NBP + 1, flags);
 }
 
 // ------------------------------------------------------------------ row interchanges
@@ -560,6 +682,14 @@ template <class C>
 static gdm_status panel_local(gdm_ctx *ctx, C *A, int64_t lda, int64_t n, int64_t c0, int w, int32_t *ipiv,
                               unsigned *growth) {
     int64_t below = n - c0 - w;
+    if (sizeof(C) == 8 && !getenv("GDM_PANEL_SMEM")) {
+        int blocks = (int)((below + 127) / 128);
+        if (blocks < 1) blocks = 1;
+        if (blocks > 4 * ctx->sm_count) blocks = 4 * ctx->sm_count;
+        k_panel_local_f32<<<blocks, 128, 0, ctx->stream>>>((float2 *)A, lda, n, c0, w, ipiv, growth, ctx->dflags);
+        GDM_LAUNCHED(ctx, "panel_local_f32");
+        return GDM_OK;
+    }
     int blocks = (int)((below + 255) / 256);
     if (blocks < 1) blocks = 1;
     if (blocks > 4 * ctx->sm_count) blocks = 4 * ctx->sm_count;
