@@ -136,6 +136,18 @@ int64_t gdm_launch_count(gdm_ctx *ctx);
  * refinement vectors). */
 gdm_status gdm_workspace_size(const gdm_problem *p, int n_rhs, gdm_precision prec, size_t *bytes);
 
+/* ---------------------------------------------------------------- polarisabilities */
+
+/* Effective electric/magnetic dipole polarisabilities from Lorentzian lines (Sec.
+ * "Effective polarizabilities", manually set lineshapes), vacuum host, for the kind 6
+ * problem's alpha6: with w = hc/lambda (eV) and k = 2 pi / lambda,
+ *   alpha0 = a^3 w0^2 / (w0^2 - w^2 - i gamma w),
+ *   alpha  = 1 / (1/alpha0 - i (2/3) k^3)        (radiative reaction, optical theorem),
+ * alpha6_i = diag(alpha_e I3, alpha_m I3). omega0_e, omega0_m: device n resonance energies
+ * (eV). alpha6_out: device n x 6 x 6 complex128 (row-major 6x6 per dipole), overwritten. */
+gdm_status gdm_alpha6_lorentz(gdm_ctx *ctx, int64_t n, const double *omega0_e, const double *omega0_m,
+                              double gamma_ev, double amp_nm, double wavelength, double *alpha6_out);
+
 /* ---------------------------------------------------------------- illumination */
 
 /* Plane wave E0(r) = e0 exp(i k khat.r), H0 = n_env khat x E0, k = n_env 2 pi / lambda0,

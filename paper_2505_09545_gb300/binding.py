@@ -77,6 +77,7 @@ _SIGS = {
     "gdm_nearfield": ([P, C.POINTER(Problem), P, P, I64, P, C.c_int, P, P], C.c_int),
     "gdm_residual": ([P, C.POINTER(Problem), P, P, C.c_int, P, P], C.c_int),
     "gdm_cross_sections": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
+    "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, P], C.c_int),
     "gdm_cross_sections_noalloc": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
     "gdm_backward": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, C.c_int, PD, PD, P, PD, P, P, P,
                       C.POINTER(SolveInfo)], C.c_int),
@@ -207,6 +208,19 @@ class GDMProblem:
 
 def padded_lda(n_sys):
     return (n_sys + 31) // 32 * 32
+
+
+def alpha6_lorentz(ctx: Context, omega0_e, omega0_m, gamma_ev, amp_nm, wavelength, out=None):
+    """Lorentzian ED/MD polarisabilities on the GPU: (n, 6, 6) complex128 device tensor."""
+    w0e = omega0_e.contiguous()
+    w0m = omega0_m.contiguous()
+    n = w0e.shape[0]
+    if out is None:
+        out = torch.empty((n, 6, 6), dtype=torch.complex128, device=w0e.device)
+    ctx._sync_stream()
+    ctx._check(lib().gdm_alpha6_lorentz(ctx.h, n, _ptr(w0e), _ptr(w0m), float(gamma_ev), float(amp_nm),
+                                        float(wavelength), _ptr(out)), "gdm_alpha6_lorentz")
+    return out
 
 
 def incident_planewave(ctx: Context, r, wavelength, e0, khat=(0.0, 0.0, 1.0), eps_env=1.0, kind_out=3):

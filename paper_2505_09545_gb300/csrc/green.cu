@@ -111,6 +111,37 @@ __global__ void k_planewave(const double *__restrict__ r, int64_t m, double k, d
     }
 }
 
+// Lorentzian ED/MD polarisabilities: one thread per dipole writes its 6x6 block (zeros off the diagonal)
+__global__ void k_alpha6_lorentz(int64_t n, const double *__restrict__ w0e, const double *__restrict__ w0m, double g,
+                                 double a3, double w, double rad, double2 *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 a[2];
+    for (int h = 0; h < 2; h++) {
+        const double w0 = h ? w0m[i] : w0e[i];
+        // 1/alpha0 = (w0^2 - w^2 - i g w) / (a^3 w0^2); minus i rad; then invert
+        const double s = 1.0 / (a3 * w0 * w0);
+        const double re = (w0 * w0 - w * w) * s, im = -g * w * s - rad;
+        const double d = re * re + im * im;
+        a[h] = make_double2(re / d, -im / d);
+    }
+    double2 *o = out + 36 * i;
+    for (int e = 0; e < 36; e++) {
+        const int r = e / 6, c = e % 6;
+        o[e] = (r == c) ? a[r / 3] : make_double2(0.0, 0.0);
+    }
+}
+
+gdm_status gdm_launch_alpha6_lorentz(gdm_ctx *ctx, int64_t n, const double *w0e, const double *w0m, double gamma_ev,
+                                     double amp_nm, double wavelength, double *out) {
+    const double hc_ev_nm = 1239.84198;  // h c in eV nm
+    const double w = hc_ev_nm / wavelength, k = 2.0 * PI_D / wavelength;
+    k_alpha6_lorentz<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(
+        n, w0e, w0m, gamma_ev, amp_nm * amp_nm * amp_nm, w, (2.0 / 3.0) * k * k * k, (double2 *)out);
+    GDM_LAUNCHED(ctx, "alpha6_lorentz");
+    return GDM_OK;
+}
+
 gdm_status gdm_launch_planewave(gdm_ctx *ctx, const double *r, int64_t m, double k, double n_env, const double *e0,
                                 const double *khat, int n_rhs, int kind_out, double *F0) {
     double *de0;

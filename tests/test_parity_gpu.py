@@ -263,3 +263,57 @@ def test_residual_matches_oracle(G, ctx, lossy):
     scale = np.abs(pr.matrix()).max() * np.abs(F).max()
     assert np.abs(r.cpu().numpy().T - ro).max() <= 1e-13 * scale
     np.testing.assert_allclose(n2.cpu().numpy(), np.sum(np.abs(ro) ** 2, axis=0), rtol=1e-10)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "fp32", "fp64"])
+def test_metasurface_medium_several_wavelengths(G, ctx, prec):
+    """ED/MD point-dipole array with electric-magnetic cross Green blocks, 6N = 1920 (four 512-column
+    blocks, ragged tail), three wavelengths across the resonance band: refined fields and cross
+    sections against the oracle's dense solve."""
+    s = W.metasurface_edmd(nx=20, ny=16, pitch=400.0, seed=4)
+    for lam in (505.0, 620.0, 790.0):
+        prob = gpu_problem(G, s, lam)
+        F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0, kind_out=6)
+        A = G.assemble(ctx, prob, "fp64" if prec == "fp64" else "fp32")
+        F, _, info = G.solve(ctx, prob, A, F0, prec)
+        pr = oracle_problem(s, lam)
+        F0o = pr.plane_wave(s.e0)
+        Fo = pr.solve(F0o)
+        err = np.linalg.norm(F.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+        assert np.all(err < 1e-9), (lam, err, info)
+        ext, sca, ab = G.cross_sections(ctx, prob, F0, F, np.ones(s.n_rhs))
+        xo = pr.cross_sections(F0o, Fo, s.e0)
+        for g, o in zip((ext, sca, ab), xo):
+            np.testing.assert_allclose(g.cpu().numpy(), o, rtol=1e-9, atol=1e-9 * abs(xo[0]).max())
+
+
+def test_metasurface_full_size_sampled_residual(G, ctx):
+    """The full 64 x 64 metasurface (6N = 24,576) in TF32 + refinement at the shortest wavelength
+    (largest phase range): the oracle evaluates F0 - A F exactly for a seeded sample of 48 dipoles,
+    which must be at the level of the FP64 refinement (1e-11 of |F0|)."""
+    s = W.metasurface_edmd(nx=64, ny=64, pitch=400.0, seed=4)
+    lam = 500.0
+    prob = gpu_problem(G, s, lam)
+    F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0, kind_out=6)
+    A = G.assemble(ctx, prob, "fp32")
+    F, _, info = G.solve(ctx, prob, A, F0, "tf32")
+    del A
+    pr = oracle_problem(s, lam)
+    rows = np.sort(np.random.default_rng(5).choice(s.n, 48, replace=False))
+    Fh = F.cpu().numpy().T
+    F0h = F0.cpu().numpy().T
+    r = O.residual_rows(pr, F0h, Fh, rows)
+    F0s = F0h.reshape(s.n, 6, -1)[rows]
+    rel = np.linalg.norm(r.reshape(-1, r.shape[-1]), axis=0) / np.linalg.norm(F0s.reshape(-1, r.shape[-1]), axis=0)
+    assert np.all(rel < 1e-11), (rel, info)
+    assert info["rel_residual"] < 1e-11, info
+
+
+def test_alpha6_lorentz(G, ctx):
+    """Lorentzian ED/MD polarisabilities on the GPU against the oracle's, across the resonance band."""
+    s = W.metasurface_edmd(nx=13, ny=11, seed=7)
+    w0e, w0m = t(s.omega0_e), t(s.omega0_m)
+    for lam in (450.0, 496.0, 620.0, 800.0):
+        ag = G.alpha6_lorentz(ctx, w0e, w0m, s.gamma_ev, s.amp_nm, lam).cpu().numpy()
+        ao = O.lorentz_alpha6(s.omega0_e, s.omega0_m, s.gamma_ev, s.amp_nm, lam)
+        np.testing.assert_allclose(ag, ao, rtol=1e-13, atol=1e-13 * np.abs(ao).max())
