@@ -178,6 +178,48 @@ gdm_status gdm_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, voi
                      int32_t *ipiv, const double *F0, double *F, int n_rhs, const gdm_solve_opts *opts,
                      gdm_solve_info *info);
 
+/* One independent problem of a batch (a structure at one wavelength with its illuminations).
+ * All pointers except e0, khat and e0_norm2 are device memory owned by the caller. */
+typedef struct {
+    gdm_problem prob;        /* structure, wavelength (device pos / eps / alpha6) */
+    void *A;                 /* (kind*n) x lda matrix storage: complex64, complex128 for GDM_FP64 */
+    int64_t lda;             /* as for gdm_assemble */
+    int32_t *ipiv;           /* kind*n pivots (written) */
+    double *F0;              /* (kind*n) x n_rhs complex128 incident field: read, or written when e0 != NULL */
+    double *F;               /* (kind*n) x n_rhs complex128 solved fields (written) */
+    double *sigma;           /* 3 x n_rhs doubles (ext row, sca row, abs row) written, or NULL */
+    const double *e0;        /* host n_rhs x 3 complex128 plane-wave amplitudes, or NULL when F0 is given */
+    const double *khat;      /* host 3 doubles, unit propagation direction (NULL: +z), used with e0 */
+    const double *e0_norm2;  /* host n_rhs |E0|^2 for sigma when e0 is NULL */
+    int32_t n_rhs;           /* 1..64 */
+    int32_t reserved;
+} gdm_batch_item;
+
+/* The per-problem path of gdm_incident_planewave (when e0 is given), gdm_assemble,
+ * gdm_solve and gdm_cross_sections (when sigma is given) for n_items independent
+ * problems of any sizes, e.g. many structures each at its own wavelength (the paper's
+ * workloads sweep wavelengths, polarisations and geometries). The items run concurrently:
+ * the context keeps up to n_streams child contexts (own stream and scratch; 0 = 8, at most
+ * 16), each driven by a host thread that takes the largest remaining item next. Work
+ * already queued on the context stream comes first and later work on it waits for the
+ * batch. Synchronous. infos: host n_items records (may be NULL), status per item.
+ * Returns GDM_OK, or the first error; a numerical failure of one item (NOT_CONVERGED,
+ * NONFINITE, SINGULAR) is recorded in its info and the other items still run, any other
+ * error stops the batch. */
+gdm_status gdm_solve_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_item *items, int n_items,
+                             const gdm_solve_opts *opts, int n_streams, gdm_solve_info *infos);
+
+/* LU block-width autotuner (no paper counterpart). For each size class present in sizes
+ * (system dimensions kind*n; classes <= 512, 1024, ..., 32768, larger), times the
+ * factorisation of a synthetic well-conditioned complex64 matrix of the class's largest
+ * size with outer block widths 128, 256 and 512, and keeps the fastest in the context
+ * (used by gdm_solve, gdm_solve_batched and gdm_backward on this context). prec:
+ * GDM_FP32 or GDM_TF32_REFINE. Allocates one scratch matrix of the largest size for the
+ * duration of the call; synchronous. nb_out: host 8 ints (chosen width per class, 0 =
+ * untouched), may be NULL. GDM_ERR_UNSUPPORTED when the GDM_LU_NB environment variable
+ * fixes the width. */
+gdm_status gdm_autotune(gdm_ctx *ctx, gdm_precision prec, const int64_t *sizes, int n_sizes, int *nb_out);
+
 /* Residual r = F0 - A F of problem p for given fields F (FP64 result), computed matrix-free: the
  * Green dyads are regenerated for every pair (double-float arithmetic for cells, FP64 for ED/MD dipoles),
  * no stored matrix. This is the residual that drives gdm_solve's refinement (Eq. GDM_system_of_equations).

@@ -3,8 +3,9 @@
 The compute lives in the CUDA library libgdm.so (C ABI: include/gdm.h); this
 package only builds/loads it and marshals arguments (see `binding`)."""
 from . import autograd  # noqa: F401
-from .binding import (Context, GDMError, GDMProblem, alpha6_lorentz, assemble, backward, cross_sections,
-                      incident_planewave, lib, nearfield, nearfield_backward, padded_lda, residual, solve)
+from .binding import (Context, GDMError, GDMProblem, alpha6_lorentz, assemble, autotune, backward, cross_sections,
+                      incident_planewave, lib, nearfield, nearfield_backward, padded_lda, residual, solve,
+                      solve_batched)
 
-__all__ = ["Context", "GDMError", "GDMProblem", "alpha6_lorentz", "assemble", "backward", "cross_sections", "incident_planewave",
-           "lib", "nearfield", "nearfield_backward", "padded_lda", "residual", "solve"]
+__all__ = ["Context", "GDMError", "GDMProblem", "alpha6_lorentz", "assemble", "autotune", "backward", "cross_sections", "incident_planewave",
+           "lib", "nearfield", "nearfield_backward", "padded_lda", "residual", "solve", "solve_batched"]

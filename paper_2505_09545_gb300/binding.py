@@ -42,6 +42,12 @@ class Problem(C.Structure):
                 ("wavelength", C.c_double)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("prob", Problem), ("A", C.c_void_p), ("lda", C.c_int64), ("ipiv", C.c_void_p), ("F0", C.c_void_p),
+                ("F", C.c_void_p), ("sigma", C.c_void_p), ("e0", C.c_void_p), ("khat", C.c_void_p),
+                ("e0_norm2", C.c_void_p), ("n_rhs", C.c_int32), ("reserved", C.c_int32)]
+
+
 class SolveOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("flags", C.c_int32), ("tol", C.c_double)]
 
@@ -78,6 +84,8 @@ _SIGS = {
     "gdm_residual": ([P, C.POINTER(Problem), P, P, C.c_int, P, P], C.c_int),
     "gdm_cross_sections": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
     "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, P], C.c_int),
+    "gdm_solve_batched": ([P, C.c_int, P, C.c_int, P, C.c_int, P], C.c_int),
+    "gdm_autotune": ([P, C.c_int, P, C.c_int, P], C.c_int),
     "gdm_cross_sections_noalloc": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
     "gdm_backward": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, C.c_int, PD, PD, P, PD, P, P, P,
                       C.POINTER(SolveInfo)], C.c_int),
@@ -323,6 +331,61 @@ def cross_sections_noalloc(ctx: Context, prob: GDMProblem, F0, F, e0_norm2, out)
     ctx._check(lib().gdm_cross_sections_noalloc(ctx.h, C.byref(s), _ptr(F0), _ptr(F), n_rhs, npp, _ptr(out[0]),
                                                 _ptr(out[1]), _ptr(out[2])), "gdm_cross_sections_noalloc")
     return out[0], out[1], out[2]
+
+
+def solve_batched(ctx: Context, probs, e0s, precision="tf32", khat=(0.0, 0.0, 1.0), n_streams=0, with_sigma=True,
+                  max_iter=0, tol=0.0):
+    """gdm_solve_batched over independent problems: probs is a list of GDMProblem, e0s a list of (n_rhs, 3)
+    complex plane-wave amplitudes (one per problem). Allocates each item's matrix, pivots, fields and
+    cross sections; returns (F list of (n_rhs, kind*n) complex128, sigma list of (3, n_rhs) or None,
+    info list of dicts)."""
+    prec = PRECISION[precision]
+    n = len(probs)
+    items = (BatchItem * n)()
+    keep = []
+    Fs, sigs = [], []
+    ka, kp = _dbl_array(khat)
+    keep.append(ka)
+    for i, (pb, e0) in enumerate(zip(probs, e0s)):
+        e0 = np.atleast_2d(np.asarray(e0, np.complex128))
+        n_rhs = e0.shape[0]
+        ns = pb.size
+        lda = padded_lda(ns)
+        dev = pb.pos.device
+        A = torch.empty((ns, lda), dtype=torch.complex128 if precision == "fp64" else torch.complex64, device=dev)
+        ipiv = torch.empty(ns, dtype=torch.int32, device=dev)
+        F0 = torch.empty((n_rhs, ns), dtype=torch.complex128, device=dev)
+        F = torch.empty_like(F0)
+        sig = torch.empty((3, n_rhs), dtype=torch.float64, device=dev) if with_sigma else None
+        ea, ep = _dbl_array(e0.view(np.float64).reshape(-1))
+        keep += [A, ipiv, F0, ea]
+        it = items[i]
+        it.prob = pb.struct()
+        it.A, it.lda, it.ipiv = A.data_ptr(), lda, ipiv.data_ptr()
+        it.F0, it.F = F0.data_ptr(), F.data_ptr()
+        it.sigma = sig.data_ptr() if sig is not None else 0
+        it.e0 = ea.ctypes.data
+        it.khat = ka.ctypes.data
+        it.e0_norm2 = 0
+        it.n_rhs = n_rhs
+        Fs.append(F)
+        sigs.append(sig)
+    opts = SolveOpts(int(max_iter), 0, float(tol))
+    infos = (SolveInfo * n)()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_solve_batched(ctx.h, prec, items, n, C.byref(opts), int(n_streams), infos),
+               "gdm_solve_batched")
+    return Fs, sigs, [infos[i].as_dict() for i in range(n)]
+
+
+def autotune(ctx: Context, sizes, precision="tf32"):
+    """gdm_autotune: LU block width per size class for this context; returns the 8-entry table."""
+    sz = np.ascontiguousarray(np.asarray(sizes, np.int64))
+    out = (C.c_int * 8)()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_autotune(ctx.h, PRECISION[precision], sz.ctypes.data_as(C.c_void_p), len(sz), out),
+               "gdm_autotune")
+    return list(out)
 
 
 def backward(ctx: Context, prob: GDMProblem, A, ipiv, F, e0, khat=(0.0, 0.0, 1.0), gF=None, g_sigma=None,

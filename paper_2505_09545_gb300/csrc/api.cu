@@ -212,7 +212,10 @@ gdm_status gdm_create(gdm_ctx **out, int device, void *stream) {
 gdm_status gdm_destroy(gdm_ctx *ctx) {
     if (!ctx) return GDM_OK;
     cudaSetDevice(ctx->device);
+    for (int i = 0; i < ctx->npool; i++) gdm_destroy(ctx->pool[i]);
+    ctx->npool = 0;
     if (ctx->stream || ctx->ws) cudaStreamSynchronize(ctx->stream);
+    if (ctx->owns_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->dflags) cudaFree(ctx->dflags);
     if (ctx->dparams) cudaFree(ctx->dparams);
@@ -341,15 +344,10 @@ gdm_status gdm_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, 
     return gdm_launch_assemble(ctx, p, prec, A, lda);
 }
 
-gdm_status gdm_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda, int32_t *ipiv,
-                     const double *F0, double *F, int n_rhs, const gdm_solve_opts *opts, gdm_solve_info *info) {
-    GDM_TRY(check_problem(ctx, p));
-    GDM_TRY(check_prec(ctx, prec));
-    if (!A || !ipiv || !F0 || !F) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
-    if (n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n_rhs must be in [1, 64]");
-    int64_t ns = p->n * p->kind;
-    GDM_TRY(check_lda(ctx, ns, lda));
-    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+// factor (local pivots, certificate, whole-column refactor if needed) and refine; arguments validated
+gdm_status gdm_solve_core(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda, int32_t *ipiv,
+                          const double *F0, double *F, int n_rhs, const gdm_solve_opts *opts, gdm_solve_info *info) {
+    const int64_t ns = p->n * p->kind;
     gdm_solve_opts o = {0, 0, 0.0};
     if (opts) o = *opts;
     if (o.max_iter <= 0) o.max_iter = (prec == GDM_FP64) ? 3 : 40;
@@ -381,6 +379,22 @@ gdm_status gdm_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, voi
         info->refactored = refactored;
     }
     return s;
+}
+
+gdm_status gdm_check_solve_args(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
+                                const int32_t *ipiv, const double *F0, const double *F, int n_rhs) {
+    GDM_TRY(check_problem(ctx, p));
+    GDM_TRY(check_prec(ctx, prec));
+    if (!A || !ipiv || !F0 || !F) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n_rhs must be in [1, 64]");
+    return check_lda(ctx, p->n * p->kind, lda);
+}
+
+gdm_status gdm_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda, int32_t *ipiv,
+                     const double *F0, double *F, int n_rhs, const gdm_solve_opts *opts, gdm_solve_info *info) {
+    GDM_TRY(gdm_check_solve_args(ctx, p, prec, A, lda, ipiv, F0, F, n_rhs));
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return gdm_solve_core(ctx, p, prec, A, lda, ipiv, F0, F, n_rhs, opts, info);
 }
 
 gdm_status gdm_residual(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F, int n_rhs, double *r,

@@ -1,0 +1,254 @@
+// Batched solves of many independent problems of uneven size (structures, wavelengths, illuminations),
+// and the LU block-width autotuner.
+//
+// gdm_solve_batched keeps a pool of child contexts inside the caller's context, each with its own stream,
+// scratch arena, flags and pinned buffers. One host worker thread per child takes items largest first
+// (longest-processing-time order) from a shared counter and runs the whole per-item path on its child's
+// stream: plane wave, assembly, LU (in-block pivots with certificate, whole-column refactor when needed),
+// FP64-refined solve, cross sections. The small launches of many problems therefore overlap on the GPU
+// instead of running one problem at a time; the refinement's per-iteration host check of one item blocks
+// only its own worker. Events order the pool after the work already queued on the caller's stream, and
+// the caller's stream after the pool.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "gdm_internal.cuh"
+
+#define PI_D 3.14159265358979323846
+
+namespace {
+
+gdm_status ensure_pool(gdm_ctx *ctx, int want) {
+    while (ctx->npool < want) {
+        cudaStream_t st = nullptr;
+        GDM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        gdm_ctx *c = nullptr;
+        gdm_status s = gdm_create(&c, ctx->device, st);
+        if (s != GDM_OK) {
+            cudaStreamDestroy(st);
+            return gdm_fail(ctx, s, "could not create a child context for the batch");
+        }
+        c->owns_stream = true;
+        ctx->pool[ctx->npool++] = c;
+    }
+    return GDM_OK;
+}
+
+// the full per-item path on one child context
+gdm_status run_item(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it, const gdm_solve_opts *opts,
+                    gdm_solve_info *info) {
+    const gdm_problem *p = &it->prob;
+    gdm_params_reset(c);
+    if (it->e0) {
+        const double n_env = sqrt(p->eps_env);
+        const double k = n_env * 2.0 * PI_D / p->wavelength;
+        static const double zhat[3] = {0.0, 0.0, 1.0};
+        GDM_TRY(gdm_launch_planewave(c, p->pos, p->n, k, n_env, it->e0, it->khat ? it->khat : zhat, it->n_rhs,
+                                     p->kind, it->F0));
+    }
+    if (!(opts && (opts->flags & GDM_SOLVE_FACTORED))) GDM_TRY(gdm_launch_assemble(c, p, prec, it->A, it->lda));
+    gdm_status s = gdm_solve_core(c, p, prec, it->A, it->lda, it->ipiv, it->F0, it->F, it->n_rhs, opts, info);
+    if (s != GDM_OK) return s;
+    if (it->sigma) {
+        double e2[64];
+        for (int q = 0; q < it->n_rhs; q++) {
+            if (it->e0) {
+                e2[q] = 0.0;
+                for (int c3 = 0; c3 < 6; c3++) e2[q] += it->e0[6 * q + c3] * it->e0[6 * q + c3];
+            } else {
+                e2[q] = it->e0_norm2[q];
+            }
+        }
+        GDM_TRY(gdm_launch_cross_sections(c, p, it->F0, it->F, it->n_rhs, e2, it->sigma, it->sigma + it->n_rhs,
+                                          it->sigma + 2 * it->n_rhs));
+    }
+    return GDM_OK;
+}
+
+bool per_item_numeric(gdm_status s) {
+    return s == GDM_ERR_NOT_CONVERGED || s == GDM_ERR_NONFINITE || s == GDM_ERR_SINGULAR;
+}
+
+}  // namespace
+
+extern "C" {
+
+gdm_status gdm_solve_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_item *items, int n_items,
+                             const gdm_solve_opts *opts, int n_streams, gdm_solve_info *infos) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    if (n_items < 0 || (n_items > 0 && !items)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "bad item list");
+    if (n_items == 0) return GDM_OK;
+    for (int i = 0; i < n_items; i++) {
+        const gdm_batch_item *it = &items[i];
+        gdm_status s = gdm_check_solve_args(ctx, &it->prob, prec, it->A, it->lda, it->ipiv, it->F0, it->F, it->n_rhs);
+        if (s != GDM_OK) return gdm_fail(ctx, s, "item %d: %s", i, ctx->err);
+        if (it->sigma && !it->e0 && !it->e0_norm2)
+            return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "item %d: cross sections need e0 or e0_norm2", i);
+        if (it->sigma && !it->e0)
+            for (int q = 0; q < it->n_rhs; q++)
+                if (!(it->e0_norm2[q] > 0)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "item %d: |E0|^2 <= 0", i);
+    }
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    int ns = n_streams > 0 ? n_streams : 8;
+    if (ns > GDM_POOL_MAX) ns = GDM_POOL_MAX;
+    if (ns > n_items) ns = n_items;
+    GDM_TRY(ensure_pool(ctx, ns));
+
+    // largest systems first
+    std::vector<int> order(n_items);
+    for (int i = 0; i < n_items; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return items[a].prob.n * items[a].prob.kind > items[b].prob.n * items[b].prob.kind;
+    });
+    std::vector<gdm_solve_info> local((size_t)n_items);
+    gdm_solve_info *inf = infos ? infos : local.data();
+    memset(inf, 0, sizeof(gdm_solve_info) * (size_t)n_items);
+
+    // the pool starts after everything already queued on the caller's stream
+    GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, ctx->stream));
+    int64_t launches0[GDM_POOL_MAX];
+    for (int w = 0; w < ns; w++) {
+        gdm_ctx *c = ctx->pool[w];
+        memcpy(c->nb_table, ctx->nb_table, sizeof(ctx->nb_table));
+        c->err[0] = 0;
+        launches0[w] = c->launches;
+        GDM_CUDA_TRY(ctx, cudaStreamWaitEvent(c->stream, ctx->ev2, 0));
+    }
+
+    std::atomic<int> next(0);
+    std::atomic<bool> stop(false);
+    std::mutex mu;
+    gdm_status first = GDM_OK;
+    int first_item = -1;
+    char first_msg[sizeof(ctx->err)] = {0};
+    auto worker = [&](int w) {
+        gdm_ctx *c = ctx->pool[w];
+        if (cudaSetDevice(ctx->device) != cudaSuccess) {
+            stop = true;
+            return;
+        }
+        for (;;) {
+            if (stop.load()) break;
+            const int k = next.fetch_add(1);
+            if (k >= n_items) break;
+            const int i = order[k];
+            gdm_status s = run_item(c, prec, &items[i], opts, &inf[i]);
+            inf[i].status = s;
+            if (s != GDM_OK) {
+                std::lock_guard<std::mutex> lock(mu);
+                if (first == GDM_OK || (per_item_numeric(first) && !per_item_numeric(s))) {
+                    first = s;
+                    first_item = i;
+                    memcpy(first_msg, c->err, sizeof(first_msg));
+                }
+                // numerical failures stay with their item; anything else ends the batch
+                if (!per_item_numeric(s)) stop = true;
+            }
+        }
+    };
+    std::vector<std::thread> threads;
+    threads.reserve(ns);
+    for (int w = 0; w < ns; w++) threads.emplace_back(worker, w);
+    for (auto &t : threads) t.join();
+
+    // the caller's stream continues after the pool
+    for (int w = 0; w < ns; w++) {
+        gdm_ctx *c = ctx->pool[w];
+        ctx->launches += c->launches - launches0[w];
+        GDM_CUDA_TRY(ctx, cudaEventRecord(c->ev2, c->stream));
+        GDM_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, c->ev2, 0));
+    }
+    if (first != GDM_OK) return gdm_fail(ctx, first, "item %d: %s", first_item, first_msg);
+    return GDM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+// deterministic well-conditioned test matrix: diagonal 4 + hashed entries in [-0.5, 0.5]^2 / sqrt(n)
+__global__ void k_tune_matrix(float2 *A, int64_t n, int64_t lda, float scale) {
+    const int64_t total = n * lda;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / lda, r = e % lda;
+        uint64_t h = (uint64_t)e * 0x9E3779B97F4A7C15ull;
+        h ^= h >> 31;
+        h *= 0xBF58476D1CE4E5B9ull;
+        h ^= h >> 29;
+        float re = ((float)(h & 0xffffff) / 16777216.0f - 0.5f) * scale;
+        float im = ((float)((h >> 24) & 0xffffff) / 16777216.0f - 0.5f) * scale;
+        if (r == c) re += 4.0f;
+        A[e] = (r < n) ? make_float2(re, im) : make_float2(0.f, 0.f);
+    }
+}
+}  // namespace
+
+extern "C" gdm_status gdm_autotune(gdm_ctx *ctx, gdm_precision prec, const int64_t *sizes, int n_sizes,
+                                   int *nb_out) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    if (!sizes || n_sizes < 1) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "no sizes");
+    if (prec != GDM_FP32 && prec != GDM_TF32_REFINE)
+        return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "the block width is tuned for the FP32 precisions only");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    int64_t cls_max[GDM_NB_CLASSES] = {0};
+    for (int i = 0; i < n_sizes; i++) {
+        if (sizes[i] < 1) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "sizes must be >= 1");
+        const int c = gdm_size_class(sizes[i]);
+        cls_max[c] = std::max(cls_max[c], sizes[i]);
+    }
+    int64_t nmax = 0;
+    for (int c = 0; c < GDM_NB_CLASSES; c++) nmax = std::max(nmax, cls_max[c]);
+    const int64_t ldmax = (nmax + 31) / 32 * 32;
+    float2 *A = nullptr;
+    int32_t *ipiv = nullptr;
+    GDM_CUDA_TRY(ctx, cudaMalloc(&A, sizeof(float2) * nmax * ldmax));
+    cudaError_t e = cudaMalloc(&ipiv, sizeof(int32_t) * nmax);
+    if (e != cudaSuccess) {
+        cudaFree(A);
+        return gdm_fail(ctx, GDM_ERR_OOM, "autotune buffers");
+    }
+    gdm_status st = GDM_OK;
+    const int cand[3] = {128, 256, 512};
+    const char *env = getenv("GDM_LU_NB");
+    if (env) st = gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "GDM_LU_NB is set: it overrides any tuned width");
+    for (int c = 0; c < GDM_NB_CLASSES && st == GDM_OK; c++) {
+        const int64_t n = cls_max[c];
+        if (!n) continue;
+        const int64_t lda = (n + 31) / 32 * 32;
+        float best = 1e30f;
+        int best_nb = 512;
+        for (int j = 0; j < 3 && st == GDM_OK; j++) {
+            if (cand[j] > 2 * n && j > 0) break;
+            ctx->nb_table[c] = cand[j];
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && st == GDM_OK; rep++) {
+                k_tune_matrix<<<4 * ctx->sm_count, 256, 0, ctx->stream>>>(A, n, lda, 1.0f / sqrtf((float)n));
+                if (cudaGetLastError() != cudaSuccess) {
+                    st = gdm_fail(ctx, GDM_ERR_CUDA, "autotune matrix");
+                    break;
+                }
+                if (cudaEventRecord(ctx->ev0, ctx->stream) != cudaSuccess) st = GDM_ERR_CUDA;
+                if (st == GDM_OK) st = gdm_lu_factor(ctx, prec, A, n, lda, ipiv, 0, nullptr);
+                if (st == GDM_OK && cudaEventRecord(ctx->ev1, ctx->stream) != cudaSuccess) st = GDM_ERR_CUDA;
+                if (st == GDM_OK && cudaEventSynchronize(ctx->ev1) != cudaSuccess) st = GDM_ERR_CUDA;
+                if (st == GDM_OK) cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            }
+            if (st == GDM_OK && ms < best) {
+                best = ms;
+                best_nb = cand[j];
+            }
+        }
+        ctx->nb_table[c] = best_nb;
+    }
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(A);
+    cudaFree(ipiv);
+    if (st != GDM_OK) return st;
+    if (nb_out)
+        for (int c = 0; c < GDM_NB_CLASSES; c++) nb_out[c] = ctx->nb_table[c];
+    return GDM_OK;
+}

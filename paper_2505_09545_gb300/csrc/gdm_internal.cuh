@@ -10,6 +10,8 @@
 #include "../../include/gdm.h"
 
 // ------------------------------------------------------------------ context
+#define GDM_NB_CLASSES 8  // system size classes: <= 512, 1024, 2048, ..., 32768, larger
+#define GDM_POOL_MAX 16
 struct gdm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -39,6 +41,12 @@ struct gdm_ctx {
     int ph_n = 0;
     cudaEvent_t *ph_ev = nullptr;  // 2 * GDM_PH_MAX events
     int *ph_id = nullptr;
+    // LU block width per size class (0 = built-in default), set by gdm_autotune
+    int nb_table[GDM_NB_CLASSES] = {0};
+    // child contexts of gdm_solve_batched (each owns its stream)
+    gdm_ctx *pool[GDM_POOL_MAX] = {nullptr};
+    int npool = 0;
+    bool owns_stream = false;
 };
 #define GDM_PH_MAX 32768
 #define GDM_PROF_MAX 4096
@@ -206,7 +214,8 @@ gdm_status gdm_trsv_persistent(gdm_ctx *ctx, gdm_precision prec, const void *A, 
 size_t gdm_trsv_inv_bytes(int64_t n);
 gdm_status gdm_trsv_prepare(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda,
                             const int32_t *ipiv, void *dinv);
-int gdm_lu_block(gdm_precision prec);
+int gdm_lu_block(const gdm_ctx *ctx, gdm_precision prec, int64_t n);
+int gdm_size_class(int64_t n);
 // refine.cu
 gdm_status gdm_refined_solve(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
                              const int32_t *ipiv, const double *rhs, double *X, int n_rhs, int adjoint,
@@ -223,3 +232,10 @@ gdm_status gdm_launch_nearfield_backward(gdm_ctx *ctx, const gdm_problem *p, con
 
 // problem helpers
 static inline double gdm_k0(const gdm_problem *p) { return 2.0 * 3.14159265358979323846 / p->wavelength; }
+
+// shared by gdm_solve and gdm_solve_batched (defined in the C-ABI translation unit)
+extern "C" __attribute__((visibility("hidden"))) gdm_status gdm_check_solve_args(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
+                                const int32_t *ipiv, const double *F0, const double *F, int n_rhs);
+extern "C" __attribute__((visibility("hidden"))) gdm_status gdm_solve_core(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda,
+                                     int32_t *ipiv, const double *F0, double *F, int n_rhs,
+                                     const gdm_solve_opts *opts, gdm_solve_info *info);

@@ -27,9 +27,11 @@
 gdm_status gdm_tc_trailing_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t b0,
                                   int64_t nb, void *ws, size_t ws_bytes);
 size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec);
+gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_t ldc, int64_t r0, int64_t c0,
+                             const float2 *L, int64_t ldl, const float2 *U, int64_t ldu, int64_t u_r0, int64_t u_c0,
+                             int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof);
 gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t r0, int64_t c0,
                          int64_t k0, int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof);
-int gdm_lu_block(gdm_precision prec);
 
 // ------------------------------------------------------------------ bounded grid barrier
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -455,6 +457,90 @@ __global__ void __launch_bounds__(128) k_panel_local_f32(float2 *__restrict__ A,
     panel_store_diag_last(A, lda, c0, w, &U[0][0], NBP + 1, flags);
 }
 
+// ------------------------------------------------------------------ block operator for the U12 row block
+// For the outer block [b0, b0+nb) (nb a multiple of 32, pivots of each 32-row panel inside that panel),
+// form negM = -(L_S^{-1} P_S ... L_1^{-1} P_1) restricted to the block's rows: the product form the
+// factorisation produced (each panel's L below its diagonal block is stored in the row order before the
+// later panels' interchanges). Then U12 = -negM A12 for the block's rows of the trailing columns. CTA
+// (g, h) forms columns 32 g + 8 h .. + 8 of the operator by applying the panels to those columns of I in
+// shared memory; panels before g leave them untouched (their rows are zero there).
+__global__ void __launch_bounds__(512) k_block_linv(const float2 *__restrict__ A, int64_t lda, int64_t b0, int nb,
+                                                    const int32_t *__restrict__ ipiv, float2 *__restrict__ negM) {
+    extern __shared__ __align__(16) float2 X[];  // X[c * nb + r], 8 columns
+    __shared__ float2 Lpp[32][33];
+    const int g = blockIdx.x >> 2, h = blockIdx.x & 3;
+    const int col0 = 32 * g + 8 * h;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < 8 * nb; e += blockDim.x) {
+        const int c = e / nb, r = e % nb;
+        X[e] = make_float2(r == col0 + c ? 1.f : 0.f, 0.f);
+    }
+    const float2 *D = A + b0 * lda + b0;  // block-local view: D[r + c * lda]
+    for (int q0 = 32 * g; q0 < nb; q0 += 32) {
+        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+            const int i = e & 31, j = e >> 5;
+            Lpp[i][j] = (i > j) ? D[(int64_t)(q0 + j) * lda + q0 + i] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        // the panel's interchanges (inside its 32 rows), one thread per column
+        if (tid < 8) {
+            float2 *x = X + tid * nb;
+            for (int t = 0; t < 32; t++) {
+                const int r2 = (int)(ipiv[b0 + q0 + t] - b0);
+                if (r2 != q0 + t && r2 >= q0 && r2 < q0 + 32) {
+                    const float2 a = x[q0 + t];
+                    x[q0 + t] = x[r2];
+                    x[r2] = a;
+                }
+            }
+        }
+        __syncthreads();
+        // unit-lower solve with the diagonal block: warp c takes column c, lane = row inside the panel
+        if (warp < 8) {
+            float2 *x = X + warp * nb + q0;
+            float2 v = x[lane];
+            for (int t = 0; t < 31; t++) {
+                const float2 xt = make_float2(__shfl_sync(0xffffffffu, v.x, t), __shfl_sync(0xffffffffu, v.y, t));
+                if (lane > t) cfms(v, Lpp[lane][t], xt);
+            }
+            x[lane] = v;
+        }
+        __syncthreads();
+        // rows of the later panels: x_r -= L[r, panel] x_panel (one thread per row)
+        for (int r = q0 + 32 + tid; r < nb; r += blockDim.x) {
+            float2 l[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++) l[j] = D[(int64_t)(q0 + j) * lda + r];
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                float2 acc = X[c * nb + r];
+                const float2 *xp = X + c * nb + q0;
+#pragma unroll
+                for (int j = 0; j < 32; j++) cfms(acc, l[j], xp[j]);
+                X[c * nb + r] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < 8 * nb; e += blockDim.x) {
+        const int c = e / nb, r = e % nb;
+        const float2 v = X[e];
+        negM[(int64_t)(col0 + c) * nb + r] = make_float2(-v.x, -v.y);
+    }
+}
+
+// T[i + c * nb] = A[b0 + i, c0 + c] and zero the source (the U12 GEMM accumulates into it)
+__global__ void k_gather_zero(float2 *__restrict__ A, int64_t lda, int64_t b0, int64_t c0, int nb, int64_t nc,
+                              float2 *__restrict__ T) {
+    const int64_t total = (int64_t)nb * nc;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / nb, i = e % nb;
+        float2 *a = A + (c0 + c) * lda + b0 + i;
+        T[e] = *a;
+        *a = make_float2(0.f, 0.f);
+    }
+}
+
 // ------------------------------------------------------------------ row interchanges
 // Apply pivots ipiv[k_begin..k_end) in order to columns [cb, ce) (one thread per column).
 template <class C>
@@ -657,10 +743,19 @@ static gdm_status trsm_small(gdm_ctx *ctx, C *A, int64_t lda, int64_t c0, int w,
     return GDM_OK;
 }
 
-int gdm_lu_block(gdm_precision prec) {
+int gdm_size_class(int64_t n) {
+    int c = 0;
+    while (c < GDM_NB_CLASSES - 1 && n > ((int64_t)512 << c)) c++;
+    return c;
+}
+
+// outer block width of the LU: FP64 128 (SIMT updates); otherwise GDM_LU_NB if set, else the context's
+// autotuned width for this size class, else 512
+int gdm_lu_block(const gdm_ctx *ctx, gdm_precision prec, int64_t n) {
     if (prec == GDM_FP64) return 128;
     const char *e = getenv("GDM_LU_NB");
-    int nb = e ? atoi(e) : 512;
+    int nb = e ? atoi(e) : 0;
+    if (!nb && ctx) nb = ctx->nb_table[gdm_size_class(n)];
     if (nb < 64 || nb > 1024 || nb % 32) nb = 512;
     return nb;
 }
@@ -702,15 +797,20 @@ template <class C>
 static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n, int64_t lda, int32_t *ipiv,
                               int global_pivot, unsigned *growth) {
     // whole-column pivoting moves rows below the block, so it factors one 32-column panel per block
-    const int NB = global_pivot ? NBP : gdm_lu_block(prec);
+    const int NB = global_pivot ? NBP : gdm_lu_block(ctx, prec, n);
     int pmax = ctx->sm_count;
     // scratch: panel candidates + tensor-core operand buffers
     size_t pbytes = ScratchCarver::round(2 * pmax * sizeof(double)) + ScratchCarver::round(2 * pmax * sizeof(int64_t)) +
                     ScratchCarver::round((size_t)2 * pmax * NBP * sizeof(C)) +
                     ScratchCarver::round(2 * NBP * sizeof(C));
     size_t tcbytes = (sizeof(C) == 8) ? gdm_tc_workspace_bytes(n, NB, prec) : 0;
+    // U12 through the block operator (tensor cores, local pivots): operator and gathered row block
+    const bool u12_op = sizeof(C) == 8 && tcbytes && !global_pivot && NB <= 512 && !getenv("GDM_U12_PANELS");
+    size_t opbytes = u12_op ? ScratchCarver::round((size_t)NB * NB * sizeof(C)) +
+                                  ScratchCarver::round((size_t)NB * n * sizeof(C))
+                            : 0;
     void *ws;
-    GDM_TRY(gdm_scratch(ctx, pbytes + tcbytes + 1024, &ws));
+    GDM_TRY(gdm_scratch(ctx, pbytes + tcbytes + opbytes + 1024, &ws));
     ScratchCarver sc(ws);
     PanelScratch<C> ps;
     ps.cand_val = sc.take<double>(2 * pmax);
@@ -718,6 +818,8 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
     ps.cand_vals = sc.take<C>((size_t)2 * pmax * NBP);
     ps.top_row = sc.take<C>(2 * NBP);
     void *tcws = tcbytes ? sc.take<char>(tcbytes) : nullptr;
+    float2 *negM = u12_op ? sc.take<float2>((size_t)NB * NB) : nullptr;
+    float2 *T12 = u12_op ? sc.take<float2>((size_t)NB * n) : nullptr;
     for (int64_t b0 = 0; b0 < n; b0 += NB) {
         int64_t nb = n - b0 < NB ? n - b0 : NB;
         int64_t be = b0 + nb;
@@ -739,7 +841,32 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
                 GDM_TRY(gdm_phase_end(ctx, GDM_PH_INBLOCK));
             }
         }
-        if (be < n) {
+        if (be < n && u12_op) {
+            // U12 = M A12 with the block operator M = L_S^{-1} P_S ... L_1^{-1} P_1 (one tensor-core GEMM)
+            GDM_TRY(gdm_phase_begin(ctx, GDM_PH_U12));
+            const int nbi = (int)nb;
+            const size_t sm = (size_t)8 * nbi * sizeof(float2);
+            static bool attr = false;
+            if (!attr) {
+                GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_block_linv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)((size_t)8 * 512 * sizeof(float2))));
+                attr = true;
+            }
+            // 8 warps at least (one per operator column in the panel solve), one thread per row up to 512
+            const int bthreads = nbi < 256 ? 256 : (nbi > 512 ? 512 : nbi);
+            k_block_linv<<<(unsigned)(nbi / 32 * 4), bthreads, sm, ctx->stream>>>(
+                (const float2 *)A, lda, b0, nbi, ipiv, negM);
+            GDM_LAUNCHED(ctx, "block_linv");
+            const int64_t nc = n - be;
+            const int64_t tot = (int64_t)nbi * nc;
+            unsigned gb = (unsigned)((tot + 255) / 256);
+            if (gb > (unsigned)(8 * ctx->sm_count)) gb = 8 * ctx->sm_count;
+            k_gather_zero<<<gb, 256, 0, ctx->stream>>>((float2 *)A, lda, b0, be, nbi, nc, T12);
+            GDM_LAUNCHED(ctx, "gather_zero");
+            GDM_TRY(gdm_tc_update_ext(ctx, prec, (float2 *)A, lda, b0, be, negM, nbi, T12, nbi, 0, 0, nbi, nc, nbi,
+                                      tcws, tcbytes, 0));
+            GDM_TRY(gdm_phase_end(ctx, GDM_PH_U12));
+        } else if (be < n) {
             // U12 = L11^{-1} A12 panel by panel; each panel's interchanges reach the trailing columns just
             // before its triangular solve (L rows of later panels are still in their pre-interchange order)
             for (int64_t c0 = b0; c0 < be; c0 += NBP) {
@@ -756,6 +883,8 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
                     GDM_TRY(gdm_phase_end(ctx, GDM_PH_U12));
                 }
             }
+        }
+        if (be < n) {
             // A22 -= A21 U12
             GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRAILING));
             gdm_status s = GDM_ERR_UNSUPPORTED;
@@ -913,10 +1042,8 @@ __global__ void k_gemv_h_sub(const C *__restrict__ A, int64_t lda, int64_t r0, i
 template <class C>
 static gdm_status lu_solve_t(gdm_ctx *ctx, gdm_precision prec, const C *A, int64_t n, int64_t lda,
                              const int32_t *ipiv, C *B, int64_t ldb, int n_rhs, int conj_trans) {
-    const int NB = gdm_lu_block(prec);
     const int wpb = 4;
     unsigned nbq = (unsigned)((n_rhs + wpb - 1) / wpb);
-    (void)NB;
     if (!conj_trans) {
         for (int64_t b0 = 0; b0 < n; b0 += NBP) {
             int64_t be = b0 + NBP < n ? b0 + NBP : n;

@@ -533,17 +533,19 @@ size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec) {
     return prec == GDM_FP32 ? 2 * lx + 2 * u + 4096 : lx + 4096;
 }
 
-// General update of a sub-block of the complex64 matrix A (n x n, lda):
-//   A[r0 : r0+Mc, c0 : c0+Nc] -= A[r0 : r0+Mc, k0 : k0+Kc] * A[k0 : k0+Kc, c0 : c0+Nc].
+// C[r0 : r0+Mc, c0 : c0+Nc] -= L[0 : Mc, 0 : Kc] U[u_r0 : u_r0+Kc, u_c0 : u_c0+Nc] with complex64 operands in
+// column-major storage (C with ldc, L with ldl, U with ldu); C may alias L or U only as disjoint blocks.
 // The C chunks are clipped to the sub-block through the tensor-map extents (rows < r0+Mc, columns
 // < c0+Nc), so columns and rows outside it are never written. prof = 1 records the launch as the
 // factorisation's dominant kernel (gdm_profile_enable).
-gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t r0, int64_t c0,
-                         int64_t k0, int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof) {
+gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_t ldc, int64_t r0, int64_t c0,
+                             const float2 *L, int64_t ldl, const float2 *U, int64_t ldu, int64_t u_r0, int64_t u_c0,
+                             int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof) {
     if (prec == GDM_FP64) return GDM_ERR_UNSUPPORTED;
     if (Mc <= 0 || Nc <= 0 || Kc <= 0) return GDM_OK;
     if (getenv("GDM_TC_DISABLE")) return GDM_ERR_UNSUPPORTED;
-    if (((uintptr_t)A & 15) || (lda & 1) || (r0 & 1) || (k0 & 1)) return GDM_ERR_UNSUPPORTED;
+    if (((uintptr_t)C & 15) || (ldc & 1) || (r0 & 1) || ((uintptr_t)U & 15) || (ldu & 1) || (u_r0 & 1))
+        return GDM_ERR_UNSUPPORTED;
     const int split = (prec == GDM_FP32) ? 3 : 1;
     const int M = (int)(2 * Mc), N = (int)Nc, K = (int)(2 * Kc);
     ScratchCarver sc(ws);
@@ -552,22 +554,21 @@ gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t ld
     float *Uhi = split == 3 ? sc.take<float>((size_t)N * K) : nullptr;
     float *Ulo = split == 3 ? sc.take<float>((size_t)N * K) : nullptr;
     if (sc.off > ws_bytes) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "tensor-core workspace too small");
-    const float2 *L = A + k0 * lda + r0;
     dim3 pg((unsigned)((Mc + 31) / 32), (unsigned)((Kc + 31) / 32));
     if (split == 3) {
-        k_prep_lx<3><<<pg, 256, 0, ctx->stream>>>(L, lda, (int)Mc, (int)Kc, Lx, Llo);
+        k_prep_lx<3><<<pg, 256, 0, ctx->stream>>>(L, ldl, (int)Mc, (int)Kc, Lx, Llo);
         GDM_LAUNCHED(ctx, "prep_lx");
         int64_t cnt = Kc * Nc;
-        k_split_u<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(A + c0 * lda + k0, lda, (int)Kc, (int)Nc, Uhi,
-                                                                          Ulo);
+        k_split_u<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(U + u_c0 * ldu + u_r0, ldu, (int)Kc, (int)Nc,
+                                                                          Uhi, Ulo);
         GDM_LAUNCHED(ctx, "split_u");
     } else {
-        k_prep_lx<1><<<pg, 256, 0, ctx->stream>>>(L, lda, (int)Mc, (int)Kc, Lx, nullptr);
+        k_prep_lx<1><<<pg, 256, 0, ctx->stream>>>(L, ldl, (int)Mc, (int)Kc, Lx, nullptr);
         GDM_LAUNCHED(ctx, "prep_lx");
     }
     CUtensorMap ta0, ta1, tb0, tb1, tc;
     bool ok = make_map(&ta0, Lx, K, M, K, BM) &&
-              make_map_c(&tc, (const float *)A, (uint64_t)(2 * (r0 + Mc)), (uint64_t)(c0 + Nc), (uint64_t)2 * lda);
+              make_map_c(&tc, (const float *)C, (uint64_t)(2 * (r0 + Mc)), (uint64_t)(c0 + Nc), (uint64_t)2 * ldc);
     int slot = -1;
     double fl = 8.0 * (double)Mc * (double)Nc * (double)Kc;
     double by = 16.0 * (double)Mc * Nc + 4.0 * ((double)M * K + (double)N * K) * (split == 3 ? 2 : 1);
@@ -578,15 +579,25 @@ gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t ld
         if (prof) GDM_TRY(gdm_prof_begin(ctx, &slot));
         GDM_TRY(launch_update<128, 3>(ctx, ta0, ta1, tb0, tb1, tc, (int)(2 * r0), (int)c0, M, N, K, 0, 0));
     } else {
-        // U straight from the matrix: real rows [2 k0, 2 k0 + K) of columns [c0, c0 + Nc) (zero beyond)
-        ok = ok && make_map(&tb0, (const float *)A, (uint64_t)2 * lda, (uint64_t)(c0 + Nc), (uint64_t)2 * lda, 256);
+        // U straight from its storage: real rows [2 u_r0, 2 u_r0 + K) of columns [u_c0, u_c0 + Nc) (zero beyond)
+        ok = ok && make_map(&tb0, (const float *)U, (uint64_t)2 * ldu, (uint64_t)(u_c0 + Nc), (uint64_t)2 * ldu, 256);
         if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         if (prof) GDM_TRY(gdm_prof_begin(ctx, &slot));
-        GDM_TRY(launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * k0),
-                                      (int)c0));
+        GDM_TRY(launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * u_r0),
+                                      (int)u_c0));
     }
     if (prof) GDM_TRY(gdm_prof_end(ctx, slot, fl, by));
     return GDM_OK;
+}
+
+// General update of a sub-block of the complex64 matrix A (n x n, lda):
+//   A[r0 : r0+Mc, c0 : c0+Nc] -= A[r0 : r0+Mc, k0 : k0+Kc] * A[k0 : k0+Kc, c0 : c0+Nc].
+gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t r0, int64_t c0,
+                         int64_t k0, int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof) {
+    (void)n;
+    if ((k0 & 1)) return GDM_ERR_UNSUPPORTED;
+    return gdm_tc_update_ext(ctx, prec, A, lda, r0, c0, A + k0 * lda + r0, lda, A, lda, k0, c0, Mc, Nc, Kc, ws,
+                             ws_bytes, prof);
 }
 
 // A22 -= A21 U12 for the block [b0, b0+nb) of the complex64 matrix A (n x n, lda).
