@@ -461,6 +461,79 @@ __global__ void __launch_bounds__(ASM_TI) k_assemble6(typename cplx<T>::t *__res
     }
 }
 
+// kind 3, complex64 output, stores through the bulk-copy engine. Block (128 targets i) x (8 sources j):
+// the CTA builds its 384-row x 24-column tile of A in shared memory (each thread its 3x3 blocks, plain
+// shared stores), then one cp.async.bulk per column moves the 3 KB column segment to HBM. A warp's
+// direct stores of interleaved 3-row blocks would touch every 32-byte sector three times through L1.
+#define ASB_TI 128
+#define ASB_TJ 8
+#define ASB_ROWS (3 * ASB_TI)
+__global__ void __launch_bounds__(ASB_TI) k_assemble3_f32_bulk(float2 *__restrict__ A, int64_t lda, int64_t n,
+                                                              const DipF *__restrict__ dip, float khi, float klo,
+                                                              float inv_eps) {
+    extern __shared__ __align__(128) float2 stile[];  // [3 * ASB_TJ columns][ASB_ROWS rows]
+    __shared__ DipF sj[ASB_TJ];
+    const int64_t i0 = (int64_t)blockIdx.x * ASB_TI, j0 = (int64_t)blockIdx.y * ASB_TJ;
+    if (threadIdx.x < ASB_TJ && j0 + threadIdx.x < n) sj[threadIdx.x] = dip[j0 + threadIdx.x];
+    __syncthreads();
+    const int64_t i = i0 + threadIdx.x;
+    const int jn = (int)min((int64_t)ASB_TJ, n - j0);
+    const int ni = (int)min((int64_t)ASB_TI, n - i0);
+    if (i < n) {
+        const DipF ti = dip[i];
+        const ff kff = {khi, klo};
+        const float kf = khi, k2 = khi * khi;
+        for (int jj = 0; jj < jn; jj++) {
+            float2 *col = stile + (3 * jj) * ASB_ROWS + 3 * threadIdx.x;
+            if (j0 + jj == i) {
+                const float2 dg = sj[jj].diag, z = make_float2(0.f, 0.f);
+                col[0] = dg; col[1] = z; col[2] = z;
+                col += ASB_ROWS;
+                col[0] = z; col[1] = dg; col[2] = z;
+                col += ASB_ROWS;
+                col[0] = z; col[1] = z; col[2] = dg;
+                continue;
+            }
+            PairG<float> g = pair_green_f32(ti, sj[jj], kff, kf, k2, 0.f, inv_eps, false);
+            const float2 al = sj[jj].alpha;
+            float2 na = cmul(g.a, al), nb = cmul(g.b, al);
+            na = make_float2(-na.x, -na.y);
+            nb = make_float2(-nb.x, -nb.y);
+            const float u[3] = {g.ux, g.uy, g.uz};
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                float2 v0 = cscale(nb, u[0] * u[b]);
+                float2 v1 = cscale(nb, u[1] * u[b]);
+                float2 v2 = cscale(nb, u[2] * u[b]);
+                if (b == 0) v0 = cadd(v0, na);
+                if (b == 1) v1 = cadd(v1, na);
+                if (b == 2) v2 = cadd(v2, na);
+                col[0] = v0; col[1] = v1; col[2] = v2;
+                col += ASB_ROWS;
+            }
+        }
+    }
+    // shared-memory writes of the generic proxy must be visible to the bulk-copy (async) proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    const int rows = 3 * ni;
+    const int rows16 = rows & ~1;  // a whole number of 16-byte units
+    if ((int)threadIdx.x < 3 * jn) {
+        const int c = threadIdx.x;
+        float2 *dst = A + (3 * j0 + c) * lda + 3 * i0;
+        const float2 *src = stile + c * ASB_ROWS;
+        if (rows16 > 0) {
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                         "r"((uint32_t)__cvta_generic_to_shared(src)), "r"((uint32_t)(rows16 * sizeof(float2)))
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+        if (rows & 1) dst[rows - 1] = src[rows - 1];
+        // the shared tile must stay until the engine has read it
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+}
+
 gdm_status gdm_launch_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda) {
     int64_t n = p->n;
     double k0 = gdm_k0(p);
@@ -489,10 +562,24 @@ gdm_status gdm_launch_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision
         } else {
             k_prep_dipf<<<nb, bs, 0, ctx->stream>>>(p->pos, (const double2 *)p->eps, n, p->eps_env, d3_4pi, dipf);
             GDM_LAUNCHED(ctx, "prep_dipf");
-            dim3 grid((unsigned)((n + ASM_TI - 1) / ASM_TI), (unsigned)((n + ASM_TJ3 - 1) / ASM_TJ3));
-            k_assemble3_f32<<<grid, blk, 0, ctx->stream>>>((float2 *)A, lda, n, dipf, khi, klo,
-                                                          (float)(1.0 / p->eps_env));
-            GDM_LAUNCHED(ctx, "assemble3_f32");
+            if (((uintptr_t)A & 15) == 0 && (lda & 1) == 0 && !getenv("GDM_ASSEMBLE_DIRECT")) {
+                const int smem = 3 * ASB_TJ * ASB_ROWS * (int)sizeof(float2);
+                static bool attr = false;
+                if (!attr) {
+                    GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_assemble3_f32_bulk,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                    attr = true;
+                }
+                dim3 grid((unsigned)((n + ASB_TI - 1) / ASB_TI), (unsigned)((n + ASB_TJ - 1) / ASB_TJ));
+                k_assemble3_f32_bulk<<<grid, ASB_TI, smem, ctx->stream>>>((float2 *)A, lda, n, dipf, khi, klo,
+                                                                         (float)(1.0 / p->eps_env));
+                GDM_LAUNCHED(ctx, "assemble3_f32_bulk");
+            } else {
+                dim3 grid((unsigned)((n + ASM_TI - 1) / ASM_TI), (unsigned)((n + ASM_TJ3 - 1) / ASM_TJ3));
+                k_assemble3_f32<<<grid, blk, 0, ctx->stream>>>((float2 *)A, lda, n, dipf, khi, klo,
+                                                              (float)(1.0 / p->eps_env));
+                GDM_LAUNCHED(ctx, "assemble3_f32");
+            }
         }
     } else {
         dim3 grid((unsigned)((n + ASM_TI - 1) / ASM_TI), (unsigned)((n + ASM_TJ6 - 1) / ASM_TJ6));
