@@ -351,6 +351,13 @@ __global__ void __launch_bounds__(256) k_panel_local(C *__restrict__ A, int64_t 
     panel_store_diag_last(A, lda, c0, w, &D[0][0], NBP + 1, flags);
 }
 
+// 1/x for normal positive x: approximate reciprocal + one Newton step (relative error ~1 ulp)
+__device__ __forceinline__ float rcp_nr(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r * fmaf(-x, r, 2.0f);
+}
+
 // FP32 version of the same panel with the diagonal block held in registers: lane q of warp 0 keeps row q
 // of D. Instead of moving rows, each lane tracks the position its row occupies in the LAPACK-style swap
 // sequence (pos), so the pivot of step t is the largest |re|+|im| in column t among the rows not yet
@@ -408,10 +415,12 @@ __global__ void __launch_bounds__(128) k_panel_local_f32(float2 *__restrict__ A,
                     float2 l = make_float2(0.f, 0.f);
                     const float sc = fmaxf(fabsf(piv.x), fabsf(piv.y));
                     if (sc > 0.f) {
-                        // 1/piv = conj(piv/sc) / (|piv/sc|^2 sc), scaled against overflow
-                        const float is = __frcp_rn(sc);
+                        // 1/piv = conj(piv/sc) / (|piv/sc|^2 sc), scaled against overflow; reciprocals from
+                        // the hardware approximation refined by one Newton step (on the critical path of
+                        // every pivot step, so no division subroutine here)
+                        const float is = rcp_nr(sc);
                         const float ax = piv.x * is, ay = piv.y * is;
-                        const float rr = __frcp_rn(fmaf(ax, ax, ay * ay) * sc);
+                        const float rr = rcp_nr(fmaf(ax, ax, ay * ay) * sc);
                         l = cmul(row[t], make_float2(ax * rr, -ay * rr));
                     }
                     row[t] = l;
