@@ -405,7 +405,7 @@ gdm_status gdm_residual(gdm_ctx *ctx, const gdm_problem *p, const double *F0, co
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     gdm_params_reset(ctx);
     const int64_t cnt = p->n * p->kind * n_rhs;
-    const bool ff = (p->kind == 3 && !getenv("GDM_RESIDUAL_FP64"));
+    const bool ff = !getenv("GDM_RESIDUAL_FP64");
     size_t pb = gdm_green_partial_bytes(ctx, p->n, p->n, p->kind);
     size_t need = ScratchCarver::round(cnt * sizeof(double2)) + ScratchCarver::round(pb) +
                   ScratchCarver::round(gdm_ff_scratch_bytes(p->n)) + 1024;

@@ -810,7 +810,7 @@ gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const doub
     for (int q0 = 0; q0 < n_rhs; q0 += 2) {
         int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
         int nc;
-        if (kind == 3 && ffws) {
+        if (ffws) {
             int64_t chunk;
             green_grid(ctx, n, n, &chunk, &nc);
             GDM_TRY(gdm_launch_green_sum_ff(ctx, p, Pbuf, q0, nr, chunk, nc, ffws, partial, ff_prepare && q0 == 0));

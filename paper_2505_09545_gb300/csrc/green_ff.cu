@@ -1,4 +1,4 @@
-// Matrix-free refinement residual in double-float arithmetic (cells, kind 3).
+// Matrix-free refinement residual in double-float arithmetic (cells, kind 3; vacuum ED/MD dipoles, kind 6).
 //
 // The residual r = F0 - A F of the FP64 refinement needs the Green dyad G^Ep of every pair to ~1e-13
 // relative. GB300 runs FP64 at ~1/64 of its FP32 rate, so this kernel regenerates G in double-float
@@ -8,7 +8,9 @@
 //   * e^{i theta}: table of cos/sin at multiples of pi/128 (double-float entries computed on the host in
 //     double precision) times cos/sin of the remainder |delta| <= pi/256 from its Taylor series
 //     (cos: 1 - d^2/2 + d^4/24 - d^6/720, sin: d - d^3/6 + d^5/120; the neglected terms are < 1e-15);
-//   * G s = a s + b u (u.s), accumulated in double-float, written as FP64 partial sums for the FP64 finalize.
+//   * G s = a s + b u (u.s), accumulated in double-float, written as FP64 partial sums for the FP64 finalize;
+//     for ED/MD dipoles (vacuum) the 6x6 dyad acts on (p, m): (G p - C m, C p + G m) with C s = c (u x s),
+//     c = e^{ikR} (k^2/R + i k/R^2).
 #include <math.h>
 
 #include "gdm_internal.cuh"
@@ -122,8 +124,8 @@ struct DipF {
 #define RF_T 128
 #define RF_S 32
 
-// partial[c][q][t][3] (FP64) = sum over sources j != t of chunk c of G^Ep(r_t - r_j) P_j
-template <int NR>
+// partial[c][q][t][KIND] (FP64) = sum over sources j != t of chunk c of the dyad of (r_t - r_j) times P_j
+template <int KIND, int NR>
 __global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ dip, int64_t n,
                                                       const double2 *__restrict__ P, int rhs0, int nr_here, float khi,
                                                       float klo, float k2hi, float k2lo, float ie_hi, float ie_lo,
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ 
                                                       double2 *__restrict__ partial) {
     __shared__ float4 tab[257];
     __shared__ float sxyz[RF_S][6];
-    __shared__ float4 sm[RF_S][3][NR];  // (re_hi, re_lo, im_hi, im_lo)
+    __shared__ float4 sm[RF_S][KIND][NR];  // (re_hi, re_lo, im_hi, im_lo)
     for (int e = threadIdx.x; e < 257; e += RF_T) tab[e] = gtab[e];
     const int64_t t = (int64_t)blockIdx.x * RF_T + threadIdx.x;
     const bool valid = t < n;
@@ -139,12 +141,12 @@ __global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ 
     const int64_t jb = c * chunk, je = min(n, jb + chunk);
     DipF ti = valid ? dip[t] : dip[0];
     const ff kf = mk(khi, klo), k2 = mk(k2hi, k2lo), ie = mk(ie_hi, ie_lo);
-    cff acc[NR][3];
+    cff acc[NR][KIND];
 #pragma unroll
     for (int q = 0; q < NR; q++)
 #pragma unroll
-        for (int a = 0; a < 3; a++) acc[q][a] = {mk(0, 0), mk(0, 0)};
-    const int64_t ld = 3 * n;
+        for (int a = 0; a < KIND; a++) acc[q][a] = {mk(0, 0), mk(0, 0)};
+    const int64_t ld = KIND * n;
     for (int64_t s0 = jb; s0 < je; s0 += RF_S) {
         const int sn = (int)min((int64_t)RF_S, je - s0);
         __syncthreads();
@@ -157,10 +159,10 @@ __global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ 
             sxyz[e][4] = d.yl;
             sxyz[e][5] = d.zl;
         }
-        for (int e = threadIdx.x; e < sn * 3 * NR; e += RF_T) {
-            int jj = e / (3 * NR), rem = e % (3 * NR), a = rem / NR, q = rem % NR;
+        for (int e = threadIdx.x; e < sn * KIND * NR; e += RF_T) {
+            int jj = e / (KIND * NR), rem = e % (KIND * NR), a = rem / NR, q = rem % NR;
             double2 v = make_double2(0.0, 0.0);
-            if (q < nr_here) v = P[(rhs0 + q) * ld + 3 * (s0 + jj) + a];
+            if (q < nr_here) v = P[(rhs0 + q) * ld + KIND * (s0 + jj) + a];
             float rh = (float)v.x, ih = (float)v.y;
             sm[jj][a][q] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
         }
@@ -185,21 +187,41 @@ __global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ 
             cff ca = {sub(k2r1, ri3), kri2};
             cff cb = {sub(mulf(ri3, 3.0f), k2r1), neg(mulf(kri2, 3.0f))};
             cff a = cmulff(e, ca), b = cmulff(e, cb);
+            // magnetic-electric coupling (kind 6, vacuum): c = e (k^2/R + i k/R^2)
+            cff cc = {mk(0, 0), mk(0, 0)};
+            if (KIND == 6) cc = cmulff(e, cff{k2r1, kri2});
 #pragma unroll
             for (int q = 0; q < NR; q++) {
-                cff s[3];
 #pragma unroll
-                for (int aa = 0; aa < 3; aa++) {
-                    float4 v = sm[jj][aa][q];
-                    s[aa] = {mk(v.x, v.y), mk(v.z, v.w)};
-                }
-                cff us = {add(add(mul(u[0], s[0].re), mul(u[1], s[1].re)), mul(u[2], s[2].re)),
-                          add(add(mul(u[0], s[0].im), mul(u[1], s[1].im)), mul(u[2], s[2].im))};
-                cff bus = cmulff(b, us);
+                for (int h = 0; h < KIND / 3; h++) {  // h = 0: electric part, h = 1: magnetic part
+                    cff s[3];
 #pragma unroll
-                for (int aa = 0; aa < 3; aa++) {
-                    cff v = caddff(cmulff(a, s[aa]), cscaleff(bus, u[aa]));
-                    acc[q][aa] = caddff(acc[q][aa], v);
+                    for (int aa = 0; aa < 3; aa++) {
+                        float4 v = sm[jj][3 * h + aa][q];
+                        s[aa] = {mk(v.x, v.y), mk(v.z, v.w)};
+                    }
+                    cff us = {add(add(mul(u[0], s[0].re), mul(u[1], s[1].re)), mul(u[2], s[2].re)),
+                              add(add(mul(u[0], s[0].im), mul(u[1], s[1].im)), mul(u[2], s[2].im))};
+                    cff bus = cmulff(b, us);
+#pragma unroll
+                    for (int aa = 0; aa < 3; aa++) {
+                        cff v = caddff(cmulff(a, s[aa]), cscaleff(bus, u[aa]));
+                        acc[q][3 * h + aa] = caddff(acc[q][3 * h + aa], v);
+                    }
+                    if (KIND == 6) {
+                        // u x s, added as +c (u x p) to the magnetic rows (h = 0) or -c (u x m) to the electric
+                        // rows (h = 1)
+                        cff x[3];
+                        x[0] = {sub(mul(u[1], s[2].re), mul(u[2], s[1].re)), sub(mul(u[1], s[2].im), mul(u[2], s[1].im))};
+                        x[1] = {sub(mul(u[2], s[0].re), mul(u[0], s[2].re)), sub(mul(u[2], s[0].im), mul(u[0], s[2].im))};
+                        x[2] = {sub(mul(u[0], s[1].re), mul(u[1], s[0].re)), sub(mul(u[0], s[1].im), mul(u[1], s[0].im))};
+#pragma unroll
+                        for (int aa = 0; aa < 3; aa++) {
+                            cff v = cmulff(cc, x[aa]);
+                            if (h == 0) acc[q][3 + aa] = caddff(acc[q][3 + aa], v);
+                            else acc[q][aa] = caddff(acc[q][aa], cff{neg(v.re), neg(v.im)});
+                        }
+                    }
                 }
             }
         }
@@ -208,9 +230,9 @@ __global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ 
 #pragma unroll
     for (int q = 0; q < NR; q++) {
         if (q >= nr_here) break;
-        double2 *o = partial + ((c * 2 + q) * n + t) * 3;
+        double2 *o = partial + ((c * 2 + q) * n + t) * KIND;
 #pragma unroll
-        for (int a = 0; a < 3; a++)
+        for (int a = 0; a < KIND; a++)
             o[a] = make_double2((double)acc[q][a].re.hi + (double)acc[q][a].re.lo,
                                 (double)acc[q][a].im.hi + (double)acc[q][a].im.lo);
     }
@@ -269,12 +291,19 @@ gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const dou
     split(k * k, &k2hi, &k2lo);
     split(1.0 / p->eps_env, &iehi, &ielo);
     dim3 grid((unsigned)((n + RF_T - 1) / RF_T), (unsigned)nchunks);
-    if (nr == 1)
-        k_green_sum_ff<1><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo, tab,
-                                                          chunk, partial);
+    if (p->kind == 6) {
+        if (nr == 1)
+            k_green_sum_ff<6, 1><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo,
+                                                                 tab, chunk, partial);
+        else
+            k_green_sum_ff<6, 2><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo,
+                                                                 tab, chunk, partial);
+    } else if (nr == 1)
+        k_green_sum_ff<3, 1><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo, tab,
+                                                             chunk, partial);
     else
-        k_green_sum_ff<2><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo, tab,
-                                                          chunk, partial);
+        k_green_sum_ff<3, 2><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo, tab,
+                                                             chunk, partial);
     GDM_LAUNCHED(ctx, "green_sum_ff");
     return GDM_OK;
 }

@@ -105,8 +105,9 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     double *dnorm = sc.take<double>(4 * n_rhs);
     int *tsync = sc.take<int>(gdm_trsv_sync_bytes(ns) / sizeof(int));
     void *dinv = sc.take<char>(gdm_trsv_inv_bytes(ns));
-    // double-float residual for cells unless GDM_RESIDUAL_FP64 is set
-    void *ffws = (p->kind == 3 && !getenv("GDM_RESIDUAL_FP64")) ? sc.take<char>(gdm_ff_scratch_bytes(p->n)) : nullptr;
+    // double-float residual unless GDM_RESIDUAL_FP64 is set (the adjoint residual of ED/MD dipoles is not built)
+    void *ffws = (!getenv("GDM_RESIDUAL_FP64") && (p->kind == 3 || !adjoint)) ? sc.take<char>(gdm_ff_scratch_bytes(p->n))
+                                                                               : nullptr;
     double *hn;
     GDM_TRY(gdm_pinned(ctx, sizeof(double) * 4 * n_rhs, (void **)&hn));
     const unsigned nb = (unsigned)((ns + 255) / 256);

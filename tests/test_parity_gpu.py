@@ -265,6 +265,32 @@ def test_residual_matches_oracle(G, ctx, lossy):
     np.testing.assert_allclose(n2.cpu().numpy(), np.sum(np.abs(ro) ** 2, axis=0), rtol=1e-10)
 
 
+@pytest.mark.parametrize("subset", [False, True])
+def test_residual_matches_oracle_edmd(G, ctx, subset):
+    """gdm_residual for ED/MD dipoles (double-float 6x6 dyads with the electric-magnetic cross blocks) =
+    the oracle's F0 - A F for arbitrary fields and three right-hand sides (a two-RHS and a one-RHS pass),
+    to 1e-13 of the largest term; the subset case scatters 150 dipoles over the full 64 x 64 array, so
+    the phases k R reach ~450 rad."""
+    if subset:
+        s = W.metasurface_edmd(nx=64, ny=64, pitch=400.0, seed=4)
+        sub = np.sort(np.random.default_rng(8).choice(s.n, 150, replace=False))
+        s.pos, s.omega0_e, s.omega0_m = s.pos[sub], s.omega0_e[sub], s.omega0_m[sub]
+    else:
+        s = W.metasurface_edmd(nx=14, ny=12, pitch=400.0, seed=6)
+    lam = 505.0
+    prob = gpu_problem(G, s, lam)
+    rng = np.random.default_rng(3)
+    e0 = np.array([[1, 0, 0], [0, 1, 0], [1, 1j, 0]], complex) / np.array([[1.0], [1.0], [np.sqrt(2.0)]])
+    F = rng.standard_normal((3, 6 * s.n)) + 1j * rng.standard_normal((3, 6 * s.n))
+    F0 = G.incident_planewave(ctx, prob.pos, lam, e0, kind_out=6)
+    r, n2 = G.residual(ctx, prob, F0, t(F))
+    pr = oracle_problem(s, lam)
+    ro = O.residual_rows(pr, F0.cpu().numpy().T, F.T, np.arange(s.n)).reshape(6 * s.n, 3)
+    scale = np.abs(pr.matrix()).max() * np.abs(F).max()
+    assert np.abs(r.cpu().numpy().T - ro).max() <= 1e-13 * scale
+    np.testing.assert_allclose(n2.cpu().numpy(), np.sum(np.abs(ro) ** 2, axis=0), rtol=1e-10)
+
+
 @pytest.mark.parametrize("prec", ["tf32", "fp32", "fp64"])
 def test_metasurface_medium_several_wavelengths(G, ctx, prec):
     """ED/MD point-dipole array with electric-magnetic cross Green blocks, 6N = 1920 (four 512-column
