@@ -538,6 +538,71 @@ __global__ void __launch_bounds__(512) k_block_linv(const float2 *__restrict__ A
     }
 }
 
+// In-place triangular step of the recursive block factorisation: rows [lo, lo + nr) (nr a multiple of 32, the
+// factored left part, pivots of each 32-row panel inside that panel) of columns [col0, col0 + ncols) become
+// U = L_S^{-1} P_S ... L_1^{-1} P_1 A (the product form of the left part's panels). CTA b takes 8 columns
+// into shared memory and applies the panels in order, as k_block_linv does for the identity.
+__global__ void __launch_bounds__(512) k_panels_apply(float2 *__restrict__ A, int64_t lda, int64_t lo, int nr,
+                                                      int64_t col0, int ncols, const int32_t *__restrict__ ipiv) {
+    extern __shared__ __align__(16) float2 X[];  // X[c * nr + r], 8 columns
+    __shared__ float2 Lpp[32][33];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c_first = 8 * blockIdx.x;
+    const int nc = min(8, ncols - c_first);
+    float2 *D = A + lo * lda + lo;  // D[r + c * lda], rows and columns relative to lo
+    for (int e = tid; e < 8 * nr; e += blockDim.x) {
+        const int c = e / nr, r = e % nr;
+        X[e] = (c < nc) ? A[(col0 + c_first + c) * lda + lo + r] : make_float2(0.f, 0.f);
+    }
+    for (int q0 = 0; q0 < nr; q0 += 32) {
+        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+            const int i = e & 31, j = e >> 5;
+            Lpp[i][j] = (i > j) ? D[(int64_t)(q0 + j) * lda + q0 + i] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (tid < 8) {
+            float2 *x = X + tid * nr;
+            for (int t = 0; t < 32; t++) {
+                const int r2 = (int)(ipiv[lo + q0 + t] - lo);
+                if (r2 != q0 + t && r2 >= q0 && r2 < q0 + 32) {
+                    const float2 a = x[q0 + t];
+                    x[q0 + t] = x[r2];
+                    x[r2] = a;
+                }
+            }
+        }
+        __syncthreads();
+        if (warp < 8) {
+            float2 *x = X + warp * nr + q0;
+            float2 v = x[lane];
+            for (int t = 0; t < 31; t++) {
+                const float2 xt = make_float2(__shfl_sync(0xffffffffu, v.x, t), __shfl_sync(0xffffffffu, v.y, t));
+                if (lane > t) cfms(v, Lpp[lane][t], xt);
+            }
+            x[lane] = v;
+        }
+        __syncthreads();
+        for (int r = q0 + 32 + tid; r < nr; r += blockDim.x) {
+            float2 l[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++) l[j] = D[(int64_t)(q0 + j) * lda + r];
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                float2 acc = X[c * nr + r];
+                const float2 *xp = X + c * nr + q0;
+#pragma unroll
+                for (int j = 0; j < 32; j++) cfms(acc, l[j], xp[j]);
+                X[c * nr + r] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < 8 * nr; e += blockDim.x) {
+        const int c = e / nr, r = e % nr;
+        if (c < nc) A[(col0 + c_first + c) * lda + lo + r] = X[e];
+    }
+}
+
 // T[i + c * nb] = A[b0 + i, c0 + c] and zero the source (the U12 GEMM accumulates into it)
 __global__ void k_gather_zero(float2 *__restrict__ A, int64_t lda, int64_t b0, int64_t c0, int nb, int64_t nc,
                               float2 *__restrict__ T) {
@@ -802,6 +867,40 @@ static gdm_status panel_local(gdm_ctx *ctx, C *A, int64_t lda, int64_t n, int64_
     return GDM_OK;
 }
 
+// Recursive factorisation of the columns [lo, hi) of one outer block (rows [lo, n)), FP32 factors on tensor
+// cores: factor the left part (a multiple of 32 columns), turn the right part's top rows into U with the
+// left part's panels, update the right part's rows below with one GEMM (K = width of the left part), then
+// factor the right part. Same arithmetic as panel-by-panel right-looking updates, but the GEMMs have
+// K = 256, 128, 64, 32 instead of fifteen K = 32 updates of the full remaining block width.
+static gdm_status factor_rec(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t lo,
+                             int64_t hi, int32_t *ipiv, unsigned *growth, void *tcws, size_t tcbytes) {
+    const int64_t w = hi - lo;
+    if (w <= NBP) {
+        GDM_TRY(gdm_phase_begin(ctx, GDM_PH_PANEL));
+        GDM_TRY(panel_local<float2>(ctx, A, lda, n, lo, (int)w, ipiv, growth));
+        return gdm_phase_end(ctx, GDM_PH_PANEL);
+    }
+    const int64_t mid = lo + NBP * ((w + 2 * NBP - 1) / (2 * NBP));
+    GDM_TRY(factor_rec(ctx, prec, A, lda, n, lo, mid, ipiv, growth, tcws, tcbytes));
+    const int nr = (int)(mid - lo), ncols = (int)(hi - mid);
+    GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRSM));
+    const size_t sm = (size_t)8 * nr * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_panels_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)((size_t)8 * 1024 * sizeof(float2))));
+        attr = true;
+    }
+    const int bthreads = nr < 256 ? 256 : (nr > 512 ? 512 : nr);
+    k_panels_apply<<<(unsigned)((ncols + 7) / 8), bthreads, sm, ctx->stream>>>(A, lda, lo, nr, mid, ncols, ipiv);
+    GDM_LAUNCHED(ctx, "panels_apply");
+    GDM_TRY(gdm_phase_end(ctx, GDM_PH_TRSM));
+    GDM_TRY(gdm_phase_begin(ctx, GDM_PH_INBLOCK));
+    GDM_TRY(update<float2>(ctx, prec, A, lda, n, mid, mid, lo, n - mid, hi - mid, mid - lo, tcws, tcbytes));
+    GDM_TRY(gdm_phase_end(ctx, GDM_PH_INBLOCK));
+    return factor_rec(ctx, prec, A, lda, n, mid, hi, ipiv, growth, tcws, tcbytes);
+}
+
 template <class C>
 static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n, int64_t lda, int32_t *ipiv,
                               int global_pivot, unsigned *growth) {
@@ -829,9 +928,16 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
     void *tcws = tcbytes ? sc.take<char>(tcbytes) : nullptr;
     float2 *negM = u12_op ? sc.take<float2>((size_t)NB * NB) : nullptr;
     float2 *T12 = u12_op ? sc.take<float2>((size_t)NB * n) : nullptr;
+    // recursive blocks pay off on large systems; small ones (the batched workloads) keep the panel-by-panel
+    // updates, whose per-problem latency is lower
+    const bool recursive =
+        u12_op && NB <= 1024 && (n >= 8192 || getenv("GDM_LU_RECURSIVE")) && !getenv("GDM_INBLOCK_PANELS");
     for (int64_t b0 = 0; b0 < n; b0 += NB) {
         int64_t nb = n - b0 < NB ? n - b0 : NB;
         int64_t be = b0 + nb;
+        if (recursive)
+            GDM_TRY(factor_rec(ctx, prec, (float2 *)A, lda, n, b0, be, ipiv, growth, tcws, tcbytes));
+        else
         for (int64_t c0 = b0; c0 < be; c0 += NBP) {
             int w = (int)(be - c0 < NBP ? be - c0 : NBP);
             GDM_TRY(gdm_phase_begin(ctx, GDM_PH_PANEL));

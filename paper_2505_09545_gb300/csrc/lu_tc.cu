@@ -50,6 +50,12 @@ template <int BN, int SPLIT> struct Cfg {
     // instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = BN
     static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(BM >> 4) << 24);
+    // the same descriptor with the MMA's N set to n_cols (a multiple of 32 up to BN): narrow column tiles
+    // (the last one of a GEMM whose N is not a multiple of BN, or a GEMM narrower than BN) run only the
+    // columns that exist
+    static __device__ __forceinline__ uint32_t idesc_n(int n_cols) {
+        return (IDESC & ~(0x3Fu << 17)) | ((uint32_t)(n_cols >> 3) << 17);
+    }
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -158,6 +164,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 
 struct TileMap {
     int num_m, num_n, group;
+    // 32-column chunks of column tile nt that hold columns < N (tiles are bn wide)
+    __device__ __forceinline__ int chunks(int nt, int N, int bn) const {
+        const int left = N - nt * bn;
+        return left >= bn ? bn / 32 : (left + 31) / 32;
+    }
     __device__ __forceinline__ void get(int t, int &m, int &n) const {
         // groups of `group` column tiles; inside a group the row tile varies slowest across the
         // group's columns so that concurrently running CTAs share operand tiles in L2
@@ -273,6 +284,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!mbar_wait(&tempty[b], tph ^ 1, abort_flag, gflags)) break;
                 tc_fence_after();
                 const uint32_t dt = tmem_base + (uint32_t)(b * BN);
+                int mt_i, nt_i;
+                tm.get(t, mt_i, nt_i);
+                const uint32_t idesc = CF::idesc_n(32 * tm.chunks(nt_i, N, BN));
                 bool ok = true;
                 for (int kc = 0; kc < nk; kc++) {
                     if (!mbar_wait(&full[s], ph, abort_flag, gflags)) {
@@ -287,12 +301,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     for (int k = 0; k < BK / 8; k++) {
                         // advance 8 TF32 = 32 bytes along K inside the swizzled row: +2 in the 16-B address field
                         const uint64_t ko = (uint64_t)(2 * k);
-                        umma_tf32(dt, a0 + ko, b0 + ko, CF::IDESC, (kc | k) ? 1u : 0u);
+                        umma_tf32(dt, a0 + ko, b0 + ko, idesc, (kc | k) ? 1u : 0u);
                         if (SPLIT == 3) {
                             const uint64_t a1 = desc_sw128(sa + CF::A_BYTES + CF::B_BYTES);
                             const uint64_t b1 = desc_sw128(sa + 2 * CF::A_BYTES + CF::B_BYTES);
-                            umma_tf32(dt, a0 + ko, b1 + ko, CF::IDESC, 1u);
-                            umma_tf32(dt, a1 + ko, b0 + ko, CF::IDESC, 1u);
+                            umma_tf32(dt, a0 + ko, b1 + ko, idesc, 1u);
+                            umma_tf32(dt, a1 + ko, b0 + ko, idesc, 1u);
                         }
                     }
                     issued_any = true;
@@ -320,24 +334,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int q = warp & 3;
         const int et = threadIdx.x - 64;  // 0..127
         const bool leader = (et == 0);
-        constexpr int CPT = BN / 32;      // chunks per tile
-        const int my_tiles = (blockIdx.x < ntiles) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-        const int total = my_tiles * CPT;
-        auto coords = [&](int g, int &x, int &y) {
-            int lt2 = g / CPT, ch = g % CPT, mt, nt;
+        // Chunks are numbered over the valid 32-column chunks of this CTA's tiles only (a narrow tile has
+        // fewer than BN/32); g indexes that sequence, and the loads run LOOK chunks ahead on a cursor.
+        auto tile_chunks = [&](int lt2, int &mt, int &nt) {
             tm.get(blockIdx.x + lt2 * gridDim.x, mt, nt);
-            x = cx0 + mt * BM;
-            y = cy0 + nt * BN + ch * 32;
+            return tm.chunks(nt, N, BN);
         };
+        int total = 0;
+        for (int t2 = blockIdx.x; t2 < ntiles; t2 += gridDim.x) {
+            int mt, nt;
+            tm.get(t2, mt, nt);
+            total += tm.chunks(nt, N, BN);
+        }
+        int ld_lt = 0, ld_ch = 0;  // load cursor: tile (local index) and chunk of the next chunk to load
         auto issue_load = [&](int g) {
-            int x, y;
-            coords(g, x, y);
+            int mt, nt;
+            const int nch = tile_chunks(ld_lt, mt, nt);
             const int b = g % CF::NCB;
             mbar_expect_tx(&cbar[b], CF::CB_BYTES);
-            tma_load_2d(cbuf + (size_t)b * (CF::CB_BYTES / 4), &tmC, x, y, &cbar[b]);
+            tma_load_2d(cbuf + (size_t)b * (CF::CB_BYTES / 4), &tmC, cx0 + mt * BM, cy0 + nt * BN + ld_ch * 32,
+                        &cbar[b]);
+            if (++ld_ch == nch) {
+                ld_ch = 0;
+                ld_lt++;
+            }
         };
         if (leader)
             for (int g = 0; g < CF::LOOK && g < total; g++) issue_load(g);
+        int g = 0;  // valid chunks consumed so far
         const int row = q * 32 + lane;
         // Only the leader waits on mbarriers; it publishes each outcome in dec[] (two parity slots) before a
         // named barrier of the four epilogue warps, so all of them take the same branch (no divergent exit).
@@ -359,9 +383,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (!agree(ok)) break;
             tc_fence_after();
             bool alive = true;
+            int mt_c, nt_c;
+            const int nch = tile_chunks(lt, mt_c, nt_c);
 #pragma unroll 1
-            for (int ch = 0; ch < CPT; ch++) {
-                const int g = lt * CPT + ch;
+            for (int ch = 0; ch < nch; ch++, g++) {
                 const int cb = g % CF::NCB;
                 ok = true;
                 if (leader) {
@@ -384,9 +409,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 fence_proxy_async_smem();
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (leader) {
-                    int x, y;
-                    coords(g, x, y);
-                    tma_store_2d(&tmC, buf, x, y);
+                    tma_store_2d(&tmC, buf, cx0 + mt_c * BM, cy0 + nt_c * BN + ch * 32);
                     bulk_commit();
                 }
             }

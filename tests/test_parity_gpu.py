@@ -220,6 +220,27 @@ def test_lu_factor_quality(G, ctx, prec, tol_plain, max_iters):
     assert np.all(e2 < 1e-9) and info["iterations"] <= max_iters, (e1, e2, info)
 
 
+@pytest.mark.parametrize("prec", ["tf32", "fp32"])
+def test_recursive_block_factorisation(G, ctx, prec, monkeypatch):
+    """The recursive in-block factorisation (used from n = 8192 on; forced here at 3N = 2100: four full
+    512-column blocks split 256/128/64/32 and a ragged 52-column last block) gives factors of the
+    precision's quality and refined fields at 1e-9, like the panel-by-panel path."""
+    monkeypatch.setenv("GDM_LU_RECURSIVE", "1")
+    s = W.random_cells(700, seed=12)
+    lam = float(s.wavelengths[0])
+    prob = gpu_problem(G, s, lam)
+    F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0)
+    pr = oracle_problem(s, lam)
+    Fo = pr.solve(pr.plane_wave(s.e0))
+    A = G.assemble(ctx, prob, prec)
+    F1, ipiv, _ = G.solve(ctx, prob, A, F0, prec, no_refine=True)
+    e1 = np.linalg.norm(F1.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+    assert np.all(e1 < (5e-2 if prec == "tf32" else 1e-4)), e1
+    F2, _, info = G.solve(ctx, prob, A, F0, prec, ipiv=ipiv, factored=True)
+    e2 = np.linalg.norm(F2.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+    assert np.all(e2 < 1e-9), (e1, e2, info)
+
+
 @pytest.mark.parametrize("eps,expect_refactor", [(12.25 + 0.0j, False), (-8.0 + 0.5j, False), (-2.2 + 0.3j, True)])
 def test_pivoting_certificate_and_fallback(G, ctx, eps, expect_refactor):
     """Pivots are searched inside each 32 x 32 diagonal block and certified against the rows below.
