@@ -209,6 +209,34 @@ typedef struct {
 gdm_status gdm_solve_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_item *items, int n_items,
                              const gdm_solve_opts *opts, int n_streams, gdm_solve_info *infos);
 
+/* One wavelength of a spectrum for gdm_backward_batched: the factors, pivots and fields of
+ * that wavelength's solve, and the upstream gradients. Pointers are device memory unless
+ * marked host. */
+typedef struct {
+    gdm_problem prob;          /* kind 3; n, pos, eps, step and eps_env shared by all items */
+    const void *A;             /* factors from gdm_solve / gdm_solve_batched */
+    int64_t lda;
+    const int32_t *ipiv;
+    const double *F;           /* (3n) x n_rhs complex128 solved fields */
+    const double *gF;          /* (3n) x n_rhs dL/dF^* (conjugate Wirtinger), or NULL */
+    const double *g_sigma;     /* host n_rhs x 3 dL/d(ext, sca, abs), or NULL */
+    const double *e0;          /* host n_rhs x 3 complex128 plane-wave amplitudes */
+    const double *khat;        /* host 3 doubles (NULL: +z) */
+    double *grad_wavelength;   /* one double: dL/dlambda of this item ADDED here, or NULL */
+    int32_t n_rhs;
+    int32_t reserved;
+} gdm_backward_item;
+
+/* gdm_backward for a loss summed over the wavelengths of one structure (the paper's spectral
+ * inverse-design losses, e.g. a target response over a band): every item's adjoint solve
+ * and gradient kernels, run concurrently on up to n_streams child contexts (0 = 8, at most
+ * 16) like gdm_solve_batched, with the position and permittivity gradients of all items
+ * summed and ADDED to grad_pos (n x 3) and grad_eps (n complex128; either may be NULL). The
+ * items must share the structure (same n, pos and eps pointers, step, eps_env). Synchronous;
+ * infos: host n_items records or NULL. Errors as gdm_solve_batched. */
+gdm_status gdm_backward_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_backward_item *items, int n_items,
+                                int n_streams, double *grad_pos, double *grad_eps, gdm_solve_info *infos);
+
 /* LU block-width autotuner (no paper counterpart). For each size class present in sizes
  * (system dimensions kind*n; classes <= 512, 1024, ..., 32768, larger), times the
  * factorisation of a synthetic well-conditioned complex64 matrix of the class's largest

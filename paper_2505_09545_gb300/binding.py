@@ -42,6 +42,12 @@ class Problem(C.Structure):
                 ("wavelength", C.c_double)]
 
 
+class BackwardItem(C.Structure):
+    _fields_ = [("prob", Problem), ("A", C.c_void_p), ("lda", C.c_int64), ("ipiv", C.c_void_p), ("F", C.c_void_p),
+                ("gF", C.c_void_p), ("g_sigma", C.c_void_p), ("e0", C.c_void_p), ("khat", C.c_void_p),
+                ("grad_wavelength", C.c_void_p), ("n_rhs", C.c_int32), ("reserved", C.c_int32)]
+
+
 class BatchItem(C.Structure):
     _fields_ = [("prob", Problem), ("A", C.c_void_p), ("lda", C.c_int64), ("ipiv", C.c_void_p), ("F0", C.c_void_p),
                 ("F", C.c_void_p), ("sigma", C.c_void_p), ("e0", C.c_void_p), ("khat", C.c_void_p),
@@ -86,6 +92,7 @@ _SIGS = {
     "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, P], C.c_int),
     "gdm_solve_batched": ([P, C.c_int, P, C.c_int, P, C.c_int, P], C.c_int),
     "gdm_autotune": ([P, C.c_int, P, C.c_int, P], C.c_int),
+    "gdm_backward_batched": ([P, C.c_int, P, C.c_int, C.c_int, P, P, P], C.c_int),
     "gdm_cross_sections_noalloc": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
     "gdm_backward": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, C.c_int, PD, PD, P, PD, P, P, P,
                       C.POINTER(SolveInfo)], C.c_int),
@@ -334,7 +341,7 @@ def cross_sections_noalloc(ctx: Context, prob: GDMProblem, F0, F, e0_norm2, out)
 
 
 def solve_batched(ctx: Context, probs, e0s, precision="tf32", khat=(0.0, 0.0, 1.0), n_streams=0, with_sigma=True,
-                  max_iter=0, tol=0.0):
+                  max_iter=0, tol=0.0, return_factors=False):
     """gdm_solve_batched over independent problems: probs is a list of GDMProblem, e0s a list of (n_rhs, 3)
     complex plane-wave amplitudes (one per problem). Allocates each item's matrix, pivots, fields and
     cross sections; returns (F list of (n_rhs, kind*n) complex128, sigma list of (3, n_rhs) or None,
@@ -343,7 +350,7 @@ def solve_batched(ctx: Context, probs, e0s, precision="tf32", khat=(0.0, 0.0, 1.
     n = len(probs)
     items = (BatchItem * n)()
     keep = []
-    Fs, sigs = [], []
+    Fs, sigs, As, ipivs = [], [], [], []
     ka, kp = _dbl_array(khat)
     keep.append(ka)
     for i, (pb, e0) in enumerate(zip(probs, e0s)):
@@ -370,12 +377,61 @@ def solve_batched(ctx: Context, probs, e0s, precision="tf32", khat=(0.0, 0.0, 1.
         it.n_rhs = n_rhs
         Fs.append(F)
         sigs.append(sig)
+        As.append(A)
+        ipivs.append(ipiv)
     opts = SolveOpts(int(max_iter), 0, float(tol))
     infos = (SolveInfo * n)()
     ctx._sync_stream()
     ctx._check(lib().gdm_solve_batched(ctx.h, prec, items, n, C.byref(opts), int(n_streams), infos),
                "gdm_solve_batched")
-    return Fs, sigs, [infos[i].as_dict() for i in range(n)]
+    out = (Fs, sigs, [infos[i].as_dict() for i in range(n)])
+    return out + (As, ipivs) if return_factors else out
+
+
+def backward_batched(ctx: Context, probs, As, ipivs, Fs, e0, precision="tf32", khat=(0.0, 0.0, 1.0), gFs=None,
+                     g_sigmas=None, grad_pos=None, grad_eps=None, grad_wavelengths=None, n_streams=0):
+    """gdm_backward_batched for one structure at several wavelengths (probs share pos and eps): the position
+    and eps gradients of all items summed into grad_pos / grad_eps, dL/dlambda per item into
+    grad_wavelengths (len(probs) doubles). gFs: list of dL/dF^* tensors (or None), g_sigmas: list of host
+    (n_rhs, 3) arrays (or None)."""
+    n = len(probs)
+    dev = Fs[0].device
+    nc = probs[0].n
+    if grad_pos is None:
+        grad_pos = torch.zeros((nc, 3), dtype=torch.float64, device=dev)
+    if grad_eps is None:
+        grad_eps = torch.zeros(nc, dtype=torch.complex128, device=dev)
+    if grad_wavelengths is None:
+        grad_wavelengths = torch.zeros(n, dtype=torch.float64, device=dev)
+    e0 = np.atleast_2d(np.asarray(e0, np.complex128))
+    ea, ep = _dbl_array(e0.view(np.float64).reshape(-1))
+    ka, kp = _dbl_array(khat)
+    keep = [ea, ka]
+    items = (BackwardItem * n)()
+    for i in range(n):
+        it = items[i]
+        it.prob = probs[i].struct()
+        it.A, it.lda, it.ipiv = As[i].data_ptr(), As[i].shape[1], ipivs[i].data_ptr()
+        F = Fs[i].contiguous()
+        keep.append(F)
+        it.F = F.data_ptr()
+        if gFs is not None and gFs[i] is not None:
+            g = gFs[i].contiguous()
+            keep.append(g)
+            it.gF = g.data_ptr()
+        if g_sigmas is not None and g_sigmas[i] is not None:
+            ga, gp = _dbl_array(np.asarray(g_sigmas[i], np.float64).reshape(-1))
+            keep.append(ga)
+            it.g_sigma = ga.ctypes.data
+        it.e0 = ea.ctypes.data
+        it.khat = ka.ctypes.data
+        it.grad_wavelength = grad_wavelengths.data_ptr() + 8 * i
+        it.n_rhs = e0.shape[0]
+    infos = (SolveInfo * n)()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_backward_batched(ctx.h, PRECISION[precision], items, n, int(n_streams), _ptr(grad_pos),
+                                          _ptr(grad_eps), infos), "gdm_backward_batched")
+    return grad_pos, grad_eps, grad_wavelengths, [infos[i].as_dict() for i in range(n)]
 
 
 def autotune(ctx: Context, sizes, precision="tf32"):

@@ -73,6 +73,105 @@ bool per_item_numeric(gdm_status s) {
     return s == GDM_ERR_NOT_CONVERGED || s == GDM_ERR_NONFINITE || s == GDM_ERR_SINGULAR;
 }
 
+// Runs fn(child, item, info) for every item on up to n_streams child contexts, largest first. The pool
+// starts after the work queued on the caller's stream; once the children have finished and the caller's
+// stream waits for them, after(ctx, children used, after_arg) may queue follow-up work on that stream.
+// Numerical failures stay with their item; any other error stops the remaining items.
+template <class Fn>
+gdm_status run_pool(gdm_ctx *ctx, int n_items, const int64_t *size, int n_streams, gdm_solve_info *infos, Fn fn,
+                    gdm_status (*after)(gdm_ctx *, int, void *), void *after_arg = nullptr) {
+    int ns = n_streams > 0 ? n_streams : 8;
+    if (ns > GDM_POOL_MAX) ns = GDM_POOL_MAX;
+    if (ns > n_items) ns = n_items;
+    GDM_TRY(ensure_pool(ctx, ns));
+    std::vector<int> order(n_items);
+    for (int i = 0; i < n_items; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return size[a] > size[b]; });
+    std::vector<gdm_solve_info> local((size_t)n_items);
+    gdm_solve_info *inf = infos ? infos : local.data();
+    memset(inf, 0, sizeof(gdm_solve_info) * (size_t)n_items);
+
+    GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, ctx->stream));
+    int64_t launches0[GDM_POOL_MAX];
+    for (int w = 0; w < ns; w++) {
+        gdm_ctx *c = ctx->pool[w];
+        memcpy(c->nb_table, ctx->nb_table, sizeof(ctx->nb_table));
+        c->err[0] = 0;
+        launches0[w] = c->launches;
+        GDM_CUDA_TRY(ctx, cudaStreamWaitEvent(c->stream, ctx->ev2, 0));
+    }
+    std::atomic<int> next(0);
+    std::atomic<bool> stop(false);
+    std::mutex mu;
+    gdm_status first = GDM_OK;
+    int first_item = -1;
+    char first_msg[sizeof(ctx->err)] = {0};
+    auto worker = [&](int w) {
+        gdm_ctx *c = ctx->pool[w];
+        if (cudaSetDevice(ctx->device) != cudaSuccess) {
+            stop = true;
+            return;
+        }
+        for (;;) {
+            if (stop.load()) break;
+            const int k = next.fetch_add(1);
+            if (k >= n_items) break;
+            const int i = order[k];
+            gdm_status s = fn(c, w, i, &inf[i]);
+            inf[i].status = s;
+            if (s != GDM_OK) {
+                std::lock_guard<std::mutex> lock(mu);
+                if (first == GDM_OK || (per_item_numeric(first) && !per_item_numeric(s))) {
+                    first = s;
+                    first_item = i;
+                    memcpy(first_msg, c->err, sizeof(first_msg));
+                }
+                if (!per_item_numeric(s)) stop = true;
+            }
+        }
+    };
+    std::vector<std::thread> threads;
+    threads.reserve(ns);
+    for (int w = 0; w < ns; w++) threads.emplace_back(worker, w);
+    for (auto &t : threads) t.join();
+    for (int w = 0; w < ns; w++) {
+        gdm_ctx *c = ctx->pool[w];
+        ctx->launches += c->launches - launches0[w];
+        GDM_CUDA_TRY(ctx, cudaEventRecord(c->ev2, c->stream));
+        GDM_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, c->ev2, 0));
+    }
+    if (after) GDM_TRY(after(ctx, ns, after_arg));
+    if (first != GDM_OK) return gdm_fail(ctx, first, "item %d: %s", first_item, first_msg);
+    return GDM_OK;
+}
+
+// grad[i] += sum_w acc[w][i] over the children's gradient accumulators (5 doubles per cell: 3 position,
+// then 2 for the complex eps gradient)
+__global__ void k_sum_children(const double *__restrict__ acc, int nw, int64_t n, double *grad_pos, double *grad_eps) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 5 * n) return;
+    double s = 0.0;
+    for (int w = 0; w < nw; w++) s += acc[(int64_t)w * 5 * n + i];
+    if (i < 3 * n) {
+        if (grad_pos) grad_pos[i] += s;
+    } else if (grad_eps) {
+        grad_eps[i - 3 * n] += s;
+    }
+}
+
+struct BackwardSum {
+    double *acc;
+    int64_t n;
+    double *grad_pos, *grad_eps;
+};
+gdm_status backward_sum(gdm_ctx *ctx, int nw, void *arg) {
+    BackwardSum *b = (BackwardSum *)arg;
+    k_sum_children<<<(unsigned)((5 * b->n + 255) / 256), 256, 0, ctx->stream>>>(b->acc, nw, b->n, b->grad_pos,
+                                                                              b->grad_eps);
+    GDM_LAUNCHED(ctx, "sum_children");
+    return GDM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -93,77 +192,57 @@ gdm_status gdm_solve_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_i
                 if (!(it->e0_norm2[q] > 0)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "item %d: |E0|^2 <= 0", i);
     }
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    std::vector<int64_t> size((size_t)n_items);
+    for (int i = 0; i < n_items; i++) size[i] = items[i].prob.n * items[i].prob.kind;
+    return run_pool(ctx, n_items, size.data(), n_streams, infos,
+                    [&](gdm_ctx *c, int, int i, gdm_solve_info *inf) { return run_item(c, prec, &items[i], opts, inf); },
+                    nullptr);
+}
+
+gdm_status gdm_backward_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_backward_item *items, int n_items,
+                                int n_streams, double *grad_pos, double *grad_eps, gdm_solve_info *infos) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    if (n_items < 0 || (n_items > 0 && !items)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "bad item list");
+    if (n_items == 0) return GDM_OK;
+    const gdm_problem *p0 = &items[0].prob;
+    for (int i = 0; i < n_items; i++) {
+        const gdm_backward_item *it = &items[i];
+        const gdm_problem *p = &it->prob;
+        if (p->kind != 3) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "item %d: the adjoint is implemented for kind 3", i);
+        if (p->n != p0->n || p->pos != p0->pos || p->eps != p0->eps || p->step != p0->step ||
+            p->eps_env != p0->eps_env)
+            return gdm_fail(ctx, GDM_ERR_INVALID_ARG,
+                            "item %d: the items must share one structure (n, pos, eps, step, eps_env); only the "
+                            "wavelength may differ",
+                            i);
+        gdm_status s = gdm_check_solve_args(ctx, p, prec, it->A, it->lda, it->ipiv, it->F, it->F, it->n_rhs);
+        if (s != GDM_OK) return gdm_fail(ctx, s, "item %d: %s", i, ctx->err);
+        if (!it->e0) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "item %d: e0 is NULL", i);
+    }
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const int64_t n = p0->n;
     int ns = n_streams > 0 ? n_streams : 8;
     if (ns > GDM_POOL_MAX) ns = GDM_POOL_MAX;
     if (ns > n_items) ns = n_items;
-    GDM_TRY(ensure_pool(ctx, ns));
-
-    // largest systems first
-    std::vector<int> order(n_items);
-    for (int i = 0; i < n_items; i++) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return items[a].prob.n * items[a].prob.kind > items[b].prob.n * items[b].prob.kind;
-    });
-    std::vector<gdm_solve_info> local((size_t)n_items);
-    gdm_solve_info *inf = infos ? infos : local.data();
-    memset(inf, 0, sizeof(gdm_solve_info) * (size_t)n_items);
-
-    // the pool starts after everything already queued on the caller's stream
-    GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, ctx->stream));
-    int64_t launches0[GDM_POOL_MAX];
-    for (int w = 0; w < ns; w++) {
-        gdm_ctx *c = ctx->pool[w];
-        memcpy(c->nb_table, ctx->nb_table, sizeof(ctx->nb_table));
-        c->err[0] = 0;
-        launches0[w] = c->launches;
-        GDM_CUDA_TRY(ctx, cudaStreamWaitEvent(c->stream, ctx->ev2, 0));
-    }
-
-    std::atomic<int> next(0);
-    std::atomic<bool> stop(false);
-    std::mutex mu;
-    gdm_status first = GDM_OK;
-    int first_item = -1;
-    char first_msg[sizeof(ctx->err)] = {0};
-    auto worker = [&](int w) {
-        gdm_ctx *c = ctx->pool[w];
-        if (cudaSetDevice(ctx->device) != cudaSuccess) {
-            stop = true;
-            return;
-        }
-        for (;;) {
-            if (stop.load()) break;
-            const int k = next.fetch_add(1);
-            if (k >= n_items) break;
-            const int i = order[k];
-            gdm_status s = run_item(c, prec, &items[i], opts, &inf[i]);
-            inf[i].status = s;
-            if (s != GDM_OK) {
-                std::lock_guard<std::mutex> lock(mu);
-                if (first == GDM_OK || (per_item_numeric(first) && !per_item_numeric(s))) {
-                    first = s;
-                    first_item = i;
-                    memcpy(first_msg, c->err, sizeof(first_msg));
-                }
-                // numerical failures stay with their item; anything else ends the batch
-                if (!per_item_numeric(s)) stop = true;
-            }
-        }
-    };
-    std::vector<std::thread> threads;
-    threads.reserve(ns);
-    for (int w = 0; w < ns; w++) threads.emplace_back(worker, w);
-    for (auto &t : threads) t.join();
-
-    // the caller's stream continues after the pool
-    for (int w = 0; w < ns; w++) {
-        gdm_ctx *c = ctx->pool[w];
-        ctx->launches += c->launches - launches0[w];
-        GDM_CUDA_TRY(ctx, cudaEventRecord(c->ev2, c->stream));
-        GDM_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, c->ev2, 0));
-    }
-    if (first != GDM_OK) return gdm_fail(ctx, first, "item %d: %s", first_item, first_msg);
-    return GDM_OK;
+    // one gradient accumulator per child: a child runs its items one after another on its own stream
+    double *acc = nullptr;
+    GDM_CUDA_TRY(ctx, cudaMallocAsync((void **)&acc, sizeof(double) * 5 * n * ns, ctx->stream));
+    GDM_CUDA_TRY(ctx, cudaMemsetAsync(acc, 0, sizeof(double) * 5 * n * ns, ctx->stream));
+    std::vector<int64_t> size((size_t)n_items, n);
+    static const double zhat[3] = {0.0, 0.0, 1.0};
+    BackwardSum bs = {acc, n, grad_pos, grad_eps};
+    gdm_status st = run_pool(
+        ctx, n_items, size.data(), ns, infos,
+        [&](gdm_ctx *c, int w, int i, gdm_solve_info *inf) {
+            const gdm_backward_item *it = &items[i];
+            double *a = acc + (int64_t)w * 5 * n;
+            return gdm_launch_backward(c, &it->prob, prec, it->A, it->lda, it->ipiv, it->F, it->n_rhs, it->e0,
+                                       it->khat ? it->khat : zhat, it->gF, it->g_sigma, a, a + 3 * n,
+                                       it->grad_wavelength, inf);
+        },
+        backward_sum, &bs);
+    cudaFreeAsync(acc, ctx->stream);
+    return st;
 }
 
 }  // extern "C"

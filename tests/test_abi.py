@@ -59,26 +59,29 @@ def test_built_for_sm103a():
     assert os.path.exists(_build.LIB)
 
 
-def test_batch_item_layout_matches_the_header(tmp_path):
-    """The ctypes mirror of gdm_batch_item has the C compiler's size and field offsets."""
+@pytest.mark.parametrize("cname,pyname", [("gdm_batch_item", "BatchItem"), ("gdm_backward_item", "BackwardItem")])
+def test_batch_item_layout_matches_the_header(tmp_path, cname, pyname):
+    """The ctypes mirrors of the batch structs have the C compiler's size and field offsets."""
     import shutil
     import subprocess
     from paper_2505_09545_gb300 import binding
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    fields = [f for f, _ in binding.BatchItem._fields_]
+    cls = getattr(binding, pyname)
+    fields = [f for f, _ in cls._fields_]
     src = tmp_path / "layout.c"
-    body = "".join(f'printf("%zu\\n", offsetof(gdm_batch_item, {f}));' for f in fields)
+    body = "".join(f'printf("%zu\\n", offsetof({cname}, {f}));' for f in fields)
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gdm.h"\n'
-                   f'int main(void) {{ printf("%zu\\n", sizeof(gdm_batch_item)); {body} return 0; }}\n')
+                   f'int main(void) {{ printf("%zu\\n", sizeof({cname})); {body} return 0; }}\n')
     exe = tmp_path / "layout"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    assert out[0] == C.sizeof(binding.BatchItem)
-    assert out[1:] == [getattr(binding.BatchItem, f).offset for f in fields]
+    assert out[0] == C.sizeof(cls)
+    assert out[1:] == [getattr(cls, f).offset for f in fields]
 
 
 def test_batched_and_autotune_reject_a_null_context(lib):
     assert lib.gdm_solve_batched(None, 2, None, 0, None, 0, None) == 1
     assert lib.gdm_autotune(None, 2, None, 0, None) == 1
+    assert lib.gdm_backward_batched(None, 2, None, 0, 0, None, None, None) == 1

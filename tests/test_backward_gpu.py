@@ -91,3 +91,38 @@ def test_backward_matches_finite_differences(G, ctx):
         np.testing.assert_allclose(gp[l, c], fd, rtol=1e-5, atol=1e-7 * np.abs(gp).max())
     fd = (L(lm=lam + h) - L(lm=lam - h)) / (2 * h)
     np.testing.assert_allclose(gl, fd, rtol=1e-5)
+
+
+def spectrum_loss_and_grads(G, ctx, cyl, lams, precision, n_streams):
+    from paper_2505_09545_gb300 import autograd as AG
+    pos = torch.tensor(cyl.pos, device=DEV, requires_grad=True)
+    eps = torch.tensor(cyl.eps, device=DEV, requires_grad=True)
+    wls = torch.tensor(lams, dtype=torch.float64, device=DEV, requires_grad=True)
+    rp = torch.tensor(cyl.r_eval, device=DEV)
+    F, sig = AG.scatter_spectrum(pos, eps, wls, ctx, cyl.step, cyl.e0, precision=precision, n_streams=n_streams)
+    L = 0.0
+    for i in range(len(lams)):
+        E = AG.nearfield(pos, eps, wls[i], F[i], rp, ctx, cyl.step, cyl.e0)
+        L = L + (E.abs() ** 2).sum() + sig[i, :, 1].sum()
+    L.backward()
+    return float(L.detach()), pos.grad.cpu().numpy(), eps.grad.cpu().numpy(), wls.grad.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision,n_streams", [("tf32", 3), ("fp64", 2)])
+def test_spectrum_backward_matches_oracle(G, ctx, precision, n_streams):
+    """Loss summed over three wavelengths through scatter_spectrum (concurrent forward solves and adjoint
+    solves, gradients summed on the GPU): the loss and every gradient against the oracle's adjoint summed
+    over the same wavelengths (1e-8 normwise), and each wavelength's own gradient."""
+    cyl = small_cylinder()
+    lams = [455.0, 610.0, 780.0]
+    L, gp, ge, gl = spectrum_loss_and_grads(G, ctx, cyl, lams, precision, n_streams)
+    Lo, gpo, geo, glo = 0.0, 0.0, 0.0, []
+    for lam in lams:
+        pr = O.Problem(cyl.pos, lam, 3, eps=cyl.eps, step=cyl.step)
+        a, b, c, d = O.loss_and_grad_probe_sca(pr, cyl.e0, cyl.r_eval[0])
+        Lo, gpo, geo = Lo + a, gpo + b, geo + c
+        glo.append(d)
+    assert abs(L - Lo) <= 1e-9 * abs(Lo)
+    assert np.linalg.norm(gp - gpo) <= 1e-8 * np.linalg.norm(gpo)
+    assert np.linalg.norm(ge - geo) <= 1e-8 * np.linalg.norm(geo)
+    np.testing.assert_allclose(gl, np.array(glo), rtol=1e-8, atol=1e-14)
