@@ -41,9 +41,16 @@ template <int BN, int SPLIT> struct Cfg {
     static constexpr int A_BYTES = BM * BK * 4;
     static constexpr int B_BYTES = BN * BK * 4;
     static constexpr int STAGE_BYTES = NP * (A_BYTES + B_BYTES);
+    // operand stages and C staging buffers share the 227 KB: the TF32 update (48 KB stages) takes four
+    // stages and two C buffers unless GDM_TC_STAGES3 selects three and four at build time
+#ifdef GDM_TC_STAGES3
     static constexpr int STAGES = 3;
+    static constexpr int NCB = (SPLIT == 3) ? 2 : 4;
+#else
+    static constexpr int STAGES = (SPLIT == 3) ? 3 : 4;
+    static constexpr int NCB = 2;
+#endif
     static constexpr int TMEM_COLS = 2 * BN;
-    static constexpr int NCB = (SPLIT == 3) ? 2 : 4;         // C staging buffers (128 rows x 32 columns each)
     static constexpr int CB_BYTES = BM * 32 * 4;
     static constexpr int LOOK = NCB / 2;                      // C chunks loaded ahead
     static constexpr int SMEM = STAGES * STAGE_BYTES + NCB * CB_BYTES + 1024 /*alignment*/ + 512 /*barriers*/;
