@@ -208,3 +208,49 @@ def random_cells(n, step=10.0, seed=0, box=None, lossy=True):
 
 def omega_ev_to_wavelength_nm(w_ev):
     return HC_EV_NM / np.asarray(w_ev, np.float64)
+
+
+def sphere_points(n, radius, center=(0.0, 0.0, 0.0), seed=0):
+    """n seeded points uniformly distributed on a sphere (probe and source positions around a structure)."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return np.asarray(center, np.float64) + radius * v
+
+
+def farthest_points(pos, m, seed=0):
+    """m positions picked from pos by farthest-point sampling from a seeded start (effective-dipole sites
+    spread through a structure)."""
+    pos = np.asarray(pos, np.float64)
+    rng = np.random.default_rng(seed)
+    idx = [int(rng.integers(len(pos)))]
+    d = np.linalg.norm(pos - pos[idx[0]], axis=1)
+    while len(idx) < m:
+        j = int(np.argmax(d))
+        idx.append(j)
+        d = np.minimum(d, np.linalg.norm(pos - pos[j], axis=1))
+    return pos[np.sort(idx)]
+
+
+def gpm_illumination_set(n_angles=8, n_sources=8, source_radius=200.0, center=(0.0, 0.0, 0.0), seed=0):
+    """Illuminations for an effective-model extraction: plane waves along n_angles seeded directions with
+    two orthogonal polarisations each (khat, e0 lists), and n_sources electric dipole sources of seeded
+    orientation on a sphere of radius source_radius (positions (s, 3), moments (s, 6)); the source moments
+    have magnitude source_radius^3 so that their near fields at the centre are of order one, like the
+    plane waves'."""
+    rng = np.random.default_rng(seed)
+    khat, e0 = [], []
+    for _ in range(n_angles):
+        k = rng.standard_normal(3)
+        k /= np.linalg.norm(k)
+        a = np.cross(k, [1.0, 0.0, 0.0] if abs(k[0]) < 0.9 else [0.0, 1.0, 0.0])
+        a /= np.linalg.norm(a)
+        b = np.cross(k, a)
+        for pol in (a, b):
+            khat.append(k)
+            e0.append(pol.astype(np.complex128))
+    ds_pos = sphere_points(n_sources, source_radius, center, seed + 1)
+    mom = np.zeros((n_sources, 6), np.complex128)
+    d = rng.standard_normal((n_sources, 3))
+    mom[:, :3] = source_radius ** 3 * d / np.linalg.norm(d, axis=1, keepdims=True)
+    return khat, e0, ds_pos, mom

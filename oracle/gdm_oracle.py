@@ -407,6 +407,56 @@ def loss_and_grad_probe_sca(prob: Problem, e0, r_probe, khat=(0.0, 0.0, 1.0)):
     return L, gpos, grad_eps, dLdk * dkdlam
 
 
+# ----------------------------------------------------------------------------- effective models (GPM)
+def dipole_source_fields(r_eval, r_src, moments, k0, k):
+    """Fields of local point-dipole sources in vacuum, used as illuminations for the effective-model
+    extraction (Sec. "Effective polarizabilities ..."): [E; H](r) = G6(r - r_s) [p_s; m_s] with the 6x6
+    dyad of Eq. (superprop_G). r_src (s, 3), moments (s, 6) complex. Returns (6 m, s): column q holds the
+    (E, H) of source q at every point."""
+    r_eval = np.asarray(r_eval, np.float64)
+    R = r_eval[:, None, :] - np.asarray(r_src, np.float64)[None, :, :]
+    EH = np.einsum("iqab,qb->iaq", green6(R, k0, k), np.asarray(moments, np.complex128))
+    return EH.reshape(-1, len(r_src))
+
+
+def gpm_illuminations(prob: Problem, r_eval, pw_khat, pw_e0, ds_pos, ds_mom):
+    """The extraction's illumination set at r_eval: plane waves (one per (khat, e0) pair, unit-free
+    amplitudes e0), then local dipole sources. Returns (6 m, n_ill) incident (E, H) per point."""
+    cols = [plane_wave(r_eval, prob.k, np.sqrt(prob.eps_env), e0, kh, 6) for kh, e0 in zip(pw_khat, pw_e0)]
+    if len(ds_pos):
+        cols.append(dipole_source_fields(r_eval, ds_pos, ds_mom, prob.k0, prob.k))
+    return np.concatenate(cols, axis=1)
+
+
+def gpm_extract(prob: Problem, r_gpm, r_probe, pw_khat, pw_e0, ds_pos, ds_mom):
+    """Global polarizability matrix of a discretised structure (Sec. "Effective polarizabilities",
+    GPM extraction), in the paper's order:
+      1. full simulations of the structure for every illumination of the set;
+      2. its scattered fields (E, H) at the probe positions;
+      3. the effective electric and magnetic dipole moments at the M positions r_gpm that reproduce
+         those fields best in the L2 sense (least squares through the 6x6 dyads);
+      4. alpha_eff (6M x 6M) minimising || alpha_eff F0 - P || over the illuminations, F0 the incident
+         (E, H) at the M positions and P the fitted moments: alpha_eff = P F0^+.
+    Vacuum host (the 6x6 dyads are the vacuum ones). LAPACK least squares (numpy lstsq) as the
+    library step. Returns (alpha_eff, P, F0g, rel_fit) with rel_fit the relative residual of step 3."""
+    assert prob.kind == 3 and prob.eps_env == 1.0
+    n = prob.n
+    F0c = gpm_illuminations(prob, prob.pos, pw_khat, pw_e0, ds_pos, ds_mom)
+    nill = F0c.shape[1]
+    F0c = F0c.reshape(n, 6, nill)[:, :3].reshape(3 * n, nill)
+    F = prob.solve(F0c)
+    E, H = prob.nearfield(F, r_probe, None, with_incident=False)
+    S = np.concatenate([E, H], axis=1).reshape(-1, nill)
+    R = np.asarray(r_probe, np.float64)[:, None, :] - np.asarray(r_gpm, np.float64)[None, :, :]
+    G6 = green6(R, prob.k0, prob.k)                                   # (P, M, 6, 6)
+    Gp = G6.transpose(0, 2, 1, 3).reshape(6 * len(r_probe), 6 * len(r_gpm))
+    P = np.linalg.lstsq(Gp, S, rcond=None)[0]
+    rel_fit = np.linalg.norm(Gp @ P - S) / np.linalg.norm(S)
+    F0g = gpm_illuminations(prob, r_gpm, pw_khat, pw_e0, ds_pos, ds_mom)
+    alpha_t = np.linalg.lstsq(F0g.T, P.T, rcond=None)[0]
+    return alpha_t.T, P, F0g, rel_fit
+
+
 # ----------------------------------------------------------------------------- Mie theory
 def mie_coefficients(m, x, n_max=None):
     """Bohren & Huffman sphere coefficients a_n, b_n (n = 1..n_max) for relative index m
