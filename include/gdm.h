@@ -237,6 +237,30 @@ typedef struct {
 gdm_status gdm_backward_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_backward_item *items, int n_items,
                                 int n_streams, double *grad_pos, double *grad_eps, gdm_solve_info *infos);
 
+/* ---------------------------------------------------------------- effective models */
+
+/* Global polarizability matrix (GPM) of a discretised structure (Sec. "Effective
+ * polarizabilities", GPM extraction; vacuum host, kind 3): the structure is assembled into A
+ * (as gdm_assemble), factored once and solved (FP64-refined) for n_pw plane waves and n_ds
+ * local dipole sources; its scattered (E, H) at the n_probe probe positions are fitted in the
+ * least-squares sense by electric and magnetic dipoles at the n_sites positions r_gpm (one
+ * moment set per illumination); then alpha_eff (6M x 6M, M = n_sites) minimises
+ * || alpha_eff F0 - P || over the illuminations, F0 the incident (E, H) at the sites and P the
+ * fitted moments, i.e. alpha_eff = P F0^+.
+ * A, lda, ipiv: matrix storage and pivots as for gdm_solve (overwritten).
+ * r_gpm: device M x 3 (1 <= M <= 64). r_probe: device n_probe x 3 (n_probe >= M).
+ * pw_khat: host n_pw x 3 unit directions; pw_e0: host n_pw x 3 complex128 amplitudes.
+ * ds_pos: device n_ds x 3; ds_mom: device n_ds x 6 complex128 (p, m) source moments.
+ * n_pw + n_ds <= 512 and >= 6 M. alpha_eff: device (6M) x (6M) complex128, column-major,
+ * per site (E, H) -> (p, m) ordering. moments: device (6M) x (n_pw + n_ds) complex128 or NULL.
+ * rel_fit: host, relative L2 residual of the moment fit, or NULL. Synchronous.
+ * GDM_ERR_SINGULAR when the fit's normal matrix is not positive definite (too few or badly
+ * placed probes or illuminations for the number of sites). */
+gdm_status gdm_gpm_extract(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, void *A, int64_t lda,
+                           int32_t *ipiv, const double *r_gpm, int n_sites, const double *r_probe, int n_probe,
+                           int n_pw, const double *pw_khat, const double *pw_e0, int n_ds, const double *ds_pos,
+                           const double *ds_mom, double *alpha_eff, double *moments, double *rel_fit);
+
 /* LU block-width autotuner (no paper counterpart). For each size class present in sizes
  * (system dimensions kind*n; classes <= 512, 1024, ..., 32768, larger), times the
  * factorisation of a synthetic well-conditioned complex64 matrix of the class's largest

@@ -92,6 +92,8 @@ _SIGS = {
     "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, P], C.c_int),
     "gdm_solve_batched": ([P, C.c_int, P, C.c_int, P, C.c_int, P], C.c_int),
     "gdm_autotune": ([P, C.c_int, P, C.c_int, P], C.c_int),
+    "gdm_gpm_extract": ([P, C.c_int, C.POINTER(Problem), P, I64, P, P, C.c_int, P, C.c_int, C.c_int, P, P, C.c_int,
+                         P, P, P, P, PD], C.c_int),
     "gdm_backward_batched": ([P, C.c_int, P, C.c_int, C.c_int, P, P, P], C.c_int),
     "gdm_cross_sections_noalloc": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
     "gdm_backward": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, C.c_int, PD, PD, P, PD, P, P, P,
@@ -432,6 +434,35 @@ def backward_batched(ctx: Context, probs, As, ipivs, Fs, e0, precision="tf32", k
     ctx._check(lib().gdm_backward_batched(ctx.h, PRECISION[precision], items, n, int(n_streams), _ptr(grad_pos),
                                           _ptr(grad_eps), infos), "gdm_backward_batched")
     return grad_pos, grad_eps, grad_wavelengths, [infos[i].as_dict() for i in range(n)]
+
+
+def gpm_extract(ctx: Context, prob: GDMProblem, r_gpm, r_probe, pw_khat, pw_e0, ds_pos, ds_mom, precision="tf32"):
+    """gdm_gpm_extract: effective (E, H) -> (p, m) polarizability matrix of the structure at the sites r_gpm
+    ((M, 3) device), fitted to its scattered fields at r_probe ((P, 3) device) for plane waves (host lists
+    khat, e0) and dipole sources (device (s, 3) positions, (s, 6) moments). Returns (alpha_eff (6M, 6M),
+    moments (6M, n_ill), relative residual of the moment fit)."""
+    M = r_gpm.shape[0]
+    kh = np.ascontiguousarray(np.asarray(pw_khat, np.float64).reshape(-1, 3))
+    e0 = np.ascontiguousarray(np.asarray(pw_e0, np.complex128).reshape(-1, 3))
+    n_pw, n_ds = kh.shape[0], (0 if ds_pos is None else ds_pos.shape[0])
+    dev = r_gpm.device
+    ns = prob.size
+    A = torch.empty((ns, padded_lda(ns)), dtype=torch.complex128 if precision == "fp64" else torch.complex64,
+                    device=dev)
+    ipiv = torch.empty(ns, dtype=torch.int32, device=dev)
+    alpha = torch.empty((6 * M, 6 * M), dtype=torch.complex128, device=dev)
+    mom = torch.empty((n_pw + n_ds, 6 * M), dtype=torch.complex128, device=dev)
+    rel = D(0.0)
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_gpm_extract(ctx.h, PRECISION[precision], C.byref(s), _ptr(A), A.shape[1], _ptr(ipiv),
+                                     _ptr(r_gpm.contiguous()), M, _ptr(r_probe.contiguous()), r_probe.shape[0], n_pw,
+                                     kh.ctypes.data, e0.ctypes.data, n_ds,
+                                     _ptr(None if ds_pos is None else ds_pos.contiguous()),
+                                     _ptr(None if ds_mom is None else ds_mom.contiguous()), _ptr(alpha), _ptr(mom),
+                                     C.byref(rel)), "gdm_gpm_extract")
+    # the library writes column-major matrices
+    return alpha.t(), mom.t(), rel.value
 
 
 def autotune(ctx: Context, sizes, precision="tf32"):
