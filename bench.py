@@ -410,6 +410,50 @@ def run_gpm(args):
     ctx.close()
 
 
+def run_farfield(args):
+    """Far-field scattering cross section of the solved cuboid (N = 12,000, both polarisations): one step =
+    one gdm_sigma_farfield call on a 64 x 128 (Gauss-Legendre cos theta x uniform phi) grid, i.e.
+    8,192 directions x 12,000 cells x 2 illuminations of phased sums in FP64."""
+    import numpy as np
+    import torch
+    import gdm_workloads as W
+    import paper_2505_09545_gb300 as G
+    ws, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s = W.cuboid_precision(40, 30, 10)
+    lam = float(s.wavelengths[0])
+    ctx = G.Context(local)
+    pos = torch.tensor(s.pos, device=dev)
+    prob = G.GDMProblem(pos, lam, 3, eps=torch.tensor(s.eps, device=dev), step=s.step)
+    F0 = G.incident_planewave(ctx, pos, lam, s.e0)
+    A = G.assemble(ctx, prob, args.precision)
+    F, _, _ = G.solve(ctx, prob, A, F0, args.precision)
+    del A
+    e2 = np.ones(2)
+    for _ in range(max(1, args.warmup)):
+        sig = G.sigma_farfield(ctx, prob, F, e2, 64, 128)
+    torch.cuda.synchronize()
+    e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0_.record()
+    for _ in range(args.steps):
+        sig = G.sigma_farfield(ctx, prob, F, e2, 64, 128)
+    e1_.record()
+    torch.cuda.synchronize()
+    ms = e0_.elapsed_time(e1_) / args.steps
+    ext, sca, ab = G.cross_sections(ctx, prob, F0, F, e2)
+    pairs = 64 * 128 * s.n * 2
+    line = {"metric": "far-field sigma_sca s", "value": ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"cuboid 40x30x10 (N={s.n}) solved fields, 64x128 far-field grid, 2 illuminations"},
+            "pairs_per_s": pairs / (ms / 1e3),
+            "sigma_sca_ff_nm2": sig.cpu().tolist(), "sigma_ext_minus_abs_nm2": (ext - ab).cpu().tolist()}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -462,9 +506,10 @@ def main():
                     help="cells per axis of the cuboid workload (smaller cases are for profiling only)")
     ap.add_argument("--fp64-cuboid", default="20x15x10",
                     help="cuboid of the FP64-GPU-path comparison (40x30x10 = the full workload, ~2 min)")
-    ap.add_argument("--workload", default="cuboid", choices=["cuboid", "metasurface", "batch", "gpm"],
+    ap.add_argument("--workload", default="cuboid", choices=["cuboid", "metasurface", "batch", "gpm", "farfield"],
                     help="cuboid: the headline assemble+solve line; metasurface: 64x64 ED/MD array, 32 wavelengths; "
-                         "batch: 256 uneven blobs, each at its own wavelength; gpm: effective-model extraction")
+                         "batch: 256 uneven blobs, each at its own wavelength; gpm: effective-model extraction; "
+                         "farfield: far-field sigma_sca of the solved cuboid")
     ap.add_argument("--streams", type=int, default=0, help="batch workload: concurrent streams (0 = default)")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: keep the default LU block width")
     ap.add_argument("--no-extras", action="store_true",
@@ -484,6 +529,8 @@ def main():
         return run_batch(args)
     if args.workload == "gpm":
         return run_gpm(args)
+    if args.workload == "farfield":
+        return run_farfield(args)
 
     ws, rank, local = dist_setup()
     if ws > 1:

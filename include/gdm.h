@@ -299,6 +299,22 @@ gdm_status gdm_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, co
 gdm_status gdm_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,
                               int n_rhs, const double *e0_norm2, double *ext, double *sca, double *abs);
 
+/* Far-field scattering amplitudes (Sec. "Observables", scattering by repropagation of the dipoles
+ * to infinity): the scattered field along rhat is f(rhat) exp(ikr)/r with
+ *   f(rhat) = k^2/eps_env sum_j exp(-i k rhat.r_j) [p_j - rhat (rhat.p_j) - rhat x m_j].
+ * F: device (kind*n) x n_rhs solved fields. dirs: device q x 3 unit vectors. f_out: device
+ * (3q) x n_rhs complex128. FP64. */
+gdm_status gdm_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int n_rhs, const double *dirs,
+                        int64_t q, double *f_out);
+
+/* Scattering cross section from the far field: sigma_sca,ff = integral of |f|^2 over the unit
+ * sphere / |E0|^2, with n_theta Gauss-Legendre nodes in cos(theta) times n_phi uniform azimuths
+ * (the library builds the grid). For radiatively consistent models it equals sigma_ext -
+ * sigma_abs; for cells it is the far-field value that gdm_cross_sections' sigma_sca (a
+ * difference) approximates. e0_norm2: host n_rhs |E0|^2; sigma: device n_rhs doubles (nm^2). */
+gdm_status gdm_sigma_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int n_rhs, const double *e0_norm2,
+                              int n_theta, int n_phi, double *sigma);
+
 /* Largest ceil(n/256) * n_rhs that gdm_cross_sections_noalloc accepts: its fixed device
  * scratch holds this many (ext, abs) partial-sum pairs, 1 MiB per device. */
 #define GDM_XSEC_NOALLOC_MAX_PARTS 65536

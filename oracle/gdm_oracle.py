@@ -243,6 +243,21 @@ class Problem:
         ab = pref * ab
         return ext, ext - ab, ab
 
+    def farfield_amplitude(self, F, dirs):
+        """Far-field amplitude f(rhat) at unit directions dirs (q, 3) (Sec. "Observables", repropagation to
+        infinity): the scattered field along rhat is f exp(ikr)/r, f = k^2/eps_env sum_j exp(-ik rhat.r_j)
+        [p_j - rhat (rhat.p_j) - rhat x m_j]. Returns (q, 3, n_rhs)."""
+        rh = np.asarray(dirs, np.float64)
+        nr = F.shape[1]
+        P = self.moments(F).reshape(self.n, self.kind, nr)
+        phase = np.exp(-1j * self.k * (rh @ self.pos.T))
+        p = np.einsum("qj,jar->qar", phase, P[:, :3])
+        f = p - rh[:, :, None] * np.einsum("qa,qar->qr", rh, p)[:, None, :]
+        if self.kind == 6:
+            mm = np.einsum("qj,jar->qar", phase, P[:, 3:])
+            f = f - np.cross(rh[:, :, None], mm, axisa=1, axisb=1, axisc=1)
+        return f * self.k ** 2 / self.eps_env
+
     def farfield_scattering(self, F, e0, n_theta=64, n_phi=128):
         """sigma_sca by integrating the far-field intensity over the unit sphere
         (Sec. "Observables", scattered intensity via repropagation). Gauss-Legendre in

@@ -92,6 +92,8 @@ _SIGS = {
     "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, P], C.c_int),
     "gdm_solve_batched": ([P, C.c_int, P, C.c_int, P, C.c_int, P], C.c_int),
     "gdm_autotune": ([P, C.c_int, P, C.c_int, P], C.c_int),
+    "gdm_farfield": ([P, C.POINTER(Problem), P, C.c_int, P, I64, P], C.c_int),
+    "gdm_sigma_farfield": ([P, C.POINTER(Problem), P, C.c_int, PD, C.c_int, C.c_int, P], C.c_int),
     "gdm_gpm_extract": ([P, C.c_int, C.POINTER(Problem), P, I64, P, P, C.c_int, P, C.c_int, C.c_int, P, P, C.c_int,
                          P, P, P, P, PD], C.c_int),
     "gdm_backward_batched": ([P, C.c_int, P, C.c_int, C.c_int, P, P, P], C.c_int),
@@ -463,6 +465,30 @@ def gpm_extract(ctx: Context, prob: GDMProblem, r_gpm, r_probe, pw_khat, pw_e0, 
                                      C.byref(rel)), "gdm_gpm_extract")
     # the library writes column-major matrices
     return alpha.t(), mom.t(), rel.value
+
+
+def farfield(ctx: Context, prob: GDMProblem, F, dirs):
+    """Far-field amplitudes f(rhat) at the unit directions dirs ((q, 3) device): (n_rhs, 3q) complex128."""
+    n_rhs = F.shape[0]
+    q = dirs.shape[0]
+    out = torch.empty((n_rhs, 3 * q), dtype=torch.complex128, device=F.device)
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_farfield(ctx.h, C.byref(s), _ptr(F.contiguous()), n_rhs, _ptr(dirs.contiguous()), q,
+                                  _ptr(out)), "gdm_farfield")
+    return out
+
+
+def sigma_farfield(ctx: Context, prob: GDMProblem, F, e0_norm2, n_theta=64, n_phi=128):
+    """sigma_sca from the far-field integral (device (n_rhs,) float64, nm^2)."""
+    n_rhs = F.shape[0]
+    na, npp = _dbl_array(e0_norm2)
+    out = torch.empty(n_rhs, dtype=torch.float64, device=F.device)
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_sigma_farfield(ctx.h, C.byref(s), _ptr(F.contiguous()), n_rhs, npp, int(n_theta),
+                                        int(n_phi), _ptr(out)), "gdm_sigma_farfield")
+    return out
 
 
 def autotune(ctx: Context, sizes, precision="tf32"):

@@ -4,6 +4,8 @@
 
 #include <new>
 
+#include <vector>
+
 #include "gdm_internal.cuh"
 
 #include <stdlib.h>
@@ -436,6 +438,86 @@ gdm_status gdm_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *
         if (!(e0_norm2[r] > 0)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "|E0|^2 must be > 0");
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     return gdm_launch_cross_sections(ctx, p, F0, F, n_rhs, e0_norm2, ext, sca, abs);
+}
+
+gdm_status gdm_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int n_rhs, const double *dirs, int64_t q,
+                        double *f_out) {
+    GDM_TRY(check_problem(ctx, p));
+    if (!F || !dirs || !f_out) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (q < 1 || n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "need q >= 1, n_rhs in [1, 64]");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return gdm_launch_farfield(ctx, p, F, n_rhs, dirs, q, f_out, nullptr, nullptr, nullptr);
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n from the Chebyshev-like guess)
+static void gauss_legendre(int n, double *x, double *w) {
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; i++) {
+        double z = cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int l = 2; l <= n; l++) {
+                const double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) {
+                p1 = z;
+                p0 = 1.0;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int l = 2; l <= n; l++) {
+            const double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) p0 = 1.0;
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+gdm_status gdm_sigma_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int n_rhs, const double *e0_norm2,
+                              int n_theta, int n_phi, double *sigma) {
+    GDM_TRY(check_problem(ctx, p));
+    if (!F || !e0_norm2 || !sigma) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n_rhs must be in [1, 64]");
+    if (n_theta < 2 || n_theta > 4096 || n_phi < 1 || n_phi > 8192)
+        return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "need 2 <= n_theta <= 4096 and 1 <= n_phi <= 8192");
+    for (int r = 0; r < n_rhs; r++)
+        if (!(e0_norm2[r] > 0)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "|E0|^2 must be > 0");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const int64_t q = (int64_t)n_theta * n_phi;
+    std::vector<double> x(n_theta), w(n_theta), h((size_t)4 * q + n_rhs);
+    gauss_legendre(n_theta, x.data(), w.data());
+    const double pi = 3.14159265358979323846, dphi = 2.0 * pi / n_phi;
+    for (int i = 0; i < n_theta; i++) {
+        const double ct = x[i], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+        for (int j = 0; j < n_phi; j++) {
+            const int64_t t = (int64_t)i * n_phi + j;
+            h[3 * t] = st * cos(j * dphi);
+            h[3 * t + 1] = st * sin(j * dphi);
+            h[3 * t + 2] = ct;
+            h[3 * q + t] = w[i] * dphi;
+        }
+    }
+    for (int r = 0; r < n_rhs; r++) h[4 * q + r] = 1.0 / e0_norm2[r];
+    double *d = nullptr;
+    GDM_CUDA_TRY(ctx, cudaMallocAsync((void **)&d, h.size() * sizeof(double), ctx->stream));
+    gdm_status st = GDM_OK;
+    if (cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        st = gdm_fail(ctx, GDM_ERR_CUDA, "far-field grid upload");
+    if (st == GDM_OK) st = gdm_launch_farfield(ctx, p, F, n_rhs, d, q, nullptr, d + 3 * q, d + 4 * q, sigma);
+    // the host grid must stay alive until the copy has been consumed
+    cudaStreamSynchronize(ctx->stream);
+    cudaFreeAsync(d, ctx->stream);
+    return st;
 }
 
 gdm_status gdm_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,

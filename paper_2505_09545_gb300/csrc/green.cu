@@ -884,6 +884,148 @@ gdm_status gdm_launch_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double
     return GDM_OK;
 }
 
+// ================================================================== far field
+// f(rhat) = k^2/eps_env sum_j exp(-i k rhat.r_j) [p_j - rhat (rhat.p_j) - rhat x m_j] for q directions; one
+// thread per direction, sources staged through shared memory, FP64. Optional quadrature: per CTA the
+// weighted sum of |f|^2 per RHS (partials for a deterministic final reduction).
+#define FF_T 128
+#define FF_S 64
+template <int KIND, int NR>
+__global__ void __launch_bounds__(FF_T) k_farfield(const double *__restrict__ dirs, int64_t q, const double *__restrict__ pos,
+                                                  const double2 *__restrict__ P, int64_t n, int rhs0, int nr_here,
+                                                  double k, double pref, double2 *__restrict__ f_out, int64_t n_rhs_out,
+                                                  const double *__restrict__ wts, double *__restrict__ part) {
+    __shared__ double sp[FF_S][3];
+    __shared__ double2 sm[FF_S][KIND][NR];
+    const int64_t t = blockIdx.x * (int64_t)FF_T + threadIdx.x;
+    const bool valid = t < q;
+    double rx = 0, ry = 0, rz = 1;
+    if (valid) {
+        rx = dirs[3 * t];
+        ry = dirs[3 * t + 1];
+        rz = dirs[3 * t + 2];
+    }
+    double2 acc[NR][KIND];
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+#pragma unroll
+        for (int a = 0; a < KIND; a++) acc[r][a] = make_double2(0.0, 0.0);
+    const int64_t ld = (int64_t)KIND * n;
+    for (int64_t s0 = 0; s0 < n; s0 += FF_S) {
+        const int sn = (int)min((int64_t)FF_S, n - s0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < sn * 3; e += FF_T) sp[e / 3][e % 3] = pos[3 * s0 + e];
+        for (int e = threadIdx.x; e < sn * KIND * NR; e += FF_T) {
+            const int jj = e / (KIND * NR), rem = e % (KIND * NR), a = rem / NR, r = rem % NR;
+            sm[jj][a][r] = (r < nr_here) ? P[(rhs0 + r) * ld + KIND * (s0 + jj) + a] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        if (valid)
+            for (int jj = 0; jj < sn; jj++) {
+                double sn_, cs_;
+                sincos(-k * (rx * sp[jj][0] + ry * sp[jj][1] + rz * sp[jj][2]), &sn_, &cs_);
+                const double2 e = make_double2(cs_, sn_);
+#pragma unroll
+                for (int r = 0; r < NR; r++)
+#pragma unroll
+                    for (int a = 0; a < KIND; a++) acc[r][a] = cadd(acc[r][a], cmul(e, sm[jj][a][r]));
+            }
+    }
+    double w2[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        w2[r] = 0.0;
+        if (!valid || r >= nr_here) continue;
+        const double2 *p = acc[r];
+        const double2 rp = cadd(cadd(cscale(p[0], rx), cscale(p[1], ry)), cscale(p[2], rz));
+        double2 f[3] = {csub(p[0], cscale(rp, rx)), csub(p[1], cscale(rp, ry)), csub(p[2], cscale(rp, rz))};
+        if (KIND == 6) {  // - rhat x m
+            const double2 *m = acc[r] + 3;
+            f[0] = csub(f[0], csub(cscale(m[2], ry), cscale(m[1], rz)));
+            f[1] = csub(f[1], csub(cscale(m[0], rz), cscale(m[2], rx)));
+            f[2] = csub(f[2], csub(cscale(m[1], rx), cscale(m[0], ry)));
+        }
+        double s2 = 0.0;
+        for (int a = 0; a < 3; a++) {
+            f[a] = cscale(f[a], pref);
+            s2 += f[a].x * f[a].x + f[a].y * f[a].y;
+            if (f_out) f_out[(int64_t)(rhs0 + r) * 3 * q + 3 * t + a] = f[a];
+        }
+        if (wts) w2[r] = wts[t] * s2;
+    }
+    if (part) {
+        __shared__ double red[NR][FF_T / 32];
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            double v = w2[r];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) red[r][threadIdx.x >> 5] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < NR) {
+            double v = 0.0;
+            for (int w = 0; w < FF_T / 32; w++) v += red[threadIdx.x][w];
+            part[(int64_t)(rhs0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+        }
+    }
+}
+
+__global__ void k_farfield_sum(const double *__restrict__ part, int nb, int n_rhs, const double *__restrict__ inv_e2,
+                               double *sigma) {
+    const int r = blockIdx.x;
+    if (r >= n_rhs) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) v += part[(int64_t)r * nb + b];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) sigma[r] = v * inv_e2[r];
+}
+
+gdm_status gdm_launch_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int n_rhs, const double *dirs,
+                               int64_t q, double *f_out, const double *wts, const double *inv_e2, double *sigma) {
+    const int64_t n = p->n;
+    const int kind = p->kind;
+    const double k = sqrt(p->eps_env) * gdm_k0(p);
+    const double d3_4pi = kind == 3 ? p->step * p->step * p->step / (4.0 * PI_D) : 0.0;
+    const unsigned nb = (unsigned)((q + FF_T - 1) / FF_T);
+    size_t need = ScratchCarver::round((size_t)kind * n * n_rhs * sizeof(double2)) +
+                  ScratchCarver::round((size_t)nb * n_rhs * sizeof(double)) + 1024;
+    void *ws;
+    GDM_TRY(gdm_scratch(ctx, need, &ws));
+    ScratchCarver sc(ws);
+    double2 *Pbuf = sc.take<double2>((size_t)kind * n * n_rhs);
+    double *part = sc.take<double>((size_t)nb * n_rhs);
+    dim3 g1((unsigned)((n + 127) / 128), (unsigned)n_rhs);
+    k_moments<<<g1, 128, 0, ctx->stream>>>((const double2 *)F, n, kind, n_rhs, (const double2 *)p->eps, p->eps_env,
+                                            d3_4pi, (const double2 *)p->alpha6, 0, Pbuf);
+    GDM_LAUNCHED(ctx, "moments");
+    const double pref = k * k / p->eps_env;
+    double *pt = wts ? part : nullptr;
+    for (int q0 = 0; q0 < n_rhs; q0 += 2) {
+        const int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
+        if (kind == 3) {
+            if (nr == 2)
+                k_farfield<3, 2><<<nb, FF_T, 0, ctx->stream>>>(dirs, q, p->pos, Pbuf, n, q0, nr, k, pref,
+                                                               (double2 *)f_out, n_rhs, wts, pt);
+            else
+                k_farfield<3, 1><<<nb, FF_T, 0, ctx->stream>>>(dirs, q, p->pos, Pbuf, n, q0, nr, k, pref,
+                                                               (double2 *)f_out, n_rhs, wts, pt);
+        } else {
+            if (nr == 2)
+                k_farfield<6, 2><<<nb, FF_T, 0, ctx->stream>>>(dirs, q, p->pos, Pbuf, n, q0, nr, k, pref,
+                                                               (double2 *)f_out, n_rhs, wts, pt);
+            else
+                k_farfield<6, 1><<<nb, FF_T, 0, ctx->stream>>>(dirs, q, p->pos, Pbuf, n, q0, nr, k, pref,
+                                                               (double2 *)f_out, n_rhs, wts, pt);
+        }
+        GDM_LAUNCHED(ctx, "farfield");
+    }
+    if (wts) {
+        k_farfield_sum<<<n_rhs, 32, 0, ctx->stream>>>(part, (int)nb, n_rhs, inv_e2, sigma);
+        GDM_LAUNCHED(ctx, "farfield_sum");
+    }
+    return GDM_OK;
+}
+
 // ================================================================== cross sections
 #define XS_BS 256
 __global__ void k_xsec_partial(const double2 *__restrict__ F0, const double2 *__restrict__ F, int64_t n, int kind,

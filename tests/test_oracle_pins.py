@@ -451,3 +451,22 @@ def test_gpm_fit_improves_with_the_number_of_sites():
         rels.append(O.gpm_extract(pr, r_gpm, r_probe, khat, e0, ds_pos, ds_mom)[3])
     assert all(b < a for a, b in zip(rels, rels[1:])), rels
     assert rels[-1] < 5e-3, rels
+
+
+@pytest.mark.parametrize("kind", [3, 6])
+def test_farfield_amplitude_is_the_limit_of_the_near_field(kind):
+    """f(rhat) = lim r exp(-ikr) E_sca(r rhat): the oracle's far-field amplitude against its own repropagated
+    near field at r = 4e8 nm (relative error ~ size/r and 1/(kr))."""
+    if kind == 3:
+        s = W.random_cells(30, seed=4)
+        pr = O.Problem(s.pos, 540.0, 3, eps=s.eps, step=s.step)
+    else:
+        s = W.metasurface_edmd(nx=3, ny=2, seed=3)
+        pr = O.Problem(s.pos, 640.0, 6, alpha6=O.lorentz_alpha6(s.omega0_e, s.omega0_m, s.gamma_ev, s.amp_nm, 640.0))
+    F = pr.solve(pr.plane_wave(s.e0))
+    dirs = W.sphere_points(7, 1.0, seed=5)
+    f = pr.farfield_amplitude(F, dirs)
+    r = 4e8
+    E, _ = pr.nearfield(F, r * dirs, None, with_incident=False)
+    lim = E * r * np.exp(-1j * pr.k * r)
+    assert np.abs(lim - f).max() <= 1e-5 * np.abs(f).max()
