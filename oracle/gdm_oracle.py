@@ -434,6 +434,37 @@ def dipole_source_fields(r_eval, r_src, moments, k0, k):
     return EH.reshape(-1, len(r_src))
 
 
+def dipole_illumination(prob: Problem, r_eval, src_pos, src_mom, kind_out=3):
+    """Incident field of point-dipole sources (Sec. "Illuminations": electric and magnetic dipole sources;
+    vacuum): column q = fields of source q at r_eval, (kind_out m, n_src)."""
+    EH = dipole_source_fields(r_eval, src_pos, src_mom, prob.k0, prob.k)
+    m = len(r_eval)
+    if kind_out == 6:
+        return EH
+    return EH.reshape(m, 6, -1)[:, :3].reshape(3 * m, -1)
+
+
+def ldos(prob: Problem, r0, magnetic=False):
+    """Partial local density of states of the structured environment, normalised to vacuum (Sec.
+    "Observables": electric and magnetic LDOS): for a unit dipole u (x, y, z) at r0, the structure is solved
+    under its field and rho_u / rho_0 = 1 + 3/(2 k^3) Im(u . E_sca(r0)) (H_sca for a magnetic dipole), the
+    emitter's decay rate relative to free space. Vacuum host, cells. Returns (n_pos, 3)."""
+    assert prob.kind == 3 and prob.eps_env == 1.0
+    r0 = np.asarray(r0, np.float64)
+    out = np.zeros((len(r0), 3))
+    for e, r in enumerate(r0):
+        mom = np.zeros((3, 6), np.complex128)
+        for u in range(3):
+            mom[u, u + (3 if magnetic else 0)] = 1.0
+        F0 = dipole_illumination(prob, prob.pos, np.repeat(r[None], 3, 0), mom, 3)
+        F = prob.solve(F0)
+        E, H = prob.nearfield(F, r[None], None, with_incident=False)
+        field = H if magnetic else E
+        for u in range(3):
+            out[e, u] = 1.0 + 1.5 / prob.k ** 3 * field[0, u, u].imag
+    return out
+
+
 def gpm_illuminations(prob: Problem, r_eval, pw_khat, pw_e0, ds_pos, ds_mom):
     """The extraction's illumination set at r_eval: plane waves (one per (khat, e0) pair, unit-free
     amplitudes e0), then local dipole sources. Returns (6 m, n_ill) incident (E, H) per point."""

@@ -470,3 +470,42 @@ def test_farfield_amplitude_is_the_limit_of_the_near_field(kind):
     E, _ = pr.nearfield(F, r * dirs, None, with_incident=False)
     lim = E * r * np.exp(-1j * pr.k * r)
     assert np.abs(lim - f).max() <= 1e-5 * np.abs(f).max()
+
+
+# ----------------------------------------------------------------------------- LDOS
+@pytest.mark.parametrize("magnetic", [False, True])
+def test_ldos_single_cell_closed_form(magnetic):
+    """One cell near an emitter: the scattered field at the emitter is G(r0 - r_c) alpha/(1 - S alpha)
+    E_src(r_c), with E_src = G^Ep(r_c - r0) u for an electric and G^Em = -G^Hp for a magnetic emitter, and
+    the returned field G^Ep (G^Hp) p_c: LDOS = 1 + 3/(2 k^3) Im(u . field)."""
+    step, eps, lam = 12.0, 9.0 + 0.4j, 610.0
+    rc = np.zeros((1, 3))
+    r0 = np.array([[0.0, 10.0, 25.0]])
+    pr = O.Problem(rc, lam, 3, eps=np.array([eps]), step=step)
+    got = O.ldos(pr, r0, magnetic=magnetic)[0]
+    al = O.cell_polarizability(eps, 1.0, step)
+    aeff = al / (1.0 - O.cubic_selfterm(1.0, step) * al)
+    k0 = k = 2 * np.pi / lam
+    R = rc[0] - r0[0]
+    want = []
+    for u in range(3):
+        e_u = np.eye(3)[u]
+        if magnetic:
+            Einc = -O.green_hp(R, k0, k) @ e_u
+            field = O.green_hp(-R, k0, k) @ (aeff * Einc)
+        else:
+            Einc = O.green_ep(R, k) @ e_u
+            field = O.green_ep(-R, k) @ (aeff * Einc)
+        want.append(1.0 + 1.5 / k ** 3 * np.imag(e_u @ field))
+    np.testing.assert_allclose(got, want, rtol=1e-12)
+
+
+def test_ldos_limits():
+    """Vacuum cells (eps = 1) leave the LDOS at exactly 1; a distant emitter sees ~1."""
+    s = W.random_cells(20, seed=3)
+    pr = O.Problem(s.pos, 600.0, 3, eps=np.ones(s.n, complex), step=s.step)
+    np.testing.assert_allclose(O.ldos(pr, np.array([[0.0, 0.0, 80.0]])), 1.0, atol=1e-15)
+    pr = O.Problem(s.pos, 600.0, 3, eps=s.eps, step=s.step)
+    far = O.ldos(pr, np.array([[0.0, 0.0, 2e5]]))
+    near = O.ldos(pr, np.array([[0.0, 0.0, 40.0]]))
+    assert np.all(np.abs(far - 1.0) < 1e-4) and np.abs(near - 1.0).max() > 1e-2
