@@ -454,6 +454,43 @@ def run_farfield(args):
     ctx.close()
 
 
+def run_ldos(args):
+    """Electric LDOS around the dielectric sphere (R = 60 nm, d = 10 nm, N = 925, eps = 12.25, lambda =
+    600 nm) at 32 emitter positions 15 nm outside its surface: one step = one gdm_ldos call (96 dipole
+    illuminations, one factorisation, refined solves, scattered fields at the emitters)."""
+    import torch
+    import gdm_workloads as W
+    import paper_2505_09545_gb300 as G
+    ws, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s = W.sphere_plain_fp64()
+    lam = float(s.wavelengths[0])
+    ctx = G.Context(local)
+    prob = G.GDMProblem(torch.tensor(s.pos, device=dev), lam, 3, eps=torch.tensor(s.eps, device=dev), step=s.step)
+    r0 = torch.tensor(W.sphere_points(32, 80.0, seed=3), device=dev)
+    for _ in range(max(1, args.warmup)):
+        out = G.ldos(ctx, prob, r0, precision=args.precision)
+    torch.cuda.synchronize()
+    e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0_.record()
+    for _ in range(args.steps):
+        out = G.ldos(ctx, prob, r0, precision=args.precision)
+    e1_.record()
+    torch.cuda.synchronize()
+    ms = e0_.elapsed_time(e1_) / args.steps
+    line = {"metric": "LDOS s (32 emitter positions x 3 orientations)", "value": ms / 1e3, "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64-tf32+f64" if args.precision == "tf32" else args.precision, "data": "synthetic",
+            "config": {"workload": f"sphere R=60 d=10 nm (N={s.n}), eps=12.25, lambda={lam:g} nm, 32 emitters on an "
+                                   "80 nm sphere, electric LDOS along x, y, z"},
+            "ldos_range": [float(out.min()), float(out.max())]}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -506,10 +543,10 @@ def main():
                     help="cells per axis of the cuboid workload (smaller cases are for profiling only)")
     ap.add_argument("--fp64-cuboid", default="20x15x10",
                     help="cuboid of the FP64-GPU-path comparison (40x30x10 = the full workload, ~2 min)")
-    ap.add_argument("--workload", default="cuboid", choices=["cuboid", "metasurface", "batch", "gpm", "farfield"],
+    ap.add_argument("--workload", default="cuboid", choices=["cuboid", "metasurface", "batch", "gpm", "farfield", "ldos"],
                     help="cuboid: the headline assemble+solve line; metasurface: 64x64 ED/MD array, 32 wavelengths; "
                          "batch: 256 uneven blobs, each at its own wavelength; gpm: effective-model extraction; "
-                         "farfield: far-field sigma_sca of the solved cuboid")
+                         "farfield: far-field sigma_sca of the solved cuboid; ldos: electric LDOS around the sphere")
     ap.add_argument("--streams", type=int, default=0, help="batch workload: concurrent streams (0 = default)")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: keep the default LU block width")
     ap.add_argument("--no-extras", action="store_true",
@@ -531,6 +568,8 @@ def main():
         return run_gpm(args)
     if args.workload == "farfield":
         return run_farfield(args)
+    if args.workload == "ldos":
+        return run_ldos(args)
 
     ws, rank, local = dist_setup()
     if ws > 1:

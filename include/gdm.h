@@ -158,6 +158,13 @@ gdm_status gdm_incident_planewave(gdm_ctx *ctx, const double *r, int64_t m, doub
                                   double eps_env, const double *e0, const double *khat, int n_rhs,
                                   int kind_out, double *F0);
 
+/* Incident field of point-dipole sources (Sec. "Illuminations": electric and magnetic dipole
+ * sources), vacuum: column q is [E; H](r) = G6(r - r_q) [p_q; m_q] at the m points r_eval.
+ * src_pos: device n_src x 3; src_mom: device n_src x 6 complex128 (p, m); 1 <= n_src <= 1024.
+ * kind_out 3 writes E only, 6 writes (E, H) per point. F0: device (kind_out*m) x n_src complex128. */
+gdm_status gdm_incident_dipole(gdm_ctx *ctx, const double *r_eval, int64_t m, double wavelength,
+                               const double *src_pos, const double *src_mom, int n_src, int kind_out, double *F0);
+
 /* ---------------------------------------------------------------- hot path */
 
 /* Assemble the dense system matrix A = I - G alpha (Eq. GDM_system_of_equations):
@@ -314,6 +321,16 @@ gdm_status gdm_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int
  * difference) approximates. e0_norm2: host n_rhs |E0|^2; sigma: device n_rhs doubles (nm^2). */
 gdm_status gdm_sigma_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int n_rhs, const double *e0_norm2,
                               int n_theta, int n_phi, double *sigma);
+
+/* Partial local density of states of the structured environment, normalised to vacuum (Sec.
+ * "Observables": electric and magnetic LDOS; the decay-rate enhancement of a dipole emitter):
+ * for unit dipoles along x, y, z at each of the n_pos positions r0, the structure (kind 3,
+ * vacuum) is solved under the emitter's field (one factorisation for all, FP64-refined) and
+ * rho_u / rho_0 = 1 + 3/(2 k^3) Im(u . E_sca(r0)) (H_sca when magnetic != 0).
+ * A, lda, ipiv: storage as for gdm_solve (assembled and factored here). r0: device n_pos x 3
+ * (1 <= n_pos <= 340, not on a cell). ldos: device n_pos x 3 doubles. Synchronous. */
+gdm_status gdm_ldos(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, void *A, int64_t lda, int32_t *ipiv,
+                    const double *r0, int n_pos, int magnetic, double *ldos);
 
 /* Largest ceil(n/256) * n_rhs that gdm_cross_sections_noalloc accepts: its fixed device
  * scratch holds this many (ext, abs) partial-sum pairs, 1 MiB per device. */

@@ -92,6 +92,8 @@ _SIGS = {
     "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, P], C.c_int),
     "gdm_solve_batched": ([P, C.c_int, P, C.c_int, P, C.c_int, P], C.c_int),
     "gdm_autotune": ([P, C.c_int, P, C.c_int, P], C.c_int),
+    "gdm_incident_dipole": ([P, P, I64, C.c_double, P, P, C.c_int, C.c_int, P], C.c_int),
+    "gdm_ldos": ([P, C.c_int, C.POINTER(Problem), P, I64, P, P, C.c_int, C.c_int, P], C.c_int),
     "gdm_farfield": ([P, C.POINTER(Problem), P, C.c_int, P, I64, P], C.c_int),
     "gdm_sigma_farfield": ([P, C.POINTER(Problem), P, C.c_int, PD, C.c_int, C.c_int, P], C.c_int),
     "gdm_gpm_extract": ([P, C.c_int, C.POINTER(Problem), P, I64, P, P, C.c_int, P, C.c_int, C.c_int, P, P, C.c_int,
@@ -488,6 +490,33 @@ def sigma_farfield(ctx: Context, prob: GDMProblem, F, e0_norm2, n_theta=64, n_ph
     ctx._sync_stream()
     ctx._check(lib().gdm_sigma_farfield(ctx.h, C.byref(s), _ptr(F.contiguous()), n_rhs, npp, int(n_theta),
                                         int(n_phi), _ptr(out)), "gdm_sigma_farfield")
+    return out
+
+
+def incident_dipole(ctx: Context, r, wavelength, src_pos, src_mom, kind_out=3):
+    """Fields of point dipoles (device (s, 3) positions, (s, 6) complex moments) at r ((m, 3) device):
+    (s, kind_out*m) complex128, one row per source."""
+    n_src = src_pos.shape[0]
+    out = torch.empty((n_src, kind_out * r.shape[0]), dtype=torch.complex128, device=r.device)
+    ctx._sync_stream()
+    ctx._check(lib().gdm_incident_dipole(ctx.h, _ptr(r.contiguous()), r.shape[0], float(wavelength),
+                                         _ptr(src_pos.contiguous()), _ptr(src_mom.contiguous()), n_src, kind_out,
+                                         _ptr(out)), "gdm_incident_dipole")
+    return out
+
+
+def ldos(ctx: Context, prob: GDMProblem, r0, magnetic=False, precision="tf32"):
+    """Electric (or magnetic) partial LDOS rho_u/rho_0 for u = x, y, z at r0 ((n, 3) device): (n, 3) float64."""
+    ns = prob.size
+    dev = r0.device
+    A = torch.empty((ns, padded_lda(ns)), dtype=torch.complex128 if precision == "fp64" else torch.complex64,
+                    device=dev)
+    ipiv = torch.empty(ns, dtype=torch.int32, device=dev)
+    out = torch.empty((r0.shape[0], 3), dtype=torch.float64, device=dev)
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_ldos(ctx.h, PRECISION[precision], C.byref(s), _ptr(A), A.shape[1], _ptr(ipiv),
+                              _ptr(r0.contiguous()), r0.shape[0], 1 if magnetic else 0, _ptr(out)), "gdm_ldos")
     return out
 
 

@@ -1,4 +1,5 @@
-// Effective-model (global polarizability matrix, GPM) extraction from a discretised structure
+// Point-dipole illuminations, the local density of states (LDOS) of a structured environment, and
+// effective-model (global polarizability matrix, GPM) extraction from a discretised structure
 // (Sec. "Effective polarizabilities", GPM extraction), all steps on the GPU:
 //   1. illumination fields: plane waves and local dipole sources, at the cells (E) and at the effective
 //      sites (E, H);
@@ -234,7 +235,111 @@ gdm_status lstsq(gdm_ctx *ctx, const double2 *A, int64_t lda, int ta, const doub
     return GDM_OK;
 }
 
+// moments of the LDOS emitters: source 3 e + u is a unit dipole along u (electric or magnetic) at r0[e]
+__global__ void k_ldos_sources(const double *__restrict__ r0, int n_pos, int magnetic, double *pos3, double2 *mom) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 3 * n_pos) return;
+    const int e = q / 3, u = q % 3;
+    for (int c = 0; c < 3; c++) pos3[3 * q + c] = r0[3 * e + c];
+    for (int c = 0; c < 6; c++) mom[6 * q + c] = make_double2(c == u + (magnetic ? 3 : 0) ? 1.0 : 0.0, 0.0);
+}
+
+// rho_u / rho_0 = 1 + 3/(2 k^3) Im(field_u at the emitter, from the emitter's own illumination)
+__global__ void k_ldos_extract(const double2 *__restrict__ field, int n_pos, double c, double *out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 3 * n_pos) return;
+    const int e = q / 3, u = q % 3;
+    out[q] = 1.0 + c * field[(int64_t)q * 3 * n_pos + 3 * e + u].y;
+}
+
+// E (and H) at m points of n_src point dipoles (device positions n_src x 3, moments n_src x 6), column q
+// = source q; id6 (36 n_src) and onehot (6 n_src x n_src) are scratch
+gdm_status dipole_fields(gdm_ctx *ctx, double wavelength, const double *src_pos, const double2 *mom, int n_src,
+                         const double *r_eval, int64_t m, double2 *E, double2 *H, double2 *id6, double2 *onehot) {
+    k_identity6<<<nblk(36 * (int64_t)n_src), 256, 0, ctx->stream>>>(id6, n_src);
+    GDM_LAUNCHED(ctx, "identity6");
+    k_onehot<<<nblk(6 * (int64_t)n_src * n_src), 256, 0, ctx->stream>>>(mom, n_src, onehot);
+    GDM_LAUNCHED(ctx, "onehot");
+    gdm_problem src = {n_src, 6, 0, src_pos, nullptr, (const double *)id6, 0.0, 1.0, wavelength};
+    return gdm_launch_nearfield(ctx, &src, (const double *)onehot, r_eval, m, nullptr, n_src, (double *)E, (double *)H);
+}
+
 }  // namespace
+
+extern "C" gdm_status gdm_incident_dipole(gdm_ctx *ctx, const double *r_eval, int64_t m, double wavelength,
+                                          const double *src_pos, const double *src_mom, int n_src, int kind_out,
+                                          double *F0) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    if (!r_eval || !src_pos || !src_mom || !F0) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (m < 1 || n_src < 1 || n_src > 1024) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "need m >= 1, 1 <= n_src <= 1024");
+    if (kind_out != 3 && kind_out != 6) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "kind_out must be 3 or 6");
+    if (!(wavelength > 0) || !isfinite(wavelength)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "bad wavelength");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    gdm_params_reset(ctx);
+    double2 *buf = nullptr;
+    const size_t cnt = (size_t)36 * n_src + (size_t)6 * n_src * n_src + (kind_out == 6 ? (size_t)6 * m * n_src : 0);
+    GDM_CUDA_TRY(ctx, cudaMallocAsync((void **)&buf, cnt * sizeof(double2), ctx->stream));
+    double2 *id6 = buf, *onehot = buf + 36 * n_src, *E = onehot + (size_t)6 * n_src * n_src, *H = E + 3 * m * n_src;
+    gdm_status st;
+    if (kind_out == 3) {
+        st = dipole_fields(ctx, wavelength, src_pos, (const double2 *)src_mom, n_src, r_eval, m, (double2 *)F0, nullptr,
+                           id6, onehot);
+    } else {
+        st = dipole_fields(ctx, wavelength, src_pos, (const double2 *)src_mom, n_src, r_eval, m, E, H, id6, onehot);
+        if (st == GDM_OK) {
+            k_interleave<<<nblk(6 * m * (int64_t)n_src), 256, 0, ctx->stream>>>(E, H, m, n_src, (double2 *)F0, 6 * m);
+            st = gdm_after_launch(ctx, "interleave");
+        }
+    }
+    cudaFreeAsync(buf, ctx->stream);
+    return st;
+}
+
+extern "C" gdm_status gdm_ldos(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, void *A, int64_t lda,
+                               int32_t *ipiv, const double *r0, int n_pos, int magnetic, double *ldos) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    GDM_TRY(gdm_check_solve_args(ctx, p, prec, A, lda, ipiv, r0, r0, 1));
+    if (p->kind != 3 || p->eps_env != 1.0)
+        return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "LDOS: discretised structures (kind 3) in vacuum");
+    if (!ldos) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (n_pos < 1 || n_pos > 340) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n_pos must be in [1, 340]");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    gdm_params_reset(ctx);
+    const int64_t n = p->n;
+    const int ns = 3 * n_pos;
+    const size_t c16 = sizeof(double2);
+    const size_t bytes = c16 * ((size_t)36 * ns + (size_t)6 * ns * ns + (size_t)6 * ns + (size_t)3 * n * ns * 2 +
+                                (size_t)3 * n_pos * ns * 2) +
+                         sizeof(double) * 3 * ns + 4096;
+    char *buf = nullptr;
+    GDM_CUDA_TRY(ctx, cudaMallocAsync((void **)&buf, bytes, ctx->stream));
+    ScratchCarver sc(buf);
+    double2 *id6 = sc.take<double2>((size_t)36 * ns), *onehot = sc.take<double2>((size_t)6 * ns * ns);
+    double2 *mom = sc.take<double2>((size_t)6 * ns);
+    double2 *F0 = sc.take<double2>((size_t)3 * n * ns), *F = sc.take<double2>((size_t)3 * n * ns);
+    double2 *Es = sc.take<double2>((size_t)3 * n_pos * ns), *Hs = sc.take<double2>((size_t)3 * n_pos * ns);
+    double *pos3 = sc.take<double>((size_t)3 * ns);
+    auto run = [&]() -> gdm_status {
+        k_ldos_sources<<<nblk(ns), 256, 0, ctx->stream>>>(r0, n_pos, magnetic, pos3, mom);
+        GDM_LAUNCHED(ctx, "ldos_sources");
+        GDM_TRY(dipole_fields(ctx, p->wavelength, pos3, mom, ns, p->pos, n, F0, nullptr, id6, onehot));
+        GDM_TRY(gdm_launch_assemble(ctx, p, prec, A, lda));
+        for (int q0 = 0; q0 < ns; q0 += 64) {
+            const int nr = ns - q0 < 64 ? ns - q0 : 64;
+            gdm_solve_opts o = {0, q0 ? GDM_SOLVE_FACTORED : 0, 0.0};
+            GDM_TRY(gdm_solve_core(ctx, p, prec, A, lda, ipiv, (const double *)(F0 + (int64_t)q0 * 3 * n),
+                                   (double *)(F + (int64_t)q0 * 3 * n), nr, &o, nullptr));
+        }
+        GDM_TRY(gdm_launch_nearfield(ctx, p, (const double *)F, r0, n_pos, nullptr, ns, (double *)Es, (double *)Hs));
+        const double k = 2.0 * 3.14159265358979323846 / p->wavelength;
+        k_ldos_extract<<<nblk(ns), 256, 0, ctx->stream>>>(magnetic ? Hs : Es, n_pos, 1.5 / (k * k * k), ldos);
+        GDM_LAUNCHED(ctx, "ldos_extract");
+        return GDM_OK;
+    };
+    gdm_status st = run();
+    cudaFreeAsync(buf, ctx->stream);
+    return st;
+}
 
 extern "C" gdm_status gdm_gpm_extract(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, void *A, int64_t lda,
                                       int32_t *ipiv, const double *r_gpm, int n_sites, const double *r_probe,
