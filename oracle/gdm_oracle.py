@@ -298,6 +298,36 @@ def plane_wave(r, k, n_env, e0, khat, kind_out):
     return np.concatenate([E, H], axis=1).reshape(-1, e0.shape[0])
 
 
+def gaussian_paraxial(r, k, n_env, e0, w0, focus=(0.0, 0.0, 0.0), theta=0.0, kind_out=3):
+    """Paraxial focused Gaussian beam (Sec. "Illuminations": GaussianParaxial, after the cited nano-optics
+    textbook), with the longitudinal field from the divergence condition (the paper's correction for tight
+    focus). Beam frame: propagation along z', focus at `focus`, incidence angle theta in the XZ plane
+    (z' = (sin theta, 0, cos theta) in the lab). With z0 = k w0^2 / 2 and g = 1 + i z'/z0:
+      E_t  = e0 exp(i k z') exp(-(x'^2 + y'^2) / (w0^2 g)) / g          (e0 transverse: x', y' components)
+      E_z' = (i/k) (dE_x'/dx' + dE_y'/dy'),  H_t = n_env z' x E_t,  H_z' = (i/k) (dH_x'/dx' + dH_y'/dy').
+    e0: (n_rhs, 3) complex in the beam frame (z' component ignored). Returns (m kind_out, n_rhs)."""
+    r = np.asarray(r, np.float64) - np.asarray(focus, np.float64)
+    e0 = np.atleast_2d(np.asarray(e0, np.complex128))
+    ct, st = np.cos(theta), np.sin(theta)
+    ex, ey, ez = np.array([ct, 0.0, -st]), np.array([0.0, 1.0, 0.0]), np.array([st, 0.0, ct])
+    xp, yp, zp = r @ ex, r @ ey, r @ ez
+    z0 = k * w0 * w0 / 2.0
+    g = 1.0 + 1j * zp / z0
+    u = np.exp(1j * k * zp) * np.exp(-(xp * xp + yp * yp) / (w0 * w0 * g)) / g      # (m,)
+    d = -2.0 / (w0 * w0 * g)                                                         # d/dx' of the envelope: d x' u
+    out = []
+    for q in range(e0.shape[0]):
+        a, b = e0[q, 0], e0[q, 1]
+        Ex, Ey = a * u, b * u
+        Ez = (1j / k) * d * (xp * a + yp * b) * u
+        Hx, Hy = -n_env * b * u, n_env * a * u
+        Hz = (1j / k) * d * (xp * (-n_env * b) + yp * (n_env * a)) * u
+        E = Ex[:, None] * ex + Ey[:, None] * ey + Ez[:, None] * ez
+        H = Hx[:, None] * ex + Hy[:, None] * ey + Hz[:, None] * ez
+        out.append(np.concatenate([E, H], 1) if kind_out == 6 else E)
+    return np.stack(out, -1).reshape(-1, e0.shape[0])
+
+
 # ----------------------------------------------------------------------------- sampled forms
 def residual_rows(prob: Problem, F0, F, rows):
     """r_i = F0_i - sum_j A_ij F_j for the dipoles in `rows` (O(N) per row): the

@@ -509,3 +509,61 @@ def test_ldos_limits():
     far = O.ldos(pr, np.array([[0.0, 0.0, 2e5]]))
     near = O.ldos(pr, np.array([[0.0, 0.0, 40.0]]))
     assert np.all(np.abs(far - 1.0) < 1e-4) and np.abs(near - 1.0).max() > 1e-2
+
+
+# ----------------------------------------------------------------------------- Gaussian beam
+def test_gaussian_beam_plane_wave_limit():
+    """A very wide beam (w0 = 1e6 nm) is the plane wave along its axis near the focus, E and H, also at an
+    oblique angle."""
+    k = 2 * np.pi / 600.0
+    r = W.sphere_points(40, 300.0, seed=1)
+    for theta in (0.0, 0.4):
+        e0 = np.array([[1.0, 0.3j, 0.0], [0.0, 1.0, 0.0]])
+        g = O.gaussian_paraxial(r, k, 1.0, e0, 1e6, theta=theta, kind_out=6)
+        kh = np.array([np.sin(theta), 0.0, np.cos(theta)])
+        lab = np.stack([e0[:, 0] * np.cos(theta), e0[:, 1], -e0[:, 0] * np.sin(theta)], 1)
+        pw = O.plane_wave(r, k, 1.0, lab, kh, 6)
+        np.testing.assert_allclose(g, pw, atol=1e-6)
+
+
+def test_gaussian_beam_power_is_conserved_along_the_axis():
+    """Paraxial energy conservation: the transverse integral of |E_t|^2 is pi w0^2 / 2 in every plane."""
+    k = 2 * np.pi / 600.0
+    w0 = 900.0
+    z0 = k * w0 * w0 / 2
+    x = np.linspace(-6 * w0 * 3, 6 * w0 * 3, 601)
+    X, Y = np.meshgrid(x, x)
+    for z in (0.0, z0, 3 * z0):
+        r = np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], 1)
+        E = O.gaussian_paraxial(r, k, 1.0, [[1.0, 0.0, 0.0]], w0).reshape(-1, 3)
+        power = np.sum(np.abs(E[:, 0]) ** 2 + np.abs(E[:, 1]) ** 2) * (x[1] - x[0]) ** 2
+        np.testing.assert_allclose(power, np.pi * w0 * w0 / 2, rtol=1e-6)
+
+
+def test_gaussian_beam_divergence_correction():
+    """The longitudinal field makes the beam divergence-free to the next paraxial order: central differences
+    of div E with it, relative to without it, shrink like 1/(k w0) (0.18 at w0 = 400 nm, 600 nm light;
+    four times smaller at w0 = 1600 nm)."""
+    k = 2 * np.pi / 600.0
+    h = 1e-2
+
+    def ratio(w0):
+        pts = W.sphere_points(20, 0.9 * w0, seed=4)
+
+        def div(with_z):
+            out = 0.0
+            for c in range(3):
+                dp = pts.copy(); dp[:, c] += h
+                dm = pts.copy(); dm[:, c] -= h
+                Ep = O.gaussian_paraxial(dp, k, 1.0, [[1.0, 0.0, 0.0]], w0).reshape(-1, 3)
+                Em = O.gaussian_paraxial(dm, k, 1.0, [[1.0, 0.0, 0.0]], w0).reshape(-1, 3)
+                if not with_z:
+                    Ep[:, 2] = 0
+                    Em[:, 2] = 0
+                out = out + (Ep[:, c] - Em[:, c]) / (2 * h)
+            return np.abs(out).max()
+
+        return div(True) / div(False)
+
+    r1, r4 = ratio(400.0), ratio(1600.0)
+    assert r1 < 0.3 and r4 < 0.4 * r1, (r1, r4)
