@@ -158,6 +158,17 @@ gdm_status gdm_incident_planewave(gdm_ctx *ctx, const double *r, int64_t m, doub
                                   double eps_env, const double *e0, const double *khat, int n_rhs,
                                   int kind_out, double *F0);
 
+/* Paraxial focused Gaussian beam (Sec. "Illuminations": GaussianParaxial, with the longitudinal
+ * field that keeps it divergence-free for tight focus). Beam frame: propagation along
+ * z' = (sin theta, 0, cos theta), focus at focus (host 3 doubles, nm), waist w0 (nm); with
+ * z0 = k w0^2/2 and g = 1 + i z'/z0 the transverse field is e0 exp(i k z')
+ * exp(-(x'^2 + y'^2)/(w0^2 g))/g, E_z' = (i/k) div_t E_t, H_t = n_env z' x E_t, H_z' likewise.
+ * e0: host n_rhs x 3 complex128 in the beam frame (x', y' used). r: device m x 3.
+ * F0: device (kind_out*m) x n_rhs complex128. */
+gdm_status gdm_incident_gaussian(gdm_ctx *ctx, const double *r, int64_t m, double wavelength, double eps_env,
+                                 const double *e0, double w0, const double *focus, double theta, int n_rhs,
+                                 int kind_out, double *F0);
+
 /* Incident field of point-dipole sources (Sec. "Illuminations": electric and magnetic dipole
  * sources), vacuum: column q is [E; H](r) = G6(r - r_q) [p_q; m_q] at the m points r_eval.
  * src_pos: device n_src x 3; src_mom: device n_src x 6 complex128 (p, m); 1 <= n_src <= 1024.

@@ -4,8 +4,8 @@ The compute lives in the CUDA library libgdm.so (C ABI: include/gdm.h); this
 package only builds/loads it and marshals arguments (see `binding`)."""
 from . import autograd  # noqa: F401
 from .binding import (Context, GDMError, GDMProblem, alpha6_lorentz, assemble, autotune, backward, cross_sections,
-                      farfield, gpm_extract, incident_dipole, ldos, sigma_farfield, incident_planewave, lib, nearfield, nearfield_backward, padded_lda, residual,
+                      farfield, gpm_extract, incident_dipole, incident_gaussian, ldos, sigma_farfield, incident_planewave, lib, nearfield, nearfield_backward, padded_lda, residual,
                       solve, solve_batched)
 
-__all__ = ["Context", "GDMError", "GDMProblem", "alpha6_lorentz", "assemble", "autotune", "backward", "cross_sections", "farfield", "gpm_extract", "incident_dipole", "ldos", "sigma_farfield", "incident_planewave",
+__all__ = ["Context", "GDMError", "GDMProblem", "alpha6_lorentz", "assemble", "autotune", "backward", "cross_sections", "farfield", "gpm_extract", "incident_dipole", "incident_gaussian", "ldos", "sigma_farfield", "incident_planewave",
            "lib", "nearfield", "nearfield_backward", "padded_lda", "residual", "solve", "solve_batched"]

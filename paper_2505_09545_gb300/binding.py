@@ -92,6 +92,8 @@ _SIGS = {
     "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, P], C.c_int),
     "gdm_solve_batched": ([P, C.c_int, P, C.c_int, P, C.c_int, P], C.c_int),
     "gdm_autotune": ([P, C.c_int, P, C.c_int, P], C.c_int),
+    "gdm_incident_gaussian": ([P, P, I64, C.c_double, C.c_double, PD, C.c_double, PD, C.c_double, C.c_int, C.c_int,
+                               P], C.c_int),
     "gdm_incident_dipole": ([P, P, I64, C.c_double, P, P, C.c_int, C.c_int, P], C.c_int),
     "gdm_ldos": ([P, C.c_int, C.POINTER(Problem), P, I64, P, P, C.c_int, C.c_int, P], C.c_int),
     "gdm_farfield": ([P, C.POINTER(Problem), P, C.c_int, P, I64, P], C.c_int),
@@ -490,6 +492,23 @@ def sigma_farfield(ctx: Context, prob: GDMProblem, F, e0_norm2, n_theta=64, n_ph
     ctx._sync_stream()
     ctx._check(lib().gdm_sigma_farfield(ctx.h, C.byref(s), _ptr(F.contiguous()), n_rhs, npp, int(n_theta),
                                         int(n_phi), _ptr(out)), "gdm_sigma_farfield")
+    return out
+
+
+def incident_gaussian(ctx: Context, r, wavelength, e0, w0, focus=(0.0, 0.0, 0.0), theta=0.0, eps_env=1.0,
+                      kind_out=3):
+    """Paraxial Gaussian beam at r ((m, 3) device): (n_rhs, kind_out*m) complex128; e0 (n_rhs, 3) in the beam
+    frame, waist w0, focus, incidence angle theta in the XZ plane."""
+    e0 = np.atleast_2d(np.asarray(e0, np.complex128))
+    n_rhs = e0.shape[0]
+    ea, ep = _dbl_array(e0.view(np.float64).reshape(-1))
+    fa, fp = _dbl_array(focus)
+    r = r.contiguous()
+    out = torch.empty((n_rhs, kind_out * r.shape[0]), dtype=torch.complex128, device=r.device)
+    ctx._sync_stream()
+    ctx._check(lib().gdm_incident_gaussian(ctx.h, _ptr(r), r.shape[0], float(wavelength), float(eps_env), ep,
+                                           float(w0), fp, float(theta), n_rhs, kind_out, _ptr(out)),
+               "gdm_incident_gaussian")
     return out
 
 

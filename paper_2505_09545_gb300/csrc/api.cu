@@ -337,6 +337,22 @@ gdm_status gdm_incident_planewave(gdm_ctx *ctx, const double *r, int64_t m, doub
     return gdm_launch_planewave(ctx, r, m, k, n_env, e0, khat, n_rhs, kind_out, F0);
 }
 
+gdm_status gdm_incident_gaussian(gdm_ctx *ctx, const double *r, int64_t m, double wavelength, double eps_env,
+                                 const double *e0, double w0, const double *focus, double theta, int n_rhs,
+                                 int kind_out, double *F0) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    if (!r || !e0 || !focus || !F0) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
+    if (m < 1 || n_rhs < 1 || n_rhs > 64) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "need m >= 1, n_rhs in [1, 64]");
+    if (kind_out != 3 && kind_out != 6) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "kind_out must be 3 or 6");
+    if (!(wavelength > 0) || !(eps_env > 0) || !(w0 > 0) || !isfinite(theta))
+        return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "need wavelength, eps_env, w0 > 0 and a finite angle");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    gdm_params_reset(ctx);
+    const double n_env = sqrt(eps_env);
+    const double k = n_env * 2.0 * 3.14159265358979323846 / wavelength;
+    return gdm_launch_gaussian(ctx, r, m, k, n_env, w0, focus, theta, e0, n_rhs, kind_out, F0);
+}
+
 gdm_status gdm_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda) {
     GDM_TRY(check_problem(ctx, p));
     GDM_TRY(check_prec(ctx, prec));

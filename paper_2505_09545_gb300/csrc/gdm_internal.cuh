@@ -192,6 +192,9 @@ gdm_status gdm_launch_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const d
                                      const double *e0_norm2, double *ext, double *sca, double *abs);
 gdm_status gdm_launch_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int n_rhs, const double *dirs,
                                int64_t q, double *f_out, const double *wts, const double *inv_e2, double *sigma);
+gdm_status gdm_launch_gaussian(gdm_ctx *ctx, const double *r, int64_t m, double k, double n_env, double w0,
+                               const double *focus, double theta, const double *e0, int n_rhs, int kind_out,
+                               double *F0);
 gdm_status gdm_launch_alpha6_lorentz(gdm_ctx *ctx, int64_t n, const double *w0e, const double *w0m, double gamma_ev,
                                      double amp_nm, double wavelength, double *out);
 gdm_status gdm_launch_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,

@@ -111,6 +111,57 @@ __global__ void k_planewave(const double *__restrict__ r, int64_t m, double k, d
     }
 }
 
+// Paraxial Gaussian beam at points (one thread per point and illumination): beam frame x' = (cos t, 0, -sin t),
+// y' = y, z' = (sin t, 0, cos t) about the focus; z0 = k w0^2/2, g = 1 + i z'/z0,
+// u = exp(i k z') exp(-(x'^2 + y'^2)/(w0^2 g)) / g; E_t = e0 u, E_z' = (i/k) (-2/(w0^2 g)) (x' e0x + y' e0y) u;
+// H_t = n z' x E_t and H_z' from the same divergence condition.
+__global__ void k_gaussian(const double *__restrict__ r, int64_t m, double k, double n_env, double w0, double fx,
+                           double fy, double fz, double ct, double st, const double *__restrict__ e0, int n_rhs,
+                           int kind_out, double2 *__restrict__ F0) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (i >= m || q >= n_rhs) return;
+    const double rx = r[3 * i] - fx, ry = r[3 * i + 1] - fy, rz = r[3 * i + 2] - fz;
+    const double xp = ct * rx - st * rz, yp = ry, zp = st * rx + ct * rz;
+    const double z0 = 0.5 * k * w0 * w0;
+    const double2 g = make_double2(1.0, zp / z0);
+    const double2 ig = crecip(g);
+    // exp(-(x'^2 + y'^2) ig / w0^2) exp(i k z')
+    const double2 ex = cscale(ig, -(xp * xp + yp * yp) / (w0 * w0));
+    double s, c;
+    sincos(k * zp + ex.y, &s, &c);
+    const double2 u = cmul(cscale(make_double2(c, s), exp(ex.x)), ig);
+    const double2 a = make_double2(e0[6 * q], e0[6 * q + 1]), b = make_double2(e0[6 * q + 2], e0[6 * q + 3]);
+    const double2 d = cscale(ig, -2.0 / (w0 * w0));                 // derivative factor
+    const double2 ik = make_double2(0.0, 1.0 / k);
+    const double2 Ex = cmul(a, u), Ey = cmul(b, u);
+    const double2 Ez = cmul(cmul(ik, d), cmul(cadd(cscale(a, xp), cscale(b, yp)), u));
+    const double2 Hx = cscale(cmul(b, u), -n_env), Hy = cscale(cmul(a, u), n_env);
+    const double2 Hz = cmul(cmul(ik, d), cmul(cadd(cscale(b, -n_env * xp), cscale(a, n_env * yp)), u));
+    double2 *o = F0 + (int64_t)q * kind_out * m + (int64_t)kind_out * i;
+    // lab = x' ex + y' ey + z' ez with ex = (ct, 0, -st), ey = (0, 1, 0), ez = (st, 0, ct)
+    o[0] = cadd(cscale(Ex, ct), cscale(Ez, st));
+    o[1] = Ey;
+    o[2] = cadd(cscale(Ex, -st), cscale(Ez, ct));
+    if (kind_out == 6) {
+        o[3] = cadd(cscale(Hx, ct), cscale(Hz, st));
+        o[4] = Hy;
+        o[5] = cadd(cscale(Hx, -st), cscale(Hz, ct));
+    }
+}
+
+gdm_status gdm_launch_gaussian(gdm_ctx *ctx, const double *r, int64_t m, double k, double n_env, double w0,
+                               const double *focus, double theta, const double *e0, int n_rhs, int kind_out,
+                               double *F0) {
+    double *de0;
+    GDM_TRY(gdm_upload(ctx, e0, sizeof(double) * 6 * n_rhs, (void **)&de0));
+    dim3 grid((unsigned)((m + 127) / 128), (unsigned)n_rhs);
+    k_gaussian<<<grid, 128, 0, ctx->stream>>>(r, m, k, n_env, w0, focus[0], focus[1], focus[2], cos(theta),
+                                              sin(theta), de0, n_rhs, kind_out, (double2 *)F0);
+    GDM_LAUNCHED(ctx, "gaussian");
+    return GDM_OK;
+}
+
 // Lorentzian ED/MD polarisabilities: one thread per dipole writes its 6x6 block (zeros off the diagonal)
 __global__ void k_alpha6_lorentz(int64_t n, const double *__restrict__ w0e, const double *__restrict__ w0m, double g,
                                  double a3, double w, double rad, double2 *__restrict__ out) {

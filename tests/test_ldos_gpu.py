@@ -52,3 +52,14 @@ def test_ldos_matches_oracle(G, ctx, magnetic, precision):
     got = G.ldos(ctx, prob, t(r0), magnetic=magnetic, precision=precision).cpu().numpy()
     want = O.ldos(pr, r0, magnetic=magnetic)
     np.testing.assert_allclose(got, want, rtol=1e-9)
+
+
+@pytest.mark.parametrize("theta,kind_out", [(0.0, 3), (0.35, 6)])
+def test_incident_gaussian_matches_oracle(G, ctx, theta, kind_out):
+    """Paraxial Gaussian beam (tight focus, oblique) against the oracle at 1e-13 of the largest entry."""
+    r = W.sphere_points(500, 400.0, seed=8) * np.random.default_rng(1).uniform(0, 1, (500, 1))
+    e0 = np.array([[1.0, 0.5j, 0.0], [0.2, 1.0, 0.0]])
+    lam, w0, focus = 610.0, 450.0, (20.0, -10.0, 35.0)
+    got = G.incident_gaussian(ctx, t(r), lam, e0, w0, focus=focus, theta=theta, kind_out=kind_out).cpu().numpy().T
+    want = O.gaussian_paraxial(r, 2 * np.pi / lam, 1.0, e0, w0, focus=focus, theta=theta, kind_out=kind_out)
+    np.testing.assert_allclose(got, want, atol=1e-13 * np.abs(want).max())
