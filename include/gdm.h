@@ -126,6 +126,13 @@ gdm_status gdm_set_stream(gdm_ctx *ctx, void *stream);
 /* Waits for the context's stream, then returns the first device-side error
  * recorded since the last check (GDM_OK if none) and clears it. */
 gdm_status gdm_ctx_check(gdm_ctx *ctx);
+
+/* Failure-detection check (no paper counterpart): launches one thread that waits for a device
+ * flag which nothing sets, giving up after limit_ms (<= 2000) like every bounded wait of the
+ * library's persistent kernels, records GDM_ERR_TIMEOUT in the context's device error record
+ * and returns what gdm_ctx_check reads back: GDM_ERR_TIMEOUT, with the context usable
+ * afterwards (the record is cleared by the read). Synchronous. */
+gdm_status gdm_diag_wait_timeout(gdm_ctx *ctx, double limit_ms);
 const char *gdm_status_string(gdm_status s);
 const char *gdm_last_error(gdm_ctx *ctx);
 /* Number of kernel launches this context has issued so far. */

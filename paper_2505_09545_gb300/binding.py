@@ -92,6 +92,7 @@ _SIGS = {
     "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, P], C.c_int),
     "gdm_solve_batched": ([P, C.c_int, P, C.c_int, P, C.c_int, P], C.c_int),
     "gdm_autotune": ([P, C.c_int, P, C.c_int, P], C.c_int),
+    "gdm_diag_wait_timeout": ([P, C.c_double], C.c_int),
     "gdm_incident_gaussian": ([P, P, I64, C.c_double, C.c_double, PD, C.c_double, PD, C.c_double, C.c_int, C.c_int,
                                P], C.c_int),
     "gdm_incident_dipole": ([P, P, I64, C.c_double, P, P, C.c_int, C.c_int, P], C.c_int),

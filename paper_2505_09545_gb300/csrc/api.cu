@@ -244,6 +244,35 @@ gdm_status gdm_set_stream(gdm_ctx *ctx, void *stream) {
     return GDM_OK;
 }
 
+}  // extern "C"
+
+// one thread waits (bounded by the global timer) for a device flag that nothing sets, then records a timeout
+static __global__ void k_wait_unset_flag(volatile int *never_set, long long limit_ns, int *flags) {
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        if (*never_set) return;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if ((long long)(t - t0) > limit_ns) {
+            gdm_dev_error(flags, GDM_ERR_TIMEOUT, 99);
+            return;
+        }
+        __nanosleep(1000);
+    }
+}
+
+extern "C" {
+
+gdm_status gdm_diag_wait_timeout(gdm_ctx *ctx, double limit_ms) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    if (!(limit_ms > 0) || limit_ms > 2000) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "limit must be in (0, 2000] ms");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    // a flag slot that no kernel of this call sets (zeroed at context creation, never written)
+    k_wait_unset_flag<<<1, 1, 0, ctx->stream>>>(ctx->dflags + GDM_FLAG_DIAG, (long long)(limit_ms * 1e6), ctx->dflags);
+    GDM_LAUNCHED(ctx, "wait_unset_flag");
+    return gdm_ctx_check(ctx);
+}
+
 gdm_status gdm_ctx_check(gdm_ctx *ctx) {
     if (!ctx) return GDM_ERR_INVALID_ARG;
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));

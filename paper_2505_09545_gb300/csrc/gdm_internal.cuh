@@ -112,6 +112,7 @@ struct ScratchCarver {
 #define GDM_FLAG_BAR_GEN 3
 #define GDM_FLAG_GROWTH 4
 #define GDM_FLAG_PANEL_TICKET 5  // finish counter of the panel kernels (returns to 0 after each launch)
+#define GDM_FLAG_DIAG 6          // never written: the wait of gdm_diag_wait_timeout
 #define GDM_NFLAGS 8
 
 __device__ __forceinline__ void gdm_dev_error(int *flags, int status, int detail) {

@@ -164,11 +164,15 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
                 if (rr > relr) relr = rr;
             }
             if (!finite) {
+                // collect (and clear) the device record too: a singular pivot found by the factorisation is
+                // the cause to report, and must not surface in the context's next call
+                gdm_status dev = gdm_ctx_check(ctx);
+                gdm_status st = dev != GDM_OK ? dev : GDM_ERR_NONFINITE;
                 if (info) {
                     info->iterations = it;
-                    info->status = GDM_ERR_NONFINITE;
+                    info->status = st;
                 }
-                return gdm_fail(ctx, GDM_ERR_NONFINITE, "non-finite values in the refined solution");
+                return gdm_fail(ctx, st, "non-finite values in the refined solution (%s)", gdm_status_string(st));
             }
             if (relc <= opts->tol) break;
         }
