@@ -491,6 +491,23 @@ def run_ldos(args):
     ctx.close()
 
 
+def max_over_ranks(value, ws, device):
+    """The job's time is the slowest rank's: all-reduce MAX over the process group (any backend; the
+    tensor lives on `device`). Single process: the value itself."""
+    if ws <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_unit_seconds(job_ms, ws, units_per_rank=1):
+    """Replicas: every rank solves its own units; whole-job seconds per unit = slowest rank's time / all
+    units of the job."""
+    return job_ms / 1e3 / (ws * units_per_rank)
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -628,11 +645,7 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(False)
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws, dev)
 
     # one extra (untimed) step with per-phase device-time accounting
     ctx.phases(True)
@@ -662,11 +675,7 @@ def main():
     for _ in range(k_e2e):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / k_e2e
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / k_e2e, ws, dev)
 
     # assembly kernel alone against HBM: (3N)^2 complex entries written once
     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -709,7 +718,7 @@ def main():
                 "bytes": asm_bytes, "peak_source": f"{peak_src} copy bandwidth",
                 "kernel": "assemble A = I - G alpha (one launch, every entry written once)"}
     units = ws * 1
-    value = ms / 1e3 / units
+    value = per_unit_seconds(ms, ws)
     it = infos[-1]
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",

@@ -1,0 +1,56 @@
+"""The N > 1 (replica) path of bench.py on CPU: two gloo ranks agree on the slowest rank's time, the
+whole-job per-unit value follows from it, and the reference arm does no work on ranks other than 0."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import bench
+    t = bench.max_over_ranks(10.0 + 5.0 * rank, ws, torch.device("cpu"))
+    out[rank] = (t, bench.per_unit_seconds(t, ws))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    ws = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        procs = [ctx.Process(target=_rank, args=(r, ws, port, out)) for r in range(ws)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+            assert p.exitcode == 0
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 15.0
+    assert res[0][1] == pytest.approx(15.0 / 1e3 / 2)
+
+
+def test_reference_arm_skips_other_ranks(monkeypatch, capsys):
+    import argparse
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    args = argparse.Namespace(gpus=2, steps=1, warmup=0, cuboid="40x30x10", precision="tf32")
+    assert bench.run_reference(args) is None
+    assert capsys.readouterr().out == ""
