@@ -58,19 +58,22 @@ def cubic_selfterm(eps_env, step):
     return -FOUR_PI / (3.0 * eps_env * step ** 3)
 
 
-def lorentz_alpha6(omega0_e, omega0_m, gamma_ev, amp_nm, wavelength, hc_ev_nm=1239.84198):
+def lorentz_alpha6(omega0_e, omega0_m, gamma_ev, amp_nm, wavelength, hc_ev_nm=1239.84198, eps_env=1.0):
     """Effective ED/MD point polarisabilities from Lorentzian lines (Sec. "Effective
-    polarizabilities ...": manual Lorentzian lineshapes), vacuum host.
+    polarizabilities ...": manual Lorentzian lineshapes) in a host of permittivity eps_env.
 
-    alpha0(w) = a^3 w0^2 / (w0^2 - w^2 - i gamma w); dressed with radiative reaction
-    alpha = 1 / (1/alpha0 - i (2/3) k^3) so that a lone scatterer obeys the optical
-    theorem. Returns (n, 6, 6) complex: diag(alpha_e I3, alpha_m I3)."""
+    alpha0(w) = a^3 w0^2 / (w0^2 - w^2 - i gamma w); dressed with the radiative reaction of the
+    host, Im G^Ep(0) = (2/3) k^3/eps_env for the electric and Im G^Hm(0) = (2/3) k^3 for the
+    magnetic line (k = n_env k0): alpha_e = 1/(1/alpha0 - i (2/3) k^3/eps_env), alpha_m =
+    1/(1/alpha0 - i (2/3) k^3), so that a lone lossless scatterer obeys the optical theorem.
+    Returns (n, 6, 6) complex: diag(alpha_e I3, alpha_m I3)."""
     w = hc_ev_nm / float(wavelength)
-    k = 2.0 * np.pi / float(wavelength)
+    k = np.sqrt(float(eps_env)) * 2.0 * np.pi / float(wavelength)
     out = np.zeros((len(omega0_e), 6, 6), np.complex128)
     for blk, w0 in ((0, np.asarray(omega0_e)), (3, np.asarray(omega0_m))):
         a0 = amp_nm ** 3 * w0 ** 2 / (w0 ** 2 - w ** 2 - 1j * gamma_ev * w)
-        a = 1.0 / (1.0 / a0 - 1j * (2.0 / 3.0) * k ** 3)
+        rr = (2.0 / 3.0) * k ** 3 / (float(eps_env) if blk == 0 else 1.0)
+        a = 1.0 / (1.0 / a0 - 1j * rr)
         for c in range(3):
             out[:, blk + c, blk + c] = a
     return out
@@ -111,12 +114,17 @@ def green_hp(R, k0, k):
     return c[..., None, None] * cross_matrix(R / r[..., None])
 
 
-def green6(R, k0, k):
-    """Full 6x6 dyad of Eq. (superprop_G) in vacuum: G^Em = -G^Hp, G^Hm = G^Ep (electric-magnetic duality)."""
-    gep = green_ep(R, k, 1.0)
+def green6(R, k0, k, eps_env=1.0):
+    """Full 6x6 dyad of Eq. (superprop_G) in a non-magnetic host of permittivity eps_env (k = n_env k0).
+
+    The fields of a magnetic dipole follow from those of an electric one by duality: its magnetic field
+    is the electric-dipole kernel without the 1/eps_env of G^Ep (the host is non-magnetic), G^Hm =
+    eps_env G^Ep, and its electric field is E = (i/(k0 eps_env)) curl H (Ampere, exp(-i w t)), which
+    gives G^Em = -G^Hp. In vacuum: G^Hm = G^Ep, G^Em = -G^Hp."""
+    gep = green_ep(R, k, eps_env)
     ghp = green_hp(R, k0, k)
     top = np.concatenate([gep, -ghp], -1)
-    bot = np.concatenate([ghp, gep], -1)
+    bot = np.concatenate([ghp, eps_env * gep], -1)
     return np.concatenate([top, bot], -2)
 
 
@@ -125,7 +133,7 @@ class Problem:
     """Physics of one (structure, wavelength): positions, polarisabilities, wavenumbers.
 
     kind 3: discretised cells, isotropic alpha_i = (eps_i - eps_env) d^3/(4 pi), self-term S.
-    kind 6: effective point dipoles with full 6x6 alpha_i (vacuum), zero self-term."""
+    kind 6: effective point dipoles with full 6x6 alpha_i, zero self-term."""
 
     def __init__(self, pos, wavelength, kind=3, eps=None, step=0.0, alpha6=None, eps_env=1.0):
         self.pos = np.ascontiguousarray(pos, np.float64)
@@ -140,8 +148,6 @@ class Problem:
             self.alpha = cell_polarizability(self.eps, self.eps_env, self.step)
             self.selfterm = cubic_selfterm(self.eps_env, self.step)
         elif self.kind == 6:
-            if self.eps_env != 1.0:
-                raise ValueError("kind-6 (ED/MD) problems are vacuum-only")
             self.alpha6 = np.asarray(alpha6, np.complex128).reshape(self.n, 6, 6)
         else:
             raise ValueError("kind must be 3 or 6")
@@ -161,7 +167,7 @@ class Problem:
             G = green_ep(Rs, self.k, self.eps_env)
             G[same] = self.selfterm * np.eye(3)
         else:
-            G = green6(Rs, self.k0, self.k)
+            G = green6(Rs, self.k0, self.k, self.eps_env)
             G[same] = 0.0
         return G
 
@@ -215,7 +221,7 @@ class Problem:
             E = np.einsum("ijab,jbr->iar", green_ep(R, self.k, self.eps_env), P)
             H = np.einsum("ijab,jbr->iar", green_hp(R, self.k0, self.k), P)
         else:
-            G6 = green6(R, self.k0, self.k)
+            G6 = green6(R, self.k0, self.k, self.eps_env)
             EH = np.einsum("ijab,jbr->iar", G6, P)
             E, H = EH[:, :3], EH[:, 3:]
         if with_incident:
@@ -229,9 +235,12 @@ class Problem:
 
         sigma_ext = 4 pi k / (eps_env |E0|^2) sum_i Im(E0_i^* . p_i + H0_i^* . m_i)
         sigma_abs (cells)   = 4 pi k / (eps_env |E0|^2) sum_i Im(E_i^* . p_i)
-        sigma_abs (ED/MD)   = 4 pi k / |E0|^2 sum_i [Im(E_i^*.p_i) - 2/3 k^3 |p_i|^2 + Im(H_i^*.m_i) - 2/3 k^3 |m_i|^2]
+        sigma_abs (ED/MD)   = 4 pi k / (eps_env |E0|^2) sum_i [Im(E_i^*.p_i) - 2/3 k^3/eps_env |p_i|^2
+                                                           + Im(H_i^*.m_i) - 2/3 k^3 |m_i|^2]
         sigma_sca = sigma_ext - sigma_abs.
-        (Standard coupled-dipole forms; the paper cites them, Sec. "Observables".)"""
+        (Standard coupled-dipole forms; the paper cites them, Sec. "Observables". The radiated powers of
+        the electric and magnetic dipoles in the host, c k0 k^3 |p|^2/(3 eps_env) and c k0 k^3 |m|^2/3,
+        give the two radiation terms; the incident intensity is c n_env |E0|^2/(8 pi).)"""
         e0 = np.atleast_2d(np.asarray(e0, np.complex128))
         e2 = np.sum(np.abs(e0) ** 2, axis=1)
         P = self.moments(F)
@@ -239,14 +248,17 @@ class Problem:
         ext = pref * np.sum(np.imag(np.conj(F0) * P), axis=0)
         ab = np.sum(np.imag(np.conj(F) * P), axis=0)
         if self.kind == 6:
-            ab = ab - (2.0 / 3.0) * self.k ** 3 * np.sum(np.abs(P) ** 2, axis=0)
+            Pi = P.reshape(self.n, 6, -1)
+            ab = ab - (2.0 / 3.0) * self.k ** 3 * (np.sum(np.abs(Pi[:, :3]) ** 2, axis=(0, 1)) / self.eps_env
+                                                   + np.sum(np.abs(Pi[:, 3:]) ** 2, axis=(0, 1)))
         ab = pref * ab
         return ext, ext - ab, ab
 
     def farfield_amplitude(self, F, dirs):
         """Far-field amplitude f(rhat) at unit directions dirs (q, 3) (Sec. "Observables", repropagation to
         infinity): the scattered field along rhat is f exp(ikr)/r, f = k^2/eps_env sum_j exp(-ik rhat.r_j)
-        [p_j - rhat (rhat.p_j) - rhat x m_j]. Returns (q, 3, n_rhs)."""
+        [p_j - rhat (rhat.p_j) - n_env rhat x m_j] (far zone of G^Ep and of G^Em = -G^Hp, k0 k = k^2/n_env).
+        Returns (q, 3, n_rhs)."""
         rh = np.asarray(dirs, np.float64)
         nr = F.shape[1]
         P = self.moments(F).reshape(self.n, self.kind, nr)
@@ -255,14 +267,15 @@ class Problem:
         f = p - rh[:, :, None] * np.einsum("qa,qar->qr", rh, p)[:, None, :]
         if self.kind == 6:
             mm = np.einsum("qj,jar->qar", phase, P[:, 3:])
-            f = f - np.cross(rh[:, :, None], mm, axisa=1, axisb=1, axisc=1)
+            f = f - np.sqrt(self.eps_env) * np.cross(rh[:, :, None], mm, axisa=1, axisb=1, axisc=1)
         return f * self.k ** 2 / self.eps_env
 
     def farfield_scattering(self, F, e0, n_theta=64, n_phi=128):
         """sigma_sca by integrating the far-field intensity over the unit sphere
         (Sec. "Observables", scattered intensity via repropagation). Gauss-Legendre in
         cos(theta) times uniform phi. Far field: f(rhat) = k^2/eps_env sum_j exp(-ik rhat.r_j)
-        [p_j - rhat (rhat.p_j) - rhat x m_j]."""
+        [p_j - rhat (rhat.p_j) - n_env rhat x m_j]; the scattered intensity c n_env |f|^2/(8 pi r^2) over
+        the incident c n_env |E0|^2/(8 pi)."""
         e0 = np.atleast_2d(np.asarray(e0, np.complex128))
         e2 = np.sum(np.abs(e0) ** 2, axis=1)
         x, w = np.polynomial.legendre.leggauss(n_theta)
@@ -279,7 +292,7 @@ class Problem:
         f = p - rh[:, :, None] * np.einsum("qa,qar->qr", rh, p)[:, None, :]
         if self.kind == 6:
             mm = np.einsum("qj,jar->qar", phase, P[:, 3:])
-            f = f - np.cross(rh[:, :, None], mm, axisa=1, axisb=1, axisc=1)
+            f = f - np.sqrt(self.eps_env) * np.cross(rh[:, :, None], mm, axisa=1, axisb=1, axisc=1)
         f = f * self.k ** 2 / self.eps_env
         return np.einsum("q,qr->r", wt, np.sum(np.abs(f) ** 2, axis=1)) / e2
 
@@ -453,21 +466,21 @@ def loss_and_grad_probe_sca(prob: Problem, e0, r_probe, khat=(0.0, 0.0, 1.0)):
 
 
 # ----------------------------------------------------------------------------- effective models (GPM)
-def dipole_source_fields(r_eval, r_src, moments, k0, k):
-    """Fields of local point-dipole sources in vacuum, used as illuminations for the effective-model
+def dipole_source_fields(r_eval, r_src, moments, k0, k, eps_env=1.0):
+    """Fields of local point-dipole sources in the host, used as illuminations for the effective-model
     extraction (Sec. "Effective polarizabilities ..."): [E; H](r) = G6(r - r_s) [p_s; m_s] with the 6x6
     dyad of Eq. (superprop_G). r_src (s, 3), moments (s, 6) complex. Returns (6 m, s): column q holds the
     (E, H) of source q at every point."""
     r_eval = np.asarray(r_eval, np.float64)
     R = r_eval[:, None, :] - np.asarray(r_src, np.float64)[None, :, :]
-    EH = np.einsum("iqab,qb->iaq", green6(R, k0, k), np.asarray(moments, np.complex128))
+    EH = np.einsum("iqab,qb->iaq", green6(R, k0, k, eps_env), np.asarray(moments, np.complex128))
     return EH.reshape(-1, len(r_src))
 
 
 def dipole_illumination(prob: Problem, r_eval, src_pos, src_mom, kind_out=3):
-    """Incident field of point-dipole sources (Sec. "Illuminations": electric and magnetic dipole sources;
-    vacuum): column q = fields of source q at r_eval, (kind_out m, n_src)."""
-    EH = dipole_source_fields(r_eval, src_pos, src_mom, prob.k0, prob.k)
+    """Incident field of point-dipole sources (Sec. "Illuminations": electric and magnetic dipole sources)
+    in the problem's host: column q = fields of source q at r_eval, (kind_out m, n_src)."""
+    EH = dipole_source_fields(r_eval, src_pos, src_mom, prob.k0, prob.k, prob.eps_env)
     m = len(r_eval)
     if kind_out == 6:
         return EH
@@ -475,11 +488,13 @@ def dipole_illumination(prob: Problem, r_eval, src_pos, src_mom, kind_out=3):
 
 
 def ldos(prob: Problem, r0, magnetic=False):
-    """Partial local density of states of the structured environment, normalised to vacuum (Sec.
+    """Partial local density of states of the structured environment, normalised to the bare host (Sec.
     "Observables": electric and magnetic LDOS): for a unit dipole u (x, y, z) at r0, the structure is solved
-    under its field and rho_u / rho_0 = 1 + 3/(2 k^3) Im(u . E_sca(r0)) (H_sca for a magnetic dipole), the
-    emitter's decay rate relative to free space. Vacuum host, cells. Returns (n_pos, 3)."""
-    assert prob.kind == 3 and prob.eps_env == 1.0
+    under its field and the emitter's decay rate relative to the homogeneous host is its total emitted power
+    over the host's, (w/2) Im(u . E_sca(r0)) over c k0 k^3/(3 eps_env):
+    rho_u / rho_0 = 1 + 3 eps_env/(2 k^3) Im(u . E_sca(r0)), and for a magnetic emitter (host power
+    c k0 k^3/3) rho_u / rho_0 = 1 + 3/(2 k^3) Im(u . H_sca(r0)). Cells. Returns (n_pos, 3)."""
+    assert prob.kind == 3
     r0 = np.asarray(r0, np.float64)
     out = np.zeros((len(r0), 3))
     for e, r in enumerate(r0):
@@ -491,7 +506,7 @@ def ldos(prob: Problem, r0, magnetic=False):
         E, H = prob.nearfield(F, r[None], None, with_incident=False)
         field = H if magnetic else E
         for u in range(3):
-            out[e, u] = 1.0 + 1.5 / prob.k ** 3 * field[0, u, u].imag
+            out[e, u] = 1.0 + 1.5 * (1.0 if magnetic else prob.eps_env) / prob.k ** 3 * field[0, u, u].imag
     return out
 
 
@@ -500,7 +515,7 @@ def gpm_illuminations(prob: Problem, r_eval, pw_khat, pw_e0, ds_pos, ds_mom):
     amplitudes e0), then local dipole sources. Returns (6 m, n_ill) incident (E, H) per point."""
     cols = [plane_wave(r_eval, prob.k, np.sqrt(prob.eps_env), e0, kh, 6) for kh, e0 in zip(pw_khat, pw_e0)]
     if len(ds_pos):
-        cols.append(dipole_source_fields(r_eval, ds_pos, ds_mom, prob.k0, prob.k))
+        cols.append(dipole_source_fields(r_eval, ds_pos, ds_mom, prob.k0, prob.k, prob.eps_env))
     return np.concatenate(cols, axis=1)
 
 
@@ -513,9 +528,9 @@ def gpm_extract(prob: Problem, r_gpm, r_probe, pw_khat, pw_e0, ds_pos, ds_mom):
          those fields best in the L2 sense (least squares through the 6x6 dyads);
       4. alpha_eff (6M x 6M) minimising || alpha_eff F0 - P || over the illuminations, F0 the incident
          (E, H) at the M positions and P the fitted moments: alpha_eff = P F0^+.
-    Vacuum host (the 6x6 dyads are the vacuum ones). LAPACK least squares (numpy lstsq) as the
+    The 6x6 dyads are those of the problem's host. LAPACK least squares (numpy lstsq) as the
     library step. Returns (alpha_eff, P, F0g, rel_fit) with rel_fit the relative residual of step 3."""
-    assert prob.kind == 3 and prob.eps_env == 1.0
+    assert prob.kind == 3
     n = prob.n
     F0c = gpm_illuminations(prob, prob.pos, pw_khat, pw_e0, ds_pos, ds_mom)
     nill = F0c.shape[1]
@@ -524,7 +539,7 @@ def gpm_extract(prob: Problem, r_gpm, r_probe, pw_khat, pw_e0, ds_pos, ds_mom):
     E, H = prob.nearfield(F, r_probe, None, with_incident=False)
     S = np.concatenate([E, H], axis=1).reshape(-1, nill)
     R = np.asarray(r_probe, np.float64)[:, None, :] - np.asarray(r_gpm, np.float64)[None, :, :]
-    G6 = green6(R, prob.k0, prob.k)                                   # (P, M, 6, 6)
+    G6 = green6(R, prob.k0, prob.k, prob.eps_env)                     # (P, M, 6, 6)
     Gp = G6.transpose(0, 2, 1, 3).reshape(6 * len(r_probe), 6 * len(r_gpm))
     P = np.linalg.lstsq(Gp, S, rcond=None)[0]
     rel_fit = np.linalg.norm(Gp @ P - S) / np.linalg.norm(S)

@@ -73,27 +73,33 @@ def test_single_cell_internal_field(eps, eps_env):
 
 
 # ---------------------------------------------------------------- P1: single dipole vs Mie
-@pytest.mark.parametrize("radius,eps", [(50.0, 12.25 + 0j), (80.0, 9.0 + 0j), (40.0, 4.0 + 0.3j)])
-def test_single_dipole_mie_crosssections(radius, eps):
+@pytest.mark.parametrize("radius,eps,eps_env", [(50.0, 12.25 + 0j, 1.0), (80.0, 9.0 + 0j, 1.0), (40.0, 4.0 + 0.3j, 1.0),
+                                              (60.0, 12.25 + 0j, 1.77), (45.0, 6.0 + 0.4j, 2.25)])
+def test_single_dipole_mie_crosssections(radius, eps, eps_env):
     """A lone ED/MD point dipole with the Mie polarisabilities of Sec. 'Effective
-    polarizabilities' reproduces Mie's dipole-order extinction (6 pi/k^2) Re(a1+b1)
-    and scattering (6 pi/k^2)(|a1|^2+|b1|^2)."""
+    polarizabilities' (alpha_pE = (3i/2) a1/(k0^3 n_env), alpha_mH = (3i/2) b1/(k0^3 n_env^3)) reproduces
+    Mie's dipole-order extinction (6 pi/k^2) Re(a1+b1) and scattering (6 pi/k^2)(|a1|^2+|b1|^2), k = n_env k0,
+    in vacuum and in a host medium: this fixes the host factors of the cross sections, of the far field and
+    of the magnetic blocks (1/eps_env on the electric radiation term, n_env on the magnetic far field)."""
     lam = 620.0
-    k = 2 * np.pi / lam
-    ae, am = O.mie_dipole_alpha(radius, eps, lam)
+    n_env = np.sqrt(eps_env)
+    k = 2 * np.pi * n_env / lam
+    ae, am = O.mie_dipole_alpha(radius, eps, lam, eps_env)
     al = np.zeros((1, 6, 6), complex)
     al[0, :3, :3] = ae * np.eye(3)
     al[0, 3:, 3:] = am * np.eye(3)
-    pr = O.Problem(np.zeros((1, 3)), lam, 6, alpha6=al)
+    pr = O.Problem(np.zeros((1, 3)), lam, 6, alpha6=al, eps_env=eps_env)
     F0 = pr.plane_wave(W.XYPOL)
     F = pr.solve(F0)
     np.testing.assert_allclose(F, F0, rtol=0, atol=0)          # zero self-term: F = F0
     ext, sca, ab = pr.cross_sections(F0, F, W.XYPOL)
-    a, b = O.mie_coefficients(np.sqrt(eps), k * radius)
+    a, b = O.mie_coefficients(np.sqrt(eps) / n_env, k * radius)
     np.testing.assert_allclose(ext, 6 * np.pi / k ** 2 * np.real(a[0] + b[0]), rtol=1e-12)
     np.testing.assert_allclose(sca, 6 * np.pi / k ** 2 * (abs(a[0]) ** 2 + abs(b[0]) ** 2), rtol=1e-10)
     ff = pr.farfield_scattering(F, W.XYPOL, n_theta=24, n_phi=48)
     np.testing.assert_allclose(ff, sca, rtol=1e-10)
+    if eps.imag == 0:
+        assert np.abs(ab).max() < 1e-12 * ext.max()
 
 
 def test_single_electric_dipole_optical_theorem():
@@ -196,6 +202,32 @@ def test_green_curl_relations(Rvec):
     np.testing.assert_allclose(-_curl(Hm, R, h) / (1j * k0), ref, rtol=0, atol=1e-7 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("Rvec", [(37.0, -12.0, 5.0), (400.0, 150.0, -900.0)])
+@pytest.mark.parametrize("eps_env", [1.0, 1.77, 2.25])
+def test_green6_maxwell_in_host(Rvec, eps_env):
+    """The full 6x6 dyad in a non-magnetic host: for any (p, m) the fields E = G^Ep p + G^Em m,
+    H = G^Hp p + G^Hm m obey Faraday curl E = i k0 H and Ampere curl H = -i k0 eps_env E (Gaussian units,
+    exp(-i w t)), and the magnetic-dipole field H has the static limit (3 u (u.m) - m)/R^3 with no host
+    factor."""
+    lam = 560.0
+    k0, k = O.wavenumbers(lam, eps_env)
+    p = np.array([0.3 - 0.2j, 1.0, -0.7 + 0.1j])
+    m = np.array([-0.5, 0.2 + 0.9j, 0.4])
+    pm = np.concatenate([p, m])
+    R = np.array(Rvec)
+    h = 1e-3 * np.linalg.norm(R)
+    E = lambda r: O.green6(r, k0, k, eps_env)[:3] @ pm
+    H = lambda r: O.green6(r, k0, k, eps_env)[3:] @ pm
+    e, hh = E(R), H(R)
+    np.testing.assert_allclose(_curl(E, R, h), 1j * k0 * hh, rtol=0, atol=1e-7 * np.abs(k0 * hh).max())
+    np.testing.assert_allclose(_curl(H, R, h), -1j * k0 * eps_env * e, rtol=0,
+                               atol=1e-7 * np.abs(k0 * eps_env * e).max())
+    r = np.array([1e-2, -2e-2, 3e-2])
+    u = r / np.linalg.norm(r)
+    stat = (3 * u * (u @ m) - m) / np.linalg.norm(r) ** 3
+    np.testing.assert_allclose(O.green6(r, k0, k, eps_env)[3:, 3:] @ m, stat, rtol=1e-6)
+
+
 def test_green_helmholtz_and_textbook_form():
     """(lap + k^2) G^Ep p = 0 away from the source; G^Ep p equals the vector-form dipole
     field written out on scalars; Im G^Ep(R -> 0) -> (2/3) k^3 I (radiation reaction)."""
@@ -240,19 +272,26 @@ def test_energy_identity_cells(lossy):
         assert np.max(np.abs(ab)) < 1e-12 * np.max(ext)
 
 
-def test_optical_theorem_edmd_lorentz():
-    """Radiatively dressed Lorentzian ED/MD dipoles (zero self-term): sigma_ext =
-    sigma_sca(far field) + sigma_abs to quadrature accuracy."""
+@pytest.mark.parametrize("eps_env", [1.0, 1.77])
+@pytest.mark.parametrize("gamma", [None, 0.0])
+def test_optical_theorem_edmd_lorentz(eps_env, gamma):
+    """Radiatively dressed Lorentzian ED/MD dipoles (zero self-term), coupled, in vacuum and in a host:
+    sigma_ext = sigma_sca(far field) + sigma_abs to quadrature accuracy; lossless lines (gamma = 0)
+    absorb nothing."""
     ms = W.metasurface_edmd(nx=3, ny=2, pitch=400.0, n_lambda=1)
     lam = 610.0
-    al = O.lorentz_alpha6(ms.omega0_e, ms.omega0_m, ms.gamma_ev, ms.amp_nm, lam)
-    pr = O.Problem(ms.pos, lam, 6, alpha6=al)
+    g = ms.gamma_ev if gamma is None else gamma
+    al = O.lorentz_alpha6(ms.omega0_e, ms.omega0_m, g, ms.amp_nm, lam, eps_env=eps_env)
+    pr = O.Problem(ms.pos, lam, 6, alpha6=al, eps_env=eps_env)
     F0 = pr.plane_wave(W.XYPOL)
     F = pr.solve(F0)
     ext, sca, ab = pr.cross_sections(F0, F, W.XYPOL)
     ff = pr.farfield_scattering(F, W.XYPOL, n_theta=96, n_phi=192)
     np.testing.assert_allclose(sca, ff, rtol=1e-8)
-    assert np.all(ab > 0)
+    if gamma is None:
+        assert np.all(ab > 0)
+    else:
+        assert np.abs(ab).max() < 1e-12 * ext.max()
 
 
 # ---------------------------------------------------------------- P7: Mie convergence of the discretised sphere
@@ -401,37 +440,40 @@ def test_workload_shapes():
 
 
 # ----------------------------------------------------------------------------- GPM extraction
-def _gpm_case(n_cells, seed, m=None):
+def _gpm_case(n_cells, seed, m=None, eps_env=1.0):
     s = W.random_cells(n_cells, seed=seed)
     lam = 560.0
-    pr = O.Problem(s.pos, lam, 3, eps=s.eps, step=s.step)
+    pr = O.Problem(s.pos, lam, 3, eps=s.eps, step=s.step, eps_env=eps_env)
     r_gpm = s.pos if m is None else W.farthest_points(s.pos, m, seed)
     khat, e0, ds_pos, ds_mom = W.gpm_illumination_set(n_angles=12, n_sources=10, source_radius=150.0, seed=seed)
     r_probe = W.sphere_points(60, 90.0, seed=seed + 7)
     return s, pr, r_gpm, r_probe, khat, e0, ds_pos, ds_mom
 
 
-def test_gpm_single_cell_is_the_dressed_cell_polarizability():
+@pytest.mark.parametrize("eps_env", [1.0, 1.77])
+def test_gpm_single_cell_is_the_dressed_cell_polarizability(eps_env):
     """One cell, one effective dipole at the cell: alpha_eff = alpha / (1 - S alpha) in the electric block
-    (the exact internal-field relation of a lone cell) and zero in the magnetic and cross blocks."""
-    s, pr, r_gpm, r_probe, khat, e0, ds_pos, ds_mom = _gpm_case(1, 5)
+    (the exact internal-field relation of a lone cell) and zero in the magnetic and cross blocks, in vacuum
+    and in a host (where the probe fields and the dipole sources propagate through the host's dyads)."""
+    s, pr, r_gpm, r_probe, khat, e0, ds_pos, ds_mom = _gpm_case(1, 5, eps_env=eps_env)
     a, P, F0g, rel = O.gpm_extract(pr, r_gpm, r_probe, khat, e0, ds_pos, ds_mom)
-    al = O.cell_polarizability(s.eps[0], 1.0, s.step)
-    S = O.cubic_selfterm(1.0, s.step)
+    al = O.cell_polarizability(s.eps[0], eps_env, s.step)
+    S = O.cubic_selfterm(eps_env, s.step)
     want = np.zeros((6, 6), complex)
     want[:3, :3] = al / (1.0 - S * al) * np.eye(3)
     assert rel < 1e-10
     np.testing.assert_allclose(a, want, atol=1e-9 * abs(want).max())
 
 
-def test_gpm_on_the_cells_is_alpha_times_inverse_matrix():
+@pytest.mark.parametrize("eps_env", [1.0, 2.25])
+def test_gpm_on_the_cells_is_alpha_times_inverse_matrix(eps_env):
     """Effective dipoles placed on the cells themselves: the moments are P = alpha A^{-1} F0 exactly, so the
     fitted non-local polarizability is alpha A^{-1} (electric-electric blocks) and zero elsewhere; this
     checks the illumination fields, the solve, the probe fields and both least-squares fits at once."""
-    s, pr, r_gpm, r_probe, khat, e0, ds_pos, ds_mom = _gpm_case(5, 8)
+    s, pr, r_gpm, r_probe, khat, e0, ds_pos, ds_mom = _gpm_case(5, 8, eps_env=eps_env)
     a, P, F0g, rel = O.gpm_extract(pr, r_gpm, r_probe, khat, e0, ds_pos, ds_mom)
     n = s.n
-    alpha = np.repeat(O.cell_polarizability(s.eps, 1.0, s.step), 3)
+    alpha = np.repeat(O.cell_polarizability(s.eps, eps_env, s.step), 3)
     ee = alpha[:, None] * np.linalg.inv(pr.matrix())           # alpha A^{-1}, (3n, 3n)
     want = np.zeros((6 * n, 6 * n), complex)
     for j in range(n):
@@ -498,6 +540,53 @@ def test_ldos_single_cell_closed_form(magnetic):
             field = O.green_ep(-R, k) @ (aeff * Einc)
         want.append(1.0 + 1.5 / k ** 3 * np.imag(e_u @ field))
     np.testing.assert_allclose(got, want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("magnetic", [False, True])
+@pytest.mark.parametrize("eps_env", [1.0, 1.77])
+def test_ldos_is_the_emitted_power(magnetic, eps_env):
+    """Lossless cells around an emitter, in vacuum and in a host: the LDOS is the power the emitter and its
+    induced dipoles radiate to infinity over the power the emitter alone radiates in the bare host. Both
+    powers come from far-field amplitudes written out here, f = (k^2/eps_env) [p_perp - n_env u x m] summed
+    with the phases exp(-i k u.r_j), integrated by Gauss-Legendre x uniform-phi quadrature. Cells carry no
+    radiation reaction (their self-term is real), so a lossless cell still takes up the power a dressed
+    dipole would radiate, c k0 k^3 |p_j|^2/(3 eps_env), which is (8 pi/3) |p_j|^2 in the units of the
+    quadrature below: the emitted power is the far-field power minus that sum. This fixes the host factors
+    (3 eps_env/(2 k^3) electric, 3/(2 k^3) magnetic) of the LDOS."""
+    s = W.random_cells(24, seed=12)
+    eps = np.real(s.eps) + 0j
+    lam = 590.0
+    pr = O.Problem(s.pos, lam, 3, eps=eps, step=s.step, eps_env=eps_env)
+    r0 = np.array([[5.0, -10.0, 60.0]])
+    got = O.ldos(pr, r0, magnetic=magnetic)[0]
+    k, n_env = pr.k, np.sqrt(eps_env)
+    x, w = np.polynomial.legendre.leggauss(40)
+    nphi = 80
+    ct = np.repeat(x, nphi)
+    wt = np.repeat(w, nphi) * (2 * np.pi / nphi)
+    ph = np.tile(np.arange(nphi) * 2 * np.pi / nphi, 40)
+    st = np.sqrt(1 - ct ** 2)
+    U = np.stack([st * np.cos(ph), st * np.sin(ph), ct], -1)
+    for u in range(3):
+        mom = np.zeros((1, 6), complex)
+        mom[0, u + (3 if magnetic else 0)] = 1.0
+        F0 = O.dipole_illumination(pr, pr.pos, r0, mom, 3)
+        P = pr.moments(pr.solve(F0)).reshape(pr.n, 3)
+        tot = np.zeros((len(U), 3), complex)
+        src = np.zeros((len(U), 3), complex)
+        for q, uq in enumerate(U):
+            for j in range(pr.n):
+                pj = P[j]
+                tot[q] += np.exp(-1j * k * uq @ pr.pos[j]) * (pj - uq * (uq @ pj))
+            e_src = np.exp(-1j * k * uq @ r0[0])
+            if magnetic:
+                src[q] = -n_env * e_src * np.cross(uq, np.eye(3)[u])
+            else:
+                src[q] = e_src * (np.eye(3)[u] - uq * uq[u])
+        tot = tot + src
+        p_rad = 8 * np.pi / 3 * np.sum(np.abs(P) ** 2)
+        ratio = (np.sum(wt * np.sum(np.abs(tot) ** 2, 1)) - p_rad) / np.sum(wt * np.sum(np.abs(src) ** 2, 1))
+        np.testing.assert_allclose(got[u], ratio, rtol=1e-9)
 
 
 def test_ldos_limits():
