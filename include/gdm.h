@@ -74,7 +74,9 @@ typedef struct gdm_ctx gdm_ctx;
  *   (eps_i - eps_env) d^3 / (4 pi) (Sec. "Volume discretization polarizabilities"),
  *   self-term S = -I 4 pi / (3 eps_env d^3) (Eq. selfterm_SEp_cubic).
  * kind 6: effective electric/magnetic point dipoles with full 6x6 polarisability
- *   alpha_i (dipole-moment relation (p, m) = alpha F), zero self-term; vacuum only. */
+ *   alpha_i (dipole-moment relation (p, m) = alpha F), zero self-term. In a host of
+ *   permittivity eps_env (non-magnetic) the 6x6 dyad is [[G^Ep, -G^Hp], [G^Hp, eps_env G^Ep]]
+ *   with k = n_env 2 pi / lambda0 (Gaussian units, exp(-i w t)). */
 typedef struct {
     int64_t n;              /* number of dipoles (cells or effective dipoles), >= 1 */
     int32_t kind;           /* 3 or 6 */
@@ -83,7 +85,7 @@ typedef struct {
     const double *eps;      /* kind 3: device, n complex128 cell permittivities; else NULL */
     const double *alpha6;   /* kind 6: device, n x 6 x 6 complex128, row-major per dipole; else NULL */
     double step;            /* kind 3: cubic mesh step d (nm), > 0; ignored for kind 6 */
-    double eps_env;         /* real host permittivity, > 0 (kind 6: must be 1) */
+    double eps_env;         /* real host permittivity, > 0 */
     double wavelength;      /* vacuum wavelength lambda0 (nm), > 0 */
 } gdm_problem;
 
@@ -146,14 +148,16 @@ gdm_status gdm_workspace_size(const gdm_problem *p, int n_rhs, gdm_precision pre
 /* ---------------------------------------------------------------- polarisabilities */
 
 /* Effective electric/magnetic dipole polarisabilities from Lorentzian lines (Sec.
- * "Effective polarizabilities", manually set lineshapes), vacuum host, for the kind 6
- * problem's alpha6: with w = hc/lambda (eV) and k = 2 pi / lambda,
- *   alpha0 = a^3 w0^2 / (w0^2 - w^2 - i gamma w),
- *   alpha  = 1 / (1/alpha0 - i (2/3) k^3)        (radiative reaction, optical theorem),
+ * "Effective polarizabilities", manually set lineshapes) in a host of permittivity eps_env, for
+ * the kind 6 problem's alpha6: with w = hc/lambda (eV) and k = n_env 2 pi / lambda,
+ *   alpha0   = a^3 w0^2 / (w0^2 - w^2 - i gamma w),
+ *   alpha_e  = 1 / (1/alpha0 - i (2/3) k^3 / eps_env),  alpha_m = 1 / (1/alpha0 - i (2/3) k^3)
+ * (radiative reaction of the host, so that a lone lossless dipole obeys the optical theorem),
  * alpha6_i = diag(alpha_e I3, alpha_m I3). omega0_e, omega0_m: device n resonance energies
  * (eV). alpha6_out: device n x 6 x 6 complex128 (row-major 6x6 per dipole), overwritten. */
 gdm_status gdm_alpha6_lorentz(gdm_ctx *ctx, int64_t n, const double *omega0_e, const double *omega0_m,
-                              double gamma_ev, double amp_nm, double wavelength, double *alpha6_out);
+                              double gamma_ev, double amp_nm, double wavelength, double eps_env,
+                              double *alpha6_out);
 
 /* ---------------------------------------------------------------- illumination */
 
@@ -177,10 +181,11 @@ gdm_status gdm_incident_gaussian(gdm_ctx *ctx, const double *r, int64_t m, doubl
                                  int kind_out, double *F0);
 
 /* Incident field of point-dipole sources (Sec. "Illuminations": electric and magnetic dipole
- * sources), vacuum: column q is [E; H](r) = G6(r - r_q) [p_q; m_q] at the m points r_eval.
+ * sources) in a host of permittivity eps_env: column q is [E; H](r) = G6(r - r_q) [p_q; m_q] at
+ * the m points r_eval, G6 the host's 6x6 dyad (see gdm_problem).
  * src_pos: device n_src x 3; src_mom: device n_src x 6 complex128 (p, m); 1 <= n_src <= 1024.
  * kind_out 3 writes E only, 6 writes (E, H) per point. F0: device (kind_out*m) x n_src complex128. */
-gdm_status gdm_incident_dipole(gdm_ctx *ctx, const double *r_eval, int64_t m, double wavelength,
+gdm_status gdm_incident_dipole(gdm_ctx *ctx, const double *r_eval, int64_t m, double wavelength, double eps_env,
                                const double *src_pos, const double *src_mom, int n_src, int kind_out, double *F0);
 
 /* ---------------------------------------------------------------- hot path */
@@ -265,7 +270,7 @@ gdm_status gdm_backward_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_back
 /* ---------------------------------------------------------------- effective models */
 
 /* Global polarizability matrix (GPM) of a discretised structure (Sec. "Effective
- * polarizabilities", GPM extraction; vacuum host, kind 3): the structure is assembled into A
+ * polarizabilities", GPM extraction; kind 3, in the problem's host): the structure is assembled into A
  * (as gdm_assemble), factored once and solved (FP64-refined) for n_pw plane waves and n_ds
  * local dipole sources; its scattered (E, H) at the n_probe probe positions are fitted in the
  * least-squares sense by electric and magnetic dipoles at the n_sites positions r_gpm (one
@@ -316,8 +321,8 @@ gdm_status gdm_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, co
 /* Cross sections (nm^2) per illumination, FP64:
  *   ext = 4 pi k / (eps_env |E0|^2) sum_i Im(E0_i^* . p_i + H0_i^* . m_i)
  *   abs = 4 pi k / (eps_env |E0|^2) sum_i Im(E_i^* . p_i)                      (kind 3)
- *   abs = 4 pi k / |E0|^2 sum_i [Im(E_i^*.p_i) - 2/3 k^3 |p_i|^2
- *                                + Im(H_i^*.m_i) - 2/3 k^3 |m_i|^2]            (kind 6)
+ *   abs = 4 pi k / (eps_env |E0|^2) sum_i [Im(E_i^*.p_i) - 2/3 k^3/eps_env |p_i|^2
+ *                                          + Im(H_i^*.m_i) - 2/3 k^3 |m_i|^2]  (kind 6)
  *   sca = ext - abs.
  * F0, F: device (kind*n) x n_rhs complex128. e0_norm2: host n_rhs values |E0|^2.
  * ext, sca, abs: device n_rhs doubles each (any may be NULL). */
@@ -326,7 +331,7 @@ gdm_status gdm_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const double *
 
 /* Far-field scattering amplitudes (Sec. "Observables", scattering by repropagation of the dipoles
  * to infinity): the scattered field along rhat is f(rhat) exp(ikr)/r with
- *   f(rhat) = k^2/eps_env sum_j exp(-i k rhat.r_j) [p_j - rhat (rhat.p_j) - rhat x m_j].
+ *   f(rhat) = k^2/eps_env sum_j exp(-i k rhat.r_j) [p_j - rhat (rhat.p_j) - n_env rhat x m_j].
  * F: device (kind*n) x n_rhs solved fields. dirs: device q x 3 unit vectors. f_out: device
  * (3q) x n_rhs complex128. FP64. */
 gdm_status gdm_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int n_rhs, const double *dirs,
@@ -340,11 +345,12 @@ gdm_status gdm_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int
 gdm_status gdm_sigma_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, int n_rhs, const double *e0_norm2,
                               int n_theta, int n_phi, double *sigma);
 
-/* Partial local density of states of the structured environment, normalised to vacuum (Sec.
- * "Observables": electric and magnetic LDOS; the decay-rate enhancement of a dipole emitter):
- * for unit dipoles along x, y, z at each of the n_pos positions r0, the structure (kind 3,
- * vacuum) is solved under the emitter's field (one factorisation for all, FP64-refined) and
- * rho_u / rho_0 = 1 + 3/(2 k^3) Im(u . E_sca(r0)) (H_sca when magnetic != 0).
+/* Partial local density of states of the structured environment, normalised to the bare host
+ * (Sec. "Observables": electric and magnetic LDOS; the decay-rate enhancement of a dipole
+ * emitter): for unit dipoles along x, y, z at each of the n_pos positions r0, the structure
+ * (kind 3) is solved under the emitter's field (one factorisation for all, FP64-refined) and
+ * rho_u / rho_0 = 1 + 3 eps_env/(2 k^3) Im(u . E_sca(r0)), or 1 + 3/(2 k^3) Im(u . H_sca(r0))
+ * when magnetic != 0 (emitted power over the host's c k0 k^3/(3 eps_env), resp. c k0 k^3/3).
  * A, lda, ipiv: storage as for gdm_solve (assembled and factored here). r0: device n_pos x 3
  * (1 <= n_pos <= 340, not on a cell). ldos: device n_pos x 3 doubles. Synchronous. */
 gdm_status gdm_ldos(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, void *A, int64_t lda, int32_t *ipiv,

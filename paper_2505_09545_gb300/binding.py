@@ -89,13 +89,13 @@ _SIGS = {
     "gdm_nearfield": ([P, C.POINTER(Problem), P, P, I64, P, C.c_int, P, P], C.c_int),
     "gdm_residual": ([P, C.POINTER(Problem), P, P, C.c_int, P, P], C.c_int),
     "gdm_cross_sections": ([P, C.POINTER(Problem), P, P, C.c_int, PD, P, P, P], C.c_int),
-    "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, P], C.c_int),
+    "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, C.c_double, P], C.c_int),
     "gdm_solve_batched": ([P, C.c_int, P, C.c_int, P, C.c_int, P], C.c_int),
     "gdm_autotune": ([P, C.c_int, P, C.c_int, P], C.c_int),
     "gdm_diag_wait_timeout": ([P, C.c_double], C.c_int),
     "gdm_incident_gaussian": ([P, P, I64, C.c_double, C.c_double, PD, C.c_double, PD, C.c_double, C.c_int, C.c_int,
                                P], C.c_int),
-    "gdm_incident_dipole": ([P, P, I64, C.c_double, P, P, C.c_int, C.c_int, P], C.c_int),
+    "gdm_incident_dipole": ([P, P, I64, C.c_double, C.c_double, P, P, C.c_int, C.c_int, P], C.c_int),
     "gdm_ldos": ([P, C.c_int, C.POINTER(Problem), P, I64, P, P, C.c_int, C.c_int, P], C.c_int),
     "gdm_farfield": ([P, C.POINTER(Problem), P, C.c_int, P, I64, P], C.c_int),
     "gdm_sigma_farfield": ([P, C.POINTER(Problem), P, C.c_int, PD, C.c_int, C.c_int, P], C.c_int),
@@ -234,8 +234,9 @@ def padded_lda(n_sys):
     return (n_sys + 31) // 32 * 32
 
 
-def alpha6_lorentz(ctx: Context, omega0_e, omega0_m, gamma_ev, amp_nm, wavelength, out=None):
-    """Lorentzian ED/MD polarisabilities on the GPU: (n, 6, 6) complex128 device tensor."""
+def alpha6_lorentz(ctx: Context, omega0_e, omega0_m, gamma_ev, amp_nm, wavelength, out=None, eps_env=1.0):
+    """Lorentzian ED/MD polarisabilities on the GPU, dressed for a host of permittivity eps_env:
+    (n, 6, 6) complex128 device tensor."""
     w0e = omega0_e.contiguous()
     w0m = omega0_m.contiguous()
     n = w0e.shape[0]
@@ -243,7 +244,7 @@ def alpha6_lorentz(ctx: Context, omega0_e, omega0_m, gamma_ev, amp_nm, wavelengt
         out = torch.empty((n, 6, 6), dtype=torch.complex128, device=w0e.device)
     ctx._sync_stream()
     ctx._check(lib().gdm_alpha6_lorentz(ctx.h, n, _ptr(w0e), _ptr(w0m), float(gamma_ev), float(amp_nm),
-                                        float(wavelength), _ptr(out)), "gdm_alpha6_lorentz")
+                                        float(wavelength), float(eps_env), _ptr(out)), "gdm_alpha6_lorentz")
     return out
 
 
@@ -513,14 +514,14 @@ def incident_gaussian(ctx: Context, r, wavelength, e0, w0, focus=(0.0, 0.0, 0.0)
     return out
 
 
-def incident_dipole(ctx: Context, r, wavelength, src_pos, src_mom, kind_out=3):
-    """Fields of point dipoles (device (s, 3) positions, (s, 6) complex moments) at r ((m, 3) device):
-    (s, kind_out*m) complex128, one row per source."""
+def incident_dipole(ctx: Context, r, wavelength, src_pos, src_mom, kind_out=3, eps_env=1.0):
+    """Fields of point dipoles (device (s, 3) positions, (s, 6) complex moments) at r ((m, 3) device), in a
+    host of permittivity eps_env: (s, kind_out*m) complex128, one row per source."""
     n_src = src_pos.shape[0]
     out = torch.empty((n_src, kind_out * r.shape[0]), dtype=torch.complex128, device=r.device)
     ctx._sync_stream()
     ctx._check(lib().gdm_incident_dipole(ctx.h, _ptr(r.contiguous()), r.shape[0], float(wavelength),
-                                         _ptr(src_pos.contiguous()), _ptr(src_mom.contiguous()), n_src, kind_out,
+                                         float(eps_env), _ptr(src_pos.contiguous()), _ptr(src_mom.contiguous()), n_src, kind_out,
                                          _ptr(out)), "gdm_incident_dipole")
     return out
 

@@ -305,7 +305,6 @@ static gdm_status check_problem(gdm_ctx *ctx, const gdm_problem *p) {
             return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "kind 3 needs a finite mesh step > 0");
     } else {
         if (!p->alpha6) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "kind 6 needs alpha6");
-        if (p->eps_env != 1.0) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "kind 6 is implemented for vacuum only");
     }
     if (p->n * p->kind > (int64_t)1 << 30) return gdm_fail(ctx, GDM_ERR_SHAPE, "system too large");
     return GDM_OK;
@@ -340,14 +339,16 @@ gdm_status gdm_workspace_size(const gdm_problem *p, int n_rhs, gdm_precision pre
 }
 
 gdm_status gdm_alpha6_lorentz(gdm_ctx *ctx, int64_t n, const double *omega0_e, const double *omega0_m,
-                              double gamma_ev, double amp_nm, double wavelength, double *alpha6_out) {
+                              double gamma_ev, double amp_nm, double wavelength, double eps_env,
+                              double *alpha6_out) {
     if (!ctx) return GDM_ERR_INVALID_ARG;
     if (!omega0_e || !omega0_m || !alpha6_out) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
     if (n < 1) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n must be >= 1");
-    if (!(wavelength > 0) || !isfinite(wavelength) || !(amp_nm > 0) || !(gamma_ev >= 0))
-        return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "need wavelength > 0, amp_nm > 0, gamma_ev >= 0");
+    if (!(wavelength > 0) || !isfinite(wavelength) || !(amp_nm > 0) || !(gamma_ev >= 0) || !(eps_env > 0) ||
+        !isfinite(eps_env))
+        return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "need wavelength > 0, amp_nm > 0, gamma_ev >= 0, eps_env > 0");
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    return gdm_launch_alpha6_lorentz(ctx, n, omega0_e, omega0_m, gamma_ev, amp_nm, wavelength, alpha6_out);
+    return gdm_launch_alpha6_lorentz(ctx, n, omega0_e, omega0_m, gamma_ev, amp_nm, wavelength, eps_env, alpha6_out);
 }
 
 gdm_status gdm_incident_planewave(gdm_ctx *ctx, const double *r, int64_t m, double wavelength, double eps_env,

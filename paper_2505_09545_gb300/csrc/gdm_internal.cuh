@@ -197,7 +197,7 @@ gdm_status gdm_launch_gaussian(gdm_ctx *ctx, const double *r, int64_t m, double 
                                const double *focus, double theta, const double *e0, int n_rhs, int kind_out,
                                double *F0);
 gdm_status gdm_launch_alpha6_lorentz(gdm_ctx *ctx, int64_t n, const double *w0e, const double *w0m, double gamma_ev,
-                                     double amp_nm, double wavelength, double *out);
+                                     double amp_nm, double wavelength, double eps_env, double *out);
 gdm_status gdm_launch_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,
                                              int n_rhs, const double *e0_norm2, double *ext, double *sca,
                                              double *abs);

@@ -9,7 +9,8 @@
 //   5. alpha_eff = P F0^+ in the least-squares sense over the illuminations.
 // The least-squares steps use FP64 semi-normal equations (Gram matrix, Cholesky) with one refinement
 // step on the residual, which brings the solution to the accuracy of a QR solve for these well-scaled,
-// modestly conditioned problems. Vacuum host (the ED/MD dyads are the vacuum ones).
+// modestly conditioned problems. Homogeneous host of permittivity eps_env: plane waves, dipole sources and
+// the site-to-probe dyads all propagate through the host.
 #include <math.h>
 
 #include "gdm_internal.cuh"
@@ -254,26 +255,28 @@ __global__ void k_ldos_extract(const double2 *__restrict__ field, int n_pos, dou
 
 // E (and H) at m points of n_src point dipoles (device positions n_src x 3, moments n_src x 6), column q
 // = source q; id6 (36 n_src) and onehot (6 n_src x n_src) are scratch
-gdm_status dipole_fields(gdm_ctx *ctx, double wavelength, const double *src_pos, const double2 *mom, int n_src,
-                         const double *r_eval, int64_t m, double2 *E, double2 *H, double2 *id6, double2 *onehot) {
+gdm_status dipole_fields(gdm_ctx *ctx, double wavelength, double eps_env, const double *src_pos, const double2 *mom,
+                         int n_src, const double *r_eval, int64_t m, double2 *E, double2 *H, double2 *id6,
+                         double2 *onehot) {
     k_identity6<<<nblk(36 * (int64_t)n_src), 256, 0, ctx->stream>>>(id6, n_src);
     GDM_LAUNCHED(ctx, "identity6");
     k_onehot<<<nblk(6 * (int64_t)n_src * n_src), 256, 0, ctx->stream>>>(mom, n_src, onehot);
     GDM_LAUNCHED(ctx, "onehot");
-    gdm_problem src = {n_src, 6, 0, src_pos, nullptr, (const double *)id6, 0.0, 1.0, wavelength};
+    gdm_problem src = {n_src, 6, 0, src_pos, nullptr, (const double *)id6, 0.0, eps_env, wavelength};
     return gdm_launch_nearfield(ctx, &src, (const double *)onehot, r_eval, m, nullptr, n_src, (double *)E, (double *)H);
 }
 
 }  // namespace
 
 extern "C" gdm_status gdm_incident_dipole(gdm_ctx *ctx, const double *r_eval, int64_t m, double wavelength,
-                                          const double *src_pos, const double *src_mom, int n_src, int kind_out,
-                                          double *F0) {
+                                          double eps_env, const double *src_pos, const double *src_mom, int n_src,
+                                          int kind_out, double *F0) {
     if (!ctx) return GDM_ERR_INVALID_ARG;
     if (!r_eval || !src_pos || !src_mom || !F0) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
     if (m < 1 || n_src < 1 || n_src > 1024) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "need m >= 1, 1 <= n_src <= 1024");
     if (kind_out != 3 && kind_out != 6) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "kind_out must be 3 or 6");
-    if (!(wavelength > 0) || !isfinite(wavelength)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "bad wavelength");
+    if (!(wavelength > 0) || !isfinite(wavelength) || !(eps_env > 0) || !isfinite(eps_env))
+        return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "bad wavelength or eps_env");
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     gdm_params_reset(ctx);
     double2 *buf = nullptr;
@@ -282,10 +285,11 @@ extern "C" gdm_status gdm_incident_dipole(gdm_ctx *ctx, const double *r_eval, in
     double2 *id6 = buf, *onehot = buf + 36 * n_src, *E = onehot + (size_t)6 * n_src * n_src, *H = E + 3 * m * n_src;
     gdm_status st;
     if (kind_out == 3) {
-        st = dipole_fields(ctx, wavelength, src_pos, (const double2 *)src_mom, n_src, r_eval, m, (double2 *)F0, nullptr,
-                           id6, onehot);
+        st = dipole_fields(ctx, wavelength, eps_env, src_pos, (const double2 *)src_mom, n_src, r_eval, m,
+                           (double2 *)F0, nullptr, id6, onehot);
     } else {
-        st = dipole_fields(ctx, wavelength, src_pos, (const double2 *)src_mom, n_src, r_eval, m, E, H, id6, onehot);
+        st = dipole_fields(ctx, wavelength, eps_env, src_pos, (const double2 *)src_mom, n_src, r_eval, m, E, H, id6,
+                           onehot);
         if (st == GDM_OK) {
             k_interleave<<<nblk(6 * m * (int64_t)n_src), 256, 0, ctx->stream>>>(E, H, m, n_src, (double2 *)F0, 6 * m);
             st = gdm_after_launch(ctx, "interleave");
@@ -299,8 +303,7 @@ extern "C" gdm_status gdm_ldos(gdm_ctx *ctx, gdm_precision prec, const gdm_probl
                                int32_t *ipiv, const double *r0, int n_pos, int magnetic, double *ldos) {
     if (!ctx) return GDM_ERR_INVALID_ARG;
     GDM_TRY(gdm_check_solve_args(ctx, p, prec, A, lda, ipiv, r0, r0, 1));
-    if (p->kind != 3 || p->eps_env != 1.0)
-        return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "LDOS: discretised structures (kind 3) in vacuum");
+    if (p->kind != 3) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "LDOS: discretised structures (kind 3)");
     if (!ldos) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
     if (n_pos < 1 || n_pos > 340) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "n_pos must be in [1, 340]");
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
@@ -322,7 +325,7 @@ extern "C" gdm_status gdm_ldos(gdm_ctx *ctx, gdm_precision prec, const gdm_probl
     auto run = [&]() -> gdm_status {
         k_ldos_sources<<<nblk(ns), 256, 0, ctx->stream>>>(r0, n_pos, magnetic, pos3, mom);
         GDM_LAUNCHED(ctx, "ldos_sources");
-        GDM_TRY(dipole_fields(ctx, p->wavelength, pos3, mom, ns, p->pos, n, F0, nullptr, id6, onehot));
+        GDM_TRY(dipole_fields(ctx, p->wavelength, p->eps_env, pos3, mom, ns, p->pos, n, F0, nullptr, id6, onehot));
         GDM_TRY(gdm_launch_assemble(ctx, p, prec, A, lda));
         for (int q0 = 0; q0 < ns; q0 += 64) {
             const int nr = ns - q0 < 64 ? ns - q0 : 64;
@@ -331,8 +334,10 @@ extern "C" gdm_status gdm_ldos(gdm_ctx *ctx, gdm_precision prec, const gdm_probl
                                    (double *)(F + (int64_t)q0 * 3 * n), nr, &o, nullptr));
         }
         GDM_TRY(gdm_launch_nearfield(ctx, p, (const double *)F, r0, n_pos, nullptr, ns, (double *)Es, (double *)Hs));
-        const double k = 2.0 * 3.14159265358979323846 / p->wavelength;
-        k_ldos_extract<<<nblk(ns), 256, 0, ctx->stream>>>(magnetic ? Hs : Es, n_pos, 1.5 / (k * k * k), ldos);
+        // emitted power over that of the bare host: c k0 k^3/(3 eps_env) (electric), c k0 k^3/3 (magnetic)
+        const double k = sqrt(p->eps_env) * 2.0 * 3.14159265358979323846 / p->wavelength;
+        const double c = 1.5 * (magnetic ? 1.0 : p->eps_env) / (k * k * k);
+        k_ldos_extract<<<nblk(ns), 256, 0, ctx->stream>>>(magnetic ? Hs : Es, n_pos, c, ldos);
         GDM_LAUNCHED(ctx, "ldos_extract");
         return GDM_OK;
     };
@@ -348,8 +353,7 @@ extern "C" gdm_status gdm_gpm_extract(gdm_ctx *ctx, gdm_precision prec, const gd
                                       double *rel_fit) {
     if (!ctx) return GDM_ERR_INVALID_ARG;
     GDM_TRY(gdm_check_solve_args(ctx, p, prec, A, lda, ipiv, r_gpm, r_gpm, 1));
-    if (p->kind != 3 || p->eps_env != 1.0)
-        return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "GPM extraction: discretised structures (kind 3) in vacuum");
+    if (p->kind != 3) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "GPM extraction: discretised structures (kind 3)");
     const int n_ill = n_pw + n_ds;
     if (!r_gpm || !r_probe || !alpha_eff || (n_pw && (!pw_khat || !pw_e0)) || (n_ds && (!ds_pos || !ds_mom)))
         return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
@@ -369,7 +373,7 @@ extern "C" gdm_status gdm_gpm_extract(gdm_ctx *ctx, gdm_precision prec, const gd
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     gdm_params_reset(ctx);
     const int64_t n = p->n, M = n_sites, P = n_probe, M6 = 6 * M;
-    const double k = 2.0 * 3.14159265358979323846 / p->wavelength;
+    const double n_env = sqrt(p->eps_env), k = n_env * 2.0 * 3.14159265358979323846 / p->wavelength;
     // device buffers of the extraction (separate from the context arena, which the solves reuse); the
     // carving runs once on a null base to size the allocation
     const size_t c16 = sizeof(double2);
@@ -415,16 +419,16 @@ extern "C" gdm_status gdm_gpm_extract(gdm_ctx *ctx, gdm_precision prec, const gd
             // the amplitudes go through the context's parameter buffer; its copies are ordered on the stream
             // after the launches that read the previous contents, so it can restart for every wave
             gdm_params_reset(ctx);
-            GDM_TRY(gdm_launch_planewave(ctx, p->pos, n, k, 1.0, pw_e0 + 6 * q, pw_khat + 3 * q, 1, 3,
+            GDM_TRY(gdm_launch_planewave(ctx, p->pos, n, k, n_env, pw_e0 + 6 * q, pw_khat + 3 * q, 1, 3,
                                          (double *)(F0c + (int64_t)q * 3 * n)));
-            GDM_TRY(gdm_launch_planewave(ctx, r_gpm, M, k, 1.0, pw_e0 + 6 * q, pw_khat + 3 * q, 1, 6,
+            GDM_TRY(gdm_launch_planewave(ctx, r_gpm, M, k, n_env, pw_e0 + 6 * q, pw_khat + 3 * q, 1, 6,
                                          (double *)(F0g + (int64_t)q * M6)));
         }
-        //    and local dipole sources (a vacuum ED/MD "structure" with alpha = I and one-hot moments)
+        //    and local dipole sources (an ED/MD "structure" in the host with alpha = I and one-hot moments)
         if (n_ds > 0) {
             k_onehot<<<nblk(6 * (int64_t)n_ds * n_ds), 256, 0, ctx->stream>>>((const double2 *)ds_mom, n_ds, onehot);
             GDM_LAUNCHED(ctx, "onehot");
-            gdm_problem src = {n_ds, 6, 0, ds_pos, nullptr, (const double *)id6, 0.0, 1.0, p->wavelength};
+            gdm_problem src = {n_ds, 6, 0, ds_pos, nullptr, (const double *)id6, 0.0, p->eps_env, p->wavelength};
             GDM_TRY(gdm_launch_nearfield(ctx, &src, (const double *)onehot, p->pos, n, nullptr, n_ds,
                                          (double *)(F0c + (int64_t)n_pw * 3 * n), nullptr));
             GDM_TRY(gdm_launch_nearfield(ctx, &src, (const double *)onehot, r_gpm, M, nullptr, n_ds, (double *)Es,
@@ -449,7 +453,7 @@ extern "C" gdm_status gdm_gpm_extract(gdm_ctx *ctx, gdm_precision prec, const gd
         //    propagation from unit moments at the sites to the probes, stacked the same way
         k_eye<<<nblk(M6 * M6), 256, 0, ctx->stream>>>(M6, unit);
         GDM_LAUNCHED(ctx, "eye");
-        gdm_problem sites = {M, 6, 0, r_gpm, nullptr, (const double *)id6, 0.0, 1.0, p->wavelength};
+        gdm_problem sites = {M, 6, 0, r_gpm, nullptr, (const double *)id6, 0.0, p->eps_env, p->wavelength};
         GDM_TRY(gdm_launch_nearfield(ctx, &sites, (const double *)unit, r_probe, P, nullptr, (int)M6, (double *)Et,
                                      (double *)Ht));
         k_stack<<<nblk(6 * P * M6), 256, 0, ctx->stream>>>(Et, Ht, P, M6, Gp);

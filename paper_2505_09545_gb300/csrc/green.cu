@@ -7,7 +7,10 @@
 // Physics (Gaussian units, exp(-i w t)), following the paper's Eq. (superprop_G) blocks:
 //   G^Ep(R) = e^{ikR}/eps_env [ (k^2/R + ik/R^2 - 1/R^3) I + (-k^2/R - 3ik/R^2 + 3/R^3) u u^T ]
 //   G^Hp(R) = k0 k e^{ikR} (1/R + i/(k R^2)) [u]_x          ([u]_x v = u x v)
-//   vacuum ED/MD dyad: G^Em = -G^Hp, G^Hm = G^Ep.
+//   ED/MD dyad in a non-magnetic host: G^Em = -G^Hp, G^Hm = eps_env G^Ep (vacuum: G^Hm = G^Ep).
+// ED/MD sums run the dyad in its vacuum form at the host wavenumber k (kernel T = eps_env G^Ep,
+// cross term C = e^{ikR}(k^2/R + ik/R^2) [u]_x = n_env G^Hp) on the moments (p, n_env m) and scale the
+// rows afterwards: E = (T p - C n_env m)/eps_env, H = (C p + T n_env m)/n_env.
 // Cells (kind 3): alpha = (eps - eps_env) d^3/(4 pi), self-term S = -4 pi/(3 eps_env d^3) I
 // (Sec. "Volume discretization polarizabilities", Eq. selfterm_SEp_cubic).
 #include <math.h>
@@ -164,7 +167,7 @@ gdm_status gdm_launch_gaussian(gdm_ctx *ctx, const double *r, int64_t m, double 
 
 // Lorentzian ED/MD polarisabilities: one thread per dipole writes its 6x6 block (zeros off the diagonal)
 __global__ void k_alpha6_lorentz(int64_t n, const double *__restrict__ w0e, const double *__restrict__ w0m, double g,
-                                 double a3, double w, double rad, double2 *__restrict__ out) {
+                                 double a3, double w, double rad_e, double rad_m, double2 *__restrict__ out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double2 a[2];
@@ -172,7 +175,7 @@ __global__ void k_alpha6_lorentz(int64_t n, const double *__restrict__ w0e, cons
         const double w0 = h ? w0m[i] : w0e[i];
         // 1/alpha0 = (w0^2 - w^2 - i g w) / (a^3 w0^2); minus i rad; then invert
         const double s = 1.0 / (a3 * w0 * w0);
-        const double re = (w0 * w0 - w * w) * s, im = -g * w * s - rad;
+        const double re = (w0 * w0 - w * w) * s, im = -g * w * s - (h ? rad_m : rad_e);
         const double d = re * re + im * im;
         a[h] = make_double2(re / d, -im / d);
     }
@@ -183,12 +186,14 @@ __global__ void k_alpha6_lorentz(int64_t n, const double *__restrict__ w0e, cons
     }
 }
 
+// radiative dressing in the host: Im G^Ep(0) = (2/3) k^3/eps_env (electric), Im G^Hm(0) = (2/3) k^3 (magnetic)
 gdm_status gdm_launch_alpha6_lorentz(gdm_ctx *ctx, int64_t n, const double *w0e, const double *w0m, double gamma_ev,
-                                     double amp_nm, double wavelength, double *out) {
+                                     double amp_nm, double wavelength, double eps_env, double *out) {
     const double hc_ev_nm = 1239.84198;  // h c in eV nm
-    const double w = hc_ev_nm / wavelength, k = 2.0 * PI_D / wavelength;
+    const double w = hc_ev_nm / wavelength, k = sqrt(eps_env) * 2.0 * PI_D / wavelength;
+    const double rad_m = (2.0 / 3.0) * k * k * k;
     k_alpha6_lorentz<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(
-        n, w0e, w0m, gamma_ev, amp_nm * amp_nm * amp_nm, w, (2.0 / 3.0) * k * k * k, (double2 *)out);
+        n, w0e, w0m, gamma_ev, amp_nm * amp_nm * amp_nm, w, rad_m / eps_env, rad_m, (double2 *)out);
     GDM_LAUNCHED(ctx, "alpha6_lorentz");
     return GDM_OK;
 }
@@ -451,12 +456,13 @@ __global__ void __launch_bounds__(ASM_TI) k_assemble3_f64(double2 *__restrict__ 
     }
 }
 
-// kind 6 (vacuum ED/MD dipoles), generic 6x6 alpha_j. Block (128 targets) x (4 sources).
+// kind 6 (ED/MD dipoles), generic 6x6 alpha_j. Block (128 targets) x (4 sources). Host medium: the
+// dyad in its vacuum form at k acts on (x_e, n_env x_m); the rows are scaled by (1/eps_env, 1/n_env).
 template <class T>
 __global__ void __launch_bounds__(ASM_TI) k_assemble6(typename cplx<T>::t *__restrict__ A, int64_t lda, int64_t n,
                                                      const DipF *__restrict__ dipf, const double *__restrict__ pos,
                                                      const typename cplx<T>::t *__restrict__ alpha6, float khi,
-                                                     float klo, double k) {
+                                                     float klo, double k, T n_env, T inv_eps, T inv_n) {
     typedef typename cplx<T>::t C;
     __shared__ C sa[ASM_TJ6][36];
     __shared__ DipF sjf[ASM_TJ6];
@@ -499,12 +505,13 @@ __global__ void __launch_bounds__(ASM_TI) k_assemble6(typename cplx<T>::t *__res
         }
         for (int q = 0; q < 6; q++) {
             C x[6], y[6];
-            for (int a = 0; a < 6; a++) x[a] = sa[jj][a * 6 + q];
+            for (int a = 0; a < 6; a++) x[a] = a < 3 ? sa[jj][a * 6 + q] : cscale(sa[jj][a * 6 + q], n_env);
             apply_g6(g, x, y);
             for (int a = 0; a < 6; a++) {
+                const T sc = a < 3 ? -inv_eps : -inv_n;
                 C v;
-                v.x = -y[a].x;
-                v.y = -y[a].y;
+                v.x = sc * y[a].x;
+                v.y = sc * y[a].y;
                 col[a] = v;
             }
             col += lda;
@@ -634,9 +641,11 @@ gdm_status gdm_launch_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision
         }
     } else {
         dim3 grid((unsigned)((n + ASM_TI - 1) / ASM_TI), (unsigned)((n + ASM_TJ6 - 1) / ASM_TJ6));
+        const double n_env = sqrt(p->eps_env);
         if (prec == GDM_FP64) {
             k_assemble6<double><<<grid, blk, 0, ctx->stream>>>((double2 *)A, lda, n, nullptr, p->pos,
-                                                              (const double2 *)p->alpha6, khi, klo, k);
+                                                              (const double2 *)p->alpha6, khi, klo, k, n_env,
+                                                              1.0 / p->eps_env, 1.0 / n_env);
             GDM_LAUNCHED(ctx, "assemble6_f64");
         } else {
             float2 *a6 = sc.take<float2>(n * 36);
@@ -645,7 +654,9 @@ gdm_status gdm_launch_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision
             k_alpha6_f32<<<(unsigned)((n * 36 + bs - 1) / bs), bs, 0, ctx->stream>>>((const double2 *)p->alpha6,
                                                                                      n * 36, a6);
             GDM_LAUNCHED(ctx, "alpha6_f32");
-            k_assemble6<float><<<grid, blk, 0, ctx->stream>>>((float2 *)A, lda, n, dipf, p->pos, a6, khi, klo, k);
+            k_assemble6<float><<<grid, blk, 0, ctx->stream>>>((float2 *)A, lda, n, dipf, p->pos, a6, khi, klo, k,
+                                                             (float)n_env, (float)(1.0 / p->eps_env),
+                                                             (float)(1.0 / n_env));
             GDM_LAUNCHED(ctx, "assemble6_f32");
         }
     }
@@ -654,6 +665,8 @@ gdm_status gdm_launch_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision
 
 // ================================================================== FP64 matrix-free Green sums
 // Dipole moments P = alpha X (forward) or P = conj(X) (adjoint sources, kind 3); (kind*n) x n_rhs.
+// ED/MD (kind 6): the magnetic moments are stored times n_env, the form the Green sums and the far
+// field take them in.
 __global__ void k_moments(const double2 *__restrict__ X, int64_t n, int kind, int n_rhs, const double2 *__restrict__ eps,
                           double eps_env, double d3_4pi, const double2 *__restrict__ alpha6, int conj_only,
                           double2 *__restrict__ P) {
@@ -672,10 +685,11 @@ __global__ void k_moments(const double2 *__restrict__ X, int64_t n, int kind, in
         for (int a = 0; a < 3; a++) o[a] = cmul(al, x[a]);
     } else {
         const double2 *al = alpha6 + 36 * i;
+        const double n_env = sqrt(eps_env);
         for (int a = 0; a < 6; a++) {
             double2 s = make_double2(0.0, 0.0);
             for (int b = 0; b < 6; b++) cfma(s, al[6 * a + b], x[b]);
-            o[a] = s;
+            o[a] = a < 3 ? s : cscale(s, n_env);
         }
     }
 }
@@ -759,8 +773,8 @@ template <int KIND, int NR>
 __global__ void k_residual_finalize(const double2 *__restrict__ partial, int nchunks, int64_t n, int rhs0, int nr_here,
                                     const double2 *__restrict__ rhs, const double2 *__restrict__ X,
                                     const double2 *__restrict__ P, double self_S, int adjoint,
-                                    const double2 *__restrict__ eps, double eps_env, double d3_4pi,
-                                    double2 *__restrict__ r, double *__restrict__ norms2) {
+                                    const double2 *__restrict__ eps, double eps_env, double d3_4pi, double sE,
+                                    double sH, double2 *__restrict__ r, double *__restrict__ norms2) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double nrm[NR];
 #pragma unroll
@@ -777,6 +791,7 @@ __global__ void k_residual_finalize(const double2 *__restrict__ partial, int nch
                 double2 s = make_double2(0.0, 0.0);
                 for (int c = 0; c < nchunks; c++) s = cadd(s, partial[((c * NR + q) * n + t) * KIND + a]);
                 if (KIND == 3) s = cadd(s, cscale(P[col + a], self_S));
+                else s = cscale(s, a < 3 ? sE : sH);
                 double2 v;
                 if (adjoint) v = cadd(csub(rhs[col + a], X[col + a]), cmul(conjd(al), conjd(s)));
                 else v = cadd(csub(rhs[col + a], X[col + a]), s);
@@ -869,16 +884,16 @@ gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const doub
             GDM_TRY(launch_green_sum<3, 3>(ctx, p->pos, n, p->pos, Pbuf, n, q0, nr, k, k0, 1.0 / p->eps_env, 1,
                                            partial, &nc));
         else
-            GDM_TRY(launch_green_sum<6, 6>(ctx, p->pos, n, p->pos, Pbuf, n, q0, nr, k, k0, 1.0, 1, partial, &nc));
+            GDM_TRY(launch_green_sum<6, 6>(ctx, p->pos, n, p->pos, Pbuf, n, q0, nr, k, k, 1.0, 1, partial, &nc));
         unsigned nb = (unsigned)((n + 255) / 256);
         if (kind == 3)
             k_residual_finalize<3, 2><<<nb, 256, 0, ctx->stream>>>(
                 partial, nc, n, q0, nr, (const double2 *)rhs, (const double2 *)X, Pbuf, S, adjoint,
-                (const double2 *)p->eps, p->eps_env, d3_4pi, (double2 *)r, norms2);
+                (const double2 *)p->eps, p->eps_env, d3_4pi, 1.0, 1.0, (double2 *)r, norms2);
         else
             k_residual_finalize<6, 2><<<nb, 256, 0, ctx->stream>>>(
                 partial, nc, n, q0, nr, (const double2 *)rhs, (const double2 *)X, Pbuf, 0.0, 0, nullptr, 1.0, 0.0,
-                (double2 *)r, norms2);
+                1.0 / p->eps_env, 1.0 / sqrt(p->eps_env), (double2 *)r, norms2);
         GDM_LAUNCHED(ctx, "residual_finalize");
     }
     return GDM_OK;
@@ -887,8 +902,8 @@ gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const doub
 // ================================================================== near field
 template <int OUT>
 __global__ void k_nearfield_finalize(const double2 *__restrict__ partial, int nchunks, int64_t m, int rhs0, int nr_here,
-                                     const double2 *__restrict__ F0e, int n_rhs_total, double2 *__restrict__ E,
-                                     double2 *__restrict__ H) {
+                                     const double2 *__restrict__ F0e, int n_rhs_total, double sE, double sH,
+                                     double2 *__restrict__ E, double2 *__restrict__ H) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= m) return;
     for (int q = 0; q < nr_here; q++) {
@@ -896,6 +911,7 @@ __global__ void k_nearfield_finalize(const double2 *__restrict__ partial, int nc
         for (int a = 0; a < OUT; a++) {
             double2 s = make_double2(0.0, 0.0);
             for (int c = 0; c < nchunks; c++) s = cadd(s, partial[((c * 2 + q) * m + t) * OUT + a]);
+            s = cscale(s, a < 3 ? sE : sH);
             if (F0e) s = cadd(s, F0e[(int64_t)qq * 6 * m + 6 * t + a]);
             if (a < 3) E[(int64_t)qq * 3 * m + 3 * t + a] = s;
             else if (H) H[(int64_t)qq * 3 * m + 3 * t + a - 3] = s;
@@ -927,16 +943,18 @@ gdm_status gdm_launch_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double
             GDM_TRY(launch_green_sum<3, 6>(ctx, r_eval, m, p->pos, Pbuf, n, q0, nr, k, k0, 1.0 / p->eps_env, 0,
                                            partial, &nc));
         else
-            GDM_TRY(launch_green_sum<6, 6>(ctx, r_eval, m, p->pos, Pbuf, n, q0, nr, k, k0, 1.0, 0, partial, &nc));
+            GDM_TRY(launch_green_sum<6, 6>(ctx, r_eval, m, p->pos, Pbuf, n, q0, nr, k, k, 1.0, 0, partial, &nc));
+        const double sE = kind == 6 ? 1.0 / p->eps_env : 1.0, sH = kind == 6 ? 1.0 / sqrt(p->eps_env) : 1.0;
         k_nearfield_finalize<6><<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(
-            partial, nc, m, q0, nr, (const double2 *)F0_eval, n_rhs, (double2 *)E_out, (double2 *)H_out);
+            partial, nc, m, q0, nr, (const double2 *)F0_eval, n_rhs, sE, sH, (double2 *)E_out, (double2 *)H_out);
         GDM_LAUNCHED(ctx, "nearfield_finalize");
     }
     return GDM_OK;
 }
 
 // ================================================================== far field
-// f(rhat) = k^2/eps_env sum_j exp(-i k rhat.r_j) [p_j - rhat (rhat.p_j) - rhat x m_j] for q directions; one
+// f(rhat) = k^2/eps_env sum_j exp(-i k rhat.r_j) [p_j - rhat (rhat.p_j) - rhat x (n_env m_j)] for q directions
+// (the moment buffer holds n_env m_j); one
 // thread per direction, sources staged through shared memory, FP64. Optional quadrature: per CTA the
 // weighted sum of |f|^2 per RHS (partials for a deterministic final reduction).
 #define FF_T 128
@@ -1081,7 +1099,8 @@ gdm_status gdm_launch_farfield(gdm_ctx *ctx, const gdm_problem *p, const double 
 #define XS_BS 256
 __global__ void k_xsec_partial(const double2 *__restrict__ F0, const double2 *__restrict__ F, int64_t n, int kind,
                                const double2 *__restrict__ eps, double eps_env, double d3_4pi,
-                               const double2 *__restrict__ alpha6, double rad, double *__restrict__ part) {
+                               const double2 *__restrict__ alpha6, double rad_e, double rad_m,
+                               double *__restrict__ part) {
     int q = blockIdx.y;
     int64_t i = blockIdx.x * (int64_t)XS_BS + threadIdx.x;
     double se = 0.0, sa = 0.0;
@@ -1104,7 +1123,7 @@ __global__ void k_xsec_partial(const double2 *__restrict__ F0, const double2 *__
         for (int a = 0; a < kind; a++) {
             se += cconjmul(f0[a], pm[a]).y;
             sa += cconjmul(f[a], pm[a]).y;
-            if (kind == 6) sa -= rad * (pm[a].x * pm[a].x + pm[a].y * pm[a].y);
+            if (kind == 6) sa -= (a < 3 ? rad_e : rad_m) * (pm[a].x * pm[a].x + pm[a].y * pm[a].y);
         }
     }
     __shared__ double red[2][XS_BS / 32];
@@ -1162,10 +1181,12 @@ gdm_status gdm_launch_cross_sections(gdm_ctx *ctx, const gdm_problem *p, const d
     void *ws;
     GDM_TRY(gdm_scratch(ctx, (size_t)nb * n_rhs * 2 * sizeof(double) + 256, &ws));
     double *part = (double *)ws;
-    double rad = (2.0 / 3.0) * k * k * k;
+    // radiated power of the ED/MD dipoles in the host: (2/3) k^3/eps_env |p|^2 and (2/3) k^3 |m|^2
+    const double rad = (2.0 / 3.0) * k * k * k;
     k_xsec_partial<<<dim3(nb, n_rhs), XS_BS, 0, ctx->stream>>>((const double2 *)F0, (const double2 *)F, n, p->kind,
                                                                (const double2 *)p->eps, p->eps_env, d3_4pi,
-                                                               (const double2 *)p->alpha6, rad, part);
+                                                               (const double2 *)p->alpha6, rad / p->eps_env, rad,
+                                                               part);
     GDM_LAUNCHED(ctx, "xsec_partial");
     k_xsec_final<<<n_rhs, 32, 0, ctx->stream>>>(part, (int)nb, n_rhs, dpref, ext, sca, abs);
     GDM_LAUNCHED(ctx, "xsec_final");
@@ -1248,7 +1269,7 @@ gdm_status gdm_launch_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p,
     const double rad = (2.0 / 3.0) * k * k * k;
     k_xsec_partial<<<dim3((unsigned)nb, n_rhs), XS_BS, 0, ctx->stream>>>(
         (const double2 *)F0, (const double2 *)F, n, p->kind, (const double2 *)p->eps, p->eps_env, d3_4pi,
-        (const double2 *)p->alpha6, rad, part);
+        (const double2 *)p->alpha6, rad / p->eps_env, rad, part);
     GDM_LAUNCHED(ctx, "xsec_partial");
     k_xsec_final_pref<<<n_rhs, 32, 0, ctx->stream>>>(part, (int)nb, n_rhs, pref, ext, sca, abs);
     GDM_LAUNCHED(ctx, "xsec_final_pref");

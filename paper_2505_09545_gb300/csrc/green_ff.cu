@@ -1,4 +1,4 @@
-// Matrix-free refinement residual in double-float arithmetic (cells, kind 3; vacuum ED/MD dipoles, kind 6).
+// Matrix-free refinement residual in double-float arithmetic (cells, kind 3; ED/MD dipoles, kind 6).
 //
 // The residual r = F0 - A F of the FP64 refinement needs the Green dyad G^Ep of every pair to ~1e-13
 // relative. GB300 runs FP64 at ~1/64 of its FP32 rate, so this kernel regenerates G in double-float
@@ -9,8 +9,9 @@
 //     double precision) times cos/sin of the remainder |delta| <= pi/256 from its Taylor series
 //     (cos: 1 - d^2/2 + d^4/24 - d^6/720, sin: d - d^3/6 + d^5/120; the neglected terms are < 1e-15);
 //   * G s = a s + b u (u.s), accumulated in double-float, written as FP64 partial sums for the FP64 finalize;
-//     for ED/MD dipoles (vacuum) the 6x6 dyad acts on (p, m): (G p - C m, C p + G m) with C s = c (u x s),
-//     c = e^{ikR} (k^2/R + i k/R^2).
+//     for ED/MD dipoles the 6x6 dyad in its vacuum form at the host k acts on (p, n_env m):
+//     (T p - C n_env m, C p + T n_env m) with T = eps_env G^Ep, C s = c (u x s), c = e^{ikR} (k^2/R + i k/R^2);
+//     the residual's finalize scales the rows by (1/eps_env, 1/n_env).
 #include <math.h>
 
 #include "gdm_internal.cuh"
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ 
             cff ca = {sub(k2r1, ri3), kri2};
             cff cb = {sub(mulf(ri3, 3.0f), k2r1), neg(mulf(kri2, 3.0f))};
             cff a = cmulff(e, ca), b = cmulff(e, cb);
-            // magnetic-electric coupling (kind 6, vacuum): c = e (k^2/R + i k/R^2)
+            // magnetic-electric coupling (kind 6): c = e (k^2/R + i k/R^2)
             cff cc = {mk(0, 0), mk(0, 0)};
             if (KIND == 6) cc = cmulff(e, cff{k2r1, kri2});
 #pragma unroll
@@ -289,7 +290,7 @@ gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const dou
     float khi, klo, k2hi, k2lo, iehi, ielo;
     split(k, &khi, &klo);
     split(k * k, &k2hi, &k2lo);
-    split(1.0 / p->eps_env, &iehi, &ielo);
+    split(p->kind == 6 ? 1.0 : 1.0 / p->eps_env, &iehi, &ielo);  // kind 6: the vacuum-form kernel T
     dim3 grid((unsigned)((n + RF_T - 1) / RF_T), (unsigned)nchunks);
     if (p->kind == 6) {
         if (nr == 1)
