@@ -267,6 +267,43 @@ typedef struct {
 gdm_status gdm_backward_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_backward_item *items, int n_items,
                                 int n_streams, double *grad_pos, double *grad_eps, gdm_solve_info *infos);
 
+/* ---------------------------------------------------------------- iterative solver */
+
+typedef struct {
+    int32_t restart;      /* Krylov vectors per cycle m (default 60 when <= 0; at most 120) */
+    int32_t max_iter;     /* operator applications allowed in total (default 1000 when <= 0) */
+    double tol;           /* stop when max_r ||F0_r - A F_r|| / ||F0_r|| <= tol (default 1e-12 when <= 0) */
+    int32_t block_cells;  /* cells per block of the block-Jacobi part (default 512 when <= 0; at most 1024) */
+    int32_t flags;        /* GDM_GMRES_* bit flags */
+} gdm_gmres_opts;
+
+#define GDM_GMRES_NO_COARSE 1  /* leave out the coarse-model correction of the preconditioner */
+#define GDM_GMRES_NO_BLOCKS 2  /* leave out its block-Jacobi part (both flags: plain GMRES) */
+
+/* Solve A F = F0 for a discretised structure (kind 3) without forming A, for structures beyond the
+ * dense path's memory (no paper counterpart: the paper bounds its full inversion to about 10^4
+ * dipoles and names iterative schemes as the way past it, Sec. "Conclusions" and "Benchmarks").
+ * Flexible GMRES(m) in FP64 on the matrix-free operator (the double-float Green sums of the
+ * refinement residual), right-preconditioned by
+ *   M^-1 v = P A_c^-1 R v + B^-1 (v - P R v),
+ * A_c the coarser model (cells merged 2 x 2 x 2 on the lattice: centroid position, summed
+ * polarisability in the couplings, and the self-term block 1 + chi/(3 eps_env) of a cube filled
+ * with the merged cells' mean susceptibility chi), R the mean over the merged cells, P the copy
+ * back, B the exact
+ * diagonal blocks of A over runs of block_cells cells in Morton order of the lattice; A_c and the
+ * blocks are assembled and factored by the mixed-precision LU in `prec` (GDM_TF32_REFINE or
+ * GDM_FP32); a structure of at most block_cells cells is preconditioned by its whole LU alone
+ * (the coarse term is left out). Cells are assumed on a cubic lattice of step p->step (positions
+ * are rounded to it for the grouping only). F0, F: device (3n) x n_rhs complex128, 1 <= n_rhs <= 8 (all right-hand sides
+ * iterate in lockstep). Device memory: about (2m + 6) 3n n_rhs complex128 vectors, the block factors
+ * (3 block_cells x 8 bytes per row of A) and the coarse factors ((3n/8)^2 x 8 bytes); allocated and
+ * freed inside the call. info (nullable): iterations = operator applications, rel_residual = final
+ * max_r ||F0_r - A F_r|| / ||F0_r||, rel_correction = last GMRES residual estimate, factor_ms =
+ * preconditioner set-up, refine_ms = iterations, pivot_growth / refactored over all factorisations.
+ * GDM_ERR_NOT_CONVERGED when max_iter is reached first (F then holds the last iterate). Synchronous. */
+gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, const double *F0, double *F,
+                           int n_rhs, const gdm_gmres_opts *opts, gdm_solve_info *info);
+
 /* ---------------------------------------------------------------- effective models */
 
 /* Global polarizability matrix (GPM) of a discretised structure (Sec. "Effective

@@ -5,7 +5,8 @@ package only builds/loads it and marshals arguments (see `binding`)."""
 from . import autograd  # noqa: F401
 from .binding import (Context, GDMError, GDMProblem, alpha6_lorentz, assemble, autotune, backward, cross_sections,
                       farfield, gpm_extract, incident_dipole, incident_gaussian, ldos, sigma_farfield, incident_planewave, lib, nearfield, nearfield_backward, padded_lda, residual,
-                      solve, solve_batched)
+                      solve, solve_batched, solve_gmres)
 
 __all__ = ["Context", "GDMError", "GDMProblem", "alpha6_lorentz", "assemble", "autotune", "backward", "cross_sections", "farfield", "gpm_extract", "incident_dipole", "incident_gaussian", "ldos", "sigma_farfield", "incident_planewave",
-           "lib", "nearfield", "nearfield_backward", "padded_lda", "residual", "solve", "solve_batched"]
+           "lib", "nearfield", "nearfield_backward", "padded_lda", "residual", "solve", "solve_batched",
+           "solve_gmres"]

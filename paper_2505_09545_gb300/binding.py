@@ -58,6 +58,15 @@ class SolveOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("flags", C.c_int32), ("tol", C.c_double)]
 
 
+class GmresOpts(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double), ("block_cells", C.c_int32),
+                ("flags", C.c_int32)]
+
+
+GMRES_NO_COARSE = 1
+GMRES_NO_BLOCKS = 2
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("rel_correction", C.c_double),
                 ("rel_residual", C.c_double), ("factor_ms", C.c_double), ("refine_ms", C.c_double),
@@ -106,6 +115,8 @@ _SIGS = {
     "gdm_backward": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, C.c_int, PD, PD, P, PD, P, P, P,
                       C.POINTER(SolveInfo)], C.c_int),
     "gdm_nearfield_backward": ([P, C.POINTER(Problem), P, P, I64, C.c_int, PD, PD, P, P, P, P, P], C.c_int),
+    "gdm_solve_gmres": ([P, C.c_int, C.POINTER(Problem), P, P, C.c_int, C.POINTER(GmresOpts),
+                         C.POINTER(SolveInfo)], C.c_int),
     "gdm_profile_enable": ([P, C.c_int], C.c_int),
     "gdm_profile_read": ([P, C.POINTER(I64), PD, PD, PD], C.c_int),
     "gdm_profile_phases": ([P, C.c_int, PD], C.c_int),
@@ -295,6 +306,22 @@ def solve(ctx: Context, prob: GDMProblem, A, F0, precision="fp32", ipiv=None, fa
     ctx._check(lib().gdm_solve(ctx.h, C.byref(s), PRECISION[precision], _ptr(A), lda, _ptr(ipiv), _ptr(F0.contiguous()),
                                _ptr(F), n_rhs, C.byref(opts), C.byref(inf) if info else None), "gdm_solve")
     return F, ipiv, (inf.as_dict() if info else None)
+
+
+def solve_gmres(ctx: Context, prob: GDMProblem, F0, precision="tf32", restart=0, max_iter=0, tol=0.0,
+                block_cells=0, coarse=True, blocks=True, F=None):
+    """gdm_solve_gmres: matrix-free preconditioned GMRES for cells. F0: (n_rhs, 3n) complex128 device.
+    Returns (F, info dict)."""
+    if F is None:
+        F = torch.empty_like(F0)
+    flags = (0 if coarse else GMRES_NO_COARSE) | (0 if blocks else GMRES_NO_BLOCKS)
+    opts = GmresOpts(int(restart), int(max_iter), float(tol), int(block_cells), flags)
+    inf = SolveInfo()
+    s = prob.struct()
+    ctx._sync_stream()
+    ctx._check(lib().gdm_solve_gmres(ctx.h, PRECISION[precision], C.byref(s), _ptr(F0.contiguous()), _ptr(F),
+                                     F0.shape[0], C.byref(opts), C.byref(inf)), "gdm_solve_gmres")
+    return F, inf.as_dict()
 
 
 def residual(ctx: Context, prob: GDMProblem, F0, F):
