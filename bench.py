@@ -491,6 +491,56 @@ def run_ldos(args):
     ctx.close()
 
 
+def run_gmres(args):
+    """Matrix-free preconditioned GMRES on a cuboid larger than the dense workload (default 80 x 60 x 10 cells,
+    N = 48,000, 3N = 144,000: its dense complex64 matrix alone would take 166 GB): one step = one
+    gdm_solve_gmres call (partition, coarse-model and block factorisations, FGMRES to a relative residual of
+    1e-12 for both polarisations) from device-resident inputs."""
+    import numpy as np
+    import torch
+    import gdm_workloads as W
+    import paper_2505_09545_gb300 as G
+    ws, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nx, ny, nz = (int(v) for v in args.gmres_cuboid.split("x"))
+    s = W.cuboid_precision(nx, ny, nz)
+    lam = float(s.wavelengths[0])
+    ctx = G.Context(local)
+    pos = torch.tensor(s.pos, device=dev)
+    prob = G.GDMProblem(pos, lam, 3, eps=torch.tensor(s.eps, device=dev), step=s.step)
+    F0 = G.incident_planewave(ctx, pos, lam, s.e0)
+    F = torch.empty_like(F0)
+    for _ in range(max(1, args.warmup)):
+        F, info = G.solve_gmres(ctx, prob, F0, precision=args.precision if args.precision != "fp64" else "tf32", F=F)
+    torch.cuda.synchronize()
+    e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = G.lib().gdm_launch_count(ctx.h)
+    e0_.record()
+    for _ in range(args.steps):
+        F, info = G.solve_gmres(ctx, prob, F0, precision=args.precision if args.precision != "fp64" else "tf32", F=F)
+    e1_.record()
+    torch.cuda.synchronize()
+    launches = (G.lib().gdm_launch_count(ctx.h) - launches0) // args.steps
+    ms = e0_.elapsed_time(e1_) / args.steps
+    # operator throughput: each GMRES step (and each restart's residual) is one pass over all N^2 pairs for
+    # both right-hand sides
+    passes = info["iterations"] + max(1, (info["iterations"] + 59) // 60) + 1
+    line = {"metric": "GMRES solve s per (lambda, N)", "value": ms / 1e3, "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 operator, tf32 preconditioner", "data": "synthetic",
+            "config": {"workload": f"cuboid {nx}x{ny}x{nz} cells, d=10 nm, N={s.n} (3N={3 * s.n}), eps~U[2,16]+iU[0,0.5] "
+                                   "seed 2, lambda=500 nm, x- and y-polarised; FGMRES(60), coarse model + 512-cell blocks, "
+                                   "tol 1e-12"},
+            "iterations": info["iterations"], "rel_residual": info["rel_residual"],
+            "setup_ms": info["factor_ms"], "iterate_ms": info["refine_ms"],
+            "pair_evals_per_s": passes * float(s.n) ** 2 * 2 / (info["refine_ms"] / 1e3),
+            "gpu_launches": int(launches)}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+
+
 def max_over_ranks(value, ws, device):
     """The job's time is the slowest rank's: all-reduce MAX over the process group (any backend; the
     tensor lives on `device`). Single process: the value itself."""
@@ -560,10 +610,13 @@ def main():
                     help="cells per axis of the cuboid workload (smaller cases are for profiling only)")
     ap.add_argument("--fp64-cuboid", default="20x15x10",
                     help="cuboid of the FP64-GPU-path comparison (40x30x10 = the full workload, ~2 min)")
-    ap.add_argument("--workload", default="cuboid", choices=["cuboid", "metasurface", "batch", "gpm", "farfield", "ldos"],
+    ap.add_argument("--workload", default="cuboid",
+                    choices=["cuboid", "metasurface", "batch", "gpm", "farfield", "ldos", "gmres"],
                     help="cuboid: the headline assemble+solve line; metasurface: 64x64 ED/MD array, 32 wavelengths; "
                          "batch: 256 uneven blobs, each at its own wavelength; gpm: effective-model extraction; "
-                         "farfield: far-field sigma_sca of the solved cuboid; ldos: electric LDOS around the sphere")
+                         "farfield: far-field sigma_sca of the solved cuboid; ldos: electric LDOS around the sphere; "
+                         "gmres: matrix-free preconditioned GMRES on a larger cuboid")
+    ap.add_argument("--gmres-cuboid", default="80x60x10", help="gmres workload: cells per axis")
     ap.add_argument("--streams", type=int, default=0, help="batch workload: concurrent streams (0 = default)")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: keep the default LU block width")
     ap.add_argument("--no-extras", action="store_true",
@@ -587,6 +640,8 @@ def main():
         return run_farfield(args)
     if args.workload == "ldos":
         return run_ldos(args)
+    if args.workload == "gmres":
+        return run_gmres(args)
 
     ws, rank, local = dist_setup()
     if ws > 1:
