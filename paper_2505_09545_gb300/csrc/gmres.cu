@@ -203,9 +203,39 @@ __global__ void __launch_bounds__(BJ_T) k_bj_solve(const float2 *__restrict__ fa
         ysm[q * m + r] = y;
     }
     __syncthreads();
+    // the panel's 32 x 32 diagonal block, staged so that the warp-serial solve reads shared memory only
+    __shared__ float2 D[BJ_W][BJ_W + 1];
+    // y[r] -= sum_{i < w} A[r, c0 + i] y[c0 + i] for the rows r of [rb, re) (8 independent loads in flight)
+    auto update = [&](int c0, int w, int rb, int re) {
+        for (int r = rb + tid; r < re; r += BJ_T) {
+            float2 acc[NR];
+#pragma unroll
+            for (int q = 0; q < NR; q++) acc[q] = make_float2(0.f, 0.f);
+            for (int i0 = 0; i0 < w; i0 += 8) {
+                float2 a[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) a[k] = i0 + k < w ? A[(c0 + i0 + k) * ld + r] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    if (i0 + k < w) {
+#pragma unroll
+                        for (int q = 0; q < NR; q++) cfma(acc[q], a[k], ysm[q * m + c0 + i0 + k]);
+                    }
+            }
+#pragma unroll
+            for (int q = 0; q < NR; q++) ysm[q * m + r] = csub(ysm[q * m + r], acc[q]);
+        }
+    };
+    auto stage_diag = [&](int c0, int w) {
+        for (int e = tid; e < BJ_W * BJ_W; e += BJ_T) {
+            const int r = e % BJ_W, c = e / BJ_W;
+            D[r][c] = (r < w && c < w) ? A[(c0 + c) * ld + c0 + r] : make_float2(0.f, 0.f);
+        }
+    };
     // forward: P, then L^-1 (unit diagonal), panel by panel
     for (int c0 = 0; c0 < m; c0 += BJ_W) {
         const int w = min(BJ_W, m - c0);
+        stage_diag(c0, w);
         if (tid < nr) {
             float2 *y = ysm + tid * m;
             for (int k = 0; k < w; k++) {
@@ -225,57 +255,37 @@ __global__ void __launch_bounds__(BJ_T) k_bj_solve(const float2 *__restrict__ fa
                 float2 xi;
                 xi.x = __shfl_sync(0xffffffffu, x.x, i);
                 xi.y = __shfl_sync(0xffffffffu, x.y, i);
-                if (lane > i && lane < w) cfms(x, A[(c0 + i) * ld + c0 + lane], xi);
+                if (lane > i && lane < w) cfms(x, D[lane][i], xi);
             }
             if (lane < w) y[c0 + lane] = x;
         }
         __syncthreads();
-        for (int r = c0 + w + tid; r < m; r += BJ_T) {
-            float2 acc[NR];
-#pragma unroll
-            for (int q = 0; q < NR; q++) acc[q] = make_float2(0.f, 0.f);
-            for (int i = 0; i < w; i++) {
-                const float2 a = A[(c0 + i) * ld + r];
-#pragma unroll
-                for (int q = 0; q < NR; q++) cfma(acc[q], a, ysm[q * m + c0 + i]);
-            }
-#pragma unroll
-            for (int q = 0; q < NR; q++) ysm[q * m + r] = csub(ysm[q * m + r], acc[q]);
-        }
+        update(c0, w, c0 + w, m);
         __syncthreads();
     }
     // backward: U^-1, last panel first
     for (int c0 = ((m - 1) / BJ_W) * BJ_W; c0 >= 0; c0 -= BJ_W) {
         const int w = min(BJ_W, m - c0);
+        stage_diag(c0, w);
+        __syncthreads();
         if (warp < nr) {
             float2 *y = ysm + warp * m;
             float2 x = lane < w ? y[c0 + lane] : make_float2(0.f, 0.f);
             for (int i = w - 1; i >= 0; i--) {
                 if (lane == i) {
-                    const float2 u = A[(c0 + i) * ld + c0 + i];
+                    const float2 u = D[i][i];
                     const float dd = 1.0f / (u.x * u.x + u.y * u.y);
                     x = cmul(x, make_float2(u.x * dd, -u.y * dd));
                 }
                 float2 xi;
                 xi.x = __shfl_sync(0xffffffffu, x.x, i);
                 xi.y = __shfl_sync(0xffffffffu, x.y, i);
-                if (lane < i) cfms(x, A[(c0 + i) * ld + c0 + lane], xi);
+                if (lane < i) cfms(x, D[lane][i], xi);
             }
             if (lane < w) y[c0 + lane] = x;
         }
         __syncthreads();
-        for (int r = tid; r < c0; r += BJ_T) {
-            float2 acc[NR];
-#pragma unroll
-            for (int q = 0; q < NR; q++) acc[q] = make_float2(0.f, 0.f);
-            for (int i = 0; i < w; i++) {
-                const float2 a = A[(c0 + i) * ld + r];
-#pragma unroll
-                for (int q = 0; q < NR; q++) cfma(acc[q], a, ysm[q * m + c0 + i]);
-            }
-#pragma unroll
-            for (int q = 0; q < NR; q++) ysm[q * m + r] = csub(ysm[q * m + r], acc[q]);
-        }
+        update(c0, w, 0, c0);
         __syncthreads();
     }
     for (int e = tid; e < m * nr; e += BJ_T) {
@@ -340,7 +350,8 @@ __global__ void k_coarse_only(const double2 *__restrict__ v, int64_t ns, int nr,
 }
 
 // ------------------------------------------------------------------ Krylov kernels
-// part[(q * J + i) * nct + cta] = sum over the CTA's rows of conj(V_i[r, q]) w[r, q], i < J
+// part[(q * J + i) * nct + cta] = sum over the CTA's rows of conj(V_i[r, q]) w[r, q], i < J; eight basis
+// vectors per reduction round
 __global__ void __launch_bounds__(GM_T) k_gm_dots(const double2 *__restrict__ V, int64_t ns, int nr, int J,
                                                   const double2 *__restrict__ w, double2 *__restrict__ part) {
     const int cta = blockIdx.x, q = blockIdx.y, nct = gridDim.x;
@@ -350,24 +361,32 @@ __global__ void __launch_bounds__(GM_T) k_gm_dots(const double2 *__restrict__ V,
         const int64_t r = rb + threadIdx.x + k * GM_T;
         wl[k] = r < ns ? w[q * ns + r] : make_double2(0.0, 0.0);
     }
-    __shared__ double2 red[GM_T / 32];
-    for (int i = 0; i < J; i++) {
-        const double2 *vi = V + ((int64_t)i * nr + q) * ns;
-        double2 s = make_double2(0.0, 0.0);
-        for (int k = 0; k < 4; k++) {
-            const int64_t r = rb + threadIdx.x + k * GM_T;
-            if (r < ns) s = cadd(s, cconjmul(vi[r], wl[k]));
+    __shared__ double2 red[8][GM_T / 32];
+    for (int i0 = 0; i0 < J; i0 += 8) {
+        double2 s[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            s[t] = make_double2(0.0, 0.0);
+            if (i0 + t < J) {
+                const double2 *vi = V + ((int64_t)(i0 + t) * nr + q) * ns;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int64_t r = rb + threadIdx.x + k * GM_T;
+                    if (r < ns) s[t] = cadd(s[t], cconjmul(vi[r], wl[k]));
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s[t].x += __shfl_down_sync(0xffffffffu, s[t].x, o);
+                s[t].y += __shfl_down_sync(0xffffffffu, s[t].y, o);
+            }
+            if ((threadIdx.x & 31) == 0) red[t][threadIdx.x >> 5] = s[t];
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            s.x += __shfl_down_sync(0xffffffffu, s.x, o);
-            s.y += __shfl_down_sync(0xffffffffu, s.y, o);
-        }
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double2 t = red[0];
-            for (int k = 1; k < GM_T / 32; k++) t = cadd(t, red[k]);
-            part[((int64_t)q * J + i) * nct + cta] = t;
+        if (threadIdx.x < 8 && i0 + (int)threadIdx.x < J) {
+            double2 tt = red[threadIdx.x][0];
+            for (int k = 1; k < GM_T / 32; k++) tt = cadd(tt, red[threadIdx.x][k]);
+            part[((int64_t)q * J + i0 + threadIdx.x) * nct + cta] = tt;
         }
         __syncthreads();
     }
