@@ -526,6 +526,22 @@ def run_gmres(args):
     # operator throughput: each GMRES step (and each restart's residual) is one pass over all N^2 pairs for
     # both right-hand sides
     passes = info["iterations"] + max(1, (info["iterations"] + 59) // 60) + 1
+    # one more solve with phase accounting (CUDA events on the context stream around every operator
+    # application): the operator kernel k_green_sum_ff (double-float pair sums on the FP32 pipes) against
+    # the FP32 issue rate of 152 SMs x 128 lanes x 2.07 GHz; 1,406 FP32 thread instructions per
+    # (target, source) pair for two right-hand sides (ncu count, profiles/green_sum_ff_gmres_cuboid20x15x10_ncu.md)
+    ctx.phases(True)
+    G.solve_gmres(ctx, prob, F0, precision=args.precision if args.precision != "fp64" else "tf32", F=F)
+    ph = ctx.phases(False)
+    op_ms = ph["residual"]
+    inst_per_pair = 1406.0
+    peak_inst = 152 * 128 * 2.07e9
+    achieved = passes * float(s.n) ** 2 * inst_per_pair / (op_ms / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_inst, "unit": "FP32 inst/s",
+                "frac": achieved / peak_inst, "traffic": None, "kernel": "k_green_sum_ff (GMRES operator)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock)",
+                "operator_share_of_iterations": op_ms / max(ph["residual"] + ph["correction_solves"] + ph["other"], 1e-9),
+                "phases_ms": {"operator": op_ms, "preconditioner": ph["correction_solves"], "orthogonalisation": ph["other"]}}
     line = {"metric": "GMRES solve s per (lambda, N)", "value": ms / 1e3, "unit": "s", "n_gpus": 1,
             "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 operator, tf32 preconditioner", "data": "synthetic",
@@ -535,7 +551,7 @@ def run_gmres(args):
             "iterations": info["iterations"], "rel_residual": info["rel_residual"],
             "setup_ms": info["factor_ms"], "iterate_ms": info["refine_ms"],
             "pair_evals_per_s": passes * float(s.n) ** 2 * 2 / (info["refine_ms"] / 1e3),
-            "gpu_launches": int(launches)}
+            "roofline": roofline, "gpu_launches": int(launches)}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

@@ -676,7 +676,9 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
         GDM_CUDA_TRY(ctx, cudaEventElapsedTime(&setup_ms, ctx->ev0, ctx->ev1));
     }
 
+    // phase accounting (gdm_profile_phases): preconditioner as correction solves, operator as residual
     auto precond = [&](const double2 *v, double2 *z) -> gdm_status {
+        GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRSV));
         if (use_coarse) {
             k_restrict<<<nblk(nc3 * nr), GM_T, 0, ctx->stream>>>(v, ns, nr, d_coff, nc, rc, yc);
             GDM_LAUNCHED(ctx, "gmres_restrict");
@@ -695,15 +697,16 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
         } else {
             GDM_CUDA_TRY(ctx, cudaMemcpyAsync(z, v, sizeof(double2) * vec, cudaMemcpyDeviceToDevice, ctx->stream));
         }
-        return GDM_OK;
+        return gdm_phase_end(ctx, GDM_PH_TRSV);
     };
     // r = rhs - A X (double-float Green sums); norms2 (device, nr) optional
     bool ff_ready = false;
     auto residual = [&](const double2 *rhs, const double2 *X, double2 *r, double *norms2) -> gdm_status {
+        GDM_TRY(gdm_phase_begin(ctx, GDM_PH_RESIDUAL));
         GDM_TRY(gdm_launch_residual_ws(ctx, &pp, (const double *)rhs, (const double *)X, nr, 0, (double *)r, norms2,
                                        Pbuf, gpart, ffws, ff_ready ? 0 : 1));
         ff_ready = true;
-        return GDM_OK;
+        return gdm_phase_end(ctx, GDM_PH_RESIDUAL);
     };
 
     // ---- FGMRES(m)
@@ -763,6 +766,7 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
             GDM_TRY(residual(zero, Zj, w, nullptr));  // w = -A z_j
             const int J = j + 1;
             const dim3 gr((unsigned)nct, (unsigned)nr);
+            GDM_TRY(gdm_phase_begin(ctx, GDM_PH_OTHER));
             k_gm_dots<<<gr, GM_T, 0, ctx->stream>>>(V, ns, nr, J, w, dpart);
             GDM_LAUNCHED(ctx, "gmres_dots");
             k_gm_dots_final<<<dim3((unsigned)J, (unsigned)nr), 32, 0, ctx->stream>>>(dpart, nct, J, h1);
@@ -777,6 +781,7 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
             GDM_LAUNCHED(ctx, "gmres_orth");
             k_gm_norm_final<<<nr, 32, 0, ctx->stream>>>(npart, nct, nrm);
             GDM_LAUNCHED(ctx, "gmres_norm_final");
+            GDM_TRY(gdm_phase_end(ctx, GDM_PH_OTHER));
             GDM_CUDA_TRY(ctx, cudaMemcpyAsync(hh1, h1, sizeof(double2) * J * nr, cudaMemcpyDeviceToHost, ctx->stream));
             GDM_CUDA_TRY(ctx, cudaMemcpyAsync(hh2, h2, sizeof(double2) * J * nr, cudaMemcpyDeviceToHost, ctx->stream));
             GDM_CUDA_TRY(ctx, cudaMemcpyAsync(hnrm, nrm, sizeof(double) * nr, cudaMemcpyDeviceToHost, ctx->stream));
