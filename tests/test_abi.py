@@ -59,7 +59,9 @@ def test_built_for_sm103a():
     assert os.path.exists(_build.LIB)
 
 
-@pytest.mark.parametrize("cname,pyname", [("gdm_batch_item", "BatchItem"), ("gdm_backward_item", "BackwardItem")])
+@pytest.mark.parametrize("cname,pyname", [("gdm_batch_item", "BatchItem"), ("gdm_backward_item", "BackwardItem"),
+                                          ("gdm_gmres_opts", "GmresOpts"), ("gdm_solve_info", "SolveInfo"),
+                                          ("gdm_problem", "Problem")])
 def test_batch_item_layout_matches_the_header(tmp_path, cname, pyname):
     """The ctypes mirrors of the batch structs have the C compiler's size and field offsets."""
     import shutil
@@ -85,3 +87,4 @@ def test_batched_and_autotune_reject_a_null_context(lib):
     assert lib.gdm_solve_batched(None, 2, None, 0, None, 0, None) == 1
     assert lib.gdm_autotune(None, 2, None, 0, None) == 1
     assert lib.gdm_backward_batched(None, 2, None, 0, 0, None, None, None) == 1
+    assert lib.gdm_solve_gmres(None, 2, None, None, None, 1, None, None) == 1
