@@ -279,22 +279,27 @@ typedef struct {
 
 #define GDM_GMRES_NO_COARSE 1  /* leave out the coarse-model correction of the preconditioner */
 #define GDM_GMRES_NO_BLOCKS 2  /* leave out its block-Jacobi part (both flags: plain GMRES) */
+#define GDM_GMRES_EXACT_OPERATOR 4  /* Arnoldi steps on the double-float operator, not the FP32 one */
 
 /* Solve A F = F0 for a discretised structure (kind 3) without forming A, for structures beyond the
  * dense path's memory (no paper counterpart: the paper bounds its full inversion to about 10^4
  * dipoles and names iterative schemes as the way past it, Sec. "Conclusions" and "Benchmarks").
- * Flexible GMRES(m) in FP64 on the matrix-free operator (the double-float Green sums of the
- * refinement residual), right-preconditioned by
+ * Flexible GMRES(m) in FP64 on the matrix-free operator, right-preconditioned by
  *   M^-1 v = P A_c^-1 R v + B^-1 (v - P R v),
  * A_c the coarser model (cells merged 2 x 2 x 2 on the lattice: centroid position, summed
  * polarisability in the couplings, and the self-term block 1 + chi/(3 eps_env) of a cube filled
  * with the merged cells' mean susceptibility chi), R the mean over the merged cells, P the copy
- * back, B the exact
- * diagonal blocks of A over runs of block_cells cells in Morton order of the lattice; A_c and the
- * blocks are assembled and factored by the mixed-precision LU in `prec` (GDM_TF32_REFINE or
- * GDM_FP32); a structure of at most block_cells cells is preconditioned by its whole LU alone
- * (the coarse term is left out). Cells are assumed on a cubic lattice of step p->step (positions
- * are rounded to it for the grouping only). F0, F: device (3n) x n_rhs complex128, 1 <= n_rhs <= 8 (all right-hand sides
+ * back, B the exact diagonal blocks of A over runs of block_cells cells in Morton order of the
+ * lattice; A_c and the blocks are assembled and factored by the mixed-precision LU in `prec`
+ * (GDM_TF32_REFINE or GDM_FP32). A structure of at most block_cells cells is preconditioned by its
+ * whole LU alone (the coarse term is left out).
+ * Each restart cycle starts from the true residual F0 - A F in double-float arithmetic (the
+ * refinement residual of gdm_solve, ~1e-13 relative). Unless GDM_GMRES_EXACT_OPERATOR is set, its
+ * Arnoldi steps use FP32 Green sums (double-float phase, ~1e-6 relative) and the cycle ends once it
+ * has reduced its residual by 1e-4: the cycles are the outer steps of an iterative refinement, and a
+ * cycle that fails to halve the true residual switches the rest of the solve to the double-float
+ * operator. Cells are assumed on a cubic lattice of step p->step (positions are rounded to it for
+ * the grouping only). F0, F: device (3n) x n_rhs complex128, 1 <= n_rhs <= 8 (all right-hand sides
  * iterate in lockstep). Device memory: about (2m + 6) 3n n_rhs complex128 vectors, the block factors
  * (3 block_cells x 8 bytes per row of A) and the coarse factors ((3n/8)^2 x 8 bytes); allocated and
  * freed inside the call. info (nullable): iterations = operator applications, rel_residual = final

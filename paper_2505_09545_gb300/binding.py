@@ -65,6 +65,7 @@ class GmresOpts(C.Structure):
 
 GMRES_NO_COARSE = 1
 GMRES_NO_BLOCKS = 2
+GMRES_EXACT_OPERATOR = 4
 
 
 class SolveInfo(C.Structure):
@@ -309,12 +310,13 @@ def solve(ctx: Context, prob: GDMProblem, A, F0, precision="fp32", ipiv=None, fa
 
 
 def solve_gmres(ctx: Context, prob: GDMProblem, F0, precision="tf32", restart=0, max_iter=0, tol=0.0,
-                block_cells=0, coarse=True, blocks=True, F=None):
+                block_cells=0, coarse=True, blocks=True, fast_operator=True, F=None):
     """gdm_solve_gmres: matrix-free preconditioned GMRES for cells. F0: (n_rhs, 3n) complex128 device.
     Returns (F, info dict)."""
     if F is None:
         F = torch.empty_like(F0)
-    flags = (0 if coarse else GMRES_NO_COARSE) | (0 if blocks else GMRES_NO_BLOCKS)
+    flags = ((0 if coarse else GMRES_NO_COARSE) | (0 if blocks else GMRES_NO_BLOCKS)
+             | (0 if fast_operator else GMRES_EXACT_OPERATOR))
     opts = GmresOpts(int(restart), int(max_iter), float(tol), int(block_cells), flags)
     inf = SolveInfo()
     s = prob.struct()

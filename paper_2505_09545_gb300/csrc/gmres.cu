@@ -7,8 +7,14 @@
 //   * flexible GMRES(m) in FP64 (right preconditioning, the preconditioned basis Z kept explicitly so
 //     that an inexact, FP32 preconditioner is allowed), classical Gram-Schmidt with one
 //     re-orthogonalisation, Givens rotations on the host, all right-hand sides in lockstep;
-//   * the operator A z is the matrix-free double-float Green sum of the refinement residual
-//     (r = 0 - A z), so its cost is O(N^2) pair evaluations per step and its memory O(N);
+//   * the operator A z is matrix-free (O(N^2) pair evaluations per step, O(N) memory). Every cycle
+//     starts from the true residual b - A x in double-float arithmetic (the refinement residual), and
+//     its Arnoldi steps apply an FP32 operator (FP32 Green sums with a double-float phase, about 1e-6
+//     relative, ~1/9 of the double-float work) until the cycle has reduced its residual by 1e-4: the
+//     cycles are the outer steps of an iterative refinement whose inner solver is FGMRES on the
+//     low-precision operator, so the solution still reaches the double-float accuracy. A cycle that
+//     fails to halve the true residual switches the rest of the solve to the double-float operator;
+//     GDM_GMRES_EXACT_OPERATOR uses it throughout;
 //   * a two-level mixed-precision preconditioner
 //         M^-1 v = P A_c^-1 R v + B^-1 (v - P R v)
 //     A_c: a coarser model of the structure, its cells merged 2 x 2 x 2 on the lattice (position = the
@@ -41,6 +47,9 @@ gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const doub
                                   int ff_prepare);
 size_t gdm_ff_scratch_bytes(int64_t n);
 size_t gdm_green_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n, int out);
+gdm_status gdm_launch_residual_f32(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
+                                   double *r, double *norms2, double2 *Pbuf, double2 *partial, const void *dipf);
+const void *gdm_ff_positions(void *ffws);
 
 namespace {
 
@@ -51,6 +60,7 @@ constexpr int GM_T = 256;              // threads of the vector kernels
 constexpr int GM_ROWS = 4 * GM_T;      // rows per CTA of the reductions
 constexpr int BJ_T = 512;              // threads of the block solve
 constexpr int BJ_W = 32;               // panel width of the block solve (the LU's pivot panel)
+constexpr double GM_INNER = 1e-4;      // residual reduction per cycle with the FP32 operator
 
 inline unsigned nblk(int64_t n, int t = GM_T) { return (unsigned)((n + t - 1) / t); }
 
@@ -708,6 +718,15 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
         ff_ready = true;
         return gdm_phase_end(ctx, GDM_PH_RESIDUAL);
     };
+    // the same with the FP32 operator (positions prepared by the first double-float call)
+    auto residual_fast = [&](const double2 *rhs, const double2 *X, double2 *r) -> gdm_status {
+        GDM_TRY(gdm_phase_begin(ctx, GDM_PH_RESIDUAL));
+        GDM_TRY(gdm_launch_residual_f32(ctx, &pp, (const double *)rhs, (const double *)X, nr, (double *)r, nullptr,
+                                        Pbuf, gpart, gdm_ff_positions(ffws)));
+        return gdm_phase_end(ctx, GDM_PH_RESIDUAL);
+    };
+    bool fast = !(o.flags & GDM_GMRES_EXACT_OPERATOR);
+    double prev_rel = INFINITY;
 
     // ---- FGMRES(m)
     if (info) GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
@@ -747,6 +766,9 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
             break;
         }
         if (total >= max_it) break;
+        // a cycle on the FP32 operator must at least halve the true residual
+        if (fast && !(rel_true <= 0.5 * prev_rel)) fast = false;
+        prev_rel = rel_true;
         Scales sc;
         for (int q = 0; q < GM_MAX_RHS; q++) sc.s[q] = (q < nr && beta[q] > 0) ? 1.0 / beta[q] : 0.0;
         k_gm_scale<<<nblk(vec), GM_T, 0, ctx->stream>>>(w, V, ns, nr, sc);
@@ -754,16 +776,19 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
         std::fill(H.begin(), H.end(), cd(0.0));
         std::fill(g.begin(), g.end(), cd(0.0));
         std::vector<bool> active(nr);
+        std::vector<double> target(nr);
         for (int q = 0; q < nr; q++) {
             g[(size_t)q * (m + 1)] = beta[q];
             active[q] = bn[q] > 0 && beta[q] / bn[q] > tol;
             len[q] = 0;
+            target[q] = fast ? std::max(tol * bn[q], GM_INNER * beta[q]) : tol * bn[q];
         }
         int j = 0;
         for (; j < m && total < max_it; j++) {
             double2 *Vj = V + vec * j, *Zj = Z + vec * j;
             GDM_TRY(precond(Vj, Zj));
-            GDM_TRY(residual(zero, Zj, w, nullptr));  // w = -A z_j
+            if (fast) GDM_TRY(residual_fast(zero, Zj, w));  // w = -A z_j
+            else GDM_TRY(residual(zero, Zj, w, nullptr));
             const int J = j + 1;
             const dim3 gr((unsigned)nct, (unsigned)nr);
             GDM_TRY(gdm_phase_begin(ctx, GDM_PH_OTHER));
@@ -823,7 +848,7 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
                 len[q] = j + 1;
                 const double est = std::abs(gq[j + 1]) / bn[q];
                 rel_est = std::max(rel_est, est);
-                if (est <= tol || !(hn > 1e-300 * den)) active[q] = false;
+                if (std::abs(gq[j + 1]) <= target[q] || !(hn > 1e-300 * den)) active[q] = false;
                 else any = true;
             }
             if (!any) {

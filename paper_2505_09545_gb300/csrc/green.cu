@@ -857,6 +857,64 @@ static gdm_status launch_green_sum(gdm_ctx *ctx, const double *tpos, int64_t m, 
 gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const double2 *P, int rhs0, int nr,
                                    int64_t chunk, int nchunks, void *ffws, double2 *partial, int prepare);
 
+// partial[c][q][t][3] = sum over sources j != t of chunk c of G^Ep(r_t - r_j) P_j for cells, in FP32 with the
+// double-float position differences and phase of the FP32 assembly (about 1e-7 relative per pair, some 1e-6
+// for a sum): the low-precision operator of the iterative solver, ~1/9 of the double-float kernel's work
+template <int NR>
+__global__ void __launch_bounds__(GS_T) k_green_sum_f32(const DipF *__restrict__ dip, int64_t n,
+                                                       const double2 *__restrict__ P, int rhs0, int nr_here,
+                                                       float khi, float klo, float inv_eps, int64_t chunk,
+                                                       double2 *__restrict__ partial) {
+    __shared__ DipF sj[GS_S];
+    __shared__ float2 sm[GS_S][NR][3];
+    const int64_t t = (int64_t)blockIdx.x * GS_T + threadIdx.x;
+    const bool valid = t < n;
+    const int64_t c = blockIdx.y;
+    const int64_t jb = c * chunk, je = min(n, jb + chunk);
+    const DipF ti = dip[valid ? t : 0];
+    const ff kff = {khi, klo};
+    const float k2 = khi * khi;
+    float2 acc[NR][3];
+#pragma unroll
+    for (int q = 0; q < NR; q++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) acc[q][a] = make_float2(0.f, 0.f);
+    const int64_t ld = 3 * n;
+    for (int64_t s0 = jb; s0 < je; s0 += GS_S) {
+        const int sn = (int)min((int64_t)GS_S, je - s0);
+        if (threadIdx.x < sn) sj[threadIdx.x] = dip[s0 + threadIdx.x];
+        for (int e = threadIdx.x; e < sn * 3 * NR; e += GS_T) {
+            const int jj = e / (3 * NR), rem = e % (3 * NR), q = rem / 3, a = rem % 3;
+            double2 v = make_double2(0.0, 0.0);
+            if (q < nr_here) v = P[(rhs0 + q) * ld + 3 * (s0 + jj) + a];
+            sm[jj][q][a] = make_float2((float)v.x, (float)v.y);
+        }
+        __syncthreads();
+        if (valid) {
+            for (int jj = 0; jj < sn; jj++) {
+                if (s0 + jj == t) continue;
+                const PairG<float> g = pair_green_f32(ti, sj[jj], kff, khi, k2, 0.f, inv_eps, false);
+#pragma unroll
+                for (int q = 0; q < NR; q++) {
+                    float2 y[3];
+                    apply_gep(g, sm[jj][q], y);
+#pragma unroll
+                    for (int a = 0; a < 3; a++) acc[q][a] = cadd(acc[q][a], y[a]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!valid) return;
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+        if (q >= nr_here) break;
+        double2 *o = partial + ((c * NR + q) * n + t) * 3;
+#pragma unroll
+        for (int a = 0; a < 3; a++) o[a] = make_double2((double)acc[q][a].x, (double)acc[q][a].y);
+    }
+}
+
 // residual of the FP64 system (matrix-free); scratch: P (kN x n_rhs) + partial buffer; ffws (nullable):
 // double-float workspace (gdm_ff_scratch_bytes) selecting the double-float pair kernel for cells.
 gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
@@ -894,6 +952,39 @@ gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const doub
             k_residual_finalize<6, 2><<<nb, 256, 0, ctx->stream>>>(
                 partial, nc, n, q0, nr, (const double2 *)rhs, (const double2 *)X, Pbuf, 0.0, 0, nullptr, 1.0, 0.0,
                 1.0 / p->eps_env, 1.0 / sqrt(p->eps_env), (double2 *)r, norms2);
+        GDM_LAUNCHED(ctx, "residual_finalize");
+    }
+    return GDM_OK;
+}
+
+// r = rhs - X + G P for cells with the FP32 Green sums above (the iterative solver's low-precision operator);
+// same scratch as gdm_launch_residual_ws; dipf: the FP32-pair positions of gdm_launch_green_sum_ff's
+// workspace (prepared by an earlier double-float call on the same problem)
+gdm_status gdm_launch_residual_f32(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
+                                   double *r, double *norms2, double2 *Pbuf, double2 *partial, const void *dipf) {
+    const int64_t n = p->n;
+    if (p->kind != 3) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "FP32 operator implemented for kind 3");
+    const double k0 = gdm_k0(p), k = sqrt(p->eps_env) * k0;
+    const double d3_4pi = p->step * p->step * p->step / (4.0 * PI_D);
+    const double S = -4.0 * PI_D / (3.0 * p->eps_env * p->step * p->step * p->step);
+    const float khi = (float)k, klo = (float)(k - (double)khi);
+    dim3 g1((unsigned)((n + 127) / 128), (unsigned)n_rhs);
+    k_moments<<<g1, 128, 0, ctx->stream>>>((const double2 *)X, n, 3, n_rhs, (const double2 *)p->eps, p->eps_env,
+                                            d3_4pi, nullptr, 0, Pbuf);
+    GDM_LAUNCHED(ctx, "moments");
+    if (norms2) GDM_CUDA_TRY(ctx, cudaMemsetAsync(norms2, 0, sizeof(double) * n_rhs, ctx->stream));
+    for (int q0 = 0; q0 < n_rhs; q0 += 2) {
+        const int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
+        int64_t chunk;
+        int nc;
+        green_grid(ctx, n, n, &chunk, &nc);
+        dim3 grid((unsigned)((n + GS_T - 1) / GS_T), (unsigned)nc);
+        k_green_sum_f32<2><<<grid, GS_T, 0, ctx->stream>>>((const DipF *)dipf, n, Pbuf, q0, nr, khi, klo,
+                                                          (float)(1.0 / p->eps_env), chunk, partial);
+        GDM_LAUNCHED(ctx, "green_sum_f32");
+        k_residual_finalize<3, 2><<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+            partial, nc, n, q0, nr, (const double2 *)rhs, (const double2 *)X, Pbuf, S, 0, (const double2 *)p->eps,
+            p->eps_env, d3_4pi, 1.0, 1.0, (double2 *)r, norms2);
         GDM_LAUNCHED(ctx, "residual_finalize");
     }
     return GDM_OK;

@@ -265,6 +265,13 @@ void split(double v, float *h, float *l) {
 
 size_t gdm_ff_scratch_bytes(int64_t n) { return ScratchCarver::round(n * sizeof(DipF)) + 257 * 16 + 512; }
 
+// the hi/lo FP32 position pairs (48-byte records) that gdm_launch_green_sum_ff prepares at the start of its
+// workspace; valid after a call with prepare = 1 on the same problem
+const void *gdm_ff_positions(void *ffws) {
+    ScratchCarver sc(ffws);
+    return sc.take<DipF>(0);
+}
+
 // Same output as the FP64 Green sum used by the residual (partial sums per chunk, two RHS per launch).
 gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const double2 *P, int rhs0, int nr,
                                    int64_t chunk, int nchunks, void *ffws, double2 *partial, int prepare) {

@@ -60,13 +60,14 @@ def check(G, ctx, pos, eps, step, lam, eps_env=1.0, tol_f=1e-9, **kw):
     return info
 
 
-@pytest.mark.parametrize("precision", ["tf32", "fp32"])
-def test_gmres_cuboid_matches_oracle(G, ctx, precision):
+@pytest.mark.parametrize("precision,fast", [("tf32", True), ("fp32", True), ("tf32", False)])
+def test_gmres_cuboid_matches_oracle(G, ctx, precision, fast):
     """14 x 12 x 9 cells (N = 1,512) of config-2 permittivities: blocks of 256 cells (six, the last
-    ragged), coarse cells of 8 children and, on the odd face, of 4."""
+    ragged), coarse cells of 8 children and, on the odd face, of 4; Arnoldi steps on the FP32 operator
+    (cycles refined by the double-float residual) or on the double-float operator throughout."""
     pos, eps, step = cuboid(14, 12, 9, seed=2)
-    info = check(G, ctx, pos, eps, step, 500.0, precision=precision, block_cells=256)
-    assert info["iterations"] < 80, info
+    info = check(G, ctx, pos, eps, step, 500.0, precision=precision, block_cells=256, fast_operator=fast)
+    assert info["iterations"] < 100, info
 
 
 def test_gmres_blob_matches_oracle_all_variants(G, ctx):
