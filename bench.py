@@ -26,6 +26,9 @@ sys.path.insert(0, ROOT)
 METRIC = "GDM assemble+solve s per (λ,N) vs FP64 GPU path at 1e-9 rel err; adjoint grad s"
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop/FMA x max clock
+# FP32 thread instructions per (target, source) pair, 2 right-hand sides, of the GMRES FP32 operator
+# k_green_sum_f32 (ncu count: profiles/green_sum_f32_gmres_cuboid20x15x10_ncu.md)
+FP32_OPERATOR_INST_PER_PAIR = 221.0
 
 
 def load_peaks():
@@ -525,9 +528,9 @@ def run_gmres(args):
     torch.cuda.synchronize()
     launches = (G.lib().gdm_launch_count(ctx.h) - launches0) // args.steps
     ms = e0_.elapsed_time(e1_) / args.steps
-    # operator throughput: each GMRES step (and each restart's residual) is one pass over all N^2 pairs for
-    # both right-hand sides
-    passes = info["iterations"] + max(1, (info["iterations"] + 59) // 60) + 1
+    # operator throughput: each GMRES step (FP32 operator) and each true residual (double-float operator, once
+    # per restart cycle and once more at the end) is one pass over all N^2 pairs for both right-hand sides
+    passes = info["iterations"] + info["cycles"] + 1
     # one more solve with phase accounting (CUDA events on the context stream around every operator
     # application): the operator kernel k_green_sum_ff (double-float pair sums on the FP32 pipes) against
     # the FP32 issue rate of 152 SMs x 128 lanes x 2.07 GHz; 1,406 FP32 thread instructions per
@@ -535,15 +538,26 @@ def run_gmres(args):
     ctx.phases(True)
     G.solve_gmres(ctx, prob, F0, precision=args.precision if args.precision != "fp64" else "tf32", F=F)
     ph = ctx.phases(False)
-    op_ms = ph["residual"]
-    inst_per_pair = 1406.0
+    # the dominant kernel is the FP32 operator of the Arnoldi steps (k_green_sum_f32); the double-float one
+    # (k_green_sum_ff) evaluates the true residual once per restart cycle
+    fast_ms, ff_ms = ph["operator_f32"], ph["residual"]
+    cycles = info["cycles"]
+    fast_passes = info["iterations"]
+    ff_passes = passes - fast_passes
     peak_inst = 152 * 128 * 2.07e9
-    achieved = passes * float(s.n) ** 2 * inst_per_pair / (op_ms / 1e3)
+    inst_fast = FP32_OPERATOR_INST_PER_PAIR
+    achieved = fast_passes * float(s.n) ** 2 * inst_fast / (fast_ms / 1e3) if fast_ms > 0 else 0.0
+    it_ms = fast_ms + ff_ms + ph["correction_solves"] + ph["other"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_inst, "unit": "FP32 inst/s",
-                "frac": achieved / peak_inst, "traffic": None, "kernel": "k_green_sum_ff (GMRES operator)",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock)",
-                "operator_share_of_iterations": op_ms / max(ph["residual"] + ph["correction_solves"] + ph["other"], 1e-9),
-                "phases_ms": {"operator": op_ms, "preconditioner": ph["correction_solves"], "orthogonalisation": ph["other"]}}
+                "frac": achieved / peak_inst, "traffic": None, "kernel": "k_green_sum_f32 (GMRES Arnoldi operator)",
+                "inst_per_pair": inst_fast, "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock)",
+                "share_of_iterations": fast_ms / max(it_ms, 1e-9),
+                "double_float_operator": {"passes": ff_passes, "ms": ff_ms,
+                                          "fp32_inst_per_s": ff_passes * float(s.n) ** 2 * 1406.0 / (ff_ms / 1e3)
+                                          if ff_ms > 0 else 0.0},
+                "phases_ms": {"fp32_operator": fast_ms, "double_float_operator": ff_ms,
+                              "preconditioner": ph["correction_solves"], "orthogonalisation": ph["other"]},
+                "restart_cycles": cycles}
     line = {"metric": "GMRES solve s per (lambda, N)", "value": ms / 1e3, "unit": "s", "n_gpus": 1,
             "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 operator, tf32 preconditioner", "data": "synthetic",

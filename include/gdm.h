@@ -115,7 +115,8 @@ typedef struct {
     double refine_ms;            /* device time of solves + refinement */
     double pivot_growth;         /* largest |entry below| / |pivot| seen by the panels (<= 1: partial pivoting) */
     int32_t refactored;          /* 1 if the factorisation was redone with whole-column pivoting */
-    int32_t reserved;
+    int32_t cycles;              /* gdm_solve_gmres: restart cycles (the true residual is evaluated
+                                    cycles + 1 times); 0 for the direct solves */
 } gdm_solve_info;
 
 /* ---------------------------------------------------------------- context */
@@ -456,10 +457,12 @@ gdm_status gdm_profile_enable(gdm_ctx *ctx, int enable);
 gdm_status gdm_profile_read(gdm_ctx *ctx, int64_t *launches, double *total_ms, double *flops, double *bytes);
 
 /* Phase accounting: with enable = 1 subsequent calls record device time per phase of the solve
- * (CUDA events around each phase; adds host overhead, for diagnostics only). ms_out (host, 9 doubles,
+ * (CUDA events around each phase; adds host overhead, for diagnostics only). ms_out (host, 10 doubles,
  * nullable) receives the times recorded since the previous call, in the order: panel factorisation,
  * row interchanges, small triangular solves, in-block updates, U12 updates, trailing update,
- * correction solves, refinement residual, other. Synchronises the stream when ms_out != NULL. */
+ * correction solves (gdm_solve_gmres: its preconditioner), refinement residual (double-float
+ * operator), other (gdm_solve_gmres: orthogonalisation), FP32 operator of gdm_solve_gmres.
+ * Synchronises the stream when ms_out != NULL. */
 gdm_status gdm_profile_phases(gdm_ctx *ctx, int enable, double *ms_out);
 
 #ifdef __cplusplus

@@ -71,7 +71,7 @@ GMRES_EXACT_OPERATOR = 4
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("rel_correction", C.c_double),
                 ("rel_residual", C.c_double), ("factor_ms", C.c_double), ("refine_ms", C.c_double),
-                ("pivot_growth", C.c_double), ("refactored", C.c_int32), ("reserved", C.c_int32)]
+                ("pivot_growth", C.c_double), ("refactored", C.c_int32), ("cycles", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -123,7 +123,7 @@ _SIGS = {
     "gdm_profile_phases": ([P, C.c_int, PD], C.c_int),
 }
 PHASES = ["panel", "laswp", "trsm_small", "inblock_update", "u12_update", "trailing_update", "correction_solves",
-          "residual", "other"]
+          "residual", "other", "operator_f32"]
 
 
 def lib():

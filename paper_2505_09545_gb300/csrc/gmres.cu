@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(BJ_T) k_bj_solve(const float2 *__restrict__ fa
     __syncthreads();
     // the panel's 32 x 32 diagonal block, staged so that the warp-serial solve reads shared memory only
     __shared__ float2 D[BJ_W][BJ_W + 1];
+    __shared__ int spiv[BJ_W];  // the panel's row interchanges
     // y[r] -= sum_{i < w} A[r, c0 + i] y[c0 + i] for the rows r of [rb, re) (8 independent loads in flight)
     auto update = [&](int c0, int w, int rb, int re) {
         for (int r = rb + tid; r < re; r += BJ_T) {
@@ -241,15 +242,17 @@ __global__ void __launch_bounds__(BJ_T) k_bj_solve(const float2 *__restrict__ fa
             const int r = e % BJ_W, c = e / BJ_W;
             D[r][c] = (r < w && c < w) ? A[(c0 + c) * ld + c0 + r] : make_float2(0.f, 0.f);
         }
+        if (tid < w) spiv[tid] = ip[c0 + tid];
     };
     // forward: P, then L^-1 (unit diagonal), panel by panel
     for (int c0 = 0; c0 < m; c0 += BJ_W) {
         const int w = min(BJ_W, m - c0);
         stage_diag(c0, w);
+        __syncthreads();
         if (tid < nr) {
             float2 *y = ysm + tid * m;
             for (int k = 0; k < w; k++) {
-                const int r1 = c0 + k, r2 = ip[r1];
+                const int r1 = c0 + k, r2 = spiv[k];
                 if (r2 != r1) {
                     const float2 t = y[r1];
                     y[r1] = y[r2];
@@ -720,10 +723,10 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
     };
     // the same with the FP32 operator (positions prepared by the first double-float call)
     auto residual_fast = [&](const double2 *rhs, const double2 *X, double2 *r) -> gdm_status {
-        GDM_TRY(gdm_phase_begin(ctx, GDM_PH_RESIDUAL));
+        GDM_TRY(gdm_phase_begin(ctx, GDM_PH_OPERATOR_F32));
         GDM_TRY(gdm_launch_residual_f32(ctx, &pp, (const double *)rhs, (const double *)X, nr, (double *)r, nullptr,
                                         Pbuf, gpart, gdm_ff_positions(ffws)));
-        return gdm_phase_end(ctx, GDM_PH_RESIDUAL);
+        return gdm_phase_end(ctx, GDM_PH_OPERATOR_F32);
     };
     bool fast = !(o.flags & GDM_GMRES_EXACT_OPERATOR);
     double prev_rel = INFINITY;
@@ -738,7 +741,7 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
     std::vector<cd> H((size_t)nr * (m + 1) * m), g((size_t)nr * (m + 1)), cs((size_t)nr * m), sn((size_t)nr * m);
     std::vector<double> bn(nr, 0.0);
     std::vector<int> len(nr);
-    int total = 0;
+    int total = 0, cycles = 0;
     double rel_true = INFINITY, rel_est = INFINITY;
     bool converged = false;
     while (true) {
@@ -784,6 +787,7 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
             target[q] = fast ? std::max(tol * bn[q], GM_INNER * beta[q]) : tol * bn[q];
         }
         int j = 0;
+        cycles++;
         for (; j < m && total < max_it; j++) {
             double2 *Vj = V + vec * j, *Zj = Z + vec * j;
             GDM_TRY(precond(Vj, Zj));
@@ -899,6 +903,7 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
         info->refine_ms = it_ms;
         info->pivot_growth = growth_max;
         info->refactored = refactored;
+        info->cycles = cycles;
     }
     if (dev != GDM_OK) return dev;
     if (!converged)
