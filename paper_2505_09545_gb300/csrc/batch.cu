@@ -17,12 +17,12 @@
 #include <vector>
 
 #include "gdm_internal.cuh"
+#include "pool.cuh"
 
 #define PI_D 3.14159265358979323846
 
-namespace {
-
-gdm_status ensure_pool(gdm_ctx *ctx, int want) {
+// child contexts of the pool runner (pool.cuh), created on first use and owned by the context
+gdm_status gdm_ensure_pool(gdm_ctx *ctx, int want) {
     while (ctx->npool < want) {
         cudaStream_t st = nullptr;
         GDM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -30,13 +30,16 @@ gdm_status ensure_pool(gdm_ctx *ctx, int want) {
         gdm_status s = gdm_create(&c, ctx->device, st);
         if (s != GDM_OK) {
             cudaStreamDestroy(st);
-            return gdm_fail(ctx, s, "could not create a child context for the batch");
+            return gdm_fail(ctx, s, "could not create a child context for the pool");
         }
         c->owns_stream = true;
         ctx->pool[ctx->npool++] = c;
     }
     return GDM_OK;
 }
+
+
+namespace {
 
 // the full per-item path on one child context
 gdm_status run_item(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it, const gdm_solve_opts *opts,
@@ -66,82 +69,6 @@ gdm_status run_item(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it, co
         GDM_TRY(gdm_launch_cross_sections(c, p, it->F0, it->F, it->n_rhs, e2, it->sigma, it->sigma + it->n_rhs,
                                           it->sigma + 2 * it->n_rhs));
     }
-    return GDM_OK;
-}
-
-bool per_item_numeric(gdm_status s) {
-    return s == GDM_ERR_NOT_CONVERGED || s == GDM_ERR_NONFINITE || s == GDM_ERR_SINGULAR;
-}
-
-// Runs fn(child, item, info) for every item on up to n_streams child contexts, largest first. The pool
-// starts after the work queued on the caller's stream; once the children have finished and the caller's
-// stream waits for them, after(ctx, children used, after_arg) may queue follow-up work on that stream.
-// Numerical failures stay with their item; any other error stops the remaining items.
-template <class Fn>
-gdm_status run_pool(gdm_ctx *ctx, int n_items, const int64_t *size, int n_streams, gdm_solve_info *infos, Fn fn,
-                    gdm_status (*after)(gdm_ctx *, int, void *), void *after_arg = nullptr) {
-    int ns = n_streams > 0 ? n_streams : 8;
-    if (ns > GDM_POOL_MAX) ns = GDM_POOL_MAX;
-    if (ns > n_items) ns = n_items;
-    GDM_TRY(ensure_pool(ctx, ns));
-    std::vector<int> order(n_items);
-    for (int i = 0; i < n_items; i++) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return size[a] > size[b]; });
-    std::vector<gdm_solve_info> local((size_t)n_items);
-    gdm_solve_info *inf = infos ? infos : local.data();
-    memset(inf, 0, sizeof(gdm_solve_info) * (size_t)n_items);
-
-    GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, ctx->stream));
-    int64_t launches0[GDM_POOL_MAX];
-    for (int w = 0; w < ns; w++) {
-        gdm_ctx *c = ctx->pool[w];
-        memcpy(c->nb_table, ctx->nb_table, sizeof(ctx->nb_table));
-        c->err[0] = 0;
-        launches0[w] = c->launches;
-        GDM_CUDA_TRY(ctx, cudaStreamWaitEvent(c->stream, ctx->ev2, 0));
-    }
-    std::atomic<int> next(0);
-    std::atomic<bool> stop(false);
-    std::mutex mu;
-    gdm_status first = GDM_OK;
-    int first_item = -1;
-    char first_msg[sizeof(ctx->err)] = {0};
-    auto worker = [&](int w) {
-        gdm_ctx *c = ctx->pool[w];
-        if (cudaSetDevice(ctx->device) != cudaSuccess) {
-            stop = true;
-            return;
-        }
-        for (;;) {
-            if (stop.load()) break;
-            const int k = next.fetch_add(1);
-            if (k >= n_items) break;
-            const int i = order[k];
-            gdm_status s = fn(c, w, i, &inf[i]);
-            inf[i].status = s;
-            if (s != GDM_OK) {
-                std::lock_guard<std::mutex> lock(mu);
-                if (first == GDM_OK || (per_item_numeric(first) && !per_item_numeric(s))) {
-                    first = s;
-                    first_item = i;
-                    memcpy(first_msg, c->err, sizeof(first_msg));
-                }
-                if (!per_item_numeric(s)) stop = true;
-            }
-        }
-    };
-    std::vector<std::thread> threads;
-    threads.reserve(ns);
-    for (int w = 0; w < ns; w++) threads.emplace_back(worker, w);
-    for (auto &t : threads) t.join();
-    for (int w = 0; w < ns; w++) {
-        gdm_ctx *c = ctx->pool[w];
-        ctx->launches += c->launches - launches0[w];
-        GDM_CUDA_TRY(ctx, cudaEventRecord(c->ev2, c->stream));
-        GDM_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, c->ev2, 0));
-    }
-    if (after) GDM_TRY(after(ctx, ns, after_arg));
-    if (first != GDM_OK) return gdm_fail(ctx, first, "item %d: %s", first_item, first_msg);
     return GDM_OK;
 }
 
@@ -194,7 +121,7 @@ gdm_status gdm_solve_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_i
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     std::vector<int64_t> size((size_t)n_items);
     for (int i = 0; i < n_items; i++) size[i] = items[i].prob.n * items[i].prob.kind;
-    return run_pool(ctx, n_items, size.data(), n_streams, infos,
+    return gdm_run_pool(ctx, n_items, size.data(), n_streams, infos,
                     [&](gdm_ctx *c, int, int i, gdm_solve_info *inf) { return run_item(c, prec, &items[i], opts, inf); },
                     nullptr);
 }
@@ -231,7 +158,7 @@ gdm_status gdm_backward_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_back
     std::vector<int64_t> size((size_t)n_items, n);
     static const double zhat[3] = {0.0, 0.0, 1.0};
     BackwardSum bs = {acc, n, grad_pos, grad_eps};
-    gdm_status st = run_pool(
+    gdm_status st = gdm_run_pool(
         ctx, n_items, size.data(), ns, infos,
         [&](gdm_ctx *c, int w, int i, gdm_solve_info *inf) {
             const gdm_backward_item *it = &items[i];

@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "gdm_internal.cuh"
+#include "pool.cuh"
 
 gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
                                   int adjoint, double *r, double *norms2, double2 *Pbuf, double2 *partial, void *ffws,
@@ -638,46 +639,67 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
     pp.eps = (const double *)eps_p;
     double growth_max = 0.0;
     int refactored = 0;
-    auto assemble = [&](const gdm_problem *q, float2 *A, int64_t ld, bool coarse) -> gdm_status {
-        GDM_TRY(gdm_launch_assemble(ctx, q, prec, A, ld));
+    // The coarse model and the blocks are independent factorisations of latency-bound size: they run
+    // concurrently on the context's pool of child contexts (item 0 = the coarse model when used, then the
+    // blocks, largest first), each child on its own stream and scratch.
+    auto assemble_on = [&](gdm_ctx *c, const gdm_problem *q, float2 *A, int64_t ld, bool coarse) -> gdm_status {
+        GDM_TRY(gdm_launch_assemble(c, q, prec, A, ld));
         if (coarse) {
-            k_coarse_diag<<<nblk(nc3), GM_T, 0, ctx->stream>>>(A, ld, chi_c, nc, 1.0 / (3.0 * p->eps_env));
-            GDM_LAUNCHED(ctx, "gmres_coarse_diag");
+            k_coarse_diag<<<nblk(nc3), GM_T, 0, c->stream>>>(A, ld, chi_c, nc, 1.0 / (3.0 * p->eps_env));
+            GDM_LAUNCHED(c, "gmres_coarse_diag");
         }
         return GDM_OK;
     };
-    auto factor = [&](const gdm_problem *q, float2 *A, int64_t mq, int64_t ld, int32_t *ipq,
-                      bool coarse) -> gdm_status {
+    auto factor_on = [&](gdm_ctx *c, const gdm_problem *q, float2 *A, int64_t mq, int64_t ld, int32_t *ipq,
+                         bool coarse, gdm_solve_info *inf) -> gdm_status {
         float growth = 1.f;
-        GDM_TRY(assemble(q, A, ld, coarse));
-        GDM_TRY(gdm_lu_factor(ctx, prec, A, mq, ld, ipq, 0, &growth));
+        GDM_TRY(assemble_on(c, q, A, ld, coarse));
+        GDM_TRY(gdm_lu_factor(c, prec, A, mq, ld, ipq, 0, &growth));
         if (!(growth <= (float)GDM_PIVOT_GROWTH_LIMIT)) {
-            GDM_TRY(assemble(q, A, ld, coarse));
-            GDM_TRY(gdm_lu_factor(ctx, prec, A, mq, ld, ipq, 1, &growth));
-            refactored++;
+            GDM_TRY(assemble_on(c, q, A, ld, coarse));
+            GDM_TRY(gdm_lu_factor(c, prec, A, mq, ld, ipq, 1, &growth));
+            inf->refactored = 1;
         }
-        growth_max = std::max(growth_max, (double)growth);
-        return GDM_OK;
+        inf->pivot_growth = growth;
+        return gdm_ctx_check(c);
     };
+    gdm_problem pc = *p;
+    pc.n = nc;
+    pc.pos = pos_c;
+    pc.eps = (const double *)eps_c;
+    pc.step = 2.0 * p->step;
+    const int c0i = use_coarse ? 1 : 0;
+    const int n_items = c0i + (use_blocks ? nb : 0);
+    if (n_items > 0) {
+        std::vector<int64_t> isize(n_items);
+        if (use_coarse) isize[0] = nc3;
+        for (int i = c0i; i < n_items; i++) isize[i] = 3 * (int64_t)(part.boff[i - c0i + 1] - part.boff[i - c0i]);
+        std::vector<gdm_solve_info> iinfo(n_items);
+        GDM_TRY(gdm_run_pool(
+            ctx, n_items, isize.data(), 8, iinfo.data(),
+            [&](gdm_ctx *c, int, int i, gdm_solve_info *inf) -> gdm_status {
+                gdm_params_reset(c);
+                if (i < c0i) return factor_on(c, &pc, Ac, nc3, lda_c, piv_c, true, inf);
+                const int b = i - c0i;
+                gdm_problem pb = pp;
+                pb.n = part.boff[b + 1] - part.boff[b];
+                pb.pos = pos_p + 3 * (int64_t)part.boff[b];
+                pb.eps = (const double *)(eps_p + part.boff[b]);
+                return factor_on(c, &pb, fac + fac_off[b], 3 * pb.n, fac_ld[b], piv + 3 * (int64_t)part.boff[b],
+                                 false, inf);
+            },
+            nullptr));
+        for (const gdm_solve_info &x : iinfo) {
+            growth_max = std::max(growth_max, x.pivot_growth);
+            refactored += x.refactored;
+        }
+    }
     int coarse_local = 0;
     if (use_coarse) {
-        gdm_problem pc = *p;
-        pc.n = nc;
-        pc.pos = pos_c;
-        pc.eps = (const double *)eps_c;
-        pc.step = 2.0 * p->step;
-        GDM_TRY(factor(&pc, Ac, nc3, lda_c, piv_c, true));
         GDM_TRY(gdm_pivots_local(ctx, piv_c, nc3, 32, tsync, &coarse_local));
         if (coarse_local) GDM_TRY(gdm_trsv_prepare(ctx, prec, Ac, nc3, lda_c, piv_c, dinv));
     }
     if (use_blocks) {
-        for (int b = 0; b < nb; b++) {
-            gdm_problem pb = pp;
-            pb.n = part.boff[b + 1] - part.boff[b];
-            pb.pos = pos_p + 3 * (int64_t)part.boff[b];
-            pb.eps = (const double *)(eps_p + part.boff[b]);
-            GDM_TRY(factor(&pb, fac + fac_off[b], 3 * pb.n, fac_ld[b], piv + 3 * (int64_t)part.boff[b], false));
-        }
         const int smem = (int)(sizeof(float2) * (size_t)max_m * nr);
         GDM_TRY(launch_bj_nr(ctx, nr, nb, smem, fac, d_foff, d_fld, piv, d_boff, nullptr, ns, d_parent, rc, yc, nc3,
                              0, nullptr, true));
