@@ -78,7 +78,10 @@ __device__ __forceinline__ ff ff_diff(float xh, float xl, float yh, float yl) {
 #define INV_TWO_PI_F 0.15915494309189535f
 
 // e^{i x} for a double-float phase x >= 0 (|x| < 2.5e4): reduce to [-pi, pi] keeping the low part,
-// then FP32 sincos of the high part with a first-order correction for the low part.
+// then FP32 sincos of the high part with a first-order correction for the low part. FAST: the hardware
+// sine/cosine approximations for the reduced argument (absolute error about 4e-7 on [-pi, pi]), for the
+// iterative solver's low-precision operator only.
+template <bool FAST = false>
 __device__ __forceinline__ float2 ff_expi(ff x) {
     float n = rintf(x.hi * INV_TWO_PI_F);
     float t1 = fmaf(-n, TWO_PI_C1, x.hi);  // exact
@@ -86,7 +89,8 @@ __device__ __forceinline__ float2 ff_expi(ff x) {
     float lo = fmaf(-n, TWO_PI_C3, __fadd_rn(s.lo, x.lo));
     ff th = fast_two_sum(s.hi, lo);
     float sn, cs;
-    sincosf(th.hi, &sn, &cs);
+    if (FAST) __sincosf(th.hi, &sn, &cs);
+    else sincosf(th.hi, &sn, &cs);
     return make_float2(fmaf(-sn, th.lo, cs), fmaf(cs, th.lo, sn));
 }
 
@@ -270,16 +274,33 @@ template <class T> struct PairG {
 
 // FP32 with a double-float phase: the phase k R needs ~1e-9 absolute accuracy for kR up to ~1e3,
 // the amplitudes 1/R^n only FP32 relative accuracy.
+// FAST (the iterative solver's FP32 operator): R and 1/R from one hardware reciprocal square root refined
+// by a Newton step (1/R to ~1e-7, R to double-float through the usual correction term), and the hardware
+// sine/cosine in the phase; about 4e-7 on e^{ikR} instead of ~1e-7, well inside that operator's 1e-6.
+template <bool FAST = false>
 __device__ __forceinline__ PairG<float> pair_green_f32(const DipF &ti, const DipF &sj, ff kff, float kf, float k2,
                                                        float k0k, float inv_eps, bool need_c) {
     ff dx = ff_diff(ti.xh, ti.xl, sj.xh, sj.xl);
     ff dy = ff_diff(ti.yh, ti.yl, sj.yh, sj.yl);
     ff dz = ff_diff(ti.zh, ti.zl, sj.zh, sj.zl);
     ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
-    ff r = ff_sqrt(r2);
-    float r1 = 1.0f / r.hi;
+    ff r;
+    float r1;
+    if (FAST) {
+        float y = rsqrtf(r2.hi);
+        y = y * fmaf(-0.5f * r2.hi * y, y, 1.5f);
+        const float h = r2.hi * y;
+        const float p = __fmul_rn(h, h);
+        const float ep = fmaf(h, h, -p);
+        const float res = __fadd_rn(__fsub_rn(__fsub_rn(r2.hi, p), ep), r2.lo);
+        r = fast_two_sum(h, res * (0.5f * y));
+        r1 = y;
+    } else {
+        r = ff_sqrt(r2);
+        r1 = 1.0f / r.hi;
+    }
     float r2i = r1 * r1, r3i = r2i * r1;
-    float2 e = ff_expi(ff_mul(kff, r));
+    float2 e = ff_expi<FAST>(ff_mul(kff, r));
     PairG<float> g;
     if (need_c) g.c = cmul(e, make_float2(k0k * r1, k0k * r2i / kf));
     e = cscale(e, inv_eps);
@@ -893,7 +914,7 @@ __global__ void __launch_bounds__(GS_T) k_green_sum_f32(const DipF *__restrict__
         if (valid) {
             for (int jj = 0; jj < sn; jj++) {
                 if (s0 + jj == t) continue;
-                const PairG<float> g = pair_green_f32(ti, sj[jj], kff, khi, k2, 0.f, inv_eps, false);
+                const PairG<float> g = pair_green_f32<true>(ti, sj[jj], kff, khi, k2, 0.f, inv_eps, false);
 #pragma unroll
                 for (int q = 0; q < NR; q++) {
                     float2 y[3];
