@@ -28,7 +28,7 @@ NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop/FMA x max clock
 # FP32 thread instructions per (target, source) pair, 2 right-hand sides, of the GMRES FP32 operator
 # k_green_sum_f32 (ncu count: profiles/green_sum_f32_gmres_cuboid20x15x10_ncu.md)
-FP32_OPERATOR_INST_PER_PAIR = 221.0
+FP32_OPERATOR_INST_PER_PAIR = 204.0
 
 
 def load_peaks():
