@@ -95,6 +95,32 @@ def test_gmres_small_and_single_block(G, ctx):
     check(G, ctx, np.zeros((1, 3)), np.array([9.0 + 0.5j]), 10.0, 480.0)
 
 
+@pytest.mark.parametrize("n_rhs,block_cells", [(3, 300), (8, 1024)])
+def test_gmres_many_rhs_and_largest_blocks(G, ctx, n_rhs, block_cells):
+    """Right-hand sides in lockstep (an odd count; the maximum of 8 with the largest blocks, whose block
+    solve keeps 3,072 rows x 8 right-hand sides in shared memory): plane waves along seeded directions
+    with seeded polarisations, each against the oracle's dense solve."""
+    pos, eps, step = blob(1300, seed=17)
+    lam = 540.0
+    rng = np.random.default_rng(n_rhs)
+    prob = G.GDMProblem(t(pos), lam, 3, eps=t(eps), step=step)
+    pr = O.Problem(pos, lam, 3, eps=eps, step=step)
+    F0s, F0o = [], []
+    for q in range(n_rhs):
+        kh = rng.standard_normal(3)
+        kh /= np.linalg.norm(kh)
+        e0 = np.cross(kh, rng.standard_normal(3)).astype(complex)
+        e0 /= np.linalg.norm(e0)
+        F0s.append(G.incident_planewave(ctx, prob.pos, lam, e0[None, :], khat=tuple(kh)))
+        F0o.append(pr.plane_wave(e0[None, :], khat=kh))
+    F0 = torch.cat(F0s, 0)
+    F, info = G.solve_gmres(ctx, prob, F0, block_cells=block_cells)
+    Fo = pr.solve(np.concatenate(F0o, axis=1))
+    err = np.linalg.norm(F.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+    assert np.all(err < 1e-9), (err, info)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-12, info
+
+
 def test_gmres_large_sampled_residual(G, ctx):
     """24,000 cells (3N = 72,000, beyond the dense tests): the oracle's exact residual rows on 48 seeded
     cells relative to |F0| there, at the solver's tolerance."""
