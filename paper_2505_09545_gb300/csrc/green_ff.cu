@@ -272,6 +272,27 @@ const void *gdm_ff_positions(void *ffws) {
     return sc.take<DipF>(0);
 }
 
+// fill the workspace for the problem: FP32-pair positions and the (cos, sin) table of the phase reduction
+gdm_status gdm_ff_prepare(gdm_ctx *ctx, const gdm_problem *p, void *ffws) {
+    const int64_t n = p->n;
+    ScratchCarver sc(ffws);
+    DipF *dip = sc.take<DipF>(n);
+    float4 *tab = sc.take<float4>(257);
+    k_prep_dipf_pos<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(p->pos, n, dip);
+    GDM_LAUNCHED(ctx, "prep_dipf_pos");
+    float4 h[257];
+    for (int i = -128; i <= 128; i++) {
+        double a = i * (3.14159265358979323846 / 128.0);
+        float ch, cl, sh, sl;
+        split(cos(a), &ch, &cl);
+        split(sin(a), &sh, &sl);
+        h[i + 128] = make_float4(ch, cl, sh, sl);
+    }
+    GDM_CUDA_TRY(ctx, cudaMemcpyAsync(tab, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+    GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // h is a stack array
+    return GDM_OK;
+}
+
 // Same output as the FP64 Green sum used by the residual (partial sums per chunk, two RHS per launch).
 gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const double2 *P, int rhs0, int nr,
                                    int64_t chunk, int nchunks, void *ffws, double2 *partial, int prepare) {
@@ -279,20 +300,7 @@ gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const dou
     ScratchCarver sc(ffws);
     DipF *dip = sc.take<DipF>(n);
     float4 *tab = sc.take<float4>(257);
-    if (prepare) {
-        k_prep_dipf_pos<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(p->pos, n, dip);
-        GDM_LAUNCHED(ctx, "prep_dipf_pos");
-        float4 h[257];
-        for (int i = -128; i <= 128; i++) {
-            double a = i * (3.14159265358979323846 / 128.0);
-            float ch, cl, sh, sl;
-            split(cos(a), &ch, &cl);
-            split(sin(a), &sh, &sl);
-            h[i + 128] = make_float4(ch, cl, sh, sl);
-        }
-        GDM_CUDA_TRY(ctx, cudaMemcpyAsync(tab, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
-        GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // h is a stack array
-    }
+    if (prepare) GDM_TRY(gdm_ff_prepare(ctx, p, ffws));
     const double k = sqrt(p->eps_env) * gdm_k0(p);
     float khi, klo, k2hi, k2lo, iehi, ielo;
     split(k, &khi, &klo);

@@ -6,6 +6,11 @@
 //   X = X + d            (FP64)
 // until max_q ||d_q|| / ||X_q|| <= tol. The adjoint variant solves A^H X = b with the same factors
 // (conjugate-transposed triangular solves) and the matrix-free residual b - A^H X.
+// For cells (forward solves with TF32 factors) the residuals of the first steps, while the last relative
+// correction is above 1e-3, use FP32 Green sums (double-float phase, ~1e-6 relative, ~1/6 of the double-float work): the
+// correction they yield is then accurate to ~1e-2 relative, below the factorisation's own contraction
+// (~0.03 per step), so they cost no extra step; every later residual, which decides the accuracy and the
+// stop, is double-float.
 #include <math.h>
 #include <stdlib.h>
 
@@ -16,6 +21,10 @@ gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const doub
                                   int ff_prepare);
 size_t gdm_ff_scratch_bytes(int64_t n);
 size_t gdm_green_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n, int out);
+gdm_status gdm_ff_prepare(gdm_ctx *ctx, const gdm_problem *p, void *ffws);
+const void *gdm_ff_positions(void *ffws);
+gdm_status gdm_launch_residual_f32(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
+                                   double *r, double *norms2, double2 *Pbuf, double2 *partial, const void *dipf);
 
 template <class C>
 __global__ void k_to_work(const double2 *__restrict__ src, C *__restrict__ dst, int64_t count, double scale) {
@@ -110,6 +119,10 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
                                                                                : nullptr;
     double *hn;
     GDM_TRY(gdm_pinned(ctx, sizeof(double) * 4 * n_rhs, (void **)&hn));
+    // TF32 factors only: their first solution is off by ~1e-2; FP32 (3-product) and FP64 factors start
+    // closer than the FP32 residual resolves
+    const bool fast_ok = ffws && p->kind == 3 && !adjoint && prec == GDM_TF32_REFINE && !getenv("GDM_REFINE_EXACT");
+    bool ff_prepared = false;
     const unsigned nb = (unsigned)((ns + 255) / 256);
     const dim3 gq(nb, (unsigned)n_rhs);
     // ||b||^2 for the relative residual
@@ -140,8 +153,16 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
         for (it = 1; it <= opts->max_iter; it++) {
             GDM_CUDA_TRY(ctx, cudaMemsetAsync(dnorm, 0, sizeof(double) * 3 * n_rhs, ctx->stream));
             GDM_TRY(gdm_phase_begin(ctx, GDM_PH_RESIDUAL));
-            GDM_TRY(gdm_launch_residual_ws(ctx, p, rhs, X, n_rhs, adjoint, (double *)r, dnorm + 2 * n_rhs, Pbuf,
-                                           partial, ffws, it == 1));
+            if (fast_ok && relc > 1e-3) {
+                if (!ff_prepared) GDM_TRY(gdm_ff_prepare(ctx, p, ffws));
+                ff_prepared = true;
+                GDM_TRY(gdm_launch_residual_f32(ctx, p, rhs, X, n_rhs, (double *)r, dnorm + 2 * n_rhs, Pbuf, partial,
+                                                gdm_ff_positions(ffws)));
+            } else {
+                GDM_TRY(gdm_launch_residual_ws(ctx, p, rhs, X, n_rhs, adjoint, (double *)r, dnorm + 2 * n_rhs, Pbuf,
+                                               partial, ffws, ffws && !ff_prepared));
+                ff_prepared = ffws != nullptr;
+            }
             GDM_TRY(gdm_phase_end(ctx, GDM_PH_RESIDUAL));
             // scale the residual into a safe FP32 range before the low-precision solve
             k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(r, w, cnt, 1.0);
