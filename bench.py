@@ -528,9 +528,10 @@ def run_gmres(args):
     torch.cuda.synchronize()
     launches = (G.lib().gdm_launch_count(ctx.h) - launches0) // args.steps
     ms = e0_.elapsed_time(e1_) / args.steps
-    # operator throughput: each GMRES step (FP32 operator) and each true residual (double-float operator, once
-    # per restart cycle and once more at the end) is one pass over all N^2 pairs for both right-hand sides
-    passes = info["iterations"] + info["cycles"] + 1
+    # operator throughput: each GMRES step (FP32 operator) and each true residual (double-float operator, at
+    # the start of every restart cycle but the first, whose iterate is 0, and once at the end) is one pass over
+    # all N^2 pairs for both right-hand sides
+    passes = info["iterations"] + info["cycles"]
     # one more solve with phase accounting (CUDA events on the context stream around every operator
     # application): the operator kernel k_green_sum_ff (double-float pair sums on the FP32 pipes) against
     # the FP32 issue rate of 152 SMs x 128 lanes x 2.07 GHz; 1,406 FP32 thread instructions per

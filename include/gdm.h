@@ -115,8 +115,9 @@ typedef struct {
     double refine_ms;            /* device time of solves + refinement */
     double pivot_growth;         /* largest |entry below| / |pivot| seen by the panels (<= 1: partial pivoting) */
     int32_t refactored;          /* 1 if the factorisation was redone with whole-column pivoting */
-    int32_t cycles;              /* gdm_solve_gmres: restart cycles (the true residual is evaluated
-                                    cycles + 1 times); 0 for the direct solves */
+    int32_t cycles;              /* gdm_solve_gmres: restart cycles (the double-float true residual is
+                                    evaluated cycles times: before every cycle but the first, whose
+                                    iterate is 0, and at the end); 0 for the direct solves */
 } gdm_solve_info;
 
 /* ---------------------------------------------------------------- context */

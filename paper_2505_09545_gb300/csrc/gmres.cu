@@ -51,6 +51,7 @@ size_t gdm_green_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n, int out);
 gdm_status gdm_launch_residual_f32(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
                                    double *r, double *norms2, double2 *Pbuf, double2 *partial, const void *dipf);
 const void *gdm_ff_positions(void *ffws);
+gdm_status gdm_ff_prepare(gdm_ctx *ctx, const gdm_problem *p, void *ffws);
 
 namespace {
 
@@ -217,18 +218,18 @@ __global__ void __launch_bounds__(BJ_T) k_bj_solve(const float2 *__restrict__ fa
     // the panel's 32 x 32 diagonal block, staged so that the warp-serial solve reads shared memory only
     __shared__ float2 D[BJ_W][BJ_W + 1];
     __shared__ int spiv[BJ_W];  // the panel's row interchanges
-    // y[r] -= sum_{i < w} A[r, c0 + i] y[c0 + i] for the rows r of [rb, re) (8 independent loads in flight)
+    // y[r] -= sum_{i < w} A[r, c0 + i] y[c0 + i] for the rows r of [rb, re) (16 independent loads in flight)
     auto update = [&](int c0, int w, int rb, int re) {
         for (int r = rb + tid; r < re; r += BJ_T) {
             float2 acc[NR];
 #pragma unroll
             for (int q = 0; q < NR; q++) acc[q] = make_float2(0.f, 0.f);
-            for (int i0 = 0; i0 < w; i0 += 8) {
-                float2 a[8];
+            for (int i0 = 0; i0 < w; i0 += 16) {
+                float2 a[16];
 #pragma unroll
-                for (int k = 0; k < 8; k++) a[k] = i0 + k < w ? A[(c0 + i0 + k) * ld + r] : make_float2(0.f, 0.f);
+                for (int k = 0; k < 16; k++) a[k] = i0 + k < w ? A[(c0 + i0 + k) * ld + r] : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int k = 0; k < 8; k++)
+                for (int k = 0; k < 16; k++)
                     if (i0 + k < w) {
 #pragma unroll
                         for (int q = 0; q < NR; q++) cfma(acc[q], a[k], ysm[q * m + c0 + i0 + k]);
@@ -767,9 +768,19 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
     double rel_true = INFINITY, rel_est = INFINITY;
     bool converged = false;
     while (true) {
-        // true residual of the current iterate
-        GDM_CUDA_TRY(ctx, cudaMemsetAsync(bnorm2, 0, sizeof(double) * nr, ctx->stream));
-        GDM_TRY(residual(bp, x, w, bnorm2));
+        // true residual of the current iterate (the first iterate is 0: its residual is F0 itself)
+        if (total == 0) {
+            GDM_CUDA_TRY(ctx, cudaMemcpyAsync(w, bp, sizeof(double2) * vec, cudaMemcpyDeviceToDevice, ctx->stream));
+            k_gm_orth<<<dim3((unsigned)nct, (unsigned)nr), GM_T, 0, ctx->stream>>>(V, ns, nr, 0, h1, w, npart);
+            GDM_LAUNCHED(ctx, "gmres_orth");
+            k_gm_norm_final<<<nr, 32, 0, ctx->stream>>>(npart, nct, bnorm2);
+            GDM_LAUNCHED(ctx, "gmres_norm_final");
+            if (!ff_ready) GDM_TRY(gdm_ff_prepare(ctx, &pp, ffws));
+            ff_ready = true;
+        } else {
+            GDM_CUDA_TRY(ctx, cudaMemsetAsync(bnorm2, 0, sizeof(double) * nr, ctx->stream));
+            GDM_TRY(residual(bp, x, w, bnorm2));
+        }
         GDM_CUDA_TRY(ctx, cudaMemcpyAsync(hb2, bnorm2, sizeof(double) * nr, cudaMemcpyDeviceToHost, ctx->stream));
         GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         std::vector<double> beta(nr);
