@@ -311,6 +311,17 @@ typedef struct {
 gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, const double *F0, double *F,
                            int n_rhs, const gdm_gmres_opts *opts, gdm_solve_info *info);
 
+/* The host-side grouping gdm_solve_gmres applies (exposed for inspection and tests; host memory only,
+ * no context, no GPU). Cells are put on the cubic lattice of step `step` (coordinates rounded relative
+ * to the minimum corner) and sorted by the 3D Morton key of their lattice indices. perm (n int32):
+ * permuted position -> original cell. parent (n int32): permuted cell -> coarse cell, the coarse cells
+ * being the 2 x 2 x 2 lattice cubes in the same order; coarse_offsets (n + 1 int32, first *n_coarse + 1
+ * used): first permuted cell of every coarse cell, then n. The block-Jacobi blocks are the runs
+ * [b block_cells, (b + 1) block_cells) of the permuted order. GDM_ERR_INVALID_ARG on null pointers,
+ * n outside [1, 2^26], a non-positive step or non-finite positions. */
+gdm_status gdm_lattice_partition(const double *pos, int64_t n, double step, int block_cells, int32_t *perm,
+                                 int32_t *parent, int32_t *coarse_offsets, int64_t *n_coarse);
+
 /* ---------------------------------------------------------------- effective models */
 
 /* Global polarizability matrix (GPM) of a discretised structure (Sec. "Effective

@@ -118,6 +118,7 @@ _SIGS = {
     "gdm_nearfield_backward": ([P, C.POINTER(Problem), P, P, I64, C.c_int, PD, PD, P, P, P, P, P], C.c_int),
     "gdm_solve_gmres": ([P, C.c_int, C.POINTER(Problem), P, P, C.c_int, C.POINTER(GmresOpts),
                          C.POINTER(SolveInfo)], C.c_int),
+    "gdm_lattice_partition": ([P, I64, C.c_double, C.c_int, P, P, P, C.POINTER(I64)], C.c_int),
     "gdm_profile_enable": ([P, C.c_int], C.c_int),
     "gdm_profile_read": ([P, C.POINTER(I64), PD, PD, PD], C.c_int),
     "gdm_profile_phases": ([P, C.c_int, PD], C.c_int),
@@ -324,6 +325,22 @@ def solve_gmres(ctx: Context, prob: GDMProblem, F0, precision="tf32", restart=0,
     ctx._check(lib().gdm_solve_gmres(ctx.h, PRECISION[precision], C.byref(s), _ptr(F0.contiguous()), _ptr(F),
                                      F0.shape[0], C.byref(opts), C.byref(inf)), "gdm_solve_gmres")
     return F, inf.as_dict()
+
+
+def lattice_partition(pos, step, block_cells=512):
+    """gdm_lattice_partition (host only): (perm, parent, coarse_offsets) as numpy int32 arrays for host
+    positions pos ((n, 3) float64)."""
+    pos = np.ascontiguousarray(np.asarray(pos, np.float64))
+    n = pos.shape[0]
+    perm = np.empty(n, np.int32)
+    parent = np.empty(n, np.int32)
+    coff = np.empty(n + 1, np.int32)
+    nc = I64(0)
+    st = lib().gdm_lattice_partition(pos.ctypes.data, n, float(step), int(block_cells), perm.ctypes.data,
+                                     parent.ctypes.data, coff.ctypes.data, C.byref(nc))
+    if st != GDM_OK:
+        raise GDMError(st, "gdm_lattice_partition")
+    return perm, parent, coff[:nc.value + 1].copy()
 
 
 def residual(ctx: Context, prob: GDMProblem, F0, F):

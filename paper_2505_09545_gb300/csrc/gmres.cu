@@ -497,6 +497,23 @@ struct DevBuf {
 
 }  // namespace
 
+extern "C" gdm_status gdm_lattice_partition(const double *pos, int64_t n, double step, int block_cells,
+                                            int32_t *perm, int32_t *parent, int32_t *coarse_offsets,
+                                            int64_t *n_coarse) {
+    if (!pos || !perm || !parent || !coarse_offsets || !n_coarse) return GDM_ERR_INVALID_ARG;
+    if (n < 1 || n > (int64_t)1 << 26 || !(step > 0) || !isfinite(step) || block_cells < 1) return GDM_ERR_INVALID_ARG;
+    std::vector<double> hp(pos, pos + 3 * n);
+    for (double x : hp)
+        if (!isfinite(x)) return GDM_ERR_INVALID_ARG;
+    Partition part;
+    make_partition(hp, n, step, block_cells, part);
+    std::copy(part.perm.begin(), part.perm.end(), perm);
+    std::copy(part.parent.begin(), part.parent.end(), parent);
+    std::copy(part.coff.begin(), part.coff.end(), coarse_offsets);
+    *n_coarse = (int64_t)part.coff.size() - 1;
+    return GDM_OK;
+}
+
 extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, const double *F0,
                                       double *F, int n_rhs, const gdm_gmres_opts *opts, gdm_solve_info *info) {
     if (!ctx) return GDM_ERR_INVALID_ARG;
