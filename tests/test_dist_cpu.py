@@ -54,3 +54,27 @@ def test_reference_arm_skips_other_ranks(monkeypatch, capsys):
     args = argparse.Namespace(gpus=2, steps=1, warmup=0, cuboid="40x30x10", precision="tf32")
     assert bench.run_reference(args) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank0(monkeypatch, capsys):
+    """The reference arm at N = 1 (rank 0) prints one JSON line with the contract's keys: the oracle timed on
+    the host cores, its own e2e with no host-device traffic, the same config as the GPU arm."""
+    import argparse
+    import json
+    import bench
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(bench, "cpu_oracle_sample", lambda *a, **k: {
+        "value": 1.5, "unit": "s", "cores": 4, "kind": "oracle", "sample": "stub sample"})
+    args = argparse.Namespace(gpus=1, steps=2, warmup=1, cuboid="40x30x10", precision="tf32", tol=1e-10)
+    bench.run_reference(args)
+    out = capsys.readouterr().out.strip().splitlines()
+    assert len(out) == 1
+    line = json.loads(out[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["higher_is_better"] is False
+    assert line["value"] == 1.5 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 4
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["config"] == bench.workload_config(args)
