@@ -1,0 +1,90 @@
+"""Parity at the benchmark's full sizes, in the configurations bench.py times, on outputs the oracle can
+compute one by one: the exact FP64 residual rows F0 - A F of a seeded sample of cells (relative to |F0|
+there), the incident field at those cells, and the cross sections from the oracle's formula applied to
+the GPU fields. Config 2: the 40 x 30 x 10 cuboid (3N = 36,000) with TF32 factors refined to a relative
+correction of 1e-10, as bench.py runs it. Config 3: the 256 Eden blobs in one gdm_solve_batched call, every
+item's cross sections, and three sampled items (the smallest, the largest, one seeded) against the
+oracle's dense solve. The file sorts last so that its long cases run after the quick ones.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gdm_workloads as W
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+@pytest.fixture(scope="module")
+def G():
+    import paper_2505_09545_gb300 as G
+    return G
+
+
+def t(x):
+    return torch.tensor(np.ascontiguousarray(x), device=DEV)
+
+
+def sampled_residual(pr, F0h, Fh, n_rows, seed):
+    """max over right-hand sides of ||(F0 - A F)[rows]|| / ||F0[rows]|| for seeded rows (oracle, FP64)."""
+    rows = np.sort(np.random.default_rng(seed).choice(pr.n, n_rows, replace=False))
+    r = O.residual_rows(pr, F0h, Fh, rows)
+    f0 = F0h.reshape(pr.n, 3, -1)[rows]
+    nr = F0h.shape[1]
+    return float(np.max(np.linalg.norm(r.reshape(-1, nr), axis=0) / np.linalg.norm(f0.reshape(-1, nr), axis=0))), rows
+
+
+def test_cuboid_config2_full_size(G):
+    s = W.cuboid_precision()
+    lam = float(s.wavelengths[0])
+    ctx = G.Context(0)
+    try:
+        prob = G.GDMProblem(t(s.pos), lam, 3, eps=t(s.eps), step=s.step)
+        F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0)
+        A = G.assemble(ctx, prob, "tf32")
+        F, _, info = G.solve(ctx, prob, A, F0, "tf32", tol=1e-10)
+        del A
+        ext, sca, ab = (x.cpu().numpy() for x in G.cross_sections(ctx, prob, F0, F, np.ones(2)))
+        F0h, Fh = F0.cpu().numpy().T, F.cpu().numpy().T
+    finally:
+        ctx.close()
+    assert info["status"] == 0 and info["rel_correction"] <= 1e-10, info
+    pr = O.Problem(s.pos, lam, 3, eps=s.eps, step=s.step)
+    rel, rows = sampled_residual(pr, F0h, Fh, 48, seed=5)
+    assert rel < 1e-10, (rel, info)
+    # the incident field at the sampled cells
+    f0o = pr.plane_wave(s.e0).reshape(pr.n, 3, -1)[rows]
+    np.testing.assert_allclose(F0h.reshape(pr.n, 3, -1)[rows], f0o, rtol=0, atol=1e-14)
+    # cross sections: the oracle's formula on the GPU fields
+    xo = pr.cross_sections(F0h, Fh, s.e0)
+    for g, o in zip((ext, sca, ab), xo):
+        np.testing.assert_allclose(g, o, rtol=1e-9, atol=1e-9 * np.abs(xo[0]).max())
+
+
+def test_batch_config3_full_size(G):
+    ss = W.blob_batch()
+    ctx = G.Context(0)
+    try:
+        probs = [G.GDMProblem(t(s.pos), float(s.wavelengths[0]), 3, eps=t(s.eps), step=s.step) for s in ss]
+        Fs, sigs, infos = G.solve_batched(ctx, probs, [s.e0 for s in ss], precision="tf32")
+        torch.cuda.synchronize()
+        Fh = [F.cpu().numpy().T for F in Fs]
+        sig = [x.cpu().numpy() for x in sigs]
+    finally:
+        ctx.close()
+    assert all(i["status"] == 0 for i in infos), [i for i in infos if i["status"] != 0][:3]
+    sizes = np.array([s.n for s in ss])
+    pick = {int(np.argmin(sizes)), int(np.argmax(sizes)), int(np.random.default_rng(7).integers(len(ss)))}
+    for k, s in enumerate(ss):
+        lam = float(s.wavelengths[0])
+        pr = O.Problem(s.pos, lam, 3, eps=s.eps, step=s.step)
+        F0o = pr.plane_wave(s.e0)
+        xo = pr.cross_sections(F0o, Fh[k], s.e0)
+        for r in range(3):
+            np.testing.assert_allclose(sig[k][r], xo[r], rtol=1e-9, atol=1e-9 * np.abs(xo[0]).max())
+        if k in pick:
+            Fo = pr.solve(F0o)
+            err = np.linalg.norm(Fh[k] - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+            assert np.all(err < 1e-9), (s.name, s.n, err)
