@@ -4,7 +4,8 @@ there), the incident field at those cells, and the cross sections from the oracl
 the GPU fields. Config 2: the 40 x 30 x 10 cuboid (3N = 36,000) with TF32 factors refined to a relative
 correction of 1e-10, as bench.py runs it. Config 3: the 256 Eden blobs in one gdm_solve_batched call, every
 item's cross sections, and three sampled items (the smallest, the largest, one seeded) against the
-oracle's dense solve. The file sorts last so that its long cases run after the quick ones.
+oracle's dense solve. Config 5: the full cylinder's gradients at one wavelength against the oracle's
+adjoint. The file sorts last so that its long cases run after the quick ones.
 """
 import numpy as np
 import pytest
@@ -88,3 +89,32 @@ def test_batch_config3_full_size(G):
             Fo = pr.solve(F0o)
             err = np.linalg.norm(Fh[k] - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
             assert np.all(err < 1e-9), (s.name, s.n, err)
+
+
+def test_cylinder_config5_full_size_gradients(G):
+    """The differentiation workload's full cylinder (r 80, h 100, d 10: N = 1,970, eps = 12.25 + 0.05i) at
+    its first wavelength, through the autograd wrappers with TF32 factors: L = |E(probe)|^2 + sigma_sca and
+    its gradients with respect to every position, every eps and the wavelength, against the oracle's FP64
+    adjoint (1e-9 on L, 1e-8 normwise on the gradients)."""
+    from paper_2505_09545_gb300 import autograd as AG
+    cyl = W.cylinder_diff()
+    lam = float(cyl.wavelengths[0])
+    ctx = G.Context(0)
+    try:
+        pos = torch.tensor(cyl.pos, device=DEV, requires_grad=True)
+        eps = torch.tensor(cyl.eps, device=DEV, requires_grad=True)
+        wl = torch.tensor(lam, dtype=torch.float64, device=DEV, requires_grad=True)
+        rp = torch.tensor(cyl.r_eval, device=DEV)
+        F, sig = AG.scatter(pos, eps, wl, ctx, cyl.step, cyl.e0, precision="tf32")
+        E = AG.nearfield(pos, eps, wl, F, rp, ctx, cyl.step, cyl.e0)
+        L = (E.abs() ** 2).sum() + sig[:, 1].sum()
+        L.backward()
+        L, gp, ge, gl = float(L.detach()), pos.grad.cpu().numpy(), eps.grad.cpu().numpy(), float(wl.grad)
+    finally:
+        ctx.close()
+    pr = O.Problem(cyl.pos, lam, 3, eps=cyl.eps, step=cyl.step)
+    Lo, gpo, geo, glo = O.loss_and_grad_probe_sca(pr, cyl.e0, cyl.r_eval[0])
+    assert abs(L - Lo) <= 1e-9 * abs(Lo), (L, Lo)
+    assert np.linalg.norm(gp - gpo) <= 1e-8 * np.linalg.norm(gpo)
+    assert np.linalg.norm(ge - geo) <= 1e-8 * np.linalg.norm(geo)
+    assert abs(gl - glo) <= 1e-8 * abs(glo) + 1e-14
