@@ -53,7 +53,7 @@ typedef enum {
     GDM_ERR_NONFINITE = 3,     /* NaN/Inf found in an input or produced by the solve */
     GDM_ERR_SINGULAR = 4,      /* exactly zero pivot in the LU factorisation */
     GDM_ERR_NOT_CONVERGED = 5, /* iterative refinement did not reach the tolerance */
-    GDM_ERR_OOM = 6,           /* scratch allocation failed */
+    GDM_ERR_OOM = 6,           /* scratch allocation failed (device memory, or host memory / threads) */
     GDM_ERR_CUDA = 7,          /* CUDA runtime / driver error */
     GDM_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up */
     GDM_ERR_UNSUPPORTED = 9    /* valid request that this build does not implement */

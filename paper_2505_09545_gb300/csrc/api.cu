@@ -2,8 +2,8 @@
 #include <math.h>
 #include <stdarg.h>
 
+#include <exception>
 #include <new>
-
 #include <vector>
 
 #include "gdm_internal.cuh"
@@ -24,6 +24,16 @@ gdm_status gdm_fail(gdm_ctx *ctx, gdm_status s, const char *fmt, ...) {
         va_end(ap);
     }
     return s;
+}
+
+gdm_status gdm_host_exception(gdm_ctx *ctx) {
+    try {
+        throw;
+    } catch (const std::exception &e) {
+        return gdm_fail(ctx, GDM_ERR_OOM, "host allocation or thread creation failed: %s", e.what());
+    } catch (...) {
+        return gdm_fail(ctx, GDM_ERR_OOM, "host allocation or thread creation failed");
+    }
 }
 
 gdm_status gdm_after_launch(gdm_ctx *ctx, const char *what) {
@@ -539,6 +549,7 @@ gdm_status gdm_sigma_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *
     for (int r = 0; r < n_rhs; r++)
         if (!(e0_norm2[r] > 0)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "|E0|^2 must be > 0");
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    GDM_GUARD_BEGIN
     const int64_t q = (int64_t)n_theta * n_phi;
     std::vector<double> x(n_theta), w(n_theta), h((size_t)4 * q + n_rhs);
     gauss_legendre(n_theta, x.data(), w.data());
@@ -564,6 +575,7 @@ gdm_status gdm_sigma_farfield(gdm_ctx *ctx, const gdm_problem *p, const double *
     cudaStreamSynchronize(ctx->stream);
     cudaFreeAsync(d, ctx->stream);
     return st;
+    GDM_GUARD_END(ctx)
 }
 
 gdm_status gdm_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p, const double *F0, const double *F,

@@ -119,11 +119,13 @@ gdm_status gdm_solve_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_i
                 if (!(it->e0_norm2[q] > 0)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "item %d: |E0|^2 <= 0", i);
     }
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    GDM_GUARD_BEGIN
     std::vector<int64_t> size((size_t)n_items);
     for (int i = 0; i < n_items; i++) size[i] = items[i].prob.n * items[i].prob.kind;
     return gdm_run_pool(ctx, n_items, size.data(), n_streams, infos,
                     [&](gdm_ctx *c, int, int i, gdm_solve_info *inf) { return run_item(c, prec, &items[i], opts, inf); },
                     nullptr);
+    GDM_GUARD_END(ctx)
 }
 
 gdm_status gdm_backward_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_backward_item *items, int n_items,
@@ -155,19 +157,24 @@ gdm_status gdm_backward_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_back
     double *acc = nullptr;
     GDM_CUDA_TRY(ctx, cudaMallocAsync((void **)&acc, sizeof(double) * 5 * n * ns, ctx->stream));
     GDM_CUDA_TRY(ctx, cudaMemsetAsync(acc, 0, sizeof(double) * 5 * n * ns, ctx->stream));
-    std::vector<int64_t> size((size_t)n_items, n);
     static const double zhat[3] = {0.0, 0.0, 1.0};
     BackwardSum bs = {acc, n, grad_pos, grad_eps};
-    gdm_status st = gdm_run_pool(
-        ctx, n_items, size.data(), ns, infos,
-        [&](gdm_ctx *c, int w, int i, gdm_solve_info *inf) {
-            const gdm_backward_item *it = &items[i];
-            double *a = acc + (int64_t)w * 5 * n;
-            return gdm_launch_backward(c, &it->prob, prec, it->A, it->lda, it->ipiv, it->F, it->n_rhs, it->e0,
-                                       it->khat ? it->khat : zhat, it->gF, it->g_sigma, a, a + 3 * n,
-                                       it->grad_wavelength, inf);
-        },
-        backward_sum, &bs);
+    gdm_status st;
+    try {
+        std::vector<int64_t> size((size_t)n_items, n);
+        st = gdm_run_pool(
+            ctx, n_items, size.data(), ns, infos,
+            [&](gdm_ctx *c, int w, int i, gdm_solve_info *inf) {
+                const gdm_backward_item *it = &items[i];
+                double *a = acc + (int64_t)w * 5 * n;
+                return gdm_launch_backward(c, &it->prob, prec, it->A, it->lda, it->ipiv, it->F, it->n_rhs, it->e0,
+                                           it->khat ? it->khat : zhat, it->gF, it->g_sigma, a, a + 3 * n,
+                                           it->grad_wavelength, inf);
+            },
+            backward_sum, &bs);
+    } catch (...) {
+        st = gdm_host_exception(ctx);
+    }
     cudaFreeAsync(acc, ctx->stream);
     return st;
 }

@@ -72,6 +72,17 @@ gdm_status gdm_fail(gdm_ctx *ctx, gdm_status s, const char *fmt, ...);
                             "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));      \
     } while (0)
 
+// C++ exceptions (host containers, worker threads) must not cross the C ABI: entry points that use them
+// wrap their body in GDM_GUARD_BEGIN ... GDM_GUARD_END(ctx), which turns an escaping exception into
+// GDM_ERR_OOM with its message in the context
+gdm_status gdm_host_exception(gdm_ctx *ctx);
+#define GDM_GUARD_BEGIN try {
+#define GDM_GUARD_END(ctx)                 \
+    }                                      \
+    catch (...) {                          \
+        return gdm_host_exception(ctx);    \
+    }
+
 #define GDM_TRY(...)                       \
     do {                                   \
         gdm_status s_ = (__VA_ARGS__);     \

@@ -502,6 +502,7 @@ extern "C" gdm_status gdm_lattice_partition(const double *pos, int64_t n, double
                                             int64_t *n_coarse) {
     if (!pos || !perm || !parent || !coarse_offsets || !n_coarse) return GDM_ERR_INVALID_ARG;
     if (n < 1 || n > (int64_t)1 << 26 || !(step > 0) || !isfinite(step) || block_cells < 1) return GDM_ERR_INVALID_ARG;
+    GDM_GUARD_BEGIN
     std::vector<double> hp(pos, pos + 3 * n);
     for (double x : hp)
         if (!isfinite(x)) return GDM_ERR_INVALID_ARG;
@@ -512,10 +513,11 @@ extern "C" gdm_status gdm_lattice_partition(const double *pos, int64_t n, double
     std::copy(part.coff.begin(), part.coff.end(), coarse_offsets);
     *n_coarse = (int64_t)part.coff.size() - 1;
     return GDM_OK;
+    GDM_GUARD_END(nullptr)
 }
 
-extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, const double *F0,
-                                      double *F, int n_rhs, const gdm_gmres_opts *opts, gdm_solve_info *info) {
+static gdm_status solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, const double *F0, double *F,
+                              int n_rhs, const gdm_gmres_opts *opts, gdm_solve_info *info) {
     if (!ctx) return GDM_ERR_INVALID_ARG;
     if (!p || !F0 || !F) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "null pointer");
     if (p->kind != 3) return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "gdm_solve_gmres: discretised structures (kind 3)");
@@ -960,4 +962,12 @@ extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gd
         return gdm_fail(ctx, GDM_ERR_NOT_CONVERGED, "gdm_solve_gmres: relative residual %.3e > tol %.3e after %d steps",
                         rel_true, tol, total);
     return GDM_OK;
+}
+
+extern "C" gdm_status gdm_solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *p, const double *F0,
+                                      double *F, int n_rhs, const gdm_gmres_opts *opts, gdm_solve_info *info) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    GDM_GUARD_BEGIN
+    return solve_gmres(ctx, prec, p, F0, F, n_rhs, opts, info);
+    GDM_GUARD_END(ctx)
 }

@@ -62,7 +62,12 @@ gdm_status gdm_run_pool(gdm_ctx *ctx, int n_items, const int64_t *size, int n_st
             const int k = next.fetch_add(1);
             if (k >= n_items) break;
             const int i = order[k];
-            gdm_status s = fn(c, w, i, &inf[i]);
+            gdm_status s;
+            try {
+                s = fn(c, w, i, &inf[i]);
+            } catch (...) {  // an exception must not leave the worker thread
+                s = gdm_host_exception(c);
+            }
             inf[i].status = s;
             if (s != GDM_OK) {
                 std::lock_guard<std::mutex> lock(mu);
