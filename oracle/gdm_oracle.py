@@ -10,9 +10,10 @@ paper (Wiecha et al., "TorchGDM", arXiv:2505.09545) in its own notation:
 * Sec. "Formalism and implementation", Eq. (LPS_6by6) and Eq. (superprop_G):
   the 6x6 Green dyad G = [[G^Ep, G^Em], [G^Hp, G^Hm]] that propagates the
   fields of electric (p) and magnetic (m) point dipoles.  The paper defers the
-  explicit vacuum tensors to its pyGDM reference; here they are the standard
-  Gaussian-unit fields of an oscillating point dipole (time factor exp(-i w t),
-  outgoing exp(+ikR)), see `green_ep` / `green_hp`.
+  explicit tensors to its pyGDM reference; here they are the standard
+  Gaussian-unit fields of an oscillating point dipole in a non-magnetic host of
+  permittivity eps_env (time factor exp(-i w t), outgoing exp(+ikR)), see
+  `green_ep` / `green_hp` / `green6`.
 * Eq. (LPS_6by6_discrete): F_i = F0_i + sum_j G(r_i, r_j) alpha_j F_j.
 * Eq. (GDM_system_of_equations) read as  sum_j [delta_ij I - G_ij alpha_j] F_j = F0_i
   (the printed equation carries a stray F(r_j) inside the bracket; this reading
