@@ -17,6 +17,7 @@ import os
 import re
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -48,7 +49,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples: a scratch file (GDM_CLOCKS_DIR, default the system temporary directory); the summary
+        # goes into the JSON line
+        self.path = os.path.join(os.environ.get("GDM_CLOCKS_DIR", tempfile.gettempdir()), f"gdm_clocks_rank{index}.csv")
 
     def start(self):
         try:

@@ -62,7 +62,7 @@ def check(G, ctx, pos, eps, step, lam, eps_env=1.0, tol_f=1e-9, **kw):
 
 @pytest.mark.parametrize("precision,fast", [("tf32", True), ("fp32", True), ("tf32", False)])
 def test_gmres_cuboid_matches_oracle(G, ctx, precision, fast):
-    """14 x 12 x 9 cells (N = 1,512) of config-2 permittivities: blocks of 256 cells (six, the last
+    """14 x 12 x 9 cells (N = 1,512), eps ~ U[2,16] + i U[0,0.5]: blocks of 256 cells (six, the last
     ragged), coarse cells of 8 children and, on the odd face, of 4; Arnoldi steps on the FP32 operator
     (cycles refined by the double-float residual) or on the double-float operator throughout."""
     pos, eps, step = cuboid(14, 12, 9, seed=2)

@@ -83,7 +83,7 @@ def test_assembly_edmd(G, ctx, prec, tol):
 
 
 def test_assembly_large_phase(G, ctx):
-    """Config-4 extent: kR up to ~450 rad needs the double-float phase."""
+    """The 64 x 64 metasurface's extent (25.6 um): kR up to ~450 rad needs the double-float phase."""
     s = W.metasurface_edmd(nx=64, ny=64, pitch=400.0)
     rng = np.random.default_rng(0)
     sub = np.sort(rng.choice(s.n, 40, replace=False))

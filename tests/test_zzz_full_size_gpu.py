@@ -1,10 +1,10 @@
 """Parity at the benchmark's full sizes, in the configurations bench.py times, on outputs the oracle can
 compute one by one: the exact FP64 residual rows F0 - A F of a seeded sample of cells (relative to |F0|
 there), the incident field at those cells, and the cross sections from the oracle's formula applied to
-the GPU fields. Config 2: the 40 x 30 x 10 cuboid (3N = 36,000) with TF32 factors refined to a relative
-correction of 1e-10, as bench.py runs it. Config 3: the 256 Eden blobs in one gdm_solve_batched call, every
-item's cross sections, and three sampled items (the smallest, the largest, one seeded) against the
-oracle's dense solve. Config 5: the full cylinder's gradients at one wavelength against the oracle's
+the GPU fields. The 40 x 30 x 10 cuboid (3N = 36,000) with TF32 factors refined to a relative correction
+of 1e-10, as bench.py runs it; the 256 Eden blobs (50 to 1,500 cells each) in one gdm_solve_batched call,
+every item's cross sections, and three sampled items (the smallest, the largest, one seeded) against the
+oracle's dense solve; the 1,970-cell cylinder's gradients at one wavelength against the oracle's
 adjoint. The file sorts last so that its long cases run after the quick ones.
 """
 import numpy as np
@@ -37,7 +37,7 @@ def sampled_residual(pr, F0h, Fh, n_rows, seed):
     return float(np.max(np.linalg.norm(r.reshape(-1, nr), axis=0) / np.linalg.norm(f0.reshape(-1, nr), axis=0))), rows
 
 
-def test_cuboid_config2_full_size(G):
+def test_cuboid_40x30x10_full_size(G):
     s = W.cuboid_precision()
     lam = float(s.wavelengths[0])
     ctx = G.Context(0)
@@ -64,7 +64,7 @@ def test_cuboid_config2_full_size(G):
         np.testing.assert_allclose(g, o, rtol=1e-9, atol=1e-9 * np.abs(xo[0]).max())
 
 
-def test_batch_config3_full_size(G):
+def test_blob_batch_256_full_size(G):
     ss = W.blob_batch()
     ctx = G.Context(0)
     try:
@@ -91,7 +91,7 @@ def test_batch_config3_full_size(G):
             assert np.all(err < 1e-9), (s.name, s.n, err)
 
 
-def test_cylinder_config5_full_size_gradients(G):
+def test_cylinder_1970_cells_full_size_gradients(G):
     """The differentiation workload's full cylinder (r 80, h 100, d 10: N = 1,970, eps = 12.25 + 0.05i) at
     its first wavelength, through the autograd wrappers with TF32 factors: L = |E(probe)|^2 + sigma_sca and
     its gradients with respect to every position, every eps and the wavelength, against the oracle's FP64
