@@ -586,7 +586,9 @@ gdm_status gdm_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p, const 
     for (int r = 0; r < n_rhs; r++)
         if (!(e0_norm2[r] > 0)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "|E0|^2 must be > 0");
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    GDM_GUARD_BEGIN
     return gdm_launch_cross_sections_noalloc(ctx, p, F0, F, n_rhs, e0_norm2, ext, sca, abs);
+    GDM_GUARD_END(ctx)
 }
 
 gdm_status gdm_backward(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -99,6 +100,15 @@ gdm_status backward_sum(gdm_ctx *ctx, int nw, void *arg) {
     return GDM_OK;
 }
 
+// prefixes the item index to the message the argument check left in ctx->err (formatted from a copy:
+// the message buffer is also the destination)
+gdm_status fail_item(gdm_ctx *ctx, gdm_status s, int i) {
+    char msg[sizeof(ctx->err)];
+    memcpy(msg, ctx->err, sizeof(msg));
+    msg[sizeof(msg) - 1] = 0;
+    return gdm_fail(ctx, s, "item %d: %s", i, msg);
+}
+
 }  // namespace
 
 extern "C" {
@@ -111,7 +121,7 @@ gdm_status gdm_solve_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_i
     for (int i = 0; i < n_items; i++) {
         const gdm_batch_item *it = &items[i];
         gdm_status s = gdm_check_solve_args(ctx, &it->prob, prec, it->A, it->lda, it->ipiv, it->F0, it->F, it->n_rhs);
-        if (s != GDM_OK) return gdm_fail(ctx, s, "item %d: %s", i, ctx->err);
+        if (s != GDM_OK) return fail_item(ctx, s, i);
         if (it->sigma && !it->e0 && !it->e0_norm2)
             return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "item %d: cross sections need e0 or e0_norm2", i);
         if (it->sigma && !it->e0)
@@ -145,7 +155,7 @@ gdm_status gdm_backward_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_back
                             "wavelength may differ",
                             i);
         gdm_status s = gdm_check_solve_args(ctx, p, prec, it->A, it->lda, it->ipiv, it->F, it->F, it->n_rhs);
-        if (s != GDM_OK) return gdm_fail(ctx, s, "item %d: %s", i, ctx->err);
+        if (s != GDM_OK) return fail_item(ctx, s, i);
         if (!it->e0) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "item %d: e0 is NULL", i);
     }
     GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));

@@ -1,16 +1,23 @@
 // Mixed-precision iterative refinement of the GDM solve.
 //
 // X_0 = LU^{-1} b in the factor precision; then repeat
-//   r = b - A X          (FP64, matrix-free: the Green dyads are regenerated in FP64 per pair)
+//   r = b - A X          (matrix-free: the Green dyads are regenerated per pair, never stored)
 //   d = LU^{-1} r        (factor precision)
 //   X = X + d            (FP64)
 // until max_q ||d_q|| / ||X_q|| <= tol. The adjoint variant solves A^H X = b with the same factors
 // (conjugate-transposed triangular solves) and the matrix-free residual b - A^H X.
-// For cells (forward solves with TF32 factors) the residuals of the first steps, while the last relative
-// correction is above 1e-3, use FP32 Green sums (double-float phase, ~1e-6 relative, ~1/6 of the double-float work): the
-// correction they yield is then accurate to ~1e-2 relative, below the factorisation's own contraction
-// (~0.03 per step), so they cost no extra step; every later residual, which decides the accuracy and the
-// stop, is double-float.
+// Residual arithmetic: double-float (pairs of FP32 on the FP32 pipes, about 48 significand bits; the
+// GB300 FP64 pipe runs at ~1/64 of the FP32 rate), which matches the oracle's FP64 residual to ~1e-13 of
+// its largest term, four orders inside the 1e-9 field tolerance. GDM_RESIDUAL_FP64 selects FP64 Green sums
+// instead (and the adjoint of ED/MD dipoles always uses them). For cells with TF32 factors the residuals of
+// the first steps, while the last relative correction is above 1e-3, are FP32 Green sums (double-float
+// phase, ~1e-6 relative, ~1/6 of the double-float work): the correction they yield is then accurate to
+// ~1e-2 relative, below the factorisation's own contraction (~0.03 per step), so they cost no extra step;
+// every later residual, which decides the accuracy and the stop, is double-float.
+// Scaling: each right-hand side of a low-precision triangular solve (b, then every r) is multiplied by the
+// power of two that brings its largest column norm near 1, and the correction is scaled back in FP64, so
+// that a residual far below the FP32 range (a weak illumination, a late refinement step) is not flushed to
+// zero. The scale is computed on the device from the norms the previous kernels accumulated.
 #include <math.h>
 #include <stdlib.h>
 
@@ -26,10 +33,21 @@ const void *gdm_ff_positions(void *ffws);
 gdm_status gdm_launch_residual_f32(gdm_ctx *ctx, const gdm_problem *p, const double *rhs, const double *X, int n_rhs,
                                    double *r, double *norms2, double2 *Pbuf, double2 *partial, const void *dipf);
 
+// power of two that brings the largest of the n_rhs column norms (given squared) near 1; 1 if they are
+// all zero or not finite. Exact in every precision, so scaling by it loses nothing.
+__device__ __forceinline__ double work_scale(const double *__restrict__ norms2, int n_rhs) {
+    double m = 0.0;
+    for (int q = 0; q < n_rhs; q++) m = fmax(m, norms2[q]);
+    if (!(m > 0.0) || !isfinite(m)) return 1.0;
+    return ldexp(1.0, -ilogb(sqrt(m)));
+}
+
 template <class C>
-__global__ void k_to_work(const double2 *__restrict__ src, C *__restrict__ dst, int64_t count, double scale) {
+__global__ void k_to_work(const double2 *__restrict__ src, C *__restrict__ dst, int64_t count,
+                          const double *__restrict__ norms2, int n_rhs) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= count) return;
+    const double scale = work_scale(norms2, n_rhs);
     C v;
     v.x = src[i].x * scale;
     v.y = src[i].y * scale;
@@ -39,8 +57,9 @@ __global__ void k_to_work(const double2 *__restrict__ src, C *__restrict__ dst, 
 // X (+)= d/scale ; accumulate ||d||^2 and ||X||^2 per RHS; flag non-finite values
 template <class C>
 __global__ void k_update(double2 *__restrict__ X, const C *__restrict__ d, int64_t ld, int n_rhs, int accumulate,
-                         double inv_scale, double *__restrict__ norms, int *flags) {
+                         const double *__restrict__ scale_norms2, double *__restrict__ norms, int *flags) {
     int q = blockIdx.y;
+    const double inv_scale = 1.0 / work_scale(scale_norms2, n_rhs);
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double dn = 0.0, xn = 0.0;
     if (i < ld) {
@@ -142,10 +161,11 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     };
     if (info) GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     // initial solve
-    k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>((const double2 *)rhs, w, cnt, 1.0);
+    k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>((const double2 *)rhs, w, cnt,
+                                                                         dnorm + 3 * n_rhs, n_rhs);
     GDM_LAUNCHED(ctx, "to_work");
     GDM_TRY(lu_solve(w));
-    k_update<C><<<gq, 256, 0, ctx->stream>>>((double2 *)X, w, ns, n_rhs, 0, 1.0, dnorm, ctx->dflags);
+    k_update<C><<<gq, 256, 0, ctx->stream>>>((double2 *)X, w, ns, n_rhs, 0, dnorm + 3 * n_rhs, dnorm, ctx->dflags);
     GDM_LAUNCHED(ctx, "update");
     int it = 0;
     double relc = 1.0, relr = -1.0;
@@ -164,11 +184,13 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
                 ff_prepared = ffws != nullptr;
             }
             GDM_TRY(gdm_phase_end(ctx, GDM_PH_RESIDUAL));
-            // scale the residual into a safe FP32 range before the low-precision solve
-            k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(r, w, cnt, 1.0);
+            // scale the residual into a safe FP32 range before the low-precision solve (by its own norms,
+            // accumulated by the residual kernel), and the correction back
+            k_to_work<C><<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(r, w, cnt, dnorm + 2 * n_rhs, n_rhs);
             GDM_LAUNCHED(ctx, "to_work");
             GDM_TRY(lu_solve(w));
-            k_update<C><<<gq, 256, 0, ctx->stream>>>((double2 *)X, w, ns, n_rhs, 1, 1.0, dnorm, ctx->dflags);
+            k_update<C><<<gq, 256, 0, ctx->stream>>>((double2 *)X, w, ns, n_rhs, 1, dnorm + 2 * n_rhs, dnorm,
+                                                     ctx->dflags);
             GDM_LAUNCHED(ctx, "update");
             GDM_CUDA_TRY(ctx, cudaMemcpyAsync(hn, dnorm, sizeof(double) * 4 * n_rhs, cudaMemcpyDeviceToHost,
                                               ctx->stream));

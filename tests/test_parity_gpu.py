@@ -82,6 +82,19 @@ def test_assembly_edmd(G, ctx, prec, tol):
     assert block_errors(Ag, Ao, 6) < tol
 
 
+
+@pytest.mark.parametrize("eps_env", [1.0, 1.77])
+def test_assembly_edmd_several_tiles(G, ctx, eps_env):
+    """ED/MD assembly across several 64-target x 4-source tiles with ragged tails in both directions
+    (143 dipoles: 2 full target tiles + 15, 35 full source tiles + 3), in vacuum and in a host."""
+    s = W.metasurface_edmd(nx=13, ny=11, pitch=400.0, seed=9)
+    lam = 610.0
+    al = O.lorentz_alpha6(s.omega0_e, s.omega0_m, s.gamma_ev, s.amp_nm, lam, eps_env=eps_env)
+    A = G.assemble(ctx, G.GDMProblem(t(s.pos), lam, 6, alpha6=t(al), eps_env=eps_env), "fp32")
+    Ag = A.cpu().numpy()[:, :6 * s.n].T
+    Ao = O.Problem(s.pos, lam, 6, alpha6=al, eps_env=eps_env).matrix()
+    assert block_errors(Ag, Ao, 6) < 1e-6
+
 def test_assembly_large_phase(G, ctx):
     """The 64 x 64 metasurface's extent (25.6 um): kR up to ~450 rad needs the double-float phase."""
     s = W.metasurface_edmd(nx=64, ny=64, pitch=400.0)
@@ -115,6 +128,25 @@ def test_solve_cells(G, ctx, prec):
         Fo = pr.solve(pr.plane_wave(s.e0))
         err = np.linalg.norm(F.cpu().numpy().T - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
         assert np.all(err < 1e-9), (prec, err, info)
+
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+@pytest.mark.parametrize("scale", [1e-30, 1e30])
+def test_solve_illumination_far_outside_fp32_range(G, ctx, prec, scale):
+    """The solution is linear in F0: an illumination scaled by 1e-30 (or 1e30) gives the scaled fields to the
+    same accuracy. Unscaled, the FP32 refinement residuals of the weak illumination (~1e-40) would flush to
+    zero and the refinement would stop on a zero correction with an unrefined solution."""
+    s = W.random_cells(150, seed=1)
+    lam = float(s.wavelengths[0])
+    prob = gpu_problem(G, s, lam)
+    F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0)
+    A = G.assemble(ctx, prob, prec)
+    F, ipiv, info = G.solve(ctx, prob, A, F0, prec)
+    Fs, _, info_s = G.solve(ctx, prob, A, F0 * scale, prec, ipiv=ipiv, factored=True)
+    d = (Fs / scale - F).norm(dim=1) / F.norm(dim=1)
+    assert float(d.max()) < 1e-9, (d, info, info_s)
+    assert info_s["rel_residual"] < 1e-10, info_s
 
 
 def test_solve_sphere_config(G, ctx):

@@ -96,3 +96,33 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(G):
         assert close(out1, torch.stack(G.cross_sections(ctx, p1, F0, F1, [1.0])))
     finally:
         ctx.close()
+
+
+def test_noalloc_allocates_no_device_memory(G):
+    """The defining property: a call takes no device memory. The first call on a device looks up the fixed
+    buffer (and, in a fresh process, loads the module that holds it), so the check runs on a context created
+    afterwards, whose own workspace has never been allocated: free device memory must not move across the
+    call."""
+    s = W.random_cells(300, seed=21)
+    F0, F = random_fields(3 * s.n, 2, seed=8)
+    pos, eps = t(s.pos), t(s.eps)
+    out = torch.empty((3, 2), dtype=torch.float64, device=DEV)
+    warm = G.Context(0)
+    try:
+        G.binding.cross_sections_noalloc(warm, G.GDMProblem(pos, 600.0, 3, eps=eps, step=s.step), F0, F,
+                                         [1.0, 1.0], out)
+        torch.cuda.synchronize()
+    finally:
+        warm.close()
+    ctx = G.Context(0)
+    try:
+        p = G.GDMProblem(pos, 600.0, 3, eps=eps, step=s.step)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info(DEV)[0]
+        G.binding.cross_sections_noalloc(ctx, p, F0, F, [1.0, 1.0], out)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info(DEV)[0]
+        assert free1 == free0
+        assert torch.isfinite(out).all()
+    finally:
+        ctx.close()
