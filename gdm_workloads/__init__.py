@@ -125,6 +125,14 @@ def nearfield_grid_outside_sphere(half_width, n_per_axis, exclude_radius):
     return np.ascontiguousarray(g[keep])
 
 
+def nearfield_plane(n_side, half_width, z):
+    """n_side x n_side near-field map on the plane at height z: linspace(-w, w, n_side)^2 (a field map above
+    a structure, the paper's near-field example in 2D)."""
+    a = np.linspace(-half_width, half_width, n_side)
+    g = np.stack(np.meshgrid(a, a, indexing="ij"), -1).reshape(-1, 2)
+    return np.ascontiguousarray(np.concatenate([g, np.full((g.shape[0], 1), float(z))], 1))
+
+
 XPOL = np.array([[1.0, 0.0, 0.0]], complex)
 XYPOL = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]], complex)
 

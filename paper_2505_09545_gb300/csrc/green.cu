@@ -613,6 +613,89 @@ __global__ void __launch_bounds__(ASB_TI) k_assemble3_f32_bulk(float2 *__restric
     }
 }
 
+// kind 6 (ED/MD dipoles), complex64 output through the bulk-copy engine. Block (AS6_TI targets) x (4 sources),
+// one thread per ordered pair: the CTA builds its (6 AS6_TI)-row x 24-column tile of A in shared memory
+// (each thread its 6x6 block), then one cp.async.bulk per column moves the column segment to HBM. The direct
+// stores of k_assemble6 (8 bytes per lane at a 48-byte stride) are bound by the L1 store path, not by HBM.
+#define AS6_TJ 4
+template <int AS6_TI>
+__global__ void __launch_bounds__(AS6_TI * AS6_TJ) k_assemble6_f32_bulk(float2 *__restrict__ A, int64_t lda, int64_t n,
+                                                                       const DipF *__restrict__ dipf,
+                                                                       const float2 *__restrict__ alpha6, float khi,
+                                                                       float klo, float n_env, float inv_eps,
+                                                                       float inv_n) {
+    constexpr int AS6_ROWS = 6 * AS6_TI;
+    extern __shared__ __align__(128) float2 stile6[];  // [6 * AS6_TJ columns][AS6_ROWS rows]
+    __shared__ float2 sa[AS6_TJ][36];
+    __shared__ DipF sjf[AS6_TJ];
+    const int64_t i0 = (int64_t)blockIdx.x * AS6_TI, j0 = (int64_t)blockIdx.y * AS6_TJ;
+    const int jn = (int)min((int64_t)AS6_TJ, n - j0);
+    const int ni = (int)min((int64_t)AS6_TI, n - i0);
+    for (int t = threadIdx.x; t < jn * 36; t += blockDim.x) sa[t / 36][t % 36] = alpha6[(j0 + t / 36) * 36 + t % 36];
+    if ((int)threadIdx.x < jn) sjf[threadIdx.x] = dipf[j0 + threadIdx.x];
+    __syncthreads();
+    const int il = threadIdx.x % AS6_TI, jj = threadIdx.x / AS6_TI;
+    const int64_t i = i0 + il, j = j0 + jj;
+    if (il < ni && jj < jn) {
+        float2 *col = stile6 + (6 * jj) * AS6_ROWS + 6 * il;
+        if (j == i) {
+            for (int q = 0; q < 6; q++) {
+                for (int a = 0; a < 6; a++) col[a] = make_float2(a == q ? 1.f : 0.f, 0.f);
+                col += AS6_ROWS;
+            }
+        } else {
+            const DipF ti = dipf[i];
+            const ff kff = {khi, klo};
+            const PairG<float> g = pair_green_f32(ti, sjf[jj], kff, khi, khi * khi, khi * khi, 1.0f, true);
+            for (int q = 0; q < 6; q++) {
+                float2 x[6], y[6];
+#pragma unroll
+                for (int a = 0; a < 6; a++) x[a] = a < 3 ? sa[jj][a * 6 + q] : cscale(sa[jj][a * 6 + q], n_env);
+                apply_g6(g, x, y);
+#pragma unroll
+                for (int a = 0; a < 6; a++) {
+                    const float sc = a < 3 ? -inv_eps : -inv_n;
+                    col[a] = make_float2(sc * y[a].x, sc * y[a].y);
+                }
+                col += AS6_ROWS;
+            }
+        }
+    }
+    // shared-memory writes of the generic proxy must be visible to the bulk-copy (async) proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // 6 ni rows per column: always a whole number of 16-byte units; the column segment starts at row 6 i0
+    // of a column of an lda-even, 16-byte aligned matrix, so it is 16-byte aligned too
+    if ((int)threadIdx.x < 6 * jn) {
+        const int c = threadIdx.x;
+        float2 *dst = A + (6 * j0 + c) * lda + 6 * i0;
+        const float2 *src = stile6 + c * AS6_ROWS;
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                     "r"((uint32_t)__cvta_generic_to_shared(src)), "r"((uint32_t)(6 * ni * sizeof(float2)))
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        // the shared tile must stay until the engine has read it
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+}
+
+template <int TI>
+static gdm_status launch_assemble6_bulk(gdm_ctx *ctx, float2 *A, int64_t lda, int64_t n, const DipF *dipf,
+                                        const float2 *a6, float khi, float klo, double n_env, double eps_env) {
+    const int smem = 6 * AS6_TJ * 6 * TI * (int)sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_assemble6_f32_bulk<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               smem));
+        attr = true;
+    }
+    dim3 g6((unsigned)((n + TI - 1) / TI), (unsigned)((n + AS6_TJ - 1) / AS6_TJ));
+    k_assemble6_f32_bulk<TI><<<g6, TI * AS6_TJ, smem, ctx->stream>>>(A, lda, n, dipf, a6, khi, klo, (float)n_env,
+                                                                     (float)(1.0 / eps_env), (float)(1.0 / n_env));
+    GDM_LAUNCHED(ctx, "assemble6_f32_bulk");
+    return GDM_OK;
+}
+
 gdm_status gdm_launch_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, void *A, int64_t lda) {
     int64_t n = p->n;
     double k0 = gdm_k0(p);
@@ -675,10 +758,18 @@ gdm_status gdm_launch_assemble(gdm_ctx *ctx, const gdm_problem *p, gdm_precision
             k_alpha6_f32<<<(unsigned)((n * 36 + bs - 1) / bs), bs, 0, ctx->stream>>>((const double2 *)p->alpha6,
                                                                                      n * 36, a6);
             GDM_LAUNCHED(ctx, "alpha6_f32");
-            k_assemble6<float><<<grid, blk, 0, ctx->stream>>>((float2 *)A, lda, n, dipf, p->pos, a6, khi, klo, k,
-                                                             (float)n_env, (float)(1.0 / p->eps_env),
-                                                             (float)(1.0 / n_env));
-            GDM_LAUNCHED(ctx, "assemble6_f32");
+            if (((uintptr_t)A & 15) == 0 && (lda & 1) == 0 && !getenv("GDM_ASSEMBLE_DIRECT")) {
+                const char *e = getenv("GDM_AS6_TI");
+                const int ti = e ? atoi(e) : 64;
+                if (ti == 32) GDM_TRY(launch_assemble6_bulk<32>(ctx, (float2 *)A, lda, n, dipf, a6, khi, klo, n_env, p->eps_env));
+                else if (ti == 48) GDM_TRY(launch_assemble6_bulk<48>(ctx, (float2 *)A, lda, n, dipf, a6, khi, klo, n_env, p->eps_env));
+                else GDM_TRY(launch_assemble6_bulk<64>(ctx, (float2 *)A, lda, n, dipf, a6, khi, klo, n_env, p->eps_env));
+            } else {
+                k_assemble6<float><<<grid, blk, 0, ctx->stream>>>((float2 *)A, lda, n, dipf, p->pos, a6, khi, klo, k,
+                                                                 (float)n_env, (float)(1.0 / p->eps_env),
+                                                                 (float)(1.0 / n_env));
+                GDM_LAUNCHED(ctx, "assemble6_f32");
+            }
         }
     }
     return GDM_OK;
@@ -1031,32 +1122,59 @@ __global__ void k_nearfield_finalize(const double2 *__restrict__ partial, int nc
     }
 }
 
+gdm_status gdm_ff_green_sum(gdm_ctx *ctx, const gdm_problem *p, const void *tgt, int64_t m, int out,
+                            const double2 *P, int rhs0, int nr, int64_t chunk, int nchunks, void *ffws,
+                            double2 *partial, int prepare);
+gdm_status gdm_ff_targets(gdm_ctx *ctx, const double *r, int64_t m, void *out);
+size_t gdm_ff_target_bytes(int64_t m);
+size_t gdm_ff_scratch_bytes(int64_t n);
+
+// Near fields by repropagation. The Green sums run in double-float arithmetic on the FP32 pipes (the
+// refinement residual's kernel with separate evaluation points and both field blocks); GDM_NEARFIELD_FP64
+// selects FP64 sums on the FP64 pipe instead.
 gdm_status gdm_launch_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double *F, const double *r_eval, int64_t m,
                                 const double *F0_eval, int n_rhs, double *E_out, double *H_out) {
     const int64_t n = p->n;
     const int kind = p->kind;
     double k0 = gdm_k0(p), k = sqrt(p->eps_env) * k0;
     double d3_4pi = kind == 3 ? p->step * p->step * p->step / (4.0 * PI_D) : 0.0;
+    const bool ff = !getenv("GDM_NEARFIELD_FP64");
     size_t need = ScratchCarver::round((size_t)kind * n * n_rhs * sizeof(double2)) +
                   ScratchCarver::round(gdm_green_partial_bytes(ctx, m, n, 6)) + 1024;
+    if (ff) need += ScratchCarver::round(gdm_ff_scratch_bytes(n)) + ScratchCarver::round(gdm_ff_target_bytes(m));
     void *ws;
     GDM_TRY(gdm_scratch(ctx, need, &ws));
     ScratchCarver sc(ws);
     double2 *Pbuf = sc.take<double2>((size_t)kind * n * n_rhs);
     double2 *partial = sc.take<double2>(gdm_green_partial_bytes(ctx, m, n, 6) / sizeof(double2));
+    void *ffws = ff ? sc.take<char>(gdm_ff_scratch_bytes(n)) : nullptr;
+    void *tgt = ff ? sc.take<char>(gdm_ff_target_bytes(m)) : nullptr;
     dim3 g1((unsigned)((n + 127) / 128), (unsigned)n_rhs);
     k_moments<<<g1, 128, 0, ctx->stream>>>((const double2 *)F, n, kind, n_rhs, (const double2 *)p->eps, p->eps_env,
                                             d3_4pi, (const double2 *)p->alpha6, 0, Pbuf);
     GDM_LAUNCHED(ctx, "moments");
+    if (ff) GDM_TRY(gdm_ff_targets(ctx, r_eval, m, tgt));
     for (int q0 = 0; q0 < n_rhs; q0 += 2) {
         int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
         int nc;
-        if (kind == 3)
+        if (ff) {
+            int64_t chunk;
+            green_grid(ctx, m, n, &chunk, &nc);
+            GDM_TRY(gdm_ff_green_sum(ctx, p, tgt, m, 6, Pbuf, q0, nr, chunk, nc, ffws, partial, q0 == 0));
+        } else if (kind == 3)
             GDM_TRY(launch_green_sum<3, 6>(ctx, r_eval, m, p->pos, Pbuf, n, q0, nr, k, k0, 1.0 / p->eps_env, 0,
                                            partial, &nc));
         else
             GDM_TRY(launch_green_sum<6, 6>(ctx, r_eval, m, p->pos, Pbuf, n, q0, nr, k, k, 1.0, 0, partial, &nc));
-        const double sE = kind == 6 ? 1.0 / p->eps_env : 1.0, sH = kind == 6 ? 1.0 / sqrt(p->eps_env) : 1.0;
+        // rows: ED/MD sums use the vacuum-form dyad (E / eps_env, H / n_env); the cells' double-float cross
+        // term carries the 1/eps_env of the E kernel, so G^Hp p = n_env times it
+        double sE = 1.0, sH = 1.0;
+        if (kind == 6) {
+            sE = 1.0 / p->eps_env;
+            sH = 1.0 / sqrt(p->eps_env);
+        } else if (ff) {
+            sH = sqrt(p->eps_env);
+        }
         k_nearfield_finalize<6><<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(
             partial, nc, m, q0, nr, (const double2 *)F0_eval, n_rhs, sE, sH, (double2 *)E_out, (double2 *)H_out);
         GDM_LAUNCHED(ctx, "nearfield_finalize");

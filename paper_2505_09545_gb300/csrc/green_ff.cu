@@ -125,115 +125,218 @@ struct DipF {
 #define RF_T 128
 #define RF_S 32
 
-// partial[c][q][t][KIND] (FP64) = sum over sources j != t of chunk c of the dyad of (r_t - r_j) times P_j
+// Source records, one per source, laid out so that a tile of RF_S consecutive sources is one contiguous
+// block that a single bulk copy moves into shared memory: 8 floats (x, y, z hi; x, y, z lo; 2 pad), then
+// the moments of the NR right-hand sides of this launch as double-float complex numbers, float4
+// (re_hi, re_lo, im_hi, im_lo) per component, [KIND][NR].
+template <int KIND, int NR> struct SrcRecLayout {
+    static constexpr int FLOATS = 8 + 4 * KIND * NR;
+    static constexpr int BYTES = 4 * FLOATS;  // a multiple of 16
+};
+
 template <int KIND, int NR>
-__global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ dip, int64_t n,
-                                                      const double2 *__restrict__ P, int rhs0, int nr_here, float khi,
-                                                      float klo, float k2hi, float k2lo, float ie_hi, float ie_lo,
-                                                      const float4 *__restrict__ gtab, int64_t chunk,
-                                                      double2 *__restrict__ partial) {
+__global__ void k_prep_src(const DipF *__restrict__ dip, int64_t n, const double2 *__restrict__ P, int rhs0,
+                           int nr_here, float *__restrict__ rec) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float *o = rec + j * SrcRecLayout<KIND, NR>::FLOATS;
+    const DipF d = dip[j];
+    o[0] = d.xh;
+    o[1] = d.yh;
+    o[2] = d.zh;
+    o[3] = d.xl;
+    o[4] = d.yl;
+    o[5] = d.zl;
+    o[6] = 0.f;
+    o[7] = 0.f;
+    const int64_t ld = KIND * n;
+    float4 *m = (float4 *)(o + 8);
+#pragma unroll
+    for (int a = 0; a < KIND; a++)
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            double2 v = make_double2(0.0, 0.0);
+            if (q < nr_here) v = P[(rhs0 + q) * ld + KIND * j + a];
+            const float rh = (float)v.x, ih = (float)v.y;
+            m[a * NR + q] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+        }
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gtimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait (~2 s) for the phase of the given parity
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = gtimer_ns();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (gtimer_ns() - t0 > 2000000000ull) return false;
+    }
+}
+// one bulk copy global -> shared completing on an mbarrier (addresses 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// partial[c][q][t][OUT] (FP64) = sum over the sources j of chunk c (j != t when self_exclude) of the dyad of
+// (r_t - r_j) times the moments of source j: OUT = 3: G^Ep s (cells' residual); OUT = 6 with KIND = 3:
+// (G^Ep p, G^Hp-form cross term c (u x p)) (cells' near field); OUT = 6 with KIND = 6: the 6x6 vacuum-form
+// dyad on (p, n_env m) (ED/MD residual and near field). Targets and sources are FP32 (hi, lo) position
+// pairs. Source tiles (RF_S records) are double-buffered in shared memory by bulk copies issued one tile
+// ahead by one thread; every wait on them is bounded (on timeout the device error record gets
+// GDM_ERR_TIMEOUT and the CTA stops summing).
+template <int KIND, int OUT, int NR>
+__global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ tgt, int64_t m,
+                                                      const float *__restrict__ rec, int64_t n, float khi, float klo,
+                                                      float k2hi, float k2lo, float ie_hi, float ie_lo,
+                                                      const float4 *__restrict__ gtab, int64_t chunk, int self_exclude,
+                                                      double2 *__restrict__ partial, int *flags) {
+    using L = SrcRecLayout<KIND, NR>;
     __shared__ float4 tab[257];
-    __shared__ float sxyz[RF_S][6];
-    __shared__ float4 sm[RF_S][KIND][NR];  // (re_hi, re_lo, im_hi, im_lo)
+    __shared__ __align__(16) float sbuf[2][RF_S * L::FLOATS];
+    __shared__ uint64_t bar[2];
+    __shared__ int abort_cta;
     for (int e = threadIdx.x; e < 257; e += RF_T) tab[e] = gtab[e];
     const int64_t t = (int64_t)blockIdx.x * RF_T + threadIdx.x;
-    const bool valid = t < n;
+    const bool valid = t < m;
     const int64_t c = blockIdx.y;
     const int64_t jb = c * chunk, je = min(n, jb + chunk);
-    DipF ti = valid ? dip[t] : dip[0];
+    const int ntile = je > jb ? (int)((je - jb + RF_S - 1) / RF_S) : 0;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_cta = 0;
+    }
+    __syncthreads();
+    auto tile_src = [&](int it, uint32_t *bytes) {
+        const int64_t s0 = jb + (int64_t)it * RF_S;
+        *bytes = (uint32_t)(min((int64_t)RF_S, je - s0) * L::BYTES);
+        return rec + s0 * L::FLOATS;
+    };
+    if (threadIdx.x == 0 && ntile > 0) {
+        uint32_t by;
+        const float *src = tile_src(0, &by);
+        bulk_load(sbuf[0], src, by, &bar[0]);
+    }
+    const DipF ti = valid ? tgt[t] : tgt[0];
     const ff kf = mk(khi, klo), k2 = mk(k2hi, k2lo), ie = mk(ie_hi, ie_lo);
-    cff acc[NR][KIND];
+    cff acc[NR][OUT];
 #pragma unroll
     for (int q = 0; q < NR; q++)
 #pragma unroll
-        for (int a = 0; a < KIND; a++) acc[q][a] = {mk(0, 0), mk(0, 0)};
-    const int64_t ld = KIND * n;
-    for (int64_t s0 = jb; s0 < je; s0 += RF_S) {
+        for (int a = 0; a < OUT; a++) acc[q][a] = {mk(0, 0), mk(0, 0)};
+    int it = 0;
+    for (; it < ntile; it++) {
+        const int b = it & 1;
+        // the other buffer was read in the previous iteration, which every thread has left (barrier below)
+        if (threadIdx.x == 0 && it + 1 < ntile) {
+            uint32_t by;
+            const float *src = tile_src(it + 1, &by);
+            bulk_load(sbuf[b ^ 1], src, by, &bar[b ^ 1]);
+        }
+        const int64_t s0 = jb + (int64_t)it * RF_S;
         const int sn = (int)min((int64_t)RF_S, je - s0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < sn; e += RF_T) {
-            DipF d = dip[s0 + e];
-            sxyz[e][0] = d.xh;
-            sxyz[e][1] = d.yh;
-            sxyz[e][2] = d.zh;
-            sxyz[e][3] = d.xl;
-            sxyz[e][4] = d.yl;
-            sxyz[e][5] = d.zl;
+        const bool landed = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1));
+        if (!landed) {
+            abort_cta = 1;
+            gdm_dev_error(flags, GDM_ERR_TIMEOUT, 3);
         }
-        for (int e = threadIdx.x; e < sn * KIND * NR; e += RF_T) {
-            int jj = e / (KIND * NR), rem = e % (KIND * NR), a = rem / NR, q = rem % NR;
-            double2 v = make_double2(0.0, 0.0);
-            if (q < nr_here) v = P[(rhs0 + q) * ld + KIND * (s0 + jj) + a];
-            float rh = (float)v.x, ih = (float)v.y;
-            sm[jj][a][q] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
-        }
-        __syncthreads();
-        if (!valid) continue;
-        for (int jj = 0; jj < sn; jj++) {
-            if (s0 + jj == t) continue;
-            ff dx = add(two_sum(ti.xh, -sxyz[jj][0]), mk(__fsub_rn(ti.xl, sxyz[jj][3]), 0.f));
-            ff dy = add(two_sum(ti.yh, -sxyz[jj][1]), mk(__fsub_rn(ti.yl, sxyz[jj][4]), 0.f));
-            ff dz = add(two_sum(ti.zh, -sxyz[jj][2]), mk(__fsub_rn(ti.zl, sxyz[jj][5]), 0.f));
-            ff r2 = add(add(sqr(dx), sqr(dy)), sqr(dz));
-            ff r = ffsqrt(r2);
-            ff r1 = recip(r);
-            ff ri2 = sqr(r1);
-            ff ri3 = mul(ri2, r1);
-            ff u[3] = {mul(dx, r1), mul(dy, r1), mul(dz, r1)};
-            cff e = expi_ff(mul(kf, r), tab);
-            e = cscaleff(e, ie);
-            ff k2r1 = mul(k2, r1);
-            ff kri2 = mul(kf, ri2);
-            // a = e (k^2/R - 1/R^3 + i k/R^2),  b = e (3/R^3 - k^2/R - 3 i k/R^2)
-            cff ca = {sub(k2r1, ri3), kri2};
-            cff cb = {sub(mulf(ri3, 3.0f), k2r1), neg(mulf(kri2, 3.0f))};
-            cff a = cmulff(e, ca), b = cmulff(e, cb);
-            // magnetic-electric coupling (kind 6): c = e (k^2/R + i k/R^2)
-            cff cc = {mk(0, 0), mk(0, 0)};
-            if (KIND == 6) cc = cmulff(e, cff{k2r1, kri2});
+        if (valid && landed) {
+            const float *tb = sbuf[b];
+            for (int jj = 0; jj < sn; jj++) {
+                if (self_exclude && s0 + jj == t) continue;
+                const float *sr = tb + jj * L::FLOATS;
+                ff dx = add(two_sum(ti.xh, -sr[0]), mk(__fsub_rn(ti.xl, sr[3]), 0.f));
+                ff dy = add(two_sum(ti.yh, -sr[1]), mk(__fsub_rn(ti.yl, sr[4]), 0.f));
+                ff dz = add(two_sum(ti.zh, -sr[2]), mk(__fsub_rn(ti.zl, sr[5]), 0.f));
+                ff r2 = add(add(sqr(dx), sqr(dy)), sqr(dz));
+                ff r = ffsqrt(r2);
+                ff r1 = recip(r);
+                ff ri2 = sqr(r1);
+                ff ri3 = mul(ri2, r1);
+                ff u[3] = {mul(dx, r1), mul(dy, r1), mul(dz, r1)};
+                cff e = expi_ff(mul(kf, r), tab);
+                e = cscaleff(e, ie);
+                ff k2r1 = mul(k2, r1);
+                ff kri2 = mul(kf, ri2);
+                // a = e (k^2/R - 1/R^3 + i k/R^2),  b = e (3/R^3 - k^2/R - 3 i k/R^2)
+                cff ca = {sub(k2r1, ri3), kri2};
+                cff cb = {sub(mulf(ri3, 3.0f), k2r1), neg(mulf(kri2, 3.0f))};
+                cff a = cmulff(e, ca), bb = cmulff(e, cb);
+                // electric-magnetic coupling: c = e (k^2/R + i k/R^2)
+                cff cc = {mk(0, 0), mk(0, 0)};
+                if (OUT == 6) cc = cmulff(e, cff{k2r1, kri2});
+                const float4 *mom = (const float4 *)(sr + 8);
 #pragma unroll
-            for (int q = 0; q < NR; q++) {
+                for (int q = 0; q < NR; q++) {
 #pragma unroll
-                for (int h = 0; h < KIND / 3; h++) {  // h = 0: electric part, h = 1: magnetic part
-                    cff s[3];
-#pragma unroll
-                    for (int aa = 0; aa < 3; aa++) {
-                        float4 v = sm[jj][3 * h + aa][q];
-                        s[aa] = {mk(v.x, v.y), mk(v.z, v.w)};
-                    }
-                    cff us = {add(add(mul(u[0], s[0].re), mul(u[1], s[1].re)), mul(u[2], s[2].re)),
-                              add(add(mul(u[0], s[0].im), mul(u[1], s[1].im)), mul(u[2], s[2].im))};
-                    cff bus = cmulff(b, us);
-#pragma unroll
-                    for (int aa = 0; aa < 3; aa++) {
-                        cff v = caddff(cmulff(a, s[aa]), cscaleff(bus, u[aa]));
-                        acc[q][3 * h + aa] = caddff(acc[q][3 * h + aa], v);
-                    }
-                    if (KIND == 6) {
-                        // u x s, added as +c (u x p) to the magnetic rows (h = 0) or -c (u x m) to the electric
-                        // rows (h = 1)
-                        cff x[3];
-                        x[0] = {sub(mul(u[1], s[2].re), mul(u[2], s[1].re)), sub(mul(u[1], s[2].im), mul(u[2], s[1].im))};
-                        x[1] = {sub(mul(u[2], s[0].re), mul(u[0], s[2].re)), sub(mul(u[2], s[0].im), mul(u[0], s[2].im))};
-                        x[2] = {sub(mul(u[0], s[1].re), mul(u[1], s[0].re)), sub(mul(u[0], s[1].im), mul(u[1], s[0].im))};
+                    for (int h = 0; h < KIND / 3; h++) {  // h = 0: electric moment, h = 1: magnetic moment
+                        cff sv[3];
 #pragma unroll
                         for (int aa = 0; aa < 3; aa++) {
-                            cff v = cmulff(cc, x[aa]);
-                            if (h == 0) acc[q][3 + aa] = caddff(acc[q][3 + aa], v);
-                            else acc[q][aa] = caddff(acc[q][aa], cff{neg(v.re), neg(v.im)});
+                            const float4 v = mom[(3 * h + aa) * NR + q];
+                            sv[aa] = {mk(v.x, v.y), mk(v.z, v.w)};
+                        }
+                        cff us = {add(add(mul(u[0], sv[0].re), mul(u[1], sv[1].re)), mul(u[2], sv[2].re)),
+                                  add(add(mul(u[0], sv[0].im), mul(u[1], sv[1].im)), mul(u[2], sv[2].im))};
+                        cff bus = cmulff(bb, us);
+#pragma unroll
+                        for (int aa = 0; aa < 3; aa++) {
+                            cff v = caddff(cmulff(a, sv[aa]), cscaleff(bus, u[aa]));
+                            acc[q][3 * h + aa] = caddff(acc[q][3 * h + aa], v);
+                        }
+                        if (OUT == 6) {
+                            // u x s, added as +c (u x p) to the magnetic rows (h = 0) or -c (u x m) to the electric
+                            // rows (h = 1)
+                            cff x[3];
+                            x[0] = {sub(mul(u[1], sv[2].re), mul(u[2], sv[1].re)),
+                                    sub(mul(u[1], sv[2].im), mul(u[2], sv[1].im))};
+                            x[1] = {sub(mul(u[2], sv[0].re), mul(u[0], sv[2].re)),
+                                    sub(mul(u[2], sv[0].im), mul(u[0], sv[2].im))};
+                            x[2] = {sub(mul(u[0], sv[1].re), mul(u[1], sv[0].re)),
+                                    sub(mul(u[0], sv[1].im), mul(u[1], sv[0].im))};
+#pragma unroll
+                            for (int aa = 0; aa < 3; aa++) {
+                                cff v = cmulff(cc, x[aa]);
+                                if (h == 0) acc[q][3 + aa] = caddff(acc[q][3 + aa], v);
+                                else acc[q][aa] = caddff(acc[q][aa], cff{neg(v.re), neg(v.im)});
+                            }
                         }
                     }
                 }
             }
         }
+        __syncthreads();
+        if (abort_cta) break;
+    }
+    if (abort_cta && threadIdx.x == 0 && it + 1 < ntile) {
+        // the copy issued for the next tile must land before the CTA's shared memory goes away
+        mbar_wait_bounded(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1));
     }
     if (!valid) return;
 #pragma unroll
     for (int q = 0; q < NR; q++) {
-        if (q >= nr_here) break;
-        double2 *o = partial + ((c * 2 + q) * n + t) * KIND;
+        double2 *o = partial + ((c * 2 + q) * m + t) * OUT;
 #pragma unroll
-        for (int a = 0; a < KIND; a++)
+        for (int a = 0; a < OUT; a++)
             o[a] = make_double2((double)acc[q][a].re.hi + (double)acc[q][a].re.lo,
                                 (double)acc[q][a].im.hi + (double)acc[q][a].im.lo);
     }
@@ -263,7 +366,12 @@ void split(double v, float *h, float *l) {
 
 }  // namespace
 
-size_t gdm_ff_scratch_bytes(int64_t n) { return ScratchCarver::round(n * sizeof(DipF)) + 257 * 16 + 512; }
+// workspace: the sources' FP32-pair positions (DipF records, first, so that other kernels can use them),
+// the (cos, sin) table of the phase reduction, and the source records of one launch (up to KIND 6, NR 2)
+size_t gdm_ff_scratch_bytes(int64_t n) {
+    return ScratchCarver::round(n * sizeof(DipF)) + ScratchCarver::round(257 * 16) +
+           ScratchCarver::round((size_t)n * SrcRecLayout<6, 2>::BYTES) + 512;
+}
 
 // the hi/lo FP32 position pairs (48-byte records) that gdm_launch_green_sum_ff prepares at the start of its
 // workspace; valid after a call with prepare = 1 on the same problem
@@ -293,33 +401,67 @@ gdm_status gdm_ff_prepare(gdm_ctx *ctx, const gdm_problem *p, void *ffws) {
     return GDM_OK;
 }
 
-// Same output as the FP64 Green sum used by the residual (partial sums per chunk, two RHS per launch).
-gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const double2 *P, int rhs0, int nr,
-                                   int64_t chunk, int nchunks, void *ffws, double2 *partial, int prepare) {
+namespace {
+template <int KIND, int OUT, int NR>
+gdm_status launch_ff(gdm_ctx *ctx, const DipF *tgt, int64_t m, const DipF *dip, int64_t n, const double2 *P, int rhs0,
+                     int nr, float *rec, const float *kk, const float4 *tab, int64_t chunk, int nchunks,
+                     int self_exclude, double2 *partial) {
+    k_prep_src<KIND, NR><<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(dip, n, P, rhs0, nr, rec);
+    GDM_LAUNCHED(ctx, "prep_src");
+    dim3 grid((unsigned)((m + RF_T - 1) / RF_T), (unsigned)nchunks);
+    k_green_sum_ff<KIND, OUT, NR><<<grid, RF_T, 0, ctx->stream>>>(tgt, m, rec, n, kk[0], kk[1], kk[2], kk[3], kk[4],
+                                                                   kk[5], tab, chunk, self_exclude, partial,
+                                                                   ctx->dflags);
+    GDM_LAUNCHED(ctx, "green_sum_ff");
+    return GDM_OK;
+}
+}  // namespace
+
+// Double-float Green sums from the problem's dipoles (moments P: (KIND n) x n_rhs, right-hand sides
+// rhs0 .. rhs0 + nr - 1, nr <= 2) to m targets. tgt = NULL: the targets are the dipoles themselves, each
+// without its own term (the residual); otherwise FP32-pair target positions (gdm_ff_targets). out = KIND for
+// the residual, 6 for near fields. partial[c][q][t][out] as the FP64 Green sum writes it.
+gdm_status gdm_ff_green_sum(gdm_ctx *ctx, const gdm_problem *p, const void *tgt, int64_t m, int out,
+                            const double2 *P, int rhs0, int nr, int64_t chunk, int nchunks, void *ffws,
+                            double2 *partial, int prepare) {
     const int64_t n = p->n;
     ScratchCarver sc(ffws);
     DipF *dip = sc.take<DipF>(n);
     float4 *tab = sc.take<float4>(257);
+    float *rec = (float *)sc.take<char>((size_t)n * SrcRecLayout<6, 2>::BYTES);
     if (prepare) GDM_TRY(gdm_ff_prepare(ctx, p, ffws));
     const double k = sqrt(p->eps_env) * gdm_k0(p);
-    float khi, klo, k2hi, k2lo, iehi, ielo;
-    split(k, &khi, &klo);
-    split(k * k, &k2hi, &k2lo);
-    split(p->kind == 6 ? 1.0 : 1.0 / p->eps_env, &iehi, &ielo);  // kind 6: the vacuum-form kernel T
-    dim3 grid((unsigned)((n + RF_T - 1) / RF_T), (unsigned)nchunks);
+    float kk[6];
+    split(k, &kk[0], &kk[1]);
+    split(k * k, &kk[2], &kk[3]);
+    // the E kernel of cells carries 1/eps_env; ED/MD sums run the vacuum-form kernel (rows scaled afterwards)
+    split(p->kind == 6 ? 1.0 : 1.0 / p->eps_env, &kk[4], &kk[5]);
+    const DipF *t = tgt ? (const DipF *)tgt : dip;
+    const int self = tgt ? 0 : 1;
+    if (!tgt) m = n;
     if (p->kind == 6) {
-        if (nr == 1)
-            k_green_sum_ff<6, 1><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo,
-                                                                 tab, chunk, partial);
-        else
-            k_green_sum_ff<6, 2><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo,
-                                                                 tab, chunk, partial);
-    } else if (nr == 1)
-        k_green_sum_ff<3, 1><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo, tab,
-                                                             chunk, partial);
-    else
-        k_green_sum_ff<3, 2><<<grid, RF_T, 0, ctx->stream>>>(dip, n, P, rhs0, nr, khi, klo, k2hi, k2lo, iehi, ielo, tab,
-                                                             chunk, partial);
-    GDM_LAUNCHED(ctx, "green_sum_ff");
+        if (nr == 1) return launch_ff<6, 6, 1>(ctx, t, m, dip, n, P, rhs0, nr, rec, kk, tab, chunk, nchunks, self, partial);
+        return launch_ff<6, 6, 2>(ctx, t, m, dip, n, P, rhs0, nr, rec, kk, tab, chunk, nchunks, self, partial);
+    }
+    if (out == 6) {
+        if (nr == 1) return launch_ff<3, 6, 1>(ctx, t, m, dip, n, P, rhs0, nr, rec, kk, tab, chunk, nchunks, self, partial);
+        return launch_ff<3, 6, 2>(ctx, t, m, dip, n, P, rhs0, nr, rec, kk, tab, chunk, nchunks, self, partial);
+    }
+    if (nr == 1) return launch_ff<3, 3, 1>(ctx, t, m, dip, n, P, rhs0, nr, rec, kk, tab, chunk, nchunks, self, partial);
+    return launch_ff<3, 3, 2>(ctx, t, m, dip, n, P, rhs0, nr, rec, kk, tab, chunk, nchunks, self, partial);
+}
+
+// Same output as the FP64 Green sum used by the residual (partial sums per chunk, two RHS per launch).
+gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const double2 *P, int rhs0, int nr,
+                                   int64_t chunk, int nchunks, void *ffws, double2 *partial, int prepare) {
+    return gdm_ff_green_sum(ctx, p, nullptr, p->n, p->kind, P, rhs0, nr, chunk, nchunks, ffws, partial, prepare);
+}
+
+// FP32-pair positions of m evaluation points (48-byte records into out, m of them)
+gdm_status gdm_ff_targets(gdm_ctx *ctx, const double *r, int64_t m, void *out) {
+    k_prep_dipf_pos<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(r, m, (DipF *)out);
+    GDM_LAUNCHED(ctx, "prep_dipf_pos");
     return GDM_OK;
 }
+
+size_t gdm_ff_target_bytes(int64_t m) { return (size_t)m * sizeof(DipF); }
