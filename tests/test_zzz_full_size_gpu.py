@@ -1,12 +1,15 @@
-"""Parity at the benchmark's full sizes, in the configurations bench.py times, on outputs the oracle can
-compute one by one: the exact FP64 residual rows F0 - A F of a seeded sample of cells (relative to |F0|
-there), the incident field at those cells, and the cross sections from the oracle's formula applied to
-the GPU fields. The 40 x 30 x 10 cuboid (3N = 36,000) with TF32 factors refined to a relative correction
-of 1e-10, as bench.py runs it; the 256 Eden blobs (50 to 1,500 cells each) in one gdm_solve_batched call,
-every item's cross sections, and three sampled items (the smallest, the largest, one seeded) against the
-oracle's dense solve; the 1,970-cell cylinder's gradients at one wavelength against the oracle's
-adjoint. The file sorts last so that its long cases run after the quick ones.
+"""Parity at the benchmark's full sizes, in the configurations bench.py times. The 40 x 30 x 10 cuboid
+(3N = 36,000) with TF32 factors refined to a relative correction of 1e-10, as bench.py runs it: every
+field element against the oracle's dense FP64 solution of the same system (stored once under
+tests/golden/ by oracle/make_golden_cuboid.py, which calls only the oracle), the cross sections against
+the oracle's, the exact FP64 residual rows F0 - A F of a seeded sample of cells (relative to |F0|
+there) and the incident field at those cells; the 256 Eden blobs (50 to 1,500 cells each) in one
+gdm_solve_batched call, every item's cross sections, and three sampled items (the smallest, the largest,
+one seeded) against the oracle's dense solve; the 1,970-cell cylinder's gradients at one wavelength
+against the oracle's adjoint. The file sorts after the quick ones so that its long cases run late.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -16,6 +19,7 @@ import oracle as O
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cuboid40x30x10_oracle.npz")
 
 
 @pytest.fixture(scope="module")
@@ -52,6 +56,14 @@ def test_cuboid_40x30x10_full_size(G):
     finally:
         ctx.close()
     assert info["status"] == 0 and info["rel_correction"] <= 1e-10, info
+    # every element of both fields against the oracle's dense FP64 solve: ||dF_q|| / ||F_q|| <= 1e-9
+    gold = np.load(GOLDEN)
+    Fo = gold["F"]
+    assert Fo.shape == Fh.shape
+    err = np.linalg.norm(Fh - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+    assert np.all(err < 1e-9), (err, info)
+    for g, o in zip((ext, sca, ab), gold["sigma"]):
+        np.testing.assert_allclose(g, o, rtol=1e-9, atol=1e-9 * np.abs(gold["sigma"][0]).max())
     pr = O.Problem(s.pos, lam, 3, eps=s.eps, step=s.step)
     rel, rows = sampled_residual(pr, F0h, Fh, 48, seed=5)
     assert rel < 1e-10, (rel, info)
@@ -63,6 +75,31 @@ def test_cuboid_40x30x10_full_size(G):
     for g, o in zip((ext, sca, ab), xo):
         np.testing.assert_allclose(g, o, rtol=1e-9, atol=1e-9 * np.abs(xo[0]).max())
 
+
+
+def test_cuboid_nearfield_map_full_size(G):
+    """The near-field leg of bench.py at its size: the 320 x 320 map 50 nm above the 40 x 30 x 10 cuboid (102,400
+    points x 12,000 dipoles, E and H, both illuminations) from the oracle's stored fields, so that the kernel alone
+    is compared: 64 seeded points against the oracle's repropagation, 1e-10 relative to the largest field value."""
+    gold = np.load(GOLDEN)
+    Fo = gold["F"]
+    s = W.cuboid_precision()
+    lam = float(s.wavelengths[0])
+    r = W.nearfield_plane(320, 400.0, 100.0)
+    ctx = G.Context(0)
+    try:
+        prob = G.GDMProblem(t(s.pos), lam, 3, eps=t(s.eps), step=s.step)
+        E, H = G.nearfield(ctx, prob, t(Fo.T), t(r))
+        pick = np.sort(np.random.default_rng(11).choice(r.shape[0], 64, replace=False))
+        Eg = E.cpu().numpy().reshape(2, -1, 3)[:, pick]
+        Hg = H.cpu().numpy().reshape(2, -1, 3)[:, pick]
+    finally:
+        ctx.close()
+    pr = O.Problem(s.pos, lam, 3, eps=s.eps, step=s.step)
+    Eo, Ho = pr.nearfield(Fo, r[pick], s.e0, with_incident=False)   # (64, 3, n_rhs)
+    Eo, Ho = Eo.transpose(2, 0, 1), Ho.transpose(2, 0, 1)
+    assert np.abs(Eg - Eo).max() <= 1e-10 * np.abs(Eo).max()
+    assert np.abs(Hg - Ho).max() <= 1e-10 * np.abs(Ho).max()
 
 def test_blob_batch_256_full_size(G):
     ss = W.blob_batch()
