@@ -437,6 +437,322 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------- CTA-pair variant (TF32, one product)
+// The same update with 256-row tiles on a CTA pair (a cluster of two CTAs on two SMs): tcgen05.mma with
+// cta_group::2 multiplies a 256 x 32 A slab (128 rows in each CTA's shared memory) by a 32 x N B slab whose
+// columns are split between the two CTAs (N/2 each), into 128 x N accumulators in each CTA's tensor memory.
+// Each CTA fetches only its own half of A and of B, so per pair a B tile crosses L2 once where two
+// independent CTAs fetched it twice: operand traffic per flop falls by a third, and the 32 KB stages (against
+// 48 KB) leave room for five of them and four C chunk buffers (two C loads in flight ahead of the epilogue,
+// whose read-modify-write of C otherwise waits on one HBM round trip per 32-column chunk).
+//   leader CTA (rank 0): warp 0 TMA producer (its halves), warp 1 MMA issuer for the pair, warps 2-5 epilogue
+//     of rows 0..127 of each tile;
+//   peer CTA (rank 1):   warp 0 TMA producer (its halves), warps 2-5 epilogue of rows 128..255.
+// Both producers complete their copies on the leader's stage barrier (which expects both CTAs' bytes); the
+// MMA commits release the stage in both CTAs and signal both CTAs' epilogues; both epilogues release an
+// accumulator on the leader's barrier. Every wait is bounded as in k_tc_update.
+constexpr int PBM = 256;         // rows of the real embedding per pair tile (MMA M)
+constexpr int PBN = 256;         // columns per pair tile (MMA N); each CTA holds PBN / 2 of B
+constexpr int P_STAGES = 5;
+constexpr int P_NCB = 4;          // C chunk buffers: loads run P_NCB / 2 chunks ahead of the subtraction
+constexpr int P_A_BYTES = 128 * BK * 4;
+constexpr int P_B_BYTES = (PBN / 2) * BK * 4;
+constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;
+constexpr int P_CB_BYTES = 128 * 32 * 4;
+constexpr int P_SMEM = P_STAGES * P_STAGE_BYTES + P_NCB * P_CB_BYTES + 1024 + 512;
+constexpr int P_TMEM_COLS = 2 * PBN;
+// D = F32, A = B = TF32, both K-major, M = 256, N = PBN
+constexpr uint32_t P_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(PBN >> 3) << 17) |
+                             ((uint32_t)(PBM >> 4) << 24);
+__device__ __forceinline__ uint32_t p_idesc_n(int n_cols) {
+    return (P_IDESC & ~(0x3Fu << 17)) | ((uint32_t)(n_cols >> 3) << 17);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// 2D tile load into this CTA's shared memory, completing on an mbarrier that may sit in the peer CTA
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int x, int y, uint32_t bar_cluster) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cluster)
+        : "memory");
+}
+__device__ __forceinline__ void umma_tf32_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+            dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+// arrive once on the mbarrier at this shared-memory offset in both CTAs of the pair when the pair's MMAs
+// issued so far have completed
+__device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    k_tc_update_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmC, int cx0, int cy0, int M, int N, int K, int bx0, int by0,
+                     int *gflags) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(base + P_STAGES * P_STAGE_BYTES);
+    uint64_t *full = bars;                     // [P_STAGES] (leader's are used)
+    uint64_t *empty = bars + P_STAGES;         // [P_STAGES]
+    uint64_t *tfull = bars + 2 * P_STAGES;     // [2]
+    uint64_t *tempty = tfull + 2;              // [2]   (leader's are used)
+    uint64_t *drain = tempty + 2;              // [1]
+    uint64_t *cbar = drain + 1;                // [P_NCB]
+    float *cbuf = (float *)(base + P_STAGES * P_STAGE_BYTES + 512);
+    uint32_t *tmem_slot = (uint32_t *)(cbar + P_NCB);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    const int nk = (K + BK - 1) / BK;
+    TileMap tm{(M + PBM - 1) / PBM, (N + PBN - 1) / PBN, 8};
+    const int ntiles = tm.num_m * tm.num_n;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P_STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);  // four epilogue warps in each CTA
+        }
+        mbar_init(drain, 1);
+        for (int b = 0; b < P_NCB; b++) mbar_init(&cbar[b], 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)P_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    // both CTAs' barriers are initialised before any copy or arrival crosses to the other CTA
+    cluster_sync_all();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer (both CTAs): this CTA's 128 rows of A and PBN/2 columns of B
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int issued = 0;
+            for (int t = pair; t < ntiles && !*abort_flag; t += npairs) {
+                int mt, nt;
+                tm.get(t, mt, nt);
+                const int ncol = 32 * tm.chunks(nt, N, PBN);  // MMA N of this tile
+                for (int kc = 0; kc < nk; kc++) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, gflags)) break;
+                    unsigned char *st = base + s * P_STAGE_BYTES;
+                    const uint32_t fb = mapa_rank(smem_u32(&full[s]), 0);
+                    if (leader) mbar_expect_tx(&full[s], 2 * P_STAGE_BYTES);
+                    tma_load_2d_pair(st, &tmA, kc * BK, mt * PBM + (int)rank * 128, fb);
+                    tma_load_2d_pair(st + P_A_BYTES, &tmB, bx0 + kc * BK, by0 + nt * PBN + (int)rank * (ncol / 2), fb);
+                    issued++;
+                    if (++s == P_STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            if (*abort_flag && leader) {
+                // let the copies already expected land before the pair's shared memory goes away
+                int s2 = s, ph2 = ph;
+                for (int i = 0; i < P_STAGES && i < issued; i++) {
+                    if (--s2 < 0) {
+                        s2 = P_STAGES - 1;
+                        ph2 ^= 1;
+                    }
+                    uint64_t t0 = gtimer();
+                    while (!mbar_try_wait(&full[s2], ph2) && gtimer() - t0 < 2000000000ull) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (leader only)
+        if (lane == 0 && leader) {
+            int s = 0;
+            uint32_t ph = 0;
+            int lt = 0;
+            bool issued_any = false;
+            for (int t = pair; t < ntiles && !*abort_flag; t += npairs, lt++) {
+                const int b = lt & 1;
+                const uint32_t tph = (lt >> 1) & 1;
+                if (!mbar_wait(&tempty[b], tph ^ 1, abort_flag, gflags)) break;
+                tc_fence_after();
+                const uint32_t dt = tmem_base + (uint32_t)(b * PBN);
+                int mt_i, nt_i;
+                tm.get(t, mt_i, nt_i);
+                const uint32_t idesc = p_idesc_n(32 * tm.chunks(nt_i, N, PBN));
+                bool ok = true;
+                for (int kc = 0; kc < nk; kc++) {
+                    if (!mbar_wait(&full[s], ph, abort_flag, gflags)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(base + s * P_STAGE_BYTES);
+                    const uint64_t a0 = desc_sw128(sa);
+                    const uint64_t b0 = desc_sw128(sa + P_A_BYTES);
+#pragma unroll
+                    for (int k = 0; k < BK / 8; k++) {
+                        const uint64_t ko = (uint64_t)(2 * k);
+                        umma_tf32_pair(dt, a0 + ko, b0 + ko, idesc, (kc | k) ? 1u : 0u);
+                    }
+                    issued_any = true;
+                    umma_commit_pair(&empty[s]);
+                    if (++s == P_STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+                if (!ok) break;
+                umma_commit_pair(&tfull[b]);
+            }
+            // all MMAs of the pair complete before tensor memory is released (the commit reaches both CTAs)
+            if (issued_any) umma_commit_pair(drain);
+            else mbar_arrive_cluster(mapa_rank(smem_u32(drain), 1)), mbar_arrive(drain);
+        }
+        if (lane == 0) {
+            uint64_t t0 = gtimer();
+            while (!mbar_try_wait(drain, 0) && gtimer() - t0 < 2000000000ull) {
+            }
+        }
+    } else {
+        // ---------------- epilogue (both CTAs): rows rank*128 .. +128 of each tile, as in k_tc_update
+        const int q = warp & 3;
+        const int et = threadIdx.x - 64;  // 0..127
+        const bool eleader = (et == 0);
+        const uint32_t tempty_leader0 = mapa_rank(smem_u32(&tempty[0]), 0);
+        const uint32_t tempty_leader1 = mapa_rank(smem_u32(&tempty[1]), 0);
+        // valid 32-column chunks of a tile for this CTA: none when its 128 rows lie beyond M
+        auto tile_chunks = [&](int lt2, int &mt, int &nt) {
+            tm.get(pair + lt2 * npairs, mt, nt);
+            if (mt * PBM + (int)rank * 128 >= M) return 0;
+            return tm.chunks(nt, N, PBN);
+        };
+        int total = 0;
+        for (int lt2 = 0; pair + lt2 * npairs < ntiles; lt2++) {
+            int mt, nt;
+            total += tile_chunks(lt2, mt, nt);
+        }
+        int ld_lt = 0, ld_ch = 0;
+        auto issue_load = [&](int g) {
+            int mt, nt;
+            int nch = tile_chunks(ld_lt, mt, nt);
+            while (nch == 0) nch = tile_chunks(++ld_lt, mt, nt);
+            const int b = g % P_NCB;
+            mbar_expect_tx(&cbar[b], P_CB_BYTES);
+            tma_load_2d(cbuf + (size_t)b * (P_CB_BYTES / 4), &tmC, cx0 + mt * PBM + (int)rank * 128,
+                        cy0 + nt * PBN + ld_ch * 32, &cbar[b]);
+            if (++ld_ch == nch) {
+                ld_ch = 0;
+                ld_lt++;
+            }
+        };
+        if (eleader)
+            for (int g = 0; g < P_NCB / 2 && g < total; g++) issue_load(g);
+        int g = 0;
+        const int row = q * 32 + lane;
+        volatile int *dec = (volatile int *)(abort_flag + 1);
+        int dc = 0;
+        auto agree = [&](bool leader_ok) -> bool {
+            if (eleader) dec[dc & 1] = leader_ok ? 1 : 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            bool r = dec[dc & 1] != 0;
+            dc++;
+            return r;
+        };
+        int lt = 0;
+        for (int t = pair; t < ntiles; t += npairs, lt++) {
+            const int b = lt & 1;
+            const uint32_t tph = (lt >> 1) & 1;
+            bool ok = true;
+            if (eleader) ok = mbar_wait(&tfull[b], tph, abort_flag, gflags);
+            if (!agree(ok)) break;
+            tc_fence_after();
+            bool alive = true;
+            int mt_c, nt_c;
+            const int nch = tile_chunks(lt, mt_c, nt_c);
+#pragma unroll 1
+            for (int ch = 0; ch < nch; ch++, g++) {
+                const int cb = g % P_NCB;
+                ok = true;
+                if (eleader) {
+                    if (g + P_NCB / 2 < total) {
+                        bulk_wait_read<P_NCB - P_NCB / 2 - 1>();
+                        issue_load(g + P_NCB / 2);
+                    }
+                    ok = mbar_wait(&cbar[cb], (uint32_t)((g / P_NCB) & 1), abort_flag, gflags);
+                }
+                float v[32];
+                tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * PBN + ch * 32), v);
+                if (!agree(ok)) {
+                    alive = false;
+                    break;
+                }
+                float *buf = cbuf + (size_t)cb * (P_CB_BYTES / 4);
+#pragma unroll
+                for (int j = 0; j < 32; j++) buf[j * 128 + row] -= v[j];
+                fence_proxy_async_smem();
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (eleader) {
+                    tma_store_2d(&tmC, buf, cx0 + mt_c * PBM + (int)rank * 128, cy0 + nt_c * PBN + ch * 32);
+                    bulk_commit();
+                }
+            }
+            if (!alive) break;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(b ? tempty_leader1 : tempty_leader0);
+        }
+        if (eleader) bulk_wait_all();
+    }
+    tc_fence_before();
+    __syncthreads();
+    // no CTA of the pair leaves while the other may still signal its barriers or share its tensor memory
+    cluster_sync_all();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"((uint32_t)P_TMEM_COLS)
+                     : "memory");
+    }
+}
+
 // ---------------------------------------------------------------- operand preparation
 __device__ __forceinline__ float tf32_round(float x) {
     uint32_t r;
@@ -556,6 +872,48 @@ gdm_status launch_update(gdm_ctx *ctx, const CUtensorMap &a0, const CUtensorMap 
     return GDM_OK;
 }
 
+// CTA pairs that fit on the GPU at once with the pair kernel's shared memory (a persistent grid larger than
+// that would leave some pairs waiting for others to finish)
+int max_pairs(gdm_ctx *ctx) {
+    static int cached = -1;
+    if (cached < 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(ctx->sm_count & ~1));
+        cfg.blockDim = dim3(NTHREADS);
+        cfg.dynamicSmemBytes = P_SMEM;
+        cudaLaunchAttribute at;
+        at.id = cudaLaunchAttributeClusterDimension;
+        at.val.clusterDim.x = 2;
+        at.val.clusterDim.y = 1;
+        at.val.clusterDim.z = 1;
+        cfg.attrs = &at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_update_pair, &cfg) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = 0;
+        }
+        cached = n;
+    }
+    return cached;
+}
+
+gdm_status launch_update_pair(gdm_ctx *ctx, const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &cm,
+                              int cx0, int cy0, int M, int N, int K, int bx0, int by0) {
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_update_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM));
+        attr = true;
+    }
+    const int np = max_pairs(ctx);
+    if (np < 1) return GDM_ERR_UNSUPPORTED;
+    const int ntiles = ((M + PBM - 1) / PBM) * ((N + PBN - 1) / PBN);
+    const int pairs = ntiles < np ? ntiles : np;
+    k_tc_update_pair<<<2 * pairs, NTHREADS, P_SMEM, ctx->stream>>>(a, b, cm, cx0, cy0, M, N, K, bx0, by0, ctx->dflags);
+    GDM_LAUNCHED(ctx, "tc_update_pair");
+    return GDM_OK;
+}
+
 }  // namespace
 
 size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec) {
@@ -612,11 +970,26 @@ gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_
         GDM_TRY(launch_update<128, 3>(ctx, ta0, ta1, tb0, tb1, tc, (int)(2 * r0), (int)c0, M, N, K, 0, 0));
     } else {
         // U straight from its storage: real rows [2 u_r0, 2 u_r0 + K) of columns [u_c0, u_c0 + Nc) (zero beyond)
-        ok = ok && make_map(&tb0, (const float *)U, (uint64_t)2 * ldu, (uint64_t)(u_c0 + Nc), (uint64_t)2 * ldu, 256);
+        // 256-row tiles on CTA pairs (each CTA loads 128 columns of U), unless the update has fewer rows
+        // (narrow GEMMs, the in-block updates of at most 256 columns, keep the single-CTA tiles, which do
+        // better there)
+        const bool pair = M >= PBM && N >= 2 * PBN && !getenv("GDM_TC_SINGLE");
+        ok = ok && make_map(&tb0, (const float *)U, (uint64_t)2 * ldu, (uint64_t)(u_c0 + Nc), (uint64_t)2 * ldu,
+                            pair ? PBN / 2 : 256);
         if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         if (prof) GDM_TRY(gdm_prof_begin(ctx, &slot));
-        GDM_TRY(launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * u_r0),
-                                      (int)u_c0));
+        gdm_status st = GDM_ERR_UNSUPPORTED;
+        if (pair)
+            st = launch_update_pair(ctx, ta0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * u_r0), (int)u_c0);
+        if (st == GDM_ERR_UNSUPPORTED) {
+            if (pair) {
+                ok = make_map(&tb0, (const float *)U, (uint64_t)2 * ldu, (uint64_t)(u_c0 + Nc), (uint64_t)2 * ldu, 256);
+                if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+            }
+            st = launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * u_r0),
+                                       (int)u_c0);
+        }
+        GDM_TRY(st);
     }
     if (prof) GDM_TRY(gdm_prof_end(ctx, slot, fl, by));
     return GDM_OK;
