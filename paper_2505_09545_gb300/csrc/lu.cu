@@ -358,112 +358,167 @@ __device__ __forceinline__ float rcp_nr(float x) {
     return r * fmaf(-x, r, 2.0f);
 }
 
-// FP32 version of the same panel with the diagonal block held in registers: lane q of warp 0 keeps row q
-// of D. Instead of moving rows, each lane tracks the position its row occupies in the LAPACK-style swap
-// sequence (pos), so the pivot of step t is the largest |re|+|im| in column t among the rows not yet
-// chosen, ties going to the lowest current position, exactly as with explicit swaps (two warp
-// reductions: the maximum of the magnitudes' bit patterns, then the lowest position attaining it);
-// ipiv[t] is the position the chosen row occupied. The chosen row publishes itself in shared memory
-// (double-buffered by step parity, so one warp barrier per step suffices) and the other rows take the
-// multiplier and update their remaining columns from it. The rows below then solve x U = a by forward
-// substitution against U in shared memory (independent updates of the remaining columns), with the
-// same certificate as above.
+// FP32 version of the same panel, written as compact loops: every CTA factors the 32 x 32 diagonal block in
+// warp 0 and then solves its rows below, and straight-line code for either part (the 32 steps unrolled) runs
+// once per warp and stalls on instruction fetch, so both parts are runtime loops over the step k whose bodies
+// touch registers at fixed indices only. A lane keeps the not yet eliminated part of its row shifted to the
+// front of a register window, x[i] = column k + i, so that column k is always x[0]; each step removes x[0]
+// and shifts the window by one while it subtracts the multiple of the pivot row. U is kept in shared memory
+// in position order, zero-padded to 64 columns, so the window's reads past column 31 see zeros.
+// Pivoting as in k_panel_local: lane q of warp 0 holds row q of the diagonal block and tracks the position
+// its row occupies in the LAPACK-style swap sequence (pos); the pivot of step t is the largest |re|+|im| in
+// column t among the rows not yet chosen, ties going to the lowest current position (two warp reductions:
+// the maximum of the magnitudes' bit patterns, then the lowest position attaining it); ipiv[t] is the
+// position the chosen row occupied. The rows below solve x U = a by forward substitution, in four phases
+// whose windows shrink with the remaining columns (32, 24, 16, 8), with the growth certificate of
+// k_panel_local.
+__device__ __forceinline__ float2 cmul_inv_piv(float2 a, float2 piv) {
+    // a / piv with 1/piv = conj(piv/sc) / (|piv/sc|^2 sc) (scaled against overflow), reciprocals from the
+    // hardware approximation refined by one Newton step
+    const float sc = fmaxf(fabsf(piv.x), fabsf(piv.y));
+    if (!(sc > 0.f)) return make_float2(0.f, 0.f);
+    const float is = rcp_nr(sc);
+    const float ax = piv.x * is, ay = piv.y * is;
+    const float rr = rcp_nr(fmaf(ax, ax, ay * ay) * sc);
+    return cmul(a, make_float2(ax * rr, -ay * rr));
+}
+
+// one forward-substitution step on a window of W unknowns (x[0] = column k): returns the multiplier and
+// shifts the window, x[i] <- x[i + 1] - l U[k][k + 1 + i]
+template <int W>
+__device__ __forceinline__ float2 subst_step(float2 *x, const float2 *__restrict__ Urow, float2 invd_k) {
+    const float2 l = cmul(x[0], invd_k);
+#pragma unroll
+    for (int i = 0; i < W - 1; i++) {
+        x[i] = x[i + 1];
+        cfms(x[i], l, Urow[1 + i]);
+    }
+    x[W - 1] = make_float2(0.f, 0.f);
+    return l;
+}
+
+// one elimination step of the diagonal block on a window of W columns (r[0] = column t). (m, key) is the
+// pivot of column t, found by the previous step: the chosen row publishes itself into U, the others take
+// their multiplier and the shifted update. Column t + 1 is updated first and its pivot search (two warp
+// reductions: the maximum of the magnitudes' bit patterns among the rows not yet chosen, then the lowest
+// position attaining it) is issued before the rest of the update, which hides the reductions' latency. The
+// update is unconditional (multiplier 0 for rows already chosen, whose registers are not read again).
+template <int W>
+__device__ __forceinline__ void diag_step(float2 *r, int t, int lane, int &pos, bool &done, unsigned &m,
+                                          unsigned &key, float2 (*Uz)[2 * NBP], float2 (*Lr)[NBP + 1], int64_t c0,
+                                          int32_t *__restrict__ ipiv, int *flags) {
+    if (blockIdx.x == 0 && lane == 0) {
+        ipiv[c0 + t] = (int32_t)(c0 + key);
+        if (!(__uint_as_float(m) > 0.f)) gdm_dev_error(flags, GDM_ERR_SINGULAR, (int)(c0 + t));
+    }
+    const bool is_p = !done && pos == (int)key;
+    if (is_p) {
+#pragma unroll
+        for (int i = 0; i < W; i++) Uz[t][t + i] = r[i];
+    }
+    // the row at position t moves to the pivot's old position
+    if (pos == t) pos = (int)key;
+    if (is_p) {
+        pos = t;
+        done = true;
+    }
+    __syncwarp();
+    const float2 l = done ? make_float2(0.f, 0.f) : cmul_inv_piv(r[0], Uz[t][t]);
+    Lr[lane][t] = l;
+    float2 n0 = r[1];
+    cfms(n0, l, Uz[t][t + 1]);
+    // |re|+|im| >= 0, so its bit pattern orders like the value
+    const unsigned vb = done ? 0u : __float_as_uint(fabsf(n0.x) + fabsf(n0.y));
+    m = __reduce_max_sync(0xffffffffu, vb);
+    key = __reduce_min_sync(0xffffffffu, (!done && vb == m) ? (unsigned)pos : 0xffffffffu);
+#pragma unroll
+    for (int i = 1; i < W - 1; i++) {
+        r[i] = r[i + 1];
+        cfms(r[i], l, Uz[t][t + 1 + i]);
+    }
+    r[0] = n0;
+    r[W - 1] = make_float2(0.f, 0.f);
+}
+
 __global__ void __launch_bounds__(128) k_panel_local_f32(float2 *__restrict__ A, int64_t lda, int64_t n, int64_t c0,
                                                          int w, int32_t *__restrict__ ipiv, unsigned *growth,
                                                          int *flags) {
-    __shared__ float2 U[NBP][NBP + 1];  // factored diagonal block in position order
+    __shared__ float2 Uz[NBP][2 * NBP];   // U in position order, row t = columns t.. ; zero elsewhere
+    __shared__ float2 Lr[NBP][NBP + 1];   // multipliers of lane q's row, by step
+    __shared__ float2 F[NBP][NBP + 1];    // factored diagonal block in position order (for the final store)
     __shared__ float2 invd[NBP];
-    __shared__ float2 prow[2][NBP];     // pivot row of the current step
+    __shared__ float inv_pa[NBP];
+    __shared__ int posof[NBP];
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t r_first = c0 + w + blockIdx.x * (int64_t)blockDim.x + tid;
     const int64_t r_step = (int64_t)gridDim.x * blockDim.x;
+    for (int e = tid; e < NBP * 2 * NBP; e += blockDim.x) (&Uz[0][0])[e] = make_float2(0.f, 0.f);
+    // the first row below is loaded while warp 0 factors the diagonal block
+    float2 x[NBP];
+#pragma unroll
+    for (int c = 0; c < NBP; c++)
+        x[c] = (c < w && r_first < n) ? A[(c0 + c) * lda + r_first] : make_float2(0.f, 0.f);
+    __syncthreads();
     if (tid < 32) {
-        float2 row[NBP];
+        float2 r[NBP];
 #pragma unroll
         for (int c = 0; c < NBP; c++) {
-            row[c] = make_float2(0.f, 0.f);
-            if (c < w && lane < w) row[c] = A[(c0 + c) * lda + c0 + lane];
+            r[c] = make_float2(0.f, 0.f);
+            if (c < w && lane < w) r[c] = A[(c0 + c) * lda + c0 + lane];
         }
         int pos = lane;         // current position of this lane's row
         bool done = lane >= w;  // chosen as a pivot row already (or outside the block)
-#pragma unroll
-        for (int t = 0; t < NBP; t++) {
-            if (t < w) {
-                // |re|+|im| >= 0, so its bit pattern orders like the value
-                const unsigned vb = done ? 0u : __float_as_uint(fabsf(row[t].x) + fabsf(row[t].y));
-                const unsigned m = __reduce_max_sync(0xffffffffu, vb);
-                const unsigned key = __reduce_min_sync(0xffffffffu, (!done && vb == m) ? (unsigned)pos : 0xffffffffu);
-                if (blockIdx.x == 0 && lane == 0) {
-                    ipiv[c0 + t] = (int32_t)(c0 + key);
-                    if (!(__uint_as_float(m) > 0.f)) gdm_dev_error(flags, GDM_ERR_SINGULAR, (int)(c0 + t));
-                }
-                const bool is_p = !done && pos == (int)key;
-                float2 *P = prow[t & 1];
-                if (is_p) {
-#pragma unroll
-                    for (int c = t; c < NBP; c++) P[c] = row[c];
-                }
-                // the row at position t moves to the pivot's old position
-                if (pos == t) pos = (int)key;
-                if (is_p) {
-                    pos = t;
-                    done = true;
-                }
-                __syncwarp();
-                if (!done) {
-                    const float2 piv = P[t];
-                    float2 l = make_float2(0.f, 0.f);
-                    const float sc = fmaxf(fabsf(piv.x), fabsf(piv.y));
-                    if (sc > 0.f) {
-                        // 1/piv = conj(piv/sc) / (|piv/sc|^2 sc), scaled against overflow; reciprocals from
-                        // the hardware approximation refined by one Newton step (on the critical path of
-                        // every pivot step, so no division subroutine here)
-                        const float is = rcp_nr(sc);
-                        const float ax = piv.x * is, ay = piv.y * is;
-                        const float rr = rcp_nr(fmaf(ax, ax, ay * ay) * sc);
-                        l = cmul(row[t], make_float2(ax * rr, -ay * rr));
-                    }
-                    row[t] = l;
-#pragma unroll
-                    for (int c = t + 1; c < NBP; c++) cfms(row[c], l, P[c]);
-                }
-            }
-        }
-        if (lane < w) {
-#pragma unroll
-            for (int c = 0; c < NBP; c++) U[pos][c] = row[c];
-        }
+        // pivot of column 0; every step then finds the next one
+        const unsigned vb0 = done ? 0u : __float_as_uint(fabsf(r[0].x) + fabsf(r[0].y));
+        unsigned m = __reduce_max_sync(0xffffffffu, vb0);
+        unsigned key = __reduce_min_sync(0xffffffffu, (!done && vb0 == m) ? (unsigned)pos : 0xffffffffu);
+        // windows shrink with the columns left: 32 - t <= W
+        int t = 0;
+#pragma unroll 1
+        for (; t < w && t < 8; t++) diag_step<32>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags);
+#pragma unroll 1
+        for (; t < w && t < 16; t++) diag_step<24>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags);
+#pragma unroll 1
+        for (; t < w && t < 24; t++) diag_step<16>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags);
+#pragma unroll 1
+        for (; t < w; t++) diag_step<8>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags);
+        if (lane < w) posof[lane] = pos;
     }
     __syncthreads();
     if (tid < w) {
-        const float2 d = U[tid][tid];
-        invd[tid] = (fabsf(d.x) + fabsf(d.y) > 0.f) ? crecip(d) : make_float2(0.f, 0.f);
+        const float2 d = Uz[tid][tid];
+        const float pa = fabsf(d.x) + fabsf(d.y);
+        invd[tid] = pa > 0.f ? crecip(d) : make_float2(0.f, 0.f);
+        inv_pa[tid] = pa > 0.f ? 1.0f / pa : 0.f;
+        const int p = posof[tid];
+        for (int c = 0; c < w; c++) F[p][c] = c < p ? Lr[tid][c] : Uz[p][c];
     }
     __syncthreads();
     float worst = 0.f;
     for (int64_t r = r_first; r < n; r += r_step) {
-        float2 x[NBP];
+        if (r != r_first) {
 #pragma unroll
-        for (int c = 0; c < NBP; c++) x[c] = (c < w) ? A[(c0 + c) * lda + r] : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < NBP; k++) {
-            if (k < w) {
-                const float2 ukk = U[k][k];
-                const float pa = fabsf(ukk.x) + fabsf(ukk.y);
-                if (pa > 0.f) worst = fmaxf(worst, (fabsf(x[k].x) + fabsf(x[k].y)) / pa);
-                const float2 l = cmul(x[k], invd[k]);
-                x[k] = l;
-#pragma unroll
-                for (int c = k + 1; c < NBP; c++) cfms(x[c], l, U[k][c]);
-            }
+            for (int c = 0; c < NBP; c++) x[c] = (c < w) ? A[(c0 + c) * lda + r] : make_float2(0.f, 0.f);
         }
-#pragma unroll
-        for (int c = 0; c < NBP; c++)
-            if (c < w) A[(c0 + c) * lda + r] = x[c];
+        int k = 0;
+#define PANEL_PHASE(W_, KEND)                                                                      \
+    for (; k < w && k < (KEND); k++) {                                                             \
+        worst = fmaxf(worst, (fabsf(x[0].x) + fabsf(x[0].y)) * inv_pa[k]);                         \
+        A[(c0 + k) * lda + r] = subst_step<W_>(x, &Uz[k][k], invd[k]);                             \
+    }
+#pragma unroll 1
+        PANEL_PHASE(32, 8)
+#pragma unroll 1
+        PANEL_PHASE(24, 16)
+#pragma unroll 1
+        PANEL_PHASE(16, 24)
+#pragma unroll 1
+        PANEL_PHASE(8, 32)
+#undef PANEL_PHASE
     }
     for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_down_sync(0xffffffffu, worst, o));
     if (lane == 0 && worst > 0.f) atomicMax(growth, __float_as_uint(worst));
-    panel_store_diag_last(A, lda, c0, w, &U[0][0], NBP + 1, flags);
+    panel_store_diag_last(A, lda, c0, w, &F[0][0], NBP + 1, flags);
 }
 
 // ------------------------------------------------------------------ block operator for the U12 row block
