@@ -932,24 +932,58 @@ __global__ void k_residual_finalize(const double2 *__restrict__ partial, int nch
     }
 }
 
-static void green_grid(gdm_ctx *ctx, int64_t m, int64_t n, int64_t *chunk, int *nchunks) {
-    int64_t tb = (m + GS_T - 1) / GS_T;
-    int64_t want = (4 * (int64_t)ctx->sm_count + tb - 1) / tb;
+// Grid of a Green-sum launch: ceil(m / GS_T) target blocks times nc source chunks (multiples of GS_S sources).
+// The kernels are ALU-bound and a CTA's time is about proportional to its chunk, so the last partial wave of
+// CTAs idles the rest of the GPU; nc is the number of chunks (at most 64) that wastes the least of the
+// occ x SMs resident-CTA slots over the whole launch (fewest chunks among equals).
+static void green_grid(gdm_ctx *ctx, int64_t m, int64_t n, int occ, int64_t *chunk, int *nchunks) {
+    const int64_t tb = (m + GS_T - 1) / GS_T;
+    const int64_t slots = (int64_t)(occ < 1 ? 1 : occ) * ctx->sm_count;
     int64_t maxc = (n + GS_S - 1) / GS_S;
-    int64_t nc = want < 1 ? 1 : (want > maxc ? maxc : want);
-    if (nc > 64) nc = 64;
-    int64_t ch = (n + nc - 1) / nc;
-    ch = (ch + GS_S - 1) / GS_S * GS_S;
-    *chunk = ch;
-    *nchunks = (int)((n + ch - 1) / ch);
+    if (maxc > 64) maxc = 64;
+    int64_t best_ch = (n + GS_S - 1) / GS_S * GS_S;
+    double best = -1.0;
+    for (int64_t nc = 1; nc <= maxc; nc++) {
+        const int64_t ch = ((n + nc - 1) / nc + GS_S - 1) / GS_S * GS_S;
+        const int64_t ctas = tb * ((n + ch - 1) / ch);
+        const int64_t waves = (ctas + slots - 1) / slots;
+        const double eff = (double)ctas / (double)(waves * slots);
+        if (eff > best + 1e-9) {
+            best = eff;
+            best_ch = ch;
+        }
+    }
+    *chunk = best_ch;
+    *nchunks = (int)((n + best_ch - 1) / best_ch);
 }
 
+// partial-sum bytes that any Green-sum launch over m targets and n sources may use (every occupancy the
+// kernels have: 1 to 8 resident CTAs per SM)
 size_t gdm_green_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n, int out) {
-    int64_t chunk;
-    int nc;
-    green_grid(ctx, m, n, &chunk, &nc);
-    return (size_t)nc * 2 * m * out * sizeof(double2);
+    int mx = 1;
+    for (int occ = 1; occ <= 8; occ++) {
+        int64_t chunk;
+        int nc;
+        green_grid(ctx, m, n, occ, &chunk, &nc);
+        if (nc > mx) mx = nc;
+    }
+    return (size_t)mx * 2 * m * out * sizeof(double2);
 }
+
+// resident CTAs per SM of a kernel launched with GS_T threads and no dynamic shared memory (cached per kernel)
+template <class K> static int occupancy_of(K kernel) {
+    static int cached = 0;
+    if (!cached) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, GS_T, 0) != cudaSuccess || b < 1) {
+            cudaGetLastError();
+            b = 4;
+        }
+        cached = b > 8 ? 8 : b;
+    }
+    return cached;
+}
+int gdm_ff_occupancy(int kind, int out, int nr);
 
 template <int KIND, int OUT>
 static gdm_status launch_green_sum(gdm_ctx *ctx, const double *tpos, int64_t m, const double *spos,
@@ -957,7 +991,7 @@ static gdm_status launch_green_sum(gdm_ctx *ctx, const double *tpos, int64_t m, 
                                    double inv_eps, int self_exclude, double2 *partial, int *nchunks_out) {
     int64_t chunk;
     int nc;
-    green_grid(ctx, m, n, &chunk, &nc);
+    green_grid(ctx, m, n, occupancy_of(k_green_sum<KIND, OUT, 2>), &chunk, &nc);
     dim3 grid((unsigned)((m + GS_T - 1) / GS_T), (unsigned)nc);
     k_green_sum<KIND, OUT, 2><<<grid, GS_T, 0, ctx->stream>>>(tpos, m, spos, P, n, rhs0, nr_here, k, k0, inv_eps,
                                                               chunk, self_exclude, partial);
@@ -1048,7 +1082,7 @@ gdm_status gdm_launch_residual_ws(gdm_ctx *ctx, const gdm_problem *p, const doub
         int nc;
         if (ffws) {
             int64_t chunk;
-            green_grid(ctx, n, n, &chunk, &nc);
+            green_grid(ctx, n, n, gdm_ff_occupancy(kind, kind, nr), &chunk, &nc);
             GDM_TRY(gdm_launch_green_sum_ff(ctx, p, Pbuf, q0, nr, chunk, nc, ffws, partial, ff_prepare && q0 == 0));
         } else if (kind == 3)
             GDM_TRY(launch_green_sum<3, 3>(ctx, p->pos, n, p->pos, Pbuf, n, q0, nr, k, k0, 1.0 / p->eps_env, 1,
@@ -1089,7 +1123,7 @@ gdm_status gdm_launch_residual_f32(gdm_ctx *ctx, const gdm_problem *p, const dou
         const int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
         int64_t chunk;
         int nc;
-        green_grid(ctx, n, n, &chunk, &nc);
+        green_grid(ctx, n, n, occupancy_of(k_green_sum_f32<2>), &chunk, &nc);
         dim3 grid((unsigned)((n + GS_T - 1) / GS_T), (unsigned)nc);
         k_green_sum_f32<2><<<grid, GS_T, 0, ctx->stream>>>((const DipF *)dipf, n, Pbuf, q0, nr, khi, klo,
                                                           (float)(1.0 / p->eps_env), chunk, partial);
@@ -1159,7 +1193,7 @@ gdm_status gdm_launch_nearfield(gdm_ctx *ctx, const gdm_problem *p, const double
         int nc;
         if (ff) {
             int64_t chunk;
-            green_grid(ctx, m, n, &chunk, &nc);
+            green_grid(ctx, m, n, gdm_ff_occupancy(kind, 6, nr), &chunk, &nc);
             GDM_TRY(gdm_ff_green_sum(ctx, p, tgt, m, 6, Pbuf, q0, nr, chunk, nc, ffws, partial, q0 == 0));
         } else if (kind == 3)
             GDM_TRY(launch_green_sum<3, 6>(ctx, r_eval, m, p->pos, Pbuf, n, q0, nr, k, k0, 1.0 / p->eps_env, 0,

@@ -451,6 +451,29 @@ gdm_status gdm_ff_green_sum(gdm_ctx *ctx, const gdm_problem *p, const void *tgt,
     return launch_ff<3, 3, 2>(ctx, t, m, dip, n, P, rhs0, nr, rec, kk, tab, chunk, nchunks, self, partial);
 }
 
+// resident CTAs per SM of the double-float kernel for (kind, out, nr) (cached; 4 if the query fails)
+namespace {
+template <int KIND, int OUT, int NR> int ff_occ() {
+    static int cached = 0;
+    if (!cached) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_green_sum_ff<KIND, OUT, NR>, RF_T, 0) != cudaSuccess ||
+            b < 1) {
+            cudaGetLastError();
+            b = 4;
+        }
+        cached = b > 8 ? 8 : b;
+    }
+    return cached;
+}
+}  // namespace
+
+int gdm_ff_occupancy(int kind, int out, int nr) {
+    if (kind == 6) return nr == 1 ? ff_occ<6, 6, 1>() : ff_occ<6, 6, 2>();
+    if (out == 6) return nr == 1 ? ff_occ<3, 6, 1>() : ff_occ<3, 6, 2>();
+    return nr == 1 ? ff_occ<3, 3, 1>() : ff_occ<3, 3, 2>();
+}
+
 // Same output as the FP64 Green sum used by the residual (partial sums per chunk, two RHS per launch).
 gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const double2 *P, int rhs0, int nr,
                                    int64_t chunk, int nchunks, void *ffws, double2 *partial, int prepare) {
