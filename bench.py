@@ -92,8 +92,8 @@ class ClockSampler:
 
 def cpu_oracle_sample(nx=18, ny=14, nz=10, target_n=12000):
     """The CPU FP64 oracle as it stands on a bounded sample of the workload: the same cuboid
-    recipe at nx*ny*nz cells, assembly + dense solve, scaled to N = target_n by N^2 (assembly)
-    and N^3 (solve)."""
+    recipe at nx*ny*nz cells, assembly + dense solve (LAPACK zgesv through numpy), scaled to N = target_n
+    by N^2 (assembly) and N^3 (solve)."""
     import numpy as np
     import gdm_workloads as W
     import oracle as O
@@ -108,10 +108,60 @@ def cpu_oracle_sample(nx=18, ny=14, nz=10, target_n=12000):
     ratio = target_n / s.n
     est = (t1 - t0) * ratio ** 2 + (t2 - t1) * ratio ** 3
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    if os.environ.get("OPENBLAS_NUM_THREADS") == "1":
+        cores = 1
     return {"value": est, "unit": "s", "cores": cores, "kind": "oracle",
+            "assembly_s": (t1 - t0) * ratio ** 2, "zgesv_s": (t2 - t1) * ratio ** 3,
             "sample": f"oracle assemble+solve of the same cuboid recipe at {nx}x{ny}x{nz} cells (N={s.n}, "
-                      f"{t2 - t0:.2f} s measured: assembly {t1 - t0:.2f} s, solve {t2 - t1:.2f} s), "
+                      f"{t2 - t0:.2f} s measured: assembly {t1 - t0:.2f} s, LAPACK zgesv {t2 - t1:.2f} s), "
                       f"scaled to N={target_n} by N^2 (assembly) and N^3 (solve)"}
+
+
+def cpu_oracle_one_core(nx=12, ny=10, nz=10):
+    """The same sample on one host core: a child process with one BLAS thread (the oracle's assembly is
+    single-threaded numpy already), so that the parent's BLAS pool is untouched."""
+    code = ("import json, bench; print(json.dumps(bench.cpu_oracle_sample(%d, %d, %d)))" % (nx, ny, nz))
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=300)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # the one-core figure is context only
+        return {"unavailable": f"{type(e).__name__}: {e}"}
+
+
+def oracle_full_size_records():
+    """Wall times of the oracle's full-size solve of the 40 x 30 x 10 cuboid (N = 12,000), measured once per
+    host by oracle/make_golden_cuboid.py and stored beside its golden fields."""
+    out = {}
+    for tag, name in (("dev_host_x86", "cuboid40x30x10_oracle.json"),
+                      ("gb300_host", "cuboid40x30x10_oracle_gb300_host.json")):
+        try:
+            with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+                r = json.load(f)
+            out[tag] = {"total_s": r["total_s"], "assembly_s": r["assembly_s"], "zgesv_s": r["solve_s"],
+                        "host": r["host"], "runs": 1}
+        except (OSError, KeyError, ValueError):
+            pass
+    return out
+
+
+def cpu_baseline_leg():
+    """cpu_baseline of the bench line: the bounded sample on all host cores (the value), its one-core
+    counterpart, and the stored full-size measurements."""
+    cb = cpu_oracle_sample()
+    cb["one_core"] = cpu_oracle_one_core()
+    cb["full_size_measured"] = oracle_full_size_records()
+    return cb
+
+
+def golden_fields():
+    """The oracle's dense FP64 solution of the 40 x 30 x 10 cuboid (tests/golden), or None."""
+    try:
+        import numpy as np
+        return np.load(os.path.join(ROOT, "tests", "golden", "cuboid40x30x10_oracle.npz"))["F"]
+    except Exception:
+        return None
 
 
 def adjoint_leg(G, ctx, dev, precision, warmup, steps):
@@ -160,28 +210,28 @@ def adjoint_leg(G, ctx, dev, precision, warmup, steps):
             "timing": "wall clock with device synchronisation, median of the timed repetitions"}
 
 
-def fp64_compare(G, ctx, dev, precision, cuboid, tol):
+def fp64_compare(G, ctx, dev, precision, cuboid, tol, golden=None):
     """The plain FP64 GPU path (FP64 assembly, FP64 LU, FP64 solve) against the mixed-precision path on
-    the same cuboid: seconds per assemble+solve and the relative field difference between the two."""
+    the same cuboid: seconds per assemble+solve and the relative field difference between the two (and,
+    where the oracle's stored solution of this cuboid exists, each path's error against it). The FP64
+    path is warmed up on a 3N = 1,800 cuboid (allocations, module loading) and timed once: one full-size
+    FP64 solve takes minutes, so its launch overheads are far below the timer's resolution."""
     import torch
     import gdm_workloads as W
     nx, ny, nz = (int(v) for v in cuboid.split("x"))
-    s = W.cuboid_precision(nx, ny, nz)
-    lam = float(s.wavelengths[0])
-    pos = torch.tensor(s.pos, device=dev)
-    prob = G.GDMProblem(pos, lam, 3, eps=torch.tensor(s.eps, device=dev), step=s.step)
-    F0 = G.incident_planewave(ctx, pos, lam, s.e0)
     out = {}
     fields = {}
-    for prec in ("fp64", precision):
+
+    def run(prec, nxyz, reps, t):
+        s = W.cuboid_precision(*nxyz)
+        lam = float(s.wavelengths[0])
+        pos = torch.tensor(s.pos, device=dev)
+        prob = G.GDMProblem(pos, lam, 3, eps=torch.tensor(s.eps, device=dev), step=s.step)
+        F0 = G.incident_planewave(ctx, pos, lam, s.e0)
         A = torch.empty((prob.size, G.padded_lda(prob.size)),
                         dtype=torch.complex128 if prec == "fp64" else torch.complex64, device=dev)
         ipiv = torch.empty(prob.size, dtype=torch.int32, device=dev)
         F = torch.empty_like(F0)
-        reps = 1 if prec == "fp64" else 3
-        t = 0.0 if prec == "fp64" else tol
-        G.assemble(ctx, prob, prec, out=A)
-        G.solve(ctx, prob, A, F0, prec, ipiv=ipiv, F=F, tol=t)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -190,14 +240,27 @@ def fp64_compare(G, ctx, dev, precision, cuboid, tol):
             G.solve(ctx, prob, A, F0, prec, ipiv=ipiv, F=F, tol=t)
         e1.record()
         torch.cuda.synchronize()
-        out[prec] = e0.elapsed_time(e1) / reps / 1e3
-        fields[prec] = F.clone()
         del A
+        return e0.elapsed_time(e1) / reps / 1e3, F, s
+
+    run("fp64", (10, 6, 10), 1, 0.0)                     # warm-up
+    out["fp64"], fields["fp64"], s = run("fp64", (nx, ny, nz), 1, 0.0)
+    run(precision, (nx, ny, nz), 1, tol)                 # warm-up
+    out[precision], fields[precision], _ = run(precision, (nx, ny, nz), 3, tol)
     d = (fields[precision] - fields["fp64"]).norm(dim=1) / fields["fp64"].norm(dim=1)
-    return {"workload": f"cuboid {nx}x{ny}x{nz} (3N={3 * s.n})", "fp64_s": out["fp64"],
-            f"{precision}_s": out[precision], "speedup": out["fp64"] / out[precision],
-            "rel_field_diff_vs_fp64": float(d.max()), "tol": tol,
-            "timing": "CUDA events; FP64 one timed repetition after one warm-up, mixed precision three"}
+    res = {"workload": f"cuboid {nx}x{ny}x{nz} (3N={3 * s.n})", "fp64_s": out["fp64"],
+           f"{precision}_s": out[precision], "speedup": out["fp64"] / out[precision],
+           "rel_field_diff_vs_fp64": float(d.max()), "tol": tol,
+           "fp64_tflops": 8.0 / 3.0 * (3.0 * s.n) ** 3 / out["fp64"] / 1e12,
+           "timing": "CUDA events; FP64 one timed run (after a warm-up on a 3N=1,800 cuboid), "
+                     "mixed precision the mean of three after one warm-up"}
+    if golden is not None and (nx, ny, nz) == (40, 30, 10):
+        import numpy as np
+        for prec in ("fp64", precision):
+            Fh = fields[prec].cpu().numpy().T
+            res[f"{prec}_field_err_vs_oracle"] = float(np.max(np.linalg.norm(Fh - golden, axis=0)
+                                                              / np.linalg.norm(golden, axis=0)))
+    return res
 
 
 def traffic_record(kernel_src):
@@ -220,20 +283,87 @@ def traffic_record(kernel_src):
         return None
 
 
-def run_metasurface(args):
-    """ED/MD metasurface: 64 x 64 dipoles (6N = 24,576), Lorentzian 6x6 polarisabilities, 32 wavelengths
-    500-800 nm, x- and y-polarised normal incidence; per wavelength on the GPU: polarisabilities,
-    incident field, assemble + mixed-precision LU + FP64-refined solve + cross sections. One step = all
-    32 wavelengths; the value is seconds per (lambda, N) solve."""
-    import numpy as np
+# FP32 thread instructions per (evaluation point, dipole) pair, 2 right-hand sides, E and H, of the near-field
+# kernel k_green_sum_ff<3, 6, 2> (ncu count: profiles/green_sum_ff_nearfield_cuboid20x15x10_ncu.md)
+NEARFIELD_INST_PER_PAIR = 2175.0
+
+
+def nearfield_leg(G, ctx, dev, prob, F, n_side=320, reps=5):
+    """Near field of the solved cuboid on a map above it: n_side^2 points (102,400 by default) on the plane
+    z = 100 nm (50 nm above the top face) spanning +-400 nm, E and H for both illuminations, by one
+    gdm_nearfield call (double-float Green sums over every (point, dipole) pair). Against the FP32 issue
+    peak: ncu instructions per pair x pairs / CUDA-event time of the whole call (moment and target
+    preparation, O(N + M), included)."""
+    import torch
+    import gdm_workloads as W
+    r = torch.tensor(W.nearfield_plane(n_side, 400.0, 100.0), device=dev)
+    m = r.shape[0]
+    G.nearfield(ctx, prob, F, r)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        E, H = G.nearfield(ctx, prob, F, r)
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / reps / 1e3
+    pairs = float(m) * prob.n
+    peak = 152 * 128 * 2.07e9
+    out = {"workload": f"{m} points (plane z=100 nm, +-400 nm) x {prob.n} dipoles, E and H, {F.shape[0]} RHS",
+           "s": s, "pairs_per_s": pairs / s}
+    if NEARFIELD_INST_PER_PAIR:
+        ach = pairs * NEARFIELD_INST_PER_PAIR / s
+        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "FP32 inst/s", "frac": ach / peak,
+                           "inst_per_pair": NEARFIELD_INST_PER_PAIR,
+                           "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock)"}
+    return out
+
+
+def run_nearfield(args):
+    """Near-field map of the solved 40 x 30 x 10 cuboid (N = 12,000): one step = one gdm_nearfield call over
+    320 x 320 points, E and H, both illuminations."""
     import torch
     import gdm_workloads as W
     import paper_2505_09545_gb300 as G
     ws, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    s = W.metasurface_edmd()
+    nx, ny, nz = (int(v) for v in args.cuboid.split("x"))
+    s = W.cuboid_precision(nx, ny, nz)
+    lam = float(s.wavelengths[0])
     ctx = G.Context(local)
+    pos = torch.tensor(s.pos, device=dev)
+    prob = G.GDMProblem(pos, lam, 3, eps=torch.tensor(s.eps, device=dev), step=s.step)
+    F0 = G.incident_planewave(ctx, pos, lam, s.e0)
+    A = G.assemble(ctx, prob, args.precision)
+    F, _, _ = G.solve(ctx, prob, A, F0, args.precision)
+    del A
+    for _ in range(max(1, args.warmup)):
+        nearfield_leg(G, ctx, dev, prob, F, args.nearfield_side, 1)
+    leg = nearfield_leg(G, ctx, dev, prob, F, args.nearfield_side, args.steps)
+    line = {"metric": "near-field map s", "value": leg["s"], "unit": "s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(1, args.warmup), "ms_per_step": leg["s"] * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2 (double-float)", "data": "synthetic",
+            "config": {"workload": f"cuboid {nx}x{ny}x{nz} (N={s.n}) solved fields; " + leg["workload"]},
+            "pairs_per_s": leg["pairs_per_s"], "roofline": leg.get("roofline")}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+
+
+def metasurface_leg(G, ctx, dev, precision, tol, eps_env, warmup, steps, peaks, units=None):
+    """ED/MD metasurface: 64 x 64 dipoles (6N = 24,576), Lorentzian 6x6 polarisabilities, 32 wavelengths
+    500-800 nm, x- and y-polarised normal incidence; per wavelength on the GPU: polarisabilities, incident
+    field, assemble + mixed-precision LU + FP64-refined solve + cross sections. One step = all 32
+    wavelengths; the value is seconds per (lambda, N) solve. Also: the assembly kernel alone against HBM,
+    and the whole wavelength's (8/3)(6N)^3 LU flops against the TF32 denominator. units = (lo, hi): only the
+    wavelengths [lo, hi) (this rank's share of the spectrum)."""
+    import numpy as np
+    import torch
+    import gdm_workloads as W
+    s = W.metasurface_edmd()
+    if units is not None:
+        s.wavelengths = s.wavelengths[units[0]:units[1]]
     pos = torch.tensor(s.pos, device=dev)
     ns = 6 * s.n
     A = torch.empty((ns, G.padded_lda(ns)), dtype=torch.complex64, device=dev)
@@ -248,64 +378,106 @@ def run_metasurface(args):
         infos.clear()
         for i, lam in enumerate(s.wavelengths):
             lam = float(lam)
-            G.alpha6_lorentz(ctx, w0e, w0m, s.gamma_ev, s.amp_nm, lam, out=al, eps_env=args.eps_env)
-            prob = G.GDMProblem(pos, lam, 6, alpha6=al, eps_env=args.eps_env)
-            F0 = G.incident_planewave(ctx, pos, lam, s.e0, kind_out=6, eps_env=args.eps_env)
+            G.alpha6_lorentz(ctx, w0e, w0m, s.gamma_ev, s.amp_nm, lam, out=al, eps_env=eps_env)
+            prob = G.GDMProblem(pos, lam, 6, alpha6=al, eps_env=eps_env)
+            F0 = G.incident_planewave(ctx, pos, lam, s.e0, kind_out=6, eps_env=eps_env)
             G.assemble(ctx, prob, "fp32", out=A)
-            F, _, info = G.solve(ctx, prob, A, F0, args.precision, ipiv=ipiv, tol=args.tol)
+            F, _, info = G.solve(ctx, prob, A, F0, precision, ipiv=ipiv, tol=tol)
             e, c, b = G.cross_sections(ctx, prob, F0, F, np.ones(2))
             sig[i, 0], sig[i, 1], sig[i, 2] = e, c, b
             infos.append(info)
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         step()
     torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record()
     torch.cuda.synchronize()
-    clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     nl = len(s.wavelengths)
     # one extra (untimed) wavelength with per-phase device-time accounting, plus its assembly alone
     lam = float(s.wavelengths[0])
-    G.alpha6_lorentz(ctx, w0e, w0m, s.gamma_ev, s.amp_nm, lam, out=al, eps_env=args.eps_env)
-    prob = G.GDMProblem(pos, lam, 6, alpha6=al, eps_env=args.eps_env)
-    F0 = G.incident_planewave(ctx, pos, lam, s.e0, kind_out=6, eps_env=args.eps_env)
+    G.alpha6_lorentz(ctx, w0e, w0m, s.gamma_ev, s.amp_nm, lam, out=al, eps_env=eps_env)
+    prob = G.GDMProblem(pos, lam, 6, alpha6=al, eps_env=eps_env)
+    F0 = G.incident_planewave(ctx, pos, lam, s.e0, kind_out=6, eps_env=eps_env)
+    G.assemble(ctx, prob, "fp32", out=A)
     torch.cuda.synchronize()
     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ea.record()
-    G.assemble(ctx, prob, "fp32", out=A)
+    for _ in range(5):
+        G.assemble(ctx, prob, "fp32", out=A)
     eb.record()
     torch.cuda.synchronize()
-    asm_ms = ea.elapsed_time(eb)
+    asm_ms = ea.elapsed_time(eb) / 5
+    asm_bytes = float(ns) * ns * 8
     ctx.phases(True)
-    G.solve(ctx, prob, A, F0, args.precision, ipiv=ipiv, tol=args.tol)
+    G.solve(ctx, prob, A, F0, precision, ipiv=ipiv, tol=tol)
     phases = {k: round(v, 2) for k, v in ctx.phases(False).items()}
-    line = {"metric": METRIC, "value": ms / 1e3 / nl, "unit": "s", "n_gpus": 1, "steps": args.steps,
-            "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64-tf32+f64" if args.precision == "tf32" else args.precision,
-            "data": "synthetic",
-            "config": {"workload": f"ED/MD metasurface 64x64, pitch 400 nm (6N={ns}), Lorentzian alpha_e, alpha_m "
-                                   f"omega0~U[2,3] eV, width 0.1 eV, seed 4; {nl} wavelengths 500-800 nm, x/y-pol; "
-                                   "assemble + LU + FP64-refined solve + cross sections per wavelength; host "
-                                   f"eps_env={args.eps_env:g}; relative correction <= {args.tol:g}",
-                       "precision": args.precision,
-                       "l2": "inputs larger than L2 (4.8 GB complex64 matrix rewritten per wavelength)"},
+    per_lam = ms / 1e3 / nl
+    tf32_peak = peaks["bf16_tflops_sustained"] * NOMINAL_TF32_OVER_BF16
+    lu_flops = 8.0 / 3.0 * float(ns) ** 3
+    del A
+    return {"value": per_lam, "unit": "s", "steps": steps, "ms_per_step": ms,
+            "workload": f"ED/MD metasurface 64x64, pitch 400 nm (6N={ns}), Lorentzian alpha_e, alpha_m omega0~U[2,3] "
+                        f"eV, width 0.1 eV, seed 4; {nl} wavelengths 500-800 nm, x/y-pol; assemble + LU + "
+                        f"FP64-refined solve + cross sections per wavelength; host eps_env={eps_env:g}; relative "
+                        f"correction <= {tol:g}",
             "accuracy": {"max_refine_iters": max(i["iterations"] for i in infos),
                          "max_rel_residual_fp64": max(i["rel_residual"] for i in infos),
                          "refactored": int(sum(bool(i["refactored"]) for i in infos))},
-            "sigma_ext_range_nm2": [float(sig[:, 0].min()), float(sig[:, 0].max())],
+            "sigma_ext_range_nm2": [float(sig[:, 0].min()), float(sig[:, 0].max())], "sigma": sig,
             "phases_ms_one_wavelength": phases,
-            "assembly_ms_one_wavelength": asm_ms,
-            "clocks": clocks}
+            "assembly_roofline": {"bound": "hbm", "achieved": asm_bytes / (asm_ms / 1e3) / 1e9,
+                                  "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                  "frac": asm_bytes / (asm_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "ms": asm_ms,
+                                  "bytes": asm_bytes, "kernel": "assemble A = I - G alpha, 6x6 blocks"},
+            "lu_tensor_frac_whole_wavelength": {"flops": lu_flops, "tflops": lu_flops / per_lam / 1e12,
+                                                "peak": tf32_peak, "frac": lu_flops / per_lam / 1e12 / tf32_peak,
+                                                "note": "(8/3)(6N)^3 over the whole wavelength's time (assembly, "
+                                                        "panels, solves and refinement included)"}}
+
+
+def run_metasurface(args):
+    """The ED/MD metasurface workload as its own line (see metasurface_leg). Under torchrun the 32 wavelengths
+    are split contiguously across the ranks (independent units, no collective on the data path); the job's
+    time is the slowest rank's and the cross sections are gathered once at the end."""
+    import torch
+    import paper_2505_09545_gb300 as G
+    from paper_2505_09545_gb300 import shard
+    import gdm_workloads as W
+    ws, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if ws > 1:
+        torch.distributed.init_process_group("nccl")
+    n_units = len(W.metasurface_edmd().wavelengths)
+    lo, hi = shard.unit_range(n_units, ws, rank)
+    ctx = G.Context(local)
+    peaks, _ = load_peaks()
+    clk = ClockSampler(local)
+    clk.start()
+    leg = metasurface_leg(G, ctx, dev, args.precision, args.tol, args.eps_env, args.warmup, args.steps, peaks,
+                          units=(lo, hi))
+    clocks = clk.stop()
+    ms = max_over_ranks(leg.pop("ms_per_step"), ws, dev)
+    sig = shard.gather_units(leg.pop("sigma"), lo, n_units)
+    leg.pop("value")
+    line = {"metric": METRIC, "value": ms / 1e3 / n_units, "unit": leg.pop("unit"), "n_gpus": ws,
+            "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "strong" if ws > 1 else "weak", "vs_baseline": None,
+            "dtype": "c64-tf32+f64" if args.precision == "tf32" else args.precision, "data": "synthetic",
+            "config": {"workload": leg.pop("workload"), "precision": args.precision,
+                       "parallelism": f"wavelengths split contiguously over {ws} rank(s)",
+                       "l2": "inputs larger than L2 (4.8 GB complex64 matrix rewritten per wavelength)"},
+            **leg, "sigma_ext_range_nm2": [float(sig[:, 0].min()), float(sig[:, 0].max())], "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_batch(args):
@@ -317,10 +489,16 @@ def run_batch(args):
     import torch
     import gdm_workloads as W
     import paper_2505_09545_gb300 as G
+    from paper_2505_09545_gb300 import shard
     ws, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    ss = W.blob_batch()
+    if ws > 1:
+        torch.distributed.init_process_group("nccl")
+    ss_all = W.blob_batch()
+    # under torchrun: contiguous ranges of structures with near-equal LU work (3N)^3 per rank
+    lo, hi = shard.weighted_unit_range([(3.0 * s.n) ** 3 for s in ss_all], ws, rank)
+    ss = ss_all[lo:hi]
     ctx = G.Context(local)
     probs = [G.GDMProblem(torch.tensor(s.pos, device=dev), float(s.wavelengths[0]), 3,
                           eps=torch.tensor(s.eps, device=dev), step=s.step) for s in ss]
@@ -347,18 +525,20 @@ def run_batch(args):
     torch.cuda.synchronize()
     clocks = clk.stop()
     launches = ctx.launches - l0
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws, dev)
     infos = out[2]
-    flops = sum(8.0 / 3.0 * n ** 3 for n in sizes)
-    line = {"metric": METRIC, "value": ms / 1e3 / len(ss), "unit": "s", "n_gpus": 1, "steps": args.steps,
-            "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+    flops = sum(8.0 / 3.0 * (3.0 * s.n) ** 3 for s in ss_all)
+    line = {"metric": METRIC, "value": ms / 1e3 / len(ss_all), "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "strong" if ws > 1 else "weak",
             "vs_baseline": None, "dtype": "c64-tf32+f64" if args.precision == "tf32" else args.precision,
             "data": "synthetic",
-            "config": {"workload": f"{len(ss)} Eden blobs, N~U{{50..1500}} cells (sum N={sum(s.n for s in ss)}), "
+            "config": {"workload": f"{len(ss_all)} Eden blobs, N~U{{50..1500}} cells (sum N={sum(s.n for s in ss_all)}), "
                                    "d=15 nm, eps~U[2,16], own lambda~U[400,1000] nm each, x/y-pol; plane wave + "
                                    "assemble + LU + FP64-refined solve + cross sections, one gdm_solve_batched call",
                        "precision": args.precision, "streams": args.streams or 8,
                        "lu_block_table": table,
+                       "parallelism": f"structures split contiguously over {ws} rank(s) by LU work",
                        "l2": f"inputs larger than L2 ({sum(n * n for n in sizes) * 8 / 1e9:.1f} GB of complex64 "
                              "matrices rewritten every step)"},
             "batch_s": ms / 1e3, "lu_tflops_effective": flops / (ms / 1e3) / 1e12,
@@ -369,6 +549,8 @@ def run_batch(args):
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_gpm(args):
@@ -617,6 +799,7 @@ def run_reference(args):
     v = statistics.mean(times)
     cb = dict(last)
     cb["value"] = v
+    cb["full_size_measured"] = oracle_full_size_records()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -648,14 +831,16 @@ def main():
                          "(measured and reported in 'accuracy'), inside the metric's 1e-9")
     ap.add_argument("--cuboid", default="40x30x10",
                     help="cells per axis of the cuboid workload (smaller cases are for profiling only)")
-    ap.add_argument("--fp64-cuboid", default="20x15x10",
-                    help="cuboid of the FP64-GPU-path comparison (40x30x10 = the full workload, ~2 min)")
+    ap.add_argument("--fp64-cuboid", default="40x30x10",
+                    help="cuboid of the FP64-GPU-path comparison (default the full workload, ~2 min)")
     ap.add_argument("--workload", default="cuboid",
-                    choices=["cuboid", "metasurface", "batch", "gpm", "farfield", "ldos", "gmres"],
+                    choices=["cuboid", "metasurface", "batch", "gpm", "farfield", "ldos", "gmres", "nearfield"],
                     help="cuboid: the headline assemble+solve line; metasurface: 64x64 ED/MD array, 32 wavelengths; "
                          "batch: 256 uneven blobs, each at its own wavelength; gpm: effective-model extraction; "
                          "farfield: far-field sigma_sca of the solved cuboid; ldos: electric LDOS around the sphere; "
-                         "gmres: matrix-free preconditioned GMRES on a larger cuboid")
+                         "gmres: matrix-free preconditioned GMRES on a larger cuboid; nearfield: E and H map of the "
+                         "solved cuboid")
+    ap.add_argument("--nearfield-side", type=int, default=320, help="nearfield workload: points per side of the map")
     ap.add_argument("--gmres-cuboid", default="80x60x10", help="gmres workload: cells per axis")
     ap.add_argument("--eps-env", type=float, default=1.0, help="metasurface workload: host permittivity")
     ap.add_argument("--streams", type=int, default=0, help="batch workload: concurrent streams (0 = default)")
@@ -683,6 +868,8 @@ def main():
         return run_ldos(args)
     if args.workload == "gmres":
         return run_gmres(args)
+    if args.workload == "nearfield":
+        return run_nearfield(args)
 
     ws, rank, local = dist_setup()
     if ws > 1:
@@ -693,7 +880,7 @@ def main():
     torch.cuda.set_device(dev)
     cpu_base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu_base = cpu_oracle_sample()  # before any GPU work of this process
+        cpu_base = cpu_baseline_leg()  # before any GPU work of this process
 
     nx, ny, nz = (int(v) for v in args.cuboid.split("x"))
     s = W.cuboid_precision(nx, ny, nz)
@@ -748,6 +935,12 @@ def main():
     F_ref = torch.empty_like(F)
     G.solve(ctx, prob, A, F0, args.precision, ipiv=ipiv, F=F_ref, factored=True, tol=1e-12)
     field_err = float(((F - F_ref).norm(dim=1) / F_ref.norm(dim=1)).max())
+    # and against the oracle's dense FP64 solution of the same system, where it is stored
+    golden = golden_fields() if args.cuboid == "40x30x10" else None
+    oracle_err = None
+    if golden is not None:
+        Fh = F.cpu().numpy().T
+        oracle_err = float(np.max(np.linalg.norm(Fh - golden, axis=0) / np.linalg.norm(golden, axis=0)))
 
     # one extra (untimed) step with per-phase device-time accounting
     ctx.phases(True)
@@ -794,7 +987,10 @@ def main():
     extras = {}
     if not args.no_extras:
         extras["adjoint"] = adjoint_leg(G, ctx, dev, args.precision, args.warmup, args.steps)
-        extras["fp64_gpu_path"] = fp64_compare(G, ctx, dev, args.precision, args.fp64_cuboid, args.tol)
+        extras["nearfield"] = nearfield_leg(G, ctx, dev, prob, F)
+        extras["metasurface"] = metasurface_leg(G, ctx, dev, args.precision, args.tol, 1.0, 1, 1, load_peaks()[0])
+        extras["metasurface"].pop("sigma")
+        extras["fp64_gpu_path"] = fp64_compare(G, ctx, dev, args.precision, args.fp64_cuboid, args.tol, golden)
 
     peaks, peak_src = load_peaks()
     per_launch_ms = prof["ms"] / max(1, prof["launches"])
@@ -827,7 +1023,8 @@ def main():
             "vs_baseline": None, "dtype": "c64-tf32+f64" if args.precision == "tf32" else
             ("c64-3xtf32+f64" if args.precision == "fp32" else "f64"),
             "data": "synthetic", "config": workload_config(args),
-            "accuracy": {"tol": args.tol, "field_err_vs_solve_to_1e-12": field_err,
+            "accuracy": {"tol": args.tol, "field_err_vs_oracle": oracle_err,
+                         "field_err_vs_solve_to_1e-12": field_err,
                          "refine_iters": it["iterations"], "rel_correction": it["rel_correction"],
                          "rel_residual_fp64": it["rel_residual"], "factor_ms": it["factor_ms"],
                          "refine_ms": it["refine_ms"]},
