@@ -263,11 +263,13 @@ def fp64_compare(G, ctx, dev, precision, cuboid, tol, golden=None):
     return res
 
 
-def traffic_record(kernel_src):
-    """Per-launch DRAM traffic of the trailing update from the committed ncu summary, if it was taken on
-    the kernel source as it is now (sha256 of the file); else None."""
+def traffic_record(kernel_src, algorithmic_bytes_per_launch):
+    """Per-launch DRAM traffic of the trailing update: the ratio of DRAM bytes to algorithmic bytes from the
+    committed ncu capture of one launch of the 3N = 9,000 case, times this run's algorithmic bytes per launch
+    (C, the largest term, scales with m^2 in both); None unless the capture was taken on the kernel source as
+    it is now (sha256 of the file)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "tc_update_tf32_cuboid40x30x10_traffic.md")
+    path = os.path.join(ROOT, "profiles", "tc_update_pair_tf32_cuboid20x15x10_ncu.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -278,7 +280,7 @@ def traffic_record(kernel_src):
     if vals.get("source_sha256") != sha:
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals["traffic_over_algorithmic"]) * algorithmic_bytes_per_launch
     except (KeyError, ValueError):
         return None
 
@@ -1003,8 +1005,8 @@ def main():
         rl = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"] * NOMINAL_TF32_OVER_BF16,
               "peak_src": f"{peak_src} sustained bf16 x nominal TF32/BF16 ratio 1.1/2.25"}
     achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12 if per_launch_ms > 0 else 0.0
-    traffic = traffic_record("lu_tc.cu") if (rl["bound"] == "tensor" and args.precision == "tf32"
-                                             and args.cuboid == "40x30x10") else None
+    traffic = traffic_record("lu_tc.cu", prof["bytes"] / max(1, prof["launches"])) if (
+        rl["bound"] == "tensor" and args.precision == "tf32" and args.cuboid == "40x30x10") else None
     roofline = {"bound": rl["bound"], "achieved": achieved, "peak": rl["peak"], "unit": "TFLOP/s",
                 "frac": achieved / rl["peak"], "traffic": traffic, "kernel": "LU trailing update A22 -= A21 U12",
                 "algorithmic_bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
