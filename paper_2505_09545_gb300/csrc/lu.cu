@@ -29,7 +29,8 @@ gdm_status gdm_tc_trailing_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, i
 size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec);
 gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_t ldc, int64_t r0, int64_t c0,
                              const float2 *L, int64_t ldl, const float2 *U, int64_t ldu, int64_t u_r0, int64_t u_c0,
-                             int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof);
+                             int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof,
+                             int u_is_tf32);
 gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t r0, int64_t c0,
                          int64_t k0, int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof);
 
@@ -659,13 +660,21 @@ __global__ void __launch_bounds__(512) k_panels_apply(float2 *__restrict__ A, in
 }
 
 // T[i + c * nb] = A[b0 + i, c0 + c] and zero the source (the U12 GEMM accumulates into it)
+// round_tf32: T rounded to TF32 (nearest), for the single-product updates whose tensor cores would otherwise
+// truncate it
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
 __global__ void k_gather_zero(float2 *__restrict__ A, int64_t lda, int64_t b0, int64_t c0, int nb, int64_t nc,
-                              float2 *__restrict__ T) {
+                              float2 *__restrict__ T, int round_tf32) {
     const int64_t total = (int64_t)nb * nc;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = e / nb, i = e % nb;
         float2 *a = A + (c0 + c) * lda + b0 + i;
-        T[e] = *a;
+        const float2 v = *a;
+        T[e] = round_tf32 ? make_float2(tf32_rna(v.x), tf32_rna(v.y)) : v;
         *a = make_float2(0.f, 0.f);
     }
 }
@@ -1031,10 +1040,12 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
             const int64_t tot = (int64_t)nbi * nc;
             unsigned gb = (unsigned)((tot + 255) / 256);
             if (gb > (unsigned)(8 * ctx->sm_count)) gb = 8 * ctx->sm_count;
-            k_gather_zero<<<gb, 256, 0, ctx->stream>>>((float2 *)A, lda, b0, be, nbi, nc, T12);
+            k_gather_zero<<<gb, 256, 0, ctx->stream>>>((float2 *)A, lda, b0, be, nbi, nc, T12,
+                                                       prec != GDM_FP32 && !getenv("GDM_TC_TRUNCATE"));
             GDM_LAUNCHED(ctx, "gather_zero");
             GDM_TRY(gdm_tc_update_ext(ctx, prec, (float2 *)A, lda, b0, be, negM, nbi, T12, nbi, 0, 0, nbi, nc, nbi,
-                                      tcws, tcbytes, 0));
+                                      tcws, tcbytes, 0,
+                                      prec != GDM_FP32 && !getenv("GDM_TC_TRUNCATE")));
             GDM_TRY(gdm_phase_end(ctx, GDM_PH_U12));
         } else if (be < n) {
             // U12 = L11^{-1} A12 panel by panel; each panel's interchanges reach the trailing columns just

@@ -24,6 +24,7 @@
 // frees its tensor memory and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <stdlib.h>
 
 #include <nvtx3/nvToolsExt.h>
@@ -464,8 +465,11 @@ constexpr int P_TMEM_COLS = 2 * PBN;
 // D = F32, A = B = TF32, both K-major, M = 256, N = PBN
 constexpr uint32_t P_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(PBN >> 3) << 17) |
                              ((uint32_t)(PBM >> 4) << 24);
-__device__ __forceinline__ uint32_t p_idesc_n(int n_cols) {
-    return (P_IDESC & ~(0x3Fu << 17)) | ((uint32_t)(n_cols >> 3) << 17);
+// kind::f16 with BF16 A and B (format 1), D = F32
+constexpr uint32_t P_IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(PBN >> 3) << 17) |
+                                  ((uint32_t)(PBM >> 4) << 24);
+template <bool BF16> __device__ __forceinline__ uint32_t p_idesc_n(int n_cols) {
+    return ((BF16 ? P_IDESC_BF16 : P_IDESC) & ~(0x3Fu << 17)) | ((uint32_t)(n_cols >> 3) << 17);
 }
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -498,6 +502,14 @@ __device__ __forceinline__ void umma_tf32_pair(uint32_t dtmem, uint64_t adesc, u
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
+__device__ __forceinline__ void umma_bf16_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
 // arrive once on the mbarrier at this shared-memory offset in both CTAs of the pair when the pair's MMAs
 // issued so far have completed
 __device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
@@ -511,6 +523,9 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
 
+// BF16: the same tiles with BF16 operands (64 elements = 128 bytes per stage row, MMA K = 16), for the
+// GDM_BF16_REFINE trailing update; the operands are BF16 copies prepared by k_prep_lx_bf16 / k_u_to_bf16.
+template <bool BF16>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     k_tc_update_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmC, int cx0, int cy0, int M, int N, int K, int bx0, int by0,
@@ -532,7 +547,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     const uint32_t rank = cluster_rank();
     const bool leader = rank == 0;
     const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
-    const int nk = (K + BK - 1) / BK;
+    constexpr int KE = BF16 ? 2 * BK : BK;  // K elements per stage (128 bytes per row)
+    const int nk = (K + KE - 1) / KE;
     TileMap tm{(M + PBM - 1) / PBM, (N + PBN - 1) / PBN, 8};
     const int ntiles = tm.num_m * tm.num_n;
 
@@ -578,8 +594,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                     unsigned char *st = base + s * P_STAGE_BYTES;
                     const uint32_t fb = mapa_rank(smem_u32(&full[s]), 0);
                     if (leader) mbar_expect_tx(&full[s], 2 * P_STAGE_BYTES);
-                    tma_load_2d_pair(st, &tmA, kc * BK, mt * PBM + (int)rank * 128, fb);
-                    tma_load_2d_pair(st + P_A_BYTES, &tmB, bx0 + kc * BK, by0 + nt * PBN + (int)rank * (ncol / 2), fb);
+                    tma_load_2d_pair(st, &tmA, kc * KE, mt * PBM + (int)rank * 128, fb);
+                    tma_load_2d_pair(st + P_A_BYTES, &tmB, bx0 + kc * KE, by0 + nt * PBN + (int)rank * (ncol / 2), fb);
                     issued++;
                     if (++s == P_STAGES) {
                         s = 0;
@@ -616,7 +632,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 const uint32_t dt = tmem_base + (uint32_t)(b * PBN);
                 int mt_i, nt_i;
                 tm.get(t, mt_i, nt_i);
-                const uint32_t idesc = p_idesc_n(32 * tm.chunks(nt_i, N, PBN));
+                const uint32_t idesc = p_idesc_n<BF16>(32 * tm.chunks(nt_i, N, PBN));
                 bool ok = true;
                 for (int kc = 0; kc < nk; kc++) {
                     if (!mbar_wait(&full[s], ph, abort_flag, gflags)) {
@@ -629,8 +645,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                     const uint64_t b0 = desc_sw128(sa + P_A_BYTES);
 #pragma unroll
                     for (int k = 0; k < BK / 8; k++) {
+                        // 32 bytes along K per MMA (8 TF32 or 16 BF16): +2 in the 16-byte address field
                         const uint64_t ko = (uint64_t)(2 * k);
-                        umma_tf32_pair(dt, a0 + ko, b0 + ko, idesc, (kc | k) ? 1u : 0u);
+                        if (BF16) umma_bf16_pair(dt, a0 + ko, b0 + ko, idesc, (kc | k) ? 1u : 0u);
+                        else umma_tf32_pair(dt, a0 + ko, b0 + ko, idesc, (kc | k) ? 1u : 0u);
                     }
                     issued_any = true;
                     umma_commit_pair(&empty[s]);
@@ -762,9 +780,24 @@ __device__ __forceinline__ float tf32_round(float x) {
 
 // Lx[(2i+c) * K' + 2k + c'] from L = A21 (complex column-major at L, ld lda), rows i < m, cols k < nb.
 // SPLIT = 3 writes the TF32 hi part to Lx and the remainder to Llo.
+// SPLIT = 1 with Ut: the z = 1 slice of the grid also writes U12 (complex nb x n_cols at U, ld ldu) as a
+// K-major real plane Ut[j][2nb] rounded to TF32, so that both operands of a single-product update are rounded
+// to nearest rather than truncated by the tensor core.
 template <int SPLIT>
 __global__ void k_prep_lx(const float2 *__restrict__ L, int64_t lda, int m, int nb, float *__restrict__ Lx,
-                          float *__restrict__ Llo) {
+                          float *__restrict__ Llo, const float2 *__restrict__ U = nullptr, int64_t ldu = 0,
+                          int n_cols = 0, float *__restrict__ Ut = nullptr) {
+    if (blockIdx.z == 1) {
+        const int64_t total = (int64_t)nb * n_cols;
+        const int64_t stride = (int64_t)gridDim.x * gridDim.y * blockDim.x;
+        for (int64_t e = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+             e += stride) {
+            const int j = (int)(e / nb), k = (int)(e % nb);
+            const float2 v = U[(int64_t)j * ldu + k];
+            *(float2 *)(Ut + (int64_t)j * 2 * nb + 2 * k) = make_float2(tf32_round(v.x), tf32_round(v.y));
+        }
+        return;
+    }
     __shared__ float2 tile[32][33];
     const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
@@ -791,8 +824,10 @@ __global__ void k_prep_lx(const float2 *__restrict__ L, int64_t lda, int m, int 
             *(float2 *)(Llo + (int64_t)(2 * i) * K2 + 2 * k) = make_float2(r0.x - h0.x, r0.y - h0.y);
             *(float2 *)(Llo + (int64_t)(2 * i + 1) * K2 + 2 * k) = make_float2(r1.x - h1.x, r1.y - h1.y);
         } else {
-            *o0 = r0;
-            *o1 = r1;
+            // rounded to TF32 here (nearest): the tensor core would otherwise drop the low mantissa bits, a
+            // truncation whose bias accumulates over the K sums of the update
+            *o0 = make_float2(tf32_round(r0.x), tf32_round(r0.y));
+            *o1 = make_float2(tf32_round(r1.x), tf32_round(r1.y));
         }
     }
 }
@@ -807,6 +842,37 @@ __global__ void k_split_u(const float2 *__restrict__ U, int64_t lda, int nb, int
     float2 h = make_float2(tf32_round(v.x), tf32_round(v.y));
     *(float2 *)(Uhi + (int64_t)j * 2 * nb + 2 * k) = h;
     *(float2 *)(Ulo + (int64_t)j * 2 * nb + 2 * k) = make_float2(v.x - h.x, v.y - h.y);
+}
+
+// BF16 operands of the GDM_BF16_REFINE trailing update, rounded to nearest even:
+// Lb[(2i+c) * K' + 2k + c'] as Lx above, and Ub[j * K' + 2k + c] = U12 column j seen as reals (K-major)
+__global__ void k_prep_lx_bf16(const float2 *__restrict__ L, int64_t lda, int m, int nb, __nv_bfloat16 *__restrict__ Lb) {
+    __shared__ float2 tile[32][33];
+    const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    for (int kk = ty; kk < 32; kk += 8) {
+        int i = i0 + tx, k = k0 + kk;
+        float2 v = make_float2(0.f, 0.f);
+        if (i < m && k < nb) v = L[(int64_t)k * lda + i];
+        tile[kk][tx] = v;
+    }
+    __syncthreads();
+    const int K2 = 2 * nb;
+    for (int ii = ty; ii < 32; ii += 8) {
+        int i = i0 + ii, k = k0 + tx;
+        if (i >= m || k >= nb) continue;
+        const float2 l = tile[tx][ii];
+        *(__nv_bfloat162 *)(Lb + (int64_t)(2 * i) * K2 + 2 * k) = __floats2bfloat162_rn(l.x, -l.y);
+        *(__nv_bfloat162 *)(Lb + (int64_t)(2 * i + 1) * K2 + 2 * k) = __floats2bfloat162_rn(l.y, l.x);
+    }
+}
+
+__global__ void k_u_to_bf16(const float2 *__restrict__ U, int64_t lda, int nb, int m, __nv_bfloat16 *__restrict__ Ub) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nb * m) return;
+    int j = (int)(e / nb), k = (int)(e % nb);
+    const float2 v = U[(int64_t)j * lda + k];
+    *(__nv_bfloat162 *)(Ub + (int64_t)j * 2 * nb + 2 * k) = __floats2bfloat162_rn(v.x, v.y);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -833,6 +899,22 @@ bool make_map(CUtensorMap *map, const float *gptr, uint64_t inner, uint64_t oute
     cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)gptr, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// 2D BF16 tensor map: inner extent `inner` elements (contiguous), `outer` rows with row pitch `pitch` elements,
+// box 64 x box_rows (128-byte rows), 128-byte swizzle, zero fill out of bounds.
+bool make_map_bf16(CUtensorMap *map, const __nv_bfloat16 *gptr, uint64_t inner, uint64_t outer, uint64_t pitch,
+                   uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {pitch * 2};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * BK), box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)gptr, dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -874,9 +956,15 @@ gdm_status launch_update(gdm_ctx *ctx, const CUtensorMap &a0, const CUtensorMap 
 
 // CTA pairs that fit on the GPU at once with the pair kernel's shared memory (a persistent grid larger than
 // that would leave some pairs waiting for others to finish)
-int max_pairs(gdm_ctx *ctx) {
+template <bool BF16> int max_pairs(gdm_ctx *ctx) {
     static int cached = -1;
     if (cached < 0) {
+        // the occupancy query needs the kernel's shared-memory limit raised first
+        if (cudaFuncSetAttribute(k_tc_update_pair<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(ctx->sm_count & ~1));
         cfg.blockDim = dim3(NTHREADS);
@@ -889,7 +977,7 @@ int max_pairs(gdm_ctx *ctx) {
         cfg.attrs = &at;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_update_pair, &cfg) != cudaSuccess || n < 1) {
+        if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_update_pair<BF16>, &cfg) != cudaSuccess || n < 1) {
             cudaGetLastError();
             n = 0;
         }
@@ -898,19 +986,16 @@ int max_pairs(gdm_ctx *ctx) {
     return cached;
 }
 
+template <bool BF16>
 gdm_status launch_update_pair(gdm_ctx *ctx, const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &cm,
                               int cx0, int cy0, int M, int N, int K, int bx0, int by0) {
-    static bool attr = false;
-    if (!attr) {
-        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_update_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM));
-        attr = true;
-    }
-    const int np = max_pairs(ctx);
+    const int np = max_pairs<BF16>(ctx);  // raises the kernel's shared-memory limit on first use
     if (np < 1) return GDM_ERR_UNSUPPORTED;
     const int ntiles = ((M + PBM - 1) / PBM) * ((N + PBN - 1) / PBN);
     const int pairs = ntiles < np ? ntiles : np;
-    k_tc_update_pair<<<2 * pairs, NTHREADS, P_SMEM, ctx->stream>>>(a, b, cm, cx0, cy0, M, N, K, bx0, by0, ctx->dflags);
-    GDM_LAUNCHED(ctx, "tc_update_pair");
+    k_tc_update_pair<BF16><<<2 * pairs, NTHREADS, P_SMEM, ctx->stream>>>(a, b, cm, cx0, cy0, M, N, K, bx0, by0,
+                                                                          ctx->dflags);
+    GDM_LAUNCHED(ctx, BF16 ? "tc_update_pair_bf16" : "tc_update_pair");
     return GDM_OK;
 }
 
@@ -920,17 +1005,21 @@ size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec) {
     if (prec == GDM_FP64) return 0;
     size_t lx = (size_t)2 * n * 2 * nb * sizeof(float);  // Lx: (2m) x (2nb)
     size_t u = (size_t)n * 2 * nb * sizeof(float);       // one U plane: m x (2nb)
-    return prec == GDM_FP32 ? 2 * lx + 2 * u + 4096 : lx + 4096;
+    // TF32: Lx and a rounded copy of U12; BF16_REFINE: BF16 copies of both (12 m nb bytes) fit in the same space
+    return prec == GDM_FP32 ? 2 * lx + 2 * u + 4096 : lx + u + 4096;
 }
 
 // C[r0 : r0+Mc, c0 : c0+Nc] -= L[0 : Mc, 0 : Kc] U[u_r0 : u_r0+Kc, u_c0 : u_c0+Nc] with complex64 operands in
 // column-major storage (C with ldc, L with ldl, U with ldu); C may alias L or U only as disjoint blocks.
 // The C chunks are clipped to the sub-block through the tensor-map extents (rows < r0+Mc, columns
 // < c0+Nc), so columns and rows outside it are never written. prof = 1 records the launch as the
-// factorisation's dominant kernel (gdm_profile_enable).
+// factorisation's dominant kernel (gdm_profile_enable). Single-product (TF32) updates read both operands
+// rounded to TF32 (nearest): Lx by its preparation, U through a rounded copy unless u_is_tf32 says that U
+// holds TF32 values already.
 gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_t ldc, int64_t r0, int64_t c0,
                              const float2 *L, int64_t ldl, const float2 *U, int64_t ldu, int64_t u_r0, int64_t u_c0,
-                             int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof) {
+                             int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof,
+                             int u_is_tf32) {
     if (prec == GDM_FP64) return GDM_ERR_UNSUPPORTED;
     if (Mc <= 0 || Nc <= 0 || Kc <= 0) return GDM_OK;
     if (getenv("GDM_TC_DISABLE")) return GDM_ERR_UNSUPPORTED;
@@ -938,6 +1027,32 @@ gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_
         return GDM_ERR_UNSUPPORTED;
     const int split = (prec == GDM_FP32) ? 3 : 1;
     const int M = (int)(2 * Mc), N = (int)Nc, K = (int)(2 * Kc);
+    if (prec == GDM_BF16_REFINE && prof && M >= PBM && N >= 2 * PBN && !getenv("GDM_TC_SINGLE") &&
+        max_pairs<true>(ctx) >= 1) {
+        // the trailing update in BF16 on CTA pairs; BF16 copies of the embedded L panel and of U12
+        ScratchCarver sb(ws);
+        __nv_bfloat16 *Lb = sb.take<__nv_bfloat16>((size_t)M * K);
+        __nv_bfloat16 *Ub = sb.take<__nv_bfloat16>((size_t)N * K);
+        if (sb.off > ws_bytes) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "tensor-core workspace too small");
+        dim3 pg((unsigned)((Mc + 31) / 32), (unsigned)((Kc + 31) / 32));
+        k_prep_lx_bf16<<<pg, 256, 0, ctx->stream>>>(L, ldl, (int)Mc, (int)Kc, Lb);
+        GDM_LAUNCHED(ctx, "prep_lx_bf16");
+        const int64_t cnt = Kc * Nc;
+        k_u_to_bf16<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(U + u_c0 * ldu + u_r0, ldu, (int)Kc,
+                                                                            (int)Nc, Ub);
+        GDM_LAUNCHED(ctx, "u_to_bf16");
+        CUtensorMap ta, tb, tcm;
+        if (!(make_map_bf16(&ta, Lb, K, M, K, 128) && make_map_bf16(&tb, Ub, K, N, K, PBN / 2) &&
+              make_map_c(&tcm, (const float *)C, (uint64_t)(2 * (r0 + Mc)), (uint64_t)(c0 + Nc), (uint64_t)2 * ldc)))
+            return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        int slot = -1;
+        const double fl = 8.0 * (double)Mc * (double)Nc * (double)Kc;
+        const double by = 16.0 * (double)Mc * Nc + 2.0 * ((double)M * K + (double)N * K);
+        GDM_TRY(gdm_prof_begin(ctx, &slot));
+        GDM_TRY(launch_update_pair<true>(ctx, ta, tb, tcm, (int)(2 * r0), (int)c0, M, N, K, 0, 0));
+        return gdm_prof_end(ctx, slot, fl, by);
+    }
+    // every other update (and BF16_REFINE's in-block and U12 updates) in TF32
     ScratchCarver sc(ws);
     float *Lx = sc.take<float>((size_t)M * K);
     float *Llo = split == 3 ? sc.take<float>((size_t)M * K) : nullptr;
@@ -952,8 +1067,17 @@ gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_
         k_split_u<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(U + u_c0 * ldu + u_r0, ldu, (int)Kc, (int)Nc,
                                                                           Uhi, Ulo);
         GDM_LAUNCHED(ctx, "split_u");
-    } else {
-        k_prep_lx<1><<<pg, 256, 0, ctx->stream>>>(L, ldl, (int)Mc, (int)Kc, Lx, nullptr);
+    }
+    // single product: a TF32-rounded K-major copy of U12 next to Lx, made by the same launch
+    float *Ut = nullptr;
+    if (split == 1) {
+        if (!u_is_tf32 && !getenv("GDM_TC_TRUNCATE")) {
+            Ut = sc.take<float>((size_t)N * K);
+            if (sc.off > ws_bytes) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "tensor-core workspace too small");
+        }
+        dim3 pg1(pg.x, pg.y, Ut ? 2 : 1);
+        k_prep_lx<1><<<pg1, 256, 0, ctx->stream>>>(L, ldl, (int)Mc, (int)Kc, Lx, nullptr, U + u_c0 * ldu + u_r0, ldu,
+                                                   (int)Nc, Ut);
         GDM_LAUNCHED(ctx, "prep_lx");
     }
     CUtensorMap ta0, ta1, tb0, tb1, tc;
@@ -974,20 +1098,29 @@ gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_
         // (narrow GEMMs, the in-block updates of at most 256 columns, keep the single-CTA tiles, which do
         // better there)
         const bool pair = M >= PBM && N >= 2 * PBN && !getenv("GDM_TC_SINGLE");
-        ok = ok && make_map(&tb0, (const float *)U, (uint64_t)2 * ldu, (uint64_t)(u_c0 + Nc), (uint64_t)2 * ldu,
-                            pair ? PBN / 2 : 256);
+        if (Ut) {
+            ok = ok && make_map(&tb0, Ut, K, N, K, pair ? PBN / 2 : 256);
+        } else {
+            ok = ok && make_map(&tb0, (const float *)U, (uint64_t)2 * ldu, (uint64_t)(u_c0 + Nc), (uint64_t)2 * ldu,
+                                pair ? PBN / 2 : 256);
+        }
         if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         if (prof) GDM_TRY(gdm_prof_begin(ctx, &slot));
         gdm_status st = GDM_ERR_UNSUPPORTED;
         if (pair)
-            st = launch_update_pair(ctx, ta0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * u_r0), (int)u_c0);
+            st = Ut ? launch_update_pair<false>(ctx, ta0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, 0, 0)
+                    : launch_update_pair<false>(ctx, ta0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * u_r0),
+                                                (int)u_c0);
         if (st == GDM_ERR_UNSUPPORTED) {
             if (pair) {
-                ok = make_map(&tb0, (const float *)U, (uint64_t)2 * ldu, (uint64_t)(u_c0 + Nc), (uint64_t)2 * ldu, 256);
+                ok = Ut ? make_map(&tb0, Ut, K, N, K, 256)
+                        : make_map(&tb0, (const float *)U, (uint64_t)2 * ldu, (uint64_t)(u_c0 + Nc), (uint64_t)2 * ldu,
+                                   256);
                 if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
             }
-            st = launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * u_r0),
-                                       (int)u_c0);
+            st = Ut ? launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, 0, 0)
+                    : launch_update<256, 1>(ctx, ta0, ta0, tb0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K,
+                                            (int)(2 * u_r0), (int)u_c0);
         }
         GDM_TRY(st);
     }
@@ -1002,7 +1135,7 @@ gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t ld
     (void)n;
     if ((k0 & 1)) return GDM_ERR_UNSUPPORTED;
     return gdm_tc_update_ext(ctx, prec, A, lda, r0, c0, A + k0 * lda + r0, lda, A, lda, k0, c0, Mc, Nc, Kc, ws,
-                             ws_bytes, prof);
+                             ws_bytes, prof, 0);
 }
 
 // A22 -= A21 U12 for the block [b0, b0+nb) of the complex64 matrix A (n x n, lda).
