@@ -263,6 +263,47 @@ def fp64_compare(G, ctx, dev, precision, cuboid, tol, golden=None):
     return res
 
 
+def precision_leg(G, ctx, dev, precision, tol, golden, reps=3):
+    """The headline cuboid step (assemble + LU + refined solve) in another factor precision: seconds per step
+    (CUDA events, mean of `reps` after one warm-up), refinement steps, the fields' error against the stored
+    oracle solution, and the trailing update's rate (CUDA events on its launch stream)."""
+    import numpy as np
+    import torch
+    import gdm_workloads as W
+    s = W.cuboid_precision()
+    lam = float(s.wavelengths[0])
+    pos = torch.tensor(s.pos, device=dev)
+    prob = G.GDMProblem(pos, lam, 3, eps=torch.tensor(s.eps, device=dev), step=s.step)
+    F0 = G.incident_planewave(ctx, pos, lam, s.e0)
+    A = torch.empty((prob.size, G.padded_lda(prob.size)), dtype=torch.complex64, device=dev)
+    ipiv = torch.empty(prob.size, dtype=torch.int32, device=dev)
+    F = torch.empty_like(F0)
+
+    def step():
+        G.assemble(ctx, prob, precision, out=A)
+        return G.solve(ctx, prob, A, F0, precision, ipiv=ipiv, F=F, tol=tol)[2]
+
+    step()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        info = step()
+    e1.record()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    out = {"precision": precision, "s": e0.elapsed_time(e1) / reps / 1e3, "refine_iters": info["iterations"],
+           "rel_residual_fp64": info["rel_residual"],
+           "trailing_update_tflops": prof["flops"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] > 0 else None}
+    if golden is not None:
+        Fh = F.cpu().numpy().T
+        out["field_err_vs_oracle"] = float(np.max(np.linalg.norm(Fh - golden, axis=0) / np.linalg.norm(golden, axis=0)))
+    del A
+    return out
+
+
 def traffic_record(kernel_src, algorithmic_bytes_per_launch):
     """Per-launch DRAM traffic of the trailing update: the ratio of DRAM bytes to algorithmic bytes from the
     committed ncu capture of one launch of the 3N = 9,000 case, times this run's algorithmic bytes per launch
@@ -825,7 +866,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32", "fp64", "bf16"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-10,
@@ -990,6 +1031,8 @@ def main():
     if not args.no_extras:
         extras["adjoint"] = adjoint_leg(G, ctx, dev, args.precision, args.warmup, args.steps)
         extras["nearfield"] = nearfield_leg(G, ctx, dev, prob, F)
+        if args.precision == "tf32" and args.cuboid == "40x30x10":
+            extras["bf16_refine"] = precision_leg(G, ctx, dev, "bf16", args.tol, golden)
         extras["metasurface"] = metasurface_leg(G, ctx, dev, args.precision, args.tol, 1.0, 1, 1, load_peaks()[0])
         extras["metasurface"].pop("sigma")
         extras["fp64_gpu_path"] = fp64_compare(G, ctx, dev, args.precision, args.fp64_cuboid, args.tol, golden)
@@ -999,6 +1042,9 @@ def main():
     flops_per_launch = prof["flops"] / max(1, prof["launches"])
     if args.precision == "fp64":
         rl = {"bound": "alu", "peak": 1.05, "peak_src": "FP64 rate measured with torch float64 matmul on GB300"}
+    elif args.precision == "bf16":
+        rl = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"],
+              "peak_src": f"{peak_src} sustained bf16 (cuBLAS)"}
     elif os.environ.get("GDM_TC_DISABLE") or prof.get("tc", True) is False:
         rl = {"bound": "alu", "peak": FP32_SIMT_PEAK_TFLOPS, "peak_src": "FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
     else:
@@ -1022,8 +1068,8 @@ def main():
     it = infos[-1]
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64-tf32+f64" if args.precision == "tf32" else
-            ("c64-3xtf32+f64" if args.precision == "fp32" else "f64"),
+            "vs_baseline": None, "dtype": {"tf32": "c64-tf32+f64", "fp32": "c64-3xtf32+f64",
+                                           "bf16": "c64-bf16+f64"}.get(args.precision, "f64"),
             "data": "synthetic", "config": workload_config(args),
             "accuracy": {"tol": args.tol, "field_err_vs_oracle": oracle_err,
                          "field_err_vs_solve_to_1e-12": field_err,

@@ -64,8 +64,16 @@ typedef enum {
  * GDM_FP32        : complex64 matrix, LU with FP32-accurate tensor-core trailing
  *                   updates (TF32 hi/lo split, three products), FP64 refinement.
  * GDM_TF32_REFINE : complex64 matrix, LU with single-pass TF32 tensor-core
- *                   trailing updates, FP64 refinement. */
-typedef enum { GDM_FP64 = 0, GDM_FP32 = 1, GDM_TF32_REFINE = 2 } gdm_precision;
+ *                   trailing updates, FP64 refinement.
+ * GDM_BF16_REFINE : complex64 matrix, LU whose trailing updates A22 -= A21 U12 run
+ *                   with BF16 operands (rounded to nearest even) and FP32 accumulation
+ *                   on the tensor cores, the rest as GDM_TF32_REFINE; FP64 refinement,
+ *                   which takes more steps than with TF32 factors (8 significand bits
+ *                   against 11). The paper's solve is a plain LU (Sec. "Numerical
+ *                   solution"); lower-precision factors with refinement are this
+ *                   library's own. BF16 has FP32's exponent range, so no scaling is
+ *                   needed beyond the refinement's own right-hand-side scaling. */
+typedef enum { GDM_FP64 = 0, GDM_FP32 = 1, GDM_TF32_REFINE = 2, GDM_BF16_REFINE = 3 } gdm_precision;
 
 typedef struct gdm_ctx gdm_ctx;
 

@@ -24,7 +24,7 @@ GDM_OK = 0
 STATUS = {0: "GDM_OK", 1: "GDM_ERR_INVALID_ARG", 2: "GDM_ERR_SHAPE", 3: "GDM_ERR_NONFINITE", 4: "GDM_ERR_SINGULAR",
           5: "GDM_ERR_NOT_CONVERGED", 6: "GDM_ERR_OOM", 7: "GDM_ERR_CUDA", 8: "GDM_ERR_TIMEOUT",
           9: "GDM_ERR_UNSUPPORTED"}
-PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 SOLVE_FACTORED = 1
 SOLVE_NO_REFINE = 2
 SOLVE_GLOBAL_PIVOT = 4

@@ -321,7 +321,7 @@ static gdm_status check_problem(gdm_ctx *ctx, const gdm_problem *p) {
 }
 
 static gdm_status check_prec(gdm_ctx *ctx, gdm_precision prec) {
-    if (prec != GDM_FP64 && prec != GDM_FP32 && prec != GDM_TF32_REFINE)
+    if (prec != GDM_FP64 && prec != GDM_FP32 && prec != GDM_TF32_REFINE && prec != GDM_BF16_REFINE)
         return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     return GDM_OK;
 }

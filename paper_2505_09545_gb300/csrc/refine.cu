@@ -138,9 +138,10 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
                                                                                : nullptr;
     double *hn;
     GDM_TRY(gdm_pinned(ctx, sizeof(double) * 4 * n_rhs, (void **)&hn));
-    // TF32 factors only: their first solution is off by ~1e-2; FP32 (3-product) and FP64 factors start
+    // TF32 and BF16 factors only: their first solution is off by ~1e-2; FP32 (3-product) and FP64 factors start
     // closer than the FP32 residual resolves
-    const bool fast_ok = ffws && p->kind == 3 && !adjoint && prec == GDM_TF32_REFINE && !getenv("GDM_REFINE_EXACT");
+    const bool fast_ok = ffws && p->kind == 3 && !adjoint && (prec == GDM_TF32_REFINE || prec == GDM_BF16_REFINE) &&
+                         !getenv("GDM_REFINE_EXACT");
     bool ff_prepared = false;
     const unsigned nb = (unsigned)((ns + 255) / 256);
     const dim3 gq(nb, (unsigned)n_rhs);

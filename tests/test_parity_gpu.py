@@ -116,7 +116,7 @@ def test_planewave(G, ctx):
     np.testing.assert_allclose(F0.cpu().numpy().T, ref, rtol=1e-14, atol=1e-14)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
 def test_solve_cells(G, ctx, prec):
     for s in structures():
         lam = float(s.wavelengths[0])
@@ -232,11 +232,13 @@ def test_invalid_arguments(G, ctx):
         G.assemble(ctx, bad, "fp32")
 
 
-@pytest.mark.parametrize("prec,tol_plain,max_iters", [("tf32", 5e-2, 16), ("fp32", 1e-4, 5), ("fp64", 1e-11, 2)])
+@pytest.mark.parametrize("prec,tol_plain,max_iters", [("tf32", 5e-2, 16), ("bf16", 2e-1, 30), ("fp32", 1e-4, 5),
+                                                        ("fp64", 1e-11, 2)])
 def test_lu_factor_quality(G, ctx, prec, tol_plain, max_iters):
     """The factors themselves (no refinement) solve the system to the precision's level, so a wrong
     trailing update cannot hide behind the FP64 refinement. 3N = 2100: eight outer blocks, the
-    tensor-core update runs with trailing sizes 1844 ... 52 (ragged tiles)."""
+    tensor-core update runs with trailing sizes 1844 ... 52 (ragged tiles; with BF16 the updates of at
+    least 512 columns run on the BF16 pair kernel, 256-row tiles with ragged ends in both directions)."""
     s = W.random_cells(700, seed=12)
     lam = float(s.wavelengths[0])
     prob = gpu_problem(G, s, lam)

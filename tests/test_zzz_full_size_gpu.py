@@ -77,6 +77,26 @@ def test_cuboid_40x30x10_full_size(G):
 
 
 
+def test_cuboid_40x30x10_full_size_bf16(G):
+    """The headline system with BF16 trailing updates (GDM_BF16_REFINE) refined to a relative correction of
+    1e-10: every field element against the oracle's stored dense FP64 solution at 1e-9."""
+    s = W.cuboid_precision()
+    lam = float(s.wavelengths[0])
+    ctx = G.Context(0)
+    try:
+        prob = G.GDMProblem(t(s.pos), lam, 3, eps=t(s.eps), step=s.step)
+        F0 = G.incident_planewave(ctx, prob.pos, lam, s.e0)
+        A = G.assemble(ctx, prob, "bf16")
+        F, _, info = G.solve(ctx, prob, A, F0, "bf16", tol=1e-10)
+        del A
+        Fh = F.cpu().numpy().T
+    finally:
+        ctx.close()
+    assert info["status"] == 0 and info["rel_correction"] <= 1e-10, info
+    Fo = np.load(GOLDEN)["F"]
+    err = np.linalg.norm(Fh - Fo, axis=0) / np.linalg.norm(Fo, axis=0)
+    assert np.all(err < 1e-9), (err, info)
+
 def test_cuboid_nearfield_map_full_size(G):
     """The near-field leg of bench.py at its size: the 320 x 320 map 50 nm above the 40 x 30 x 10 cuboid (102,400
     points x 12,000 dipoles, E and H, both illuminations) from the oracle's stored fields, so that the kernel alone
