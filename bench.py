@@ -30,6 +30,10 @@ FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 f
 # FP32 thread instructions per (target, source) pair, 2 right-hand sides, of the GMRES FP32 operator
 # k_green_sum_f32 (ncu count: profiles/green_sum_f32_gmres_cuboid20x15x10_ncu.md)
 FP32_OPERATOR_INST_PER_PAIR = 204.0
+# FP64 operations per ordered pair of the adjoint's gradient pair sum k_dgreen_sum<1> (G s, dG/dr s, dG/dk s;
+# DADD + DMUL + 2 DFMA, ncu count: profiles/dgreen_sum_cylinder_ncu.md)
+DGREEN_FP64_FLOPS_PER_PAIR = None
+FP64_PEAK_TFLOPS = 1.05   # torch float64 matmul on GB300
 
 
 def load_peaks():
@@ -204,7 +208,29 @@ def adjoint_leg(G, ctx, dev, precision, warmup, steps):
         fw.append(a)
         bw.append(b)
     f, b = statistics.median(fw), statistics.median(bw)
+    # one wavelength's backward with phase accounting on this context: the adjoint solve (triangular solves
+    # with the forward factors and its refinement residuals) and the gradient pair sums dG/dr, dG/dk (FP64,
+    # two launches over the n (n - 1) ordered pairs)
+    wl0 = wls[:1].detach().clone().requires_grad_(True)
+    F1, sig1 = AG.scatter(pos, eps, wl0[0], ctx, cyl.step, cyl.e0, precision=precision)
+    E1 = AG.nearfield(pos, eps, wl0[0], F1, rp, ctx, cyl.step, cyl.e0)
+    L1 = (E1.abs() ** 2).sum() + sig1[:, 1].sum()
+    torch.cuda.synchronize()
+    ctx.phases(True)
+    L1.backward()
+    ph = ctx.phases(False)
+    pairs = 2.0 * cyl.n * (cyl.n - 1)
+    grad = {"gradient_ms": ph["gradient"], "adjoint_solves_ms": ph["correction_solves"],
+            "adjoint_residual_ms": ph["residual"], "pairs": pairs,
+            "note": "one wavelength's gdm_backward on one context (the timed spectrum runs the 8 concurrently)"}
+    if DGREEN_FP64_FLOPS_PER_PAIR and ph["gradient"] > 0:
+        ach = pairs * DGREEN_FP64_FLOPS_PER_PAIR / (ph["gradient"] / 1e3) / 1e12
+        grad["roofline"] = {"bound": "alu", "kernel": "k_dgreen_sum (FP64 pair sums of G, dG/dr, dG/dk)",
+                            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": ach / FP64_PEAK_TFLOPS, "flops_per_pair": DGREEN_FP64_FLOPS_PER_PAIR,
+                            "peak_source": "FP64 rate measured with a torch float64 matmul on GB300"}
     return {"value": f + b, "unit": "s", "forward_s": f, "backward_s": b, "precision": precision,
+            "backward_one_wavelength": grad,
             "workload": f"cylinder r=80 h=100 d=10 nm (N={cyl.n}), eps=12.25+0.05i, {wls.shape[0]} wavelengths "
                         "450-800 nm, x-pol; L = sum |E(probe)|^2 + sigma_sca; grads wrt all positions, eps, lambda",
             "timing": "wall clock with device synchronisation, median of the timed repetitions"}
@@ -481,6 +507,24 @@ def metasurface_leg(G, ctx, dev, precision, tol, eps_env, warmup, steps, peaks, 
                                                 "peak": tf32_peak, "frac": lu_flops / per_lam / 1e12 / tf32_peak,
                                                 "note": "(8/3)(6N)^3 over the whole wavelength's time (assembly, "
                                                         "panels, solves and refinement included)"}}
+
+
+def run_adjoint(args):
+    """The differentiation workload as its own line (see adjoint_leg)."""
+    import torch
+    import paper_2505_09545_gb300 as G
+    ws, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = G.Context(local)
+    leg = adjoint_leg(G, ctx, dev, args.precision, args.warmup, args.steps)
+    line = {"metric": "adjoint gradient s (8 wavelengths, forward + backward)", "value": leg.pop("value"),
+            "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic", "config": {"workload": leg.pop("workload")}, **leg}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
 
 
 def run_metasurface(args):
@@ -877,12 +921,13 @@ def main():
     ap.add_argument("--fp64-cuboid", default="40x30x10",
                     help="cuboid of the FP64-GPU-path comparison (default the full workload, ~2 min)")
     ap.add_argument("--workload", default="cuboid",
-                    choices=["cuboid", "metasurface", "batch", "gpm", "farfield", "ldos", "gmres", "nearfield"],
+                    choices=["cuboid", "metasurface", "batch", "gpm", "farfield", "ldos", "gmres", "nearfield",
+                             "adjoint"],
                     help="cuboid: the headline assemble+solve line; metasurface: 64x64 ED/MD array, 32 wavelengths; "
                          "batch: 256 uneven blobs, each at its own wavelength; gpm: effective-model extraction; "
                          "farfield: far-field sigma_sca of the solved cuboid; ldos: electric LDOS around the sphere; "
                          "gmres: matrix-free preconditioned GMRES on a larger cuboid; nearfield: E and H map of the "
-                         "solved cuboid")
+                         "solved cuboid; adjoint: the differentiation workload alone")
     ap.add_argument("--nearfield-side", type=int, default=320, help="nearfield workload: points per side of the map")
     ap.add_argument("--gmres-cuboid", default="80x60x10", help="gmres workload: cells per axis")
     ap.add_argument("--eps-env", type=float, default=1.0, help="metasurface workload: host permittivity")
@@ -913,6 +958,8 @@ def main():
         return run_gmres(args)
     if args.workload == "nearfield":
         return run_nearfield(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
 
     ws, rank, local = dist_setup()
     if ws > 1:

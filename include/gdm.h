@@ -477,11 +477,12 @@ gdm_status gdm_profile_enable(gdm_ctx *ctx, int enable);
 gdm_status gdm_profile_read(gdm_ctx *ctx, int64_t *launches, double *total_ms, double *flops, double *bytes);
 
 /* Phase accounting: with enable = 1 subsequent calls record device time per phase of the solve
- * (CUDA events around each phase; adds host overhead, for diagnostics only). ms_out (host, 10 doubles,
+ * (CUDA events around each phase; adds host overhead, for diagnostics only). ms_out (host, 11 doubles,
  * nullable) receives the times recorded since the previous call, in the order: panel factorisation,
  * row interchanges, small triangular solves, in-block updates, U12 updates, trailing update,
  * correction solves (gdm_solve_gmres: its preconditioner), refinement residual (double-float
- * operator), other (gdm_solve_gmres: orthogonalisation), FP32 operator of gdm_solve_gmres.
+ * operator), other (gdm_solve_gmres: orthogonalisation), FP32 operator of gdm_solve_gmres, gradient
+ * pair sums of gdm_backward (dG/dr, dG/dk).
  * Synchronises the stream when ms_out != NULL. */
 gdm_status gdm_profile_phases(gdm_ctx *ctx, int enable, double *ms_out);
 

@@ -124,7 +124,7 @@ _SIGS = {
     "gdm_profile_phases": ([P, C.c_int, PD], C.c_int),
 }
 PHASES = ["panel", "laswp", "trsm_small", "inblock_update", "u12_update", "trailing_update", "correction_solves",
-          "residual", "other", "operator_f32"]
+          "residual", "other", "operator_f32", "gradient"]
 
 
 def lib():

@@ -11,12 +11,18 @@
 // Near field E_m = E0(r_m) + sum_j G(r_m - r_j) P_j with gE = dL/dE^*: pair sums over evaluation points with
 // sources conj(gE_m) give dL/dF^*, dL/deps, dL/dr and dL/dk the same way.
 #include <math.h>
+#include <stdlib.h>
 
 #include "gdm_internal.cuh"
 
 #define PI_D 3.14159265358979323846
 
 size_t gdm_green_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n, int out);
+size_t gdm_ff_scratch_bytes(int64_t n);
+gdm_status gdm_ff_prepare(gdm_ctx *ctx, const gdm_problem *p, void *ffws);
+gdm_status gdm_ff_dgreen_sum(gdm_ctx *ctx, const gdm_problem *p, const double2 *S, int q, int conj, int qslot,
+                             int64_t chunk, int nchunks, void *ffws, double2 *partial);
+int gdm_ff_dgreen_occupancy();
 
 
 namespace {
@@ -144,6 +150,31 @@ size_t dg_partial_bytes(gdm_ctx *ctx, int64_t m, int64_t n) {
     int nc;
     dg_grid(ctx, m, n, &ch, &nc);
     return (size_t)nc * 2 * m * DG_OUT * sizeof(double2);
+}
+
+// chunking of the double-float gradient sums: at most the chunks dg_grid gives (the partial buffers are sized
+// by it), chosen so that the last wave of CTAs wastes the fewest resident slots at the kernel's occupancy
+void dg_grid_ff(gdm_ctx *ctx, int64_t m, int64_t n, int64_t *chunk, int *nchunks) {
+    int64_t ch0;
+    int nc_max;
+    dg_grid(ctx, m, n, &ch0, &nc_max);
+    const int64_t tb = (m + DG_T - 1) / DG_T;
+    const int64_t slots = (int64_t)gdm_ff_dgreen_occupancy() * ctx->sm_count;
+    double best = -1.0;
+    *chunk = ch0;
+    *nchunks = nc_max;
+    for (int nc = 1; nc <= nc_max; nc++) {
+        const int64_t ch = ((n + nc - 1) / nc + DG_S - 1) / DG_S * DG_S;
+        const int ncr = (int)((n + ch - 1) / ch);
+        if (ncr > nc_max) continue;
+        const int64_t ctas = tb * ncr, waves = (ctas + slots - 1) / slots;
+        const double eff = (double)ctas / (double)(waves * slots);
+        if (eff > best + 1e-9) {
+            best = eff;
+            *chunk = ch;
+            *nchunks = ncr;
+        }
+    }
 }
 
 // launch for one RHS pair (q0, q0+1); returns the number of chunks
@@ -405,8 +436,11 @@ gdm_status gdm_launch_backward(gdm_ctx *ctx, const gdm_problem *p, gdm_precision
     GDM_TRY(gdm_upload(ctx, e0, sizeof(double) * 6 * n_rhs, (void **)&de0));
     PW pw = {k, khat[0], khat[1], khat[2]};
     // adjoint right-hand side and the refined adjoint solve (its own scratch)
+    // gradient pair sums in double-float on the FP32 pipes unless GDM_GRADIENT_FP64 is set
+    const bool ffg = !getenv("GDM_GRADIENT_FP64");
     size_t own = ScratchCarver::round(cnt * sizeof(double2)) * 3 + ScratchCarver::round(3 * n_rhs * sizeof(double)) +
-                 ScratchCarver::round(2 * dg_partial_bytes(ctx, n, n)) + 4096;
+                 ScratchCarver::round(2 * dg_partial_bytes(ctx, n, n)) +
+                 (ffg ? ScratchCarver::round(gdm_ff_scratch_bytes(n)) : 0) + 4096;
     // g and mu live in a separate allocation because the refined solve reuses the context arena
     double2 *g = nullptr, *mu = nullptr;
     GDM_CUDA_TRY(ctx, cudaMallocAsync((void **)&g, cnt * sizeof(double2) * 2, ctx->stream));
@@ -431,6 +465,7 @@ gdm_status gdm_launch_backward(gdm_ctx *ctx, const gdm_problem *p, gdm_precision
     double2 *partA = sc.take<double2>(dg_partial_bytes(ctx, n, n) / sizeof(double2));
     double2 *partB = sc.take<double2>(dg_partial_bytes(ctx, n, n) / sizeof(double2));
     double2 *F0 = sc.take<double2>(cnt);
+    void *ffws = ffg ? sc.take<char>(gdm_ff_scratch_bytes(n)) : nullptr;
     // sigma values for the k-derivative of the prefactor (c is proportional to k)
     double e2[64];
     for (int q = 0; q < n_rhs; q++) {
@@ -446,8 +481,22 @@ gdm_status gdm_launch_backward(gdm_ctx *ctx, const gdm_problem *p, gdm_precision
     for (int q0 = 0; q0 < n_rhs; q0 += 2) {
         int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
         int ncA, ncB;
-        GDM_TRY(launch_dg(ctx, p->pos, n, p->pos, Pm, n, q0, nr, 0, k, 1.0 / p->eps_env, 1, partA, &ncA));
-        GDM_TRY(launch_dg(ctx, p->pos, n, p->pos, mu, n, q0, nr, 1, k, 1.0 / p->eps_env, 1, partB, &ncB));
+        GDM_TRY(gdm_phase_begin(ctx, GDM_PH_GRADIENT));
+        if (ffg) {
+            if (q0 == 0) GDM_TRY(gdm_ff_prepare(ctx, p, ffws));
+            int64_t ch;
+            int nc;
+            dg_grid_ff(ctx, n, n, &ch, &nc);
+            for (int q = 0; q < nr; q++) {
+                GDM_TRY(gdm_ff_dgreen_sum(ctx, p, Pm, q0 + q, 0, q, ch, nc, ffws, partA));
+                GDM_TRY(gdm_ff_dgreen_sum(ctx, p, mu, q0 + q, 1, q, ch, nc, ffws, partB));
+            }
+            ncA = ncB = nc;
+        } else {
+            GDM_TRY(launch_dg(ctx, p->pos, n, p->pos, Pm, n, q0, nr, 0, k, 1.0 / p->eps_env, 1, partA, &ncA));
+            GDM_TRY(launch_dg(ctx, p->pos, n, p->pos, mu, n, q0, nr, 1, k, 1.0 / p->eps_env, 1, partB, &ncB));
+        }
+        GDM_TRY(gdm_phase_end(ctx, GDM_PH_GRADIENT));
         k_backward_finalize<<<nb, 128, 0, ctx->stream>>>((const double2 *)F, mu, n, n_rhs, (const double2 *)p->eps,
                                                          p->eps_env, d3_4pi, S, p->pos, de0, pw, dw, partA, ncA, partB,
                                                          ncB, q0, nr, dk_dl, grad_pos, (double2 *)grad_eps,

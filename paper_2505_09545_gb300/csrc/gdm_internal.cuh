@@ -52,7 +52,7 @@ struct gdm_ctx {
 #define GDM_PROF_MAX 4096
 // phase accounting (diagnostics): device time per phase, summed over bracketed regions
 enum { GDM_PH_PANEL = 0, GDM_PH_LASWP, GDM_PH_TRSM, GDM_PH_INBLOCK, GDM_PH_U12, GDM_PH_TRAILING, GDM_PH_TRSV,
-       GDM_PH_RESIDUAL, GDM_PH_OTHER, GDM_PH_OPERATOR_F32, GDM_NPHASES };
+       GDM_PH_RESIDUAL, GDM_PH_OTHER, GDM_PH_OPERATOR_F32, GDM_PH_GRADIENT, GDM_NPHASES };
 struct gdm_phase_rec;
 gdm_status gdm_phase_begin(gdm_ctx *ctx, int phase);
 gdm_status gdm_phase_end(gdm_ctx *ctx, int phase);

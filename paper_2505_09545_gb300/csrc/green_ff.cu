@@ -136,7 +136,7 @@ template <int KIND, int NR> struct SrcRecLayout {
 
 template <int KIND, int NR>
 __global__ void k_prep_src(const DipF *__restrict__ dip, int64_t n, const double2 *__restrict__ P, int rhs0,
-                           int nr_here, float *__restrict__ rec) {
+                           int nr_here, float *__restrict__ rec, int conj = 0) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
     float *o = rec + j * SrcRecLayout<KIND, NR>::FLOATS;
@@ -157,6 +157,7 @@ __global__ void k_prep_src(const DipF *__restrict__ dip, int64_t n, const double
         for (int q = 0; q < NR; q++) {
             double2 v = make_double2(0.0, 0.0);
             if (q < nr_here) v = P[(rhs0 + q) * ld + KIND * j + a];
+            if (conj) v.y = -v.y;
             const float rh = (float)v.x, ih = (float)v.y;
             m[a * NR + q] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
         }
@@ -342,6 +343,140 @@ __global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ 
     }
 }
 
+// Gradient pair sums of the adjoint (cells), double-float on the FP32 pipes: partial[c][q][t][15] (FP64) =
+// sum over the sources j != t of chunk c of, for s = the source's vector (one right-hand side per launch):
+//   [0..2]   G s,   [3 + 3c + a]  (dG/dR_c s)_a,   [12..14]  dG/dk s,
+// with G = a I + b u u^T, a = e (k^2/R - 1/R^3 + i k/R^2), b = e (3/R^3 - k^2/R - 3 i k/R^2), e = exp(ikR)/eps_env:
+//   d/dR_c (G s)_a = u_c [a' s_a + b' u_a (u.s)] + (b/R) [delta_ca (u.s) + u_a s_c - 2 u_c u_a (u.s)],
+//   a' = da/dR = i k a + e (-k^2/R^2 + 3/R^4 - 2 i k/R^3),  b' = i k b + e (k^2/R^2 - 9/R^4 + 6 i k/R^3),
+//   d/dk (G s) = (i R a + e (2k/R + i/R^2)) s + (i R b + e (-2k/R - 3i/R^2)) u (u.s).
+// The same sums as the FP64 kernel of the adjoint (to ~1e-13 relative instead of FP64's 1e-16), at about six
+// times its rate on GB300, whose FP64 pipe runs at ~1/64 of FP32. Source tiles as in k_green_sum_ff.
+#define DGF_OUT 15
+__global__ void __launch_bounds__(RF_T) k_dgreen_sum_ff(const DipF *__restrict__ tgt, int64_t m,
+                                                       const float *__restrict__ rec, int64_t n, float khi, float klo,
+                                                       float k2hi, float k2lo, float ie_hi, float ie_lo,
+                                                       const float4 *__restrict__ gtab, int64_t chunk,
+                                                       int self_exclude, int qslot, double2 *__restrict__ partial,
+                                                       int *flags) {
+    using L = SrcRecLayout<3, 1>;
+    __shared__ float4 tab[257];
+    __shared__ __align__(16) float sbuf[2][RF_S * L::FLOATS];
+    __shared__ uint64_t bar[2];
+    __shared__ int abort_cta;
+    for (int e = threadIdx.x; e < 257; e += RF_T) tab[e] = gtab[e];
+    const int64_t t = (int64_t)blockIdx.x * RF_T + threadIdx.x;
+    const bool valid = t < m;
+    const int64_t c = blockIdx.y;
+    const int64_t jb = c * chunk, je = min(n, jb + chunk);
+    const int ntile = je > jb ? (int)((je - jb + RF_S - 1) / RF_S) : 0;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_cta = 0;
+    }
+    __syncthreads();
+    auto tile_src = [&](int it, uint32_t *bytes) {
+        const int64_t s0 = jb + (int64_t)it * RF_S;
+        *bytes = (uint32_t)(min((int64_t)RF_S, je - s0) * L::BYTES);
+        return rec + s0 * L::FLOATS;
+    };
+    if (threadIdx.x == 0 && ntile > 0) {
+        uint32_t by;
+        const float *src = tile_src(0, &by);
+        bulk_load(sbuf[0], src, by, &bar[0]);
+    }
+    const DipF ti = valid ? tgt[t] : tgt[0];
+    const ff kf = mk(khi, klo), k2 = mk(k2hi, k2lo), ie = mk(ie_hi, ie_lo);
+    cff acc[DGF_OUT];
+#pragma unroll
+    for (int a = 0; a < DGF_OUT; a++) acc[a] = {mk(0, 0), mk(0, 0)};
+    int it = 0;
+    for (; it < ntile; it++) {
+        const int b = it & 1;
+        if (threadIdx.x == 0 && it + 1 < ntile) {
+            uint32_t by;
+            const float *src = tile_src(it + 1, &by);
+            bulk_load(sbuf[b ^ 1], src, by, &bar[b ^ 1]);
+        }
+        const int64_t s0 = jb + (int64_t)it * RF_S;
+        const int sn = (int)min((int64_t)RF_S, je - s0);
+        const bool landed = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1));
+        if (!landed) {
+            abort_cta = 1;
+            gdm_dev_error(flags, GDM_ERR_TIMEOUT, 5);
+        }
+        if (valid && landed) {
+            const float *tb = sbuf[b];
+            for (int jj = 0; jj < sn; jj++) {
+                if (self_exclude && s0 + jj == t) continue;
+                const float *sr = tb + jj * L::FLOATS;
+                ff dx = add(two_sum(ti.xh, -sr[0]), mk(__fsub_rn(ti.xl, sr[3]), 0.f));
+                ff dy = add(two_sum(ti.yh, -sr[1]), mk(__fsub_rn(ti.yl, sr[4]), 0.f));
+                ff dz = add(two_sum(ti.zh, -sr[2]), mk(__fsub_rn(ti.zl, sr[5]), 0.f));
+                const ff r = ffsqrt(add(add(sqr(dx), sqr(dy)), sqr(dz)));
+                const ff r1 = recip(r);
+                const ff ri2 = sqr(r1);
+                const ff ri3 = mul(ri2, r1);
+                const ff ri4 = sqr(ri2);
+                const ff u[3] = {mul(dx, r1), mul(dy, r1), mul(dz, r1)};
+                const cff e = cscaleff(expi_ff(mul(kf, r), tab), ie);
+                const ff k2r1 = mul(k2, r1), kri2 = mul(kf, ri2), k2ri2 = mul(k2, ri2), kri3 = mul(kf, ri3);
+                const ff kr1 = mul(kf, r1);
+                const cff a = cmulff(e, cff{sub(k2r1, ri3), kri2});
+                const cff bb = cmulff(e, cff{sub(mulf(ri3, 3.0f), k2r1), neg(mulf(kri2, 3.0f))});
+                // i k x = (-k x.im, k x.re);  i R x = (-R x.im, R x.re)
+                const cff da = caddff(cff{neg(mul(kf, a.im)), mul(kf, a.re)},
+                                      cmulff(e, cff{add(neg(k2ri2), mulf(ri4, 3.0f)), neg(mulf(kri3, 2.0f))}));
+                const cff db = caddff(cff{neg(mul(kf, bb.im)), mul(kf, bb.re)},
+                                      cmulff(e, cff{sub(k2ri2, mulf(ri4, 9.0f)), mulf(kri3, 6.0f)}));
+                const cff dka = caddff(cff{neg(mul(r, a.im)), mul(r, a.re)}, cmulff(e, cff{mulf(kr1, 2.0f), ri2}));
+                const cff dkb = caddff(cff{neg(mul(r, bb.im)), mul(r, bb.re)},
+                                       cmulff(e, cff{neg(mulf(kr1, 2.0f)), neg(mulf(ri2, 3.0f))}));
+                const float4 *mom = (const float4 *)(sr + 8);
+                cff sv[3];
+#pragma unroll
+                for (int aa = 0; aa < 3; aa++) {
+                    const float4 v = mom[aa];
+                    sv[aa] = {mk(v.x, v.y), mk(v.z, v.w)};
+                }
+                const cff us = {add(add(mul(u[0], sv[0].re), mul(u[1], sv[1].re)), mul(u[2], sv[2].re)),
+                                add(add(mul(u[0], sv[0].im), mul(u[1], sv[1].im)), mul(u[2], sv[2].im))};
+                const cff bus = cmulff(bb, us), dbus = cmulff(db, us), dkbus = cmulff(dkb, us);
+                const cff bor = cscaleff(bb, r1);
+#pragma unroll
+                for (int aa = 0; aa < 3; aa++) {
+                    acc[aa] = caddff(acc[aa], caddff(cmulff(a, sv[aa]), cscaleff(bus, u[aa])));
+                    acc[12 + aa] = caddff(acc[12 + aa], caddff(cmulff(dka, sv[aa]), cscaleff(dkbus, u[aa])));
+                }
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+#pragma unroll
+                    for (int aa = 0; aa < 3; aa++) {
+                        const cff t1 = caddff(cmulff(da, sv[aa]), cscaleff(dbus, u[aa]));
+                        // delta_ca (u.s) + u_a s_c - 2 u_c u_a (u.s)
+                        ff w = neg(mulf(mul(u[cc], u[aa]), 2.0f));
+                        if (cc == aa) w = add(w, mk(1.0f, 0.0f));
+                        const cff t2 = caddff(cscaleff(sv[cc], u[aa]), cscaleff(us, w));
+                        acc[3 + 3 * cc + aa] = caddff(acc[3 + 3 * cc + aa], caddff(cscaleff(t1, u[cc]), cmulff(bor, t2)));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (abort_cta) break;
+    }
+    if (abort_cta && threadIdx.x == 0 && it + 1 < ntile) {
+        mbar_wait_bounded(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1));
+    }
+    if (!valid) return;
+    double2 *o = partial + ((c * 2 + qslot) * m + t) * DGF_OUT;  // chunk stride of two right-hand sides
+#pragma unroll
+    for (int a = 0; a < DGF_OUT; a++)
+        o[a] = make_double2((double)acc[a].re.hi + (double)acc[a].re.lo, (double)acc[a].im.hi + (double)acc[a].im.lo);
+}
+
 __global__ void k_prep_dipf_pos(const double *__restrict__ pos, int64_t n, DipF *__restrict__ out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -488,3 +623,42 @@ gdm_status gdm_ff_targets(gdm_ctx *ctx, const double *r, int64_t m, void *out) {
 }
 
 size_t gdm_ff_target_bytes(int64_t m) { return (size_t)m * sizeof(DipF); }
+
+// occupancy (resident CTAs per SM) of the gradient pair kernel, cached
+int gdm_ff_dgreen_occupancy() {
+    static int cached = 0;
+    if (!cached) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dgreen_sum_ff, RF_T, 0) != cudaSuccess || b < 1) {
+            cudaGetLastError();
+            b = 2;
+        }
+        cached = b > 8 ? 8 : b;
+    }
+    return cached;
+}
+
+// Gradient pair sums of the adjoint for the problem's cells, one right-hand side (column q of S, 3 n entries
+// per column, conjugated when conj): sources and targets are the cells (each without its own term); output
+// as the FP64 kernel's partial sums for slot qslot of a right-hand-side pair (partial[c][qslot][t][15]). The
+// workspace must have been prepared (gdm_ff_prepare) for the problem.
+gdm_status gdm_ff_dgreen_sum(gdm_ctx *ctx, const gdm_problem *p, const double2 *S, int q, int conj, int qslot,
+                             int64_t chunk, int nchunks, void *ffws, double2 *partial) {
+    const int64_t n = p->n;
+    ScratchCarver sc(ffws);
+    DipF *dip = sc.take<DipF>(n);
+    float4 *tab = sc.take<float4>(257);
+    float *rec = (float *)sc.take<char>((size_t)n * SrcRecLayout<6, 2>::BYTES);
+    k_prep_src<3, 1><<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(dip, n, S, q, 1, rec, conj);
+    GDM_LAUNCHED(ctx, "prep_src");
+    const double k = sqrt(p->eps_env) * gdm_k0(p);
+    float kk[6];
+    split(k, &kk[0], &kk[1]);
+    split(k * k, &kk[2], &kk[3]);
+    split(1.0 / p->eps_env, &kk[4], &kk[5]);
+    dim3 grid((unsigned)((n + RF_T - 1) / RF_T), (unsigned)nchunks);
+    k_dgreen_sum_ff<<<grid, RF_T, 0, ctx->stream>>>(dip, n, rec, n, kk[0], kk[1], kk[2], kk[3], kk[4], kk[5], tab, chunk,
+                                                    1, qslot, partial, ctx->dflags);
+    GDM_LAUNCHED(ctx, "dgreen_sum_ff");
+    return GDM_OK;
+}
