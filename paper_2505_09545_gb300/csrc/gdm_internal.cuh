@@ -230,7 +230,7 @@ gdm_status gdm_trsv_persistent(gdm_ctx *ctx, gdm_precision prec, const void *A, 
                                const void *dinv);
 size_t gdm_trsv_inv_bytes(int64_t n);
 gdm_status gdm_trsv_prepare(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda,
-                            const int32_t *ipiv, void *dinv);
+                            const int32_t *ipiv, void *dinv, int conj_trans);
 int gdm_lu_block(const gdm_ctx *ctx, gdm_precision prec, int64_t n);
 int gdm_size_class(int64_t n);
 // refine.cu

@@ -717,7 +717,7 @@ static gdm_status solve_gmres(gdm_ctx *ctx, gdm_precision prec, const gdm_proble
     int coarse_local = 0;
     if (use_coarse) {
         GDM_TRY(gdm_pivots_local(ctx, piv_c, nc3, 32, tsync, &coarse_local));
-        if (coarse_local) GDM_TRY(gdm_trsv_prepare(ctx, prec, Ac, nc3, lda_c, piv_c, dinv));
+        if (coarse_local) GDM_TRY(gdm_trsv_prepare(ctx, prec, Ac, nc3, lda_c, piv_c, dinv, 0));
     }
     if (use_blocks) {
         const int smem = (int)(sizeof(float2) * (size_t)max_m * nr);

@@ -152,7 +152,7 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     // persistent block solves when every pivot stays inside its row block
     int local = 0;
     if (prec != GDM_FP64 && !getenv("GDM_TRSV_LAUNCHES")) GDM_TRY(gdm_pivots_local(ctx, ipiv, ns, 32, tsync, &local));
-    if (local) GDM_TRY(gdm_trsv_prepare(ctx, prec, A, ns, lda, ipiv, dinv));
+    if (local) GDM_TRY(gdm_trsv_prepare(ctx, prec, A, ns, lda, ipiv, dinv, adjoint));
     auto lu_solve = [&](void *w) -> gdm_status {
         GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRSV));
         gdm_status st = local ? gdm_trsv_persistent(ctx, prec, A, ns, lda, ipiv, w, ns, n_rhs, adjoint, tsync, dinv)

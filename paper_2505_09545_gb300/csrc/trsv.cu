@@ -23,6 +23,7 @@
 #include "gdm_internal.cuh"
 
 #define TRSV_NBS_F32 128
+#define TRSV_W_MIN_BLOCKS 32  // row blocks from which the last dependency is folded into W_j (3N >= 3,969)
 
 namespace {
 
@@ -96,6 +97,88 @@ __global__ void __launch_bounds__(NBS) k_block_ops(const C *__restrict__ A, int6
     }
 }
 
+// ------------------------------------------------------------------ last-dependency operators
+// W_j folds block j's last dependency into its operator, so that once y of the preceding block (in solve order)
+// is published, y_j = z_j - W_j y_pred needs one 128 x 128 product instead of two:
+//   mode 0 (L):   W = M_j D_{j,j-1},            mode 1 (U):   W = Ui_j D_{j,j+1},
+//   mode 2 (U^H): W = Ui_j^H D_{j-1,j}^H,       mode 3 (L^H): W = M_j^H D_{j+1,j}^H,
+// with D_{i,k} the 128 x 128 block of the factors (rows of block i, columns of block k, zero past n), and
+// z_j = Op_j (b_j - all other dependencies), computed before y_pred is available. CTA (j, mode) forms W in 16-wide
+// K chunks staged in shared memory, each thread an 8 x 8 tile of it; W is stored column-major.
+__global__ void __launch_bounds__(256) k_block_w(const float2 *__restrict__ A, int64_t lda, int64_t n,
+                                                 const float2 *__restrict__ ops, float2 *__restrict__ wops,
+                                                 int mode0) {
+    constexpr int NBS = TRSV_NBS_F32;
+    constexpr int KC = 16;               // K chunk
+    __shared__ float2 Op[NBS][KC + 1];   // Op[r][kk]
+    __shared__ float2 Dk[KC][NBS + 1];   // D[kk][c]
+    const int j = blockIdx.x, mode = mode0 + (int)blockIdx.y;
+    const int nblk = (int)((n + NBS - 1) / NBS);
+    const int pred = (mode == 0 || mode == 2) ? j - 1 : j + 1;
+    float2 *W = wops + (size_t)(4 * j + mode) * NBS * NBS;
+    const int tid = threadIdx.x;
+    if (pred < 0 || pred >= nblk) {
+        for (int e = tid; e < NBS * NBS; e += blockDim.x) W[e] = make_float2(0.f, 0.f);
+        return;
+    }
+    // operator planes: 4j + 2 tri + layout (tri 0: M_j, tri 1: Ui_j; layout 0 column-, 1 row-major)
+    const bool herm = mode >= 2;
+    const int tri = (mode == 1 || mode == 2) ? 1 : 0;
+    const float2 *X = ops + (size_t)(4 * j + 2 * tri + (herm ? 1 : 0)) * NBS * NBS;
+    const int64_t rj = (int64_t)j * NBS, rp = (int64_t)pred * NBS;
+    const int tr = tid >> 4, tc = tid & 15;  // rows 8 tr .. +8, columns 8 tc .. +8
+    float2 acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; a++)
+#pragma unroll
+        for (int b = 0; b < 8; b++) acc[a][b] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < NBS; k0 += KC) {
+        __syncthreads();
+        // Op[r][k0 + kk]: plain operator X[r][k] = X_cm[k NBS + r]; hermitian conj(X[k][r]) = conj(X_rm[k NBS + r])
+        for (int e = tid; e < NBS * KC; e += blockDim.x) {
+            const int r = e % NBS, kk = e / NBS;
+            float2 v = X[(size_t)(k0 + kk) * NBS + r];
+            if (herm) v.y = -v.y;
+            Op[r][kk] = v;
+        }
+        // D_eff[k0 + kk][c]: modes 0/1: A[rj + k, rp + c]; modes 2/3: conj(A[rp + c, rj + k])
+        for (int e = tid; e < KC * NBS; e += blockDim.x) {
+            float2 v = make_float2(0.f, 0.f);
+            if (!herm) {
+                const int kk = e % KC, c = e / KC;
+                const int64_t row = rj + k0 + kk, col = rp + c;
+                if (row < n && col < n) v = A[col * lda + row];
+                Dk[kk][c] = v;
+            } else {
+                const int c = e % NBS, kk = e / NBS;
+                const int64_t row = rp + c, col = rj + k0 + kk;
+                if (row < n && col < n) {
+                    v = A[col * lda + row];
+                    v.y = -v.y;
+                }
+                Dk[kk][c] = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < KC; kk++) {
+            float2 o[8], d[8];
+#pragma unroll
+            for (int a = 0; a < 8; a++) o[a] = Op[8 * tr + a][kk];
+#pragma unroll
+            for (int b = 0; b < 8; b++) d[b] = Dk[kk][8 * tc + b];
+#pragma unroll
+            for (int a = 0; a < 8; a++)
+#pragma unroll
+                for (int b = 0; b < 8; b++) cfma(acc[a][b], o[a], d[b]);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 8; b++)
+#pragma unroll
+        for (int a = 0; a < 8; a++) W[(size_t)(8 * tc + b) * NBS + 8 * tr + a] = acc[a][b];
+}
+
 // ------------------------------------------------------------------ TMA-fed persistent solve
 // Per CTA (row block j): warps 0..7 compute, warp 8 streams data with the TMA engine into a ring of
 // NSTAGE shared-memory stages of HALF = NBS/2 columns x NBS rows (one half of a 128 x 128 block):
@@ -157,8 +240,8 @@ __device__ __forceinline__ void bulk1d(void *dst, const void *src, uint32_t byte
 template <int NR>
 __global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUtensorMap tmA, int64_t n,
                                                    float2 *__restrict__ B, int64_t ldb, int rhs0, int nr_here,
-                                                   int mode, const float2 *__restrict__ ops, int *sync_buf,
-                                                   int *gflags) {
+                                                   int mode, const float2 *__restrict__ ops,
+                                                   const float2 *__restrict__ wops, int *sync_buf, int *gflags) {
     constexpr int NBS = TS_NBS, HALF = TS_HALF;
     extern __shared__ __align__(1024) unsigned char tsm[];
     float2 *ring = (float2 *)tsm;  // [NSTAGE][HALF][NBS]
@@ -187,8 +270,13 @@ __global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUt
     const int j = fwd ? tk : nblk - 1 - tk;
     const int64_t r0 = (int64_t)j * NBS;
     const int nr = (int)min((int64_t)NBS, n - r0);
-    const int nitems = 2 * tk + 2;  // halves of the dependency blocks, then the two halves of the operator
+    // items: halves of the dependency blocks (with W: all but the last), the two halves of the operator, then (with
+    // W, tk >= 1) the two halves of W_j, which applies the last dependency y_pred once it is published
+    const bool has_w = wops != nullptr && tk >= 1;
+    const int ndep = has_w ? tk - 1 : tk;
+    const int nitems = 2 * ndep + 2 + (has_w ? 2 : 0);
     const float2 *opm = ops + (int64_t)(4 * j + 2 * ((mode == 1 || mode == 2) ? 1 : 0) + (mode >= 2 ? 1 : 0)) * NBS * NBS;
+    const float2 *wopm = has_w ? wops + (int64_t)(4 * j + mode) * NBS * NBS : nullptr;
 
     if (warp == 8) {
         // ---------------- producer
@@ -202,7 +290,7 @@ __global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUt
                 float2 *dst = ring + (size_t)st * HALF * NBS;
                 tmbar_expect_tx(&full[st], TS_STAGE_BYTES);
                 const int half = it & 1;
-                if (it < 2 * tk) {
+                if (it < 2 * ndep) {
                     const int s = it / 2;
                     const int k = fwd ? s : nblk - 1 - s;
                     const int64_t k0 = (int64_t)k * NBS;
@@ -210,8 +298,10 @@ __global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUt
                     const int x = (int)(2 * ((mode <= 1) ? r0 : k0));
                     const int y = (int)(((mode <= 1) ? k0 : r0) + half * HALF);
                     tma2d(dst, &tmA, x, y, &full[st]);
-                } else {
+                } else if (it < 2 * ndep + 2) {
                     bulk1d(dst, opm + (size_t)half * HALF * NBS, TS_STAGE_BYTES, &full[st]);
+                } else {
+                    bulk1d(dst, wopm + (size_t)half * HALF * NBS, TS_STAGE_BYTES, &full[st]);
                 }
             }
             // on an abort, let the copies still in flight land before the CTA (and its shared memory) goes away;
@@ -243,11 +333,17 @@ __global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUt
         acc[r][q] = (r < nr && q < nr_here) ? B[(int64_t)(rhs0 + q) * ldb + r0 + r] : make_float2(0.f, 0.f);
     }
     const int r = tid % NBS, hh = tid / NBS;  // row and which 32-column quarter pair (no-trans)
+    float2 zr[NR];                            // z_j = Op_j acc of row r (threads hh == 0), before W_j y_pred
     int it = 0;
-    for (int s = 0; s <= tk; s++) {
-        const bool is_op = (s == tk);
+    // stage s: 0 .. ndep-1 dependencies, ndep the operator, ndep + 1 (has_w) the last dependency through W_j
+    const int nstage = ndep + 1 + (has_w ? 1 : 0);
+    for (int s = 0; s < nstage; s++) {
+        const bool is_op = (s == ndep);
+        const bool is_w = (s == ndep + 1);
         if (!is_op) {
-            const int k = fwd ? s : nblk - 1 - s;
+            // dependency s, or for is_w (s = tk) the preceding block in solve order, dependency tk - 1
+            const int sk = is_w ? s - 1 : s;
+            const int k = fwd ? sk : nblk - 1 - sk;
             const int64_t k0 = (int64_t)k * NBS;
             const int nk = (int)min((int64_t)NBS, n - k0);
             bool ok0 = true;
@@ -296,8 +392,9 @@ __global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUt
             }
             const float2 *sb = ring + (size_t)st * HALF * NBS;  // sb[c * NBS + row]
             const float2(*src)[NR] = is_op ? acc : yk;
-            if (mode <= 1 || is_op) {
-                // y_r -= sum_c M[r][c] v[c] (operator: y_r = sum_c Op[r][c] acc[c]); thread (r, hh) takes 32 columns
+            if (mode <= 1 || is_op || is_w) {
+                // y_r -= sum_c M[r][c] v[c] (operator: y_r = sum_c Op[r][c] acc[c]; W: sum_c W[r][c] y_pred[c]);
+                // thread (r, hh) takes 32 columns
                 const bool herm = is_op && mode >= 2;
 #pragma unroll 8
                 for (int c = hh * 32; c < hh * 32 + 32; c++) {
@@ -334,15 +431,21 @@ __global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUt
             __syncwarp();
             if (lane == 0) tmbar_arrive(&empty[st]);
         }
-        if (mode <= 1 || is_op) {
+        if (mode <= 1 || is_op || is_w) {
             if (hh == 1)
 #pragma unroll
                 for (int q = 0; q < NR; q++) part[r][q] = sum[q];
             asm volatile("bar.sync 1, 256;" ::: "memory");
             if (hh == 0 && r < nr) {
-                if (is_op) {
+                if (is_op && !has_w) {
                     for (int q = 0; q < NR; q++)
                         if (q < nr_here) B[(int64_t)(rhs0 + q) * ldb + r0 + r] = cadd(sum[q], part[r][q]);
+                } else if (is_op) {
+#pragma unroll
+                    for (int q = 0; q < NR; q++) zr[q] = cadd(sum[q], part[r][q]);
+                } else if (is_w) {
+                    for (int q = 0; q < NR; q++)
+                        if (q < nr_here) B[(int64_t)(rhs0 + q) * ldb + r0 + r] = csub(zr[q], cadd(sum[q], part[r][q]));
                 } else {
 #pragma unroll
                     for (int q = 0; q < NR; q++) acc[r][q] = csub(acc[r][q], cadd(sum[q], part[r][q]));
@@ -400,7 +503,8 @@ gdm_status launch_modes_f32(gdm_ctx *ctx, const float2 *A, int64_t lda, int64_t 
         for (int q0 = 0; q0 < n_rhs; q0 += 2) {
             int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
             GDM_CUDA_TRY(ctx, cudaMemsetAsync(sync_buf, 0, sizeof(int) * (nblk + 2), ctx->stream));
-            k_trsv_tma<2><<<nblk, 288, smem, ctx->stream>>>(map, n, B, ldb, q0, nr, modes[mi], ops, sync_buf,
+            const float2 *wops = nblk >= TRSV_W_MIN_BLOCKS ? ops + (size_t)4 * nblk * TS_NBS * TS_NBS : nullptr;
+            k_trsv_tma<2><<<nblk, 288, smem, ctx->stream>>>(map, n, B, ldb, q0, nr, modes[mi], ops, wops, sync_buf,
                                                             ctx->dflags);
             GDM_LAUNCHED(ctx, "trsv_tma");
         }
@@ -409,7 +513,7 @@ gdm_status launch_modes_f32(gdm_ctx *ctx, const float2 *A, int64_t lda, int64_t 
 }
 
 template <class C, int NBS> gdm_status launch_ops(gdm_ctx *ctx, const C *A, int64_t lda, int64_t n, const int32_t *ipiv,
-                                                  C *ops) {
+                                                  C *ops, int conj_trans) {
     const size_t smem = sizeof(C) * NBS * (NBS + 1);
     static bool attr = false;
     if (!attr) {
@@ -420,6 +524,14 @@ template <class C, int NBS> gdm_status launch_ops(gdm_ctx *ctx, const C *A, int6
     const int nblk = (int)((n + NBS - 1) / NBS);
     k_block_ops<C, NBS><<<2 * nblk, NBS, smem, ctx->stream>>>(A, lda, n, ipiv, ops);
     GDM_LAUNCHED(ctx, "block_ops");
+    // the last-dependency operators W of the two modes of this solve direction (after all operator planes), for
+    // systems long enough that the shorter dependency chain repays forming them
+    if (nblk >= TRSV_W_MIN_BLOCKS) {
+        k_block_w<<<dim3((unsigned)nblk, 2), 256, 0, ctx->stream>>>((const float2 *)A, lda, n, (const float2 *)ops,
+                                                                    (float2 *)ops + (size_t)4 * nblk * NBS * NBS,
+                                                                    conj_trans ? 2 : 0);
+        GDM_LAUNCHED(ctx, "block_w");
+    }
     return GDM_OK;
 }
 
@@ -427,10 +539,11 @@ template <class C, int NBS> gdm_status launch_ops(gdm_ctx *ctx, const C *A, int6
 
 size_t gdm_trsv_sync_bytes(int64_t n) { return sizeof(int) * ((n + 31) / 32 + 8); }
 
-// bytes of the FP32 block operators (4 planes of 128 x 128 per row block)
+// bytes of the FP32 block operators (4 planes of 128 x 128 per row block) and the last-dependency operators W
+// (one plane per solve mode and row block)
 size_t gdm_trsv_inv_bytes(int64_t n) {
     const int64_t nb32 = (n + TRSV_NBS_F32 - 1) / TRSV_NBS_F32;
-    return (size_t)4 * nb32 * TRSV_NBS_F32 * TRSV_NBS_F32 * sizeof(float2);
+    return (size_t)8 * nb32 * TRSV_NBS_F32 * TRSV_NBS_F32 * sizeof(float2);
 }
 
 // 1 if all pivots stay inside their nbs-row block (synchronises)
@@ -447,9 +560,9 @@ gdm_status gdm_pivots_local(gdm_ctx *ctx, const int32_t *ipiv, int64_t n, int nb
 }
 
 gdm_status gdm_trsv_prepare(gdm_ctx *ctx, gdm_precision prec, const void *A, int64_t n, int64_t lda,
-                            const int32_t *ipiv, void *ops) {
+                            const int32_t *ipiv, void *ops, int conj_trans) {
     if (prec == GDM_FP64) return GDM_ERR_UNSUPPORTED;  // the FP64 path uses the launch-per-panel solver
-    return launch_ops<float2, TRSV_NBS_F32>(ctx, (const float2 *)A, lda, n, ipiv, (float2 *)ops);
+    return launch_ops<float2, TRSV_NBS_F32>(ctx, (const float2 *)A, lda, n, ipiv, (float2 *)ops, conj_trans);
 }
 
 // solve with the factors: conj_trans = 0: U^{-1} L^{-1} P b; conj_trans = 1: P^T L^{-H} U^{-H} b
