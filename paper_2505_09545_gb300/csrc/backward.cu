@@ -164,7 +164,7 @@ void dg_grid_ff(gdm_ctx *ctx, int64_t m, int64_t n, int64_t *chunk, int *nchunks
     *chunk = ch0;
     *nchunks = nc_max;
     for (int nc = 1; nc <= nc_max; nc++) {
-        const int64_t ch = ((n + nc - 1) / nc + DG_S - 1) / DG_S * DG_S;
+        const int64_t ch = (n + nc - 1) / nc;  // any chunk length: the kernel stages partial tiles
         const int ncr = (int)((n + ch - 1) / ch);
         if (ncr > nc_max) continue;
         const int64_t ctas = tb * ncr, waves = (ctas + slots - 1) / slots;

@@ -932,7 +932,7 @@ __global__ void k_residual_finalize(const double2 *__restrict__ partial, int nch
     }
 }
 
-// Grid of a Green-sum launch: ceil(m / GS_T) target blocks times nc source chunks (multiples of GS_S sources).
+// Grid of a Green-sum launch: ceil(m / GS_T) target blocks times nc source chunks of ceil(n / nc) sources.
 // The kernels are ALU-bound and a CTA's time is about proportional to its chunk, so the last partial wave of
 // CTAs idles the rest of the GPU; nc is the number of chunks (at most 64) that wastes the least of the
 // occ x SMs resident-CTA slots over the whole launch (fewest chunks among equals).
@@ -941,10 +941,10 @@ static void green_grid(gdm_ctx *ctx, int64_t m, int64_t n, int occ, int64_t *chu
     const int64_t slots = (int64_t)(occ < 1 ? 1 : occ) * ctx->sm_count;
     int64_t maxc = (n + GS_S - 1) / GS_S;
     if (maxc > 64) maxc = 64;
-    int64_t best_ch = (n + GS_S - 1) / GS_S * GS_S;
+    int64_t best_ch = n;
     double best = -1.0;
     for (int64_t nc = 1; nc <= maxc; nc++) {
-        const int64_t ch = ((n + nc - 1) / nc + GS_S - 1) / GS_S * GS_S;
+        const int64_t ch = (n + nc - 1) / nc;  // any chunk length: the kernels stage partial tiles
         const int64_t ctas = tb * ((n + ch - 1) / ch);
         const int64_t waves = (ctas + slots - 1) / slots;
         const double eff = (double)ctas / (double)(waves * slots);
