@@ -30,10 +30,9 @@ FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 f
 # FP32 thread instructions per (target, source) pair, 2 right-hand sides, of the GMRES FP32 operator
 # k_green_sum_f32 (ncu count: profiles/green_sum_f32_gmres_cuboid20x15x10_ncu.md)
 FP32_OPERATOR_INST_PER_PAIR = 204.0
-# FP64 operations per ordered pair of the adjoint's gradient pair sum k_dgreen_sum<1> (G s, dG/dr s, dG/dk s;
-# DADD + DMUL + 2 DFMA, ncu count: profiles/dgreen_sum_cylinder_ncu.md)
-DGREEN_FP64_FLOPS_PER_PAIR = None
-FP64_PEAK_TFLOPS = 1.05   # torch float64 matmul on GB300
+# FP32 thread instructions per ordered pair of the adjoint's double-float gradient pair sum k_dgreen_sum_ff (G s,
+# dG/dr s, dG/dk s; one right-hand side; ncu count: profiles/dgreen_sum_ff_cylinder_ncu.md)
+DGREEN_FF_INST_PER_PAIR = 3627.0
 
 
 def load_peaks():
@@ -223,12 +222,13 @@ def adjoint_leg(G, ctx, dev, precision, warmup, steps):
     grad = {"gradient_ms": ph["gradient"], "adjoint_solves_ms": ph["correction_solves"],
             "adjoint_residual_ms": ph["residual"], "pairs": pairs,
             "note": "one wavelength's gdm_backward on one context (the timed spectrum runs the 8 concurrently)"}
-    if DGREEN_FP64_FLOPS_PER_PAIR and ph["gradient"] > 0:
-        ach = pairs * DGREEN_FP64_FLOPS_PER_PAIR / (ph["gradient"] / 1e3) / 1e12
-        grad["roofline"] = {"bound": "alu", "kernel": "k_dgreen_sum (FP64 pair sums of G, dG/dr, dG/dk)",
-                            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": ach / FP64_PEAK_TFLOPS, "flops_per_pair": DGREEN_FP64_FLOPS_PER_PAIR,
-                            "peak_source": "FP64 rate measured with a torch float64 matmul on GB300"}
+    if DGREEN_FF_INST_PER_PAIR and ph["gradient"] > 0:
+        peak = 152 * 128 * 2.07e9
+        ach = pairs * DGREEN_FF_INST_PER_PAIR / (ph["gradient"] / 1e3)
+        grad["roofline"] = {"bound": "alu", "kernel": "k_dgreen_sum_ff (double-float pair sums of G, dG/dr, dG/dk)",
+                            "achieved": ach, "peak": peak, "unit": "FP32 inst/s", "frac": ach / peak,
+                            "inst_per_pair": DGREEN_FF_INST_PER_PAIR,
+                            "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock)"}
     return {"value": f + b, "unit": "s", "forward_s": f, "backward_s": b, "precision": precision,
             "backward_one_wavelength": grad,
             "workload": f"cylinder r=80 h=100 d=10 nm (N={cyl.n}), eps=12.25+0.05i, {wls.shape[0]} wavelengths "
