@@ -227,6 +227,7 @@ gdm_status gdm_destroy(gdm_ctx *ctx) {
     for (int i = 0; i < ctx->npool; i++) gdm_destroy(ctx->pool[i]);
     ctx->npool = 0;
     if (ctx->stream || ctx->ws) cudaStreamSynchronize(ctx->stream);
+    gdm_glu_release(ctx);
     if (ctx->owns_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->dflags) cudaFree(ctx->dflags);

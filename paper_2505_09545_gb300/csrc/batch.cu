@@ -42,9 +42,8 @@ gdm_status gdm_ensure_pool(gdm_ctx *ctx, int want) {
 
 namespace {
 
-// the full per-item path on one child context
-gdm_status run_item(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it, const gdm_solve_opts *opts,
-                    gdm_solve_info *info) {
+// plane wave (when e0 is given) and, unless the item is factored already, assembly
+gdm_status item_inputs(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it, bool assemble) {
     const gdm_problem *p = &it->prob;
     gdm_params_reset(c);
     if (it->e0) {
@@ -54,7 +53,14 @@ gdm_status run_item(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it, co
         GDM_TRY(gdm_launch_planewave(c, p->pos, p->n, k, n_env, it->e0, it->khat ? it->khat : zhat, it->n_rhs,
                                      p->kind, it->F0));
     }
-    if (!(opts && (opts->flags & GDM_SOLVE_FACTORED))) GDM_TRY(gdm_launch_assemble(c, p, prec, it->A, it->lda));
+    if (assemble) GDM_TRY(gdm_launch_assemble(c, p, prec, it->A, it->lda));
+    return GDM_OK;
+}
+
+// factorisation (unless FACTORED), refined solve and cross sections of one item
+gdm_status item_solve(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it, const gdm_solve_opts *opts,
+                      gdm_solve_info *info) {
+    const gdm_problem *p = &it->prob;
     gdm_status s = gdm_solve_core(c, p, prec, it->A, it->lda, it->ipiv, it->F0, it->F, it->n_rhs, opts, info);
     if (s != GDM_OK) return s;
     if (it->sigma) {
@@ -71,6 +77,77 @@ gdm_status run_item(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it, co
                                           it->sigma + 2 * it->n_rhs));
     }
     return GDM_OK;
+}
+
+// the full per-item path on one child context
+gdm_status run_item(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it, const gdm_solve_opts *opts,
+                    gdm_solve_info *info) {
+    GDM_TRY(item_inputs(c, prec, it, !(opts && (opts->flags & GDM_SOLVE_FACTORED))));
+    return item_solve(c, prec, it, opts, info);
+}
+
+// Items factored together by the grouped LU (batch_lu.cu): TF32 factors with in-panel pivots, matrices
+// whose storage the tensor maps accept (16-byte aligned, even leading dimension); GDM_BATCH_POOL keeps the
+// per-item factorisations (diagnostics)
+bool grouped_ok(gdm_precision prec, const gdm_batch_item *items, int n_items, const gdm_solve_opts *opts) {
+    if (prec != GDM_TF32_REFINE || n_items < 2 || getenv("GDM_BATCH_POOL")) return false;
+    if (opts && (opts->flags & (GDM_SOLVE_FACTORED | GDM_SOLVE_GLOBAL_PIVOT))) return false;
+    for (int i = 0; i < n_items; i++)
+        if (((uintptr_t)items[i].A & 15) || (items[i].lda & 1)) return false;
+    return true;
+}
+
+// outer block width of the grouped LU: GDM_BATCH_NB if set, else the tuned width, else 256
+int grouped_nb(const gdm_ctx *ctx) {
+    const char *e = getenv("GDM_BATCH_NB");
+    int nb = e ? atoi(e) : ctx->glu_nb;
+    if (nb < 64 || nb > 512 || nb % 32) nb = 256;
+    return nb;
+}
+
+// plane waves and assembly on the pool, one grouped factorisation on the context stream, then refined
+// solves and cross sections on the pool. An item whose in-panel pivots fail the certificate (or that met
+// a zero pivot) is re-assembled and factored alone with pivots over whole columns.
+gdm_status solve_grouped(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_item *items, int n_items,
+                         const gdm_solve_opts *opts, int n_streams, gdm_solve_info *infos,
+                         const std::vector<int64_t> &size) {
+    GDM_TRY(gdm_run_pool(ctx, n_items, size.data(), n_streams, infos,
+                         [&](gdm_ctx *c, int, int i, gdm_solve_info *) { return item_inputs(c, prec, &items[i], true); },
+                         nullptr));
+    std::vector<float2 *> A((size_t)n_items);
+    std::vector<int64_t> lda((size_t)n_items);
+    std::vector<int32_t *> ipiv((size_t)n_items);
+    std::vector<float> growth((size_t)n_items, 0.f);
+    std::vector<int> st((size_t)n_items, 0);
+    for (int i = 0; i < n_items; i++) {
+        A[i] = (float2 *)items[i].A;
+        lda[i] = items[i].lda;
+        ipiv[i] = items[i].ipiv;
+    }
+    float ms = 0.f;
+    GDM_TRY(gdm_glu_factor(ctx, n_items, A.data(), lda.data(), size.data(), ipiv.data(), grouped_nb(ctx),
+                           growth.data(), st.data(), &ms));
+    gdm_solve_opts fo = {0, 0, 0.0};
+    if (opts) fo = *opts;
+    gdm_solve_opts go = fo;
+    fo.flags |= GDM_SOLVE_FACTORED;
+    go.flags |= GDM_SOLVE_GLOBAL_PIVOT;
+    return gdm_run_pool(
+        ctx, n_items, size.data(), n_streams, infos,
+        [&](gdm_ctx *c, int, int i, gdm_solve_info *inf) {
+            const gdm_batch_item *it = &items[i];
+            if (st[i] != GDM_OK || !(growth[i] <= (float)GDM_PIVOT_GROWTH_LIMIT)) {
+                GDM_TRY(item_inputs(c, prec, it, true));
+                gdm_status s = item_solve(c, prec, it, &go, inf);
+                inf->refactored = 1;
+                return s;
+            }
+            gdm_status s = item_solve(c, prec, it, &fo, inf);
+            inf->factor_ms = ms;
+            inf->pivot_growth = growth[i];
+            return s;
+        },
+        nullptr);
 }
 
 // grad[i] += sum_w acc[w][i] over the children's gradient accumulators (5 doubles per cell: 3 position,
@@ -132,6 +209,8 @@ gdm_status gdm_solve_batched(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_i
     GDM_GUARD_BEGIN
     std::vector<int64_t> size((size_t)n_items);
     for (int i = 0; i < n_items; i++) size[i] = items[i].prob.n * items[i].prob.kind;
+    if (grouped_ok(prec, items, n_items, opts))
+        return solve_grouped(ctx, prec, items, n_items, opts, n_streams, infos, size);
     return gdm_run_pool(ctx, n_items, size.data(), n_streams, infos,
                     [&](gdm_ctx *c, int, int i, gdm_solve_info *inf) { return run_item(c, prec, &items[i], opts, inf); },
                     nullptr);

@@ -47,6 +47,10 @@ struct gdm_ctx {
     gdm_ctx *pool[GDM_POOL_MAX] = {nullptr};
     int npool = 0;
     bool owns_stream = false;
+    // schedule, tables and captured graph of the last grouped factorisation (batch_lu.cu), and its outer
+    // block width (0 = built-in default), set by gdm_autotune_batched
+    void *glu = nullptr;
+    int glu_nb = 0;
 };
 #define GDM_PH_MAX 32768
 #define GDM_PROF_MAX 4096
@@ -246,6 +250,119 @@ gdm_status gdm_launch_nearfield_backward(gdm_ctx *ctx, const gdm_problem *p, con
                                          int64_t m, int n_rhs, const double *e0, const double *khat, const double *gE,
                                          double *gF_accum, double *grad_pos, double *grad_eps,
                                          double *grad_wavelength);
+
+// ------------------------------------------------------------------ grouped LU of a batch (batch_lu.cu)
+// The problems of a batch are factored in lock step: every launch covers one step (a panel, or the trailing
+// update of an outer block) of all problems that still have it, through a table sorted by decreasing size,
+// so that the problems of a launch are a prefix of the table and the launch's work is split by a prefix sum
+// of per-problem counts (CTA b belongs to problem i when prefix[i] <= b < prefix[i + 1]).
+struct GluItem {
+    float2 *A;
+    int64_t lda, n;
+    int32_t *ipiv;
+    unsigned *growth;  // pivot certificate (float bits), as gdm_lu_factor's growth record
+    int *status;       // [0] first error status, [1] detail (the layout of the context flags)
+    int *ticket;       // finish counter of the panel kernels
+    float *lx;         // TF32 embedding of the current outer block's L (rows from the block's first row on):
+                       // real rows 2 (r - b0) and 2 (r - b0) + 1 of 2 nbo floats each
+};
+struct alignas(64) GluMap {  // an encoded TMA descriptor (CUtensorMap)
+    unsigned char bytes[128];
+};
+struct GluMaps {
+    GluMap lx, b, c;  // A operand (the embedding of L), B operand and C chunks (both on the matrix)
+};
+enum { GLU_PANEL = 0, GLU_TRAIL = 1 };
+#define GLU_SWAP_COLS 128  // columns per CTA of the grouped interchange and solve
+
+// problem owning work unit b: the largest i in [0, na) with prefix[i] <= b (called by a whole warp; two rounds
+// of 32 parallel probes cover 1024 problems, more rounds beyond)
+__device__ __forceinline__ int glu_find_item(const int *__restrict__ prefix, int na, int b) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = na;
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) / 32;
+        const int idx = lo + lane * step;
+        const bool ok = idx < hi && __ldg(&prefix[idx]) <= b;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        lo += (31 - __clz(m)) * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
+// Regions of C updated by one grouped GEMM launch for a problem of order n (complex rows x columns):
+//   GLU_PANEL after the 32-column panel at c0 of the block [b0, b0 + nbo): the block's columns right of the
+//     panel, all rows below it (A: Ma x Na), and the block's rows below the panel, columns right of the block
+//     (B: Mb x Nb); both with K = 32 (the panel). The C block right of and below the outer block waits for
+//   GLU_TRAIL after the block: rows and columns right of it (A: Ma x Na, K = nbo).
+__host__ __device__ inline void glu_regions(int kind, int64_t n, int64_t b0, int64_t c0, int nbo, int64_t &Ma,
+                                            int64_t &Na, int64_t &Mb, int64_t &Nb) {
+    if (kind == GLU_PANEL) {
+        const int64_t be = (b0 + nbo < n) ? b0 + nbo : n, base = c0 + 32;
+        Ma = n - base;
+        Na = be - base;
+        Mb = Na;
+        Nb = n - be;
+    } else {
+        Ma = Na = n - (b0 + nbo);
+        Mb = Nb = 0;
+    }
+    if (Ma <= 0 || Na <= 0) Ma = Na = 0;
+    if (Mb <= 0 || Nb <= 0) Mb = Nb = 0;
+}
+// 128 x 256 tiles of the real embedding (2M real rows) of a region
+__host__ __device__ inline int glu_region_tiles(int64_t M, int64_t N) {
+    return (M > 0 && N > 0) ? (int)((2 * M + 127) / 128) * (int)((N + 255) / 256) : 0;
+}
+__host__ __device__ inline int glu_tiles(int kind, int64_t n, int64_t b0, int64_t c0, int nbo) {
+    int64_t Ma, Na, Mb, Nb;
+    glu_regions(kind, n, b0, c0, nbo, Ma, Na, Mb, Nb);
+    return glu_region_tiles(Ma, Na) + glu_region_tiles(Mb, Nb);
+}
+// tile t of a problem: real-row tile mt, first column col0 (relative to the region origin, which is the
+// launch's base row and column) and width ncols, real rows below mlim updated. Inside a region, groups of 8
+// column tiles with the row tile varying slowest across a group's columns (operand tiles shared in L2).
+struct GluTile {
+    int mt, col0, ncols, mlim;
+};
+__host__ __device__ inline GluTile glu_tile(int kind, int64_t n, int64_t b0, int64_t c0, int nbo, int t) {
+    int64_t Ma, Na, Mb, Nb;
+    glu_regions(kind, n, b0, c0, nbo, Ma, Na, Mb, Nb);
+    const int tA = glu_region_tiles(Ma, Na);
+    int64_t M = Ma, N = Na, off = 0;
+    if (t >= tA) {
+        t -= tA;
+        M = Mb;
+        N = Nb;
+        off = Na;
+    }
+    const int num_m = (int)((2 * M + 127) / 128), num_n = (int)((N + 255) / 256);
+    const int per_group = num_m * 8, g = t / per_group, idx = t - g * per_group;
+    const int gn = (num_n - g * 8) < 8 ? (num_n - g * 8) : 8;
+    const int nt = g * 8 + idx % gn;
+    GluTile r;
+    r.mt = idx / gn;
+    r.col0 = (int)(off + (int64_t)nt * 256);
+    r.ncols = (int)((N - (int64_t)nt * 256) < 256 ? (N - (int64_t)nt * 256) : 256);
+    r.mlim = (int)(2 * M);
+    return r;
+}
+// launches of the grouped LU (lu.cu, lu_tc.cu)
+gdm_status gdm_glu_panel(gdm_ctx *ctx, const GluItem *items, const int *prefix, int na, int nblocks, int64_t b0,
+                         int64_t c0, int nbo);
+gdm_status gdm_glu_swap_trsm(gdm_ctx *ctx, const GluItem *items, const int *prefix, int na, int nblocks,
+                             int64_t c0);
+gdm_status gdm_glu_gemm(gdm_ctx *ctx, const GluItem *items, const GluMaps *maps, const int *prefix, int na,
+                        int ntiles, int kind, int64_t b0, int64_t c0, int nbo);
+gdm_status gdm_glu_gemm_init(gdm_ctx *ctx);
+gdm_status gdm_glu_panel_init(gdm_ctx *ctx);
+// encodes the tensor maps of every problem (host); false if the driver's encoder is unavailable or refuses
+bool gdm_glu_encode(const GluItem *items, int n_items, int nbo, GluMaps *maps);
+// the grouped factorisation of a batch (batch_lu.cu) and the release of its cached schedule
+gdm_status gdm_glu_factor(gdm_ctx *ctx, int n_items, float2 *const *A, const int64_t *lda, const int64_t *n,
+                          int32_t *const *ipiv, int nbo, float *growth, int *status, float *ms);
+void gdm_glu_release(gdm_ctx *ctx);
 
 // problem helpers
 static inline double gdm_k0(const gdm_problem *p) { return 2.0 * 3.14159265358979323846 / p->wavelength; }

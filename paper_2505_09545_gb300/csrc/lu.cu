@@ -241,13 +241,15 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(C *__restrict__ A, int6
 // Every CTA of a panel launch reads the unfactored diagonal block from A at its start, so the factored
 // block may only be stored once no CTA can still read it: the last CTA to finish (ticket in the flags)
 // stores its own copy and returns the ticket to 0 for the next launch.
+// (ticket: the finish counter; nblk: the CTAs that factor this panel)
 template <class C>
-__device__ void panel_store_diag_last(C *A, int64_t lda, int64_t c0, int w, const C *D, int ldd, int *flags) {
+__device__ void panel_store_diag_last(C *A, int64_t lda, int64_t c0, int w, const C *D, int ldd, int *ticket,
+                                      int nblk) {
     __shared__ int s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = atomicAdd(&flags[GDM_FLAG_PANEL_TICKET], 1) == (int)gridDim.x - 1;
+        s_last = atomicAdd(ticket, 1) == nblk - 1;
     }
     __syncthreads();
     if (!s_last) return;
@@ -255,7 +257,11 @@ __device__ void panel_store_diag_last(C *A, int64_t lda, int64_t c0, int w, cons
         int r = e % w, c = e / w;
         A[(c0 + c) * lda + c0 + r] = D[r * ldd + c];
     }
-    if (threadIdx.x == 0) atomicExch(&flags[GDM_FLAG_PANEL_TICKET], 0);
+    if (threadIdx.x == 0) atomicExch(ticket, 0);
+}
+template <class C>
+__device__ void panel_store_diag_last(C *A, int64_t lda, int64_t c0, int w, const C *D, int ldd, int *flags) {
+    panel_store_diag_last(A, lda, c0, w, D, ldd, &flags[GDM_FLAG_PANEL_TICKET], (int)gridDim.x);
 }
 
 template <class C>
@@ -407,8 +413,8 @@ __device__ __forceinline__ float2 subst_step(float2 *x, const float2 *__restrict
 template <int W>
 __device__ __forceinline__ void diag_step(float2 *r, int t, int lane, int &pos, bool &done, unsigned &m,
                                           unsigned &key, float2 (*Uz)[2 * NBP], float2 (*Lr)[NBP + 1], int64_t c0,
-                                          int32_t *__restrict__ ipiv, int *flags) {
-    if (blockIdx.x == 0 && lane == 0) {
+                                          int32_t *__restrict__ ipiv, int *flags, bool first) {
+    if (first && lane == 0) {
         ipiv[c0 + t] = (int32_t)(c0 + key);
         if (!(__uint_as_float(m) > 0.f)) gdm_dev_error(flags, GDM_ERR_SINGULAR, (int)(c0 + t));
     }
@@ -441,9 +447,22 @@ __device__ __forceinline__ void diag_step(float2 *r, int t, int lane, int &pos, 
     r[W - 1] = make_float2(0.f, 0.f);
 }
 
-__global__ void __launch_bounds__(128) k_panel_local_f32(float2 *__restrict__ A, int64_t lda, int64_t n, int64_t c0,
-                                                         int w, int32_t *__restrict__ ipiv, unsigned *growth,
-                                                         int *flags) {
+// The body is shared with the grouped panel of a batch (GROUPED): CTA bid of nblk factoring this panel, the
+// finish counter in *ticket, and the multipliers of every full panel also written, rounded to TF32, into the
+// real embedding that the batch's tensor-core updates read (Lx: real rows 2 (r - b0) and 2 (r - b0) + 1,
+// columns lx_col .. lx_col + 64 of rows of lx_pitch floats), so that no separate pass reads L again. There
+// the rows run in CTA-wide rounds whose multipliers pass through shared memory (Ls, dynamic), so that the
+// embedding goes out in coalesced 16-byte stores.
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+template <bool GROUPED>
+__device__ __forceinline__ void panel_f32_body(float2 *__restrict__ A, int64_t lda, int64_t n, int64_t c0, int w,
+                                               int32_t *__restrict__ ipiv, unsigned *growth, int *ticket,
+                                               int *flags, int bid, int nblk, float *__restrict__ Lx,
+                                               int64_t b0, int lx_col, int lx_pitch, float2 (*Ls)[NBP + 1]) {
     __shared__ float2 Uz[NBP][2 * NBP];   // U in position order, row t = columns t.. ; zero elsewhere
     __shared__ float2 Lr[NBP][NBP + 1];   // multipliers of lane q's row, by step
     __shared__ float2 F[NBP][NBP + 1];    // factored diagonal block in position order (for the final store)
@@ -451,8 +470,8 @@ __global__ void __launch_bounds__(128) k_panel_local_f32(float2 *__restrict__ A,
     __shared__ float inv_pa[NBP];
     __shared__ int posof[NBP];
     const int tid = threadIdx.x, lane = tid & 31;
-    const int64_t r_first = c0 + w + blockIdx.x * (int64_t)blockDim.x + tid;
-    const int64_t r_step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t r_first = c0 + w + bid * (int64_t)blockDim.x + tid;
+    const int64_t r_step = (int64_t)nblk * blockDim.x;
     for (int e = tid; e < NBP * 2 * NBP; e += blockDim.x) (&Uz[0][0])[e] = make_float2(0.f, 0.f);
     // the first row below is loaded while warp 0 factors the diagonal block
     float2 x[NBP];
@@ -476,13 +495,13 @@ __global__ void __launch_bounds__(128) k_panel_local_f32(float2 *__restrict__ A,
         // windows shrink with the columns left: 32 - t <= W
         int t = 0;
 #pragma unroll 1
-        for (; t < w && t < 8; t++) diag_step<32>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags);
+        for (; t < w && t < 8; t++) diag_step<32>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, bid == 0);
 #pragma unroll 1
-        for (; t < w && t < 16; t++) diag_step<24>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags);
+        for (; t < w && t < 16; t++) diag_step<24>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, bid == 0);
 #pragma unroll 1
-        for (; t < w && t < 24; t++) diag_step<16>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags);
+        for (; t < w && t < 24; t++) diag_step<16>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, bid == 0);
 #pragma unroll 1
-        for (; t < w; t++) diag_step<8>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags);
+        for (; t < w; t++) diag_step<8>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, bid == 0);
         if (lane < w) posof[lane] = pos;
     }
     __syncthreads();
@@ -496,31 +515,89 @@ __global__ void __launch_bounds__(128) k_panel_local_f32(float2 *__restrict__ A,
     }
     __syncthreads();
     float worst = 0.f;
-    for (int64_t r = r_first; r < n; r += r_step) {
-        if (r != r_first) {
-#pragma unroll
-            for (int c = 0; c < NBP; c++) x[c] = (c < w) ? A[(c0 + c) * lda + r] : make_float2(0.f, 0.f);
-        }
-        int k = 0;
 #define PANEL_PHASE(W_, KEND)                                                                      \
     for (; k < w && k < (KEND); k++) {                                                             \
         worst = fmaxf(worst, (fabsf(x[0].x) + fabsf(x[0].y)) * inv_pa[k]);                         \
-        A[(c0 + k) * lda + r] = subst_step<W_>(x, &Uz[k][k], invd[k]);                             \
+        const float2 l_ = subst_step<W_>(x, &Uz[k][k], invd[k]);                                   \
+        A[(c0 + k) * lda + r] = l_;                                                                \
+        if (GROUPED) Ls[tid][k] = l_;                                                              \
     }
-#pragma unroll 1
-        PANEL_PHASE(32, 8)
-#pragma unroll 1
-        PANEL_PHASE(24, 16)
-#pragma unroll 1
-        PANEL_PHASE(16, 24)
-#pragma unroll 1
-        PANEL_PHASE(8, 32)
+#define PANEL_ROW()                                                                                \
+    {                                                                                              \
+        int k = 0;                                                                                 \
+        _Pragma("unroll 1") PANEL_PHASE(32, 8)                                                     \
+        _Pragma("unroll 1") PANEL_PHASE(24, 16)                                                    \
+        _Pragma("unroll 1") PANEL_PHASE(16, 24)                                                    \
+        _Pragma("unroll 1") PANEL_PHASE(8, 32)                                                     \
+    }
+    if (!GROUPED) {
+        for (int64_t r = r_first; r < n; r += r_step) {
+            if (r != r_first) {
+#pragma unroll
+                for (int c = 0; c < NBP; c++) x[c] = (c < w) ? A[(c0 + c) * lda + r] : make_float2(0.f, 0.f);
+            }
+            PANEL_ROW()
+        }
+    } else {
+        for (int64_t rb = r_first - tid; rb < n; rb += r_step) {
+            const int64_t r = rb + tid;
+            if (r < n) {
+                if (rb != r_first - tid) {
+#pragma unroll
+                    for (int c = 0; c < NBP; c++) x[c] = (c < w) ? A[(c0 + c) * lda + r] : make_float2(0.f, 0.f);
+                }
+                PANEL_ROW()
+            }
+            __syncthreads();
+            if (w == NBP) {
+                // real rows 2 (r - b0) + h, floats lx_col + 4 q .. + 4 (the column pairs k = 2q, 2q + 1)
+                const int nrow = (int)min((int64_t)blockDim.x, n - rb);
+                for (int e = tid; e < nrow * 32; e += blockDim.x) {
+                    const int i = e >> 5, h = (e >> 4) & 1, q = e & 15;
+                    const float2 a = Ls[i][2 * q], b = Ls[i][2 * q + 1];
+                    const float4 v = h ? make_float4(tf32_rna(a.y), tf32_rna(a.x), tf32_rna(b.y), tf32_rna(b.x))
+                                       : make_float4(tf32_rna(a.x), tf32_rna(-a.y), tf32_rna(b.x), tf32_rna(-b.y));
+                    *(float4 *)(Lx + (2 * (rb + i - b0) + h) * (int64_t)lx_pitch + lx_col + 4 * q) = v;
+                }
+            }
+            __syncthreads();
+        }
+    }
+#undef PANEL_ROW
 #undef PANEL_PHASE
-    }
     for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_down_sync(0xffffffffu, worst, o));
     if (lane == 0 && worst > 0.f) atomicMax(growth, __float_as_uint(worst));
-    panel_store_diag_last(A, lda, c0, w, &F[0][0], NBP + 1, flags);
+    panel_store_diag_last(A, lda, c0, w, &F[0][0], NBP + 1, ticket, nblk);
 }
+
+__global__ void __launch_bounds__(128) k_panel_local_f32(float2 *__restrict__ A, int64_t lda, int64_t n, int64_t c0,
+                                                         int w, int32_t *__restrict__ ipiv, unsigned *growth,
+                                                         int *flags) {
+    panel_f32_body<false>(A, lda, n, c0, w, ipiv, growth, &flags[GDM_FLAG_PANEL_TICKET], flags, blockIdx.x,
+                          gridDim.x, nullptr, 0, 0, 0, nullptr);
+}
+
+// Grouped panel of a batch (lock-step over the problems of a decreasing-size table): CTA b works for the
+// problem whose CTA range [prefix[i], prefix[i+1]) holds b, on its panel [c0, c0 + w) of the outer block
+// [b0, b0 + nbo); pivots, certificate and errors go to the problem's own records.
+__global__ void __launch_bounds__(128) k_glu_panel(const GluItem *__restrict__ items, const int *__restrict__ prefix,
+                                                   int na, int64_t b0, int64_t c0, int nbo) {
+    extern __shared__ float2 glu_ls[];  // 128 x (NBP + 1) multipliers of a round of rows
+    __shared__ int s_item;
+    if (threadIdx.x < 32) {
+        const int i = glu_find_item(prefix, na, (int)blockIdx.x);
+        if (threadIdx.x == 0) s_item = i;
+    }
+    __syncthreads();
+    const int i = s_item;
+    const GluItem g = items[i];
+    const int64_t be = min(b0 + nbo, g.n);
+    const int w = (int)min((int64_t)NBP, be - c0);
+    panel_f32_body<true>(g.A, g.lda, g.n, c0, w, g.ipiv, g.growth, g.ticket, g.status, (int)blockIdx.x - prefix[i],
+                         prefix[i + 1] - prefix[i], g.lx, b0, (int)(2 * (c0 - b0)), 2 * nbo,
+                         (float2(*)[NBP + 1])glu_ls);
+}
+constexpr int GLU_PANEL_SMEM = 128 * (NBP + 1) * (int)sizeof(float2);
 
 // ------------------------------------------------------------------ block operator for the U12 row block
 // For the outer block [b0, b0+nb) (nb a multiple of 32, pivots of each 32-row panel inside that panel),
@@ -662,11 +739,6 @@ __global__ void __launch_bounds__(512) k_panels_apply(float2 *__restrict__ A, in
 // T[i + c * nb] = A[b0 + i, c0 + c] and zero the source (the U12 GEMM accumulates into it)
 // round_tf32: T rounded to TF32 (nearest), for the single-product updates whose tensor cores would otherwise
 // truncate it
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
 __global__ void k_gather_zero(float2 *__restrict__ A, int64_t lda, int64_t b0, int64_t c0, int nb, int64_t nc,
                               float2 *__restrict__ T, int round_tf32) {
     const int64_t total = (int64_t)nb * nc;
@@ -745,6 +817,100 @@ __global__ void k_trsm_small(C *__restrict__ A, int64_t lda, int64_t c0, int w, 
         if (lane > i && lane < w) cfms(v, L[lane][i], xi);
     }
     if (lane < w) bcol[lane] = v;
+}
+
+// Grouped interchanges and triangular solve of a batch, after the panel at c0 (32 columns, its pivots inside
+// its own 32 rows) of every problem that has columns right of it: rows c0 .. c0 + 32 of those columns get
+// the panel's interchanges in order, then L11^{-1} (unit lower), and are stored rounded to TF32 (nearest),
+// the value the tensor-core updates read as their B operand. One warp solves 4 columns side by side (lane =
+// row), GLU_SWAP_COLS columns per CTA; CTA b works for the problem whose range of the prefix sum holds b.
+__global__ void __launch_bounds__(256) k_glu_swap_trsm(const GluItem *__restrict__ items,
+                                                       const int *__restrict__ prefix, int na, int64_t c0) {
+    __shared__ float2 L[NBP][NBP + 1];
+    __shared__ int src[NBP], piv[NBP];
+    __shared__ int s_item;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        const int i = glu_find_item(prefix, na, (int)blockIdx.x);
+        if (lane == 0) s_item = i;
+    }
+    __syncthreads();
+    const int i = s_item;
+    float2 *__restrict__ A = items[i].A;
+    const int64_t lda = items[i].lda, n = items[i].n;
+    for (int e = threadIdx.x; e < NBP * NBP; e += blockDim.x) {
+        const int r = e % NBP, c = e / NBP;
+        L[r][c] = A[(c0 + c) * lda + c0 + r];
+    }
+    if (warp == 0) {
+        // final position -> source row of the interchange sequence (position t swapped with ipiv[t])
+        piv[lane] = items[i].ipiv[c0 + lane] - (int)c0;
+        src[lane] = lane;
+        __syncwarp();
+        if (lane == 0) {
+            for (int t = 0; t < NBP; t++) {
+                const int qt = piv[t];
+                if (qt > t && qt < NBP) {
+                    const int a = src[t];
+                    src[t] = src[qt];
+                    src[qt] = a;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int sr = src[lane];
+#pragma unroll 1
+    for (int grp = 0; grp < GLU_SWAP_COLS / 32; grp++) {
+        const int64_t col0 = c0 + NBP + (int64_t)(blockIdx.x - prefix[i]) * GLU_SWAP_COLS + grp * 32 + warp * 4;
+        if (col0 >= n) break;
+        float2 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            v[j] = col0 + j < n ? A[(col0 + j) * lda + c0 + sr] : make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int k = 0; k < NBP; k++) {
+            const float2 lk = L[lane][k];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float2 xk;
+                xk.x = __shfl_sync(0xffffffffu, v[j].x, k);
+                xk.y = __shfl_sync(0xffffffffu, v[j].y, k);
+                if (lane > k) cfms(v[j], lk, xk);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (col0 + j < n) A[(col0 + j) * lda + c0 + lane] = make_float2(tf32_rna(v[j].x), tf32_rna(v[j].y));
+    }
+}
+
+// raises the grouped panel's dynamic shared-memory limit (once, before any launch is captured into a graph)
+gdm_status gdm_glu_panel_init(gdm_ctx *ctx) {
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_glu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               GLU_PANEL_SMEM));
+        attr = true;
+    }
+    return GDM_OK;
+}
+
+gdm_status gdm_glu_panel(gdm_ctx *ctx, const GluItem *items, const int *prefix, int na, int nblocks, int64_t b0,
+                         int64_t c0, int nbo) {
+    if (nblocks <= 0) return GDM_OK;
+    GDM_TRY(gdm_glu_panel_init(ctx));
+    k_glu_panel<<<(unsigned)nblocks, 128, GLU_PANEL_SMEM, ctx->stream>>>(items, prefix, na, b0, c0, nbo);
+    GDM_LAUNCHED(ctx, "glu_panel");
+    return GDM_OK;
+}
+
+gdm_status gdm_glu_swap_trsm(gdm_ctx *ctx, const GluItem *items, const int *prefix, int na, int nblocks,
+                             int64_t c0) {
+    if (nblocks <= 0) return GDM_OK;
+    k_glu_swap_trsm<<<(unsigned)nblocks, 256, 0, ctx->stream>>>(items, prefix, na, c0);
+    GDM_LAUNCHED(ctx, "glu_swap_trsm");
+    return GDM_OK;
 }
 
 // ------------------------------------------------------------------ SIMT complex GEMM  C -= A * B

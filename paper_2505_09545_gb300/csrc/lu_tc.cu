@@ -438,6 +438,289 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------- grouped update of a batch
+// k_tc_update (TF32, one product, 128 x 256 tiles) over the tiles of every problem of one lock-step launch
+// of the grouped LU: tile t belongs to the problem whose range of the prefix sum holds it, and its operands
+// come through that problem's tensor maps: A = the TF32 embedding of L that the panel kernel wrote (GluItem
+// lxp / lxt), B = U read straight from the matrix (rounded to TF32 by the interchange and solve kernel),
+// C = the matrix. The maps clip only at the matrix edge, so real rows of a tile at or beyond its region's
+// mlim are loaded and stored back unchanged (no other tile of the launch touches them).
+struct GDec {
+    const GluMaps *m;
+    GluTile t;
+};
+__device__ __forceinline__ GDec glu_decode(const GluItem *__restrict__ items, const GluMaps *__restrict__ maps,
+                                           const int *__restrict__ prefix, int na, int kind, int64_t b0, int64_t c0,
+                                           int nbo, int t) {
+    int lo = 0, hi = na;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&prefix[mid]) <= t) lo = mid;
+        else hi = mid;
+    }
+    GDec d;
+    d.m = &maps[lo];
+    d.t = glu_tile(kind, items[lo].n, b0, c0, nbo, t - __ldg(&prefix[lo]));
+    return d;
+}
+// the tensor maps were written by the host before the launch; order those writes before the copies that
+// read the descriptor
+__device__ __forceinline__ void tmap_acquire(const void *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)map) : "memory");
+}
+
+// stages of operands and C chunk buffers: the K = 32 updates (two K chunks per tile) stream C, and keep
+// more C chunks in flight; the K = nbo updates keep more operand stages
+template <int ST, int NC> struct GCfg {
+    static constexpr int STAGES = ST, NCB = NC, LOOK = NC / 2;
+    static constexpr int A_BYTES = BM * BK * 4, B_BYTES = 256 * BK * 4, STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int CB_BYTES = BM * 32 * 4, TMEM_COLS = 512;
+    static constexpr int SMEM = ST * STAGE_BYTES + NC * CB_BYTES + 1024 + 512;
+    static __device__ __forceinline__ uint32_t idesc_n(int n_cols) { return Cfg<256, 1>::idesc_n(n_cols); }
+};
+using GCfgPanel = GCfg<2, 8>;
+using GCfgTrail = GCfg<4, 2>;
+
+template <class CF>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_glu_gemm(const GluItem *__restrict__ items, const GluMaps *__restrict__ maps, const int *__restrict__ prefix,
+               int na, int ntiles, int kind, int64_t b0, int64_t c0, int nbo, int *gflags) {
+    constexpr int BN = 256;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(base + CF::STAGES * CF::STAGE_BYTES);
+    uint64_t *full = bars;                       // [STAGES]
+    uint64_t *empty = bars + CF::STAGES;         // [STAGES]
+    uint64_t *tfull = bars + 2 * CF::STAGES;     // [2]
+    uint64_t *tempty = tfull + 2;                // [2]
+    uint64_t *drain = tempty + 2;                // [1]
+    uint64_t *cbar = drain + 1;                  // [NCB] C chunk loads
+    float *cbuf = (float *)(base + CF::STAGES * CF::STAGE_BYTES + 512);  // NCB x (32 cols x 128 rows)
+    uint32_t *tmem_slot = (uint32_t *)(cbar + CF::NCB);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = kind == GLU_PANEL ? 64 : 2 * nbo;
+    const int nk = K / BK;
+    const int64_t org = kind == GLU_PANEL ? c0 + 32 : b0 + nbo;  // origin (row and column) of the regions
+    const int kx0 = (int)(2 * (kind == GLU_PANEL ? c0 : b0));     // B: real rows of U
+    const int cx0 = (int)(2 * org), cy0 = (int)org;
+    // A: the panel's column pair range and the first row below it, in the embedding of the block's L
+    const int ax0 = kind == GLU_PANEL ? (int)(2 * (c0 - b0)) : 0, ay0 = (int)(2 * (org - b0));
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CF::STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(drain, 1);
+        for (int b = 0; b < CF::NCB; b++) mbar_init(&cbar[b], 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)CF::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int issued = 0;
+            const GluMaps *last = nullptr;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                const GDec d = glu_decode(items, maps, prefix, na, kind, b0, c0, nbo, t);
+                const CUtensorMap *am = (const CUtensorMap *)&d.m->lx;
+                const CUtensorMap *bm = (const CUtensorMap *)&d.m->b;
+                if (d.m != last) {
+                    tmap_acquire(am);
+                    tmap_acquire(bm);
+                    last = d.m;
+                }
+                for (int kc = 0; kc < nk; kc++) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, gflags)) break;
+                    unsigned char *st = base + s * CF::STAGE_BYTES;
+                    mbar_expect_tx(&full[s], CF::STAGE_BYTES);
+                    tma_load_2d(st, am, ax0 + kc * BK, ay0 + d.t.mt * BM, &full[s]);
+                    tma_load_2d(st + CF::A_BYTES, bm, kx0 + kc * BK, cy0 + d.t.col0, &full[s]);
+                    issued++;
+                    if (++s == CF::STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            if (*abort_flag) {
+                // let the copies already issued land before the CTA's shared memory goes away
+                int s2 = s, ph2 = ph;
+                for (int i = 0; i < CF::STAGES && i < issued; i++) {
+                    if (--s2 < 0) {
+                        s2 = CF::STAGES - 1;
+                        ph2 ^= 1;
+                    }
+                    uint64_t t0 = gtimer();
+                    while (!mbar_try_wait(&full[s2], ph2) && gtimer() - t0 < 2000000000ull) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int lt = 0;
+            bool issued_any = false;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, lt++) {
+                const int b = lt & 1;
+                const uint32_t tph = (lt >> 1) & 1;
+                if (!mbar_wait(&tempty[b], tph ^ 1, abort_flag, gflags)) break;
+                tc_fence_after();
+                const uint32_t dt = tmem_base + (uint32_t)(b * BN);
+                const GDec d = glu_decode(items, maps, prefix, na, kind, b0, c0, nbo, t);
+                const uint32_t idesc = CF::idesc_n(32 * ((d.t.ncols + 31) / 32));
+                bool ok = true;
+                for (int kc = 0; kc < nk; kc++) {
+                    if (!mbar_wait(&full[s], ph, abort_flag, gflags)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(base + s * CF::STAGE_BYTES);
+                    const uint64_t a0 = desc_sw128(sa);
+                    const uint64_t bd = desc_sw128(sa + CF::A_BYTES);
+#pragma unroll
+                    for (int k = 0; k < BK / 8; k++) {
+                        const uint64_t ko = (uint64_t)(2 * k);
+                        umma_tf32(dt, a0 + ko, bd + ko, idesc, (kc | k) ? 1u : 0u);
+                    }
+                    issued_any = true;
+                    umma_commit(&empty[s]);
+                    if (++s == CF::STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(&tfull[b]);
+            }
+            if (issued_any) {
+                umma_commit(drain);
+                uint64_t t0 = gtimer();
+                while (!mbar_try_wait(drain, 0) && gtimer() - t0 < 2000000000ull) {
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, as in k_tc_update; the C loads run LOOK chunks ahead on a
+        // cursor that walks this CTA's tiles and their valid 32-column chunks
+        const int q = warp & 3;
+        const int et = threadIdx.x - 64;  // 0..127
+        const bool leader = (et == 0);
+        int ld_t = blockIdx.x, ld_ch = 0;
+        GDec ld_d;
+        const GluMaps *last = nullptr;
+        if (leader && ld_t < ntiles) ld_d = glu_decode(items, maps, prefix, na, kind, b0, c0, nbo, ld_t);
+        auto issue_load = [&](int g) {
+            const int b = g % CF::NCB;
+            const CUtensorMap *cm = (const CUtensorMap *)&ld_d.m->c;
+            if (ld_d.m != last) {
+                tmap_acquire(cm);
+                last = ld_d.m;
+            }
+            mbar_expect_tx(&cbar[b], CF::CB_BYTES);
+            tma_load_2d(cbuf + (size_t)b * (CF::CB_BYTES / 4), cm, cx0 + ld_d.t.mt * BM, cy0 + ld_d.t.col0 + ld_ch * 32,
+                        &cbar[b]);
+            if (++ld_ch == (ld_d.t.ncols + 31) / 32) {
+                ld_ch = 0;
+                ld_t += gridDim.x;
+                if (ld_t < ntiles) ld_d = glu_decode(items, maps, prefix, na, kind, b0, c0, nbo, ld_t);
+            }
+        };
+        if (leader)
+            for (int g = 0; g < CF::LOOK && ld_t < ntiles; g++) issue_load(g);
+        int g = 0;
+        const int row = q * 32 + lane;
+        volatile int *dec = (volatile int *)(abort_flag + 1);
+        int dc = 0;
+        auto agree = [&](bool leader_ok) -> bool {
+            if (leader) dec[dc & 1] = leader_ok ? 1 : 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            bool r = dec[dc & 1] != 0;
+            dc++;
+            return r;
+        };
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, lt++) {
+            const int b = lt & 1;
+            const uint32_t tph = (lt >> 1) & 1;
+            bool ok = true;
+            if (leader) ok = mbar_wait(&tfull[b], tph, abort_flag, gflags);
+            if (!agree(ok)) break;
+            tc_fence_after();
+            bool alive = true;
+            const GDec d = glu_decode(items, maps, prefix, na, kind, b0, c0, nbo, t);
+            const int nch = (d.t.ncols + 31) / 32;
+            const bool live_row = d.t.mt * BM + row < d.t.mlim;
+#pragma unroll 1
+            for (int ch = 0; ch < nch; ch++, g++) {
+                const int cb = g % CF::NCB;
+                ok = true;
+                if (leader) {
+                    if (ld_t < ntiles) {
+                        // the buffer's previous chunk must have been read out by its store
+                        bulk_wait_read<CF::NCB - CF::LOOK - 1>();
+                        issue_load(g + CF::LOOK);
+                    }
+                    ok = mbar_wait(&cbar[cb], (uint32_t)((g / CF::NCB) & 1), abort_flag, gflags);
+                }
+                float v[32];
+                tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + ch * 32), v);
+                if (!agree(ok)) {
+                    alive = false;
+                    break;
+                }
+                float *buf = cbuf + (size_t)cb * (CF::CB_BYTES / 4);
+                if (live_row) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) buf[j * BM + row] -= v[j];
+                }
+                fence_proxy_async_smem();
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (leader) {
+                    tma_store_2d((const CUtensorMap *)&d.m->c, buf, cx0 + d.t.mt * BM, cy0 + d.t.col0 + ch * 32);
+                    bulk_commit();
+                }
+            }
+            if (!alive) break;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+        if (leader) bulk_wait_all();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"((uint32_t)CF::TMEM_COLS)
+                     : "memory");
+    }
+}
+
 // ---------------------------------------------------------------- CTA-pair variant (TF32, one product)
 // The same update with 256-row tiles on a CTA pair (a cluster of two CTAs on two SMs): tcgen05.mma with
 // cta_group::2 multiplies a 256 x 32 A slab (128 rows in each CTA's shared memory) by a 32 x N B slab whose
@@ -1148,4 +1431,50 @@ gdm_status gdm_tc_trailing_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, i
     gdm_status s = gdm_tc_update(ctx, prec, A, lda, n, be, be, b0, m, m, nb, ws, ws_bytes, 1);
     nvtxRangePop();
     return s;
+}
+
+// ---------------------------------------------------------------- grouped LU of a batch: maps and launches
+bool gdm_glu_encode(const GluItem *items, int n_items, int nbo, GluMaps *maps) {
+    for (int i = 0; i < n_items; i++) {
+        const GluItem &g = items[i];
+        GluMaps &m = maps[i];
+        memset(&m, 0, sizeof(m));
+        if (g.n <= 32) continue;  // no update reaches a problem of one panel
+        if (!(make_map((CUtensorMap *)&m.lx, g.lx, (uint64_t)(2 * nbo), (uint64_t)(2 * g.n), (uint64_t)(2 * nbo),
+                       BM) &&
+              make_map((CUtensorMap *)&m.b, (const float *)g.A, (uint64_t)(2 * g.n), (uint64_t)g.n,
+                       (uint64_t)(2 * g.lda), 256) &&
+              make_map_c((CUtensorMap *)&m.c, (const float *)g.A, (uint64_t)(2 * g.n), (uint64_t)g.n,
+                         (uint64_t)(2 * g.lda))))
+            return false;
+    }
+    return true;
+}
+
+// raises the update kernel's shared-memory limit (once, before any launch is captured into a graph)
+gdm_status gdm_glu_gemm_init(gdm_ctx *ctx) {
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_glu_gemm<GCfgPanel>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               GCfgPanel::SMEM));
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_glu_gemm<GCfgTrail>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               GCfgTrail::SMEM));
+        attr = true;
+    }
+    return GDM_OK;
+}
+
+gdm_status gdm_glu_gemm(gdm_ctx *ctx, const GluItem *items, const GluMaps *maps, const int *prefix, int na,
+                        int ntiles, int kind, int64_t b0, int64_t c0, int nbo) {
+    if (ntiles <= 0) return GDM_OK;
+    GDM_TRY(gdm_glu_gemm_init(ctx));
+    const int grid = ntiles < ctx->sm_count ? ntiles : ctx->sm_count;
+    if (kind == GLU_PANEL)
+        k_glu_gemm<GCfgPanel><<<grid, NTHREADS, GCfgPanel::SMEM, ctx->stream>>>(items, maps, prefix, na, ntiles, kind,
+                                                                                b0, c0, nbo, ctx->dflags);
+    else
+        k_glu_gemm<GCfgTrail><<<grid, NTHREADS, GCfgTrail::SMEM, ctx->stream>>>(items, maps, prefix, na, ntiles, kind,
+                                                                                b0, c0, nbo, ctx->dflags);
+    GDM_LAUNCHED(ctx, kind == GLU_PANEL ? "glu_gemm_panel" : "glu_gemm_trailing");
+    return GDM_OK;
 }

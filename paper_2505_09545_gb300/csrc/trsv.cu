@@ -41,60 +41,119 @@ template <class C> __device__ __forceinline__ C cz() {
 }
 
 // ------------------------------------------------------------------ block operators
-// One CTA per (row block j, triangle): X = I, then the block's panel sequence (L) or back substitution (U)
-// applied to the columns of X (one thread per column), stored column-major and row-major.
-template <class C, int NBS>
-__global__ void __launch_bounds__(NBS) k_block_ops(const C *__restrict__ A, int64_t lda, int64_t n,
-                                                   const int32_t *__restrict__ ipiv, C *__restrict__ ops) {
-    extern __shared__ __align__(16) unsigned char xsm[];
-    C(*X)[NBS + 1] = (C(*)[NBS + 1])xsm;  // X[r][c]
-    const int j = blockIdx.x >> 1, tri = blockIdx.x & 1;
+// Per (row block j, triangle) the explicit operator of the block's diagonal part: M_j = L_S^{-1} P_S ...
+// L_1^{-1} P_1 (the block's 32-row panels, pivots inside each panel) or Ui_j = U_jj^{-1}, applied to the
+// columns of I and stored column-major (coalesced for y = X acc) and row-major (for y = X^H acc).
+// A warp solves two columns of X (lane = row within each 32-row group, 4 groups in registers); a CTA of 8
+// warps covers 16 columns, so that a triangle takes 8 CTAs. The block's factor columns are staged in shared
+// memory one 32-column panel at a time: L forward (interchanges of the panel across lanes, then unit lower
+// substitution into its own and the later row groups), U backward (division by the diagonal, then the
+// column's multiple subtracted from the rows above).
+constexpr int OPS_CPW = 2;  // columns per warp
+__global__ void __launch_bounds__(256, 2) k_block_ops(const float2 *__restrict__ A, int64_t lda, int64_t n,
+                                                   const int32_t *__restrict__ ipiv, float2 *__restrict__ ops) {
+    constexpr int NBS = TRSV_NBS_F32, R = NBS / 32, CGS = NBS / (8 * OPS_CPW);
+    __shared__ float2 Ds[32][NBS + 1];
+    __shared__ int piv[NBS];
+    const int cg = blockIdx.x % CGS, tri = (blockIdx.x / CGS) & 1, j = blockIdx.x / (2 * CGS);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t r0 = (int64_t)j * NBS;
     if (r0 >= n) return;
     const int nr = (int)min((int64_t)NBS, n - r0);
-    const int c = threadIdx.x;
-    for (int r = 0; r < NBS; r++) {
-        C v = cz<C>();
-        if (r == c && c < nr) v.x = 1;
-        X[r][c] = v;
-    }
-    __syncthreads();
-    const C *D = A + r0 * lda + r0;  // D[r + k*lda]
-    if (c < nr) {
-        if (tri == 0) {
-            for (int p0 = 0; p0 < nr; p0 += 32) {
-                const int w = min(32, nr - p0);
-                for (int t = 0; t < w; t++) {
-                    int q = (int)(ipiv[r0 + p0 + t] - r0);
-                    if (q != p0 + t && q >= p0 && q < p0 + w) {
-                        C a = X[p0 + t][c];
-                        X[p0 + t][c] = X[q][c];
-                        X[q][c] = a;
+    const float2 *D = A + r0 * lda + r0;  // D[r + k*lda]
+    const int cb = cg * 8 * OPS_CPW + warp * OPS_CPW;
+    float2 x[OPS_CPW][R];
+#pragma unroll
+    for (int u = 0; u < OPS_CPW; u++)
+#pragma unroll
+        for (int q = 0; q < R; q++)
+            x[u][q] = make_float2((q * 32 + lane == cb + u && cb + u < nr) ? 1.f : 0.f, 0.f);
+    if (tri == 0) {
+        for (int t = tid; t < nr; t += blockDim.x) piv[t] = (int)(ipiv[r0 + t] - r0);
+#pragma unroll
+        for (int p = 0; p < R; p++) {
+            const int p0 = 32 * p;
+            if (p0 >= nr) break;
+            const int w = min(32, nr - p0);
+            __syncthreads();
+            for (int e = tid; e < 32 * NBS; e += blockDim.x) {
+                const int t = e / NBS, row = e % NBS;
+                Ds[t][row] = (t < w && row < nr) ? D[(int64_t)(p0 + t) * lda + row] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            // the panel's interchanges, in order: rows p0 + t and p0 + q exchange (lanes t and q)
+            for (int t = 0; t < w; t++) {
+                const int q = piv[p0 + t] - p0;
+                if (q > t && q < w) {
+#pragma unroll
+                    for (int u = 0; u < OPS_CPW; u++) {
+                        const float2 vt = make_float2(__shfl_sync(0xffffffffu, x[u][p].x, t),
+                                                      __shfl_sync(0xffffffffu, x[u][p].y, t));
+                        const float2 vq = make_float2(__shfl_sync(0xffffffffu, x[u][p].x, q),
+                                                      __shfl_sync(0xffffffffu, x[u][p].y, q));
+                        if (lane == t) x[u][p] = vq;
+                        else if (lane == q) x[u][p] = vt;
                     }
                 }
-                // rows of the panel: unit lower substitution; rows below: subtract L[r][panel] x_panel
-                for (int t = 0; t < w; t++) {
-                    C xt = X[p0 + t][c];
-                    for (int r = p0 + t + 1; r < nr; r++) cfms(X[r][c], D[(int64_t)(p0 + t) * lda + r], xt);
+            }
+            for (int t = 0; t < w; t++) {
+                float2 xt[OPS_CPW];
+#pragma unroll
+                for (int u = 0; u < OPS_CPW; u++)
+                    xt[u] = make_float2(__shfl_sync(0xffffffffu, x[u][p].x, t), __shfl_sync(0xffffffffu, x[u][p].y, t));
+#pragma unroll
+                for (int q2 = p; q2 < R; q2++) {
+                    if (q2 > p || lane > t) {
+                        const float2 l = Ds[t][q2 * 32 + lane];
+#pragma unroll
+                        for (int u = 0; u < OPS_CPW; u++) cfms(x[u][q2], l, xt[u]);
+                    }
                 }
             }
-        } else {
-            for (int r = nr - 1; r >= 0; r--) {
-                C s = X[r][c];
-                for (int k = r + 1; k < nr; k++) cfms(s, D[(int64_t)k * lda + r], X[k][c]);
-                C d = D[(int64_t)r * lda + r];
-                X[r][c] = cabs1(d) > 0 ? cmul(s, crecip(d)) : s;
+        }
+    } else {
+#pragma unroll
+        for (int p = R - 1; p >= 0; p--) {
+            const int p0 = 32 * p;
+            if (p0 >= nr) continue;
+            const int w = min(32, nr - p0);
+            __syncthreads();
+            for (int e = tid; e < 32 * NBS; e += blockDim.x) {
+                const int t = e / NBS, row = e % NBS;
+                Ds[t][row] = (t < w && row < p0 + w) ? D[(int64_t)(p0 + t) * lda + row] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            for (int t = w - 1; t >= 0; t--) {
+                const float2 d = Ds[t][p0 + t];
+                float2 xr[OPS_CPW];
+#pragma unroll
+                for (int u = 0; u < OPS_CPW; u++) {
+                    float2 v = make_float2(__shfl_sync(0xffffffffu, x[u][p].x, t), __shfl_sync(0xffffffffu, x[u][p].y, t));
+                    v = cabs1(d) > 0 ? cmul(v, crecip(d)) : v;
+                    if (lane == t) x[u][p] = v;
+                    xr[u] = v;
+                }
+#pragma unroll
+                for (int q2 = 0; q2 <= p; q2++) {
+                    if (q2 < p || lane < t) {
+                        const float2 uk = Ds[t][q2 * 32 + lane];
+#pragma unroll
+                        for (int u = 0; u < OPS_CPW; u++) cfms(x[u][q2], uk, xr[u]);
+                    }
+                }
             }
         }
     }
-    __syncthreads();
-    // two layouts of the operator: column-major (coalesced for y = X acc) and row-major (for y = X^H acc)
-    C *ocm = ops + (int64_t)(4 * j + 2 * tri) * NBS * NBS;
-    C *orm = ocm + (int64_t)NBS * NBS;
-    for (int r = 0; r < NBS; r++) {
-        orm[r * NBS + c] = X[r][c];
-        ocm[c * NBS + r] = X[r][c];
-    }
+    float2 *ocm = ops + (int64_t)(4 * j + 2 * tri) * NBS * NBS;
+    float2 *orm = ocm + (int64_t)NBS * NBS;
+#pragma unroll
+    for (int u = 0; u < OPS_CPW; u++)
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            const int row = q * 32 + lane, col = cb + u;
+            ocm[col * NBS + row] = x[u][q];
+            orm[row * NBS + col] = x[u][q];
+        }
 }
 
 // ------------------------------------------------------------------ last-dependency operators
@@ -514,15 +573,10 @@ gdm_status launch_modes_f32(gdm_ctx *ctx, const float2 *A, int64_t lda, int64_t 
 
 template <class C, int NBS> gdm_status launch_ops(gdm_ctx *ctx, const C *A, int64_t lda, int64_t n, const int32_t *ipiv,
                                                   C *ops, int conj_trans) {
-    const size_t smem = sizeof(C) * NBS * (NBS + 1);
-    static bool attr = false;
-    if (!attr) {
-        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_block_ops<C, NBS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem));
-        attr = true;
-    }
+    static_assert(NBS == TRSV_NBS_F32, "block operators of 128-row blocks");
     const int nblk = (int)((n + NBS - 1) / NBS);
-    k_block_ops<C, NBS><<<2 * nblk, NBS, smem, ctx->stream>>>(A, lda, n, ipiv, ops);
+    k_block_ops<<<(unsigned)(2 * nblk * (NBS / (8 * OPS_CPW))), 256, 0, ctx->stream>>>(
+        (const float2 *)A, lda, n, ipiv, (float2 *)ops);
     GDM_LAUNCHED(ctx, "block_ops");
     // the last-dependency operators W of the two modes of this solve direction (after all operator planes), for
     // systems long enough that the shorter dependency chain repays forming them
