@@ -33,6 +33,9 @@ FP32_OPERATOR_INST_PER_PAIR = 204.0
 # FP32 thread instructions per ordered pair of the adjoint's double-float gradient pair sum k_dgreen_sum_ff (G s,
 # dG/dr s, dG/dk s; one right-hand side; ncu count: profiles/dgreen_sum_ff_cylinder_ncu.md)
 DGREEN_FF_INST_PER_PAIR = 3627.0
+# FP32 thread instructions per ordered pair, 2 right-hand sides, of the double-float residual sum
+# k_green_sum_ff<3, 3, 2> (ncu count)
+RESIDUAL_FF_INST_PER_PAIR = 1406.0
 
 
 def load_peaks():
@@ -567,12 +570,85 @@ def run_metasurface(args):
         torch.distributed.destroy_process_group()
 
 
+def batch_roofline_sum(ss, infos, ms, precision):
+    """The batch's time against the sum of its kernels' rooflines: every structure's assembly (HBM store of
+    (3N)^2 complex64), LU ((8/3)(3N)^3 flops at the TF32 tensor rate), triangular solves (one pass over the
+    factors per solve, initial plus one per refinement iteration, at HBM rate) and refinement residuals (one
+    FP32 Green sum, then double-float ones, at the FP32 issue rate with the ncu instruction counts per pair),
+    with each structure's own iteration count. frac = summed roofline time / measured time."""
+    peaks, src = load_peaks()
+    hbm = peaks["hbm_gbs"] * 1e9
+    tc = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 1e12
+    if precision == "tf32":
+        tc *= NOMINAL_TF32_OVER_BF16
+    issue = 152 * 128 * 2.07e9
+    asm = lu = sol = res = 0.0
+    for s, info in zip(ss, infos):
+        n3 = 3.0 * s.n
+        it = max(1, int(info["iterations"]))
+        asm += n3 * n3 * 8.0 / hbm
+        lu += 8.0 / 3.0 * n3 ** 3 / tc
+        sol += n3 * n3 * 8.0 * (it + 1) / hbm
+        res += float(s.n) ** 2 * (FP32_OPERATOR_INST_PER_PAIR + (it - 1) * RESIDUAL_FF_INST_PER_PAIR) / issue
+    ideal = asm + lu + sol + res
+    return {"assembly_ms": asm * 1e3, "lu_ms": lu * 1e3, "solves_ms": sol * 1e3, "residuals_ms": res * 1e3,
+            "ideal_ms": ideal * 1e3, "measured_ms": ms, "frac": ideal * 1e3 / ms,
+            "peaks": f"{src}: HBM {peaks['hbm_gbs']:.0f} GB/s, tensor {tc / 1e12:.0f} TFLOP/s, "
+                     f"FP32 issue {issue / 1e12:.1f} T inst/s"}
+
+
+def batch_leg(G, ctx, dev, ss, precision, tol, streams, autotune, warmup, steps, ws=1):
+    """The batch of structures ss through gdm_solve_batched: tuned widths (the grouped factorisation's for
+    TF32, the per-problem table otherwise), warm-up, then steps timed with CUDA events. Returns the timing,
+    the results' accuracy record and the batch against its summed per-kernel rooflines."""
+    import torch
+    probs = [G.GDMProblem(torch.tensor(s.pos, device=dev), float(s.wavelengths[0]), 3,
+                          eps=torch.tensor(s.eps, device=dev), step=s.step) for s in ss]
+    sizes = [p.size for p in probs]
+    table, glu_nb = None, None
+    if autotune and precision != "fp64":
+        table = G.autotune(ctx, sizes, precision=precision)
+        if precision == "tf32" and len(sizes) > 1:
+            glu_nb = G.autotune_batched(ctx, sizes)
+    e0s = [s.e0 for s in ss]
+
+    def step():
+        return G.solve_batched(ctx, probs, e0s, precision=precision, n_streams=streams, tol=tol)
+
+    for _ in range(max(1, warmup)):
+        out = step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev.index or 0)
+    clk.start()
+    l0 = ctx.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        out = step()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, ws, dev)
+    infos = out[2]
+    return {"ms": ms, "launches": ctx.launches - l0, "clocks": clocks, "lu_block_table": table,
+            "grouped_lu_block": glu_nb, "factor_ms": infos[0]["factor_ms"] if glu_nb or precision == "tf32" else None,
+            "roofline_sum": batch_roofline_sum(ss, infos, ms, precision),
+            "accuracy": {"tol": tol, "max_refine_iters": max(i["iterations"] for i in infos),
+                         "max_rel_residual_fp64": max(i["rel_residual"] for i in infos),
+                         "refactored": int(sum(i["refactored"] for i in infos))},
+            "sizes_gb": sum(n * n for n in sizes) * 8 / 1e9}
+
+
+BATCH_WORKLOAD = ("{n} Eden blobs, N~U{{50..1500}} cells (sum N={sum_n}), d=15 nm, eps~U[2,16], own "
+                  "lambda~U[400,1000] nm each, x/y-pol; plane wave + assemble + LU + FP64-refined solve + cross "
+                  "sections, one gdm_solve_batched call")
+
+
 def run_batch(args):
     """Batching workload: 256 independent Eden blobs of N ~ U{50..1500} cells on a 15 nm mesh
     (3N = 150 ... 4500), eps ~ U[2,16], each at its own wavelength ~ U[400,1000] nm with x- and
     y-polarised plane waves; one step = plane wave + assemble + LU + FP64-refined solve + cross sections
     of all 256 through one gdm_solve_batched call. The value is seconds per (lambda, N) solve."""
-    import numpy as np
     import torch
     import gdm_workloads as W
     import paper_2505_09545_gb300 as G
@@ -587,52 +663,24 @@ def run_batch(args):
     lo, hi = shard.weighted_unit_range([(3.0 * s.n) ** 3 for s in ss_all], ws, rank)
     ss = ss_all[lo:hi]
     ctx = G.Context(local)
-    probs = [G.GDMProblem(torch.tensor(s.pos, device=dev), float(s.wavelengths[0]), 3,
-                          eps=torch.tensor(s.eps, device=dev), step=s.step) for s in ss]
-    sizes = [p.size for p in probs]
-    table = None
-    if not args.no_autotune and args.precision != "fp64":
-        table = G.autotune(ctx, sizes, precision=args.precision)
-    e0s = [s.e0 for s in ss]
-
-    def step():
-        return G.solve_batched(ctx, probs, e0s, precision=args.precision, n_streams=args.streams)
-
-    for _ in range(max(1, args.warmup)):
-        out = step()
-    torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    clk.start()
-    l0 = ctx.launches
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        out = step()
-    e1.record()
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    launches = ctx.launches - l0
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws, dev)
-    infos = out[2]
+    leg = batch_leg(G, ctx, dev, ss, args.precision, args.tol, args.streams, not args.no_autotune, args.warmup,
+                    args.steps, ws)
+    ms = leg["ms"]
     flops = sum(8.0 / 3.0 * (3.0 * s.n) ** 3 for s in ss_all)
     line = {"metric": METRIC, "value": ms / 1e3 / len(ss_all), "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": False,
             "scaling": "strong" if ws > 1 else "weak",
             "vs_baseline": None, "dtype": "c64-tf32+f64" if args.precision == "tf32" else args.precision,
             "data": "synthetic",
-            "config": {"workload": f"{len(ss_all)} Eden blobs, N~U{{50..1500}} cells (sum N={sum(s.n for s in ss_all)}), "
-                                   "d=15 nm, eps~U[2,16], own lambda~U[400,1000] nm each, x/y-pol; plane wave + "
-                                   "assemble + LU + FP64-refined solve + cross sections, one gdm_solve_batched call",
+            "config": {"workload": BATCH_WORKLOAD.format(n=len(ss_all), sum_n=sum(s.n for s in ss_all)),
                        "precision": args.precision, "streams": args.streams or 8,
-                       "lu_block_table": table,
+                       "lu_block_table": leg["lu_block_table"], "grouped_lu_block": leg["grouped_lu_block"],
                        "parallelism": f"structures split contiguously over {ws} rank(s) by LU work",
-                       "l2": f"inputs larger than L2 ({sum(n * n for n in sizes) * 8 / 1e9:.1f} GB of complex64 "
+                       "l2": f"inputs larger than L2 ({leg['sizes_gb']:.1f} GB of complex64 "
                              "matrices rewritten every step)"},
             "batch_s": ms / 1e3, "lu_tflops_effective": flops / (ms / 1e3) / 1e12,
-            "accuracy": {"max_refine_iters": max(i["iterations"] for i in infos),
-                         "max_rel_residual_fp64": max(i["rel_residual"] for i in infos),
-                         "refactored": int(sum(i["refactored"] for i in infos))},
-            "gpu_launches": launches, "clocks": clocks}
+            "grouped_factor_ms": leg["factor_ms"], "roofline_sum": leg["roofline_sum"],
+            "accuracy": leg["accuracy"], "gpu_launches": leg["launches"], "clocks": leg["clocks"]}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -826,7 +874,7 @@ def run_gmres(args):
                 "inst_per_pair": inst_fast, "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock)",
                 "share_of_iterations": fast_ms / max(it_ms, 1e-9),
                 "double_float_operator": {"passes": ff_passes, "ms": ff_ms,
-                                          "fp32_inst_per_s": ff_passes * float(s.n) ** 2 * 1406.0 / (ff_ms / 1e3)
+                                          "fp32_inst_per_s": ff_passes * float(s.n) ** 2 * RESIDUAL_FF_INST_PER_PAIR / (ff_ms / 1e3)
                                           if ff_ms > 0 else 0.0},
                 "phases_ms": {"fp32_operator": fast_ms, "double_float_operator": ff_ms,
                               "preconditioner": ph["correction_solves"], "orthogonalisation": ph["other"]},
@@ -1083,6 +1131,17 @@ def main():
         extras["metasurface"] = metasurface_leg(G, ctx, dev, args.precision, args.tol, 1.0, 1, 1, load_peaks()[0])
         extras["metasurface"].pop("sigma")
         extras["fp64_gpu_path"] = fp64_compare(G, ctx, dev, args.precision, args.fp64_cuboid, args.tol, golden)
+        if ws == 1:
+            import gdm_workloads as W
+            ss_b = W.blob_batch()
+            bl = batch_leg(G, ctx, dev, ss_b, args.precision, args.tol, 0, True, 2, 3)
+            extras["batch"] = {"workload": BATCH_WORKLOAD.format(n=len(ss_b), sum_n=sum(s.n for s in ss_b)),
+                               "batch_s": bl["ms"] / 1e3, "s_per_solve": bl["ms"] / 1e3 / len(ss_b),
+                               "lu_tflops_effective": sum(8.0 / 3.0 * (3.0 * s.n) ** 3 for s in ss_b) /
+                               (bl["ms"] / 1e3) / 1e12,
+                               "grouped_factor_ms": bl["factor_ms"], "grouped_lu_block": bl["grouped_lu_block"],
+                               "roofline_sum": bl["roofline_sum"], "accuracy": bl["accuracy"],
+                               "gpu_launches_per_step": bl["launches"] / 3}
 
     peaks, peak_src = load_peaks()
     per_launch_ms = prof["ms"] / max(1, prof["launches"])

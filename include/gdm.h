@@ -365,6 +365,15 @@ gdm_status gdm_gpm_extract(gdm_ctx *ctx, gdm_precision prec, const gdm_problem *
  * fixes the width. */
 gdm_status gdm_autotune(gdm_ctx *ctx, gdm_precision prec, const int64_t *sizes, int n_sizes, int *nb_out);
 
+/* Outer block width of the grouped factorisation that gdm_solve_batched uses for a whole TF32
+ * batch (no paper counterpart): times that factorisation (all problems in lock step, one
+ * CUDA graph) on synthetic well-conditioned complex64 matrices of exactly the given system
+ * dimensions sizes[0..n_sizes) (kind*n each, n_sizes >= 2) with widths 128, 256 and 512, and
+ * keeps the fastest in the context. Allocates the matrices (sum of sizes^2 complex64) for the
+ * duration of the call; synchronous. nb_out: host int, the chosen width, may be NULL.
+ * GDM_ERR_UNSUPPORTED when the GDM_BATCH_NB environment variable fixes the width. */
+gdm_status gdm_autotune_batched(gdm_ctx *ctx, const int64_t *sizes, int n_sizes, int *nb_out);
+
 /* Residual r = F0 - A F of problem p for given fields F (FP64 result), computed matrix-free: the
  * Green dyads are regenerated for every pair (double-float arithmetic for cells, FP64 for ED/MD dipoles),
  * no stored matrix. This is the residual that drives gdm_solve's refinement (Eq. GDM_system_of_equations).

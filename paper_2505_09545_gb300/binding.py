@@ -102,6 +102,7 @@ _SIGS = {
     "gdm_alpha6_lorentz": ([P, I64, P, P, C.c_double, C.c_double, C.c_double, C.c_double, P], C.c_int),
     "gdm_solve_batched": ([P, C.c_int, P, C.c_int, P, C.c_int, P], C.c_int),
     "gdm_autotune": ([P, C.c_int, P, C.c_int, P], C.c_int),
+    "gdm_autotune_batched": ([P, P, C.c_int, P], C.c_int),
     "gdm_diag_wait_timeout": ([P, C.c_double], C.c_int),
     "gdm_incident_gaussian": ([P, P, I64, C.c_double, C.c_double, PD, C.c_double, PD, C.c_double, C.c_int, C.c_int,
                                P], C.c_int),
@@ -595,6 +596,17 @@ def autotune(ctx: Context, sizes, precision="tf32"):
     ctx._check(lib().gdm_autotune(ctx.h, PRECISION[precision], sz.ctypes.data_as(C.c_void_p), len(sz), out),
                "gdm_autotune")
     return list(out)
+
+
+def autotune_batched(ctx: Context, sizes):
+    """gdm_autotune_batched: outer block width of the grouped (lock-step) factorisation of a TF32 batch with
+    these system sizes, kept in the context; returns it."""
+    sz = np.ascontiguousarray(np.asarray(sizes, np.int64))
+    out = C.c_int(0)
+    ctx._sync_stream()
+    ctx._check(lib().gdm_autotune_batched(ctx.h, sz.ctypes.data_as(C.c_void_p), len(sz), C.byref(out)),
+               "gdm_autotune_batched")
+    return out.value
 
 
 def backward(ctx: Context, prob: GDMProblem, A, ipiv, F, e0, khat=(0.0, 0.0, 1.0), gF=None, g_sigma=None,

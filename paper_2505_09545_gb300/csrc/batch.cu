@@ -354,3 +354,68 @@ extern "C" gdm_status gdm_autotune(gdm_ctx *ctx, gdm_precision prec, const int64
         for (int c = 0; c < GDM_NB_CLASSES; c++) nb_out[c] = ctx->nb_table[c];
     return GDM_OK;
 }
+
+// Grouped-factorisation width for one batch's sizes: the lock-step LU of synthetic matrices of those sizes,
+// timed per candidate width (the second of two runs: the first captures the schedule's graph)
+extern "C" gdm_status gdm_autotune_batched(gdm_ctx *ctx, const int64_t *sizes, int n_sizes, int *nb_out) {
+    if (!ctx) return GDM_ERR_INVALID_ARG;
+    if (!sizes || n_sizes < 2) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "need at least two sizes");
+    if (getenv("GDM_BATCH_NB"))
+        return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "GDM_BATCH_NB is set: it overrides any tuned width");
+    GDM_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    GDM_GUARD_BEGIN
+    std::vector<int64_t> lda((size_t)n_sizes), n(sizes, sizes + n_sizes);
+    std::vector<size_t> off((size_t)n_sizes), poff((size_t)n_sizes);
+    size_t elems = 0, pv = 0;
+    for (int i = 0; i < n_sizes; i++) {
+        if (sizes[i] < 1) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "sizes must be >= 1");
+        lda[i] = (sizes[i] + 31) / 32 * 32;
+        off[i] = elems;
+        elems += (size_t)sizes[i] * lda[i];
+        poff[i] = pv;
+        pv += (size_t)(sizes[i] + 63) / 64 * 64;
+    }
+    float2 *M = nullptr;
+    int32_t *piv = nullptr;
+    GDM_CUDA_TRY(ctx, cudaMalloc(&M, sizeof(float2) * elems));
+    if (cudaMalloc(&piv, sizeof(int32_t) * pv) != cudaSuccess) {
+        cudaFree(M);
+        return gdm_fail(ctx, GDM_ERR_OOM, "autotune buffers");
+    }
+    std::vector<float2 *> Ap((size_t)n_sizes);
+    std::vector<int32_t *> pp((size_t)n_sizes);
+    for (int i = 0; i < n_sizes; i++) {
+        Ap[i] = M + off[i];
+        pp[i] = piv + poff[i];
+    }
+    const int cand[3] = {128, 256, 512};
+    int best_nb = 256;
+    float best = 1e30f;
+    gdm_status st = GDM_OK;
+    for (int c = 0; c < 3 && st == GDM_OK; c++) {
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && st == GDM_OK; rep++) {
+            for (int i = 0; i < n_sizes; i++) {
+                k_tune_matrix<<<2 * ctx->sm_count, 256, 0, ctx->stream>>>(Ap[i], n[i], lda[i],
+                                                                          1.0f / sqrtf((float)n[i]));
+                if (cudaGetLastError() != cudaSuccess) st = gdm_fail(ctx, GDM_ERR_CUDA, "autotune matrix");
+            }
+            if (st == GDM_OK)
+                st = gdm_glu_factor(ctx, n_sizes, Ap.data(), lda.data(), n.data(), pp.data(), cand[c], nullptr,
+                                    nullptr, &ms);
+        }
+        if (st == GDM_OK && ms < best) {
+            best = ms;
+            best_nb = cand[c];
+        }
+    }
+    cudaStreamSynchronize(ctx->stream);
+    gdm_glu_release(ctx);  // the synthetic matrices' table goes with them
+    cudaFree(M);
+    cudaFree(piv);
+    if (st != GDM_OK) return st;
+    ctx->glu_nb = best_nb;
+    if (nb_out) *nb_out = best_nb;
+    return GDM_OK;
+    GDM_GUARD_END(ctx)
+}

@@ -51,6 +51,9 @@ struct gdm_ctx {
     // block width (0 = built-in default), set by gdm_autotune_batched
     void *glu = nullptr;
     int glu_nb = 0;
+    // SMs a Green-sum launch sizes its source split for (0: all): a child of the pool shares the GPU with
+    // the other children running at the same time
+    int share_sms = 0;
 };
 #define GDM_PH_MAX 32768
 #define GDM_PROF_MAX 4096

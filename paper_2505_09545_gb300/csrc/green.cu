@@ -935,10 +935,12 @@ __global__ void k_residual_finalize(const double2 *__restrict__ partial, int nch
 // Grid of a Green-sum launch: ceil(m / GS_T) target blocks times nc source chunks of ceil(n / nc) sources.
 // The kernels are ALU-bound and a CTA's time is about proportional to its chunk, so the last partial wave of
 // CTAs idles the rest of the GPU; nc is the number of chunks (at most 64) that wastes the least of the
-// occ x SMs resident-CTA slots over the whole launch (fewest chunks among equals).
+// occ x SMs resident-CTA slots over the whole launch (fewest chunks among equals); a context that shares the
+// GPU with concurrent work counts only its share of the SMs.
 static void green_grid(gdm_ctx *ctx, int64_t m, int64_t n, int occ, int64_t *chunk, int *nchunks) {
     const int64_t tb = (m + GS_T - 1) / GS_T;
-    const int64_t slots = (int64_t)(occ < 1 ? 1 : occ) * ctx->sm_count;
+    const int sms = ctx->share_sms > 0 && ctx->share_sms < ctx->sm_count ? ctx->share_sms : ctx->sm_count;
+    const int64_t slots = (int64_t)(occ < 1 ? 1 : occ) * sms;
     int64_t maxc = (n + GS_S - 1) / GS_S;
     if (maxc > 64) maxc = 64;
     int64_t best_ch = n;

@@ -469,8 +469,8 @@ __device__ __forceinline__ void tmap_acquire(const void *map) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)map) : "memory");
 }
 
-// stages of operands and C chunk buffers: the K = 32 updates (two K chunks per tile) stream C, and keep
-// more C chunks in flight; the K = nbo updates keep more operand stages
+// stages of operands and C chunk buffers: the K = 32 updates (two K chunks per tile) mostly stream C and keep
+// eight C chunks in flight; the K = nbo updates split the room between three operand stages and four C chunks
 template <int ST, int NC> struct GCfg {
     static constexpr int STAGES = ST, NCB = NC, LOOK = NC / 2;
     static constexpr int A_BYTES = BM * BK * 4, B_BYTES = 256 * BK * 4, STAGE_BYTES = A_BYTES + B_BYTES;
@@ -479,7 +479,7 @@ template <int ST, int NC> struct GCfg {
     static __device__ __forceinline__ uint32_t idesc_n(int n_cols) { return Cfg<256, 1>::idesc_n(n_cols); }
 };
 using GCfgPanel = GCfg<2, 8>;
-using GCfgTrail = GCfg<4, 2>;
+using GCfgTrail = GCfg<3, 4>;
 
 template <class CF>
 __global__ void __launch_bounds__(NTHREADS, 1)

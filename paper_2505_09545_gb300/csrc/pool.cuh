@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -13,6 +14,9 @@
 
 // create child contexts until the context has `want` of them (at most GDM_POOL_MAX)
 gdm_status gdm_ensure_pool(gdm_ctx *ctx, int want);
+
+// GDM_POOL_FULL_GRIDS: children size their Green sums for the whole GPU (diagnostics)
+inline bool share_env() { return getenv("GDM_POOL_FULL_GRIDS") != nullptr; }
 
 inline bool gdm_per_item_numeric(gdm_status s) {
     return s == GDM_ERR_NOT_CONVERGED || s == GDM_ERR_NONFINITE || s == GDM_ERR_SINGULAR;
@@ -41,6 +45,7 @@ gdm_status gdm_run_pool(gdm_ctx *ctx, int n_items, const int64_t *size, int n_st
     for (int w = 0; w < ns; w++) {
         gdm_ctx *c = ctx->pool[w];
         memcpy(c->nb_table, ctx->nb_table, sizeof(ctx->nb_table));
+        c->share_sms = share_env() ? 0 : std::max(16, ctx->sm_count / ns);
         c->err[0] = 0;
         launches0[w] = c->launches;
         GDM_CUDA_TRY(ctx, cudaStreamWaitEvent(c->stream, ctx->ev2, 0));

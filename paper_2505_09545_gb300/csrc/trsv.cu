@@ -24,6 +24,16 @@
 
 #define TRSV_NBS_F32 128
 #define TRSV_W_MIN_BLOCKS 32  // row blocks from which the last dependency is folded into W_j (3N >= 3,969)
+// the threshold, or GDM_TRSV_W_MIN when set (diagnostics: W_j for shorter systems too)
+static int trsv_w_min() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("GDM_TRSV_W_MIN");
+        v = e ? atoi(e) : TRSV_W_MIN_BLOCKS;
+        if (v < 2) v = 2;
+    }
+    return v;
+}
 
 namespace {
 
@@ -562,7 +572,7 @@ gdm_status launch_modes_f32(gdm_ctx *ctx, const float2 *A, int64_t lda, int64_t 
         for (int q0 = 0; q0 < n_rhs; q0 += 2) {
             int nr = n_rhs - q0 < 2 ? n_rhs - q0 : 2;
             GDM_CUDA_TRY(ctx, cudaMemsetAsync(sync_buf, 0, sizeof(int) * (nblk + 2), ctx->stream));
-            const float2 *wops = nblk >= TRSV_W_MIN_BLOCKS ? ops + (size_t)4 * nblk * TS_NBS * TS_NBS : nullptr;
+            const float2 *wops = nblk >= trsv_w_min() ? ops + (size_t)4 * nblk * TS_NBS * TS_NBS : nullptr;
             k_trsv_tma<2><<<nblk, 288, smem, ctx->stream>>>(map, n, B, ldb, q0, nr, modes[mi], ops, wops, sync_buf,
                                                             ctx->dflags);
             GDM_LAUNCHED(ctx, "trsv_tma");
@@ -580,7 +590,7 @@ template <class C, int NBS> gdm_status launch_ops(gdm_ctx *ctx, const C *A, int6
     GDM_LAUNCHED(ctx, "block_ops");
     // the last-dependency operators W of the two modes of this solve direction (after all operator planes), for
     // systems long enough that the shorter dependency chain repays forming them
-    if (nblk >= TRSV_W_MIN_BLOCKS) {
+    if (nblk >= trsv_w_min()) {
         k_block_w<<<dim3((unsigned)nblk, 2), 256, 0, ctx->stream>>>((const float2 *)A, lda, n, (const float2 *)ops,
                                                                     (float2 *)ops + (size_t)4 * nblk * NBS * NBS,
                                                                     conj_trans ? 2 : 0);

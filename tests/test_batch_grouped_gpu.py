@@ -94,3 +94,24 @@ def test_per_problem_path_agrees(G, reference, monkeypatch):
         check(ss, ref, Fs, sigs, infos)
     finally:
         ctx.close()
+
+
+def test_autotuned_grouped_width(G, reference, monkeypatch):
+    """gdm_autotune_batched picks one of the candidate widths for these sizes, keeps it in the context, and
+    the batch factored with it still matches the oracle; a width fixed by GDM_BATCH_NB makes it refuse."""
+    ss, ref = reference
+    monkeypatch.delenv("GDM_BATCH_NB", raising=False)
+    monkeypatch.delenv("GDM_BATCH_POOL", raising=False)
+    ctx = G.Context(0)
+    try:
+        probs = [G.GDMProblem(t(s.pos), float(s.wavelengths[0]), 3, eps=t(s.eps), step=s.step) for s in ss]
+        nb = G.autotune_batched(ctx, [p.size for p in probs])
+        assert nb in (128, 256, 512)
+        Fs, sigs, infos = G.solve_batched(ctx, probs, [s.e0 for s in ss], precision="tf32", n_streams=2)
+        torch.cuda.synchronize()
+        check(ss, ref, Fs, sigs, infos)
+        monkeypatch.setenv("GDM_BATCH_NB", "256")
+        with pytest.raises(G.GDMError):
+            G.autotune_batched(ctx, [p.size for p in probs])
+    finally:
+        ctx.close()
