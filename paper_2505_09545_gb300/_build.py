@@ -14,7 +14,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libgdm.so")
-SOURCES = ["api.cu", "green.cu", "green_ff.cu", "lu.cu", "lu_tc.cu", "trsv.cu", "refine.cu", "backward.cu", "batch.cu", "batch_lu.cu", "gpm.cu", "gmres.cu"]
+SOURCES = ["api.cu", "green.cu", "green_ff.cu", "lu.cu", "lu_tc.cu", "trsv.cu", "refine.cu", "backward.cu", "batch.cu", "batch_lu.cu", "batch_refine.cu", "gpm.cu", "gmres.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-diag-suppress", "177,550"]

@@ -228,6 +228,7 @@ gdm_status gdm_destroy(gdm_ctx *ctx) {
     ctx->npool = 0;
     if (ctx->stream || ctx->ws) cudaStreamSynchronize(ctx->stream);
     gdm_glu_release(ctx);
+    gdm_gr_release(ctx);
     if (ctx->owns_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->dflags) cudaFree(ctx->dflags);

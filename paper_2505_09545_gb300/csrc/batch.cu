@@ -57,12 +57,20 @@ gdm_status item_inputs(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it,
     return GDM_OK;
 }
 
+gdm_status item_xsec(gdm_ctx *c, const gdm_batch_item *it);
+
 // factorisation (unless FACTORED), refined solve and cross sections of one item
 gdm_status item_solve(gdm_ctx *c, gdm_precision prec, const gdm_batch_item *it, const gdm_solve_opts *opts,
                       gdm_solve_info *info) {
     const gdm_problem *p = &it->prob;
     gdm_status s = gdm_solve_core(c, p, prec, it->A, it->lda, it->ipiv, it->F0, it->F, it->n_rhs, opts, info);
     if (s != GDM_OK) return s;
+    return item_xsec(c, it);
+}
+
+// cross sections of one solved item, if asked for
+gdm_status item_xsec(gdm_ctx *c, const gdm_batch_item *it) {
+    const gdm_problem *p = &it->prob;
     if (it->sigma) {
         double e2[64];
         for (int q = 0; q < it->n_rhs; q++) {
@@ -132,10 +140,38 @@ gdm_status solve_grouped(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_item 
     gdm_solve_opts go = fo;
     fo.flags |= GDM_SOLVE_FACTORED;
     go.flags |= GDM_SOLVE_GLOBAL_PIVOT;
+    // refined solves: cells with one or two illuminations all together (batch_refine.cu), unless
+    // GDM_BATCH_REFINE_POOL keeps them per item on the pool (diagnostics)
+    std::vector<int> gpos((size_t)n_items, -1);
+    std::vector<GrProblem> gp;
+    const bool grouped_refine = !getenv("GDM_BATCH_REFINE_POOL") && !(fo.flags & GDM_SOLVE_NO_REFINE);
+    for (int i = 0; i < n_items; i++) {
+        const gdm_batch_item *it = &items[i];
+        if (grouped_refine && it->prob.kind == 3 && it->n_rhs <= 2 && st[i] == GDM_OK &&
+            growth[i] <= (float)GDM_PIVOT_GROWTH_LIMIT) {
+            gpos[i] = (int)gp.size();
+            gp.push_back(GrProblem{&it->prob, A[i], lda[i], ipiv[i], it->F0, it->F, it->n_rhs});
+        }
+    }
+    std::vector<gdm_solve_info> ginf(gp.size());
+    if (!gp.empty()) {
+        memset(ginf.data(), 0, sizeof(gdm_solve_info) * gp.size());
+        GDM_TRY(gdm_gr_refine(ctx, (int)gp.size(), gp.data(), fo.tol > 0 ? fo.tol : 1e-12,
+                              fo.max_iter > 0 ? fo.max_iter : 40, ginf.data()));
+    }
     return gdm_run_pool(
         ctx, n_items, size.data(), n_streams, infos,
         [&](gdm_ctx *c, int, int i, gdm_solve_info *inf) {
             const gdm_batch_item *it = &items[i];
+            if (gpos[i] >= 0) {
+                *inf = ginf[gpos[i]];
+                inf->factor_ms = ms;
+                inf->pivot_growth = growth[i];
+                if (inf->status != GDM_OK)
+                    return gdm_fail(c, (gdm_status)inf->status, "refinement of the item: %s",
+                                    gdm_status_string((gdm_status)inf->status));
+                return item_xsec(c, it);
+            }
             if (st[i] != GDM_OK || !(growth[i] <= (float)GDM_PIVOT_GROWTH_LIMIT)) {
                 GDM_TRY(item_inputs(c, prec, it, true));
                 gdm_status s = item_solve(c, prec, it, &go, inf);

@@ -51,6 +51,8 @@ struct gdm_ctx {
     // block width (0 = built-in default), set by gdm_autotune_batched
     void *glu = nullptr;
     int glu_nb = 0;
+    // tables and scratch of the last grouped refinement (batch_refine.cu)
+    void *grf = nullptr;
     // SMs a Green-sum launch sizes its source split for (0: all): a child of the pool shares the GPU with
     // the other children running at the same time
     int share_sms = 0;
@@ -366,6 +368,85 @@ bool gdm_glu_encode(const GluItem *items, int n_items, int nbo, GluMaps *maps);
 gdm_status gdm_glu_factor(gdm_ctx *ctx, int n_items, float2 *const *A, const int64_t *lda, const int64_t *n,
                           int32_t *const *ipiv, int nbo, float *growth, int *status, float *ms);
 void gdm_glu_release(gdm_ctx *ctx);
+
+// ------------------------------------------------------------------ grouped refinement of a batch (batch_refine.cu)
+// Cells (kind 3) with at most two right-hand sides, factored by the grouped LU: every refinement step of
+// all problems still refining runs as one launch per kernel, the problems' work units split by a prefix
+// sum over a list of problem indices (CTA b works for problem list[k] when prefix[k] <= b < prefix[k + 1]).
+struct GrItem {
+    int64_t n;        // cells; the system has 3n rows
+    int nr;           // right-hand sides (1 or 2)
+    int nblk;         // 128-row blocks of the system
+    const double *pos;
+    const double2 *eps;
+    double eps_env, d3_4pi, self_S;
+    float kk[6];                // k, k^2 and 1/eps_env as FP32 (hi, lo) pairs (double-float sums)
+    float khi, klo, inv_eps;    // the FP32 sums' wavenumber pair and 1/eps_env
+    const float2 *A;            // factors
+    int64_t lda;
+    const int32_t *ipiv;        // their pivots (inside 32-row panels)
+    const double2 *rhs;         // (3n) x nr
+    double2 *X;                 // (3n) x nr solution
+    double2 *r, *P, *partial;   // residual, moments, Green-sum partials (nc x 2 x n x 3)
+    float2 *w;                  // work vector of the triangular solves, (3n) x nr
+    void *dip;                  // FP32-pair positions (48-byte records)
+    float *rec;                 // double-float source records of the residual
+    float2 *ops;                // block operators, 4 planes of 128 x 128 per block
+    int *sync;                  // triangular-solve flags (nblk + 2)
+    double *norms;              // [2q] ||d_q||^2, [2q + 1] ||X_q||^2, [4 + q] ||r_q||^2, [6 + q] ||rhs_q||^2
+    int64_t chunk;              // sources per Green-sum chunk
+    int nc;                     // chunks
+};
+// problem of work unit b of a grouped launch: k with prefix[k] <= b < prefix[k + 1] (whole CTA; uses a warp)
+__device__ __forceinline__ int gr_unit(const int *__restrict__ list, const int *__restrict__ prefix, int na, int b,
+                                       int *local) {
+    __shared__ int s_k;
+    if (threadIdx.x < 32) {
+        const int k = glu_find_item(prefix, na, b);
+        if (threadIdx.x == 0) s_k = k;
+    }
+    __syncthreads();
+    const int k = s_k;
+    *local = b - __ldg(&prefix[k]);
+    return __ldg(&list[k]);
+}
+// grouped launches (green.cu, green_ff.cu, trsv.cu, refine.cu); units per problem as their comments say
+gdm_status gdm_gr_prep_dip(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units);
+gdm_status gdm_gr_moments(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units);
+gdm_status gdm_gr_green_f32(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units);
+gdm_status gdm_gr_prep_src(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units);
+gdm_status gdm_gr_green_ff(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units,
+                           const void *tab);
+gdm_status gdm_gr_finalize(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units);
+gdm_status gdm_gr_block_ops(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units);
+gdm_status gdm_gr_trsv(gdm_ctx *ctx, const GrItem *it, const void *maps, const int *list, const int *jprefix,
+                       int nj, int units, int mode, int *ticket);
+gdm_status gdm_gr_norm2(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units);
+gdm_status gdm_gr_to_work(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units,
+                          int from_r);
+gdm_status gdm_gr_update(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units,
+                         int accumulate);
+// one problem of a grouped refinement (host view) and the refinement itself (batch_refine.cu): solves
+// A F = F0 for every problem with the factors in A, ipiv, refined to max_q ||dF_q|| / ||F_q|| <= tol within
+// max_iter steps; fills infos (iterations, rel_correction, rel_residual, refine_ms, status per problem:
+// GDM_OK, GDM_ERR_NOT_CONVERGED or GDM_ERR_NONFINITE). Returns a failure of the call itself only.
+struct GrProblem {
+    const gdm_problem *p;
+    const float2 *A;
+    int64_t lda;
+    const int32_t *ipiv;
+    const double *F0;
+    double *F;
+    int n_rhs;
+};
+gdm_status gdm_gr_refine(gdm_ctx *ctx, int n_items, const GrProblem *pb, double tol, int max_iter,
+                         gdm_solve_info *infos);
+void gdm_gr_release(gdm_ctx *ctx);
+// host: the TMA descriptor of a problem's factors for the triangular solves (128 bytes into map); false if
+// the encoder refuses
+bool gdm_trsv_encode_map(const float2 *A, int64_t n, int64_t lda, void *map);
+// fills dev_tab (257 x 16 bytes, device) with the phase-reduction table of the double-float sums
+gdm_status gdm_ff_table_fill(gdm_ctx *ctx, void *dev_tab);
 
 // problem helpers
 static inline double gdm_k0(const gdm_problem *p) { return 2.0 * 3.14159265358979323846 / p->wavelength; }

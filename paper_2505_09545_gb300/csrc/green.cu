@@ -882,12 +882,14 @@ __global__ void __launch_bounds__(GS_T) k_green_sum(const double *__restrict__ t
 // r = rhs - X + (G P)  [forward, P = alpha X, self-term S P_t for cells]
 // r = rhs - X + conj(alpha_t) conj(G P)  [adjoint kind 3, P = conj(X): (A^H X)_t = X_t - conj(alpha_t (G conj X)_t)]
 template <int KIND, int NR>
-__global__ void k_residual_finalize(const double2 *__restrict__ partial, int nchunks, int64_t n, int rhs0, int nr_here,
-                                    const double2 *__restrict__ rhs, const double2 *__restrict__ X,
-                                    const double2 *__restrict__ P, double self_S, int adjoint,
-                                    const double2 *__restrict__ eps, double eps_env, double d3_4pi, double sE,
-                                    double sH, double2 *__restrict__ r, double *__restrict__ norms2) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void residual_finalize_body(const double2 *__restrict__ partial, int nchunks, int64_t n,
+                                                       int rhs0, int nr_here, const double2 *__restrict__ rhs,
+                                                       const double2 *__restrict__ X, const double2 *__restrict__ P,
+                                                       double self_S, int adjoint, const double2 *__restrict__ eps,
+                                                       double eps_env, double d3_4pi, double sE, double sH,
+                                                       double2 *__restrict__ r, double *__restrict__ norms2,
+                                                       int64_t bx) {
+    int64_t t = bx * (int64_t)blockDim.x + threadIdx.x;
     double nrm[NR];
 #pragma unroll
     for (int q = 0; q < NR; q++) nrm[q] = 0.0;
@@ -930,6 +932,15 @@ __global__ void k_residual_finalize(const double2 *__restrict__ partial, int nch
             if (threadIdx.x == 0 && q < nr_here) atomicAdd(&norms2[rhs0 + q], v);
         }
     }
+}
+template <int KIND, int NR>
+__global__ void k_residual_finalize(const double2 *__restrict__ partial, int nchunks, int64_t n, int rhs0, int nr_here,
+                                    const double2 *__restrict__ rhs, const double2 *__restrict__ X,
+                                    const double2 *__restrict__ P, double self_S, int adjoint,
+                                    const double2 *__restrict__ eps, double eps_env, double d3_4pi, double sE,
+                                    double sH, double2 *__restrict__ r, double *__restrict__ norms2) {
+    residual_finalize_body<KIND, NR>(partial, nchunks, n, rhs0, nr_here, rhs, X, P, self_S, adjoint, eps, eps_env,
+                                     d3_4pi, sE, sH, r, norms2, blockIdx.x);
 }
 
 // Grid of a Green-sum launch: ceil(m / GS_T) target blocks times nc source chunks of ceil(n / nc) sources.
@@ -1009,15 +1020,14 @@ gdm_status gdm_launch_green_sum_ff(gdm_ctx *ctx, const gdm_problem *p, const dou
 // double-float position differences and phase of the FP32 assembly (about 1e-7 relative per pair, some 1e-6
 // for a sum): the low-precision operator of the iterative solver, ~1/9 of the double-float kernel's work
 template <int NR>
-__global__ void __launch_bounds__(GS_T) k_green_sum_f32(const DipF *__restrict__ dip, int64_t n,
-                                                       const double2 *__restrict__ P, int rhs0, int nr_here,
-                                                       float khi, float klo, float inv_eps, int64_t chunk,
-                                                       double2 *__restrict__ partial) {
+__device__ __forceinline__ void green_sum_f32_body(const DipF *__restrict__ dip, int64_t n,
+                                                   const double2 *__restrict__ P, int rhs0, int nr_here, float khi,
+                                                   float klo, float inv_eps, int64_t chunk,
+                                                   double2 *__restrict__ partial, int64_t bx, int64_t c) {
     __shared__ DipF sj[GS_S];
     __shared__ float2 sm[GS_S][NR][3];
-    const int64_t t = (int64_t)blockIdx.x * GS_T + threadIdx.x;
+    const int64_t t = bx * GS_T + threadIdx.x;
     const bool valid = t < n;
-    const int64_t c = blockIdx.y;
     const int64_t jb = c * chunk, je = min(n, jb + chunk);
     const DipF ti = dip[valid ? t : 0];
     const ff kff = {khi, klo};
@@ -1061,6 +1071,13 @@ __global__ void __launch_bounds__(GS_T) k_green_sum_f32(const DipF *__restrict__
 #pragma unroll
         for (int a = 0; a < 3; a++) o[a] = make_double2((double)acc[q][a].x, (double)acc[q][a].y);
     }
+}
+template <int NR>
+__global__ void __launch_bounds__(GS_T) k_green_sum_f32(const DipF *__restrict__ dip, int64_t n,
+                                                       const double2 *__restrict__ P, int rhs0, int nr_here,
+                                                       float khi, float klo, float inv_eps, int64_t chunk,
+                                                       double2 *__restrict__ partial) {
+    green_sum_f32_body<NR>(dip, n, P, rhs0, nr_here, khi, klo, inv_eps, chunk, partial, blockIdx.x, blockIdx.y);
 }
 
 // residual of the FP64 system (matrix-free); scratch: P (kN x n_rhs) + partial buffer; ffws (nullable):
@@ -1539,5 +1556,64 @@ gdm_status gdm_launch_cross_sections_noalloc(gdm_ctx *ctx, const gdm_problem *p,
     GDM_LAUNCHED(ctx, "xsec_partial");
     k_xsec_final_pref<<<n_rhs, 32, 0, ctx->stream>>>(part, (int)nb, n_rhs, pref, ext, sca, abs);
     GDM_LAUNCHED(ctx, "xsec_final_pref");
+    return GDM_OK;
+}
+
+// ================================================================== grouped refinement residual of a batch
+namespace {
+// P = alpha X of every listed problem (cells): ceil(3n nr / 256) CTAs of 256 per problem
+__global__ void __launch_bounds__(256) k_gr_moments(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                    const int *__restrict__ prefix, int na) {
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t ld = 3 * g.n, e = (int64_t)local * 256 + threadIdx.x;
+    if (e >= ld * g.nr) return;
+    const int64_t c = e % ld, q = e / ld, cell = c / 3;
+    const double2 ep = g.eps[cell];
+    const double2 al = make_double2((ep.x - g.eps_env) * g.d3_4pi, ep.y * g.d3_4pi);
+    g.P[q * ld + c] = cmul(al, g.X[q * ld + c]);
+}
+
+// the first refinement steps' FP32 sums: ceil(n / GS_T) target blocks x nc chunks per problem
+__global__ void __launch_bounds__(GS_T) k_gr_green_f32(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                       const int *__restrict__ prefix, int na) {
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t tb = (g.n + GS_T - 1) / GS_T;
+    green_sum_f32_body<2>((const DipF *)g.dip, g.n, g.P, 0, g.nr, g.khi, g.klo, g.inv_eps, g.chunk, g.partial,
+                          local % tb, local / tb);
+}
+
+// r = rhs - X + (G P + S P) and ||r_q||^2: ceil(n / 256) CTAs of 256 per problem
+__global__ void __launch_bounds__(256) k_gr_finalize(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                     const int *__restrict__ prefix, int na) {
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    residual_finalize_body<3, 2>(g.partial, g.nc, g.n, 0, g.nr, g.rhs, g.X, g.P, g.self_S, 0, g.eps, g.eps_env,
+                                 g.d3_4pi, 1.0, 1.0, g.r, g.norms + 4, local);
+}
+}  // namespace
+
+gdm_status gdm_gr_moments(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units) {
+    if (units <= 0) return GDM_OK;
+    k_gr_moments<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_moments");
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_green_f32(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units) {
+    if (units <= 0) return GDM_OK;
+    k_gr_green_f32<<<(unsigned)units, GS_T, 0, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_green_f32");
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_finalize(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units) {
+    if (units <= 0) return GDM_OK;
+    k_gr_finalize<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_finalize");
     return GDM_OK;
 }

@@ -203,21 +203,22 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // pairs. Source tiles (RF_S records) are double-buffered in shared memory by bulk copies issued one tile
 // ahead by one thread; every wait on them is bounded (on timeout the device error record gets
 // GDM_ERR_TIMEOUT and the CTA stops summing).
+// (the body takes the target block bx and the chunk c explicitly, so that the grouped sums of a batch run it
+// for any problem)
 template <int KIND, int OUT, int NR>
-__global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ tgt, int64_t m,
-                                                      const float *__restrict__ rec, int64_t n, float khi, float klo,
-                                                      float k2hi, float k2lo, float ie_hi, float ie_lo,
-                                                      const float4 *__restrict__ gtab, int64_t chunk, int self_exclude,
-                                                      double2 *__restrict__ partial, int *flags) {
+__device__ __forceinline__ void green_sum_ff_body(const DipF *__restrict__ tgt, int64_t m,
+                                                  const float *__restrict__ rec, int64_t n, float khi, float klo,
+                                                  float k2hi, float k2lo, float ie_hi, float ie_lo,
+                                                  const float4 *__restrict__ gtab, int64_t chunk, int self_exclude,
+                                                  double2 *__restrict__ partial, int *flags, int64_t bx, int64_t c) {
     using L = SrcRecLayout<KIND, NR>;
     __shared__ float4 tab[257];
     __shared__ __align__(16) float sbuf[2][RF_S * L::FLOATS];
     __shared__ uint64_t bar[2];
     __shared__ int abort_cta;
     for (int e = threadIdx.x; e < 257; e += RF_T) tab[e] = gtab[e];
-    const int64_t t = (int64_t)blockIdx.x * RF_T + threadIdx.x;
+    const int64_t t = bx * RF_T + threadIdx.x;
     const bool valid = t < m;
-    const int64_t c = blockIdx.y;
     const int64_t jb = c * chunk, je = min(n, jb + chunk);
     const int ntile = je > jb ? (int)((je - jb + RF_S - 1) / RF_S) : 0;
     if (threadIdx.x == 0) {
@@ -341,6 +342,15 @@ __global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ 
             o[a] = make_double2((double)acc[q][a].re.hi + (double)acc[q][a].re.lo,
                                 (double)acc[q][a].im.hi + (double)acc[q][a].im.lo);
     }
+}
+template <int KIND, int OUT, int NR>
+__global__ void __launch_bounds__(RF_T) k_green_sum_ff(const DipF *__restrict__ tgt, int64_t m,
+                                                      const float *__restrict__ rec, int64_t n, float khi, float klo,
+                                                      float k2hi, float k2lo, float ie_hi, float ie_lo,
+                                                      const float4 *__restrict__ gtab, int64_t chunk, int self_exclude,
+                                                      double2 *__restrict__ partial, int *flags) {
+    green_sum_ff_body<KIND, OUT, NR>(tgt, m, rec, n, khi, klo, k2hi, k2lo, ie_hi, ie_lo, gtab, chunk, self_exclude,
+                                     partial, flags, blockIdx.x, blockIdx.y);
 }
 
 // Gradient pair sums of the adjoint (cells), double-float on the FP32 pipes: partial[c][q][t][15] (FP64) =
@@ -660,5 +670,115 @@ gdm_status gdm_ff_dgreen_sum(gdm_ctx *ctx, const gdm_problem *p, const double2 *
     k_dgreen_sum_ff<<<grid, RF_T, 0, ctx->stream>>>(dip, n, rec, n, kk[0], kk[1], kk[2], kk[3], kk[4], kk[5], tab, chunk,
                                                     1, qslot, partial, ctx->dflags);
     GDM_LAUNCHED(ctx, "dgreen_sum_ff");
+    return GDM_OK;
+}
+
+// ---------------------------------------------------------------- grouped sums of a batch's refinement
+namespace {
+// FP32-pair positions of every listed problem: ceil(n / 256) CTAs of 256 per problem
+__global__ void __launch_bounds__(256) k_gr_prep_dip(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                     const int *__restrict__ prefix, int na) {
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const int64_t j = (int64_t)local * 256 + threadIdx.x;
+    if (j >= items[i].n) return;
+    const double *pos = items[i].pos;
+    DipF d;
+    const double x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
+    d.xh = (float)x;
+    d.yh = (float)y;
+    d.zh = (float)z;
+    d.xl = (float)(x - (double)d.xh);
+    d.yl = (float)(y - (double)d.yh);
+    d.zl = (float)(z - (double)d.zh);
+    d.alpha = make_float2(0.f, 0.f);
+    d.diag = make_float2(0.f, 0.f);
+    d.pad[0] = d.pad[1] = 0.f;
+    ((DipF *)items[i].dip)[j] = d;
+}
+
+// source records (positions and the moments P of both right-hand sides as double-float pairs):
+// ceil(n / 256) CTAs of 256 per problem
+__global__ void __launch_bounds__(256) k_gr_prep_src(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                     const int *__restrict__ prefix, int na) {
+    using L = SrcRecLayout<3, 2>;
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t j = (int64_t)local * 256 + threadIdx.x;
+    if (j >= g.n) return;
+    float *o = g.rec + j * L::FLOATS;
+    const DipF d = ((const DipF *)g.dip)[j];
+    o[0] = d.xh;
+    o[1] = d.yh;
+    o[2] = d.zh;
+    o[3] = d.xl;
+    o[4] = d.yl;
+    o[5] = d.zl;
+    o[6] = 0.f;
+    o[7] = 0.f;
+    const int64_t ld = 3 * g.n;
+    float4 *m = (float4 *)(o + 8);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            double2 v = make_double2(0.0, 0.0);
+            if (q < g.nr) v = g.P[q * ld + 3 * j + a];
+            const float rh = (float)v.x, ih = (float)v.y;
+            m[a * 2 + q] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+        }
+}
+
+// the residual's double-float sums, every pair (t, j != t) of each listed problem: ceil(n / RF_T) target
+// blocks x nc chunks per problem
+__global__ void __launch_bounds__(RF_T) k_gr_green_ff(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                      const int *__restrict__ prefix, int na,
+                                                      const float4 *__restrict__ tab, int *flags) {
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t tb = (g.n + RF_T - 1) / RF_T;
+    green_sum_ff_body<3, 3, 2>((const DipF *)g.dip, g.n, g.rec, g.n, g.kk[0], g.kk[1], g.kk[2], g.kk[3], g.kk[4],
+                               g.kk[5], tab, g.chunk, 1, g.partial, flags, local % tb, local / tb);
+}
+}  // namespace
+
+gdm_status gdm_gr_prep_dip(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units) {
+    if (units <= 0) return GDM_OK;
+    k_gr_prep_dip<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_prep_dip");
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_prep_src(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units) {
+    if (units <= 0) return GDM_OK;
+    k_gr_prep_src<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_prep_src");
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_green_ff(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units,
+                           const void *tab) {
+    if (units <= 0) return GDM_OK;
+    k_gr_green_ff<<<(unsigned)units, RF_T, 0, ctx->stream>>>(it, list, prefix, na, (const float4 *)tab, ctx->dflags);
+    GDM_LAUNCHED(ctx, "gr_green_ff");
+    return GDM_OK;
+}
+
+gdm_status gdm_ff_table_fill(gdm_ctx *ctx, void *dev_tab) {
+    static float4 h[257];
+    static bool made = false;
+    if (!made) {
+        for (int i = -128; i <= 128; i++) {
+            const double a = i * (3.14159265358979323846 / 128.0);
+            float ch, cl, sh, sl;
+            split(cos(a), &ch, &cl);
+            split(sin(a), &sh, &sl);
+            h[i + 128] = make_float4(ch, cl, sh, sl);
+        }
+        made = true;
+    }
+    GDM_CUDA_TRY(ctx, cudaMemcpyAsync(dev_tab, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
     return GDM_OK;
 }

@@ -111,6 +111,129 @@ __global__ void k_norm2(const double2 *__restrict__ v, int64_t ld, double *__res
     }
 }
 
+// ---------------------------------------------------------------- grouped refinement steps of a batch
+// (every kernel: ceil(3n nr / 256) CTAs of 256 per listed problem, element e = q (3n) + row)
+namespace {
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[2 * w] = a;
+        red[2 * w + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+            a += red[2 * k];
+            b += red[2 * k + 1];
+        }
+}
+
+// ||rhs_q||^2 into norms[6 + q]
+__global__ void __launch_bounds__(256) k_gr_norm2(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                  const int *__restrict__ prefix, int na) {
+    __shared__ double red[16];
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t ld = 3 * g.n, e0 = (int64_t)local * 256;
+    const int64_t e = e0 + threadIdx.x;
+    const int q = (int)(e0 / ld);  // a CTA spans at most one column boundary: split its sum by column
+    double a = 0.0, b = 0.0;
+    if (e < ld * g.nr) {
+        const double2 v = g.rhs[e];
+        const double s2 = v.x * v.x + v.y * v.y;
+        if (e / ld == q) a = s2;
+        else b = s2;
+    }
+    block_sum2(a, b, red);
+    if (threadIdx.x == 0) {
+        atomicAdd(&g.norms[6 + q], a);
+        if (b != 0.0) atomicAdd(&g.norms[6 + q + 1], b);
+    }
+}
+
+// w = (r or rhs) x the power of two that brings the largest column norm near 1
+__global__ void __launch_bounds__(256) k_gr_to_work(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                    const int *__restrict__ prefix, int na, int from_r) {
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t e = (int64_t)local * 256 + threadIdx.x;
+    if (e >= 3 * g.n * g.nr) return;
+    const double scale = work_scale(g.norms + (from_r ? 4 : 6), g.nr);
+    const double2 v = from_r ? g.r[e] : g.rhs[e];
+    g.w[e] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+}
+
+// X (+)= w / scale; ||d_q||^2 into norms[2q], ||X_q||^2 into norms[2q + 1]
+__global__ void __launch_bounds__(256) k_gr_update(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                   const int *__restrict__ prefix, int na, int accumulate) {
+    __shared__ double red[16];
+    __shared__ double red2[16];
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t ld = 3 * g.n, e0 = (int64_t)local * 256;
+    const int64_t e = e0 + threadIdx.x;
+    const int q = (int)(e0 / ld);
+    const double inv_scale = 1.0 / work_scale(g.norms + (accumulate ? 4 : 6), g.nr);
+    double dn0 = 0.0, dn1 = 0.0, xn0 = 0.0, xn1 = 0.0;
+    if (e < ld * g.nr) {
+        const float2 dv = g.w[e];
+        const double dx = dv.x * inv_scale, dy = dv.y * inv_scale;
+        double2 x = accumulate ? g.X[e] : make_double2(0.0, 0.0);
+        x.x += dx;
+        x.y += dy;
+        g.X[e] = x;
+        const double d2 = dx * dx + dy * dy, x2 = x.x * x.x + x.y * x.y;
+        if (e / ld == q) {
+            dn0 = d2;
+            xn0 = x2;
+        } else {
+            dn1 = d2;
+            xn1 = x2;
+        }
+    }
+    block_sum2(dn0, dn1, red);
+    block_sum2(xn0, xn1, red2);
+    if (threadIdx.x == 0) {
+        atomicAdd(&g.norms[2 * q], dn0);
+        atomicAdd(&g.norms[2 * q + 1], xn0);
+        if (dn1 != 0.0 || xn1 != 0.0) {
+            atomicAdd(&g.norms[2 * q + 2], dn1);
+            atomicAdd(&g.norms[2 * q + 3], xn1);
+        }
+    }
+}
+}  // namespace
+
+gdm_status gdm_gr_norm2(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units) {
+    if (units <= 0) return GDM_OK;
+    k_gr_norm2<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_norm2");
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_to_work(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units,
+                          int from_r) {
+    if (units <= 0) return GDM_OK;
+    k_gr_to_work<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na, from_r);
+    GDM_LAUNCHED(ctx, "gr_to_work");
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_update(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units,
+                         int accumulate) {
+    if (units <= 0) return GDM_OK;
+    k_gr_update<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na, accumulate);
+    GDM_LAUNCHED(ctx, "gr_update");
+    return GDM_OK;
+}
+
 template <class C>
 static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision prec, const void *A, int64_t lda,
                             const int32_t *ipiv, const double *rhs, double *X, int n_rhs, int adjoint,

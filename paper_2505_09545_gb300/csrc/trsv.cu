@@ -60,12 +60,12 @@ template <class C> __device__ __forceinline__ C cz() {
 // substitution into its own and the later row groups), U backward (division by the diagonal, then the
 // column's multiple subtracted from the rows above).
 constexpr int OPS_CPW = 2;  // columns per warp
-__global__ void __launch_bounds__(256, 2) k_block_ops(const float2 *__restrict__ A, int64_t lda, int64_t n,
-                                                   const int32_t *__restrict__ ipiv, float2 *__restrict__ ops) {
+__device__ __forceinline__ void block_ops_body(const float2 *__restrict__ A, int64_t lda, int64_t n,
+                                               const int32_t *__restrict__ ipiv, float2 *__restrict__ ops, int bid) {
     constexpr int NBS = TRSV_NBS_F32, R = NBS / 32, CGS = NBS / (8 * OPS_CPW);
     __shared__ float2 Ds[32][NBS + 1];
     __shared__ int piv[NBS];
-    const int cg = blockIdx.x % CGS, tri = (blockIdx.x / CGS) & 1, j = blockIdx.x / (2 * CGS);
+    const int cg = bid % CGS, tri = (bid / CGS) & 1, j = bid / (2 * CGS);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t r0 = (int64_t)j * NBS;
     if (r0 >= n) return;
@@ -164,6 +164,18 @@ __global__ void __launch_bounds__(256, 2) k_block_ops(const float2 *__restrict__
             ocm[col * NBS + row] = x[u][q];
             orm[row * NBS + col] = x[u][q];
         }
+}
+__global__ void __launch_bounds__(256, 2) k_block_ops(const float2 *__restrict__ A, int64_t lda, int64_t n,
+                                                      const int32_t *__restrict__ ipiv, float2 *__restrict__ ops) {
+    block_ops_body(A, lda, n, ipiv, ops, blockIdx.x);
+}
+// the same for every listed problem of a batch: nblk x 16 CTAs per problem
+__global__ void __launch_bounds__(256, 2) k_gr_block_ops(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                         const int *__restrict__ prefix, int na) {
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    block_ops_body(g.A, g.lda, 3 * g.n, g.ipiv, g.ops, local);
 }
 
 // ------------------------------------------------------------------ last-dependency operators
@@ -306,11 +318,13 @@ __device__ __forceinline__ void bulk1d(void *dst, const void *src, uint32_t byte
                  : "memory");
 }
 
+// (the body takes the descriptor by address and, for the grouped solves of a batch, the block's position in
+// solve order tk_given; tk_given < 0 takes a ticket from sync_buf[0])
 template <int NR>
-__global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUtensorMap tmA, int64_t n,
-                                                   float2 *__restrict__ B, int64_t ldb, int rhs0, int nr_here,
-                                                   int mode, const float2 *__restrict__ ops,
-                                                   const float2 *__restrict__ wops, int *sync_buf, int *gflags) {
+__device__ __forceinline__ void trsv_tma_body(const CUtensorMap *tmAp, int64_t n, float2 *__restrict__ B,
+                                              int64_t ldb, int rhs0, int nr_here, int mode,
+                                              const float2 *__restrict__ ops, const float2 *__restrict__ wops,
+                                              int *sync_buf, int *gflags, int tk_given) {
     constexpr int NBS = TS_NBS, HALF = TS_HALF;
     extern __shared__ __align__(1024) unsigned char tsm[];
     float2 *ring = (float2 *)tsm;  // [NSTAGE][HALF][NBS]
@@ -324,7 +338,7 @@ __global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUt
     volatile int *flags = (volatile int *)(sync_buf + 2);
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     if (tid == 0) {
-        s_ticket = atomicAdd(ticket, 1);
+        s_ticket = tk_given >= 0 ? tk_given : atomicAdd(ticket, 1);
         for (int st = 0; st < TS_NSTAGE; st++) {
             tmbar_init(&full[st], 1);
             tmbar_init(&empty[st], 8);
@@ -366,7 +380,7 @@ __global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUt
                     // no-trans: columns of block k, rows of block j; conj-trans: columns of block j, rows of block k
                     const int x = (int)(2 * ((mode <= 1) ? r0 : k0));
                     const int y = (int)(((mode <= 1) ? k0 : r0) + half * HALF);
-                    tma2d(dst, &tmA, x, y, &full[st]);
+                    tma2d(dst, tmAp, x, y, &full[st]);
                 } else if (it < 2 * ndep + 2) {
                     bulk1d(dst, opm + (size_t)half * HALF * NBS, TS_STAGE_BYTES, &full[st]);
                 } else {
@@ -527,6 +541,36 @@ __global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUt
     asm volatile("bar.sync 1, 256;" ::: "memory");
     if (tid == 0) atomicExch((int *)(flags + j), 1);
 }
+template <int NR>
+__global__ void __launch_bounds__(288, 1) k_trsv_tma(const __grid_constant__ CUtensorMap tmA, int64_t n,
+                                                   float2 *__restrict__ B, int64_t ldb, int rhs0, int nr_here,
+                                                   int mode, const float2 *__restrict__ ops,
+                                                   const float2 *__restrict__ wops, int *sync_buf, int *gflags) {
+    trsv_tma_body<NR>(&tmA, n, B, ldb, rhs0, nr_here, mode, ops, wops, sync_buf, gflags, -1);
+}
+// The solves of every listed problem of a batch in one launch: a global ticket T (taken in launch order)
+// enumerates (position tk in solve order, problem) with tk slowest, so that every problem's blocks come in
+// dependency order and the first blocks of all problems come first; jprefix[tk] counts the tickets before
+// position tk (the problems with more than tk blocks are a prefix of the list, which is sorted by
+// decreasing size). Each problem has its own flags (GrItem sync) and descriptor (maps).
+__global__ void __launch_bounds__(288, 1) k_gr_trsv(const GrItem *__restrict__ items, const CUtensorMap *maps,
+                                                    const int *__restrict__ list, const int *__restrict__ jprefix,
+                                                    int nj, int mode, int *ticket, int *gflags) {
+    __shared__ int s_t[2];
+    if (threadIdx.x == 0) {
+        const int T = atomicAdd(ticket, 1);
+        int tk = 0;
+        while (tk + 1 < nj && jprefix[tk + 1] <= T) tk++;
+        s_t[0] = tk;
+        s_t[1] = list[T - jprefix[tk]];
+    }
+    __syncthreads();
+    const int tk = s_t[0], i = s_t[1];
+    const GrItem &g = items[i];
+    // the descriptor was written by the host before the launch: order that write before the copies
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&maps[i]) : "memory");
+    trsv_tma_body<2>(&maps[i], 3 * g.n, g.w, 3 * g.n, 0, g.nr, mode, g.ops, nullptr, g.sync, gflags, tk);
+}
 
 // every pivot inside its own block of nbs rows?
 __global__ void k_pivots_local(const int32_t *__restrict__ ipiv, int64_t n, int nbs, int *bad) {
@@ -600,6 +644,42 @@ template <class C, int NBS> gdm_status launch_ops(gdm_ctx *ctx, const C *A, int6
 }
 
 }  // namespace
+
+bool gdm_trsv_encode_map(const float2 *A, int64_t n, int64_t lda, void *map) {
+    auto fn = trsv_encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * n), (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)(2 * lda * 4)};
+    cuuint32_t box[2] = {2 * TS_NBS, TS_HALF};
+    cuuint32_t es[2] = {1, 1};
+    return fn((CUtensorMap *)map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)A, dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+gdm_status gdm_gr_block_ops(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units) {
+    if (units <= 0) return GDM_OK;
+    k_gr_block_ops<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_block_ops");
+    return GDM_OK;
+}
+
+// one triangle (mode 0: L, mode 1: U) of every listed problem; the flags of those problems and *ticket must
+// be zero at the launch
+gdm_status gdm_gr_trsv(gdm_ctx *ctx, const GrItem *it, const void *maps, const int *list, const int *jprefix,
+                       int nj, int units, int mode, int *ticket) {
+    if (units <= 0) return GDM_OK;
+    const int smem = TS_NSTAGE * TS_STAGE_BYTES;
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_gr_trsv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+    }
+    k_gr_trsv<<<(unsigned)units, 288, smem, ctx->stream>>>(it, (const CUtensorMap *)maps, list, jprefix, nj, mode,
+                                                          ticket, ctx->dflags);
+    GDM_LAUNCHED(ctx, "gr_trsv");
+    return GDM_OK;
+}
 
 size_t gdm_trsv_sync_bytes(int64_t n) { return sizeof(int) * ((n + 31) / 32 + 8); }
 

@@ -1,6 +1,8 @@
-"""The grouped factorisation of a batch: gdm_solve_batched at TF32 factors all its problems together, one
-lock-step launch per panel step of the largest problem (panels, interchanges with the U rows, tensor-core
-updates over the tiles of every problem), captured once into a CUDA graph and replayed.
+"""The grouped factorisation and refinement of a batch: gdm_solve_batched at TF32 factors all its problems
+together, one lock-step launch per panel step of the largest problem (panels, interchanges with the U rows,
+tensor-core updates over the tiles of every problem), captured once into a CUDA graph and replayed; then
+refines all of them together (residuals, scaling, both triangular solves and the update as one launch each
+per step, one host check of every problem's norms per step).
 
 The sizes sit on and around the panel (32 rows) and outer block (128/256/512 rows) boundaries, from a
 single cell (3N = 3) up to 3N = 1,029, with ragged tails, so that problems drop out of the lock step at
@@ -83,9 +85,12 @@ def test_grouped_factorisation_matches_oracle(G, reference, nb, monkeypatch):
         ctx.close()
 
 
-def test_per_problem_path_agrees(G, reference, monkeypatch):
+@pytest.mark.parametrize("switch", ["GDM_BATCH_POOL", "GDM_BATCH_REFINE_POOL"])
+def test_per_problem_path_agrees(G, reference, monkeypatch, switch):
+    """The per-problem factorisations (GDM_BATCH_POOL) and the per-problem refinements on the stream pool
+    (GDM_BATCH_REFINE_POOL) reach the oracle too."""
     ss, ref = reference
-    monkeypatch.setenv("GDM_BATCH_POOL", "1")
+    monkeypatch.setenv(switch, "1")
     ctx = G.Context(0)
     try:
         probs = [G.GDMProblem(t(s.pos), float(s.wavelengths[0]), 3, eps=t(s.eps), step=s.step) for s in ss]
@@ -113,5 +118,23 @@ def test_autotuned_grouped_width(G, reference, monkeypatch):
         monkeypatch.setenv("GDM_BATCH_NB", "256")
         with pytest.raises(G.GDMError):
             G.autotune_batched(ctx, [p.size for p in probs])
+    finally:
+        ctx.close()
+
+
+def test_grouped_refinement_reports_non_convergence(G, reference):
+    """A refinement cap of one step with an unreachable tolerance: every problem of the grouped refinement
+    reports GDM_ERR_NOT_CONVERGED in its record and the call fails with it; the context still solves the
+    batch correctly afterwards."""
+    ss, ref = reference
+    ctx = G.Context(0)
+    try:
+        probs = [G.GDMProblem(t(s.pos), float(s.wavelengths[0]), 3, eps=t(s.eps), step=s.step) for s in ss]
+        with pytest.raises(G.GDMError) as e:
+            G.solve_batched(ctx, probs, [s.e0 for s in ss], precision="tf32", n_streams=2, max_iter=1, tol=1e-30)
+        assert "NOT_CONVERGED" in str(e.value)
+        Fs, sigs, infos = G.solve_batched(ctx, probs, [s.e0 for s in ss], precision="tf32", n_streams=2)
+        torch.cuda.synchronize()
+        check(ss, ref, Fs, sigs, infos)
     finally:
         ctx.close()
