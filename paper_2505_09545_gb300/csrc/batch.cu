@@ -119,60 +119,93 @@ int grouped_nb(const gdm_ctx *ctx) {
 gdm_status solve_grouped(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_item *items, int n_items,
                          const gdm_solve_opts *opts, int n_streams, gdm_solve_info *infos,
                          const std::vector<int64_t> &size) {
-    GDM_TRY(gdm_run_pool(ctx, n_items, size.data(), n_streams, infos,
-                         [&](gdm_ctx *c, int, int i, gdm_solve_info *) { return item_inputs(c, prec, &items[i], true); },
-                         nullptr));
-    std::vector<float2 *> A((size_t)n_items);
-    std::vector<int64_t> lda((size_t)n_items);
-    std::vector<int32_t *> ipiv((size_t)n_items);
-    std::vector<float> growth((size_t)n_items, 0.f);
-    std::vector<int> st((size_t)n_items, 0);
-    for (int i = 0; i < n_items; i++) {
-        A[i] = (float2 *)items[i].A;
-        lda[i] = items[i].lda;
-        ipiv[i] = items[i].ipiv;
-    }
-    float ms = 0.f;
-    GDM_TRY(gdm_glu_factor(ctx, n_items, A.data(), lda.data(), size.data(), ipiv.data(), grouped_nb(ctx),
-                           growth.data(), st.data(), &ms));
     gdm_solve_opts fo = {0, 0, 0.0};
     if (opts) fo = *opts;
     gdm_solve_opts go = fo;
     fo.flags |= GDM_SOLVE_FACTORED;
     go.flags |= GDM_SOLVE_GLOBAL_PIVOT;
-    // refined solves: cells with one or two illuminations all together (batch_refine.cu), unless
-    // GDM_BATCH_REFINE_POOL keeps them per item on the pool (diagnostics)
+    std::vector<float2 *> A((size_t)n_items);
+    std::vector<int64_t> lda((size_t)n_items);
+    std::vector<int32_t *> ipiv((size_t)n_items);
+    for (int i = 0; i < n_items; i++) {
+        A[i] = (float2 *)items[i].A;
+        lda[i] = items[i].lda;
+        ipiv[i] = items[i].ipiv;
+    }
+    // cells with one or two illuminations are refined (and their cross sections summed) all together
+    // (batch_refine.cu), unless GDM_BATCH_REFINE_POOL keeps them per item on the pool (diagnostics); when
+    // every item is such a problem, their plane waves and assembly run together too
     std::vector<int> gpos((size_t)n_items, -1);
     std::vector<GrProblem> gp;
     const bool grouped_refine = !getenv("GDM_BATCH_REFINE_POOL") && !(fo.flags & GDM_SOLVE_NO_REFINE);
     for (int i = 0; i < n_items; i++) {
         const gdm_batch_item *it = &items[i];
-        if (grouped_refine && it->prob.kind == 3 && it->n_rhs <= 2 && st[i] == GDM_OK &&
-            growth[i] <= (float)GDM_PIVOT_GROWTH_LIMIT) {
+        if (grouped_refine && it->prob.kind == 3 && it->n_rhs <= 2) {
             gpos[i] = (int)gp.size();
-            gp.push_back(GrProblem{&it->prob, A[i], lda[i], ipiv[i], it->F0, it->F, it->n_rhs});
+            gp.push_back(GrProblem{&it->prob, A[i], lda[i], ipiv[i], it->F0, it->F, it->n_rhs, it->e0, it->khat,
+                                   it->e0_norm2, it->sigma});
         }
     }
+    const bool all_grouped = (int)gp.size() == n_items;
+    if (!gp.empty()) GDM_TRY(gdm_gr_prepare(ctx, (int)gp.size(), gp.data()));
+    if (all_grouped) {
+        GDM_TRY(gdm_gr_inputs(ctx));
+    } else {
+        GDM_TRY(gdm_run_pool(
+            ctx, n_items, size.data(), n_streams, infos,
+            [&](gdm_ctx *c, int, int i, gdm_solve_info *) { return item_inputs(c, prec, &items[i], true); }, nullptr));
+    }
+    std::vector<float> growth((size_t)n_items, 0.f);
+    std::vector<int> st((size_t)n_items, 0);
+    float ms = 0.f;
+    GDM_TRY(gdm_glu_factor(ctx, n_items, A.data(), lda.data(), size.data(), ipiv.data(), grouped_nb(ctx),
+                           growth.data(), st.data(), &ms));
+    auto cert_ok = [&](int i) { return st[i] == GDM_OK && growth[i] <= (float)GDM_PIVOT_GROWTH_LIMIT; };
+    std::vector<unsigned char> use(gp.size(), 0);
     std::vector<gdm_solve_info> ginf(gp.size());
+    int n_pool = 0;
+    for (int i = 0; i < n_items; i++) {
+        if (gpos[i] >= 0 && cert_ok(i)) use[gpos[i]] = 1;
+        else n_pool++;
+    }
     if (!gp.empty()) {
         memset(ginf.data(), 0, sizeof(gdm_solve_info) * gp.size());
-        GDM_TRY(gdm_gr_refine(ctx, (int)gp.size(), gp.data(), fo.tol > 0 ? fo.tol : 1e-12,
-                              fo.max_iter > 0 ? fo.max_iter : 40, ginf.data()));
+        GDM_TRY(gdm_gr_refine(ctx, use.data(), fo.tol > 0 ? fo.tol : 1e-12, fo.max_iter > 0 ? fo.max_iter : 40,
+                              ginf.data()));
+        GDM_TRY(gdm_gr_xsec(ctx, use.data()));
+    }
+    auto grouped_info = [&](int i, gdm_solve_info *inf) {
+        *inf = ginf[gpos[i]];
+        inf->factor_ms = ms;
+        inf->pivot_growth = growth[i];
+        return (gdm_status)inf->status;
+    };
+    if (n_pool == 0) {
+        // every item was refined together: records, and the first numerical failure as the call's status
+        gdm_status first = GDM_OK;
+        int first_item = -1;
+        for (int i = 0; i < n_items; i++) {
+            gdm_solve_info tmp;
+            const gdm_status s = grouped_info(i, infos ? &infos[i] : &tmp);
+            if (s != GDM_OK && first == GDM_OK) {
+                first = s;
+                first_item = i;
+            }
+        }
+        if (first != GDM_OK)
+            return gdm_fail(ctx, first, "item %d: refinement: %s", first_item, gdm_status_string(first));
+        return GDM_OK;
     }
     return gdm_run_pool(
         ctx, n_items, size.data(), n_streams, infos,
         [&](gdm_ctx *c, int, int i, gdm_solve_info *inf) {
             const gdm_batch_item *it = &items[i];
-            if (gpos[i] >= 0) {
-                *inf = ginf[gpos[i]];
-                inf->factor_ms = ms;
-                inf->pivot_growth = growth[i];
-                if (inf->status != GDM_OK)
-                    return gdm_fail(c, (gdm_status)inf->status, "refinement of the item: %s",
-                                    gdm_status_string((gdm_status)inf->status));
-                return item_xsec(c, it);
+            if (gpos[i] >= 0 && use[gpos[i]]) {
+                const gdm_status s = grouped_info(i, inf);
+                if (s != GDM_OK) return gdm_fail(c, s, "refinement of the item: %s", gdm_status_string(s));
+                return GDM_OK;
             }
-            if (st[i] != GDM_OK || !(growth[i] <= (float)GDM_PIVOT_GROWTH_LIMIT)) {
+            if (!cert_ok(i)) {
                 GDM_TRY(item_inputs(c, prec, it, true));
                 gdm_status s = item_solve(c, prec, it, &go, inf);
                 inf->refactored = 1;

@@ -23,6 +23,7 @@ constexpr int GR_CHUNK = 256;  // sources per Green-sum chunk
 struct RPlan {
     std::vector<int64_t> n;  // signature: cells per problem (sorted, decreasing)
     std::vector<int> nr;
+    std::vector<int> order;  // table position -> caller's index (of the prepared call)
     char *dmem = nullptr;    // tables, scratch and flags
     GrItem *d_items = nullptr;
     void *d_maps = nullptr;  // one 128-byte descriptor per problem
@@ -48,7 +49,8 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 inline int units_elem(const GrItem &g) { return (int)((3 * g.n * g.nr + 255) / 256); }
 inline int units_cell(const GrItem &g) { return (int)((g.n + 255) / 256); }
 inline int units_green(const GrItem &g) { return (int)((g.n + 127) / 128) * g.nc; }
-inline int units_ops(const GrItem &g) { return g.nblk * 16; }
+inline int units_ops(const GrItem &g) { return g.nblk * TRSV_OPS_CTAS; }
+inline int units_asm(const GrItem &g) { return (int)((g.n + 127) / 128) * (int)((g.n + 7) / 8); }
 
 }  // namespace
 
@@ -68,7 +70,8 @@ gdm_status alloc_rplan(gdm_ctx *ctx, RPlan &R) {
     const size_t o_tab = take(257 * 16);
     const size_t o_tickets = take(sizeof(int) * 8);
     const size_t o_norms = take(sizeof(double) * 8 * N);
-    std::vector<size_t> o_r(N), o_P(N), o_w(N), o_part(N), o_dip(N), o_rec(N), o_ops(N), o_sync(N);
+    const size_t o_xs = take(sizeof(double) * 4 * N);
+    std::vector<size_t> o_r(N), o_P(N), o_w(N), o_part(N), o_dip(N), o_dipa(N), o_rec(N), o_ops(N), o_sync(N);
     size_t sync_ints = 0;
     for (int i = 0; i < N; i++) {
         const int64_t n = R.n[i], ns = 3 * n;
@@ -79,6 +82,7 @@ gdm_status alloc_rplan(gdm_ctx *ctx, RPlan &R) {
         o_w[i] = take(sizeof(float2) * ns * 2);
         o_part[i] = take(sizeof(double2) * nc * 2 * ns);
         o_dip[i] = take((size_t)48 * n);
+        o_dipa[i] = take((size_t)48 * n);
         o_rec[i] = take((size_t)4 * (8 + 4 * 3 * 2) * n);
         o_ops[i] = take(sizeof(float2) * 4 * nblk * 128 * 128);
         o_sync[i] = sync_ints;
@@ -111,6 +115,8 @@ gdm_status alloc_rplan(gdm_ctx *ctx, RPlan &R) {
         g.w = (float2 *)(b + o_w[i]);
         g.partial = (double2 *)(b + o_part[i]);
         g.dip = b + o_dip[i];
+        g.dipa = b + o_dipa[i];
+        g.xs = (double *)(b + o_xs) + 4 * i;
         g.rec = (float *)(b + o_rec[i]);
         g.ops = (float2 *)(b + o_ops[i]);
         g.sync = R.d_sync + o_sync[i];
@@ -156,12 +162,40 @@ void gdm_gr_release(gdm_ctx *ctx) {
     ctx->grf = nullptr;
 }
 
-gdm_status gdm_gr_refine(gdm_ctx *ctx, int n_items, const GrProblem *pb, double tol, int max_iter,
-                         gdm_solve_info *infos) {
-    if (n_items < 1) return GDM_OK;
+namespace {
+// host staging areas of the pinned block: descriptors, the table, the lists of one step, the norms
+struct Staging {
+    char *maps;
+    GrItem *items;
+    int *lists;
+    double *norms;
+};
+Staging staging(RPlan &R) {
+    const int N = (int)R.n.size();
+    Staging st;
+    st.maps = R.h_pinned;
+    st.items = (GrItem *)(R.h_pinned + R.maps_bytes);
+    st.lists = (int *)((char *)st.items + up256(sizeof(GrItem) * N));
+    st.norms = (double *)((char *)st.lists + R.stage_bytes);
+    return st;
+}
+
+// copies a step's lists to the device (the previous step's copy has completed: every step ends with a
+// synchronisation)
+gdm_status upload_lists(gdm_ctx *ctx, RPlan &R, const std::vector<int> &stage) {
+    if (stage.size() > R.lists_cap) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "grouped lists");
+    int *h = staging(R).lists;
+    memcpy(h, stage.data(), sizeof(int) * stage.size());
+    GDM_CUDA_TRY(ctx, cudaMemcpyAsync(R.d_lists, h, sizeof(int) * stage.size(), cudaMemcpyHostToDevice, ctx->stream));
+    return GDM_OK;
+}
+}  // namespace
+
+gdm_status gdm_gr_prepare(gdm_ctx *ctx, int n_items, const GrProblem *pb) {
+    if (n_items < 1) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "grouped batch: no problems");
     for (int i = 0; i < n_items; i++)
         if (pb[i].p->kind != 3 || pb[i].n_rhs < 1 || pb[i].n_rhs > 2)
-            return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "grouped refinement: cells with one or two right-hand sides");
+            return gdm_fail(ctx, GDM_ERR_UNSUPPORTED, "grouped batch: cells with one or two right-hand sides");
     // table order: decreasing size (the solves' tickets need it)
     std::vector<int> order(n_items);
     for (int i = 0; i < n_items; i++) order[i] = i;
@@ -184,53 +218,93 @@ gdm_status gdm_gr_refine(gdm_ctx *ctx, int n_items, const GrProblem *pb, double 
             return s;
         }
     }
-    // this call's problems: pointers and scalars into the table, descriptors of the factors
+    R->order = order;
+    // this call's problems: pointers, scalars, amplitudes and descriptors of the factors' storage
     const double PI = 3.14159265358979323846;
-    char *hmaps = R->h_pinned;
-    GrItem *hitems = (GrItem *)(R->h_pinned + R->maps_bytes);
-    int *hstage = (int *)((char *)hitems + up256(sizeof(GrItem) * n_items));
-    double *hnorms = (double *)((char *)hstage + R->stage_bytes);
+    const Staging st = staging(*R);
     GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // the staging buffers are free
     for (int k = 0; k < n_items; k++) {
         const GrProblem &q = pb[order[k]];
-        GrItem g = R->h_items[k];
+        GrItem &g = R->h_items[k];
         const gdm_problem *p = q.p;
-        const double k0 = 2.0 * PI / p->wavelength, kk = sqrt(p->eps_env) * k0;
+        g.n_env = sqrt(p->eps_env);
+        g.k = g.n_env * 2.0 * PI / p->wavelength;
         g.pos = p->pos;
         g.eps = (const double2 *)p->eps;
         g.eps_env = p->eps_env;
         g.d3_4pi = p->step * p->step * p->step / (4.0 * PI);
         g.self_S = -4.0 * PI / (3.0 * p->eps_env * p->step * p->step * p->step);
-        const double v[3] = {kk, kk * kk, 1.0 / p->eps_env};
+        const double v[3] = {g.k, g.k * g.k, 1.0 / p->eps_env};
         for (int t = 0; t < 3; t++) {
             g.kk[2 * t] = (float)v[t];
             g.kk[2 * t + 1] = (float)(v[t] - (double)g.kk[2 * t]);
         }
-        g.khi = (float)kk;
-        g.klo = (float)(kk - (double)g.khi);
+        g.khi = (float)g.k;
+        g.klo = (float)(g.k - (double)g.khi);
         g.inv_eps = (float)(1.0 / p->eps_env);
         g.A = q.A;
         g.lda = q.lda;
         g.ipiv = q.ipiv;
         g.rhs = (const double2 *)q.F0;
         g.X = (double2 *)q.F;
-        hitems[k] = g;
-        if (!gdm_trsv_encode_map(q.A, 3 * p->n, q.lda, hmaps + (size_t)128 * k))
+        g.has_e0 = q.e0 != nullptr;
+        memset(g.e0, 0, sizeof(g.e0));
+        static const double zhat[3] = {0.0, 0.0, 1.0};
+        const double *kh = q.khat ? q.khat : zhat;
+        for (int t = 0; t < 3; t++) g.khat[t] = kh[t];
+        for (int r = 0; r < q.n_rhs; r++) {
+            double e2 = 0.0;
+            if (q.e0) {
+                for (int c = 0; c < 6; c++) {
+                    g.e0[6 * r + c] = q.e0[6 * r + c];
+                    e2 += q.e0[6 * r + c] * q.e0[6 * r + c];
+                }
+            } else if (q.e0_norm2) {
+                e2 = q.e0_norm2[r];
+            }
+            g.pref[r] = e2 > 0 ? 4.0 * PI * g.k / (p->eps_env * e2) : 0.0;
+        }
+        g.has_sigma = q.sigma != nullptr;
+        g.sigma = q.sigma;
+        st.items[k] = g;
+        if (!gdm_trsv_encode_map(q.A, 3 * p->n, q.lda, st.maps + (size_t)128 * k))
             return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the grouped solves");
     }
-    GDM_CUDA_TRY(ctx, cudaMemcpyAsync(R->d_items, hitems, sizeof(GrItem) * n_items, cudaMemcpyHostToDevice,
+    GDM_CUDA_TRY(ctx, cudaMemcpyAsync(R->d_items, st.items, sizeof(GrItem) * n_items, cudaMemcpyHostToDevice,
                                       ctx->stream));
-    GDM_CUDA_TRY(ctx, cudaMemcpyAsync(R->d_maps, hmaps, (size_t)128 * n_items, cudaMemcpyHostToDevice, ctx->stream));
+    GDM_CUDA_TRY(ctx, cudaMemcpyAsync(R->d_maps, st.maps, (size_t)128 * n_items, cudaMemcpyHostToDevice,
+                                      ctx->stream));
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_inputs(gdm_ctx *ctx) {
+    RPlan *R = (RPlan *)ctx->grf;
+    if (!R) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "grouped batch not prepared");
+    const int N = (int)R->n.size();
+    std::vector<int> all(N), stage;
+    for (int k = 0; k < N; k++) all[k] = k;
+    const LaunchLists Lc = add_launch(stage, all, R->h_items, units_cell);
+    const LaunchLists La = add_launch(stage, all, R->h_items, units_asm);
+    GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // the lists' staging buffer is free
+    GDM_TRY(upload_lists(ctx, *R, stage));
+    const int *dl = R->d_lists;
+    GDM_TRY(gdm_gr_planewave(ctx, R->d_items, dl + Lc.list_off, dl + Lc.prefix_off, Lc.na, Lc.units));
+    GDM_TRY(gdm_gr_prep_dipa(ctx, R->d_items, dl + Lc.list_off, dl + Lc.prefix_off, Lc.na, Lc.units));
+    return gdm_gr_assemble(ctx, R->d_items, dl + La.list_off, dl + La.prefix_off, La.na, La.units);
+}
+
+gdm_status gdm_gr_refine(gdm_ctx *ctx, const unsigned char *use, double tol, int max_iter, gdm_solve_info *infos) {
+    RPlan *R = (RPlan *)ctx->grf;
+    if (!R) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "grouped batch not prepared");
+    const int N = (int)R->n.size();
     const std::vector<GrItem> &items = R->h_items;
-    // the lists of a step: staged on the host, one copy per step
+    const Staging sg = staging(*R);
+    std::vector<int> sel;
+    for (int k = 0; k < N; k++)
+        if (use[R->order[k]]) sel.push_back(k);
+    if (sel.empty()) return GDM_OK;
+    GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // the lists' staging buffer is free
     std::vector<int> stage;
-    auto upload = [&]() -> gdm_status {
-        if (stage.size() > R->lists_cap) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "grouped refinement lists");
-        memcpy(hstage, stage.data(), sizeof(int) * stage.size());
-        GDM_CUDA_TRY(ctx, cudaMemcpyAsync(R->d_lists, hstage, sizeof(int) * stage.size(), cudaMemcpyHostToDevice,
-                                          ctx->stream));
-        return GDM_OK;
-    };
     const int *dl = R->d_lists;
     struct Solve {
         int list_off, jp_off, nj, units;
@@ -262,39 +336,29 @@ gdm_status gdm_gr_refine(gdm_ctx *ctx, int n_items, const GrProblem *pb, double 
         }
         return GDM_OK;
     };
-    auto lp = [&](const LaunchLists &L, const int **list, const int **pre) {
-        *list = dl + L.list_off;
-        *pre = dl + L.prefix_off;
-    };
-    const int *li, *pr;
+#define GR_ARGS(L) R->d_items, dl + (L).list_off, dl + (L).prefix_off, (L).na, (L).units
     GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     // set-up and the first solve: X = LU^{-1} F0
-    std::vector<int> all(n_items);
-    for (int k = 0; k < n_items; k++) all[k] = k;
-    GDM_CUDA_TRY(ctx, cudaMemsetAsync(R->d_norms, 0, sizeof(double) * 8 * n_items, ctx->stream));
+    GDM_CUDA_TRY(ctx, cudaMemsetAsync(R->d_norms, 0, sizeof(double) * 8 * N, ctx->stream));
     {
         stage.clear();
-        const LaunchLists Lc = add_launch(stage, all, items, units_cell);
-        const LaunchLists Lo = add_launch(stage, all, items, units_ops);
-        const LaunchLists Le = add_launch(stage, all, items, units_elem);
-        const Solve T = add_solve(all);
-        GDM_TRY(upload());
-        lp(Lc, &li, &pr);
-        GDM_TRY(gdm_gr_prep_dip(ctx, R->d_items, li, pr, Lc.na, Lc.units));
-        lp(Lo, &li, &pr);
-        GDM_TRY(gdm_gr_block_ops(ctx, R->d_items, li, pr, Lo.na, Lo.units));
-        lp(Le, &li, &pr);
-        GDM_TRY(gdm_gr_norm2(ctx, R->d_items, li, pr, Le.na, Le.units));
-        GDM_TRY(gdm_gr_to_work(ctx, R->d_items, li, pr, Le.na, Le.units, 0));
+        const LaunchLists Lc = add_launch(stage, sel, items, units_cell);
+        const LaunchLists Lo = add_launch(stage, sel, items, units_ops);
+        const LaunchLists Le = add_launch(stage, sel, items, units_elem);
+        const Solve T = add_solve(sel);
+        GDM_TRY(upload_lists(ctx, *R, stage));
+        GDM_TRY(gdm_gr_prep_dip(ctx, GR_ARGS(Lc)));
+        GDM_TRY(gdm_gr_block_ops(ctx, GR_ARGS(Lo)));
+        GDM_TRY(gdm_gr_norm2(ctx, GR_ARGS(Le)));
+        GDM_TRY(gdm_gr_to_work(ctx, GR_ARGS(Le), 0));
         GDM_TRY(solve(T));
-        lp(Le, &li, &pr);
-        GDM_TRY(gdm_gr_update(ctx, R->d_items, li, pr, Le.na, Le.units, 0));
+        GDM_TRY(gdm_gr_update(ctx, GR_ARGS(Le), 0));
     }
-    std::vector<double> relc(n_items, 1.0), relr(n_items, -1.0);
-    std::vector<int> done(n_items, 0), iters(n_items, 0), stat(n_items, GDM_OK);
+    std::vector<double> relc(N, 1.0), relr(N, -1.0);
+    std::vector<int> done(N, 0), iters(N, 0), stat(N, GDM_OK);
     for (int it = 1; it <= max_iter; it++) {
         std::vector<int> act, f32, ff;
-        for (int k = 0; k < n_items; k++)
+        for (int k : sel)
             if (!done[k]) {
                 act.push_back(k);
                 // FP32 residuals while the last relative correction is above 1e-3 (as refine.cu)
@@ -302,8 +366,7 @@ gdm_status gdm_gr_refine(gdm_ctx *ctx, int n_items, const GrProblem *pb, double 
             }
         if (act.empty()) break;
         // ||d||, ||X||, ||r|| of every problem start from zero; ||F0|| stays
-        GDM_CUDA_TRY(ctx, cudaMemset2DAsync(R->d_norms, 8 * sizeof(double), 0, 6 * sizeof(double), n_items,
-                                            ctx->stream));
+        GDM_CUDA_TRY(ctx, cudaMemset2DAsync(R->d_norms, 8 * sizeof(double), 0, 6 * sizeof(double), N, ctx->stream));
         stage.clear();
         const LaunchLists Le = add_launch(stage, act, items, units_elem);
         const LaunchLists Lf = add_launch(stage, f32, items, units_green);
@@ -311,27 +374,20 @@ gdm_status gdm_gr_refine(gdm_ctx *ctx, int n_items, const GrProblem *pb, double 
         const LaunchLists Lg = add_launch(stage, ff, items, units_green);
         const LaunchLists Lc = add_launch(stage, act, items, units_cell);
         const Solve T = add_solve(act);
-        GDM_TRY(upload());
-        lp(Le, &li, &pr);
-        GDM_TRY(gdm_gr_moments(ctx, R->d_items, li, pr, Le.na, Le.units));
-        lp(Lf, &li, &pr);
-        GDM_TRY(gdm_gr_green_f32(ctx, R->d_items, li, pr, Lf.na, Lf.units));
-        lp(Ls, &li, &pr);
-        GDM_TRY(gdm_gr_prep_src(ctx, R->d_items, li, pr, Ls.na, Ls.units));
-        lp(Lg, &li, &pr);
-        GDM_TRY(gdm_gr_green_ff(ctx, R->d_items, li, pr, Lg.na, Lg.units, R->d_tab));
-        lp(Lc, &li, &pr);
-        GDM_TRY(gdm_gr_finalize(ctx, R->d_items, li, pr, Lc.na, Lc.units));
-        lp(Le, &li, &pr);
-        GDM_TRY(gdm_gr_to_work(ctx, R->d_items, li, pr, Le.na, Le.units, 1));
+        GDM_TRY(upload_lists(ctx, *R, stage));
+        GDM_TRY(gdm_gr_moments(ctx, GR_ARGS(Le)));
+        GDM_TRY(gdm_gr_green_f32(ctx, GR_ARGS(Lf)));
+        GDM_TRY(gdm_gr_prep_src(ctx, GR_ARGS(Ls)));
+        GDM_TRY(gdm_gr_green_ff(ctx, GR_ARGS(Lg), R->d_tab));
+        GDM_TRY(gdm_gr_finalize(ctx, GR_ARGS(Lc)));
+        GDM_TRY(gdm_gr_to_work(ctx, GR_ARGS(Le), 1));
         GDM_TRY(solve(T));
-        lp(Le, &li, &pr);
-        GDM_TRY(gdm_gr_update(ctx, R->d_items, li, pr, Le.na, Le.units, 1));
-        GDM_CUDA_TRY(ctx, cudaMemcpyAsync(hnorms, R->d_norms, sizeof(double) * 8 * n_items, cudaMemcpyDeviceToHost,
+        GDM_TRY(gdm_gr_update(ctx, GR_ARGS(Le), 1));
+        GDM_CUDA_TRY(ctx, cudaMemcpyAsync(sg.norms, R->d_norms, sizeof(double) * 8 * N, cudaMemcpyDeviceToHost,
                                           ctx->stream));
         GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         for (int k : act) {
-            const double *h = hnorms + 8 * k;
+            const double *h = sg.norms + 8 * k;
             double c = 0.0, rr = 0.0;
             bool finite = true;
             for (int q = 0; q < items[k].nr; q++) {
@@ -351,15 +407,16 @@ gdm_status gdm_gr_refine(gdm_ctx *ctx, int n_items, const GrProblem *pb, double 
             }
         }
     }
+#undef GR_ARGS
     GDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, ctx->stream));
     GDM_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev2));
     // a timed-out wait in a kernel is the whole call's failure
     GDM_TRY(gdm_ctx_check(ctx));
     float ms = 0.f;
     GDM_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev1, ctx->ev2));
-    for (int k = 0; k < n_items; k++) {
+    for (int k : sel) {
         if (!done[k]) stat[k] = GDM_ERR_NOT_CONVERGED;
-        gdm_solve_info &inf = infos[order[k]];
+        gdm_solve_info &inf = infos[R->order[k]];
         inf.iterations = iters[k];
         inf.rel_correction = relc[k];
         inf.rel_residual = relr[k];
@@ -367,4 +424,21 @@ gdm_status gdm_gr_refine(gdm_ctx *ctx, int n_items, const GrProblem *pb, double 
         inf.status = stat[k];
     }
     return GDM_OK;
+}
+
+gdm_status gdm_gr_xsec(gdm_ctx *ctx, const unsigned char *use) {
+    RPlan *R = (RPlan *)ctx->grf;
+    if (!R) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "grouped batch not prepared");
+    const int N = (int)R->n.size();
+    std::vector<int> sel, stage;
+    for (int k = 0; k < N; k++)
+        if (use[R->order[k]] && R->h_items[k].has_sigma) sel.push_back(k);
+    if (sel.empty()) return GDM_OK;
+    const LaunchLists L = add_launch(stage, sel, R->h_items, units_cell);
+    GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // the lists' staging buffer is free
+    GDM_TRY(upload_lists(ctx, *R, stage));
+    GDM_CUDA_TRY(ctx, cudaMemsetAsync(R->h_items[0].xs, 0, sizeof(double) * 4 * N, ctx->stream));
+    const int *dl = R->d_lists;
+    GDM_TRY(gdm_gr_xsec_partial(ctx, R->d_items, dl + L.list_off, dl + L.prefix_off, L.na, L.units));
+    return gdm_gr_xsec_final(ctx, R->d_items, dl + L.list_off, L.na);
 }

@@ -396,7 +396,18 @@ struct GrItem {
     double *norms;              // [2q] ||d_q||^2, [2q + 1] ||X_q||^2, [4 + q] ||r_q||^2, [6 + q] ||rhs_q||^2
     int64_t chunk;              // sources per Green-sum chunk
     int nc;                     // chunks
+    // inputs and observables (batches of cells solved wholly in lock step)
+    double k, n_env;            // host wavenumber and refractive index
+    double e0[12];              // plane-wave amplitudes (x, y, z complex per right-hand side)
+    double khat[3];             // propagation direction
+    int has_e0;                 // 1: F0 is the plane wave (written), 0: F0 is given
+    int has_sigma;
+    void *dipa;                 // FP32 assembly records (positions, alpha, diagonal block)
+    double *sigma;              // 3 x nr cross sections (ext row, sca row, abs row), device, or unused
+    double pref[2];             // 4 pi k / (eps_env |E0_q|^2)
+    double *xs;                 // [2q] sum Im(E0* . p), [2q + 1] sum Im(E* . p)
 };
+#define TRSV_OPS_CTAS 8  // CTAs per 128-row block of the block-operator kernel (both triangles)
 // problem of work unit b of a grouped launch: k with prefix[k] <= b < prefix[k + 1] (whole CTA; uses a warp)
 __device__ __forceinline__ int gr_unit(const int *__restrict__ list, const int *__restrict__ prefix, int na, int b,
                                        int *local) {
@@ -432,15 +443,31 @@ gdm_status gdm_gr_update(gdm_ctx *ctx, const GrItem *it, const int *list, const 
 // GDM_OK, GDM_ERR_NOT_CONVERGED or GDM_ERR_NONFINITE). Returns a failure of the call itself only.
 struct GrProblem {
     const gdm_problem *p;
-    const float2 *A;
+    float2 *A;
     int64_t lda;
     const int32_t *ipiv;
-    const double *F0;
+    double *F0;
     double *F;
     int n_rhs;
+    const double *e0;        // host plane-wave amplitudes (n_rhs x 3 complex), or NULL when F0 is given
+    const double *khat;      // host direction (NULL: +z)
+    const double *e0_norm2;  // host |E0_q|^2 when e0 is NULL (for the cross sections)
+    double *sigma;           // device 3 x n_rhs cross sections, or NULL
 };
-gdm_status gdm_gr_refine(gdm_ctx *ctx, int n_items, const GrProblem *pb, double tol, int max_iter,
-                         gdm_solve_info *infos);
+// gdm_gr_prepare: the table of this call's problems (kept with its scratch while the sizes stay the same);
+// gdm_gr_inputs: plane waves (problems with e0) and the FP32 assembly of every problem of the table;
+// gdm_gr_refine: the refinement of the problems with use[i] != 0 (caller's order; A holds their factors);
+// gdm_gr_xsec: their cross sections (problems with sigma)
+gdm_status gdm_gr_prepare(gdm_ctx *ctx, int n_items, const GrProblem *pb);
+gdm_status gdm_gr_inputs(gdm_ctx *ctx);
+gdm_status gdm_gr_refine(gdm_ctx *ctx, const unsigned char *use, double tol, int max_iter, gdm_solve_info *infos);
+gdm_status gdm_gr_xsec(gdm_ctx *ctx, const unsigned char *use);
+gdm_status gdm_gr_planewave(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units);
+gdm_status gdm_gr_prep_dipa(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units);
+gdm_status gdm_gr_assemble(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units);
+gdm_status gdm_gr_xsec_partial(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na,
+                               int units);
+gdm_status gdm_gr_xsec_final(gdm_ctx *ctx, const GrItem *it, const int *list, int na);
 void gdm_gr_release(gdm_ctx *ctx);
 // host: the TMA descriptor of a problem's factors for the triangular solves (128 bytes into map); false if
 // the encoder refuses

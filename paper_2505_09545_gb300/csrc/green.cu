@@ -547,12 +547,12 @@ __global__ void __launch_bounds__(ASM_TI) k_assemble6(typename cplx<T>::t *__res
 #define ASB_TI 128
 #define ASB_TJ 8
 #define ASB_ROWS (3 * ASB_TI)
-__global__ void __launch_bounds__(ASB_TI) k_assemble3_f32_bulk(float2 *__restrict__ A, int64_t lda, int64_t n,
-                                                              const DipF *__restrict__ dip, float khi, float klo,
-                                                              float inv_eps) {
+__device__ __forceinline__ void assemble3_f32_bulk_body(float2 *__restrict__ A, int64_t lda, int64_t n,
+                                                        const DipF *__restrict__ dip, float khi, float klo,
+                                                        float inv_eps, int64_t bx, int64_t by) {
     extern __shared__ __align__(128) float2 stile[];  // [3 * ASB_TJ columns][ASB_ROWS rows]
     __shared__ DipF sj[ASB_TJ];
-    const int64_t i0 = (int64_t)blockIdx.x * ASB_TI, j0 = (int64_t)blockIdx.y * ASB_TJ;
+    const int64_t i0 = bx * ASB_TI, j0 = by * ASB_TJ;
     if (threadIdx.x < ASB_TJ && j0 + threadIdx.x < n) sj[threadIdx.x] = dip[j0 + threadIdx.x];
     __syncthreads();
     const int64_t i = i0 + threadIdx.x;
@@ -611,6 +611,11 @@ __global__ void __launch_bounds__(ASB_TI) k_assemble3_f32_bulk(float2 *__restric
         // the shared tile must stay until the engine has read it
         asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
+}
+__global__ void __launch_bounds__(ASB_TI) k_assemble3_f32_bulk(float2 *__restrict__ A, int64_t lda, int64_t n,
+                                                              const DipF *__restrict__ dip, float khi, float klo,
+                                                              float inv_eps) {
+    assemble3_f32_bulk_body(A, lda, n, dip, khi, klo, inv_eps, blockIdx.x, blockIdx.y);
 }
 
 // kind 6 (ED/MD dipoles), complex64 output through the bulk-copy engine. Block (AS6_TI targets) x (4 sources),
@@ -1615,5 +1620,152 @@ gdm_status gdm_gr_finalize(gdm_ctx *ctx, const GrItem *it, const int *list, cons
     if (units <= 0) return GDM_OK;
     k_gr_finalize<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na);
     GDM_LAUNCHED(ctx, "gr_finalize");
+    return GDM_OK;
+}
+
+// ================================================================== grouped inputs and cross sections of a batch
+namespace {
+// plane wave E0 = e0 exp(i k khat . r) at every cell of the listed problems that carry amplitudes:
+// ceil(n / 256) CTAs per problem
+__global__ void __launch_bounds__(256) k_gr_planewave(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                      const int *__restrict__ prefix, int na) {
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t c = (int64_t)local * 256 + threadIdx.x;
+    if (!g.has_e0 || c >= g.n) return;
+    const double ph = g.k * (g.khat[0] * g.pos[3 * c] + g.khat[1] * g.pos[3 * c + 1] + g.khat[2] * g.pos[3 * c + 2]);
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    const double2 e = make_double2(cs, sn);
+    const int64_t ld = 3 * g.n;
+    double2 *F0 = (double2 *)g.rhs;  // written here, read by the refinement
+    for (int q = 0; q < g.nr; q++)
+        for (int a = 0; a < 3; a++)
+            F0[q * ld + 3 * c + a] = cmul(make_double2(g.e0[6 * q + 2 * a], g.e0[6 * q + 2 * a + 1]), e);
+}
+
+// FP32 assembly records (positions as FP32 pairs, alpha, 1 - S alpha): ceil(n / 256) CTAs per problem
+__global__ void __launch_bounds__(256) k_gr_prep_dipa(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                      const int *__restrict__ prefix, int na) {
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t c = (int64_t)local * 256 + threadIdx.x;
+    if (c >= g.n) return;
+    DipF d;
+    const double x = g.pos[3 * c], y = g.pos[3 * c + 1], z = g.pos[3 * c + 2];
+    d.xh = (float)x;
+    d.yh = (float)y;
+    d.zh = (float)z;
+    d.xl = (float)(x - (double)d.xh);
+    d.yl = (float)(y - (double)d.yh);
+    d.zl = (float)(z - (double)d.zh);
+    const double2 e = g.eps[c];
+    d.alpha = make_float2((float)((e.x - g.eps_env) * g.d3_4pi), (float)(e.y * g.d3_4pi));
+    d.diag = make_float2((float)(1.0 + (e.x - g.eps_env) / (3.0 * g.eps_env)), (float)(e.y / (3.0 * g.eps_env)));
+    d.pad[0] = d.pad[1] = 0.f;
+    ((DipF *)g.dipa)[c] = d;
+}
+
+// A = I - G alpha in complex64 through the bulk-copy tiles: ceil(n / ASB_TI) x ceil(n / ASB_TJ) CTAs per problem
+__global__ void __launch_bounds__(ASB_TI) k_gr_assemble(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                        const int *__restrict__ prefix, int na) {
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t tb = (g.n + ASB_TI - 1) / ASB_TI;
+    assemble3_f32_bulk_body((float2 *)g.A, g.lda, g.n, (const DipF *)g.dipa, g.khi, g.klo, g.inv_eps, local % tb,
+                            local / tb);
+}
+
+// sum Im(E0* . p) and sum Im(E* . p) per right-hand side into xs (zeroed before): ceil(n / XS_BS) CTAs per problem
+__global__ void __launch_bounds__(XS_BS) k_gr_xsec_partial(const GrItem *__restrict__ items, const int *__restrict__ list,
+                                                           const int *__restrict__ prefix, int na) {
+    __shared__ double red[4][XS_BS / 32];
+    int local;
+    const int i = gr_unit(list, prefix, na, (int)blockIdx.x, &local);
+    const GrItem &g = items[i];
+    const int64_t c = (int64_t)local * XS_BS + threadIdx.x;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    if (c < g.n) {
+        const double2 e = g.eps[c];
+        const double2 al = make_double2((e.x - g.eps_env) * g.d3_4pi, e.y * g.d3_4pi);
+        for (int q = 0; q < g.nr; q++) {
+            const int64_t off = q * 3 * g.n + 3 * c;
+            for (int a = 0; a < 3; a++) {
+                const double2 pm = cmul(al, g.X[off + a]);
+                s[2 * q] += cconjmul(g.rhs[off + a], pm).y;
+                s[2 * q + 1] += cconjmul(g.X[off + a], pm).y;
+            }
+        }
+    }
+    for (int v = 0; v < 4; v++) {
+        double x = s[v];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double x = 0.0;
+        for (int w = 0; w < XS_BS / 32; w++) x += red[threadIdx.x][w];
+        if (threadIdx.x < 2 * g.nr) atomicAdd(&g.xs[threadIdx.x], x);
+    }
+}
+
+// ext, sca, abs of every listed problem with cross sections: one thread per problem
+__global__ void k_gr_xsec_final(const GrItem *__restrict__ items, const int *__restrict__ list, int na) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    const GrItem &g = items[list[k]];
+    if (!g.has_sigma) return;
+    for (int q = 0; q < g.nr; q++) {
+        const double e = g.pref[q] * g.xs[2 * q], ab = g.pref[q] * g.xs[2 * q + 1];
+        g.sigma[q] = e;
+        g.sigma[g.nr + q] = e - ab;
+        g.sigma[2 * g.nr + q] = ab;
+    }
+}
+}  // namespace
+
+gdm_status gdm_gr_planewave(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units) {
+    if (units <= 0) return GDM_OK;
+    k_gr_planewave<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_planewave");
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_prep_dipa(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units) {
+    if (units <= 0) return GDM_OK;
+    k_gr_prep_dipa<<<(unsigned)units, 256, 0, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_prep_dipa");
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_assemble(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na, int units) {
+    if (units <= 0) return GDM_OK;
+    const int smem = 3 * ASB_TJ * ASB_ROWS * (int)sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_gr_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+    }
+    k_gr_assemble<<<(unsigned)units, ASB_TI, smem, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_assemble");
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_xsec_partial(gdm_ctx *ctx, const GrItem *it, const int *list, const int *prefix, int na,
+                               int units) {
+    if (units <= 0) return GDM_OK;
+    k_gr_xsec_partial<<<(unsigned)units, XS_BS, 0, ctx->stream>>>(it, list, prefix, na);
+    GDM_LAUNCHED(ctx, "gr_xsec_partial");
+    return GDM_OK;
+}
+
+gdm_status gdm_gr_xsec_final(gdm_ctx *ctx, const GrItem *it, const int *list, int na) {
+    if (na <= 0) return GDM_OK;
+    k_gr_xsec_final<<<(unsigned)((na + 127) / 128), 128, 0, ctx->stream>>>(it, list, na);
+    GDM_LAUNCHED(ctx, "gr_xsec_final");
     return GDM_OK;
 }
