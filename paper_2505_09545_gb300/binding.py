@@ -400,47 +400,66 @@ def cross_sections_noalloc(ctx: Context, prob: GDMProblem, F0, F, e0_norm2, out)
 def solve_batched(ctx: Context, probs, e0s, precision="tf32", khat=(0.0, 0.0, 1.0), n_streams=0, with_sigma=True,
                   max_iter=0, tol=0.0, return_factors=False):
     """gdm_solve_batched over independent problems: probs is a list of GDMProblem, e0s a list of (n_rhs, 3)
-    complex plane-wave amplitudes (one per problem). Allocates each item's matrix, pivots, fields and
-    cross sections; returns (F list of (n_rhs, kind*n) complex128, sigma list of (3, n_rhs) or None,
-    info list of dicts)."""
+    complex plane-wave amplitudes (one per problem). Allocates the items' matrices, pivots, fields and
+    cross sections (one device buffer of each kind, sliced per item); returns (F list of (n_rhs, kind*n)
+    complex128, sigma list of (3, n_rhs) or None, info list of dicts)."""
     prec = PRECISION[precision]
     n = len(probs)
     items = (BatchItem * n)()
-    keep = []
-    Fs, sigs, As, ipivs = [], [], [], []
+    e0l = [np.atleast_2d(np.asarray(e0, np.complex128)) for e0 in e0s]
+    nrhs = [e.shape[0] for e in e0l]
+    sizes = [pb.size for pb in probs]
+    ldas = [padded_lda(ns) for ns in sizes]
+    dev = probs[0].pos.device if n else torch.device("cuda")
+    cdt = torch.complex128 if precision == "fp64" else torch.complex64
+
+    def offsets(counts, align):
+        off, acc = [], 0
+        for c in counts:
+            off.append(acc)
+            acc += (c + align - 1) // align * align
+        return off, max(acc, 1)
+
+    # element offsets aligned to 256 bytes (32 complex64, 16 complex128 elements)
+    a_off, a_tot = offsets([ns * lda for ns, lda in zip(sizes, ldas)], 32)
+    p_off, p_tot = offsets(sizes, 64)
+    f_off, f_tot = offsets([r * ns for r, ns in zip(nrhs, sizes)], 16)
+    s_off, s_tot = offsets([3 * r for r in nrhs], 32)
+    Abuf = torch.empty(a_tot, dtype=cdt, device=dev)
+    Pbuf = torch.empty(p_tot, dtype=torch.int32, device=dev)
+    F0buf = torch.empty(f_tot, dtype=torch.complex128, device=dev)
+    Fbuf = torch.empty(f_tot, dtype=torch.complex128, device=dev)
+    Sbuf = torch.empty(s_tot, dtype=torch.float64, device=dev) if with_sigma else None
+    e0all = np.ascontiguousarray(np.concatenate([e.reshape(-1) for e in e0l]).view(np.float64)) if n else None
+    e0_off = np.cumsum([0] + [6 * r for r in nrhs])
     ka, kp = _dbl_array(khat)
-    keep.append(ka)
-    for i, (pb, e0) in enumerate(zip(probs, e0s)):
-        e0 = np.atleast_2d(np.asarray(e0, np.complex128))
-        n_rhs = e0.shape[0]
-        ns = pb.size
-        lda = padded_lda(ns)
-        dev = pb.pos.device
-        A = torch.empty((ns, lda), dtype=torch.complex128 if precision == "fp64" else torch.complex64, device=dev)
-        ipiv = torch.empty(ns, dtype=torch.int32, device=dev)
-        F0 = torch.empty((n_rhs, ns), dtype=torch.complex128, device=dev)
-        F = torch.empty_like(F0)
-        sig = torch.empty((3, n_rhs), dtype=torch.float64, device=dev) if with_sigma else None
-        ea, ep = _dbl_array(e0.view(np.float64).reshape(-1))
-        keep += [A, ipiv, F0, ea]
+    keep = [Abuf, Pbuf, F0buf, Fbuf, Sbuf, e0all, ka]
+    Fs, sigs, As, ipivs = [], [], [], []
+    a_ptr, p_ptr, f0_ptr, f_ptr = Abuf.data_ptr(), Pbuf.data_ptr(), F0buf.data_ptr(), Fbuf.data_ptr()
+    e_ptr = e0all.ctypes.data if n else 0
+    for i, pb in enumerate(probs):
+        ns, lda, r = sizes[i], ldas[i], nrhs[i]
         it = items[i]
         it.prob = pb.struct()
-        it.A, it.lda, it.ipiv = A.data_ptr(), lda, ipiv.data_ptr()
-        it.F0, it.F = F0.data_ptr(), F.data_ptr()
-        it.sigma = sig.data_ptr() if sig is not None else 0
-        it.e0 = ea.ctypes.data
+        it.A, it.lda = a_ptr + a_off[i] * Abuf.element_size(), lda
+        it.ipiv = p_ptr + p_off[i] * 4
+        it.F0, it.F = f0_ptr + f_off[i] * 16, f_ptr + f_off[i] * 16
+        it.sigma = Sbuf.data_ptr() + s_off[i] * 8 if with_sigma else 0
+        it.e0 = e_ptr + int(e0_off[i]) * 8
         it.khat = ka.ctypes.data
         it.e0_norm2 = 0
-        it.n_rhs = n_rhs
-        Fs.append(F)
-        sigs.append(sig)
-        As.append(A)
-        ipivs.append(ipiv)
+        it.n_rhs = r
+        Fs.append(Fbuf[f_off[i]:f_off[i] + r * ns].view(r, ns))
+        sigs.append(Sbuf[s_off[i]:s_off[i] + 3 * r].view(3, r) if with_sigma else None)
+        if return_factors:
+            As.append(Abuf[a_off[i]:a_off[i] + ns * lda].view(ns, lda))
+            ipivs.append(Pbuf[p_off[i]:p_off[i] + ns])
     opts = SolveOpts(int(max_iter), 0, float(tol))
     infos = (SolveInfo * n)()
     ctx._sync_stream()
     ctx._check(lib().gdm_solve_batched(ctx.h, prec, items, n, C.byref(opts), int(n_streams), infos),
                "gdm_solve_batched")
+    del keep
     out = (Fs, sigs, [infos[i].as_dict() for i in range(n)])
     return out + (As, ipivs) if return_factors else out
 

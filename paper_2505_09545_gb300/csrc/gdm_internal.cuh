@@ -407,7 +407,7 @@ struct GrItem {
     double pref[2];             // 4 pi k / (eps_env |E0_q|^2)
     double *xs;                 // [2q] sum Im(E0* . p), [2q + 1] sum Im(E* . p)
 };
-#define TRSV_OPS_CTAS 8  // CTAs per 128-row block of the block-operator kernel (both triangles)
+#define TRSV_OPS_CTAS 4  // CTAs per 128-row block of the block-operator kernel (both triangles)
 // problem of work unit b of a grouped launch: k with prefix[k] <= b < prefix[k + 1] (whole CTA; uses a warp)
 __device__ __forceinline__ int gr_unit(const int *__restrict__ list, const int *__restrict__ prefix, int na, int b,
                                        int *local) {

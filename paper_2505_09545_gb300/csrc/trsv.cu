@@ -54,12 +54,12 @@ template <class C> __device__ __forceinline__ C cz() {
 // Per (row block j, triangle) the explicit operator of the block's diagonal part: M_j = L_S^{-1} P_S ...
 // L_1^{-1} P_1 (the block's 32-row panels, pivots inside each panel) or Ui_j = U_jj^{-1}, applied to the
 // columns of I and stored column-major (coalesced for y = X acc) and row-major (for y = X^H acc).
-// A warp solves four columns of X (lane = row within each 32-row group, 4 groups in registers); a CTA of 8
-// warps covers 32 columns, so that a triangle takes 4 CTAs. The block's factor columns are staged in shared
+// A warp solves eight columns of X side by side (lane = row within each 32-row group, 4 groups in registers);
+// a CTA of 8 warps covers 64 columns, so that a triangle takes 2 CTAs. The block's factor columns are staged in shared
 // memory one 32-column panel at a time: L forward (interchanges of the panel across lanes, then unit lower
 // substitution into its own and the later row groups), U backward (division by the diagonal, then the
 // column's multiple subtracted from the rows above).
-constexpr int OPS_CPW = 4;  // columns per warp
+constexpr int OPS_CPW = 8;  // columns per warp
 static_assert(2 * TRSV_NBS_F32 / (8 * OPS_CPW) == TRSV_OPS_CTAS, "CTAs per row block of the operators");
 __device__ __forceinline__ void block_ops_body(const float2 *__restrict__ A, int64_t lda, int64_t n,
                                                const int32_t *__restrict__ ipiv, float2 *__restrict__ ops, int bid) {
