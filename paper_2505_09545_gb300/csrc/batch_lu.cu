@@ -4,8 +4,9 @@
 // launches per problem.
 //
 // Per outer block [b0, b0 + nbo) and per 32-column panel c0 inside it:
-//   k_glu_panel       the panel of every problem with n > c0 (pivots, certificate, L, and the TF32
-//                     embedding of L that the updates read),
+//   k_glu_diag        the panel's 32 x 32 diagonal block of every problem with n > c0 (one warp each:
+//                     pivots, the factored block, U and reciprocal pivots for the rows),
+//   k_glu_rows        the rows below it (certificate, L, and the TF32 embedding of L that the updates read),
 //   k_glu_swap_trsm   the panel's interchanges and L11^{-1} on its rows right of the panel (U, rounded to
 //                     TF32),
 //   k_glu_gemm        C -= L U with K = 32 on the block's columns right of the panel and the block's rows
@@ -27,7 +28,7 @@
 
 namespace {
 
-enum { L_PANEL = 0, L_SWAP = 1, L_GEMM_PANEL = 2, L_GEMM_TRAIL = 3 };
+enum { L_PANEL = 0, L_SWAP = 1, L_GEMM_PANEL = 2, L_GEMM_TRAIL = 3, L_DIAG = 4 };
 struct Launch {
     int type;
     int64_t b0, c0;
@@ -52,6 +53,8 @@ struct Plan {
     unsigned *d_growth = nullptr;
     int *d_status = nullptr;
     int *d_ticket = nullptr;
+    char *d_pdiag = nullptr;  // one GluPanelDiag record per problem
+    size_t pdiag_stride = 0;
     std::vector<size_t> lx_off;
     // host copies of the table (pinned staging for the uploads)
     GluItem *h_items = nullptr;
@@ -72,9 +75,8 @@ struct Plan {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// the lock-step schedule of sizes n_sorted (decreasing) with outer block nbo; panel CTAs sized so that a
-// launch fills about one wave of the panel kernel's resident CTAs (three per SM), each CTA repeating the
-// factorisation of its diagonal block only once
+// the lock-step schedule of sizes n_sorted (decreasing) with outer block nbo; the CTAs of a panel's rows
+// sized so that a launch fills about one wave of the rows kernel's resident CTAs (four per SM)
 void build_schedule(Plan &P, const std::vector<int64_t> &ns, int nbo, int sm_count) {
     const int N = (int)ns.size();
     const int64_t nmax = ns[0];
@@ -92,7 +94,7 @@ void build_schedule(Plan &P, const std::vector<int64_t> &ns, int nbo, int sm_cou
         P.prefix.push_back(acc);
         P.launches.push_back(L);
     };
-    const int64_t target_ctas = 3 * (int64_t)sm_count;
+    const int64_t target_ctas = 4 * (int64_t)sm_count;
     for (int64_t b0 = 0; b0 < nmax; b0 += nbo) {
         for (int64_t c0 = b0; c0 < b0 + nbo && c0 < nmax; c0 += 32) {
             int na = 0;
@@ -109,7 +111,9 @@ void build_schedule(Plan &P, const std::vector<int64_t> &ns, int nbo, int sm_cou
             }
             int64_t R = (rows_total + target_ctas - 1) / target_ctas;
             R = std::max<int64_t>(128, (R + 127) / 128 * 128);
-            for (int i = 0; i < na; i++) cnt[i] = (int)std::max<int64_t>(1, (rows[i] + R - 1) / R);
+            // the diagonal blocks (one warp per problem), then the rows below
+            P.launches.push_back(Launch{L_DIAG, b0, c0, na, 0, na});
+            for (int i = 0; i < na; i++) cnt[i] = (int)((rows[i] + R - 1) / R);
             add(L_PANEL, b0, c0, na, cnt);
             // interchanges and U rows right of full panels
             for (int i = 0; i < na; i++) {
@@ -144,6 +148,9 @@ gdm_status alloc_plan(gdm_ctx *ctx, Plan &P, const std::vector<int64_t> &ns) {
     off = align_up(off + sizeof(int) * 2 * N, 256);
     const size_t o_ticket = off;
     off = align_up(off + sizeof(int) * N, 256);
+    const size_t o_pdiag = off;
+    const size_t pdiag = align_up(gdm_glu_pdiag_bytes(), 256);
+    off += pdiag * N;
     GDM_CUDA_TRY(ctx, cudaMalloc((void **)&P.dmem, off));
     P.d_items = (GluItem *)(P.dmem + o_items);
     P.d_maps = (GluMaps *)(P.dmem + o_maps);
@@ -151,6 +158,8 @@ gdm_status alloc_plan(gdm_ctx *ctx, Plan &P, const std::vector<int64_t> &ns) {
     P.d_growth = (unsigned *)(P.dmem + o_growth);
     P.d_status = (int *)(P.dmem + o_status);
     P.d_ticket = (int *)(P.dmem + o_ticket);
+    P.d_pdiag = P.dmem + o_pdiag;
+    P.pdiag_stride = pdiag;
     // L embeddings: (2n) x (2 nbo) floats per problem
     size_t lx = 0;
     P.lx_off.resize(N);
@@ -182,7 +191,8 @@ gdm_status issue(gdm_ctx *ctx, Plan &P) {
     for (const Launch &L : P.launches) {
         const int *pre = P.d_prefix + L.off;
         switch (L.type) {
-        case L_PANEL: GDM_TRY(gdm_glu_panel(ctx, P.d_items, pre, L.na, L.count, L.b0, L.c0, P.nbo)); break;
+        case L_DIAG: GDM_TRY(gdm_glu_diag(ctx, P.d_items, L.na, L.b0, L.c0, P.nbo)); break;
+        case L_PANEL: GDM_TRY(gdm_glu_rows(ctx, P.d_items, pre, L.na, L.count, L.b0, L.c0, P.nbo)); break;
         case L_SWAP: GDM_TRY(gdm_glu_swap_trsm(ctx, P.d_items, pre, L.na, L.count, L.c0)); break;
         case L_GEMM_PANEL:
             GDM_TRY(gdm_glu_gemm(ctx, P.d_items, P.d_maps, pre, L.na, L.count, GLU_PANEL, L.b0, L.c0, P.nbo));
@@ -247,6 +257,7 @@ gdm_status gdm_glu_factor(gdm_ctx *ctx, int n_items, float2 *const *A, const int
         g.status = P->d_status + 2 * k;
         g.ticket = P->d_ticket + k;
         g.lx = P->dlx + P->lx_off[k] / sizeof(float);
+        g.pdiag = P->d_pdiag + P->pdiag_stride * k;
         if (changed || memcmp(&g, &P->h_items[k], sizeof(g)) != 0) {
             changed = true;
             P->h_items[k] = g;

@@ -270,6 +270,7 @@ struct GluItem {
     int *ticket;       // finish counter of the panel kernels
     float *lx;         // TF32 embedding of the current outer block's L (rows from the block's first row on):
                        // real rows 2 (r - b0) and 2 (r - b0) + 1 of 2 nbo floats each
+    void *pdiag;       // the current panel's factored diagonal block (U, reciprocal pivots) for its rows
 };
 struct alignas(64) GluMap {  // an encoded TMA descriptor (CUtensorMap)
     unsigned char bytes[128];
@@ -362,6 +363,10 @@ gdm_status gdm_glu_gemm(gdm_ctx *ctx, const GluItem *items, const GluMaps *maps,
                         int ntiles, int kind, int64_t b0, int64_t c0, int nbo);
 gdm_status gdm_glu_gemm_init(gdm_ctx *ctx);
 gdm_status gdm_glu_panel_init(gdm_ctx *ctx);
+gdm_status gdm_glu_diag(gdm_ctx *ctx, const GluItem *items, int na, int64_t b0, int64_t c0, int nbo);
+gdm_status gdm_glu_rows(gdm_ctx *ctx, const GluItem *items, const int *prefix, int na, int nblocks, int64_t b0,
+                        int64_t c0, int nbo);
+size_t gdm_glu_pdiag_bytes();
 // encodes the tensor maps of every problem (host); false if the driver's encoder is unavailable or refuses
 bool gdm_glu_encode(const GluItem *items, int n_items, int nbo, GluMaps *maps);
 // the grouped factorisation of a batch (batch_lu.cu) and the release of its cached schedule

@@ -599,6 +599,137 @@ __global__ void __launch_bounds__(128) k_glu_panel(const GluItem *__restrict__ i
 }
 constexpr int GLU_PANEL_SMEM = 128 * (NBP + 1) * (int)sizeof(float2);
 
+// The grouped panel in two launches, so that the diagonal block of a panel is factored once per problem
+// instead of once per CTA: k_glu_diag (one warp per problem) factors it (pivots, certificate base, the
+// factored block stored to A) and leaves U in position order (zero-padded to 64 columns) with the
+// reciprocal pivots in the problem's GluPanelDiag record; k_glu_rows then solves the rows below in every
+// CTA from that record, with no serial prefix.
+struct GluPanelDiag {
+    float2 Uz[NBP][2 * NBP];
+    float2 invd[NBP];
+    float inv_pa[NBP];
+};
+__global__ void __launch_bounds__(32) k_glu_diag(const GluItem *__restrict__ items, int64_t b0, int64_t c0, int nbo) {
+    __shared__ float2 Uz[NBP][2 * NBP];
+    __shared__ float2 Lr[NBP][NBP + 1];
+    const int lane = threadIdx.x;
+    const GluItem g = items[blockIdx.x];
+    const int64_t be = min(b0 + nbo, g.n);
+    const int w = (int)min((int64_t)NBP, be - c0);
+    float2 *__restrict__ A = g.A;
+    const int64_t lda = g.lda;
+    for (int e = lane; e < NBP * 2 * NBP; e += 32) (&Uz[0][0])[e] = make_float2(0.f, 0.f);
+    float2 r[NBP];
+#pragma unroll
+    for (int c = 0; c < NBP; c++) {
+        r[c] = make_float2(0.f, 0.f);
+        if (c < w && lane < w) r[c] = A[(c0 + c) * lda + c0 + lane];
+    }
+    __syncwarp();
+    int pos = lane;
+    bool done = lane >= w;
+    const unsigned vb0 = done ? 0u : __float_as_uint(fabsf(r[0].x) + fabsf(r[0].y));
+    unsigned m = __reduce_max_sync(0xffffffffu, vb0);
+    unsigned key = __reduce_min_sync(0xffffffffu, (!done && vb0 == m) ? (unsigned)pos : 0xffffffffu);
+    int t = 0;
+#pragma unroll 1
+    for (; t < w && t < 8; t++) diag_step<32>(r, t, lane, pos, done, m, key, Uz, Lr, c0, g.ipiv, g.status, true);
+#pragma unroll 1
+    for (; t < w && t < 16; t++) diag_step<24>(r, t, lane, pos, done, m, key, Uz, Lr, c0, g.ipiv, g.status, true);
+#pragma unroll 1
+    for (; t < w && t < 24; t++) diag_step<16>(r, t, lane, pos, done, m, key, Uz, Lr, c0, g.ipiv, g.status, true);
+#pragma unroll 1
+    for (; t < w; t++) diag_step<8>(r, t, lane, pos, done, m, key, Uz, Lr, c0, g.ipiv, g.status, true);
+    __syncwarp();
+    GluPanelDiag *pd = (GluPanelDiag *)g.pdiag;
+    if (lane < w) {
+        const float2 d = Uz[lane][lane];
+        const float pa = fabsf(d.x) + fabsf(d.y);
+        pd->invd[lane] = pa > 0.f ? crecip(d) : make_float2(0.f, 0.f);
+        pd->inv_pa[lane] = pa > 0.f ? 1.0f / pa : 0.f;
+        // this lane's row of the factored block sits at its final position pos: multipliers left of it, U
+        // from it on
+        for (int c = 0; c < w; c++) A[(c0 + c) * lda + c0 + pos] = c < pos ? Lr[lane][c] : Uz[pos][c];
+    } else {
+        pd->invd[lane] = make_float2(0.f, 0.f);
+        pd->inv_pa[lane] = 0.f;
+    }
+    for (int e = lane; e < NBP * 2 * NBP; e += 32) (&pd->Uz[0][0])[e] = (&Uz[0][0])[e];
+}
+
+// rows below the panel of every problem from its GluPanelDiag record: CTA b works for the problem whose
+// range of the prefix sum holds b (the rows of a problem are split over its CTAs in rounds of 128)
+__global__ void __launch_bounds__(128) k_glu_rows(const GluItem *__restrict__ items, const int *__restrict__ prefix,
+                                                  int na, int64_t b0, int64_t c0, int nbo) {
+    extern __shared__ float2 glu_ls2[];  // 128 x (NBP + 1) multipliers of a round of rows
+    float2(*Ls)[NBP + 1] = (float2(*)[NBP + 1])glu_ls2;
+    __shared__ float2 Uz[NBP][2 * NBP];
+    __shared__ float2 invd[NBP];
+    __shared__ float inv_pa[NBP];
+    __shared__ int s_item;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        const int i = glu_find_item(prefix, na, (int)blockIdx.x);
+        if (tid == 0) s_item = i;
+    }
+    __syncthreads();
+    const int ii = s_item;
+    const GluItem g = items[ii];
+    const int bid = (int)blockIdx.x - prefix[ii], nblk = prefix[ii + 1] - prefix[ii];
+    const int64_t be = min(b0 + nbo, g.n), n = g.n, lda = g.lda;
+    const int w = (int)min((int64_t)NBP, be - c0);
+    float2 *__restrict__ A = g.A;
+    const GluPanelDiag *pd = (const GluPanelDiag *)g.pdiag;
+    for (int e = tid; e < NBP * 2 * NBP; e += blockDim.x) (&Uz[0][0])[e] = (&pd->Uz[0][0])[e];
+    if (tid < NBP) {
+        invd[tid] = pd->invd[tid];
+        inv_pa[tid] = pd->inv_pa[tid];
+    }
+    __syncthreads();
+    const int lx_col = (int)(2 * (c0 - b0)), lx_pitch = 2 * nbo;
+    const int64_t r_step = (int64_t)nblk * blockDim.x;
+    float worst = 0.f;
+    float2 x[NBP];
+    for (int64_t rb = c0 + w + bid * (int64_t)blockDim.x; rb < n; rb += r_step) {
+        const int64_t r = rb + tid;
+        if (r < n) {
+#pragma unroll
+            for (int c = 0; c < NBP; c++) x[c] = (c < w) ? A[(c0 + c) * lda + r] : make_float2(0.f, 0.f);
+            int k = 0;
+#define ROWS_PHASE(W_, KEND)                                                                       \
+    for (; k < w && k < (KEND); k++) {                                                             \
+        worst = fmaxf(worst, (fabsf(x[0].x) + fabsf(x[0].y)) * inv_pa[k]);                         \
+        const float2 l_ = subst_step<W_>(x, &Uz[k][k], invd[k]);                                   \
+        A[(c0 + k) * lda + r] = l_;                                                                \
+        Ls[tid][k] = l_;                                                                           \
+    }
+#pragma unroll 1
+            ROWS_PHASE(32, 8)
+#pragma unroll 1
+            ROWS_PHASE(24, 16)
+#pragma unroll 1
+            ROWS_PHASE(16, 24)
+#pragma unroll 1
+            ROWS_PHASE(8, 32)
+#undef ROWS_PHASE
+        }
+        __syncthreads();
+        if (w == NBP) {
+            const int nrow = (int)min((int64_t)blockDim.x, n - rb);
+            for (int e = tid; e < nrow * 32; e += blockDim.x) {
+                const int i = e >> 5, h = (e >> 4) & 1, q = e & 15;
+                const float2 a = Ls[i][2 * q], b = Ls[i][2 * q + 1];
+                const float4 v = h ? make_float4(tf32_rna(a.y), tf32_rna(a.x), tf32_rna(b.y), tf32_rna(b.x))
+                                   : make_float4(tf32_rna(a.x), tf32_rna(-a.y), tf32_rna(b.x), tf32_rna(-b.y));
+                *(float4 *)(g.lx + (2 * (rb + i - b0) + h) * (int64_t)lx_pitch + lx_col + 4 * q) = v;
+            }
+        }
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_down_sync(0xffffffffu, worst, o));
+    if (lane == 0 && worst > 0.f) atomicMax(g.growth, __float_as_uint(worst));
+}
+
 // ------------------------------------------------------------------ block operator for the U12 row block
 // For the outer block [b0, b0+nb) (nb a multiple of 32, pivots of each 32-row panel inside that panel),
 // form negM = -(L_S^{-1} P_S ... L_1^{-1} P_1) restricted to the block's rows: the product form the
@@ -891,8 +1022,28 @@ gdm_status gdm_glu_panel_init(gdm_ctx *ctx) {
     if (!attr) {
         GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_glu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                GLU_PANEL_SMEM));
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_glu_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               GLU_PANEL_SMEM));
         attr = true;
     }
+    return GDM_OK;
+}
+
+size_t gdm_glu_pdiag_bytes() { return sizeof(GluPanelDiag); }
+
+gdm_status gdm_glu_diag(gdm_ctx *ctx, const GluItem *items, int na, int64_t b0, int64_t c0, int nbo) {
+    if (na <= 0) return GDM_OK;
+    k_glu_diag<<<(unsigned)na, 32, 0, ctx->stream>>>(items, b0, c0, nbo);
+    GDM_LAUNCHED(ctx, "glu_diag");
+    return GDM_OK;
+}
+
+gdm_status gdm_glu_rows(gdm_ctx *ctx, const GluItem *items, const int *prefix, int na, int nblocks, int64_t b0,
+                        int64_t c0, int nbo) {
+    if (nblocks <= 0) return GDM_OK;
+    GDM_TRY(gdm_glu_panel_init(ctx));
+    k_glu_rows<<<(unsigned)nblocks, 128, GLU_PANEL_SMEM, ctx->stream>>>(items, prefix, na, b0, c0, nbo);
+    GDM_LAUNCHED(ctx, "glu_rows");
     return GDM_OK;
 }
 
