@@ -469,17 +469,20 @@ __device__ __forceinline__ void tmap_acquire(const void *map) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)map) : "memory");
 }
 
-// stages of operands and C chunk buffers: the K = 32 updates (two K chunks per tile) mostly stream C and keep
-// eight C chunks in flight; the K = nbo updates split the room between three operand stages and four C chunks
-template <int ST, int NC> struct GCfg {
-    static constexpr int STAGES = ST, NCB = NC, LOOK = NC / 2;
+// stages of operands, C chunk buffers and C chunks loaded ahead: the K = 32 updates (two K chunks per tile)
+// mostly stream C and keep four of eight C buffers loading; the K = nbo updates split the room between three
+// operand stages and four C buffers, two of them loading (deeper look-ahead, six of eight and three of five,
+// measured no faster)
+template <int ST, int NC, int LK> struct GCfg {
+    static constexpr int STAGES = ST, NCB = NC, LOOK = LK;  // LOOK C chunks loaded ahead, LOOK < NCB
+    static_assert(LK >= 1 && LK < NC, "C look-ahead");
     static constexpr int A_BYTES = BM * BK * 4, B_BYTES = 256 * BK * 4, STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int CB_BYTES = BM * 32 * 4, TMEM_COLS = 512;
     static constexpr int SMEM = ST * STAGE_BYTES + NC * CB_BYTES + 1024 + 512;
     static __device__ __forceinline__ uint32_t idesc_n(int n_cols) { return Cfg<256, 1>::idesc_n(n_cols); }
 };
-using GCfgPanel = GCfg<2, 8>;
-using GCfgTrail = GCfg<3, 4>;
+using GCfgPanel = GCfg<2, 8, 4>;
+using GCfgTrail = GCfg<3, 4, 2>;
 
 template <class CF>
 __global__ void __launch_bounds__(NTHREADS, 1)
