@@ -16,6 +16,7 @@
 // For the FP32 precisions the trailing update A22 -= A21 U12 runs on the tcgen05 tensor cores
 // (lu_tc.cu); everything else uses the SIMT kernels of this file.
 #include <cooperative_groups.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdlib.h>
 
 #include "gdm_internal.cuh"
@@ -33,6 +34,9 @@ gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_
                              int u_is_tf32);
 gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t r0, int64_t c0,
                          int64_t k0, int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof);
+gdm_status gdm_tc_update_lx(gdm_ctx *ctx, float2 *C, int64_t ldc, int64_t r0, int64_t c0, const float *Lx,
+                            int64_t lx_pitch, const float2 *U, int64_t ldu, int64_t u_r0, int64_t u_c0, int64_t Mc,
+                            int64_t Nc, int64_t Kc, int prof);
 
 // ------------------------------------------------------------------ bounded grid barrier
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -576,6 +580,16 @@ __global__ void __launch_bounds__(128) k_panel_local_f32(float2 *__restrict__ A,
     panel_f32_body<false>(A, lda, n, c0, w, ipiv, growth, &flags[GDM_FLAG_PANEL_TICKET], flags, blockIdx.x,
                           gridDim.x, nullptr, 0, 0, 0, nullptr);
 }
+// the same, also writing the TF32 embedding of the multipliers into Lx (rows relative to b0, pitch lx_pitch
+// floats) for the updates of the recursive factorisation
+__global__ void __launch_bounds__(128) k_panel_local_f32_lx(float2 *__restrict__ A, int64_t lda, int64_t n,
+                                                            int64_t c0, int w, int32_t *__restrict__ ipiv,
+                                                            unsigned *growth, int *flags, float *__restrict__ Lx,
+                                                            int64_t b0, int lx_pitch) {
+    extern __shared__ float2 pl_ls[];  // 128 x (NBP + 1) multipliers of a round of rows
+    panel_f32_body<true>(A, lda, n, c0, w, ipiv, growth, &flags[GDM_FLAG_PANEL_TICKET], flags, blockIdx.x,
+                         gridDim.x, Lx, b0, (int)(2 * (c0 - b0)), lx_pitch, (float2(*)[NBP + 1])pl_ls);
+}
 
 // Grouped panel of a batch (lock-step over the problems of a decreasing-size table): CTA b works for the
 // problem whose CTA range [prefix[i], prefix[i+1]) holds b, on its panel [c0, c0 + w) of the outer block
@@ -807,7 +821,8 @@ __global__ void __launch_bounds__(512) k_block_linv(const float2 *__restrict__ A
 // U = L_S^{-1} P_S ... L_1^{-1} P_1 A (the product form of the left part's panels). CTA b takes 8 columns
 // into shared memory and applies the panels in order, as k_block_linv does for the identity.
 __global__ void __launch_bounds__(512) k_panels_apply(float2 *__restrict__ A, int64_t lda, int64_t lo, int nr,
-                                                      int64_t col0, int ncols, const int32_t *__restrict__ ipiv) {
+                                                      int64_t col0, int ncols, const int32_t *__restrict__ ipiv,
+                                                      int round_tf32) {
     extern __shared__ __align__(16) float2 X[];  // X[c * nr + r], 8 columns
     __shared__ float2 Lpp[32][33];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -863,7 +878,20 @@ __global__ void __launch_bounds__(512) k_panels_apply(float2 *__restrict__ A, in
     }
     for (int e = tid; e < 8 * nr; e += blockDim.x) {
         const int c = e / nr, r = e % nr;
-        if (c < nc) A[(col0 + c_first + c) * lda + lo + r] = X[e];
+        if (c < nc) A[(col0 + c_first + c) * lda + lo + r] =
+            round_tf32 ? make_float2(tf32_rna(X[e].x), tf32_rna(X[e].y)) : X[e];
+    }
+}
+
+// A[r0 + i, c0 + c] rounded to TF32 (nearest) in place, i < nr, c < nc: U12 once its GEMM is done, so that
+// the trailing update reads it straight from storage
+__global__ void k_round_tf32_block(float2 *__restrict__ A, int64_t lda, int64_t r0, int nr, int64_t c0, int64_t nc) {
+    const int64_t total = (int64_t)nr * nc;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / nr, i = e % nr;
+        float2 *a = A + (c0 + c) * lda + r0 + i;
+        const float2 v = *a;
+        *a = make_float2(tf32_rna(v.x), tf32_rna(v.y));
     }
 }
 
@@ -1228,14 +1256,34 @@ static gdm_status update(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t lda, in
     return s;
 }
 
+// the TF32 embedding of the current outer block's L that the recursive factorisation's updates read (rows
+// from b0, pitch floats per real row); Lx == nullptr: the updates prepare their operands themselves
+struct LxBuf {
+    float *Lx = nullptr;
+    int64_t b0 = 0;
+    int pitch = 0;
+};
+
 template <class C>
 static gdm_status panel_local(gdm_ctx *ctx, C *A, int64_t lda, int64_t n, int64_t c0, int w, int32_t *ipiv,
-                              unsigned *growth) {
+                              unsigned *growth, const LxBuf &lx = LxBuf()) {
     int64_t below = n - c0 - w;
     if (sizeof(C) == 8 && !getenv("GDM_PANEL_SMEM")) {
         int blocks = (int)((below + 127) / 128);
         if (blocks < 1) blocks = 1;
         if (blocks > 4 * ctx->sm_count) blocks = 4 * ctx->sm_count;
+        if (lx.Lx) {
+            static bool attr = false;
+            if (!attr) {
+                GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_panel_local_f32_lx,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, GLU_PANEL_SMEM));
+                attr = true;
+            }
+            k_panel_local_f32_lx<<<blocks, 128, GLU_PANEL_SMEM, ctx->stream>>>(
+                (float2 *)A, lda, n, c0, w, ipiv, growth, ctx->dflags, lx.Lx, lx.b0, lx.pitch);
+            GDM_LAUNCHED(ctx, "panel_local_f32_lx");
+            return GDM_OK;
+        }
         k_panel_local_f32<<<blocks, 128, 0, ctx->stream>>>((float2 *)A, lda, n, c0, w, ipiv, growth, ctx->dflags);
         GDM_LAUNCHED(ctx, "panel_local_f32");
         return GDM_OK;
@@ -1253,16 +1301,19 @@ static gdm_status panel_local(gdm_ctx *ctx, C *A, int64_t lda, int64_t n, int64_
 // left part's panels, update the right part's rows below with one GEMM (K = width of the left part), then
 // factor the right part. Same arithmetic as panel-by-panel right-looking updates, but the GEMMs have
 // K = 256, 128, 64, 32 instead of fifteen K = 32 updates of the full remaining block width.
+// With an embedding buffer (lx.Lx) the panels write L's TF32 embedding as they go, the panel applications
+// store U rounded to TF32, and the updates read both straight from there (no preparation pass).
 static gdm_status factor_rec(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t lo,
-                             int64_t hi, int32_t *ipiv, unsigned *growth, void *tcws, size_t tcbytes) {
+                             int64_t hi, int32_t *ipiv, unsigned *growth, void *tcws, size_t tcbytes,
+                             const LxBuf &lx) {
     const int64_t w = hi - lo;
     if (w <= NBP) {
         GDM_TRY(gdm_phase_begin(ctx, GDM_PH_PANEL));
-        GDM_TRY(panel_local<float2>(ctx, A, lda, n, lo, (int)w, ipiv, growth));
+        GDM_TRY(panel_local<float2>(ctx, A, lda, n, lo, (int)w, ipiv, growth, lx));
         return gdm_phase_end(ctx, GDM_PH_PANEL);
     }
     const int64_t mid = lo + NBP * ((w + 2 * NBP - 1) / (2 * NBP));
-    GDM_TRY(factor_rec(ctx, prec, A, lda, n, lo, mid, ipiv, growth, tcws, tcbytes));
+    GDM_TRY(factor_rec(ctx, prec, A, lda, n, lo, mid, ipiv, growth, tcws, tcbytes, lx));
     const int nr = (int)(mid - lo), ncols = (int)(hi - mid);
     GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRSM));
     const size_t sm = (size_t)8 * nr * sizeof(float2);
@@ -1273,13 +1324,24 @@ static gdm_status factor_rec(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_
         attr = true;
     }
     const int bthreads = nr < 256 ? 256 : (nr > 512 ? 512 : nr);
-    k_panels_apply<<<(unsigned)((ncols + 7) / 8), bthreads, sm, ctx->stream>>>(A, lda, lo, nr, mid, ncols, ipiv);
+    k_panels_apply<<<(unsigned)((ncols + 7) / 8), bthreads, sm, ctx->stream>>>(A, lda, lo, nr, mid, ncols, ipiv,
+                                                                              lx.Lx != nullptr);
     GDM_LAUNCHED(ctx, "panels_apply");
     GDM_TRY(gdm_phase_end(ctx, GDM_PH_TRSM));
     GDM_TRY(gdm_phase_begin(ctx, GDM_PH_INBLOCK));
-    GDM_TRY(update<float2>(ctx, prec, A, lda, n, mid, mid, lo, n - mid, hi - mid, mid - lo, tcws, tcbytes));
+    if (lx.Lx) {
+        // rows [mid, n) of L's columns [lo, mid) in the embedding; U = rows [lo, mid) of columns [mid, hi)
+        const float *lp = lx.Lx + 2 * (mid - lx.b0) * (int64_t)lx.pitch + 2 * (lo - lx.b0);
+        gdm_status s = gdm_tc_update_lx(ctx, A, lda, mid, mid, lp, lx.pitch, A, lda, lo, mid, n - mid, hi - mid,
+                                        mid - lo, 0);
+        if (s == GDM_ERR_UNSUPPORTED)
+            s = update<float2>(ctx, prec, A, lda, n, mid, mid, lo, n - mid, hi - mid, mid - lo, tcws, tcbytes);
+        GDM_TRY(s);
+    } else {
+        GDM_TRY(update<float2>(ctx, prec, A, lda, n, mid, mid, lo, n - mid, hi - mid, mid - lo, tcws, tcbytes));
+    }
     GDM_TRY(gdm_phase_end(ctx, GDM_PH_INBLOCK));
-    return factor_rec(ctx, prec, A, lda, n, mid, hi, ipiv, growth, tcws, tcbytes);
+    return factor_rec(ctx, prec, A, lda, n, mid, hi, ipiv, growth, tcws, tcbytes, lx);
 }
 
 template <class C>
@@ -1298,8 +1360,17 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
     size_t opbytes = u12_op ? ScratchCarver::round((size_t)NB * NB * sizeof(C)) +
                                   ScratchCarver::round((size_t)NB * n * sizeof(C))
                             : 0;
+    // recursive blocks pay off on large systems; small ones (the batched workloads) keep the panel-by-panel
+    // updates, whose per-problem latency is lower
+    const bool recursive =
+        u12_op && NB <= 1024 && (n >= 8192 || getenv("GDM_LU_RECURSIVE")) && !getenv("GDM_INBLOCK_PANELS");
+    // TF32: the panels write L's embedding for the updates as they go (rows from the outer block's first row,
+    // 2 NB floats a real row) and U is rounded in storage, so the updates need no operand preparation
+    const bool lx_path = recursive && prec == GDM_TF32_REFINE && !(lda & 1) && !((uintptr_t)A & 15) &&
+                         !getenv("GDM_LU_PREP_L") && !getenv("GDM_TC_TRUNCATE");
+    const size_t lxbytes = lx_path ? ScratchCarver::round((size_t)2 * n * 2 * NB * sizeof(float)) : 0;
     void *ws;
-    GDM_TRY(gdm_scratch(ctx, pbytes + tcbytes + opbytes + 1024, &ws));
+    GDM_TRY(gdm_scratch(ctx, pbytes + tcbytes + opbytes + lxbytes + 1024, &ws));
     ScratchCarver sc(ws);
     PanelScratch<C> ps;
     ps.cand_val = sc.take<double>(2 * pmax);
@@ -1309,15 +1380,17 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
     void *tcws = tcbytes ? sc.take<char>(tcbytes) : nullptr;
     float2 *negM = u12_op ? sc.take<float2>((size_t)NB * NB) : nullptr;
     float2 *T12 = u12_op ? sc.take<float2>((size_t)NB * n) : nullptr;
-    // recursive blocks pay off on large systems; small ones (the batched workloads) keep the panel-by-panel
-    // updates, whose per-problem latency is lower
-    const bool recursive =
-        u12_op && NB <= 1024 && (n >= 8192 || getenv("GDM_LU_RECURSIVE")) && !getenv("GDM_INBLOCK_PANELS");
+    LxBuf lx;
+    if (lx_path) {
+        lx.Lx = sc.take<float>((size_t)2 * n * 2 * NB);
+        lx.pitch = 2 * NB;
+    }
     for (int64_t b0 = 0; b0 < n; b0 += NB) {
         int64_t nb = n - b0 < NB ? n - b0 : NB;
         int64_t be = b0 + nb;
+        lx.b0 = b0;
         if (recursive)
-            GDM_TRY(factor_rec(ctx, prec, (float2 *)A, lda, n, b0, be, ipiv, growth, tcws, tcbytes));
+            GDM_TRY(factor_rec(ctx, prec, (float2 *)A, lda, n, b0, be, ipiv, growth, tcws, tcbytes, lx));
         else
         for (int64_t c0 = b0; c0 < be; c0 += NBP) {
             int w = (int)(be - c0 < NBP ? be - c0 : NBP);
@@ -1363,6 +1436,10 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
             GDM_TRY(gdm_tc_update_ext(ctx, prec, (float2 *)A, lda, b0, be, negM, nbi, T12, nbi, 0, 0, nbi, nc, nbi,
                                       tcws, tcbytes, 0,
                                       prec != GDM_FP32 && !getenv("GDM_TC_TRUNCATE")));
+            if (lx.Lx) {
+                k_round_tf32_block<<<gb, 256, 0, ctx->stream>>>((float2 *)A, lda, b0, nbi, be, nc);
+                GDM_LAUNCHED(ctx, "round_tf32_block");
+            }
             GDM_TRY(gdm_phase_end(ctx, GDM_PH_U12));
         } else if (be < n) {
             // U12 = L11^{-1} A12 panel by panel; each panel's interchanges reach the trailing columns just
@@ -1386,7 +1463,14 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
             // A22 -= A21 U12
             GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRAILING));
             gdm_status s = GDM_ERR_UNSUPPORTED;
-            if (sizeof(C) == 8 && tcws)
+            if (lx.Lx && n - be >= 64) {
+                // rows [be, n) of the block's L embedding against the rounded U12 in place
+                nvtxRangePushA("gdm_trailing_update");
+                s = gdm_tc_update_lx(ctx, (float2 *)A, lda, be, be, lx.Lx + 2 * (be - b0) * (int64_t)lx.pitch,
+                                     lx.pitch, (const float2 *)A, lda, b0, be, n - be, n - be, nb, 1);
+                nvtxRangePop();
+            }
+            if (s == GDM_ERR_UNSUPPORTED && sizeof(C) == 8 && tcws)
                 s = gdm_tc_trailing_update(ctx, prec, (float2 *)A, lda, n, b0, nb, tcws, tcbytes);
             if (s == GDM_ERR_UNSUPPORTED) {
                 int slot;

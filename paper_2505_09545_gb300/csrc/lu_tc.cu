@@ -1481,3 +1481,44 @@ gdm_status gdm_glu_gemm(gdm_ctx *ctx, const GluItem *items, const GluMaps *maps,
     GDM_LAUNCHED(ctx, kind == GLU_PANEL ? "glu_gemm_panel" : "glu_gemm_trailing");
     return GDM_OK;
 }
+
+// ---------------------------------------------------------------- update from a prepared L embedding
+// C[r0 : r0+Mc, c0 : c0+Nc] -= L U (one TF32 product) with the A operand already embedded and rounded to
+// TF32 by the panel kernel: real rows 2i and 2i+1 of L's row i at Lx + 2 i lx_pitch, K' = 2 Kc floats each
+// (Lx 16-byte aligned, lx_pitch a multiple of 4), and U read straight from its storage (values that are
+// TF32 already: rows u_r0 .. u_r0 + Kc of columns u_c0 .. u_c0 + Nc, column-major with ldu). No preparation
+// pass: the factorisation's in-block and trailing updates read what the panels and the interchange passes
+// wrote. prof = 1 records the launch as the factorisation's dominant kernel.
+gdm_status gdm_tc_update_lx(gdm_ctx *ctx, float2 *C, int64_t ldc, int64_t r0, int64_t c0, const float *Lx,
+                            int64_t lx_pitch, const float2 *U, int64_t ldu, int64_t u_r0, int64_t u_c0, int64_t Mc,
+                            int64_t Nc, int64_t Kc, int prof) {
+    if (Mc <= 0 || Nc <= 0 || Kc <= 0) return GDM_OK;
+    if (getenv("GDM_TC_DISABLE")) return GDM_ERR_UNSUPPORTED;
+    if (((uintptr_t)C & 15) || (ldc & 1) || (r0 & 1) || ((uintptr_t)U & 15) || (ldu & 1) || (u_r0 & 1) ||
+        ((uintptr_t)Lx & 15) || (lx_pitch & 3))
+        return GDM_ERR_UNSUPPORTED;
+    const int M = (int)(2 * Mc), N = (int)Nc, K = (int)(2 * Kc);
+    const bool pair = M >= PBM && N >= 2 * PBN && !getenv("GDM_TC_SINGLE");
+    CUtensorMap ta, tb, tc;
+    if (!(make_map(&ta, Lx, (uint64_t)K, (uint64_t)M, (uint64_t)lx_pitch, BM) &&
+          make_map(&tb, (const float *)U, (uint64_t)2 * ldu, (uint64_t)(u_c0 + Nc), (uint64_t)2 * ldu,
+                   pair ? PBN / 2 : 256) &&
+          make_map_c(&tc, (const float *)C, (uint64_t)(2 * (r0 + Mc)), (uint64_t)(c0 + Nc), (uint64_t)2 * ldc)))
+        return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    int slot = -1;
+    const double fl = 8.0 * (double)Mc * (double)Nc * (double)Kc;
+    const double by = 16.0 * (double)Mc * Nc + 4.0 * ((double)M * K + (double)N * K);
+    if (prof) GDM_TRY(gdm_prof_begin(ctx, &slot));
+    gdm_status st = GDM_ERR_UNSUPPORTED;
+    if (pair)
+        st = launch_update_pair<false>(ctx, ta, tb, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * u_r0), (int)u_c0);
+    if (st == GDM_ERR_UNSUPPORTED) {
+        if (pair && !make_map(&tb, (const float *)U, (uint64_t)2 * ldu, (uint64_t)(u_c0 + Nc), (uint64_t)2 * ldu, 256))
+            return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        st = launch_update<256, 1>(ctx, ta, ta, tb, tb, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * u_r0),
+                                   (int)u_c0);
+    }
+    GDM_TRY(st);
+    if (prof) GDM_TRY(gdm_prof_end(ctx, slot, fl, by));
+    return GDM_OK;
+}

@@ -254,12 +254,16 @@ def test_lu_factor_quality(G, ctx, prec, tol_plain, max_iters):
     assert np.all(e2 < 1e-9) and info["iterations"] <= max_iters, (e1, e2, info)
 
 
-@pytest.mark.parametrize("prec", ["tf32", "fp32"])
-def test_recursive_block_factorisation(G, ctx, prec, monkeypatch):
+@pytest.mark.parametrize("prec,prep_l", [("tf32", False), ("tf32", True), ("fp32", False)])
+def test_recursive_block_factorisation(G, ctx, prec, prep_l, monkeypatch):
     """The recursive in-block factorisation (used from n = 8192 on; forced here at 3N = 2100: four full
     512-column blocks split 256/128/64/32 and a ragged 52-column last block) gives factors of the
-    precision's quality and refined fields at 1e-9, like the panel-by-panel path."""
+    precision's quality and refined fields at 1e-9, like the panel-by-panel path. At TF32 the panels write
+    L's embedding for the updates and U is rounded in storage; GDM_LU_PREP_L takes the path that prepares
+    both operands before each update instead."""
     monkeypatch.setenv("GDM_LU_RECURSIVE", "1")
+    if prep_l:
+        monkeypatch.setenv("GDM_LU_PREP_L", "1")
     s = W.random_cells(700, seed=12)
     lam = float(s.wavelengths[0])
     prob = gpu_problem(G, s, lam)
