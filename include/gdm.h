@@ -107,6 +107,14 @@ typedef struct {
 #define GDM_SOLVE_FACTORED 1      /* A already holds this problem's factors and ipiv its pivots */
 #define GDM_SOLVE_NO_REFINE 2     /* return the plain triangular-solve result */
 #define GDM_SOLVE_GLOBAL_PIVOT 4  /* always search pivots over the whole column (partial pivoting) */
+/* Stop on the estimated error instead of the last correction: when the last two relative corrections
+ * c_prev, c of a right-hand side contract by rho = c / c_prev <= 1/4, the corrections that would follow sum
+ * to about rho c / (1 - rho) (a geometric tail), which is the relative error left in the returned F; the
+ * refinement stops once that estimate (else c itself) is <= tol for every right-hand side. Iterative
+ * refinement with an error estimate from the contraction of successive corrections, as in Demmel et al.,
+ * "Error bounds from extra-precise iterative refinement", ACM TOMS 32 (2006). rel_correction still reports
+ * the last correction. */
+#define GDM_SOLVE_ERR_ESTIMATE 8
 /* Pivoting: by default each 32-column panel searches its pivots among the rows of its 32 x 32
  * diagonal block and certifies the choice against all rows below. If some row below exceeds its
  * pivot by more than GDM_PIVOT_GROWTH_LIMIT, gdm_solve re-assembles A from the problem and factors

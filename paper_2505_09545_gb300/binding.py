@@ -28,6 +28,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 SOLVE_FACTORED = 1
 SOLVE_NO_REFINE = 2
 SOLVE_GLOBAL_PIVOT = 4
+SOLVE_ERR_ESTIMATE = 8
 
 
 class GDMError(RuntimeError):
@@ -290,9 +291,11 @@ def assemble(ctx: Context, prob: GDMProblem, precision="fp32", lda=None, out=Non
 
 
 def solve(ctx: Context, prob: GDMProblem, A, F0, precision="fp32", ipiv=None, factored=False, max_iter=0, tol=0.0,
-          no_refine=False, info=True, F=None, global_pivot=False):
+          no_refine=False, info=True, F=None, global_pivot=False, err_estimate=False):
     """Factor A in place (unless factored) and solve A F = F0 with FP64 refinement.
-    F0: (n_rhs, n_sys) complex128. Returns (F, ipiv, info dict or None)."""
+    F0: (n_rhs, n_sys) complex128. err_estimate: stop when the error estimated from the contraction of the
+    last two corrections is <= tol (GDM_SOLVE_ERR_ESTIMATE) instead of the last correction.
+    Returns (F, ipiv, info dict or None)."""
     ns = prob.size
     lda = A.shape[1]
     if ipiv is None:
@@ -301,7 +304,7 @@ def solve(ctx: Context, prob: GDMProblem, A, F0, precision="fp32", ipiv=None, fa
         F = torch.empty_like(F0)
     n_rhs = F0.shape[0]
     flags = ((SOLVE_FACTORED if factored else 0) | (SOLVE_NO_REFINE if no_refine else 0)
-             | (SOLVE_GLOBAL_PIVOT if global_pivot else 0))
+             | (SOLVE_GLOBAL_PIVOT if global_pivot else 0) | (SOLVE_ERR_ESTIMATE if err_estimate else 0))
     opts = SolveOpts(int(max_iter), flags, float(tol))
     inf = SolveInfo() if info else None
     s = prob.struct()
@@ -398,10 +401,11 @@ def cross_sections_noalloc(ctx: Context, prob: GDMProblem, F0, F, e0_norm2, out)
 
 
 def solve_batched(ctx: Context, probs, e0s, precision="tf32", khat=(0.0, 0.0, 1.0), n_streams=0, with_sigma=True,
-                  max_iter=0, tol=0.0, return_factors=False):
+                  max_iter=0, tol=0.0, return_factors=False, err_estimate=False):
     """gdm_solve_batched over independent problems: probs is a list of GDMProblem, e0s a list of (n_rhs, 3)
     complex plane-wave amplitudes (one per problem). Allocates the items' matrices, pivots, fields and
-    cross sections (one device buffer of each kind, sliced per item); returns (F list of (n_rhs, kind*n)
+    cross sections (one device buffer of each kind, sliced per item); err_estimate as for solve; returns
+    (F list of (n_rhs, kind*n)
     complex128, sigma list of (3, n_rhs) or None, info list of dicts)."""
     prec = PRECISION[precision]
     n = len(probs)
@@ -454,7 +458,7 @@ def solve_batched(ctx: Context, probs, e0s, precision="tf32", khat=(0.0, 0.0, 1.
         if return_factors:
             As.append(Abuf[a_off[i]:a_off[i] + ns * lda].view(ns, lda))
             ipivs.append(Pbuf[p_off[i]:p_off[i] + ns])
-    opts = SolveOpts(int(max_iter), 0, float(tol))
+    opts = SolveOpts(int(max_iter), SOLVE_ERR_ESTIMATE if err_estimate else 0, float(tol))
     infos = (SolveInfo * n)()
     ctx._sync_stream()
     ctx._check(lib().gdm_solve_batched(ctx.h, prec, items, n, C.byref(opts), int(n_streams), infos),

@@ -171,7 +171,7 @@ gdm_status solve_grouped(gdm_ctx *ctx, gdm_precision prec, const gdm_batch_item 
     if (!gp.empty()) {
         memset(ginf.data(), 0, sizeof(gdm_solve_info) * gp.size());
         GDM_TRY(gdm_gr_refine(ctx, use.data(), fo.tol > 0 ? fo.tol : 1e-12, fo.max_iter > 0 ? fo.max_iter : 40,
-                              ginf.data()));
+                              fo.flags, ginf.data()));
         GDM_TRY(gdm_gr_xsec(ctx, use.data()));
     }
     auto grouped_info = [&](int i, gdm_solve_info *inf) {

@@ -293,7 +293,8 @@ gdm_status gdm_gr_inputs(gdm_ctx *ctx) {
     return gdm_gr_assemble(ctx, R->d_items, dl + La.list_off, dl + La.prefix_off, La.na, La.units);
 }
 
-gdm_status gdm_gr_refine(gdm_ctx *ctx, const unsigned char *use, double tol, int max_iter, gdm_solve_info *infos) {
+gdm_status gdm_gr_refine(gdm_ctx *ctx, const unsigned char *use, double tol, int max_iter, int flags,
+                         gdm_solve_info *infos) {
     RPlan *R = (RPlan *)ctx->grf;
     if (!R) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "grouped batch not prepared");
     const int N = (int)R->n.size();
@@ -396,13 +397,14 @@ gdm_status gdm_gr_refine(gdm_ctx *ctx, const unsigned char *use, double tol, int
                 c = std::max(c, xq > 0 ? std::sqrt(dq / xq) : (dq > 0 ? INFINITY : 0.0));
                 rr = std::max(rr, bq > 0 ? std::sqrt(rq / bq) : 0.0);
             }
+            const double stop = gdm_refine_stop_measure(c, it > 1 ? relc[k] : -1.0, flags);
             relc[k] = c;
             relr[k] = rr;
             iters[k] = it;
             if (!finite) {
                 stat[k] = GDM_ERR_NONFINITE;
                 done[k] = 1;
-            } else if (c <= tol) {
+            } else if (stop <= tol) {
                 done[k] = 1;
             }
         }

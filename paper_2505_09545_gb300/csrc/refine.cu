@@ -4,7 +4,8 @@
 //   r = b - A X          (matrix-free: the Green dyads are regenerated per pair, never stored)
 //   d = LU^{-1} r        (factor precision)
 //   X = X + d            (FP64)
-// until max_q ||d_q|| / ||X_q|| <= tol. The adjoint variant solves A^H X = b with the same factors
+// until max_q ||d_q|| / ||X_q|| <= tol (or, with GDM_SOLVE_ERR_ESTIMATE, until the error estimate from the
+// contraction of the last two corrections is). The adjoint variant solves A^H X = b with the same factors
 // (conjugate-transposed triangular solves) and the matrix-free residual b - A^H X.
 // Residual arithmetic: double-float (pairs of FP32 on the FP32 pipes, about 48 significand bits; the
 // GB300 FP64 pipe runs at ~1/64 of the FP32 rate), which matches the oracle's FP64 residual to ~1e-13 of
@@ -292,7 +293,7 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
     k_update<C><<<gq, 256, 0, ctx->stream>>>((double2 *)X, w, ns, n_rhs, 0, dnorm + 3 * n_rhs, dnorm, ctx->dflags);
     GDM_LAUNCHED(ctx, "update");
     int it = 0;
-    double relc = 1.0, relr = -1.0;
+    double relc = 1.0, relr = -1.0, prev = -1.0, stop = 1.0;
     if (!(opts->flags & GDM_SOLVE_NO_REFINE)) {
         for (it = 1; it <= opts->max_iter; it++) {
             GDM_CUDA_TRY(ctx, cudaMemsetAsync(dnorm, 0, sizeof(double) * 3 * n_rhs, ctx->stream));
@@ -319,6 +320,7 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
             GDM_CUDA_TRY(ctx, cudaMemcpyAsync(hn, dnorm, sizeof(double) * 4 * n_rhs, cudaMemcpyDeviceToHost,
                                               ctx->stream));
             GDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            prev = it > 1 ? relc : -1.0;
             relc = 0.0;
             relr = 0.0;
             bool finite = true;
@@ -341,7 +343,8 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
                 }
                 return gdm_fail(ctx, st, "non-finite values in the refined solution (%s)", gdm_status_string(st));
             }
-            if (relc <= opts->tol) break;
+            stop = gdm_refine_stop_measure(relc, prev, opts->flags);
+            if (stop <= opts->tol) break;
         }
         if (it > opts->max_iter) it = opts->max_iter;
     }
@@ -360,7 +363,7 @@ static gdm_status refined_t(gdm_ctx *ctx, const gdm_problem *p, gdm_precision pr
         gdm_status dev = gdm_ctx_check(ctx);
         if (info) info->status = dev;
         if (dev != GDM_OK) return dev;
-        if (relc > opts->tol) {
+        if (stop > opts->tol) {
             if (info) info->status = GDM_ERR_NOT_CONVERGED;
             return gdm_fail(ctx, GDM_ERR_NOT_CONVERGED, "refinement stopped at relative correction %.3e > tol %.3e",
                             relc, opts->tol);
