@@ -451,6 +451,58 @@ __device__ __forceinline__ void diag_step(float2 *r, int t, int lane, int &pos, 
     r[W - 1] = make_float2(0.f, 0.f);
 }
 
+// Warp-wide factorisation of a w x w diagonal block at (c0, c0) whose row `lane` is in r (zero beyond w,
+// destroyed): the pivots to ipiv (first: this CTA records them and a zero pivot), U in position order into
+// Uz (zero-padded beyond the block by the caller), every row's multipliers by step into Lr[lane], and each
+// row's final position into posof.
+__device__ __forceinline__ void diag_factor_warp(float2 *r, int w, int lane, float2 (*Uz)[2 * NBP],
+                                                 float2 (*Lr)[NBP + 1], int *posof, int64_t c0,
+                                                 int32_t *__restrict__ ipiv, int *flags, bool first) {
+    int pos = lane;         // current position of this lane's row
+    bool done = lane >= w;  // chosen as a pivot row already (or outside the block)
+    // pivot of column 0; every step then finds the next one
+    const unsigned vb0 = done ? 0u : __float_as_uint(fabsf(r[0].x) + fabsf(r[0].y));
+    unsigned m = __reduce_max_sync(0xffffffffu, vb0);
+    unsigned key = __reduce_min_sync(0xffffffffu, (!done && vb0 == m) ? (unsigned)pos : 0xffffffffu);
+    // windows shrink with the columns left: 32 - t <= W
+    int t = 0;
+#pragma unroll 1
+    for (; t < w && t < 8; t++) diag_step<32>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, first);
+#pragma unroll 1
+    for (; t < w && t < 16; t++) diag_step<24>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, first);
+#pragma unroll 1
+    for (; t < w && t < 24; t++) diag_step<16>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, first);
+#pragma unroll 1
+    for (; t < w; t++) diag_step<8>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, first);
+    if (lane < w) posof[lane] = pos;
+}
+
+// Forward substitution of one row x (its 32 entries in a full panel's columns, destroyed) against the
+// panel's factored diagonal block (U in position order Uz, reciprocal pivots invd, 1 / |pivot| inv_pa): the
+// multipliers to lout[k] and, unless acol is null, to acol[k lda] (column k of the panel in this row);
+// the certificate's largest ratio into worst. Four phases whose windows shrink with the columns left.
+__device__ __forceinline__ void subst_row32(float2 *x, float2 (*Uz)[2 * NBP], const float2 *invd,
+                                            const float *inv_pa, float2 *lout, float2 *acol, int64_t lda,
+                                            float &worst) {
+#define SUBST_PHASE(W_, KEND)                                                                      \
+    for (; k < (KEND); k++) {                                                                      \
+        worst = fmaxf(worst, (fabsf(x[0].x) + fabsf(x[0].y)) * inv_pa[k]);                        \
+        const float2 l_ = subst_step<W_>(x, &Uz[k][k], invd[k]);                                   \
+        lout[k] = l_;                                                                              \
+        if (acol) acol[k * lda] = l_;                                                              \
+    }
+    int k = 0;
+#pragma unroll 1
+    SUBST_PHASE(32, 8)
+#pragma unroll 1
+    SUBST_PHASE(24, 16)
+#pragma unroll 1
+    SUBST_PHASE(16, 24)
+#pragma unroll 1
+    SUBST_PHASE(8, 32)
+#undef SUBST_PHASE
+}
+
 // The body is shared with the grouped panel of a batch (GROUPED): CTA bid of nblk factoring this panel, the
 // finish counter in *ticket, and the multipliers of every full panel also written, rounded to TF32, into the
 // real embedding that the batch's tensor-core updates read (Lx: real rows 2 (r - b0) and 2 (r - b0) + 1,
@@ -490,23 +542,7 @@ __device__ __forceinline__ void panel_f32_body(float2 *__restrict__ A, int64_t l
             r[c] = make_float2(0.f, 0.f);
             if (c < w && lane < w) r[c] = A[(c0 + c) * lda + c0 + lane];
         }
-        int pos = lane;         // current position of this lane's row
-        bool done = lane >= w;  // chosen as a pivot row already (or outside the block)
-        // pivot of column 0; every step then finds the next one
-        const unsigned vb0 = done ? 0u : __float_as_uint(fabsf(r[0].x) + fabsf(r[0].y));
-        unsigned m = __reduce_max_sync(0xffffffffu, vb0);
-        unsigned key = __reduce_min_sync(0xffffffffu, (!done && vb0 == m) ? (unsigned)pos : 0xffffffffu);
-        // windows shrink with the columns left: 32 - t <= W
-        int t = 0;
-#pragma unroll 1
-        for (; t < w && t < 8; t++) diag_step<32>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, bid == 0);
-#pragma unroll 1
-        for (; t < w && t < 16; t++) diag_step<24>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, bid == 0);
-#pragma unroll 1
-        for (; t < w && t < 24; t++) diag_step<16>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, bid == 0);
-#pragma unroll 1
-        for (; t < w; t++) diag_step<8>(r, t, lane, pos, done, m, key, Uz, Lr, c0, ipiv, flags, bid == 0);
-        if (lane < w) posof[lane] = pos;
+        diag_factor_warp(r, w, lane, Uz, Lr, posof, c0, ipiv, flags, bid == 0);
     }
     __syncthreads();
     if (tid < w) {
@@ -589,6 +625,180 @@ __global__ void __launch_bounds__(128) k_panel_local_f32_lx(float2 *__restrict__
     extern __shared__ float2 pl_ls[];  // 128 x (NBP + 1) multipliers of a round of rows
     panel_f32_body<true>(A, lda, n, c0, w, ipiv, growth, &flags[GDM_FLAG_PANEL_TICKET], flags, blockIdx.x,
                          gridDim.x, Lx, b0, (int)(2 * (c0 - b0)), lx_pitch, (float2(*)[NBP + 1])pl_ls);
+}
+
+// Two full panels in one launch, columns [c0, c0 + 64): the bottom level of the recursive block
+// factorisation, in place of panel, interchange-and-solve of the next panel's top rows, K = 32 update of its
+// columns, and panel. Every CTA
+//   1. factors the first 32 x 32 diagonal block (warp 0),
+//   2. forms the U block right of it, U12 = L11^{-1} P1 A12 (rows in position order; all four warps, eight
+//      columns each, lane = row),
+//   3. brings the second diagonal block's rows up to date (warp 0: their multipliers of the first panel, then
+//      A22 - L21 U12 in FP32) and factors it,
+// and then takes its share of the rows below: the first panel's multipliers, the row's next 32 columns
+// updated by them and U12 (FP32 products, in place of the K = 32 tensor-core update), and the second panel's
+// multipliers. Pivots, certificate and errors as in the one-panel kernel; the second panel's interchanges
+// stay inside its block (product form: the first panel's multipliers of those rows keep their order). The
+// last CTA to finish stores the 64 x 64 diagonal region. With Lx, the multipliers of both panels of the
+// rows below c0 + 64 also go out as their TF32 embedding (rows from b0, lx_pitch floats a real row),
+// staged through shared memory in CTA-wide rounds.
+constexpr int PANEL2_SMEM = (2 * NBP * 2 * NBP + 128 * (NBP + 1)) * (int)sizeof(float2);
+__global__ void __launch_bounds__(128, 2) k_panel2_f32(float2 *__restrict__ A, int64_t lda, int64_t n, int64_t c0,
+                                                      int32_t *__restrict__ ipiv, unsigned *growth, int *flags,
+                                                      float *__restrict__ Lx, int64_t b0, int lx_pitch) {
+    extern __shared__ __align__(16) float2 p2_dyn[];
+    float2(*Uz1)[2 * NBP] = (float2(*)[2 * NBP])p2_dyn;  // U of the first block, position order, zero-padded
+    float2(*Uz2)[2 * NBP] = Uz1 + NBP;                   // and of the second
+    float2(*Ls)[NBP + 1] = (float2(*)[NBP + 1])(Uz2 + NBP);  // multipliers of a round of rows
+    __shared__ float2 Lr[NBP][NBP + 1];   // multipliers of lane q's row by step (either block)
+    __shared__ float2 F1[NBP][NBP + 1];   // first diagonal block factored, position order
+    __shared__ float2 F2[NBP][NBP + 1];   // second
+    __shared__ float2 Ub[NBP][NBP + 2];   // U12: rows in the first block's position order
+    __shared__ float2 L2[NBP][NBP + 1];   // first panel's multipliers of the second block's rows
+    __shared__ float2 invd1[NBP], invd2[NBP];
+    __shared__ float inv_pa1[NBP], inv_pa2[NBP];
+    __shared__ int posof[NBP];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool first = blockIdx.x == 0;
+    const int64_t r_first = c0 + 2 * NBP + blockIdx.x * (int64_t)blockDim.x + tid;
+    const int64_t r_step = (int64_t)gridDim.x * blockDim.x;
+    for (int e = tid; e < 2 * NBP * 2 * NBP; e += blockDim.x) (&Uz1[0][0])[e] = make_float2(0.f, 0.f);
+    // the first row below is loaded while warp 0 factors the diagonal blocks
+    float2 x[NBP];
+#pragma unroll
+    for (int c = 0; c < NBP; c++) x[c] = r_first < n ? A[(c0 + c) * lda + r_first] : make_float2(0.f, 0.f);
+    __syncthreads();
+    float worst = 0.f;
+    // 1. first diagonal block
+    if (tid < 32) {
+        float2 r[NBP];
+#pragma unroll
+        for (int c = 0; c < NBP; c++) r[c] = A[(c0 + c) * lda + c0 + lane];
+        diag_factor_warp(r, NBP, lane, Uz1, Lr, posof, c0, ipiv, flags, first);
+    }
+    __syncthreads();
+    if (tid < NBP) {
+        const float2 d = Uz1[tid][tid];
+        const float pa = fabsf(d.x) + fabsf(d.y);
+        invd1[tid] = pa > 0.f ? crecip(d) : make_float2(0.f, 0.f);
+        inv_pa1[tid] = pa > 0.f ? 1.0f / pa : 0.f;
+        const int p = posof[tid];
+        for (int c = 0; c < NBP; c++) F1[p][c] = c < p ? Lr[tid][c] : Uz1[p][c];
+    }
+    __syncthreads();
+    // 2. U12 = L11^{-1} P1 A12: warp w takes columns 8w .. 8w + 8, lane = row (first the interchanges: row q
+    // of the block goes to its position posof[q], then the unit-lower solve by position)
+    {
+        float2 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) v[j] = A[(c0 + NBP + 8 * warp + j) * lda + c0 + lane];
+        const int p = posof[lane];
+#pragma unroll
+        for (int j = 0; j < 8; j++) Ub[p][8 * warp + j] = v[j];
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 8; j++) v[j] = Ub[lane][8 * warp + j];
+#pragma unroll 1
+        for (int t = 0; t < NBP - 1; t++) {
+            const float2 lt = F1[lane][t];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const float2 xt = make_float2(__shfl_sync(0xffffffffu, v[j].x, t), __shfl_sync(0xffffffffu, v[j].y, t));
+                if (lane > t) cfms(v[j], lt, xt);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) Ub[lane][8 * warp + j] = v[j];
+    }
+    __syncthreads();
+    // 3. the second block's rows: first panel's multipliers, update, factorisation
+    if (tid < 32) {
+        float2 r[NBP];
+#pragma unroll
+        for (int c = 0; c < NBP; c++) r[c] = A[(c0 + c) * lda + c0 + NBP + lane];
+        subst_row32(r, Uz1, invd1, inv_pa1, L2[lane], nullptr, lda, worst);
+#pragma unroll
+        for (int c = 0; c < NBP; c++) r[c] = A[(c0 + NBP + c) * lda + c0 + NBP + lane];
+#pragma unroll 2
+        for (int k = 0; k < NBP; k++) {
+            const float2 l = L2[lane][k];
+#pragma unroll
+            for (int c = 0; c < NBP; c++) cfms(r[c], l, Ub[k][c]);
+        }
+        diag_factor_warp(r, NBP, lane, Uz2, Lr, posof, c0 + NBP, ipiv, flags, first);
+    }
+    __syncthreads();
+    if (tid < NBP) {
+        const float2 d = Uz2[tid][tid];
+        const float pa = fabsf(d.x) + fabsf(d.y);
+        invd2[tid] = pa > 0.f ? crecip(d) : make_float2(0.f, 0.f);
+        inv_pa2[tid] = pa > 0.f ? 1.0f / pa : 0.f;
+        const int p = posof[tid];
+        for (int c = 0; c < NBP; c++) F2[p][c] = c < p ? Lr[tid][c] : Uz2[p][c];
+    }
+    __syncthreads();
+    // the rows below, in CTA-wide rounds (uniform trip count, for the barriers of the embedding stores)
+    auto store_lx = [&](int64_t rb, int col) {
+        // real rows 2 (r - b0) + h, floats col + 4 q .. + 4 (the column pairs k = 2q, 2q + 1)
+        const int nrow = (int)min((int64_t)blockDim.x, n - rb);
+        for (int e = tid; e < nrow * 32; e += blockDim.x) {
+            const int i = e >> 5, h = (e >> 4) & 1, q = e & 15;
+            const float2 a = Ls[i][2 * q], b = Ls[i][2 * q + 1];
+            const float4 v = h ? make_float4(tf32_rna(a.y), tf32_rna(a.x), tf32_rna(b.y), tf32_rna(b.x))
+                               : make_float4(tf32_rna(a.x), tf32_rna(-a.y), tf32_rna(b.x), tf32_rna(-b.y));
+            *(float4 *)(Lx + (2 * (rb + i - b0) + h) * (int64_t)lx_pitch + col + 4 * q) = v;
+        }
+    };
+    for (int64_t rb = r_first - tid; rb < n; rb += r_step) {
+        const int64_t r = rb + tid;
+        float2 y[NBP];
+        if (r < n) {
+            if (rb != r_first - tid) {
+#pragma unroll
+                for (int c = 0; c < NBP; c++) x[c] = A[(c0 + c) * lda + r];
+            }
+            subst_row32(x, Uz1, invd1, inv_pa1, Ls[tid], A + c0 * lda + r, lda, worst);
+#pragma unroll
+            for (int c = 0; c < NBP; c++) y[c] = A[(c0 + NBP + c) * lda + r];
+#pragma unroll 2
+            for (int k = 0; k < NBP; k++) {
+                const float2 l = Ls[tid][k];
+#pragma unroll
+                for (int c = 0; c < NBP; c++) cfms(y[c], l, Ub[k][c]);
+            }
+        }
+        if (Lx) {
+            __syncthreads();
+            store_lx(rb, (int)(2 * (c0 - b0)));
+            __syncthreads();
+        }
+        if (r < n) subst_row32(y, Uz2, invd2, inv_pa2, Ls[tid], A + (c0 + NBP) * lda + r, lda, worst);
+        if (Lx) {
+            __syncthreads();
+            store_lx(rb, (int)(2 * (c0 + NBP - b0)));
+            __syncthreads();
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_down_sync(0xffffffffu, worst, o));
+    if (lane == 0 && worst > 0.f) atomicMax(growth, __float_as_uint(worst));
+    // the 64 x 64 diagonal region, once no CTA can still read it
+    int *ticket = &flags[GDM_FLAG_PANEL_TICKET];
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    for (int e = tid; e < 4 * NBP * NBP; e += blockDim.x) {
+        const int rr = e & (2 * NBP - 1), cc = e >> 6;
+        float2 v;
+        if (rr < NBP) v = cc < NBP ? F1[rr][cc] : Ub[rr][cc - NBP];
+        else v = cc < NBP ? L2[rr - NBP][cc] : F2[rr - NBP][cc - NBP];
+        A[(c0 + cc) * lda + c0 + rr] = v;
+    }
+    if (tid == 0) atomicExch(ticket, 0);
 }
 
 // Grouped panel of a batch (lock-step over the problems of a decreasing-size table): CTA b works for the
@@ -1310,6 +1520,23 @@ static gdm_status factor_rec(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_
     if (w <= NBP) {
         GDM_TRY(gdm_phase_begin(ctx, GDM_PH_PANEL));
         GDM_TRY(panel_local<float2>(ctx, A, lda, n, lo, (int)w, ipiv, growth, lx));
+        return gdm_phase_end(ctx, GDM_PH_PANEL);
+    }
+    if (w == 2 * NBP && !getenv("GDM_PANEL_SINGLE") && !getenv("GDM_PANEL_SMEM")) {
+        // both panels of a 64-column block in one launch
+        GDM_TRY(gdm_phase_begin(ctx, GDM_PH_PANEL));
+        static bool attr = false;
+        if (!attr) {
+            GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_panel2_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   PANEL2_SMEM));
+            attr = true;
+        }
+        int blocks = (int)((n - hi + 127) / 128);
+        if (blocks < 1) blocks = 1;
+        if (blocks > 2 * ctx->sm_count) blocks = 2 * ctx->sm_count;  // one wave (two CTAs an SM)
+        k_panel2_f32<<<blocks, 128, PANEL2_SMEM, ctx->stream>>>(A, lda, n, lo, ipiv, growth, ctx->dflags, lx.Lx,
+                                                                 lx.b0, lx.pitch);
+        GDM_LAUNCHED(ctx, "panel2_f32");
         return gdm_phase_end(ctx, GDM_PH_PANEL);
     }
     const int64_t mid = lo + NBP * ((w + 2 * NBP - 1) / (2 * NBP));

@@ -254,16 +254,19 @@ def test_lu_factor_quality(G, ctx, prec, tol_plain, max_iters):
     assert np.all(e2 < 1e-9) and info["iterations"] <= max_iters, (e1, e2, info)
 
 
-@pytest.mark.parametrize("prec,prep_l", [("tf32", False), ("tf32", True), ("fp32", False)])
-def test_recursive_block_factorisation(G, ctx, prec, prep_l, monkeypatch):
+@pytest.mark.parametrize("prec,switch", [("tf32", None), ("tf32", "GDM_LU_PREP_L"), ("tf32", "GDM_PANEL_SINGLE"),
+                                         ("fp32", None), ("fp32", "GDM_PANEL_SINGLE")])
+def test_recursive_block_factorisation(G, ctx, prec, switch, monkeypatch):
     """The recursive in-block factorisation (used from n = 8192 on; forced here at 3N = 2100: four full
-    512-column blocks split 256/128/64/32 and a ragged 52-column last block) gives factors of the
-    precision's quality and refined fields at 1e-9, like the panel-by-panel path. At TF32 the panels write
-    L's embedding for the updates and U is rounded in storage; GDM_LU_PREP_L takes the path that prepares
-    both operands before each update instead."""
+    512-column blocks split 256/128/64 down to pairs of 32-column panels, and a ragged 52-column last
+    block) gives factors of the precision's quality and refined fields at 1e-9, like the panel-by-panel
+    path. Each 64-column leaf runs as one two-panel launch (its K = 32 update in FP32 inside the kernel);
+    GDM_PANEL_SINGLE takes the one-panel launches with the interchange pass and the tensor-core update
+    between them. At TF32 the panels write L's embedding for the updates and U is rounded in storage;
+    GDM_LU_PREP_L takes the path that prepares both operands before each update instead."""
     monkeypatch.setenv("GDM_LU_RECURSIVE", "1")
-    if prep_l:
-        monkeypatch.setenv("GDM_LU_PREP_L", "1")
+    if switch:
+        monkeypatch.setenv(switch, "1")
     s = W.random_cells(700, seed=12)
     lam = float(s.wavelengths[0])
     prob = gpu_problem(G, s, lam)
