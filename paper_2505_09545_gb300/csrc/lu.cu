@@ -955,115 +955,42 @@ __global__ void __launch_bounds__(128) k_glu_rows(const GluItem *__restrict__ it
 }
 
 // ------------------------------------------------------------------ block operator for the U12 row block
-// For the outer block [b0, b0+nb) (nb a multiple of 32, pivots of each 32-row panel inside that panel),
-// form negM = -(L_S^{-1} P_S ... L_1^{-1} P_1) restricted to the block's rows: the product form the
-// factorisation produced (each panel's L below its diagonal block is stored in the row order before the
-// later panels' interchanges). Then U12 = -negM A12 for the block's rows of the trailing columns. CTA
-// (g, h) forms columns 32 g + 8 h .. + 8 of the operator by applying the panels to those columns of I in
-// shared memory; panels before g leave them untouched (their rows are zero there).
-__global__ void __launch_bounds__(512) k_block_linv(const float2 *__restrict__ A, int64_t lda, int64_t b0, int nb,
-                                                    const int32_t *__restrict__ ipiv, float2 *__restrict__ negM) {
-    extern __shared__ __align__(16) float2 X[];  // X[c * nb + r], 8 columns
-    __shared__ float2 Lpp[32][33];
-    const int g = blockIdx.x >> 2, h = blockIdx.x & 3;
-    const int col0 = 32 * g + 8 * h;
+// Applies the panels q_begin, q_begin + 32, ... < nr of a factored block (view D, row and column 0 at the
+// block's first row; pivots of each 32-row panel inside that panel, global row indices in ipiv, base = the
+// block's first row) to CPB columns held in shared memory, X[c nr + r]: the product form the factorisation
+// produced, each panel's L below its diagonal block stored in the row order before the later panels'
+// interchanges. Per panel: the interchanges (each lane tracks where its row's content moves in the swap
+// sequence, then one scatter), the unit-lower solve with the diagonal block (warp c takes column c, lane =
+// row), and the rows of the later panels, x_r -= L[r, panel] x_panel (one thread per row).
+template <int CPB>
+__device__ __forceinline__ void apply_panels_smem(float2 *X, int nr, int q_begin, const float2 *__restrict__ D,
+                                                  int64_t lda, const int32_t *__restrict__ ipiv, int64_t base,
+                                                  float2 (*Lpp)[33]) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < 8 * nb; e += blockDim.x) {
-        const int c = e / nb, r = e % nb;
-        X[e] = make_float2(r == col0 + c ? 1.f : 0.f, 0.f);
-    }
-    const float2 *D = A + b0 * lda + b0;  // block-local view: D[r + c * lda]
-    for (int q0 = 32 * g; q0 < nb; q0 += 32) {
+    for (int q0 = q_begin; q0 < nr; q0 += 32) {
         for (int e = tid; e < 32 * 32; e += blockDim.x) {
             const int i = e & 31, j = e >> 5;
             Lpp[i][j] = (i > j) ? D[(int64_t)(q0 + j) * lda + q0 + i] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        // the panel's interchanges (inside its 32 rows), one thread per column
-        if (tid < 8) {
-            float2 *x = X + tid * nb;
+        if (warp < CPB) {
+            // lane t holds the panel-local row that step t swaps with; pos follows the content of row lane
+            const int piv = (int)(ipiv[base + q0 + lane] - base) - q0;
+            int pos = lane;
+#pragma unroll 4
             for (int t = 0; t < 32; t++) {
-                const int r2 = (int)(ipiv[b0 + q0 + t] - b0);
-                if (r2 != q0 + t && r2 >= q0 && r2 < q0 + 32) {
-                    const float2 a = x[q0 + t];
-                    x[q0 + t] = x[r2];
-                    x[r2] = a;
+                const int r2 = __shfl_sync(0xffffffffu, piv, t);
+                if (r2 != t && r2 >= 0 && r2 < 32) {
+                    if (pos == t) pos = r2;
+                    else if (pos == r2) pos = t;
                 }
             }
-        }
-        __syncthreads();
-        // unit-lower solve with the diagonal block: warp c takes column c, lane = row inside the panel
-        if (warp < 8) {
-            float2 *x = X + warp * nb + q0;
-            float2 v = x[lane];
-            for (int t = 0; t < 31; t++) {
-                const float2 xt = make_float2(__shfl_sync(0xffffffffu, v.x, t), __shfl_sync(0xffffffffu, v.y, t));
-                if (lane > t) cfms(v, Lpp[lane][t], xt);
-            }
-            x[lane] = v;
-        }
-        __syncthreads();
-        // rows of the later panels: x_r -= L[r, panel] x_panel (one thread per row)
-        for (int r = q0 + 32 + tid; r < nb; r += blockDim.x) {
-            float2 l[32];
-#pragma unroll
-            for (int j = 0; j < 32; j++) l[j] = D[(int64_t)(q0 + j) * lda + r];
-#pragma unroll
-            for (int c = 0; c < 8; c++) {
-                float2 acc = X[c * nb + r];
-                const float2 *xp = X + c * nb + q0;
-#pragma unroll
-                for (int j = 0; j < 32; j++) cfms(acc, l[j], xp[j]);
-                X[c * nb + r] = acc;
-            }
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < 8 * nb; e += blockDim.x) {
-        const int c = e / nb, r = e % nb;
-        const float2 v = X[e];
-        negM[(int64_t)(col0 + c) * nb + r] = make_float2(-v.x, -v.y);
-    }
-}
-
-// In-place triangular step of the recursive block factorisation: rows [lo, lo + nr) (nr a multiple of 32, the
-// factored left part, pivots of each 32-row panel inside that panel) of columns [col0, col0 + ncols) become
-// U = L_S^{-1} P_S ... L_1^{-1} P_1 A (the product form of the left part's panels). CTA b takes 8 columns
-// into shared memory and applies the panels in order, as k_block_linv does for the identity.
-__global__ void __launch_bounds__(512) k_panels_apply(float2 *__restrict__ A, int64_t lda, int64_t lo, int nr,
-                                                      int64_t col0, int ncols, const int32_t *__restrict__ ipiv,
-                                                      int round_tf32) {
-    extern __shared__ __align__(16) float2 X[];  // X[c * nr + r], 8 columns
-    __shared__ float2 Lpp[32][33];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c_first = 8 * blockIdx.x;
-    const int nc = min(8, ncols - c_first);
-    float2 *D = A + lo * lda + lo;  // D[r + c * lda], rows and columns relative to lo
-    for (int e = tid; e < 8 * nr; e += blockDim.x) {
-        const int c = e / nr, r = e % nr;
-        X[e] = (c < nc) ? A[(col0 + c_first + c) * lda + lo + r] : make_float2(0.f, 0.f);
-    }
-    for (int q0 = 0; q0 < nr; q0 += 32) {
-        for (int e = tid; e < 32 * 32; e += blockDim.x) {
-            const int i = e & 31, j = e >> 5;
-            Lpp[i][j] = (i > j) ? D[(int64_t)(q0 + j) * lda + q0 + i] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        if (tid < 8) {
-            float2 *x = X + tid * nr;
-            for (int t = 0; t < 32; t++) {
-                const int r2 = (int)(ipiv[lo + q0 + t] - lo);
-                if (r2 != q0 + t && r2 >= q0 && r2 < q0 + 32) {
-                    const float2 a = x[q0 + t];
-                    x[q0 + t] = x[r2];
-                    x[r2] = a;
-                }
-            }
-        }
-        __syncthreads();
-        if (warp < 8) {
             float2 *x = X + warp * nr + q0;
             float2 v = x[lane];
+            __syncwarp();
+            x[pos] = v;
+            __syncwarp();
+            v = x[lane];
             for (int t = 0; t < 31; t++) {
                 const float2 xt = make_float2(__shfl_sync(0xffffffffu, v.x, t), __shfl_sync(0xffffffffu, v.y, t));
                 if (lane > t) cfms(v, Lpp[lane][t], xt);
@@ -1076,7 +1003,7 @@ __global__ void __launch_bounds__(512) k_panels_apply(float2 *__restrict__ A, in
 #pragma unroll
             for (int j = 0; j < 32; j++) l[j] = D[(int64_t)(q0 + j) * lda + r];
 #pragma unroll
-            for (int c = 0; c < 8; c++) {
+            for (int c = 0; c < CPB; c++) {
                 float2 acc = X[c * nr + r];
                 const float2 *xp = X + c * nr + q0;
 #pragma unroll
@@ -1086,10 +1013,107 @@ __global__ void __launch_bounds__(512) k_panels_apply(float2 *__restrict__ A, in
         }
         __syncthreads();
     }
-    for (int e = tid; e < 8 * nr; e += blockDim.x) {
+}
+
+// For the outer block [b0, b0+nb) (nb a multiple of 32), form negM = -(L_S^{-1} P_S ... L_1^{-1} P_1)
+// restricted to the block's rows; then U12 = -negM A12 for the block's rows of the trailing columns. CTA b
+// forms columns CPB b .. + CPB of the operator by applying the panels to those columns of I; panels before
+// the one holding column CPB b leave them untouched (their rows are zero there).
+template <int CPB>
+__global__ void __launch_bounds__(512) k_block_linv(const float2 *__restrict__ A, int64_t lda, int64_t b0, int nb,
+                                                    const int32_t *__restrict__ ipiv, float2 *__restrict__ negM) {
+    extern __shared__ __align__(16) float2 X[];  // X[c * nb + r], CPB columns
+    __shared__ float2 Lpp[32][33];
+    const int col0 = CPB * blockIdx.x;
+    for (int e = threadIdx.x; e < CPB * nb; e += blockDim.x) {
+        const int c = e / nb, r = e % nb;
+        X[e] = make_float2(r == col0 + c ? 1.f : 0.f, 0.f);
+    }
+    apply_panels_smem<CPB>(X, nb, 32 * (col0 / 32), A + b0 * lda + b0, lda, ipiv, b0, Lpp);
+    for (int e = threadIdx.x; e < CPB * nb; e += blockDim.x) {
+        const int c = e / nb, r = e % nb;
+        const float2 v = X[e];
+        negM[(int64_t)(col0 + c) * nb + r] = make_float2(-v.x, -v.y);
+    }
+}
+
+// In-place triangular step of the recursive block factorisation: rows [lo, lo + nr) (nr a multiple of 32, the
+// factored left part, pivots of each 32-row panel inside that panel) of columns [col0, col0 + ncols) become
+// U = L_S^{-1} P_S ... L_1^{-1} P_1 A (the product form of the left part's panels). CTA b takes CPB columns
+// into shared memory and applies the panels in order. round_tf32: the result is stored rounded to TF32.
+template <int CPB>
+__global__ void __launch_bounds__(512) k_panels_apply(float2 *__restrict__ A, int64_t lda, int64_t lo, int nr,
+                                                      int64_t col0, int ncols, const int32_t *__restrict__ ipiv,
+                                                      int round_tf32) {
+    extern __shared__ __align__(16) float2 X[];  // X[c * nr + r], CPB columns
+    __shared__ float2 Lpp[32][33];
+    const int c_first = CPB * blockIdx.x;
+    const int nc = min(CPB, ncols - c_first);
+    for (int e = threadIdx.x; e < CPB * nr; e += blockDim.x) {
+        const int c = e / nr, r = e % nr;
+        X[e] = (c < nc) ? A[(col0 + c_first + c) * lda + lo + r] : make_float2(0.f, 0.f);
+    }
+    apply_panels_smem<CPB>(X, nr, 0, A + lo * lda + lo, lda, ipiv, lo, Lpp);
+    for (int e = threadIdx.x; e < CPB * nr; e += blockDim.x) {
         const int c = e / nr, r = e % nr;
         if (c < nc) A[(col0 + c_first + c) * lda + lo + r] =
             round_tf32 ? make_float2(tf32_rna(X[e].x), tf32_rna(X[e].y)) : X[e];
+    }
+}
+
+// columns per CTA of the two kernels above: about 128 CTAs for the widths met here (a CTA's panel chain is
+// serial; fewer columns per CTA shorten each of its steps)
+static int apply_cpb(int64_t cols) { return cols >= 1024 ? 8 : cols >= 512 ? 4 : cols >= 256 ? 2 : 1; }
+
+template <int CPB>
+static gdm_status launch_block_linv_t(gdm_ctx *ctx, const float2 *A, int64_t lda, int64_t b0, int nb,
+                                      const int32_t *ipiv, float2 *negM) {
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_block_linv<CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)((size_t)CPB * 1024 * sizeof(float2))));
+        attr = true;
+    }
+    const int bthreads = nb < 256 ? 256 : (nb > 512 ? 512 : nb);  // one thread per row up to 512
+    k_block_linv<CPB><<<(unsigned)(nb / CPB), bthreads, (size_t)CPB * nb * sizeof(float2), ctx->stream>>>(
+        A, lda, b0, nb, ipiv, negM);
+    GDM_LAUNCHED(ctx, "block_linv");
+    return GDM_OK;
+}
+static gdm_status launch_block_linv(gdm_ctx *ctx, const float2 *A, int64_t lda, int64_t b0, int nb,
+                                    const int32_t *ipiv, float2 *negM) {
+    if (nb > 1024 || (nb & 31)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "block operator width %d", nb);
+    switch (apply_cpb(nb)) {
+        case 8: return launch_block_linv_t<8>(ctx, A, lda, b0, nb, ipiv, negM);
+        case 4: return launch_block_linv_t<4>(ctx, A, lda, b0, nb, ipiv, negM);
+        case 2: return launch_block_linv_t<2>(ctx, A, lda, b0, nb, ipiv, negM);
+        default: return launch_block_linv_t<1>(ctx, A, lda, b0, nb, ipiv, negM);
+    }
+}
+
+template <int CPB>
+static gdm_status launch_panels_apply_t(gdm_ctx *ctx, float2 *A, int64_t lda, int64_t lo, int nr, int64_t col0,
+                                        int ncols, const int32_t *ipiv, int round_tf32) {
+    static bool attr = false;
+    if (!attr) {
+        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_panels_apply<CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)((size_t)CPB * 1024 * sizeof(float2))));
+        attr = true;
+    }
+    const int bthreads = nr < 256 ? 256 : (nr > 512 ? 512 : nr);
+    k_panels_apply<CPB><<<(unsigned)((ncols + CPB - 1) / CPB), bthreads, (size_t)CPB * nr * sizeof(float2),
+                          ctx->stream>>>(A, lda, lo, nr, col0, ncols, ipiv, round_tf32);
+    GDM_LAUNCHED(ctx, "panels_apply");
+    return GDM_OK;
+}
+static gdm_status launch_panels_apply(gdm_ctx *ctx, float2 *A, int64_t lda, int64_t lo, int nr, int64_t col0,
+                                      int ncols, const int32_t *ipiv, int round_tf32) {
+    if (nr > 1024 || (nr & 31)) return gdm_fail(ctx, GDM_ERR_INVALID_ARG, "panel application over %d rows", nr);
+    switch (apply_cpb(ncols)) {
+        case 8: return launch_panels_apply_t<8>(ctx, A, lda, lo, nr, col0, ncols, ipiv, round_tf32);
+        case 4: return launch_panels_apply_t<4>(ctx, A, lda, lo, nr, col0, ncols, ipiv, round_tf32);
+        case 2: return launch_panels_apply_t<2>(ctx, A, lda, lo, nr, col0, ncols, ipiv, round_tf32);
+        default: return launch_panels_apply_t<1>(ctx, A, lda, lo, nr, col0, ncols, ipiv, round_tf32);
     }
 }
 
@@ -1543,17 +1567,7 @@ static gdm_status factor_rec(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_
     GDM_TRY(factor_rec(ctx, prec, A, lda, n, lo, mid, ipiv, growth, tcws, tcbytes, lx));
     const int nr = (int)(mid - lo), ncols = (int)(hi - mid);
     GDM_TRY(gdm_phase_begin(ctx, GDM_PH_TRSM));
-    const size_t sm = (size_t)8 * nr * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_panels_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)((size_t)8 * 1024 * sizeof(float2))));
-        attr = true;
-    }
-    const int bthreads = nr < 256 ? 256 : (nr > 512 ? 512 : nr);
-    k_panels_apply<<<(unsigned)((ncols + 7) / 8), bthreads, sm, ctx->stream>>>(A, lda, lo, nr, mid, ncols, ipiv,
-                                                                              lx.Lx != nullptr);
-    GDM_LAUNCHED(ctx, "panels_apply");
+    GDM_TRY(launch_panels_apply(ctx, A, lda, lo, nr, mid, ncols, ipiv, lx.Lx != nullptr));
     GDM_TRY(gdm_phase_end(ctx, GDM_PH_TRSM));
     GDM_TRY(gdm_phase_begin(ctx, GDM_PH_INBLOCK));
     if (lx.Lx) {
@@ -1641,18 +1655,7 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
             // U12 = M A12 with the block operator M = L_S^{-1} P_S ... L_1^{-1} P_1 (one tensor-core GEMM)
             GDM_TRY(gdm_phase_begin(ctx, GDM_PH_U12));
             const int nbi = (int)nb;
-            const size_t sm = (size_t)8 * nbi * sizeof(float2);
-            static bool attr = false;
-            if (!attr) {
-                GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_block_linv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)((size_t)8 * 512 * sizeof(float2))));
-                attr = true;
-            }
-            // 8 warps at least (one per operator column in the panel solve), one thread per row up to 512
-            const int bthreads = nbi < 256 ? 256 : (nbi > 512 ? 512 : nbi);
-            k_block_linv<<<(unsigned)(nbi / 32 * 4), bthreads, sm, ctx->stream>>>(
-                (const float2 *)A, lda, b0, nbi, ipiv, negM);
-            GDM_LAUNCHED(ctx, "block_linv");
+            GDM_TRY(launch_block_linv(ctx, (const float2 *)A, lda, b0, nbi, ipiv, negM));
             const int64_t nc = n - be;
             const int64_t tot = (int64_t)nbi * nc;
             unsigned gb = (unsigned)((tot + 255) / 256);
