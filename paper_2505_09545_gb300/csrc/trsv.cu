@@ -264,8 +264,13 @@ __global__ void __launch_bounds__(256) k_block_w(const float2 *__restrict__ A, i
 // ------------------------------------------------------------------ TMA-fed persistent solve
 // Per CTA (row block j): warps 0..7 compute, warp 8 streams data with the TMA engine into a ring of
 // NSTAGE shared-memory stages of HALF = NBS/2 columns x NBS rows (one half of a 128 x 128 block):
-// first the dependency blocks in processing order, then the block operator. Only the short solution
-// vectors of the dependencies go through ordinary loads.
+// first the dependency blocks in processing order, then the block operator. When a dependency is already
+// published as its stage is issued, the producer also brings its solution vector y_k into that stage (one
+// bulk copy per right-hand side; B's columns 16-byte aligned, a full block), so that the consumers do not
+// stall on a load of y_k between two blocks; a dependency published later (the recent ones, on the chain
+// of the solve) is waited for and loaded by the consumers, so that its blocks are still prefetched. A
+// block is published only after all blocks before it in solve order, so one acquire of a flag covers
+// every earlier dependency too.
 #define TS_NBS 128
 #define TS_HALF 64
 #define TS_NSTAGE 3
@@ -331,6 +336,8 @@ __device__ __forceinline__ void trsv_tma_body(const CUtensorMap *tmAp, int64_t n
     float2 *ring = (float2 *)tsm;  // [NSTAGE][HALF][NBS]
     __shared__ __align__(8) uint64_t full[TS_NSTAGE], empty[TS_NSTAGE];
     __shared__ float2 acc[NBS][NR], yk[NBS][NR], part[NBS][NR];
+    __shared__ __align__(16) float2 ybuf[TS_NSTAGE][NR][NBS];  // y_k of the dependency in each stage
+    __shared__ int ymode[TS_NSTAGE];  // 1: the stage's y_k is in ybuf (set by the producer before its arrive)
     __shared__ int s_ticket, s_dec[2];
     __shared__ volatile int cta_abort;
     const int nblk = (int)((n + NBS - 1) / NBS);
@@ -338,6 +345,11 @@ __device__ __forceinline__ void trsv_tma_body(const CUtensorMap *tmAp, int64_t n
     volatile int *gabort = (volatile int *)(sync_buf + 1);
     volatile int *flags = (volatile int *)(sync_buf + 2);
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    // y_k by bulk copies: every column of B 16-byte aligned (and, per block, a full block)
+    const bool ytma = (((uintptr_t)B & 15) == 0) && ((ldb & 1) == 0);
+    // right-hand sides the bulk copies do not fill stay zero (the copies never write these, so no proxy fence)
+    for (int e = tid; e < TS_NSTAGE * NR * NBS; e += blockDim.x)
+        if ((e / NBS) % NR >= nr_here) (&ybuf[0][0][0])[e] = make_float2(0.f, 0.f);
     if (tid == 0) {
         s_ticket = tk_given >= 0 ? tk_given : atomicAdd(ticket, 1);
         for (int st = 0; st < TS_NSTAGE; st++) {
@@ -366,14 +378,43 @@ __device__ __forceinline__ void trsv_tma_body(const CUtensorMap *tmAp, int64_t n
         // ---------------- producer
         if (lane == 0) {
             int issued = 0;
+            int ypub = -1;  // dependencies known published: solve-order positions <= ypub
             for (int it = 0; it < nitems; it++) {
                 const int st = it % TS_NSTAGE;
                 const uint32_t ph = (uint32_t)((it / TS_NSTAGE) & 1);
                 if (!tmbar_wait(&empty[st], ph ^ 1, &cta_abort, gflags)) break;
                 issued = it + 1;
                 float2 *dst = ring + (size_t)st * HALF * NBS;
-                tmbar_expect_tx(&full[st], TS_STAGE_BYTES);
                 const int half = it & 1;
+                // the dependency this item belongs to (position sk in solve order, block kd), or -1
+                int sk = -1;
+                if (it < 2 * ndep) sk = it / 2;
+                else if (it >= 2 * ndep + 2) sk = tk - 1;
+                const int kd = sk < 0 ? -1 : (fwd ? sk : nblk - 1 - sk);
+                bool ycopy = false;
+                if (kd >= 0 && ytma && (int64_t)(kd + 1) * NBS <= n) {
+                    if (sk <= ypub) {
+                        ycopy = true;
+                    } else {
+                        int f;
+                        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flags + kd) : "memory");
+                        if (f != 0) {
+                            // order the published data (generic proxy) before the bulk copies' reads
+                            asm volatile("fence.proxy.async.global;" ::: "memory");
+                            ypub = sk;
+                            ycopy = true;
+                        }
+                    }
+                }
+                ymode[st] = ycopy ? 1 : 0;
+                if (ycopy) {
+                    tmbar_expect_tx(&full[st], TS_STAGE_BYTES + (uint32_t)(nr_here * NBS * 8));
+                    for (int q = 0; q < nr_here; q++)
+                        bulk1d(&ybuf[st][q][0], B + (int64_t)(rhs0 + q) * ldb + (int64_t)kd * NBS, NBS * 8,
+                               &full[st]);
+                } else {
+                    tmbar_expect_tx(&full[st], TS_STAGE_BYTES);
+                }
                 if (it < 2 * ndep) {
                     const int s = it / 2;
                     const int k = fwd ? s : nblk - 1 - s;
@@ -424,7 +465,9 @@ __device__ __forceinline__ void trsv_tma_body(const CUtensorMap *tmAp, int64_t n
     for (int s = 0; s < nstage; s++) {
         const bool is_op = (s == ndep);
         const bool is_w = (s == ndep + 1);
-        if (!is_op) {
+        // y_k loaded by the consumers (for a half whose stage did not bring it), once per dependency
+        bool have_yk = false;
+        auto load_yk = [&]() -> bool {
             // dependency s, or for is_w (s = tk) the preceding block in solve order, dependency tk - 1
             const int sk = is_w ? s - 1 : s;
             const int k = fwd ? sk : nblk - 1 - sk;
@@ -454,7 +497,7 @@ __device__ __forceinline__ void trsv_tma_body(const CUtensorMap *tmAp, int64_t n
             }
             if (!agree(ok0)) {
                 cta_abort = 1;
-                return;
+                return false;
             }
             for (int e = tid; e < NBS * NR; e += 256) {
                 int rr = e / NR, q = e % NR;
@@ -462,7 +505,8 @@ __device__ __forceinline__ void trsv_tma_body(const CUtensorMap *tmAp, int64_t n
                                                      : make_float2(0.f, 0.f);
             }
             asm volatile("bar.sync 1, 256;" ::: "memory");
-        }
+            return true;
+        };
         float2 sum[NR];
 #pragma unroll
         for (int q = 0; q < NR; q++) sum[q] = make_float2(0.f, 0.f);
@@ -474,8 +518,15 @@ __device__ __forceinline__ void trsv_tma_body(const CUtensorMap *tmAp, int64_t n
                 cta_abort = 1;
                 return;
             }
+            const bool yt = !is_op && ymode[st] != 0;
+            if (!is_op && !yt && !have_yk) {
+                if (!load_yk()) return;
+                have_yk = true;
+            }
             const float2 *sb = ring + (size_t)st * HALF * NBS;  // sb[c * NBS + row]
-            const float2(*src)[NR] = is_op ? acc : yk;
+            // the vector the block multiplies: element (row cc, right-hand side q) at src[cc * srs + q * sqs]
+            const float2 *src = is_op ? &acc[0][0] : (yt ? &ybuf[st][0][0] : &yk[0][0]);
+            const int srs = yt ? 1 : NR, sqs = yt ? NBS : 1;
             if (mode <= 1 || is_op || is_w) {
                 // y_r -= sum_c M[r][c] v[c] (operator: y_r = sum_c Op[r][c] acc[c]; W: sum_c W[r][c] y_pred[c]);
                 // thread (r, hh) takes 32 columns
@@ -486,7 +537,7 @@ __device__ __forceinline__ void trsv_tma_body(const CUtensorMap *tmAp, int64_t n
                     if (herm) m.y = -m.y;
                     const int cc = half * HALF + c;
 #pragma unroll
-                    for (int q = 0; q < NR; q++) cfma(sum[q], m, src[cc][q]);
+                    for (int q = 0; q < NR; q++) cfma(sum[q], m, src[cc * srs + q * sqs]);
                 }
             } else {
                 // acc[c] -= sum_rr conj(M[k0+rr][r0+c]) yk[rr]: 4 threads per column of this half, rows rotated
@@ -500,7 +551,7 @@ __device__ __forceinline__ void trsv_tma_body(const CUtensorMap *tmAp, int64_t n
                     float2 m = sb[c * NBS + rr];
                     m.y = -m.y;
 #pragma unroll
-                    for (int q = 0; q < NR; q++) cfma(cs[q], m, yk[rr][q]);
+                    for (int q = 0; q < NR; q++) cfma(cs[q], m, src[rr * srs + q * sqs]);
                 }
 #pragma unroll
                 for (int q = 0; q < NR; q++)
