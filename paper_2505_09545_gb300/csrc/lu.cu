@@ -631,10 +631,11 @@ __global__ void __launch_bounds__(128) k_panel_local_f32_lx(float2 *__restrict__
 // factorisation, in place of panel, interchange-and-solve of the next panel's top rows, K = 32 update of its
 // columns, and panel. Every CTA
 //   1. factors the first 32 x 32 diagonal block (warp 0),
-//   2. forms the U block right of it, U12 = L11^{-1} P1 A12 (rows in position order; all four warps, eight
-//      columns each, lane = row),
-//   3. brings the second diagonal block's rows up to date (warp 0: their multipliers of the first panel, then
-//      A22 - L21 U12 in FP32) and factors it,
+//   2. forms the U block right of it, U12 = L11^{-1} P1 A12 (rows in position order; warps 1-3, eleven
+//      columns each, lane = row), while warp 0 finds the first panel's multipliers of the second diagonal
+//      block's rows,
+//   3. brings those rows up to date, A22 - L21 U12 in FP32 (all four warps, eight columns each), and factors
+//      the second diagonal block (warp 0),
 // and then takes its share of the rows below: the first panel's multipliers, the row's next 32 columns
 // updated by them and U12 (FP32 products, in place of the K = 32 tensor-core update), and the second panel's
 // multipliers. Pivots, certificate and errors as in the one-panel kernel; the second panel's interchanges
@@ -687,45 +688,62 @@ __global__ void __launch_bounds__(128, 2) k_panel2_f32(float2 *__restrict__ A, i
         for (int c = 0; c < NBP; c++) F1[p][c] = c < p ? Lr[tid][c] : Uz1[p][c];
     }
     __syncthreads();
-    // 2. U12 = L11^{-1} P1 A12: warp w takes columns 8w .. 8w + 8, lane = row (first the interchanges: row q
-    // of the block goes to its position posof[q], then the unit-lower solve by position)
-    {
-        float2 v[8];
+    // 2. U12 = L11^{-1} P1 A12 on warps 1-3 (columns 11 (w - 1) .. + 11, lane = row: first the interchanges,
+    // row q of the block to its position posof[q], then the unit-lower solve by position); meanwhile warp 0
+    // takes the second block's rows through the first panel (their multipliers into L2)
+    if (warp > 0) {
+        constexpr int UC = 11;
+        const int cb = UC * (warp - 1), nc = min(UC, NBP - cb);
+        float2 v[UC];
 #pragma unroll
-        for (int j = 0; j < 8; j++) v[j] = A[(c0 + NBP + 8 * warp + j) * lda + c0 + lane];
+        for (int j = 0; j < UC; j++) v[j] = j < nc ? A[(c0 + NBP + cb + j) * lda + c0 + lane] : make_float2(0.f, 0.f);
         const int p = posof[lane];
 #pragma unroll
-        for (int j = 0; j < 8; j++) Ub[p][8 * warp + j] = v[j];
+        for (int j = 0; j < UC; j++)
+            if (j < nc) Ub[p][cb + j] = v[j];
         __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 8; j++) v[j] = Ub[lane][8 * warp + j];
+        for (int j = 0; j < UC; j++) v[j] = j < nc ? Ub[lane][cb + j] : make_float2(0.f, 0.f);
 #pragma unroll 1
         for (int t = 0; t < NBP - 1; t++) {
             const float2 lt = F1[lane][t];
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
+            for (int j = 0; j < UC; j++) {
                 const float2 xt = make_float2(__shfl_sync(0xffffffffu, v[j].x, t), __shfl_sync(0xffffffffu, v[j].y, t));
                 if (lane > t) cfms(v[j], lt, xt);
             }
         }
 #pragma unroll
-        for (int j = 0; j < 8; j++) Ub[lane][8 * warp + j] = v[j];
-    }
-    __syncthreads();
-    // 3. the second block's rows: first panel's multipliers, update, factorisation
-    if (tid < 32) {
+        for (int j = 0; j < UC; j++)
+            if (j < nc) Ub[lane][cb + j] = v[j];
+    } else {
         float2 r[NBP];
 #pragma unroll
         for (int c = 0; c < NBP; c++) r[c] = A[(c0 + c) * lda + c0 + NBP + lane];
         subst_row32(r, Uz1, invd1, inv_pa1, L2[lane], nullptr, lda, worst);
+    }
+    __syncthreads();
+    // 3. A22 - L21 U12 for the second block's rows (warp w: columns 8w .. 8w + 8, lane = row) into Lr, then its
+    // factorisation from there (warp 0; the factorisation's multipliers overwrite Lr after the row is read)
+    {
+        float2 v[8];
 #pragma unroll
-        for (int c = 0; c < NBP; c++) r[c] = A[(c0 + NBP + c) * lda + c0 + NBP + lane];
-#pragma unroll 2
+        for (int j = 0; j < 8; j++) v[j] = A[(c0 + NBP + 8 * warp + j) * lda + c0 + NBP + lane];
+#pragma unroll 4
         for (int k = 0; k < NBP; k++) {
             const float2 l = L2[lane][k];
 #pragma unroll
-            for (int c = 0; c < NBP; c++) cfms(r[c], l, Ub[k][c]);
+            for (int j = 0; j < 8; j++) cfms(v[j], l, Ub[k][8 * warp + j]);
         }
+#pragma unroll
+        for (int j = 0; j < 8; j++) Lr[lane][8 * warp + j] = v[j];
+    }
+    __syncthreads();
+    if (tid < 32) {
+        float2 r[NBP];
+#pragma unroll
+        for (int c = 0; c < NBP; c++) r[c] = Lr[lane][c];
+        __syncwarp();
         diag_factor_warp(r, NBP, lane, Uz2, Lr, posof, c0 + NBP, ipiv, flags, first);
     }
     __syncthreads();
