@@ -31,7 +31,7 @@ size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec);
 gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_t ldc, int64_t r0, int64_t c0,
                              const float2 *L, int64_t ldl, const float2 *U, int64_t ldu, int64_t u_r0, int64_t u_c0,
                              int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof,
-                             int u_is_tf32);
+                             int u_is_tf32, int out_mode = 0);
 gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t lda, int64_t n, int64_t r0, int64_t c0,
                          int64_t k0, int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof);
 gdm_status gdm_tc_update_lx(gdm_ctx *ctx, float2 *C, int64_t ldc, int64_t r0, int64_t c0, const float *Lx,
@@ -1147,18 +1147,18 @@ __global__ void k_round_tf32_block(float2 *__restrict__ A, int64_t lda, int64_t 
     }
 }
 
-// T[i + c * nb] = A[b0 + i, c0 + c] and zero the source (the U12 GEMM accumulates into it)
-// round_tf32: T rounded to TF32 (nearest), for the single-product updates whose tensor cores would otherwise
-// truncate it
+// T[i + c * nb] = A[b0 + i, c0 + c], and with zero_src the source zeroed (for a U12 GEMM that accumulates
+// into it; the store-only one overwrites it). round_tf32: T rounded to TF32 (nearest), for the single-product
+// updates whose tensor cores would otherwise truncate it
 __global__ void k_gather_zero(float2 *__restrict__ A, int64_t lda, int64_t b0, int64_t c0, int nb, int64_t nc,
-                              float2 *__restrict__ T, int round_tf32) {
+                              float2 *__restrict__ T, int round_tf32, int zero_src) {
     const int64_t total = (int64_t)nb * nc;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = e / nb, i = e % nb;
         float2 *a = A + (c0 + c) * lda + b0 + i;
         const float2 v = *a;
         T[e] = round_tf32 ? make_float2(tf32_rna(v.x), tf32_rna(v.y)) : v;
-        *a = make_float2(0.f, 0.f);
+        if (zero_src) *a = make_float2(0.f, 0.f);
     }
 }
 
@@ -1678,15 +1678,28 @@ static gdm_status lu_factor_t(gdm_ctx *ctx, gdm_precision prec, C *A, int64_t n,
             const int64_t tot = (int64_t)nbi * nc;
             unsigned gb = (unsigned)((tot + 255) / 256);
             if (gb > (unsigned)(8 * ctx->sm_count)) gb = 8 * ctx->sm_count;
-            k_gather_zero<<<gb, 256, 0, ctx->stream>>>((float2 *)A, lda, b0, be, nbi, nc, T12,
-                                                       prec != GDM_FP32 && !getenv("GDM_TC_TRUNCATE"));
+            const int tf32_in = prec != GDM_FP32 && !getenv("GDM_TC_TRUNCATE");
+            // the store-only product writes U12 over the block's rows (rounded to TF32 for the trailing update
+            // on the embedding path); where it does not apply, the rows are zeroed and the product accumulated
+            const bool store = tf32_in && !getenv("GDM_U12_ACCUMULATE");
+            k_gather_zero<<<gb, 256, 0, ctx->stream>>>((float2 *)A, lda, b0, be, nbi, nc, T12, tf32_in, !store);
             GDM_LAUNCHED(ctx, "gather_zero");
-            GDM_TRY(gdm_tc_update_ext(ctx, prec, (float2 *)A, lda, b0, be, negM, nbi, T12, nbi, 0, 0, nbi, nc, nbi,
-                                      tcws, tcbytes, 0,
-                                      prec != GDM_FP32 && !getenv("GDM_TC_TRUNCATE")));
-            if (lx.Lx) {
-                k_round_tf32_block<<<gb, 256, 0, ctx->stream>>>((float2 *)A, lda, b0, nbi, be, nc);
-                GDM_LAUNCHED(ctx, "round_tf32_block");
+            gdm_status s = GDM_ERR_UNSUPPORTED;
+            if (store)
+                s = gdm_tc_update_ext(ctx, prec, (float2 *)A, lda, b0, be, negM, nbi, T12, nbi, 0, 0, nbi, nc, nbi,
+                                      tcws, tcbytes, 0, tf32_in, lx.Lx ? 2 : 1);
+            if (s == GDM_ERR_UNSUPPORTED) {
+                if (store)
+                    GDM_CUDA_TRY(ctx, cudaMemset2DAsync((float2 *)A + be * lda + b0, (size_t)lda * sizeof(float2), 0,
+                                                        (size_t)nbi * sizeof(float2), (size_t)nc, ctx->stream));
+                GDM_TRY(gdm_tc_update_ext(ctx, prec, (float2 *)A, lda, b0, be, negM, nbi, T12, nbi, 0, 0, nbi, nc,
+                                          nbi, tcws, tcbytes, 0, tf32_in));
+                if (lx.Lx) {
+                    k_round_tf32_block<<<gb, 256, 0, ctx->stream>>>((float2 *)A, lda, b0, nbi, be, nc);
+                    GDM_LAUNCHED(ctx, "round_tf32_block");
+                }
+            } else {
+                GDM_TRY(s);
             }
             GDM_TRY(gdm_phase_end(ctx, GDM_PH_U12));
         } else if (be < n) {

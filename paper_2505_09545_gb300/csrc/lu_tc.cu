@@ -809,9 +809,17 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
 
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 // BF16: the same tiles with BF16 operands (64 elements = 128 bytes per stage row, MMA K = 16), for the
 // GDM_BF16_REFINE trailing update; the operands are BF16 copies prepared by k_prep_lx_bf16 / k_u_to_bf16.
-template <bool BF16>
+// MODE 0: C -= A B; MODE 1: C = -A B and MODE 2: C = -A B rounded to TF32 (nearest), both without loading C
+// (the U12 product, U12 = -negM A12, written over the block's rows of the trailing columns).
+template <bool BF16, int MODE = 0>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     k_tc_update_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmC, int cx0, int cy0, int M, int N, int K, int bx0, int by0,
@@ -987,7 +995,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 ld_lt++;
             }
         };
-        if (eleader)
+        if (MODE == 0 && eleader)
             for (int g = 0; g < P_NCB / 2 && g < total; g++) issue_load(g);
         int g = 0;
         const int row = q * 32 + lane;
@@ -1016,11 +1024,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 const int cb = g % P_NCB;
                 ok = true;
                 if (eleader) {
-                    if (g + P_NCB / 2 < total) {
-                        bulk_wait_read<P_NCB - P_NCB / 2 - 1>();
-                        issue_load(g + P_NCB / 2);
+                    if (MODE == 0) {
+                        if (g + P_NCB / 2 < total) {
+                            bulk_wait_read<P_NCB - P_NCB / 2 - 1>();
+                            issue_load(g + P_NCB / 2);
+                        }
+                        ok = mbar_wait(&cbar[cb], (uint32_t)((g / P_NCB) & 1), abort_flag, gflags);
+                    } else {
+                        // the store that last used buffer cb (chunk g - P_NCB) has read it
+                        bulk_wait_read<P_NCB - 1>();
                     }
-                    ok = mbar_wait(&cbar[cb], (uint32_t)((g / P_NCB) & 1), abort_flag, gflags);
                 }
                 float v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * PBN + ch * 32), v);
@@ -1029,8 +1042,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                     break;
                 }
                 float *buf = cbuf + (size_t)cb * (P_CB_BYTES / 4);
+                if (MODE == 0) {
 #pragma unroll
-                for (int j = 0; j < 32; j++) buf[j * 128 + row] -= v[j];
+                    for (int j = 0; j < 32; j++) buf[j * 128 + row] -= v[j];
+                } else if (MODE == 1) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) buf[j * 128 + row] = -v[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) buf[j * 128 + row] = tf32_round(-v[j]);
+                }
                 fence_proxy_async_smem();
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (eleader) {
@@ -1058,11 +1079,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------- operand preparation
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
 
 // Lx[(2i+c) * K' + 2k + c'] from L = A21 (complex column-major at L, ld lda), rows i < m, cols k < nb.
 // SPLIT = 3 writes the TF32 hi part to Lx and the remainder to Llo.
@@ -1272,15 +1288,23 @@ template <bool BF16> int max_pairs(gdm_ctx *ctx) {
     return cached;
 }
 
-template <bool BF16>
+template <bool BF16, int MODE = 0>
 gdm_status launch_update_pair(gdm_ctx *ctx, const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &cm,
                               int cx0, int cy0, int M, int N, int K, int bx0, int by0) {
     const int np = max_pairs<BF16>(ctx);  // raises the kernel's shared-memory limit on first use
     if (np < 1) return GDM_ERR_UNSUPPORTED;
+    if (MODE != 0) {
+        static bool attr = false;
+        if (!attr) {
+            GDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_update_pair<BF16, MODE>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM));
+            attr = true;
+        }
+    }
     const int ntiles = ((M + PBM - 1) / PBM) * ((N + PBN - 1) / PBN);
     const int pairs = ntiles < np ? ntiles : np;
-    k_tc_update_pair<BF16><<<2 * pairs, NTHREADS, P_SMEM, ctx->stream>>>(a, b, cm, cx0, cy0, M, N, K, bx0, by0,
-                                                                          ctx->dflags);
+    k_tc_update_pair<BF16, MODE><<<2 * pairs, NTHREADS, P_SMEM, ctx->stream>>>(a, b, cm, cx0, cy0, M, N, K, bx0,
+                                                                                by0, ctx->dflags);
     GDM_LAUNCHED(ctx, BF16 ? "tc_update_pair_bf16" : "tc_update_pair");
     return GDM_OK;
 }
@@ -1301,11 +1325,13 @@ size_t gdm_tc_workspace_bytes(int64_t n, int64_t nb, gdm_precision prec) {
 // < c0+Nc), so columns and rows outside it are never written. prof = 1 records the launch as the
 // factorisation's dominant kernel (gdm_profile_enable). Single-product (TF32) updates read both operands
 // rounded to TF32 (nearest): Lx by its preparation, U through a rounded copy unless u_is_tf32 says that U
-// holds TF32 values already.
+// holds TF32 values already. out_mode 1 writes C = -L U and 2 writes C = -L U rounded to TF32 (nearest),
+// neither reading C: only the single-product update on CTA pairs does this; GDM_ERR_UNSUPPORTED (nothing
+// launched) where that kernel does not apply.
 gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_t ldc, int64_t r0, int64_t c0,
                              const float2 *L, int64_t ldl, const float2 *U, int64_t ldu, int64_t u_r0, int64_t u_c0,
                              int64_t Mc, int64_t Nc, int64_t Kc, void *ws, size_t ws_bytes, int prof,
-                             int u_is_tf32) {
+                             int u_is_tf32, int out_mode) {
     if (prec == GDM_FP64) return GDM_ERR_UNSUPPORTED;
     if (Mc <= 0 || Nc <= 0 || Kc <= 0) return GDM_OK;
     if (getenv("GDM_TC_DISABLE")) return GDM_ERR_UNSUPPORTED;
@@ -1313,6 +1339,9 @@ gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_
         return GDM_ERR_UNSUPPORTED;
     const int split = (prec == GDM_FP32) ? 3 : 1;
     const int M = (int)(2 * Mc), N = (int)Nc, K = (int)(2 * Kc);
+    if (out_mode != 0 && (split != 1 || (prec == GDM_BF16_REFINE && prof) || M < PBM || N < 2 * PBN ||
+                          getenv("GDM_TC_SINGLE") || max_pairs<false>(ctx) < 1))
+        return GDM_ERR_UNSUPPORTED;
     if (prec == GDM_BF16_REFINE && prof && M >= PBM && N >= 2 * PBN && !getenv("GDM_TC_SINGLE") &&
         max_pairs<true>(ctx) >= 1) {
         // the trailing update in BF16 on CTA pairs; BF16 copies of the embedded L panel and of U12
@@ -1393,10 +1422,16 @@ gdm_status gdm_tc_update_ext(gdm_ctx *ctx, gdm_precision prec, float2 *C, int64_
         if (!ok) return gdm_fail(ctx, GDM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         if (prof) GDM_TRY(gdm_prof_begin(ctx, &slot));
         gdm_status st = GDM_ERR_UNSUPPORTED;
-        if (pair)
-            st = Ut ? launch_update_pair<false>(ctx, ta0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, 0, 0)
-                    : launch_update_pair<false>(ctx, ta0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, (int)(2 * u_r0),
-                                                (int)u_c0);
+        if (pair) {
+            const int bx = Ut ? 0 : (int)(2 * u_r0), by = Ut ? 0 : (int)u_c0;
+            if (out_mode == 1)
+                st = launch_update_pair<false, 1>(ctx, ta0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, bx, by);
+            else if (out_mode == 2)
+                st = launch_update_pair<false, 2>(ctx, ta0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, bx, by);
+            else
+                st = launch_update_pair<false>(ctx, ta0, tb0, tc, (int)(2 * r0), (int)c0, M, N, K, bx, by);
+        }
+        if (st == GDM_ERR_UNSUPPORTED && out_mode != 0) return GDM_ERR_UNSUPPORTED;
         if (st == GDM_ERR_UNSUPPORTED) {
             if (pair) {
                 ok = Ut ? make_map(&tb0, Ut, K, N, K, 256)
@@ -1421,7 +1456,7 @@ gdm_status gdm_tc_update(gdm_ctx *ctx, gdm_precision prec, float2 *A, int64_t ld
     (void)n;
     if ((k0 & 1)) return GDM_ERR_UNSUPPORTED;
     return gdm_tc_update_ext(ctx, prec, A, lda, r0, c0, A + k0 * lda + r0, lda, A, lda, k0, c0, Mc, Nc, Kc, ws,
-                             ws_bytes, prof, 0);
+                             ws_bytes, prof, 0, 0);
 }
 
 // A22 -= A21 U12 for the block [b0, b0+nb) of the complex64 matrix A (n x n, lda).

@@ -255,7 +255,7 @@ def test_lu_factor_quality(G, ctx, prec, tol_plain, max_iters):
 
 
 @pytest.mark.parametrize("prec,switch", [("tf32", None), ("tf32", "GDM_LU_PREP_L"), ("tf32", "GDM_PANEL_SINGLE"),
-                                         ("fp32", None), ("fp32", "GDM_PANEL_SINGLE")])
+                                         ("tf32", "GDM_U12_ACCUMULATE"), ("fp32", None), ("fp32", "GDM_PANEL_SINGLE")])
 def test_recursive_block_factorisation(G, ctx, prec, switch, monkeypatch):
     """The recursive in-block factorisation (used from n = 8192 on; forced here at 3N = 2100: four full
     512-column blocks split 256/128/64 down to pairs of 32-column panels, and a ragged 52-column last
@@ -263,7 +263,10 @@ def test_recursive_block_factorisation(G, ctx, prec, switch, monkeypatch):
     path. Each 64-column leaf runs as one two-panel launch (its K = 32 update in FP32 inside the kernel);
     GDM_PANEL_SINGLE takes the one-panel launches with the interchange pass and the tensor-core update
     between them. At TF32 the panels write L's embedding for the updates and U is rounded in storage;
-    GDM_LU_PREP_L takes the path that prepares both operands before each update instead."""
+    GDM_LU_PREP_L takes the path that prepares both operands before each update instead. U12 is written by
+    a store-only tensor-core product (rounded to TF32 in its epilogue) where the CTA-pair kernel applies
+    (the first three blocks here) and by zeroing plus an accumulating product elsewhere (the last one);
+    GDM_U12_ACCUMULATE takes the second form for every block."""
     monkeypatch.setenv("GDM_LU_RECURSIVE", "1")
     if switch:
         monkeypatch.setenv(switch, "1")
