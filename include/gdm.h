@@ -163,6 +163,12 @@ int64_t gdm_launch_count(gdm_ctx *ctx);
  * refinement vectors). */
 gdm_status gdm_workspace_size(const gdm_problem *p, int n_rhs, gdm_precision prec, size_t *bytes);
 
+/* The quantity a refinement compares with tol after a step whose largest relative correction over the
+ * right-hand sides was c, the step before having had c_prev (<= 0: no step before): c itself, or, with
+ * GDM_SOLVE_ERR_ESTIMATE in flags and a clear contraction rho = c / c_prev <= 1/4, the estimated relative
+ * error left after the step, rho c / (1 - rho). Host-only (the rule gdm_solve and gdm_solve_batched apply). */
+double gdm_refine_stop_measure(double c, double c_prev, int32_t flags);
+
 /* ---------------------------------------------------------------- polarisabilities */
 
 /* Effective electric/magnetic dipole polarisabilities from Lorentzian lines (Sec.

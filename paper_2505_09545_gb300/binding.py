@@ -93,6 +93,7 @@ _SIGS = {
     "gdm_last_error": ([P], C.c_char_p),
     "gdm_launch_count": ([P], I64),
     "gdm_workspace_size": ([C.POINTER(Problem), C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+    "gdm_refine_stop_measure": ([C.c_double, C.c_double, C.c_int32], C.c_double),
     "gdm_incident_planewave": ([P, P, I64, D, D, PD, PD, C.c_int, C.c_int, P], C.c_int),
     "gdm_assemble": ([P, C.POINTER(Problem), C.c_int, P, I64], C.c_int),
     "gdm_solve": ([P, C.POINTER(Problem), C.c_int, P, I64, P, P, P, C.c_int, C.POINTER(SolveOpts),

@@ -336,6 +336,16 @@ static gdm_status check_lda(gdm_ctx *ctx, int64_t n_sys, int64_t lda) {
 
 extern "C" {
 
+// c itself, or with GDM_SOLVE_ERR_ESTIMATE and a clear contraction (rho = c / c_prev <= 1/4) the geometric
+// tail rho c / (1 - rho) of the corrections still to come, i.e. the relative error left after this step
+double gdm_refine_stop_measure(double c, double c_prev, int32_t flags) {
+    if ((flags & GDM_SOLVE_ERR_ESTIMATE) && c_prev > 0.0 && c >= 0.0) {
+        const double rho = c / c_prev;
+        if (rho <= 0.25) return rho * c / (1.0 - rho);
+    }
+    return c;
+}
+
 gdm_status gdm_workspace_size(const gdm_problem *p, int n_rhs, gdm_precision prec, size_t *bytes) {
     if (!p || !bytes || n_rhs < 1) return GDM_ERR_INVALID_ARG;
     int64_t ns = p->n * p->kind;

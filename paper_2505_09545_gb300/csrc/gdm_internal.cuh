@@ -111,18 +111,6 @@ gdm_status gdm_pinned(gdm_ctx *ctx, size_t bytes, void **ptr);
 gdm_status gdm_upload(gdm_ctx *ctx, const void *host, size_t bytes, void **dev);
 static inline void gdm_params_reset(gdm_ctx *ctx) { ctx->param_off = 0; }
 
-// The quantity the refinements compare with tol after a step whose largest relative correction was c (the
-// step before: c_prev, <= 0 if none): c itself, or with GDM_SOLVE_ERR_ESTIMATE and a clear contraction
-// (rho = c / c_prev <= 1/4) the geometric tail rho c / (1 - rho) of the corrections still to come, i.e. the
-// relative error left in X after this step.
-static inline double gdm_refine_stop_measure(double c, double c_prev, int flags) {
-    if ((flags & GDM_SOLVE_ERR_ESTIMATE) && c_prev > 0.0 && c >= 0.0) {
-        const double rho = c / c_prev;
-        if (rho <= 0.25) return rho * c / (1.0 - rho);
-    }
-    return c;
-}
-
 // carve sub-buffers out of one scratch block
 struct ScratchCarver {
     char *base;

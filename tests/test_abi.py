@@ -88,3 +88,27 @@ def test_batched_and_autotune_reject_a_null_context(lib):
     assert lib.gdm_autotune(None, 2, None, 0, None) == 1
     assert lib.gdm_backward_batched(None, 2, None, 0, 0, None, None, None) == 1
     assert lib.gdm_solve_gmres(None, 2, None, None, None, 1, None, None) == 1
+
+
+def test_refine_stop_measure_is_host_only(lib):
+    """The refinements' stopping measure: with GDM_SOLVE_ERR_ESTIMATE and corrections contracting by
+    rho = c / c_prev <= 1/4, the tail rho c / (1 - rho) of the corrections still to come; else (no flag, no
+    step before, or rho above 1/4) the last correction itself. On an exactly geometric sequence of
+    corrections the measure equals the sum of all later corrections."""
+    from paper_2505_09545_gb300 import binding
+    f = lib.gdm_refine_stop_measure
+    E = binding.SOLVE_ERR_ESTIMATE
+    # corrections measured on the 40 x 30 x 10 cuboid after steps 2 and 3
+    c, p = 5.981e-10, 1.441e-6
+    rho = c / p
+    assert f(c, p, E) == pytest.approx(rho * c / (1 - rho), rel=1e-15)
+    assert f(c, p, E) < 1e-10 < c
+    assert f(c, p, 0) == c
+    assert f(c, -1.0, E) == c
+    assert f(0.3, 1.0, E) == 0.3
+    assert f(0.25, 1.0, E) == pytest.approx(0.25 * 0.25 / 0.75, rel=1e-15)
+    assert f(0.0, 1e-9, E) == 0.0
+    c0, q = 1e-3, 1e-2
+    for k in range(1, 5):
+        tail = sum(c0 * q ** j for j in range(k + 1, 60))
+        assert f(c0 * q ** k, c0 * q ** (k - 1), E) == pytest.approx(tail, rel=1e-12)
