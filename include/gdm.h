@@ -159,8 +159,10 @@ const char *gdm_last_error(gdm_ctx *ctx);
 int64_t gdm_launch_count(gdm_ctx *ctx);
 
 /* Scratch bytes a gdm_solve / gdm_backward of this problem will hold in the
- * context (pivot-independent panel buffers, tensor-core operand copies,
- * refinement vectors). */
+ * context (pivot-independent panel buffers, tensor-core operand buffers and the
+ * embedding of L, the U12 block operator, refinement vectors; the factorisation and
+ * the refinement share one arena, so this is the larger of the two), for the default
+ * outer block width. */
 gdm_status gdm_workspace_size(const gdm_problem *p, int n_rhs, gdm_precision prec, size_t *bytes);
 
 /* The quantity a refinement compares with tol after a step whose largest relative correction over the

@@ -349,13 +349,24 @@ double gdm_refine_stop_measure(double c, double c_prev, int32_t flags) {
 gdm_status gdm_workspace_size(const gdm_problem *p, int n_rhs, gdm_precision prec, size_t *bytes) {
     if (!p || !bytes || n_rhs < 1) return GDM_ERR_INVALID_ARG;
     int64_t ns = p->n * p->kind;
+    // refinement: vectors, Green-sum partials, solve operators and flags (the arena the factorisation used)
     size_t vec = (size_t)ns * n_rhs * 16;
     size_t b = 6 * vec + 64 * 1024;
+    if (prec != GDM_FP64) b += (size_t)ns * n_rhs * 8;
+    b += (size_t)ns * 64 * 16;
     if (prec != GDM_FP64) {
-        // tensor-core operand copies: L panel (hi/lo, 2x embedded) and U row block (hi/lo)
-        b += (size_t)ns * 256 * 4 * 4 + (size_t)ns * 512 * 4 * 2 + (size_t)ns * n_rhs * 8;
+        // factorisation at the default outer block width (an upper bound for the size-class widths): panel
+        // candidates, the tensor-core operand buffers (embedded L panel and a U12 copy; the FP32 split
+        // doubles both), the U12 block operator and row block, and for the recursive TF32 factorisation
+        // (3N >= 8192) the embedding of L that its panels write
+        const int64_t nb = gdm_lu_block(nullptr, prec, ns);
+        const size_t lx = (size_t)2 * ns * 2 * nb * 4, u = (size_t)ns * 2 * nb * 4;
+        size_t f = (size_t)2 * 256 * (16 + 32 * 8) + 64 * 1024;
+        f += (prec == GDM_FP32 ? 2 * lx + 2 * u : lx + u) + 4096;
+        if (nb <= 512) f += (size_t)nb * nb * 8 + (size_t)nb * ns * 8;
+        if (prec == GDM_TF32_REFINE && ns >= 8192 && nb <= 512) f += lx;
+        if (f > b) b = f;
     }
-    b += (size_t)ns * 64 * 16;  // panel factorisation candidates and pivots
     *bytes = b;
     return GDM_OK;
 }

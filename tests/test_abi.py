@@ -51,6 +51,12 @@ def test_workspace_size_is_host_only(lib):
     b = C.c_size_t(0)
     assert lib.gdm_workspace_size(C.byref(p), 2, 1, C.byref(b)) == 0
     assert b.value > 36000 * 2 * 16
+    # TF32 at 3N = 36,000: the recursive factorisation's L embedding (2 x 36,000 x 2 x 512 FP32), the
+    # tensor-core operand buffers of the same size plus a U12 copy, and the U12 block operator's row block
+    b32 = C.c_size_t(0)
+    assert lib.gdm_workspace_size(C.byref(p), 2, binding.PRECISION["tf32"], C.byref(b32)) == 0
+    emb = 2 * 36000 * 2 * 512 * 4
+    assert b32.value >= 2 * emb + 36000 * 2 * 512 * 4 + 512 * 36000 * 8
 
 
 def test_built_for_sm103a():
